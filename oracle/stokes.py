@@ -1,0 +1,149 @@
+"""Stokes kernels and the Nystrom matrix of the interior double-layer BIE.
+
+Sec. 2, with mu = 1 and r = x - y, n_y the outward normal at the source:
+
+* Stokeslet (Eq. stokeslet):  S(x, y) = 1/(4 pi) (-log|r| I + r r^T / |r|^2).
+* Double layer:               D(x, y) = 1/pi (r r^T / |r|^2) (r . n_y) / |r|^2.
+* Interior BIE (Eq. interior_BIE): -1/2 tau + D tau = g; the rank-one
+  nullspace is removed by N tau = n_x int tau . n_y ds_y (Remark 2.1,
+  Eq. null), giving A = -1/2 I + D + N (Eq. interior_BIE_discretized2).
+
+Nystrom discretisation (readings where the paper is silent):
+* off-diagonal 2x2 block (i != j):  w_j D(x_i, x_j) + w_j n_i n_j^T;
+* diagonal block: -1/2 I - (kappa_i w_i / (2 pi)) t_i t_i^T + w_i n_i n_i^T,
+  the smooth limit of the double-layer kernel on the curve (the 2D Stokes
+  double layer is smooth on a smooth curve, so no singular quadrature).
+* degrees of freedom interleaved: (x-component, y-component) per point.
+
+Interior velocity (Sec. 2.1): u(x) = sum_j w_j D(x, y_j) tau_j (no N term).
+"""
+import numpy as np
+
+
+def stokeslet_velocity(tx, ty, sx, sy, f):
+    """u at targets (tx, ty) from point forces f (ns x 2 or ns x 2 x nrhs) at
+    (sx, sy).  Returns array (nt, 2) or (nt, 2, nrhs)."""
+    f = np.asarray(f, dtype=np.float64)
+    squeeze = f.ndim == 2
+    if squeeze:
+        f = f[:, :, None]
+    rx = np.asarray(tx)[:, None] - np.asarray(sx)[None, :]
+    ry = np.asarray(ty)[:, None] - np.asarray(sy)[None, :]
+    r2 = rx * rx + ry * ry
+    lg = -0.5 * np.log(r2)
+    c = 1.0 / (4.0 * np.pi)
+    # u_a = sum_s c * ( -log r f_a + r_a (r . f) / r^2 )
+    fx, fy = f[:, 0, :], f[:, 1, :]                       # (ns, nrhs)
+    rdotf = rx[:, :, None] * fx[None] + ry[:, :, None] * fy[None]
+    ux = c * np.sum(lg[:, :, None] * fx[None] + rx[:, :, None] * rdotf / r2[:, :, None], axis=1)
+    uy = c * np.sum(lg[:, :, None] * fy[None] + ry[:, :, None] * rdotf / r2[:, :, None], axis=1)
+    u = np.stack([ux, uy], axis=1)
+    return u[:, :, 0] if squeeze else u
+
+
+def boundary_data(nodes, sx, sy, f):
+    """g at the nodes (interleaved, length 2N, or 2N x nrhs)."""
+    u = stokeslet_velocity(nodes["x"], nodes["y"], sx, sy, f)
+    if u.ndim == 2:
+        return u.reshape(-1)
+    return u.reshape(-1, u.shape[2])
+
+
+def matrix(nodes):
+    """Dense A = -1/2 I + D + N on a node set (2N x 2N, interleaved)."""
+    x, y = nodes["x"], nodes["y"]
+    nx, ny, w, kap = nodes["nx"], nodes["ny"], nodes["w"], nodes["kappa"]
+    N = x.size
+    rx = x[:, None] - x[None, :]
+    ry = y[:, None] - y[None, :]
+    r2 = rx * rx + ry * ry
+    np.fill_diagonal(r2, 1.0)
+    rdn = rx * nx[None, :] + ry * ny[None, :]
+    fac = w[None, :] * rdn / (np.pi * r2 * r2)
+    Dxx, Dxy, Dyy = fac * rx * rx, fac * rx * ry, fac * ry * ry
+    # diagonal: smooth limit -(kappa w / 2 pi) t t^T with t = (-ny, nx)
+    d = -kap * w / (2.0 * np.pi)
+    ii = np.arange(N)
+    Dxx[ii, ii] = d * ny * ny
+    Dxy[ii, ii] = -d * nx * ny
+    Dyy[ii, ii] = d * nx * nx
+    A = np.empty((2 * N, 2 * N))
+    A[0::2, 0::2] = Dxx + nx[:, None] * nx[None, :] * w[None, :]
+    A[0::2, 1::2] = Dxy + nx[:, None] * ny[None, :] * w[None, :]
+    A[1::2, 0::2] = Dxy + ny[:, None] * nx[None, :] * w[None, :]
+    A[1::2, 1::2] = Dyy + ny[:, None] * ny[None, :] * w[None, :]
+    A[np.arange(2 * N), np.arange(2 * N)] -= 0.5
+    return A
+
+
+def cross_matrix(rows, cols):
+    """A restricted to rows of one node set and columns of a disjoint one:
+    w_j D(x_i, y_j) + w_j n_i n_j^T (no diagonal terms)."""
+    rx = rows["x"][:, None] - cols["x"][None, :]
+    ry = rows["y"][:, None] - cols["y"][None, :]
+    r2 = rx * rx + ry * ry
+    rdn = rx * cols["nx"][None, :] + ry * cols["ny"][None, :]
+    wj = cols["w"][None, :]
+    fac = wj * rdn / (np.pi * r2 * r2)
+    M = np.empty((2 * rows["x"].size, 2 * cols["x"].size))
+    ni = (rows["nx"][:, None], rows["ny"][:, None])
+    nj = (cols["nx"][None, :], cols["ny"][None, :])
+    rr = (rx, ry)
+    for a in range(2):
+        for b in range(2):
+            M[a::2, b::2] = fac * rr[a] * rr[b] + ni[a] * nj[b] * wj
+    return M
+
+
+def velocity(nodes, tau, tx, ty):
+    """Interior velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets.
+
+    tau: interleaved density (2N) or (2N x nrhs).  Returns (nt, 2[, nrhs])."""
+    tau = np.asarray(tau, dtype=np.float64)
+    squeeze = tau.ndim == 1
+    if squeeze:
+        tau = tau[:, None]
+    rx = np.asarray(tx)[:, None] - nodes["x"][None, :]
+    ry = np.asarray(ty)[:, None] - nodes["y"][None, :]
+    r2 = rx * rx + ry * ry
+    rdn = rx * nodes["nx"][None, :] + ry * nodes["ny"][None, :]
+    fac = nodes["w"][None, :] * rdn / (np.pi * r2 * r2)
+    tx_, ty_ = tau[0::2, :], tau[1::2, :]
+    rdt = rx[:, :, None] * tx_[None] + ry[:, :, None] * ty_[None]
+    ux = np.einsum("ij,ijr->ir", fac * rx, rdt)
+    uy = np.einsum("ij,ijr->ir", fac * ry, rdt)
+    u = np.stack([ux, uy], axis=1)
+    return u[:, :, 0] if squeeze else u
+
+
+def apply_rows(nodes, tau, rows):
+    """(A tau)[rows] for selected interleaved DOFs, one row at a time.
+
+    Used to check full-size results on sampled rows.  tau is 2N (or 2N x nrhs);
+    rows are DOF indices.  Each row is the definition of A written out."""
+    tau = np.asarray(tau, dtype=np.float64)
+    squeeze = tau.ndim == 1
+    if squeeze:
+        tau = tau[:, None]
+    out = np.empty((len(rows), tau.shape[1]))
+    x, y = nodes["x"], nodes["y"]
+    nx, ny, w, kap = nodes["nx"], nodes["ny"], nodes["w"], nodes["kappa"]
+    flux = (w * nx) @ tau[0::2, :] + (w * ny) @ tau[1::2, :]   # int tau . n ds
+    for r, dof in enumerate(rows):
+        i, a = divmod(int(dof), 2)
+        rx = x[i] - x
+        ry = y[i] - y
+        r2 = rx * rx + ry * ry
+        r2[i] = 1.0
+        rdn = rx * nx + ry * ny
+        fac = w * rdn / (np.pi * r2 * r2)
+        ra = rx if a == 0 else ry
+        row_x = fac * ra * rx
+        row_y = fac * ra * ry
+        t = (-ny[i], nx[i])
+        dk = -kap[i] * w[i] / (2.0 * np.pi)
+        row_x[i] = dk * t[a] * t[0]
+        row_y[i] = dk * t[a] * t[1]
+        na = nx[i] if a == 0 else ny[i]
+        out[r] = row_x @ tau[0::2, :] + row_y @ tau[1::2, :] + na * flux - 0.5 * tau[dof, :]
+    return out[:, 0] if squeeze else out
