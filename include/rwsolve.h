@@ -1,0 +1,174 @@
+/*
+ * rwsolve -- refined-wall Stokes solver for GB300 (sm_103a).
+ *
+ * Fast direct solve of the interior Stokes double-layer boundary integral
+ * equation on a locally refined wall, after Zhang, Gillman and Veerapaneni,
+ * "A fast direct solver for integral equations on locally refined boundary
+ * discretizations" (arXiv 2108.07205):
+ *
+ *   A = -1/2 I + D + N                      (Sec. 2, Eq. interior_BIE_discretized2)
+ *   A_ext = A~ + Q,  A~ = blkdiag(A_oo, A_pp)   (Sec. 3.2, Eq. extendedlLinearSystem)
+ *   tau_ext = A~^{-1} g - A~^{-1} L (I + R A~^{-1} L)^{-1} R A~^{-1} g   (Eq. wood)
+ *
+ * with A_oo^{-1} a hierarchically block separable (HBS) compressed inverse of
+ * the reference wall built once (rw_hbs_build), Q ~= L R the uniform row-ID
+ * factorisation of Sec. 3.3-3.4 built per refinement (rw_refine_factor), and
+ * Algorithm 1's solve (rw_solve).
+ *
+ * Conventions (all calls):
+ *  - mu = 1; r = x - y; degrees of freedom interleaved (x, y) per point.
+ *  - FP64 arrays; column-major with leading dimension = number of rows.
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; host buffers are copied in and out inside the
+ *    call on the given stream and the call returns after the copy back.
+ *  - The library owns every handle and all device memory behind it.  The
+ *    caller owns the buffers it passes.
+ *  - Calls are ordered on the CUDA stream passed as `stream` (a cudaStream_t;
+ *    NULL means the legacy default stream).  Handles are not thread safe.
+ *  - Return value: RW_OK (0) or a negative RW_ERR_* code.  rw_last_error()
+ *    returns a thread-local message for the last failure on this thread.
+ */
+#ifndef RWSOLVE_H
+#define RWSOLVE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RW_OK 0
+#define RW_ERR_INVALID (-1)        /* bad argument, shape or handle            */
+#define RW_ERR_OOM (-2)            /* device allocation or admission refused   */
+#define RW_ERR_SINGULAR (-3)       /* pivot below threshold (W, A_pp, D~)       */
+#define RW_ERR_NOT_CONVERGED (-4)  /* GMRES stopped at maxit above tolerance    */
+#define RW_ERR_TIMEOUT (-5)        /* a bounded device wait gave up             */
+#define RW_ERR_CUDA (-6)           /* CUDA runtime error                        */
+
+/* Built-in wall curves, t in [0, 2 pi), counter-clockwise.
+ *  RW_CURVE_STAR:    x(t) = s (1 + a cos(k t)) (cos t, sin t);
+ *                    params = {a, k, s}.
+ *  RW_CURVE_CHANNEL: superellipse (A cos t, B sin t) (cos^p t + sin^p t)^(-1/p)
+ *                    with y scaled by 1 - delta (1 + cos(pi x / A)) / 2;
+ *                    params = {A, B, p, delta}.  The synthetic stand-in for
+ *                    the paper's spline channel (Sec. 5.1). */
+#define RW_CURVE_STAR 0
+#define RW_CURVE_CHANNEL 1
+
+typedef struct {
+  int curve_kind;     /* RW_CURVE_*                                          */
+  int n_panels;       /* P equal panels in t, 16 Gauss-Legendre points each   */
+  double params[8];   /* curve parameters, see above                        */
+} rw_wall_desc;
+
+typedef struct {
+  int leaf_points;          /* HBS leaf size in points (default 64)          */
+  double id_tol;            /* ID tolerance eps of Def. 3.1 (default 1e-12)  */
+  int n_proxy;              /* points on an HBS proxy circle (default 64)    */
+  double proxy_ratio;       /* HBS proxy radius / node radius (default 2.0)  */
+  int n_proxy_refine;       /* points on P^div and P^bas (default 96)        */
+  double div_ratio;         /* P^div radius / radius of Gamma_r (default 2)  */
+  double bas_ratio;         /* P^bas radius / radius of Gamma_r (default 1.5)*/
+  int dense_pp_max_points;  /* A_pp inverted densely up to this many added
+                               points, else by an HBS of the refined arc
+                               (Alg. 1 step 2; default = leaf_points)         */
+  int sketch_cols;          /* ID matrices wider than this are compressed by
+                               a random +-1 sketch first (default 1024)       */
+  double gmres_tol;         /* relative residual target (default 1e-10)      */
+  int gmres_maxit;          /* iterations per restart cycle (default 30)     */
+  int gmres_restarts;       /* restart cycles (default 4)                    */
+  unsigned long long seed;  /* seed of the sketch generator                  */
+} rw_opts;
+
+typedef struct {
+  int n_points;        /* N on the wall                                      */
+  int levels;          /* tree depth (root = 0, leaves = levels)             */
+  int max_rank;        /* largest node rank                                  */
+  long long inv_elems; /* matrix entries read by one inverse sweep           */
+  long long fwd_elems; /* matrix entries read by one forward apply           */
+  long long bytes;     /* device bytes held by the handle                    */
+} rw_hbs_stats;
+
+typedef struct {
+  int n_k, n_c, n_p;   /* points kept, cut and added (Sec. 3.1)              */
+  int n_n, n_ext;      /* N_n = N_k + N_p, N_ext = N_k + N_c + N_p           */
+  int k_far, k_near, k_pk;  /* ranks of the far, near and A_pk row IDs       */
+  int k;               /* Woodbury size k = k_far + k_near + k_pk            */
+  int pp_dense;        /* 1 if A_pp was inverted densely                     */
+  int pp_levels;       /* tree depth of the refined-arc HBS (0 if dense)     */
+  long long bytes;     /* device bytes held by the handle                    */
+} rw_ref_stats;
+
+typedef struct {
+  int iters;             /* GMRES iterations (0 for the direct path)         */
+  double rel_residual;   /* GMRES: final relative residual of the ELS        */
+} rw_info;
+
+typedef struct rw_hbs_s* rw_hbs_t;   /* reference wall: HBS forward + inverse */
+typedef struct rw_ref_s* rw_ref_t;   /* one refinement: Woodbury factors       */
+
+/* Fill *o with the defaults listed above. */
+int rw_default_opts(rw_opts* o);
+
+/* a0. Build the reference wall's nodes, the proxy-compressed HBS
+ * representation of A_oo and its HBS inverse (Sec. 3 preamble and Sec. 4.2:
+ * the fast direct solver for the original discretisation is taken as given;
+ * the HBS construction and inversion follow Gillman-Young-Martinsson 2012).
+ * opts may be NULL (defaults).  On success *out owns all device memory. */
+int rw_hbs_build(const rw_wall_desc* wall, const rw_opts* opts, void* stream,
+                 rw_hbs_t* out);
+
+int rw_hbs_stats_get(rw_hbs_t h, rw_hbs_stats* s);
+
+/* Copy the wall's nodes into `out` (host or device, 6 x N column-major:
+ * x, y, nx, ny, w, kappa per point, panel order). */
+int rw_hbs_nodes(rw_hbs_t h, double* out, void* stream);
+
+/* x = A_oo^{-1} b on the reference wall by the HBS inverse sweep.
+ * b, x: 2N x nrhs (host or device; may not alias). */
+int rw_hbs_apply_inverse(rw_hbs_t h, int nrhs, const double* b, double* x,
+                         void* stream);
+
+/* y = A_oo x by the HBS forward representation (used for GMRES mat-vecs). */
+int rw_hbs_apply_forward(rw_hbs_t h, int nrhs, const double* x, double* y,
+                         void* stream);
+
+/* a1-a6. Algorithm 1 pre-computation for one local refinement (Sec. 3.1-3.4):
+ * cut the n_cut panels panel_ids[] (a contiguous run modulo P, window order)
+ * and replace panel_ids[i] by 2^levels[i] equal sub-panels; build the added
+ * nodes, A_pp^{-1}, the row-ID factors Q ~= L R, X = A~^{-1} L and the LU
+ * factors of W = I + R X.  panel_ids and levels are host arrays.
+ * The handle borrows h, which must outlive it. */
+int rw_refine_factor(rw_hbs_t h, int n_cut, const int* panel_ids,
+                     const int* levels, void* stream, rw_ref_t* out);
+
+int rw_ref_stats_get(rw_ref_t r, rw_ref_stats* s);
+
+/* Copy the refined nodes in refined order (6 x N_n, as rw_hbs_nodes). */
+int rw_ref_nodes(rw_ref_t r, double* out, void* stream);
+
+/* Boundary data from point forces (Eq. stokeslet): g(x_i) = sum_s S(x_i, y_s) f_s
+ * at the refined nodes.  src: 2 x n_src (x, y); f: 2 x n_src x nrhs;
+ * g: 2 N_n x nrhs.  All host or device. */
+int rw_stokeslet_data(rw_ref_t r, int n_src, const double* src, int nrhs,
+                      const double* f, double* g, void* stream);
+
+#define RW_MODE_DIRECT 0      /* Algorithm 1 solve, FP64                     */
+#define RW_MODE_GMRES_FP32 1  /* FGMRES (FP64) on A~ + L R, preconditioned by
+                                 Algorithm 1 with FP32 HBS sweeps (Sec. 4.2) */
+
+/* s1-s3 (and m1). Solve the refined system for nrhs right-hand sides:
+ * g: 2 N_n x nrhs boundary data in refined order; tau: 2 N_n x nrhs density
+ * (output, refined order); if n_targets > 0, u: 2 n_targets x nrhs interior
+ * velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets (2 x n_targets).
+ * info may be NULL. */
+int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets,
+             const double* targets, double* u, int mode, void* stream,
+             rw_info* info);
+
+void rw_ref_free(rw_ref_t r);
+void rw_hbs_free(rw_hbs_t h);
+const char* rw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RWSOLVE_H */

@@ -1,0 +1,295 @@
+// extern "C" boundary of the rwsolve library (declared in include/rwsolve.h).
+// Argument checking, host/device pointer handling and error codes live here;
+// the work is done by refine.cu / hbs.cu and the kernels below them.
+#include "refine.cuh"
+#include <cstring>
+#include <memory>
+
+struct rw_hbs_s {
+  rw::Wall wall;
+};
+struct rw_ref_s {
+  rw::Refinement ref;
+  const rw_hbs_s* h = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return RW_OK;
+  } catch (const rw::Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(RW_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(RW_ERR_INVALID, e.what());
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller buffer: the pointer itself if it is device memory,
+// else a stream-ordered copy (copied in if `in`, copied back by `finish`).
+struct Arg {
+  const void* user = nullptr;
+  size_t bytes = 0;
+  bool device = true;
+  rw::TBuf<double> tmp;
+  double* p = nullptr;
+  Arg(const double* u, size_t count, bool in, cudaStream_t s) : user(u), bytes(count * sizeof(double)) {
+    if (!u || !count) { p = const_cast<double*>(u); return; }
+    device = is_device_ptr(u);
+    if (device) { p = const_cast<double*>(u); return; }
+    tmp = rw::TBuf<double>(count, s);
+    p = tmp.p;
+    if (in) RW_CUDA(cudaMemcpyAsync(p, u, bytes, cudaMemcpyHostToDevice, s));
+  }
+  void finish(cudaStream_t s) {
+    if (!device && bytes) {
+      RW_CUDA(cudaMemcpyAsync(const_cast<void*>(user), p, bytes, cudaMemcpyDeviceToHost, s));
+    }
+  }
+};
+
+rw::Opts to_opts(const rw_opts* o) {
+  rw::Opts r;
+  if (!o) return r;
+  rw::require(o->leaf_points >= 8 && o->leaf_points <= 512, "opts.leaf_points must be in 8..512");
+  rw::require(o->id_tol > 0 && o->id_tol < 1, "opts.id_tol must be in (0, 1)");
+  rw::require(o->n_proxy >= 8 && o->n_proxy <= 1024, "opts.n_proxy must be in 8..1024");
+  rw::require(o->proxy_ratio > 1.0, "opts.proxy_ratio must exceed 1");
+  rw::require(o->n_proxy_refine >= 8 && o->n_proxy_refine <= 1024, "opts.n_proxy_refine must be in 8..1024");
+  rw::require(o->div_ratio > o->bas_ratio && o->bas_ratio > 1.0, "opts need div_ratio > bas_ratio > 1");
+  rw::require(o->sketch_cols >= 64, "opts.sketch_cols must be >= 64");
+  rw::require(o->gmres_tol > 0 && o->gmres_maxit >= 1 && o->gmres_restarts >= 1, "bad GMRES options");
+  r.leaf_points = o->leaf_points;
+  r.id_tol = o->id_tol;
+  r.n_proxy = o->n_proxy;
+  r.proxy_ratio = o->proxy_ratio;
+  r.n_proxy_refine = o->n_proxy_refine;
+  r.div_ratio = o->div_ratio;
+  r.bas_ratio = o->bas_ratio;
+  r.dense_pp_max_points = o->dense_pp_max_points;
+  r.sketch_cols = o->sketch_cols;
+  r.gmres_tol = o->gmres_tol;
+  r.gmres_maxit = o->gmres_maxit;
+  r.gmres_restarts = o->gmres_restarts;
+  r.seed = o->seed;
+  return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rw_default_opts(rw_opts* o) {
+  if (!o) return fail(RW_ERR_INVALID, "rw_default_opts: null");
+  rw::Opts d;
+  o->leaf_points = d.leaf_points;
+  o->id_tol = d.id_tol;
+  o->n_proxy = d.n_proxy;
+  o->proxy_ratio = d.proxy_ratio;
+  o->n_proxy_refine = d.n_proxy_refine;
+  o->div_ratio = d.div_ratio;
+  o->bas_ratio = d.bas_ratio;
+  o->dense_pp_max_points = d.dense_pp_max_points;
+  o->sketch_cols = d.sketch_cols;
+  o->gmres_tol = d.gmres_tol;
+  o->gmres_maxit = d.gmres_maxit;
+  o->gmres_restarts = d.gmres_restarts;
+  o->seed = d.seed;
+  return RW_OK;
+}
+
+int rw_hbs_build(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_hbs_t* out) {
+  if (!wd || !out) return fail(RW_ERR_INVALID, "rw_hbs_build: null argument");
+  *out = nullptr;
+  std::unique_ptr<rw_hbs_s> h(new rw_hbs_s);
+  int rc = guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rw::Wall& w = h->wall;
+    w.opts = to_opts(opts);
+    rw::require(wd->n_panels >= 1 && wd->n_panels <= (1 << 20), "wall.n_panels must be in 1..2^20");
+    w.n_panels = wd->n_panels;
+    w.curve.kind = wd->curve_kind;
+    for (int i = 0; i < 8; ++i) w.curve.p[i] = wd->params[i];
+    if (wd->curve_kind == RW_CURVE_STAR) {
+      if (w.curve.p[2] == 0.0) w.curve.p[2] = 1.0;
+      rw::require(std::fabs(w.curve.p[0]) < 1.0 && w.curve.p[2] > 0, "star: need |a| < 1 and scale > 0");
+    } else if (wd->curve_kind == RW_CURVE_CHANNEL) {
+      const double def[4] = {10.0, 0.5, 8.0, 0.6};
+      bool all0 = true;
+      for (int i = 0; i < 4; ++i) all0 = all0 && w.curve.p[i] == 0.0;
+      if (all0) for (int i = 0; i < 4; ++i) w.curve.p[i] = def[i];
+      rw::require(w.curve.p[0] > 0 && w.curve.p[1] > 0 && w.curve.p[2] >= 2 && w.curve.p[3] >= 0 && w.curve.p[3] < 1,
+                  "channel: need A > 0, B > 0, p >= 2 (even), 0 <= delta < 1");
+    } else {
+      throw rw::Error(RW_ERR_INVALID, "unknown curve kind");
+    }
+    const int P = w.n_panels;
+    std::vector<double> ta(P), tb(P);
+    for (int j = 0; j < P; ++j) { ta[j] = 2.0 * rw::kPi * j / P; tb[j] = 2.0 * rw::kPi * (j + 1) / P; }
+    auto dta = rw::to_device_tmp(ta, s), dtb = rw::to_device_tmp(tb, s);
+    w.nodes.alloc(16 * P);
+    rw::eval_nodes(w.curve, dta.p, dtb.p, P, w.nodes.buf.p, 16 * P, s);
+    auto all = w.nodes.buf.download(s);
+    w.nodes.hx.assign(all.begin(), all.begin() + 16 * P);
+    w.nodes.hy.assign(all.begin() + 16 * P, all.begin() + 32 * P);
+    w.hbs.build(w.nodes, w.opts, s);
+    w.hbs.make_fp32(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+  if (rc == RW_OK) *out = h.release();
+  return rc;
+}
+
+int rw_hbs_stats_get(rw_hbs_t h, rw_hbs_stats* st) {
+  if (!h || !st) return fail(RW_ERR_INVALID, "rw_hbs_stats_get: null argument");
+  const rw::Hbs& b = h->wall.hbs;
+  st->n_points = b.N;
+  st->levels = b.L;
+  st->max_rank = b.max_rank;
+  st->inv_elems = b.inv_elems;
+  st->fwd_elems = b.fwd_elems;
+  st->bytes = (long long)(b.bytes + h->wall.nodes.buf.bytes());
+  return RW_OK;
+}
+
+int rw_hbs_nodes(rw_hbs_t h, double* out, void* stream) {
+  if (!h || !out) return fail(RW_ERR_INVALID, "rw_hbs_nodes: null argument");
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto& b = h->wall.nodes.buf;
+    RW_CUDA(cudaMemcpyAsync(out, b.p, b.bytes(), cudaMemcpyDefault, s));
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int rw_hbs_apply_inverse(rw_hbs_t h, int nrhs, const double* b, double* x, void* stream) {
+  if (!h || !b || !x || nrhs < 1) return fail(RW_ERR_INVALID, "rw_hbs_apply_inverse: bad argument");
+  if (b == x) return fail(RW_ERR_INVALID, "rw_hbs_apply_inverse: b and x may not alias");
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = size_t(2) * h->wall.nodes.n * nrhs;
+    Arg ab(b, n, true, s), ax(x, n, false, s);
+    h->wall.hbs.apply_inverse(ab.p, ax.p, nrhs, s);
+    ax.finish(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int rw_hbs_apply_forward(rw_hbs_t h, int nrhs, const double* x, double* y, void* stream) {
+  if (!h || !x || !y || nrhs < 1) return fail(RW_ERR_INVALID, "rw_hbs_apply_forward: bad argument");
+  if (x == y) return fail(RW_ERR_INVALID, "rw_hbs_apply_forward: x and y may not alias");
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = size_t(2) * h->wall.nodes.n * nrhs;
+    Arg ax(x, n, true, s), ay(y, n, false, s);
+    h->wall.hbs.apply_forward(ax.p, ay.p, nrhs, s);
+    ay.finish(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int rw_refine_factor(rw_hbs_t h, int n_cut, const int* panel_ids, const int* levels, void* stream, rw_ref_t* out) {
+  if (!h || !panel_ids || !levels || !out || n_cut < 1) return fail(RW_ERR_INVALID, "rw_refine_factor: bad argument");
+  *out = nullptr;
+  std::unique_ptr<rw_ref_s> r(new rw_ref_s);
+  r->h = h;
+  int rc = guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int> pan(panel_ids, panel_ids + n_cut), lv(levels, levels + n_cut);
+    r->ref.factor(h->wall, pan, lv, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+  if (rc == RW_OK) *out = r.release();
+  return rc;
+}
+
+int rw_ref_stats_get(rw_ref_t r, rw_ref_stats* st) {
+  if (!r || !st) return fail(RW_ERR_INVALID, "rw_ref_stats_get: null argument");
+  const rw::Refinement& f = r->ref;
+  st->n_k = f.Nk; st->n_c = f.Nc; st->n_p = f.Np; st->n_n = f.Nn; st->n_ext = f.Nk + f.Nc + f.Np;
+  st->k_far = f.kf; st->k_near = f.kn; st->k_pk = f.kpk; st->k = f.k;
+  st->pp_dense = f.pp_dense ? 1 : 0;
+  st->pp_levels = f.pp_dense ? 0 : f.hpp.L;
+  st->bytes = (long long)f.bytes;
+  return RW_OK;
+}
+
+int rw_ref_nodes(rw_ref_t r, double* out, void* stream) {
+  if (!r || !out) return fail(RW_ERR_INVALID, "rw_ref_nodes: null argument");
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto& b = r->ref.nn.buf;
+    RW_CUDA(cudaMemcpyAsync(out, b.p, b.bytes(), cudaMemcpyDefault, s));
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int rw_stokeslet_data(rw_ref_t r, int n_src, const double* src, int nrhs, const double* f, double* g, void* stream) {
+  if (!r || !src || !f || !g || n_src < 1 || nrhs < 1) return fail(RW_ERR_INVALID, "rw_stokeslet_data: bad argument");
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Arg as(src, size_t(2) * n_src, true, s), af(f, size_t(2) * n_src * nrhs, true, s);
+    Arg ag(g, size_t(2) * r->ref.Nn * nrhs, false, s);
+    rw::eval_stokeslets(r->ref.nn.view(), n_src, as.p, nrhs, af.p, ag.p, s);
+    ag.finish(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, const double* targets, double* u,
+             int mode, void* stream, rw_info* info) {
+  if (!r || !g || !tau || nrhs < 1 || n_targets < 0) return fail(RW_ERR_INVALID, "rw_solve: bad argument");
+  if (n_targets > 0 && (!targets || !u)) return fail(RW_ERR_INVALID, "rw_solve: targets and u required");
+  if (mode != RW_MODE_DIRECT && mode != RW_MODE_GMRES_FP32) return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
+  int iters = 0;
+  double relres = 0.0;
+  int rc = guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const rw::Refinement& f = r->ref;
+    const size_t n = size_t(2) * f.Nn * nrhs;
+    Arg ag(g, n, true, s), at(tau, n, false, s);
+    if (mode == RW_MODE_DIRECT) {
+      f.solve_direct(ag.p, at.p, nrhs, s);
+    } else {
+      f.solve_gmres(ag.p, at.p, nrhs, s, &iters, &relres);
+    }
+    if (n_targets > 0) {
+      Arg ax(targets, size_t(2) * n_targets, true, s), au(u, size_t(2) * n_targets * nrhs, false, s);
+      rw::eval_velocity(f.nn.view(), at.p, nrhs, n_targets, ax.p, au.p, s);
+      au.finish(s);
+    }
+    at.finish(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+    if (mode != RW_MODE_DIRECT && relres > f.wall->opts.gmres_tol)
+      throw rw::Error(RW_ERR_NOT_CONVERGED, "rw_solve: GMRES stopped at relative residual " + std::to_string(relres));
+  });
+  if (info) { info->iters = iters; info->rel_residual = relres; }
+  return rc;
+}
+
+void rw_ref_free(rw_ref_t r) { delete r; }
+void rw_hbs_free(rw_hbs_t h) { delete h; }
+const char* rw_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

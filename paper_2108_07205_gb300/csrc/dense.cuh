@@ -1,0 +1,99 @@
+// Batched dense FP64 (and FP32) building blocks of the rwsolve library.
+// Every routine takes a list of independent problems of varying size and
+// runs them in one launch; matrices are column-major.
+#pragma once
+#include "rw_common.cuh"
+
+namespace rw {
+
+// C (m x n) = alpha op(A) op(B) + beta C, op(A): m x k, op(B): k x n.
+struct GemmProb {
+  const double* A;
+  const double* B;
+  double* C;
+  int m, n, k;
+  int lda, ldb, ldc;
+  int ta, tb;  // 0 = as stored, 1 = transposed
+  double alpha, beta;
+};
+void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s);
+
+// y (m x nrhs) = alpha A x + beta y for column-major A (m x n) and a few
+// right-hand sides (nrhs <= 8).  Matrix and vector element types are
+// templated (double or float); accumulation is in double for double
+// matrices and float for float matrices.  When a problem is wide (n large
+// and m small) the columns are split into chunks whose partial sums go to a
+// scratch buffer and are added in a fixed order (deterministic).
+template <class T>
+struct GemvProb {
+  const T* A;
+  const T* x;
+  T* y;
+  int m, n, lda, ldx, ldy;
+  double alpha, beta;
+};
+
+// Scratch needed by batched_gemv for a problem list (in elements of T).
+template <class T>
+size_t gemv_scratch_elems(const std::vector<GemvProb<T>>& probs, int nrhs);
+
+// Runs the problems; `scratch` must hold gemv_scratch_elems() elements (may
+// be null when that is 0).
+template <class T>
+void batched_gemv(const std::vector<GemvProb<T>>& probs, int nrhs, T* scratch,
+                  cudaStream_t s);
+
+// y = alpha A x + beta y for a problem list and any nrhs: GEMV kernels for
+// nrhs <= 8 (chunks of 8 for FP32), the tiled GEMM above that (FP64).
+// Temporaries are stream-ordered.
+template <class T>
+void matvec(const std::vector<GemvProb<T>>& probs, int nrhs, cudaStream_t s);
+
+// Inverse of square matrices by Gauss-Jordan elimination with partial
+// pivoting (the pivot sequence of LU with partial pivoting).  A is read, Ainv
+// written (may not alias), W is an n*n work copy.  flag[i] set to 1 if a
+// pivot fell below 1e-14 * max|A|.
+struct InvProb {
+  const double* A;
+  double* Ainv;
+  double* W;
+  int n, lda, ldinv;
+  int* flag;
+};
+void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s);
+
+// Interpolative decomposition on the columns of W (the rows of Y = W^T) by
+// column-pivoted Householder QR (Def. 3.1): W (nr x nc) is overwritten;
+// stop when the largest remaining column norm is <= max(tol_abs,
+// tol_rel * first pivot norm) once at least min_rank steps were taken, or at
+// max_rank.  A min_rank above the numerical rank is met by taking further
+// candidates in pivot order as skeletons with zero coefficients.  norms[0]
+// returns the number of numerically nonzero pivots.  Outputs rank k, the pivot order piv (nc), and the interpolation
+// matrix P (nc x k, column-major, leading dimension ldp) with
+// Y ~= P Y(piv[0:k], :) and P(piv[i], :) = e_i.
+struct IdProb {
+  double* W;
+  int ldw, nr, nc;
+  double tol_abs, tol_rel;
+  int min_rank, max_rank;
+  int* piv;
+  double* norms;  // 2 * nc work
+  double* P;
+  int ldp;
+  int* rank;
+};
+void batched_id(const std::vector<IdProb>& probs, cudaStream_t s);
+
+// Writes P (nc x rank) for factorisations finished by batched_id (P may have
+// been null there).  max_elems bounds nc * rank over the list.
+void batched_id_interp(const std::vector<IdProb>& probs, int max_elems, cudaStream_t s);
+
+// Fill a buffer with random +-1 entries from a counter-based hash of
+// (seed, index) (splitmix64 finaliser).
+void fill_rademacher(double* out, size_t n, unsigned long long seed, cudaStream_t s);
+
+// Elementwise helpers.
+void fill_zero(double* p, size_t n, cudaStream_t s);
+void copy_d2f(const double* in, float* out, size_t n, cudaStream_t s);
+
+}  // namespace rw

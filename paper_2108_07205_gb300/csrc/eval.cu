@@ -1,0 +1,344 @@
+// Geometry and kernel-matrix evaluation kernels (Sec. 2, Sec. 3.1, Sec. 3.3).
+#include "eval.cuh"
+#include <algorithm>
+#include <cmath>
+
+namespace rw {
+
+// ------------------------------------------------------------ quadrature
+void gauss_legendre16(double* x, double* w) {
+  const int n = 16;
+  for (int i = 0; i < n; ++i) {
+    // Chebyshev-like initial guess, Newton on P_n via the three-term recurrence
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[n - 1 - i] = z;  // ascending
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+namespace {
+
+__constant__ double c_glx[16], c_glw[16];
+
+struct Pt { double x, y, dx, dy, ddx, ddy; };
+
+__device__ Pt curve_eval(const Curve& c, double t) {
+  Pt q;
+  if (c.kind == RW_CURVE_STAR) {
+    const double a = c.p[0], k = c.p[1], sc = c.p[2];
+    double ct, st, ck, sk;
+    sincos(t, &st, &ct);
+    sincos(k * t, &sk, &ck);
+    const double r = sc * (1.0 + a * ck), r1 = -sc * a * k * sk, r2 = -sc * a * k * k * ck;
+    q.x = r * ct; q.y = r * st;
+    q.dx = r1 * ct - r * st; q.dy = r1 * st + r * ct;
+    q.ddx = r2 * ct - 2.0 * r1 * st - r * ct;
+    q.ddy = r2 * st + 2.0 * r1 * ct - r * st;
+  } else {
+    // superellipse (A cos t, B sin t) (cos^p + sin^p)^(-1/p), y squeezed by
+    // q(x) = 1 - delta (1 + cos(pi x / A)) / 2
+    const double A = c.p[0], B = c.p[1], p = c.p[2], delta = c.p[3];
+    double ct, st;
+    sincos(t, &st, &ct);
+    const double cp = pow(ct, p), sp = pow(st, p);
+    const double cp1 = pow(ct, p - 1.0), sp1 = pow(st, p - 1.0);
+    const double cp2 = pow(ct, p - 2.0), sp2 = pow(st, p - 2.0);
+    const double h = cp + sp;
+    const double h1 = p * (-cp1 * st + sp1 * ct);
+    const double h2 = p * ((p - 1.0) * cp2 * st * st - cp + (p - 1.0) * sp2 * ct * ct - sp);
+    const double sg = pow(h, -1.0 / p);
+    const double sg1 = -(1.0 / p) * sg / h * h1;
+    const double sg2 = -(1.0 / p) * ((-1.0 / p - 1.0) * sg / (h * h) * h1 * h1 + sg / h * h2);
+    const double X = A * ct * sg, X1 = A * (-st * sg + ct * sg1), X2 = A * (-ct * sg - 2.0 * st * sg1 + ct * sg2);
+    const double Y = B * st * sg, Y1 = B * (ct * sg + st * sg1), Y2 = B * (-st * sg + 2.0 * ct * sg1 + st * sg2);
+    double sx, cx;
+    sincos(kPi * X / A, &sx, &cx);
+    const double qv = 1.0 - 0.5 * delta * (1.0 + cx);
+    const double qx = 0.5 * delta * (kPi / A) * sx;
+    const double qxx = 0.5 * delta * (kPi / A) * (kPi / A) * cx;
+    const double Q1 = qx * X1, Q2 = qxx * X1 * X1 + qx * X2;
+    q.x = X; q.dx = X1; q.ddx = X2;
+    q.y = Y * qv; q.dy = Y1 * qv + Y * Q1; q.ddy = Y2 * qv + 2.0 * Y1 * Q1 + Y * Q2;
+  }
+  return q;
+}
+
+__global__ void k_nodes(Curve c, const double* ta, const double* tb, int n_int, double* out, int ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 16 * n_int) return;
+  const int pnl = i / 16, q = i % 16;
+  const double a = ta[pnl], b = tb[pnl];
+  const double half = 0.5 * (b - a), mid = 0.5 * (b + a);
+  const double t = mid + half * c_glx[q];
+  const Pt g = curve_eval(c, t);
+  const double sp = sqrt(g.dx * g.dx + g.dy * g.dy);
+  out[i] = g.x;
+  out[i + ld] = g.y;
+  out[i + 2 * size_t(ld)] = g.dy / sp;
+  out[i + 3 * size_t(ld)] = -g.dx / sp;
+  out[i + 4 * size_t(ld)] = c_glw[q] * half * sp;
+  out[i + 5 * size_t(ld)] = (g.dx * g.ddy - g.dy * g.ddx) / (sp * sp * sp);
+}
+
+__device__ __forceinline__ double idmat_value(const IdMatProb& P, int c, int i, const NodesView& S,
+                                              const NodesView& E1, bool e1s, const NodesView& E2, bool e2s) {
+  const int d = P.cand[i];
+  const int ip = d >> 1, ia = d & 1;
+  if (c < P.n1) {
+    const int e = P.e1[c];
+    return P.kind == 0 ? a_entry(S, ip, ia, E1, e >> 1, e & 1, e1s) : a_entry(E1, e >> 1, e & 1, S, ip, ia, e1s);
+  }
+  c -= P.n1;
+  if (c < P.n2) {
+    const int e = P.e2[c];
+    return P.kind == 0 ? a_entry(S, ip, ia, E2, e >> 1, e & 1, e2s) : a_entry(E2, e >> 1, e & 1, S, ip, ia, e2s);
+  }
+  c -= P.n2;
+  const int per = P.kind == 0 ? 4 : 2;
+  if (c < per * P.M) {
+    const int q = c / per, sub = c % per;
+    double sn, cs;
+    sincospi(2.0 * q / P.M, &sn, &cs);
+    const double zx = P.cx + P.R * cs, zy = P.cy + P.R * sn;
+    if (P.kind == 0) {
+      // field at x_i of a unit source at z_q: Stokeslet (sub 0, 1) or double
+      // layer with the circle's outward normal (sub 2, 3), component b
+      const double rx = S.x[ip] - zx, ry = S.y[ip] - zy, r2 = rx * rx + ry * ry;
+      const double ra = ia ? ry : rx;
+      if (sub < 2) {
+        const double rb = sub ? ry : rx;
+        return (1.0 / (4.0 * kPi)) * ((ia == sub ? -0.5 * log(r2) : 0.0) + ra * rb / r2);
+      }
+      const double rb = (sub - 2) ? ry : rx;
+      const double rdn = rx * cs + ry * sn;
+      return ra * rb * rdn / (kPi * r2 * r2);
+    } else {
+      // field at z_q, component a' = sub, of a unit density at x_i component ia
+      const double rx = zx - S.x[ip], ry = zy - S.y[ip], r2 = rx * rx + ry * ry;
+      const double rdn = rx * S.nx[ip] + ry * S.ny[ip];
+      const double fac = S.w[ip] * rdn / (kPi * r2 * r2);
+      return fac * (sub ? ry : rx) * (ia ? ry : rx);
+    }
+  }
+  // normal column
+  const double n = ia ? S.ny[ip] : S.nx[ip];
+  return P.kind == 0 ? n : n * S.w[ip];
+}
+
+__global__ void k_idmat(const IdMatProb* probs, NodesView S, NodesView E1, bool e1s, NodesView E2, bool e2s) {
+  const IdMatProb P = probs[blockIdx.y];
+  const long long tot = (long long)P.ncol * P.m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int c = int(e % P.ncol), i = int(e / P.ncol);
+    P.W[c + size_t(i) * P.ldw] = idmat_value(P, c, i, S, E1, e1s, E2, e2s);
+  }
+}
+
+__global__ void k_blocks(const BlockProb* probs, NodesView s0, NodesView s1) {
+  const BlockProb P = probs[blockIdx.y];
+  const NodesView& R = P.rset ? s1 : s0;
+  const NodesView& C = P.cset ? s1 : s0;
+  const bool same = P.rset == P.cset;
+  const long long tot = (long long)P.mr * P.mc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int r = int(e % P.mr), c = int(e / P.mr);
+    const int dr = P.rows ? P.rows[r] : P.r0 + r;
+    const int dc = P.cols ? P.cols[c] : P.c0 + c;
+    P.out[r + size_t(c) * P.ld] = P.scale * a_entry(R, dr >> 1, dr & 1, C, dc >> 1, dc & 1, same);
+  }
+}
+
+__global__ void k_transpose(const TransProb* probs) {
+  const TransProb P = probs[blockIdx.y];
+  const long long tot = (long long)P.m * P.n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = int(e % P.n), j = int(e / P.n);  // out(i, j) = in(j, i)
+    P.out[i + size_t(j) * P.ldo] = P.in[j + size_t(i) * P.ldi];
+  }
+}
+
+__global__ void k_copy(const CopyProb* probs) {
+  const CopyProb P = probs[blockIdx.y];
+  const long long tot = (long long)P.m * P.n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = int(e % P.m), j = int(e / P.m);
+    P.out[i + size_t(j) * P.ldo] = P.in[i + size_t(j) * P.ldi];
+  }
+}
+
+__global__ void k_velocity(NodesView nd, const double* tau, int nrhs, int nt, const double* tg, double* u) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (t >= nt) return;
+  const double x = tg[2 * t], y = tg[2 * t + 1];
+  const double* tr = tau + size_t(r) * 2 * nd.n;
+  double ux = 0.0, uy = 0.0;
+  for (int j = 0; j < nd.n; ++j) {
+    const double rx = x - nd.x[j], ry = y - nd.y[j], r2 = rx * rx + ry * ry;
+    const double fac = nd.w[j] * (rx * nd.nx[j] + ry * nd.ny[j]) / (kPi * r2 * r2);
+    const double rt = rx * tr[2 * j] + ry * tr[2 * j + 1];
+    ux += fac * rx * rt;
+    uy += fac * ry * rt;
+  }
+  u[size_t(r) * 2 * nt + 2 * t] = ux;
+  u[size_t(r) * 2 * nt + 2 * t + 1] = uy;
+}
+
+__global__ void k_stokeslets(NodesView nd, int ns, const double* src, int nrhs, const double* f, double* g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= nd.n) return;
+  const double* fr = f + size_t(r) * 2 * ns;
+  double gx = 0.0, gy = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    const double rx = nd.x[i] - src[2 * s], ry = nd.y[i] - src[2 * s + 1], r2 = rx * rx + ry * ry;
+    const double lg = -0.5 * log(r2);
+    const double rf = (rx * fr[2 * s] + ry * fr[2 * s + 1]) / r2;
+    gx += lg * fr[2 * s] + rx * rf;
+    gy += lg * fr[2 * s + 1] + ry * rf;
+  }
+  g[size_t(r) * 2 * nd.n + 2 * i] = gx / (4.0 * kPi);
+  g[size_t(r) * 2 * nd.n + 2 * i + 1] = gy / (4.0 * kPi);
+}
+
+__global__ void k_max_colnorm(const double* W, int nr, int nc, int ld, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= nc) return;
+  double s = 0.0;
+  for (int i = lane; i < nr; i += 32) { double v = W[i + size_t(j) * ld]; s += v * v; }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) atomicMax(out, __double_as_longlong(sqrt(s)));  // non-negative doubles order as integers
+}
+
+__global__ void k_to_double(const unsigned long long* in, double* out) { *out = __longlong_as_double(*in); }
+
+__global__ void k_gather_scatter(const double* in, int ldi, const int* ii, double* out, int ldo, const int* io, int n) {
+  const int r = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int a = ii ? ii[i] : i, b = io ? io[i] : i;
+    out[b + size_t(r) * ldo] = in[a + size_t(r) * ldi];
+  }
+}
+
+int grid1(long long n) { return int(std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096))); }
+
+bool g_gl_ready = false;
+
+void ensure_gl() {
+  if (g_gl_ready) return;
+  double x[16], w[16];
+  gauss_legendre16(x, w);
+  RW_CUDA(cudaMemcpyToSymbol(c_glx, x, sizeof(x)));
+  RW_CUDA(cudaMemcpyToSymbol(c_glw, w, sizeof(w)));
+  g_gl_ready = true;
+}
+
+}  // namespace
+
+void eval_nodes(const Curve& c, const double* ta, const double* tb, int n_int, double* out, int ld,
+                cudaStream_t s) {
+  if (n_int <= 0) return;
+  ensure_gl();
+  k_nodes<<<ceil_div(16LL * n_int, 128), 128, 0, s>>>(c, ta, tb, n_int, out, ld);
+  RW_CHECK_LAUNCH();
+}
+
+void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S, const NodesView& E1, bool e1_same,
+                const NodesView& E2, bool e2_same, cudaStream_t s) {
+  if (probs.empty()) return;
+  long long mx = 0;
+  for (auto& p : probs) mx = std::max(mx, (long long)p.ncol * p.m);
+  if (mx == 0) return;
+  auto d = to_device_tmp(probs, s);
+  dim3 grid(std::min(grid1(mx), 1024), int(probs.size()));
+  k_idmat<<<grid, 256, 0, s>>>(d.p, S, E1, e1_same, E2, e2_same);
+  RW_CHECK_LAUNCH();
+}
+
+void eval_blocks(const std::vector<BlockProb>& probs, const NodesView& set0, const NodesView& set1,
+                 cudaStream_t s) {
+  std::vector<BlockProb> ps;
+  long long mx = 0;
+  for (auto& p : probs) if (p.mr > 0 && p.mc > 0) { ps.push_back(p); mx = std::max(mx, (long long)p.mr * p.mc); }
+  if (ps.empty()) return;
+  auto d = to_device_tmp(ps, s);
+  dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
+  k_blocks<<<grid, 256, 0, s>>>(d.p, set0, set1);
+  RW_CHECK_LAUNCH();
+}
+
+void batched_transpose(const std::vector<TransProb>& probs, cudaStream_t s) {
+  std::vector<TransProb> ps;
+  long long mx = 0;
+  for (auto& p : probs) if (p.m > 0 && p.n > 0) { ps.push_back(p); mx = std::max(mx, (long long)p.m * p.n); }
+  if (ps.empty()) return;
+  auto d = to_device_tmp(ps, s);
+  dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
+  k_transpose<<<grid, 256, 0, s>>>(d.p);
+  RW_CHECK_LAUNCH();
+}
+
+void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s) {
+  std::vector<CopyProb> ps;
+  long long mx = 0;
+  for (auto& p : probs) if (p.m > 0 && p.n > 0) { ps.push_back(p); mx = std::max(mx, (long long)p.m * p.n); }
+  if (ps.empty()) return;
+  auto d = to_device_tmp(ps, s);
+  dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
+  k_copy<<<grid, 256, 0, s>>>(d.p);
+  RW_CHECK_LAUNCH();
+}
+
+void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* u,
+                   cudaStream_t s) {
+  if (nt <= 0 || nrhs <= 0) return;
+  k_velocity<<<dim3(ceil_div(nt, 128), nrhs), 128, 0, s>>>(nodes, tau, nrhs, nt, targets, u);
+  RW_CHECK_LAUNCH();
+}
+
+void eval_stokeslets(const NodesView& nodes, int ns, const double* src, int nrhs, const double* f, double* g,
+                     cudaStream_t s) {
+  if (nodes.n <= 0 || nrhs <= 0) return;
+  k_stokeslets<<<dim3(ceil_div(nodes.n, 128), nrhs), 128, 0, s>>>(nodes, ns, src, nrhs, f, g);
+  RW_CHECK_LAUNCH();
+}
+
+void max_colnorm(const double* W, int nr, int nc, int ld, double* out, cudaStream_t s) {
+  TBuf<unsigned long long> tmp(1, s);
+  RW_CUDA(cudaMemsetAsync(tmp.p, 0, sizeof(unsigned long long), s));
+  if (nc > 0) {
+    k_max_colnorm<<<ceil_div(32LL * nc, 256), 256, 0, s>>>(W, nr, nc, ld, tmp.p);
+    RW_CHECK_LAUNCH();
+  }
+  k_to_double<<<1, 1, 0, s>>>(tmp.p, out);
+  RW_CHECK_LAUNCH();
+}
+
+void gather_scatter(const double* in, int ldi, const int* idx_in, double* out, int ldo, const int* idx_out, int n,
+                    int nrhs, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return;
+  k_gather_scatter<<<dim3(std::min(ceil_div(n, 256), 1024), nrhs), 256, 0, s>>>(in, ldi, idx_in, out, ldo, idx_out, n);
+  RW_CHECK_LAUNCH();
+}
+
+}  // namespace rw

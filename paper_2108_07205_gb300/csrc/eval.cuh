@@ -1,0 +1,108 @@
+// Geometry and kernel-matrix evaluation: wall and refined nodes from the
+// curve description, entries of A on index lists, and the proxy-augmented
+// matrices whose interpolative decompositions give the HBS bases and the
+// low-rank factors of Q.
+#pragma once
+#include "rw_common.cuh"
+
+namespace rw {
+
+// Curve description on the device (RW_CURVE_* and its parameters).
+struct Curve {
+  int kind;
+  double p[8];
+};
+
+// Gauss-Legendre nodes/weights of the 16-point rule on [-1, 1] (host table,
+// Newton iteration on the Legendre recurrence).
+void gauss_legendre16(double* x, double* w);
+
+// Nodes on t-intervals [ta[i], tb[i]] (16 Gauss-Legendre points each) into
+// `out` (6 x 16 n_int, see Nodes).  ta/tb are device arrays.
+void eval_nodes(const Curve& c, const double* ta, const double* tb, int n_int,
+                double* out, int ld, cudaStream_t s);
+
+// Columns of an ID matrix, written transposed: W (ncol x m) holds Y^T.
+// kind 0 ("outgoing", rows of A): Y[i, :] = [A(cand_i, e1) | A(cand_i, e2) |
+//   S(x_i, z_q) e_b, D(x_i, z_q) e_b for proxy points z_q | n_i]
+// kind 1 ("incoming", columns of A): Y[i, :] = [A(e1, cand_i)^T |
+//   A(e2, cand_i)^T | w_i D(z_q, x_i)[a', .] for proxy points | w_i n_i].
+// Candidates live in node set S; e1 in E1 and e2 in E2.  Proxy points are
+// z_q = c + R (cos 2 pi q / M, sin 2 pi q / M) with outward normal.
+struct IdMatProb {
+  int kind;
+  int m;
+  const int* cand;
+  int n1;
+  const int* e1;
+  int n2;
+  const int* e2;
+  double cx, cy, R;
+  int M;
+  int normal;
+  double* W;
+  int ldw;
+  int ncol;
+};
+inline int idmat_ncol(int kind, int n1, int n2, int M, int normal) {
+  return n1 + n2 + (kind == 0 ? 4 * M : 2 * M) + (normal ? 1 : 0);
+}
+void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S,
+                const NodesView& E1, bool e1_same, const NodesView& E2,
+                bool e2_same, cudaStream_t s);
+
+// Dense blocks out (mr x mc, ld) = scale * A(rows, cols); rows index DOFs of
+// node set sets[rset], cols of sets[cset] (rset == cset: same set, with the
+// diagonal blocks).  rows == nullptr means rows r0 .. r0+mr-1 (same for cols).
+struct BlockProb {
+  int mr, mc;
+  const int* rows;
+  const int* cols;
+  int r0, c0;
+  int rset, cset;
+  double scale;
+  double* out;
+  int ld;
+};
+void eval_blocks(const std::vector<BlockProb>& probs, const NodesView& set0,
+                 const NodesView& set1, cudaStream_t s);
+
+// out (n x m, ldo) = in^T (in: m x n, ldi), batched.
+struct TransProb {
+  const double* in;
+  int m, n, ldi;
+  double* out;
+  int ldo;
+};
+void batched_transpose(const std::vector<TransProb>& probs, cudaStream_t s);
+
+// out[r0:r0+m, c0:c0+n] (ldo) = in (m x n, ldi), batched copies of blocks.
+struct CopyProb {
+  const double* in;
+  int m, n, ldi;
+  double* out;
+  int ldo;
+};
+void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s);
+
+// Velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets (Sec. 2.1).
+// targets: 2 x nt; tau: 2N x nrhs (ld 2N); u: 2nt x nrhs (ld 2nt).
+void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt,
+                   const double* targets, double* u, cudaStream_t s);
+
+// g(x_i) = sum_s S(x_i, y_s) f_s (Eq. stokeslet, mu = 1) at every node.
+// src: 2 x ns; f: 2 x ns x nrhs; g: 2N x nrhs.
+void eval_stokeslets(const NodesView& nodes, int ns, const double* src,
+                     int nrhs, const double* f, double* g, cudaStream_t s);
+
+// Row-norm maximum of a column-major W (nr x nc): max_j ||W[:, j]|| into out.
+void max_colnorm(const double* W, int nr, int nc, int ld, double* out,
+                 cudaStream_t s);
+
+// Scatter/gather of interleaved DOF vectors: out[idx_out[i]] = in[idx_in[i]]
+// for i < n and every right-hand side (column strides ldi/ldo).
+void gather_scatter(const double* in, int ldi, const int* idx_in, double* out,
+                    int ldo, const int* idx_out, int n, int nrhs,
+                    cudaStream_t s);
+
+}  // namespace rw

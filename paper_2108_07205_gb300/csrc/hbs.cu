@@ -1,0 +1,788 @@
+// HBS construction, inversion and sweeps on the device (Gillman, Young and
+// Martinsson 2012, as used by the paper for A_oo and, above the dense
+// threshold, for A_pp).  Host code plans the tree and index sets; every
+// matrix entry, factorisation and product is computed by the kernels in
+// dense.cu / eval.cu.
+#include "hbs.cuh"
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <type_traits>
+
+namespace rw {
+
+// ====================================================================== IdBatch
+int IdBatch::add(const IdMatProb& spec, int sketch_cols, int sketch_width) {
+  Job j;
+  j.spec = spec;
+  j.spec.ncol = idmat_ncol(spec.kind, spec.n1, spec.n2, spec.M, spec.normal);
+  if (j.spec.ncol > sketch_cols && sketch_width < j.spec.ncol) {
+    j.sk_width = sketch_width;
+    j.nr = sketch_width;
+  } else {
+    j.nr = j.spec.ncol;
+  }
+  jobs.push_back(j);
+  return int(jobs.size()) - 1;
+}
+
+void IdBatch::run(const NodesView& S, const NodesView& E1, bool e1s, const NodesView& E2, bool e2s,
+                  double tol_rel, const std::vector<double>& tol_abs, const std::vector<int>& subset_in,
+                  const std::vector<int>& min_rank, const std::vector<int>& max_rank,
+                  unsigned long long seed, cudaStream_t s) {
+  const int nj = int(jobs.size());
+  if (!W.p) {
+    size_t w = 0, m = 0;
+    for (auto& j : jobs) {
+      j.woff = w;
+      j.moff = m;
+      w += size_t(j.nr) * j.spec.m;
+      m += j.spec.m;
+    }
+    W.alloc(std::max<size_t>(w, 1));
+    norms.alloc(std::max<size_t>(2 * m, 1));
+    piv.alloc(std::max<size_t>(m, 1));
+    rank.alloc(std::max(nj, 1));
+    h_rank.assign(nj, 0);
+  }
+  std::vector<int> subset = subset_in;
+  if (subset.empty()) { subset.resize(nj); std::iota(subset.begin(), subset.end(), 0); }
+  // evaluation: direct into W, or into Y followed by the sketch W = Omega^T Y
+  size_t ysz = 0;
+  int max_ncol = 0, max_sk = 0;
+  for (int id : subset) {
+    const Job& j = jobs[id];
+    if (j.sk_width) {
+      ysz += size_t(j.spec.ncol) * j.spec.m;
+      max_ncol = std::max(max_ncol, j.spec.ncol);
+      max_sk = std::max(max_sk, j.sk_width);
+    }
+  }
+  TBuf<double> Y(ysz, s), Om(size_t(max_ncol) * max_sk, s);
+  if (max_sk) fill_rademacher(Om.p, Om.n, seed, s);
+  std::vector<IdMatProb> ev;
+  std::vector<GemmProb> gm;
+  size_t yo = 0;
+  for (int id : subset) {
+    Job& j = jobs[id];
+    IdMatProb p = j.spec;
+    if (j.sk_width) {
+      p.W = Y.p + yo;
+      p.ldw = p.ncol;
+      GemmProb g{Om.p, p.W, W.p + j.woff, j.sk_width, p.m, p.ncol, max_ncol, p.ncol, j.sk_width, 1, 0, 1.0, 0.0};
+      gm.push_back(g);
+      yo += size_t(p.ncol) * p.m;
+    } else {
+      p.W = W.p + j.woff;
+      p.ldw = p.ncol;
+    }
+    ev.push_back(p);
+  }
+  eval_idmat(ev, S, E1, e1s, E2, e2s, s);
+  batched_gemm(gm, s);
+  std::vector<IdProb> ip;
+  for (int id : subset) {
+    Job& j = jobs[id];
+    IdProb q;
+    q.W = W.p + j.woff;
+    q.ldw = j.nr;
+    q.nr = j.nr;
+    q.nc = j.spec.m;
+    q.tol_abs = tol_abs.empty() ? 0.0 : tol_abs[id];
+    q.tol_rel = tol_rel;
+    q.min_rank = min_rank.empty() ? 0 : min_rank[id];
+    q.max_rank = max_rank.empty() ? j.spec.m : max_rank[id];
+    q.piv = piv.p + j.moff;
+    q.norms = norms.p + 2 * j.moff;
+    q.P = nullptr;
+    q.ldp = j.spec.m;
+    q.rank = rank.p + id;
+    ip.push_back(q);
+  }
+  batched_id(ip, s);
+  h_rank = rank.download(s);
+  h_rank.resize(nj);
+}
+
+void IdBatch::interp(const std::vector<double*>& P, const std::vector<int>& ldp, cudaStream_t s) {
+  std::vector<IdProb> ip;
+  int mx = 0;
+  for (size_t id = 0; id < jobs.size(); ++id) {
+    if (!P[id]) continue;
+    const Job& j = jobs[id];
+    IdProb q{};
+    q.W = W.p + j.woff;
+    q.ldw = j.nr;
+    q.nr = j.nr;
+    q.nc = j.spec.m;
+    q.piv = piv.p + j.moff;
+    q.norms = norms.p + 2 * j.moff;
+    q.P = P[id];
+    q.ldp = ldp[id];
+    q.rank = rank.p + id;
+    ip.push_back(q);
+    mx = std::max(mx, j.spec.m * h_rank[id]);
+  }
+  batched_id_interp(ip, mx, s);
+}
+
+std::vector<int> IdBatch::pivots(cudaStream_t s) const { return piv.download(s); }
+
+// ====================================================================== tree ID
+namespace {
+__global__ void k_gather_cols(const double* Z, int nr, const int* cand, int n, double* W) {
+  const long long tot = (long long)nr * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int r = int(e % nr), c = int(e / nr);
+    W[e] = Z[r + size_t(cand[c]) * nr];
+  }
+}
+}  // namespace
+
+TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
+                   const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
+                   int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s) {
+  TreeId out;
+  const int mt = int(rows.size());
+  if (mt == 0) return out;
+  auto drows = to_device_tmp(rows, s);
+  IdMatProb sp = colspec;
+  sp.kind = 0;
+  sp.m = mt;
+  sp.cand = drows.p;
+  sp.ncol = idmat_ncol(0, sp.n1, sp.n2, sp.M, sp.normal);
+  // Y^T for all rows, optionally sketched
+  int nr = sp.ncol;
+  TBuf<double> Yt(size_t(sp.ncol) * mt, s);
+  sp.W = Yt.p;
+  sp.ldw = sp.ncol;
+  eval_idmat({sp}, S, E1, e1s, E2, e2s, s);
+  TBuf<double> Zt;
+  const double* Z = Yt.p;
+  if (sp.ncol > sketch_cols && sketch_width < sp.ncol) {
+    nr = sketch_width;
+    TBuf<double> Om(size_t(sp.ncol) * nr, s);
+    fill_rademacher(Om.p, Om.n, seed, s);
+    Zt = TBuf<double>(size_t(nr) * mt, s);
+    batched_gemm({GemmProb{Om.p, Yt.p, Zt.p, nr, mt, sp.ncol, sp.ncol, sp.ncol, nr, 1, 0, 1.0, 0.0}}, s);
+    Z = Zt.p;
+  }
+  TBuf<double> mx(1, s);
+  max_colnorm(Z, nr, mt, nr, mx.p, s);
+  double hmx = 0;
+  RW_CUDA(cudaMemcpyAsync(&hmx, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  RW_CUDA(cudaStreamSynchronize(s));
+  const double tol_abs = tol * hmx;
+
+  // level structure: each job has candidate positions (into rows) and the
+  // indices of its child jobs in the previous level
+  struct TJob { std::vector<int> cand; int c0 = -1, c1 = -1; int k = 0; std::vector<int> skel; size_t poff = 0; };
+  std::vector<std::vector<TJob>> levels;
+  std::vector<DBuf<double>> Pl;  // per level: interpolation matrices (m_j x k_j, ld m_j)
+  std::vector<TJob> cur;
+  for (int r0 = 0; r0 < mt; r0 += chunk) {
+    TJob j;
+    for (int r = r0; r < std::min(mt, r0 + chunk); ++r) j.cand.push_back(r);
+    cur.push_back(j);
+  }
+  while (true) {
+    std::vector<int> cand_all;
+    for (auto& j : cur) cand_all.insert(cand_all.end(), j.cand.begin(), j.cand.end());
+    auto dcand = to_device_tmp(cand_all, s);
+    TBuf<double> Wl(size_t(nr) * cand_all.size(), s);
+    TBuf<double> nrm(2 * cand_all.size(), s);
+    TBuf<int> piv(cand_all.size(), s), rk(cur.size(), s);
+    k_gather_cols<<<std::min(ceil_div((long long)nr * cand_all.size(), 256), 4096), 256, 0, s>>>(
+        Z, nr, dcand.p, int(cand_all.size()), Wl.p);
+    RW_CHECK_LAUNCH();
+    std::vector<IdProb> ip;
+    size_t off = 0;
+    for (size_t b = 0; b < cur.size(); ++b) {
+      IdProb q{};
+      q.W = Wl.p + off * nr;
+      q.ldw = nr;
+      q.nr = nr;
+      q.nc = int(cur[b].cand.size());
+      q.tol_abs = tol_abs;
+      q.tol_rel = 0.0;
+      q.min_rank = 0;
+      q.max_rank = q.nc;
+      q.piv = piv.p + off;
+      q.norms = nrm.p + 2 * off;
+      q.P = nullptr;
+      q.ldp = q.nc;
+      q.rank = rk.p + b;
+      ip.push_back(q);
+      off += cur[b].cand.size();
+    }
+    batched_id(ip, s);
+    std::vector<int> hk(cur.size()), hp(cand_all.size());
+    RW_CUDA(cudaMemcpyAsync(hk.data(), rk.p, hk.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RW_CUDA(cudaMemcpyAsync(hp.data(), piv.p, hp.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RW_CUDA(cudaStreamSynchronize(s));
+    size_t psz = 0;
+    off = 0;
+    int mxe = 0;
+    for (size_t b = 0; b < cur.size(); ++b) {
+      cur[b].k = hk[b];
+      cur[b].skel.clear();
+      for (int i = 0; i < hk[b]; ++i) cur[b].skel.push_back(cur[b].cand[hp[off + i]]);
+      cur[b].poff = psz;
+      psz += cur[b].cand.size() * size_t(hk[b]);
+      mxe = std::max(mxe, int(cur[b].cand.size()) * hk[b]);
+      off += cur[b].cand.size();
+    }
+    DBuf<double> P(std::max<size_t>(psz, 1));
+    for (size_t b = 0; b < cur.size(); ++b) {
+      ip[b].P = P.p + cur[b].poff;
+      ip[b].ldp = int(cur[b].cand.size());
+    }
+    batched_id_interp(ip, mxe, s);
+    Pl.push_back(std::move(P));
+    levels.push_back(cur);
+    if (cur.size() == 1) break;
+    std::vector<TJob> nxt;
+    for (size_t b = 0; b < cur.size(); b += 2) {
+      TJob j;
+      j.c0 = int(b);
+      j.c1 = (b + 1 < cur.size()) ? int(b + 1) : -1;
+      j.cand = cur[b].skel;
+      if (j.c1 >= 0) j.cand.insert(j.cand.end(), cur[b + 1].skel.begin(), cur[b + 1].skel.end());
+      nxt.push_back(j);
+    }
+    // keep the (small) sync-free guard: wait for this level's buffers before reuse
+    cur = nxt;
+  }
+  const TJob& root = levels.back()[0];
+  out.k = root.k;
+  out.skel = root.skel;
+  out.P.alloc(std::max<size_t>(size_t(mt) * out.k, 1));
+  if (out.k == 0) return out;
+  // top-down products: Wmap[level][job] = (m_j x k) map of candidates to the root skeleton
+  std::vector<DBuf<double>> Wm(levels.size());
+  const int top = int(levels.size()) - 1;
+  {
+    size_t sz = 0;
+    for (auto& j : levels[top]) sz += j.cand.size() * size_t(out.k);
+    Wm[top].alloc(std::max<size_t>(sz, 1));
+    RW_CUDA(cudaMemcpyAsync(Wm[top].p, Pl[top].p + root.poff, root.cand.size() * size_t(out.k) * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  for (int lv = top; lv > 0; --lv) {
+    auto& par = levels[lv];
+    auto& ch = levels[lv - 1];
+    std::vector<size_t> woff(ch.size());
+    size_t sz = 0;
+    for (size_t b = 0; b < ch.size(); ++b) { woff[b] = sz; sz += ch[b].cand.size() * size_t(out.k); }
+    const bool bottom = (lv - 1 == 0);
+    if (!bottom) Wm[lv - 1].alloc(std::max<size_t>(sz, 1));
+    std::vector<GemmProb> gm;
+    size_t poff_in_parent = 0;
+    std::vector<size_t> wpar(par.size());
+    { size_t o = 0; for (size_t b = 0; b < par.size(); ++b) { wpar[b] = o; o += par[b].cand.size() * size_t(out.k); } }
+    for (size_t pb = 0; pb < par.size(); ++pb) {
+      const int mp = int(par[pb].cand.size());
+      int slice = 0;
+      for (int cidx : {par[pb].c0, par[pb].c1}) {
+        if (cidx < 0) continue;
+        const TJob& c = ch[cidx];
+        const double* M = Wm[lv].p + wpar[pb] + slice;  // rows slice of the parent's map, ld mp
+        double* C;
+        int ldc;
+        if (bottom) { C = out.P.p + c.cand[0]; ldc = mt; } else { C = Wm[lv - 1].p + woff[cidx]; ldc = int(c.cand.size()); }
+        gm.push_back(GemmProb{Pl[lv - 1].p + c.poff, M, C, int(c.cand.size()), out.k, c.k, int(c.cand.size()), mp, ldc,
+                              0, 0, 1.0, 0.0});
+        slice += c.k;
+      }
+    }
+    (void)poff_in_parent;
+    batched_gemm(gm, s);
+  }
+  if (top == 0) {
+    RW_CUDA(cudaMemcpyAsync(out.P.p, Pl[0].p + root.poff, size_t(mt) * out.k * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  // keep buffers alive until the stream has consumed them
+  RW_CUDA(cudaStreamSynchronize(s));
+  return out;
+}
+
+// ====================================================================== HBS build
+namespace {
+
+struct Geo { double cx, cy, rad; };
+
+Geo node_geo(const std::vector<double>& x, const std::vector<double>& y, int lo, int hi) {
+  double cx = 0, cy = 0;
+  for (int i = lo; i < hi; ++i) { cx += x[i]; cy += y[i]; }
+  cx /= (hi - lo);
+  cy /= (hi - lo);
+  double r2 = 0;
+  for (int i = lo; i < hi; ++i) r2 = std::max(r2, (x[i] - cx) * (x[i] - cx) + (y[i] - cy) * (y[i] - cy));
+  return Geo{cx, cy, std::sqrt(r2)};
+}
+
+}  // namespace
+
+void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
+  nodes_ = &nodes;
+  N = nodes.n;
+  require(N >= 1, "HBS: empty node set");
+  L = 0;
+  while ((N + (1 << L) - 1) / (1 << L) > o.leaf_points) ++L;
+  node.assign(size_t(2) << L, HbsNode());
+  node[1].lo = 0;
+  node[1].hi = N;
+  for (int h = 1; h < (1 << L); ++h) {
+    const int mid = (node[h].lo + node[h].hi) / 2;
+    node[2 * h].lo = node[h].lo;
+    node[2 * h].hi = mid;
+    node[2 * h + 1].lo = mid;
+    node[2 * h + 1].hi = node[h].hi;
+  }
+  lev.clear();
+  lev.resize(L + 1);
+  const NodesView V = nodes.view();
+  const auto& hx = nodes.hx;
+  const auto& hy = nodes.hy;
+  max_rank = 0;
+  bytes = 0;
+
+  // ---------------------------------------------------------- compression
+  for (int l = L; l >= 1; --l) {
+    const int h0 = 1 << l, nn = 1 << l;
+    std::vector<int> idx;  // candidate / near index lists, concatenated
+    std::vector<size_t> o_cr(nn), o_cc(nn), o_near(nn);
+    std::vector<int> n_near(nn), m(nn);
+    std::vector<Geo> geo(nn);
+    for (int t = 0; t < nn; ++t) {
+      HbsNode& nd = node[h0 + t];
+      std::vector<int> cr, cc;
+      if (l == L) {
+        for (int d = 2 * nd.lo; d < 2 * nd.hi; ++d) cr.push_back(d);
+        cc = cr;
+      } else {
+        const HbsNode& a = node[2 * (h0 + t)];
+        const HbsNode& b = node[2 * (h0 + t) + 1];
+        cr = a.skr; cr.insert(cr.end(), b.skr.begin(), b.skr.end());
+        cc = a.skc; cc.insert(cc.end(), b.skc.begin(), b.skc.end());
+      }
+      nd.m = int(cr.size());
+      m[t] = nd.m;
+      geo[t] = node_geo(hx, hy, nd.lo, nd.hi);
+      const double R = o.proxy_ratio * geo[t].rad, R2 = R * R;
+      o_cr[t] = idx.size(); idx.insert(idx.end(), cr.begin(), cr.end());
+      o_cc[t] = idx.size(); idx.insert(idx.end(), cc.begin(), cc.end());
+      o_near[t] = idx.size();
+      int cnt = 0;
+      for (int j = 0; j < N; ++j) {
+        if (j >= nd.lo && j < nd.hi) continue;
+        const double dx = hx[j] - geo[t].cx, dy = hy[j] - geo[t].cy;
+        if (dx * dx + dy * dy < R2) { idx.push_back(2 * j); idx.push_back(2 * j + 1); cnt += 2; }
+      }
+      n_near[t] = cnt;
+    }
+    DBuf<int> didx = to_device(idx, s);
+    IdBatch batch;
+    for (int t = 0; t < nn; ++t) {
+      const double R = o.proxy_ratio * geo[t].rad;
+      for (int kind = 0; kind < 2; ++kind) {
+        IdMatProb p{};
+        p.kind = kind;
+        p.m = m[t];
+        p.cand = didx.p + (kind == 0 ? o_cr[t] : o_cc[t]);
+        p.n1 = n_near[t];
+        p.e1 = didx.p + o_near[t];
+        p.n2 = 0;
+        p.e2 = nullptr;
+        p.cx = geo[t].cx;
+        p.cy = geo[t].cy;
+        p.R = R;
+        p.M = o.n_proxy;
+        p.normal = 1;
+        batch.add(p, o.sketch_cols, m[t] + 16);
+      }
+    }
+    batch.run(V, V, true, V, true, o.id_tol, {}, {}, {}, {}, o.seed + l, s);
+    std::vector<int> kfix(2 * nn), redo, minr(2 * nn, 0), maxr(2 * nn);
+    for (int t = 0; t < nn; ++t) {
+      int k = std::max(batch.h_rank[2 * t], batch.h_rank[2 * t + 1]);
+      k = std::max(1, std::min(k, m[t]));
+      node[h0 + t].k = k;
+      for (int q = 0; q < 2; ++q) {
+        maxr[2 * t + q] = k;
+        minr[2 * t + q] = k;
+        if (batch.h_rank[2 * t + q] != k) redo.push_back(2 * t + q);
+      }
+    }
+    if (!redo.empty()) batch.run(V, V, true, V, true, 0.0, {}, redo, minr, maxr, o.seed + l, s);
+    // storage for U (m x k), V (m x k -> transposed to Vt)
+    Level& LV = lev[l];
+    LV.oU.resize(nn); LV.oVt.resize(nn);
+    LV.koff.assign(nn + 1, 0);
+    size_t su = 0;
+    for (int t = 0; t < nn; ++t) {
+      LV.oU[t] = su;
+      su += size_t(m[t]) * node[h0 + t].k;
+      LV.koff[t + 1] = LV.koff[t] + node[h0 + t].k;
+      max_rank = std::max(max_rank, node[h0 + t].k);
+    }
+    LV.oVt = LV.oU;
+    LV.U.alloc(std::max<size_t>(su, 1));
+    LV.Vt.alloc(std::max<size_t>(su, 1));
+    TBuf<double> Vtmp(std::max<size_t>(su, 1), s);
+    std::vector<double*> Pp(2 * nn);
+    std::vector<int> ldp(2 * nn);
+    for (int t = 0; t < nn; ++t) {
+      Pp[2 * t] = LV.U.p + LV.oU[t]; ldp[2 * t] = m[t];
+      Pp[2 * t + 1] = Vtmp.p + LV.oU[t]; ldp[2 * t + 1] = m[t];
+    }
+    batch.interp(Pp, ldp, s);
+    std::vector<TransProb> tp;
+    for (int t = 0; t < nn; ++t) tp.push_back(TransProb{Vtmp.p + LV.oU[t], m[t], node[h0 + t].k, m[t], LV.Vt.p + LV.oVt[t], node[h0 + t].k});
+    batched_transpose(tp, s);
+    auto piv = batch.pivots(s);
+    for (int t = 0; t < nn; ++t) {
+      HbsNode& nd = node[h0 + t];
+      nd.skr.resize(nd.k);
+      nd.skc.resize(nd.k);
+      for (int i = 0; i < nd.k; ++i) {
+        nd.skr[i] = idx[o_cr[t] + piv[batch.piv_off(2 * t) + i]];
+        nd.skc[i] = idx[o_cc[t] + piv[batch.piv_off(2 * t + 1) + i]];
+      }
+    }
+    RW_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ---------------------------------------------------------- B and D blocks
+  {
+    std::vector<int> idx;
+    std::vector<BlockProb> bp;
+    for (int l = 0; l < L; ++l) {
+      const int h0 = 1 << l, nn = 1 << l;
+      Level& LV = lev[l];
+      LV.oB12.resize(nn); LV.oB21.resize(nn);
+      size_t sb = 0;
+      for (int t = 0; t < nn; ++t) {
+        const HbsNode& a = node[2 * (h0 + t)];
+        const HbsNode& b = node[2 * (h0 + t) + 1];
+        LV.oB12[t] = sb; sb += size_t(a.k) * b.k;
+        LV.oB21[t] = sb; sb += size_t(b.k) * a.k;
+      }
+      LV.B.alloc(std::max<size_t>(sb, 1));
+    }
+    // index lists first (device copy), then block problems
+    std::vector<size_t> pos;
+    for (int l = 0; l < L; ++l)
+      for (int t = 0; t < (1 << l); ++t) {
+        const HbsNode& a = node[2 * ((1 << l) + t)];
+        const HbsNode& b = node[2 * ((1 << l) + t) + 1];
+        for (const std::vector<int>* v : {&a.skr, &b.skc, &b.skr, &a.skc}) { pos.push_back(idx.size()); idx.insert(idx.end(), v->begin(), v->end()); }
+      }
+    DBuf<int> didx = to_device(idx, s);
+    size_t q = 0;
+    for (int l = 0; l < L; ++l)
+      for (int t = 0; t < (1 << l); ++t) {
+        const HbsNode& a = node[2 * ((1 << l) + t)];
+        const HbsNode& b = node[2 * ((1 << l) + t) + 1];
+        Level& LV = lev[l];
+        bp.push_back(BlockProb{a.k, b.k, didx.p + pos[q], didx.p + pos[q + 1], 0, 0, 0, 0, 1.0, LV.B.p + LV.oB12[t], a.k});
+        bp.push_back(BlockProb{b.k, a.k, didx.p + pos[q + 2], didx.p + pos[q + 3], 0, 0, 0, 0, 1.0, LV.B.p + LV.oB21[t], b.k});
+        q += 4;
+      }
+    Level& LL = lev[L];
+    const int nl = 1 << L;
+    LL.oD.resize(nl);
+    size_t sd = 0;
+    for (int t = 0; t < nl; ++t) { const HbsNode& nd = node[nl + t]; LL.oD[t] = sd; sd += size_t(4) * (nd.hi - nd.lo) * (nd.hi - nd.lo); }
+    LL.D.alloc(sd);
+    for (int t = 0; t < nl; ++t) {
+      const HbsNode& nd = node[nl + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      bp.push_back(BlockProb{n, n, nullptr, nullptr, 2 * nd.lo, 2 * nd.lo, 0, 0, 1.0, LL.D.p + LL.oD[t], n});
+    }
+    eval_blocks(bp, V, V, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ---------------------------------------------------------- inverse
+  // Per node: D~ (leaf: D; parent: [Dh_a B12; B21 Dh_b]); Dinv = D~^{-1};
+  // Dh = (V* Dinv U)^{-1}; E = Dinv U Dh; F* = Dh V* Dinv; G = Dinv - E V* Dinv.
+  DBuf<double> Dh_prev;  // Dh of the level below (children), offsets koff^2
+  std::vector<size_t> oDh_prev;
+  DBuf<int> flags(size_t(2) << L);
+  flags.zero(s);
+  for (int l = L; l >= 0; --l) {
+    const int h0 = 1 << l, nn = 1 << l;
+    Level& LV = lev[l];
+    std::vector<int> mm(nn);
+    size_t sG = 0;
+    LV.oG.resize(nn);
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      mm[t] = (l == L) ? 2 * (nd.hi - nd.lo) : node[2 * (h0 + t)].k + node[2 * (h0 + t) + 1].k;
+      if (l > 0) require(mm[t] == nd.m, "HBS: inconsistent candidate count");
+      LV.oG[t] = sG;
+      sG += size_t(mm[t]) * mm[t];
+    }
+    TBuf<double> Dt(sG, s), Wk(sG, s);
+    LV.G.alloc(sG);
+    // assemble D~
+    std::vector<CopyProb> cp;
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t];
+      double* dst = Dt.p + LV.oG[t];
+      if (l == L) {
+        cp.push_back(CopyProb{LV.D.p + LV.oD[t], n, n, n, dst, n});
+      } else {
+        const HbsNode& a = node[2 * (h0 + t)];
+        const HbsNode& b = node[2 * (h0 + t) + 1];
+        const int ca = 2 * t, cb = 2 * t + 1;  // child positions in the level below
+        cp.push_back(CopyProb{Dh_prev.p + oDh_prev[ca], a.k, a.k, a.k, dst, n});
+        cp.push_back(CopyProb{Dh_prev.p + oDh_prev[cb], b.k, b.k, b.k, dst + a.k + size_t(a.k) * n, n});
+        cp.push_back(CopyProb{LV.B.p + LV.oB12[t], a.k, b.k, a.k, dst + size_t(a.k) * n, n});
+        cp.push_back(CopyProb{LV.B.p + LV.oB21[t], b.k, a.k, b.k, dst + a.k, n});
+      }
+    }
+    batched_copy(cp, s);
+    // Dinv into G (root: final)
+    std::vector<InvProb> inv;
+    for (int t = 0; t < nn; ++t)
+      inv.push_back(InvProb{Dt.p + LV.oG[t], LV.G.p + LV.oG[t], Wk.p + LV.oG[t], mm[t], mm[t], mm[t], flags.p + h0 + t});
+    batched_inverse(inv, s);
+    if (l == 0) break;
+    // T1 = Dinv U (m x k), T2 = Vt Dinv (k x m), M = Vt T1 (k x k)
+    size_t sk = 0, skk = 0;
+    std::vector<size_t> oT(nn), oK(nn);
+    for (int t = 0; t < nn; ++t) { oT[t] = sk; sk += size_t(mm[t]) * node[h0 + t].k; oK[t] = skk; skk += size_t(node[h0 + t].k) * node[h0 + t].k; }
+    TBuf<double> T1(sk, s), T2(sk, s), M(skk, s), Mw(skk, s);
+    DBuf<double> Dh(std::max<size_t>(skk, 1));
+    LV.E.alloc(sk); LV.F.alloc(sk);
+    LV.oE = oT; LV.oF = oT;
+    std::vector<GemmProb> g1, g2;
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      const double* Di = LV.G.p + LV.oG[t];
+      g1.push_back(GemmProb{Di, LV.U.p + LV.oU[t], T1.p + oT[t], n, k, n, n, n, n, 0, 0, 1.0, 0.0});
+      g1.push_back(GemmProb{LV.Vt.p + LV.oVt[t], Di, T2.p + oT[t], k, n, n, k, n, k, 0, 0, 1.0, 0.0});
+    }
+    batched_gemm(g1, s);
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      g2.push_back(GemmProb{LV.Vt.p + LV.oVt[t], T1.p + oT[t], M.p + oK[t], k, k, n, k, n, k, 0, 0, 1.0, 0.0});
+    }
+    batched_gemm(g2, s);
+    std::vector<InvProb> inv2;
+    for (int t = 0; t < nn; ++t)
+      inv2.push_back(InvProb{M.p + oK[t], Dh.p + oK[t], Mw.p + oK[t], node[h0 + t].k, node[h0 + t].k, node[h0 + t].k, flags.p + h0 + t});
+    batched_inverse(inv2, s);
+    std::vector<GemmProb> g3, g4;
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      g3.push_back(GemmProb{T1.p + oT[t], Dh.p + oK[t], LV.E.p + oT[t], n, k, k, n, k, n, 0, 0, 1.0, 0.0});
+      g3.push_back(GemmProb{Dh.p + oK[t], T2.p + oT[t], LV.F.p + oT[t], k, n, k, k, k, k, 0, 0, 1.0, 0.0});
+    }
+    batched_gemm(g3, s);
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      g4.push_back(GemmProb{LV.E.p + oT[t], T2.p + oT[t], LV.G.p + LV.oG[t], n, n, k, n, k, n, 0, 0, -1.0, 1.0});
+    }
+    batched_gemm(g4, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+    Dh_prev = std::move(Dh);
+    oDh_prev = oK;
+  }
+  auto hf = flags.download(s);
+  for (int f : hf) require(f == 0, "HBS inverse: singular diagonal block", RW_ERR_SINGULAR);
+
+  // ---------------------------------------------------------- statistics
+  inv_elems = fwd_elems = 0;
+  bytes = 0;
+  for (int l = 0; l <= L; ++l) {
+    Level& LV = lev[l];
+    inv_elems += (long long)LV.G.n + (l > 0 ? (long long)LV.E.n + (long long)LV.F.n : 0);
+    fwd_elems += (long long)LV.U.n * (l > 0) + (long long)LV.Vt.n * (l > 0) + (long long)LV.B.n * (l < L) + (long long)LV.D.n;
+    bytes += LV.U.bytes() + LV.Vt.bytes() + LV.E.bytes() + LV.F.bytes() + LV.G.bytes() + LV.B.bytes() + LV.D.bytes();
+  }
+}
+
+void Hbs::make_fp32(cudaStream_t s) {
+  for (int l = 0; l <= L; ++l) {
+    Level& LV = lev[l];
+    LV.G32.alloc(LV.G.n); copy_d2f(LV.G.p, LV.G32.p, LV.G.n, s);
+    if (l > 0) {
+      LV.E32.alloc(LV.E.n); copy_d2f(LV.E.p, LV.E32.p, LV.E.n, s);
+      LV.F32.alloc(LV.F.n); copy_d2f(LV.F.p, LV.F32.p, LV.F.n, s);
+    }
+  }
+  has_fp32 = true;
+}
+
+// ====================================================================== sweeps
+template <class T>
+void Hbs::sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const {
+  const int ld = 2 * N;
+  auto Gp = [&](const Level& LV) -> const T* {
+    if constexpr (std::is_same<T, double>::value) return LV.G.p; else return LV.G32.p;
+  };
+  auto Ep = [&](const Level& LV) -> const T* {
+    if constexpr (std::is_same<T, double>::value) return LV.E.p; else return LV.E32.p;
+  };
+  auto Fp = [&](const Level& LV) -> const T* {
+    if constexpr (std::is_same<T, double>::value) return LV.F.p; else return LV.F32.p;
+  };
+  if (L == 0) {
+    matvec<T>({GemvProb<T>{Gp(lev[0]), b, x, ld, ld, ld, ld, ld, 1.0, 0.0}}, nrhs, s);
+    return;
+  }
+  // per-level vectors uh (K_l x nrhs) and qh (K_l x nrhs)
+  std::vector<TBuf<T>> uh(L + 1), qh(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    const int K = lev[l].koff.back();
+    uh[l] = TBuf<T>(size_t(K) * nrhs, s);
+    qh[l] = TBuf<T>(size_t(K) * nrhs, s);
+  }
+  // up: leaves
+  {
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const int K = LV.koff.back();
+    std::vector<GemvProb<T>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo), k = nd.k;
+      const T* in = b + 2 * nd.lo;
+      ps.push_back(GemvProb<T>{Fp(LV) + LV.oF[t], in, uh[l].p + LV.koff[t], k, n, k, ld, K, 1.0, 0.0});
+      ps.push_back(GemvProb<T>{Gp(LV) + LV.oG[t], in, x + 2 * nd.lo, n, n, n, ld, ld, 1.0, 0.0});
+    }
+    matvec<T>(ps, nrhs, s);
+  }
+  for (int l = L - 1; l >= 1; --l) {
+    const int h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    const int K = LV.koff.back(), KC = LC.koff.back();
+    std::vector<GemvProb<T>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = nd.m, k = nd.k;
+      const T* in = uh[l + 1].p + LC.koff[2 * t];
+      ps.push_back(GemvProb<T>{Fp(LV) + LV.oF[t], in, uh[l].p + LV.koff[t], k, n, k, KC, K, 1.0, 0.0});
+      ps.push_back(GemvProb<T>{Gp(LV) + LV.oG[t], in, qh[l + 1].p + LC.koff[2 * t], n, n, n, KC, KC, 1.0, 0.0});
+    }
+    matvec<T>(ps, nrhs, s);
+  }
+  {
+    const int K1 = lev[1].koff.back();
+    matvec<T>({GemvProb<T>{Gp(lev[0]), uh[1].p, qh[1].p, K1, K1, K1, K1, K1, 1.0, 0.0}}, nrhs, s);
+  }
+  for (int l = 1; l <= L - 1; ++l) {
+    const int h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    const int K = LV.koff.back(), KC = LC.koff.back();
+    std::vector<GemvProb<T>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      ps.push_back(GemvProb<T>{Ep(LV) + LV.oE[t], qh[l].p + LV.koff[t], qh[l + 1].p + LC.koff[2 * t], nd.m, nd.k, nd.m, K, KC, 1.0, 1.0});
+    }
+    matvec<T>(ps, nrhs, s);
+  }
+  {
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const int K = LV.koff.back();
+    std::vector<GemvProb<T>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      ps.push_back(GemvProb<T>{Ep(LV) + LV.oE[t], qh[l].p + LV.koff[t], x + 2 * nd.lo, n, nd.k, n, K, ld, 1.0, 1.0});
+    }
+    matvec<T>(ps, nrhs, s);
+  }
+}
+
+void Hbs::apply_inverse(const double* b, double* x, int nrhs, cudaStream_t s) const { sweep_inverse<double>(b, x, nrhs, s); }
+void Hbs::apply_inverse_f32(const float* b, float* x, int nrhs, cudaStream_t s) const {
+  require(has_fp32, "HBS: FP32 copies not built");
+  sweep_inverse<float>(b, x, nrhs, s);
+}
+
+void Hbs::apply_forward(const double* xin, double* y, int nrhs, cudaStream_t s) const {
+  const int ld = 2 * N;
+  if (L == 0) {
+    matvec<double>({GemvProb<double>{lev[0].D.p, xin, y, ld, ld, ld, ld, ld, 1.0, 0.0}}, nrhs, s);
+    return;
+  }
+  std::vector<TBuf<double>> xh(L + 1), yh(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    const int K = lev[l].koff.back();
+    xh[l] = TBuf<double>(size_t(K) * nrhs, s);
+    yh[l] = TBuf<double>(size_t(K) * nrhs, s);
+  }
+  {
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const int K = LV.koff.back();
+    std::vector<GemvProb<double>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      ps.push_back(GemvProb<double>{LV.Vt.p + LV.oVt[t], xin + 2 * nd.lo, xh[l].p + LV.koff[t], nd.k, n, nd.k, ld, K, 1.0, 0.0});
+      ps.push_back(GemvProb<double>{LV.D.p + LV.oD[t], xin + 2 * nd.lo, y + 2 * nd.lo, n, n, n, ld, ld, 1.0, 0.0});
+    }
+    matvec<double>(ps, nrhs, s);
+  }
+  for (int l = L - 1; l >= 1; --l) {
+    const int h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    const int K = LV.koff.back(), KC = LC.koff.back();
+    std::vector<GemvProb<double>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      ps.push_back(GemvProb<double>{LV.Vt.p + LV.oVt[t], xh[l + 1].p + LC.koff[2 * t], xh[l].p + LV.koff[t], nd.k, nd.m, nd.k, KC, K, 1.0, 0.0});
+    }
+    matvec<double>(ps, nrhs, s);
+  }
+  // sibling interactions at every parent, then interpolation down
+  for (int l = 0; l <= L - 1; ++l) {
+    const int h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    const int KC = LC.koff.back();
+    if (l >= 1) {
+      const int K = LV.koff.back();
+      std::vector<GemvProb<double>> ps;
+      for (int t = 0; t < nn; ++t) {
+        const HbsNode& nd = node[h0 + t];
+        ps.push_back(GemvProb<double>{LV.U.p + LV.oU[t], yh[l].p + LV.koff[t], yh[l + 1].p + LC.koff[2 * t], nd.m, nd.k, nd.m, K, KC, 1.0, 0.0});
+      }
+      matvec<double>(ps, nrhs, s);
+    }
+    std::vector<GemvProb<double>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& a = node[2 * (h0 + t)];
+      const HbsNode& b = node[2 * (h0 + t) + 1];
+      const int ia = LC.koff[2 * t], ib = LC.koff[2 * t + 1];
+      const double beta = (l >= 1) ? 1.0 : 0.0;
+      ps.push_back(GemvProb<double>{LV.B.p + LV.oB12[t], xh[l + 1].p + ib, yh[l + 1].p + ia, a.k, b.k, a.k, KC, KC, 1.0, beta});
+      ps.push_back(GemvProb<double>{LV.B.p + LV.oB21[t], xh[l + 1].p + ia, yh[l + 1].p + ib, b.k, a.k, b.k, KC, KC, 1.0, beta});
+    }
+    matvec<double>(ps, nrhs, s);
+  }
+  {
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const int K = LV.koff.back();
+    std::vector<GemvProb<double>> ps;
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      ps.push_back(GemvProb<double>{LV.U.p + LV.oU[t], yh[l].p + LV.koff[t], y + 2 * nd.lo, n, nd.k, n, K, ld, 1.0, 1.0});
+    }
+    matvec<double>(ps, nrhs, s);
+  }
+}
+
+}  // namespace rw

@@ -1,0 +1,114 @@
+// Hierarchically block separable (HBS) representation of A on a node set and
+// its inverse, after Gillman, Young and Martinsson (2012), which the paper
+// takes as its fast direct solver for the original discretisation (Sec. 3
+// preamble, Sec. 4.2).  Also the interpolative-decomposition helpers shared
+// with the refinement factorisation.
+#pragma once
+#include "dense.cuh"
+#include "eval.cuh"
+
+namespace rw {
+
+struct Opts {
+  int leaf_points = 64;
+  double id_tol = 1e-12;
+  int n_proxy = 64;
+  double proxy_ratio = 2.0;
+  int n_proxy_refine = 96;
+  double div_ratio = 2.0;
+  double bas_ratio = 1.5;
+  int dense_pp_max_points = 64;
+  int sketch_cols = 2048;
+  int sketch_width = 192;
+  double gmres_tol = 1e-10;
+  int gmres_maxit = 30;
+  int gmres_restarts = 4;
+  unsigned long long seed = 0x5eed2108ull;
+};
+
+// A list of row-interpolative decompositions evaluated on the fly: each job
+// is an IdMatProb (without output) whose matrix is optionally compressed by a
+// +-1 sketch when it has more than `sketch_cols` columns.
+class IdBatch {
+ public:
+  struct Job {
+    IdMatProb spec;
+    int sk_width = 0;  // 0: no sketch; else rows of the sketched W
+    int nr = 0;        // rows of W handed to the QR
+    size_t woff = 0, moff = 0;
+  };
+  std::vector<Job> jobs;
+  DBuf<double> W, norms;
+  DBuf<int> piv, rank;
+  std::vector<int> h_rank;
+
+  int add(const IdMatProb& spec, int sketch_cols, int sketch_width);
+  // Evaluate (all jobs, or the listed subset) and factor.  min_rank/max_rank
+  // are per job (empty: 0 / unlimited).  Returns ranks (host).
+  void run(const NodesView& S, const NodesView& E1, bool e1s, const NodesView& E2, bool e2s,
+           double tol_rel, const std::vector<double>& tol_abs, const std::vector<int>& subset,
+           const std::vector<int>& min_rank, const std::vector<int>& max_rank, unsigned long long seed,
+           cudaStream_t s);
+  // P_j (m_j x rank_j, ld ldp_j) for every job with a non-null target.
+  void interp(const std::vector<double*>& P, const std::vector<int>& ldp, cudaStream_t s);
+  std::vector<int> pivots(cudaStream_t s) const;  // concatenated, offsets moff
+  size_t piv_off(int j) const { return jobs[j].moff; }
+};
+
+// Hierarchical row ID of a tall matrix Y (rows = `rows`, DOFs of node set S;
+// columns given by a column spec as in IdMatProb): chunks of `chunk` rows are
+// decomposed independently and merged pairwise up a binary tree, so that the
+// cost stays linear in the number of rows (Sec. 3.3, the hierarchical ID of the
+// far field).  Absolute tolerance = tol * max row norm of Y (Def. 3.1 with
+// ||Y|| bounded below by its largest row norm).
+struct TreeId {
+  int k = 0;
+  std::vector<int> skel;  // positions into `rows` of the skeleton rows
+  DBuf<double> P;         // m x k interpolation matrix, P[skel] = I
+};
+TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
+                   const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
+                   int sketch_cols, int sketch_width, unsigned long long seed, int chunk,
+                   cudaStream_t s);
+
+struct HbsNode {
+  int lo = 0, hi = 0;  // point range
+  int k = 0;           // rank (skeleton size)
+  int m = 0;           // candidate count (rows of U, V, E, F^T, G)
+  std::vector<int> skr, skc;  // skeleton DOFs (rows / columns)
+};
+
+class Hbs {
+ public:
+  int N = 0, L = 0;
+  std::vector<HbsNode> node;  // heap order, index 1 .. 2^{L+1}-1
+  // per-level storage (index = level)
+  struct Level {
+    DBuf<double> U, Vt, E, F, G, B, D, Gf, Ef, Ff;  // F holds F* (k x m); *f: FP32 copies
+    DBuf<float> U32;  // unused placeholder for symmetry
+    std::vector<size_t> oU, oVt, oE, oF, oG, oB12, oB21, oD;
+    std::vector<int> koff;  // prefix sums of ranks at this level (size nn+1)
+    DBuf<float> G32, E32, F32;
+  };
+  std::vector<Level> lev;
+  long long inv_elems = 0, fwd_elems = 0;
+  size_t bytes = 0;
+  int max_rank = 0;
+
+  // Build from a node set (positions on host in `nodes.hx/hy` for planning).
+  void build(const Nodes& nodes, const Opts& o, cudaStream_t s);
+  // x = A^{-1} b, b and x: 2N x nrhs (ld 2N).  Template on the sweep type.
+  void apply_inverse(const double* b, double* x, int nrhs, cudaStream_t s) const;
+  void apply_inverse_f32(const float* b, float* x, int nrhs, cudaStream_t s) const;
+  // y = A x via the forward representation.
+  void apply_forward(const double* x, double* y, int nrhs, cudaStream_t s) const;
+  void make_fp32(cudaStream_t s);
+  bool has_fp32 = false;
+
+ private:
+  template <class T>
+  void sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const;
+  const Nodes* nodes_ = nullptr;
+};
+
+}  // namespace rw

@@ -1,0 +1,282 @@
+// Algorithm 1 (pre-computation and solve) for one local refinement.
+//
+// Ordering of the extended system: [o ; p] = the original points in panel
+// order (kept and cut interleaved as on the wall) followed by the added
+// points in window order.  A~ = blkdiag(A_oo, A_pp); the nonzero blocks of
+// Q are -A_kc, A_kp (rows in I_k) and A_pk (rows in I_p) (Sec. 3.2).
+//
+// Low-rank factors (Sec. 3.3-3.4, uniform row-ID format: L = interpolation
+// matrices, R = skeleton rows of A):
+//  * far rows of I_k (outside P^div): one hierarchical ID against proxy
+//    sources on P^bas, shared by A_kc and A_kp (Remark after Def. 3.1);
+//  * near rows of I_k: one direct ID of [A_kc^near | A_kp^near];
+//  * A_pk: one hierarchical ID of the rows of [A_{p,div} | A_pk^near];
+//  so L = blkdiag(L_k, L_pk) with L_k = [P_far ; P_near] on the k rows and
+//  R = [[0, -A(J_k, I_c), A(J_k, I_p)], [A(J_pk, I_k), 0, 0]].
+//  This is the row ID of the blockwise factor L_1 (whose kc and kp column
+//  blocks share their far and near interpolation matrices), i.e. the
+//  recompressed factorisation of Sec. 3.4 reached without duplicated columns.
+#include "refine.cuh"
+#include <algorithm>
+#include <cmath>
+
+namespace rw {
+
+namespace {
+
+__global__ void k_identity(double* W, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x)
+    W[e] = (e % n == e / n) ? 1.0 : 0.0;
+}
+
+__global__ void k_zero_cols(double* A, int ld, int nrows, const int* cols, int ncols) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nrows * ncols; e += gridDim.x * blockDim.x) {
+    const int r = e % nrows, c = e / nrows;
+    A[r + size_t(cols[c]) * ld] = 0.0;
+  }
+}
+
+}  // namespace
+
+void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::vector<int>& lvl, cudaStream_t s) {
+  wall = &w;
+  const Opts& o = w.opts;
+  const int P = w.n_panels;
+  require(!pan.empty() && pan.size() == lvl.size(), "refine: need one level per cut panel");
+  require(int(pan.size()) < P, "refine: cannot cut every panel");
+  std::vector<char> cut(P, 0);
+  for (size_t i = 0; i < pan.size(); ++i) {
+    require(pan[i] >= 0 && pan[i] < P, "refine: panel id out of range");
+    require(!cut[pan[i]], "refine: cut panels must be distinct");
+    require(lvl[i] >= 0 && lvl[i] <= 12, "refine: level must be in 0..12");
+    if (i > 0) require(pan[i] == (pan[i - 1] + 1) % P, "refine: cut panels must be a contiguous run (mod P)");
+    cut[pan[i]] = 1;
+  }
+  panels = pan;
+  levels = lvl;
+  No = w.nodes.n;
+  Ic.clear();
+  Ik.clear();
+  for (int j = 0; j < P; ++j)
+    for (int q = 0; q < 16; ++q) (cut[j] ? Ic : Ik).push_back(16 * j + q);
+  Nc = int(Ic.size());
+  Nk = int(Ik.size());
+
+  // a1: added nodes (window order)
+  std::vector<double> ta, tb;
+  std::vector<int> pstart(P, -1);
+  const double h = 2.0 * kPi / P;
+  int np = 0;
+  for (size_t i = 0; i < pan.size(); ++i) {
+    const int ns = 1 << lvl[i];
+    pstart[pan[i]] = np;
+    for (int q = 0; q < ns; ++q) {
+      ta.push_back(pan[i] * h + q * (h / ns));
+      tb.push_back(pan[i] * h + (q + 1) * (h / ns));
+    }
+    np += 16 * ns;
+  }
+  Np = np;
+  Nn = Nk + Np;
+  {
+    auto dta = to_device_tmp(ta, s), dtb = to_device_tmp(tb, s);
+    pn.alloc(Np);
+    eval_nodes(w.curve, dta.p, dtb.p, int(ta.size()), pn.buf.p, Np, s);
+    auto all = pn.buf.download(s);
+    pn.hx.assign(all.begin(), all.begin() + Np);
+    pn.hy.assign(all.begin() + Np, all.begin() + 2 * Np);
+  }
+  // refined order maps
+  {
+    std::vector<int> from_o, to_o, from_p, to_p, pts_o_src, pts_o_dst, pts_p_src, pts_p_dst;
+    int in = 0;
+    for (int j = 0; j < P; ++j) {
+      if (!cut[j]) {
+        for (int q = 0; q < 16; ++q, ++in) {
+          pts_o_src.push_back(16 * j + q); pts_o_dst.push_back(in);
+          for (int a = 0; a < 2; ++a) { from_o.push_back(2 * in + a); to_o.push_back(2 * (16 * j + q) + a); }
+        }
+      } else {
+        int ns = 0;
+        for (size_t i = 0; i < pan.size(); ++i) if (pan[i] == j) ns = 16 << lvl[i];
+        for (int q = 0; q < ns; ++q, ++in) {
+          pts_p_src.push_back(pstart[j] + q); pts_p_dst.push_back(in);
+          for (int a = 0; a < 2; ++a) { from_p.push_back(2 * in + a); to_p.push_back(2 * (pstart[j] + q) + a); }
+        }
+      }
+    }
+    n_from_o = to_device(from_o, s); n_to_o = to_device(to_o, s);
+    n_from_p = to_device(from_p, s); n_to_p = to_device(to_p, s);
+    nko = int(from_o.size());
+    nkp = int(from_p.size());
+    nn.alloc(Nn);
+    auto so = to_device_tmp(pts_o_src, s), dso = to_device_tmp(pts_o_dst, s);
+    auto sp = to_device_tmp(pts_p_src, s), dsp = to_device_tmp(pts_p_dst, s);
+    gather_scatter(w.nodes.buf.p, No, so.p, nn.buf.p, Nn, dso.p, int(pts_o_src.size()), 6, s);
+    gather_scatter(pn.buf.p, Np, sp.p, nn.buf.p, Nn, dsp.p, int(pts_p_src.size()), 6, s);
+    std::vector<int> dcv;
+    for (int i : Ic) { dcv.push_back(2 * i); dcv.push_back(2 * i + 1); }
+    dc = to_device(dcv, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  }
+  // Gamma_r: centre and radius of the cut and added points
+  double cx = 0, cy = 0;
+  for (int i : Ic) { cx += w.nodes.hx[i]; cy += w.nodes.hy[i]; }
+  for (int i = 0; i < Np; ++i) { cx += pn.hx[i]; cy += pn.hy[i]; }
+  cx /= (Nc + Np);
+  cy /= (Nc + Np);
+  double rho2 = 0;
+  for (int i : Ic) rho2 = std::max(rho2, (w.nodes.hx[i] - cx) * (w.nodes.hx[i] - cx) + (w.nodes.hy[i] - cy) * (w.nodes.hy[i] - cy));
+  for (int i = 0; i < Np; ++i) rho2 = std::max(rho2, (pn.hx[i] - cx) * (pn.hx[i] - cx) + (pn.hy[i] - cy) * (pn.hy[i] - cy));
+  const double rho = std::sqrt(rho2), Rdiv = o.div_ratio * rho, Rbas = o.bas_ratio * rho;
+  std::vector<int> far_d, near_d;
+  for (int i : Ik) {
+    const double dx = w.nodes.hx[i] - cx, dy = w.nodes.hy[i] - cy;
+    auto& v = (dx * dx + dy * dy >= Rdiv * Rdiv) ? far_d : near_d;
+    v.push_back(2 * i);
+    v.push_back(2 * i + 1);
+  }
+
+  // a2: A_pp^{-1} (dense below the threshold: a single-leaf HBS is the dense inverse)
+  {
+    Opts opp = o;
+    pp_dense = Np <= o.dense_pp_max_points;
+    if (pp_dense) opp.leaf_points = Np;
+    hpp.build(pn, opp, s);
+    hpp.make_fp32(s);
+  }
+
+  const NodesView VW = w.nodes.view(), VP = pn.view();
+  // a3: far rows of I_k against P^bas (shared by A_kc and A_kp)
+  TreeId tf, tn, tp;
+  {
+    IdMatProb cs{};
+    cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
+    tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s);
+  }
+  // near rows of I_k: [A_kc^near | A_kp^near]
+  DBuf<int> dall_p;
+  {
+    std::vector<int> pd(2 * Np);
+    for (int i = 0; i < 2 * Np; ++i) pd[i] = i;
+    dall_p = to_device(pd, s);
+    IdMatProb cs{};
+    cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
+    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
+  }
+  // A_pk: rows of [A_{p,div} | A_pk^near | n_p]
+  DBuf<int> dnear;
+  {
+    dnear = to_device(near_d, s);
+    std::vector<int> prow(2 * Np);
+    for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
+    IdMatProb cs{};
+    cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
+    tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s);
+  }
+  kf = tf.k; kn = tn.k; kpk = tp.k; kk = kf + kn; k = kk + kpk;
+
+  // L_o (2No x kk) and L_p (2Np x kpk)
+  Lo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
+  Lo.zero(s);
+  {
+    auto dfar = to_device_tmp(far_d, s);
+    if (kf) gather_scatter(tf.P.p, int(far_d.size()), nullptr, Lo.p, 2 * No, dfar.p, int(far_d.size()), kf, s);
+    if (kn) gather_scatter(tn.P.p, int(near_d.size()), nullptr, Lo.p + size_t(2) * No * kf, 2 * No, dnear.p, int(near_d.size()), kn, s);
+    Lp = std::move(tp.P);
+    RW_CUDA(cudaStreamSynchronize(s));
+  }
+  // skeleton DOFs
+  std::vector<int> Jk, Jpk;
+  for (int i : tf.skel) Jk.push_back(far_d[i]);
+  for (int i : tn.skel) Jk.push_back(near_d[i]);
+  for (int i : tp.skel) Jpk.push_back(i);
+  auto dJk = to_device_tmp(Jk, s), dJpk = to_device_tmp(Jpk, s);
+  Rkc.alloc(std::max<size_t>(size_t(kk) * 2 * Nc, 1));
+  Rkp.alloc(std::max<size_t>(size_t(kk) * 2 * Np, 1));
+  Rpk.alloc(std::max<size_t>(size_t(kpk) * 2 * No, 1));
+  eval_blocks({BlockProb{kk, 2 * Nc, dJk.p, dc.p, 0, 0, 0, 0, -1.0, Rkc.p, kk},
+               BlockProb{kk, 2 * Np, dJk.p, nullptr, 0, 0, 0, 1, 1.0, Rkp.p, kk},
+               BlockProb{kpk, 2 * No, dJpk.p, nullptr, 0, 0, 1, 0, 1.0, Rpk.p, kpk}},
+              VW, VP, s);
+  if (kpk) {
+    k_zero_cols<<<ceil_div((long long)kpk * 2 * Nc, 256), 256, 0, s>>>(Rpk.p, kpk, kpk, dc.p, 2 * Nc);
+    RW_CHECK_LAUNCH();
+  }
+  // a5: X = A~^{-1} L
+  Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
+  Xp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
+  if (kk) w.hbs.apply_inverse(Lo.p, Xo.p, kk, s);
+  if (kpk) hpp.apply_inverse(Lp.p, Xp.p, kpk, s);
+  // a6: W = I + R X and its inverse
+  {
+    TBuf<double> W(size_t(k) * k, s), Ww(size_t(k) * k, s), Xc(size_t(2) * Nc * std::max(kk, 1), s);
+    k_identity<<<ceil_div((long long)k * k, 256), 256, 0, s>>>(W.p, k);
+    RW_CHECK_LAUNCH();
+    if (kk) gather_scatter(Xo.p, 2 * No, dc.p, Xc.p, 2 * Nc, nullptr, 2 * Nc, kk, s);
+    std::vector<GemmProb> g;
+    if (kk) g.push_back(GemmProb{Rkc.p, Xc.p, W.p, kk, kk, 2 * Nc, kk, 2 * Nc, k, 0, 0, 1.0, 1.0});
+    if (kk && kpk) g.push_back(GemmProb{Rkp.p, Xp.p, W.p + size_t(kk) * k, kk, kpk, 2 * Np, kk, 2 * Np, k, 0, 0, 1.0, 1.0});
+    if (kk && kpk) g.push_back(GemmProb{Rpk.p, Xo.p, W.p + kk, kpk, kk, 2 * No, kpk, 2 * No, k, 0, 0, 1.0, 1.0});
+    batched_gemm(g, s);
+    Winv.alloc(std::max<size_t>(size_t(k) * k, 1));
+    DBuf<int> flag(1);
+    flag.zero(s);
+    batched_inverse({InvProb{W.p, Winv.p, Ww.p, k, k, k, flag.p}}, s);
+    auto hf = flag.download(s);
+    require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
+  }
+  bytes = Lo.bytes() + Lp.bytes() + Rkc.bytes() + Rkp.bytes() + Rpk.bytes() + Xo.bytes() + Xp.bytes() + Winv.bytes() +
+          hpp.bytes + pn.buf.bytes() + nn.buf.bytes();
+}
+
+void Refinement::woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t s) const {
+  if (k == 0) return;
+  TBuf<double> yc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s), z(size_t(k) * nrhs, s);
+  gather_scatter(yo, 2 * No, dc.p, yc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
+  // r = R y
+  std::vector<GemvProb<double>> p1;
+  if (kk) p1.push_back(GemvProb<double>{Rkc.p, yc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
+  if (kpk) p1.push_back(GemvProb<double>{Rpk.p, yo, r.p + kk, kpk, 2 * No, kpk, 2 * No, k, 1.0, 0.0});
+  matvec<double>(p1, nrhs, s);
+  if (kk && Np) matvec<double>({GemvProb<double>{Rkp.p, yp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, 1.0}}, nrhs, s);
+  // z = W^{-1} r
+  matvec<double>({GemvProb<double>{Winv.p, r.p, z.p, k, k, k, k, k, 1.0, 0.0}}, nrhs, s);
+  // y -= X z
+  std::vector<GemvProb<double>> p2;
+  if (kk) p2.push_back(GemvProb<double>{Xo.p, z.p, yo, 2 * No, kk, 2 * No, k, 2 * No, -1.0, 1.0});
+  if (kpk) p2.push_back(GemvProb<double>{Xp.p, z.p + kk, yp, 2 * Np, kpk, 2 * Np, k, 2 * Np, -1.0, 1.0});
+  matvec<double>(p2, nrhs, s);
+}
+
+void Refinement::solve_direct(const double* g, double* tau, int nrhs, cudaStream_t s) const {
+  TBuf<double> go(size_t(2) * No * nrhs, s), gp(size_t(2) * Np * nrhs, s);
+  TBuf<double> yo(size_t(2) * No * nrhs, s), yp(size_t(2) * Np * nrhs, s);
+  fill_zero(go.p, go.n, s);
+  gather_scatter(g, 2 * Nn, n_from_o.p, go.p, 2 * No, n_to_o.p, nko, nrhs, s);
+  gather_scatter(g, 2 * Nn, n_from_p.p, gp.p, 2 * Np, n_to_p.p, nkp, nrhs, s);
+  wall->hbs.apply_inverse(go.p, yo.p, nrhs, s);
+  hpp.apply_inverse(gp.p, yp.p, nrhs, s);
+  woodbury_correct(yo.p, yp.p, nrhs, s);
+  gather_scatter(yo.p, 2 * No, n_to_o.p, tau, 2 * Nn, n_from_o.p, nko, nrhs, s);
+  gather_scatter(yp.p, 2 * Np, n_to_p.p, tau, 2 * Nn, n_from_p.p, nkp, nrhs, s);
+}
+
+void Refinement::apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const {
+  wall->hbs.apply_forward(xo, yo, nrhs, s);
+  hpp.apply_forward(xp, yp, nrhs, s);
+  if (k == 0) return;
+  TBuf<double> xc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s);
+  gather_scatter(xo, 2 * No, dc.p, xc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
+  std::vector<GemvProb<double>> p1;
+  if (kk) p1.push_back(GemvProb<double>{Rkc.p, xc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
+  if (kpk) p1.push_back(GemvProb<double>{Rpk.p, xo, r.p + kk, kpk, 2 * No, kpk, 2 * No, k, 1.0, 0.0});
+  matvec<double>(p1, nrhs, s);
+  if (kk && Np) matvec<double>({GemvProb<double>{Rkp.p, xp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, 1.0}}, nrhs, s);
+  std::vector<GemvProb<double>> p2;
+  if (kk) p2.push_back(GemvProb<double>{Lo.p, r.p, yo, 2 * No, kk, 2 * No, k, 2 * No, 1.0, 1.0});
+  if (kpk) p2.push_back(GemvProb<double>{Lp.p, r.p + kk, yp, 2 * Np, kpk, 2 * Np, k, 2 * Np, 1.0, 1.0});
+  matvec<double>(p2, nrhs, s);
+}
+
+}  // namespace rw

@@ -1,0 +1,46 @@
+// Algorithm 1 of the paper on the device: pre-computation for one local
+// refinement (Sec. 3.1-3.4) and the Woodbury solve (Eq. wood).
+#pragma once
+#include "hbs.cuh"
+
+namespace rw {
+
+struct Wall {
+  Curve curve;
+  int n_panels = 0;
+  Opts opts;
+  Nodes nodes;  // original discretisation (panel order)
+  Hbs hbs;      // A_oo
+};
+
+struct Refinement {
+  const Wall* wall = nullptr;
+  std::vector<int> panels, levels;     // cut panels (window order) and levels
+  int No = 0, Nk = 0, Nc = 0, Np = 0, Nn = 0;
+  std::vector<int> Ic, Ik;             // point indices into the wall
+  Nodes pn;                            // added nodes, window order
+  Nodes nn;                            // refined nodes, refined order
+  Hbs hpp;                             // A_pp (single leaf = dense inverse)
+  bool pp_dense = false;
+  int kf = 0, kn = 0, kpk = 0, kk = 0, k = 0;
+  // factors: L_o (2No x kk), L_p (2Np x kpk); R blocks; X = A~^{-1} L; W^{-1}
+  DBuf<double> Lo, Lp, Rkc, Rkp, Rpk, Xo, Xp, Winv;
+  DBuf<int> dc;                  // c DOFs (2Nc) in o numbering
+  DBuf<int> n_from_o, n_to_o;    // refined DOFs that are kept: (n index, o index)
+  DBuf<int> n_from_p, n_to_p;    // refined DOFs that are added: (n index, p index)
+  int nko = 0, nkp = 0;
+  size_t bytes = 0;
+
+  void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s);
+  // Direct solve, device buffers: g, tau (2Nn x nrhs).
+  void solve_direct(const double* g, double* tau, int nrhs, cudaStream_t s) const;
+  // Woodbury apply in ext space: (yo, yp) <- Ainv_ext (yo, yp), yo/yp hold
+  // A~^{-1} g on entry (ld 2No / 2Np).
+  void woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t s) const;
+  // FGMRES on A~ + L R with the FP32-sweep Woodbury preconditioner.
+  void solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres) const;
+  // ext-space operator y = (A~ + L R) x (FP64)
+  void apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
+};
+
+}  // namespace rw

@@ -1,0 +1,185 @@
+// Shared declarations of the rwsolve CUDA library: error handling, device
+// buffers, node sets and the Stokes kernel entries of Sec. 2.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <stdexcept>
+
+#include "../../include/rwsolve.h"
+
+namespace rw {
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define RW_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      throw ::rw::Error(RW_ERR_CUDA, std::string(#call) + ": " +             \
+                                         cudaGetErrorString(e_));            \
+  } while (0)
+
+#define RW_CHECK_LAUNCH() RW_CUDA(cudaGetLastError())
+
+inline void require(bool ok, const std::string& msg, int code = RW_ERR_INVALID) {
+  if (!ok) throw Error(code, msg);
+}
+
+// ---------------------------------------------------------------- memory
+// Owning device buffer (cudaMallocAsync/cudaFreeAsync on the given stream is
+// avoided: handles outlive streams).  Moves only.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  explicit DBuf(size_t count) { alloc(count); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    n = count;
+    if (count) {
+      cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+      if (e != cudaSuccess) {
+        p = nullptr; n = 0;
+        throw Error(RW_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr; n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+  void upload(const std::vector<T>& h, cudaStream_t s) {
+    if (h.size() != n) alloc(h.size());
+    if (n) RW_CUDA(cudaMemcpyAsync(p, h.data(), bytes(), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<T> download(cudaStream_t s) const {
+    std::vector<T> h(n);
+    if (n) {
+      RW_CUDA(cudaMemcpyAsync(h.data(), p, bytes(), cudaMemcpyDeviceToHost, s));
+      RW_CUDA(cudaStreamSynchronize(s));
+    }
+    return h;
+  }
+  void zero(cudaStream_t s) { if (n) RW_CUDA(cudaMemsetAsync(p, 0, bytes(), s)); }
+};
+
+// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync): no implicit
+// device synchronisation when it is released.
+template <class T>
+struct TBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  TBuf() = default;
+  TBuf(size_t count, cudaStream_t st) : s(st) {
+    n = count;
+    if (count) {
+      cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
+      if (e != cudaSuccess) {
+        p = nullptr; n = 0;
+        throw Error(RW_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  TBuf(const TBuf&) = delete;
+  TBuf& operator=(const TBuf&) = delete;
+  TBuf(TBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+  TBuf& operator=(TBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~TBuf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr; n = 0;
+  }
+};
+
+template <class T>
+TBuf<T> to_device_tmp(const std::vector<T>& h, cudaStream_t s) {
+  TBuf<T> d(h.size(), s);
+  if (h.size()) RW_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+template <class T>
+DBuf<T> to_device(const std::vector<T>& h, cudaStream_t s) {
+  DBuf<T> d(h.size());
+  if (h.size()) RW_CUDA(cudaMemcpyAsync(d.p, h.data(), d.bytes(), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+// ---------------------------------------------------------------- nodes
+// Structure-of-arrays view of a node set on the device: position, outward
+// normal, smooth quadrature weight and signed curvature per point.
+struct NodesView {
+  const double *x, *y, *nx, *ny, *w, *kappa;
+  int n;
+};
+
+struct Nodes {
+  DBuf<double> buf;   // 6 x n column-major: x, y, nx, ny, w, kappa
+  int n = 0;
+  std::vector<double> hx, hy;  // host copy of positions (planning only)
+  void alloc(int count) { n = count; buf.alloc(size_t(6) * count); }
+  NodesView view() const {
+    const double* b = buf.p;
+    return NodesView{b, b + n, b + 2 * size_t(n), b + 3 * size_t(n),
+                     b + 4 * size_t(n), b + 5 * size_t(n), n};
+  }
+};
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// Entry of A = -1/2 I + D + N (Sec. 2, Remark 2.1) for row DOF (i, a) of node
+// set R and column DOF (j, b) of node set C.  same_set marks R == C, where
+// i == j gives the diagonal block -1/2 I - (kappa_i w_i / 2 pi) t t^T
+// + w_i n_i n_i^T (the smooth limit of the double layer on the curve).
+__device__ __forceinline__ double a_entry(const NodesView& R, int i, int a,
+                                          const NodesView& C, int j, int b,
+                                          bool same_set) {
+  const double nia = a ? R.ny[i] : R.nx[i];
+  const double njb = b ? C.ny[j] : C.nx[j];
+  const double wj = C.w[j];
+  double val = nia * njb * wj;
+  if (same_set && i == j) {
+    const double ta = a ? R.nx[i] : -R.ny[i];
+    const double tb = b ? R.nx[i] : -R.ny[i];
+    val -= R.kappa[i] * wj * (0.5 / kPi) * ta * tb;
+    if (a == b) val -= 0.5;
+  } else {
+    const double rx = R.x[i] - C.x[j], ry = R.y[i] - C.y[j];
+    const double r2 = rx * rx + ry * ry;
+    const double rdn = rx * C.nx[j] + ry * C.ny[j];
+    const double fac = wj * rdn / (kPi * r2 * r2);
+    val += fac * (a ? ry : rx) * (b ? ry : rx);
+  }
+  return val;
+}
+
+// ---------------------------------------------------------------- stream
+struct StreamGuard {
+  cudaStream_t s;
+  explicit StreamGuard(void* p) : s(static_cast<cudaStream_t>(p)) {}
+};
+
+inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
+
+}  // namespace rw

@@ -1,0 +1,245 @@
+"""Thin Python binding of the rwsolve C ABI (include/rwsolve.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/librwsolve.so``.  Arrays may be numpy arrays (host memory) or torch
+CUDA tensors (device memory); FP64, column-major as the header states (a
+C-contiguous numpy array of shape (nrhs, 2N) is the column-major 2N x nrhs
+matrix).  Streams are torch.cuda streams or raw cudaStream_t integers.
+
+Loading fails loudly if the library is missing: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RW_OK = 0
+ERRORS = {-1: "RW_ERR_INVALID", -2: "RW_ERR_OOM", -3: "RW_ERR_SINGULAR",
+          -4: "RW_ERR_NOT_CONVERGED", -5: "RW_ERR_TIMEOUT", -6: "RW_ERR_CUDA"}
+CURVE_STAR, CURVE_CHANNEL = 0, 1
+MODE_DIRECT, MODE_GMRES_FP32 = 0, 1
+
+
+class RWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class WallDesc(ctypes.Structure):
+    _fields_ = [("curve_kind", ctypes.c_int), ("n_panels", ctypes.c_int), ("params", ctypes.c_double * 8)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("leaf_points", ctypes.c_int), ("id_tol", ctypes.c_double), ("n_proxy", ctypes.c_int),
+                ("proxy_ratio", ctypes.c_double), ("n_proxy_refine", ctypes.c_int),
+                ("div_ratio", ctypes.c_double), ("bas_ratio", ctypes.c_double),
+                ("dense_pp_max_points", ctypes.c_int), ("sketch_cols", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
+                ("gmres_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+
+
+class HbsStats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int), ("levels", ctypes.c_int), ("max_rank", ctypes.c_int),
+                ("inv_elems", ctypes.c_longlong), ("fwd_elems", ctypes.c_longlong), ("bytes", ctypes.c_longlong)]
+
+
+class RefStats(ctypes.Structure):
+    _fields_ = [("n_k", ctypes.c_int), ("n_c", ctypes.c_int), ("n_p", ctypes.c_int), ("n_n", ctypes.c_int),
+                ("n_ext", ctypes.c_int), ("k_far", ctypes.c_int), ("k_near", ctypes.c_int),
+                ("k_pk", ctypes.c_int), ("k", ctypes.c_int), ("pp_dense", ctypes.c_int),
+                ("pp_levels", ctypes.c_int), ("bytes", ctypes.c_longlong)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+
+EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
+           "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_stokeslet_data",
+           "rw_solve", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load librwsolve.so (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"rwsolve CUDA library not built: {path} missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p
+    L.rw_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.rw_hbs_build.argtypes = [ctypes.POINTER(WallDesc), ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    L.rw_hbs_stats_get.argtypes = [vp, ctypes.POINTER(HbsStats)]
+    L.rw_hbs_nodes.argtypes = [vp, dp, vp]
+    L.rw_hbs_apply_inverse.argtypes = [vp, ctypes.c_int, dp, dp, vp]
+    L.rw_hbs_apply_forward.argtypes = [vp, ctypes.c_int, dp, dp, vp]
+    L.rw_refine_factor.argtypes = [vp, ctypes.c_int, ip, ip, vp, ctypes.POINTER(vp)]
+    L.rw_ref_stats_get.argtypes = [vp, ctypes.POINTER(RefStats)]
+    L.rw_ref_nodes.argtypes = [vp, dp, vp]
+    L.rw_stokeslet_data.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, dp, dp, vp]
+    L.rw_solve.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int, vp, ctypes.POINTER(Info)]
+    L.rw_ref_free.argtypes = [vp]
+    L.rw_hbs_free.argtypes = [vp]
+    L.rw_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("rw_last_error", "rw_ref_free", "rw_hbs_free"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != RW_OK:
+        raise RWError(rc, load().rw_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(a, writable=False):
+    """Raw pointer of a numpy FP64 C-contiguous array or a torch FP64 tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("torch tensors must be contiguous float64")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("numpy arrays must be C-contiguous float64")
+    if writable and not a.flags["WRITEABLE"]:
+        raise TypeError("output array is read-only")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def default_opts(**kw):
+    o = Opts()
+    _check(load().rw_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Wall:
+    """Reference wall: nodes, HBS forward representation and HBS inverse."""
+
+    def __init__(self, kind, n_panels, params=(), opts=None, stream=None):
+        L = load()
+        d = WallDesc()
+        d.curve_kind = {"star": CURVE_STAR, "channel": CURVE_CHANNEL}.get(kind, kind)
+        d.n_panels = int(n_panels)
+        for i, v in enumerate(params):
+            d.params[i] = float(v)
+        o = opts if opts is not None else default_opts()
+        h = ctypes.c_void_p()
+        _check(L.rw_hbs_build(ctypes.byref(d), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.n_panels = int(n_panels)
+
+    def stats(self):
+        s = HbsStats()
+        _check(load().rw_hbs_stats_get(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in HbsStats._fields_}
+
+    def nodes(self, stream=None):
+        n = self.stats()["n_points"]
+        out = np.empty((6, n))
+        _check(load().rw_hbs_nodes(self.h, _ptr(out, True), _stream(stream)))
+        return dict(zip(("x", "y", "nx", "ny", "w", "kappa"), out))
+
+    def apply_inverse(self, b, x, nrhs=1, stream=None):
+        _check(load().rw_hbs_apply_inverse(self.h, nrhs, _ptr(b), _ptr(x, True), _stream(stream)))
+        return x
+
+    def apply_forward(self, x, y, nrhs=1, stream=None):
+        _check(load().rw_hbs_apply_forward(self.h, nrhs, _ptr(x), _ptr(y, True), _stream(stream)))
+        return y
+
+    def refine(self, panels, levels, stream=None):
+        return Refinement(self, panels, levels, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rw_hbs_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Refinement:
+    """Algorithm 1 pre-computation for one local refinement of a Wall."""
+
+    def __init__(self, wall, panels, levels, stream=None):
+        L = load()
+        p = (ctypes.c_int * len(panels))(*[int(v) for v in panels])
+        lv = (ctypes.c_int * len(levels))(*[int(v) for v in levels])
+        h = ctypes.c_void_p()
+        _check(L.rw_refine_factor(wall.h, len(panels), p, lv, _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.wall = wall  # the wall must outlive the refinement
+
+    def stats(self):
+        s = RefStats()
+        _check(load().rw_ref_stats_get(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in RefStats._fields_}
+
+    def nodes(self, stream=None):
+        n = self.stats()["n_n"]
+        out = np.empty((6, n))
+        _check(load().rw_ref_nodes(self.h, _ptr(out, True), _stream(stream)))
+        return dict(zip(("x", "y", "nx", "ny", "w", "kappa"), out))
+
+    def stokeslet_data(self, src, f, g, nrhs=1, stream=None):
+        """g = boundary data from point forces: src (n_src, 2), f (nrhs, n_src, 2)."""
+        n_src = src.shape[0] if hasattr(src, "shape") else len(src) // 2
+        _check(load().rw_stokeslet_data(self.h, n_src, _ptr(src), nrhs, _ptr(f), _ptr(g, True), _stream(stream)))
+        return g
+
+    def solve(self, g, tau, nrhs=1, targets=None, u=None, mode=MODE_DIRECT, stream=None):
+        info = Info()
+        nt = 0 if targets is None else (targets.shape[0] if hasattr(targets, "shape") else len(targets) // 2)
+        _check(load().rw_solve(self.h, nrhs, _ptr(g), _ptr(tau, True), nt, _ptr(targets), _ptr(u, True),
+                               mode, _stream(stream), ctypes.byref(info)))
+        return {"iters": info.iters, "rel_residual": info.rel_residual}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rw_ref_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
