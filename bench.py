@@ -1,0 +1,354 @@
+"""Benchmark: refined-wall solves per second on the constricted channel.
+
+Workload (one GPU): the 1024-panel channel wall (16384 points, 32768
+unknowns, HBS leaf 64, ID tolerance 1e-12).  One step = one time step of the
+moving-window schedule: an 8-panel window advancing one panel per step,
+refined 2-5 levels (seeded), so each step runs the whole hot path:
+refinement factorisation (added nodes, A_pp^{-1}, row IDs, X, W^{-1}),
+boundary data from 5 exterior Stokeslets at the refined nodes, the Woodbury
+solve for the density, and the interior velocity at 16 targets.  The
+reference wall's HBS (built once) is static and excluded, as the paper's
+T_static.
+
+`value`: steps per second with the Stokeslet inputs resident on the device.
+`e2e`: the same through host buffers (inputs copied in and density and
+velocity copied out inside the timed region).
+--impl reference: the CPU oracle (dense Nystrom assembly + LAPACK LU) timed on
+the host cores on the same workload family (see cpu_baseline.sample).
+Multi-GPU: replicas only (independent walls and windows per rank).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P_PANELS = 1024
+TARGETS = 16
+N_SRC = 5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="direct", choices=["direct", "gmres", "refined"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (background)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--id={self.index}",
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+               "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def stokeslet_inputs(step, rank):
+    from paper_2108_07205_gb300 import inputs
+    sx, sy, f = inputs.stokeslets_channel(1000 * rank + step, nrhs=1, n=N_SRC)
+    src = np.ascontiguousarray(np.stack([sx, sy], 1))
+    fd = np.ascontiguousarray(np.transpose(f, (2, 0, 1)))
+    tx, ty = inputs.targets_channel(7 + step, TARGETS)
+    tg = np.ascontiguousarray(np.stack([tx, ty], 1))
+    return src, fd, tg
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2108_07205_gb300 import rwsolve, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    rwsolve.load(build_if_missing=True)
+    mode = {"direct": rwsolve.MODE_DIRECT, "gmres": rwsolve.MODE_GMRES_FP32,
+            "refined": rwsolve.MODE_DIRECT_REFINED}[args.mode]
+    t0 = time.time()
+    wall = rwsolve.Wall("channel", P_PANELS)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    hst = wall.stats()
+    total = args.warmup + args.steps
+    sched = inputs.time_schedule(17 + rank, P_PANELS, 2 * total + 1)
+    # device-resident inputs for every step
+    dev_in = []
+    host_in = []
+    for s in range(2 * total + 1):
+        src, fd, tg = stokeslet_inputs(s, rank)
+        host_in.append((torch.from_numpy(src).pin_memory(), torch.from_numpy(fd).pin_memory(),
+                        torch.from_numpy(tg).pin_memory()))
+        dev_in.append(tuple(x.to(dev) for x in (torch.from_numpy(src), torch.from_numpy(fd), torch.from_numpy(tg))))
+    # L2 flush buffer (> 129 MB L2)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(s, host):
+        panels, levels = sched[s]
+        ref = wall.refine(panels, levels, stream=stream)
+        n_n = ref.stats()["n_n"]
+        if host:
+            src, fd, tg = host_in[s]
+            g = torch.empty(2 * n_n, dtype=torch.float64, device=dev)
+            ref.stokeslet_data(src.numpy(), fd.numpy(), g, stream=stream)
+            tau = np.empty(2 * n_n)
+            u = np.empty(2 * TARGETS)
+            info = ref.solve(g, tau, targets=tg.numpy(), u=u, mode=mode, stream=stream)
+        else:
+            src, fd, tg = dev_in[s]
+            g = torch.empty(2 * n_n, dtype=torch.float64, device=dev)
+            ref.stokeslet_data(src, fd, g, stream=stream)
+            tau = torch.empty_like(g)
+            u = torch.empty(2 * TARGETS, dtype=torch.float64, device=dev)
+            info = ref.solve(g, tau, targets=tg, u=u, mode=mode, stream=stream)
+        st = ref.stats()
+        ref.close()
+        return st, info
+
+    def timed(offset, host):
+        for w in range(args.warmup):
+            step(offset + w, host)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        lat = []
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        stats = []
+        clk = Clocks(local)
+        clk.start()
+        n_launch0 = rwsolve.kernel_launches()
+        ev0.record(stream)
+        for i in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = step(offset + args.warmup + i, host)
+            e1.record(stream)
+            stats.append((st, info))
+            lat.append((e0, e1))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        launches = rwsolve.kernel_launches() - n_launch0
+        clocks = clk.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = ev0.elapsed_time(ev1)
+        lats = [a.elapsed_time(b) for a, b in lat]
+        return ms, lats, stats, clocks, launches
+
+    ms, lats, stats, clocks, launches = timed(0, host=False)
+    ms_e2e, lats_e2e, _, _, _ = timed(total, host=True)
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    ks = [s[0]["k"] for s in stats]
+    nps = [s[0]["n_p"] for s in stats]
+    out = {
+        "ms": ms, "ms_e2e": ms_e2e, "lat": lats, "lat_e2e": lats_e2e, "clocks": clocks,
+        "build_s": build_s, "hbs": hst, "k_mean": float(np.mean(ks)), "np_range": [min(nps), max(nps)],
+        "iters": [s[1]["iters"] for s in stats], "launches": launches,
+    }
+    # solve-only rate on one refinement (same shapes), and the sweep kernel roofline
+    panels, levels = sched[0]
+    ref = wall.refine(panels, levels, stream=stream)
+    n_n = ref.stats()["n_n"]
+    src, fd, tg = dev_in[0]
+    g = torch.empty(2 * n_n, dtype=torch.float64, device=dev)
+    ref.stokeslet_data(src, fd, g, stream=stream)
+    tau = torch.empty_like(g)
+    for _ in range(5):
+        ref.solve(g, tau, mode=mode, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    nsolve = 50
+    e0.record(stream)
+    for _ in range(nsolve):
+        ref.solve(g, tau, mode=mode, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["solve_ms"] = e0.elapsed_time(e1) / nsolve
+    ref.close()
+    # HBS inverse sweep alone (s1 on the reference wall): algorithmic bytes =
+    # matrix entries read (FP64) + vectors
+    b = torch.randn(2 * hst["n_points"], dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    for _ in range(5):
+        wall.apply_inverse(b, x, stream=stream)
+    torch.cuda.synchronize()
+    nsw = 50
+    times = []
+    for _ in range(nsw):
+        flush.zero_()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        wall.apply_inverse(b, x, stream=stream)
+        a1.record(stream)
+        times.append((a0, a1))
+    torch.cuda.synchronize()
+    sweep_ms = float(np.mean([a.elapsed_time(c) for a, c in times]))
+    out["sweep_ms"] = sweep_ms
+    out["sweep_bytes"] = 8 * hst["inv_elems"] + 8 * 4 * 2 * hst["n_points"]
+    wall.close()
+    return out
+
+
+def cpu_baseline(budget_s=25.0):
+    """Oracle (dense assembly + LAPACK LU) on the host cores on a bounded
+    sample of the workload: one moving-window step on the same channel family
+    at 256 panels (the dense solve of the 1024-panel step does not fit the
+    time budget); the rate is scaled to the full-size step by the LU flop
+    ratio (n_sample / n_full)^3."""
+    from oracle import discretize as D, stokes as S, dense as DN
+    from paper_2108_07205_gb300 import inputs
+    cores = os.cpu_count()
+    P = 256
+    sched = inputs.time_schedule(17, P, 50)
+    times, ns = [], []
+    t_start = time.time()
+    for s, (panels, levels) in enumerate(sched):
+        o = D.refine("channel", {}, P, panels, levels)
+        sx, sy, f = inputs.stokeslets_channel(s)
+        t0 = time.time()
+        g = S.boundary_data(o["n"], sx, sy, f)[:, 0]
+        DN.solve_refined(o, g)
+        times.append(time.time() - t0)
+        ns.append(2 * o["n"]["x"].size)
+        if time.time() - t_start > budget_s:
+            break
+    full = inputs.time_schedule(17, P_PANELS, 1)[0]
+    n_full = 2 * (16 * P_PANELS - 16 * len(full[0]) + 16 * sum(2 ** L for L in full[1]))
+    # the measured steps have varying sizes: scale each to the full step
+    scaled = [t * (n_full / n) ** 3 for t, n in zip(times, ns)]
+    v = 1.0 / float(np.mean(scaled))
+    return {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} steps of the 256-panel channel window schedule "
+                      f"(2N_n {min(ns)}-{max(ns)}), dense assembly + LAPACK LU, time scaled by "
+                      f"(2N_n / {n_full})^3 to the 1024-panel step; raw mean {np.mean(times):.3f} s/solve"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t_all = []
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(budget_s=budget)
+        if i >= args.warmup:
+            t_all.append(1.0 / cb["value"])
+    v = 1.0 / float(np.mean(t_all))
+    line = {"impl": "reference", "metric": "refined-wall solves/s", "value": v, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
+                             "unit": "solves/s"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(args):
+    return {"workload": "channel 1024 panels x 16 nodes (32768 unknowns), moving 8-panel window refined "
+                        "2-5 levels, refine + data + solve + velocity per step, 1 RHS",
+            "mode": args.mode, "hbs_leaf": 64, "id_tol": 1e-12, "l2": "flushed (256 MB write) before each step"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo" if args.impl == "reference" else "nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    out = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    value = world * args.steps / (out["ms"] / 1e3)
+    e2e = world * args.steps / (out["ms_e2e"] / 1e3)
+    achieved = out["sweep_bytes"] / (out["sweep_ms"] / 1e3) / 1e9
+    line = {
+        "metric": "refined-wall solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.mode != "gmres" else "f64+f32", "data": "synthetic",
+        "config": workload_config(args),
+        "p50_ms": float(np.percentile(out["lat"], 50)), "p99_ms": float(np.percentile(out["lat"], 99)),
+        "solve_only_per_s": 1e3 / out["solve_ms"], "k_mean": out["k_mean"], "n_p_range": out["np_range"],
+        "hbs_build_s": out["build_s"], "gmres_iters": out["iters"] if args.mode == "gmres" else None,
+        "e2e": {"value": e2e, "unit": "solves/s",
+                "h2d_bytes_per_step": 8 * (2 * N_SRC + 2 * N_SRC + 2 * TARGETS),
+                "d2h_bytes_per_step": 8 * (2 * TARGETS) + 8 * 2 * 16 * P_PANELS},
+        "roofline": {"kernel": "HBS inverse sweep (s1, FP64, 1 RHS)", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "clocks": out["clocks"],
+        "gpu_launches": out["launches"],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

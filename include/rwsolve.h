@@ -154,15 +154,31 @@ int rw_stokeslet_data(rw_ref_t r, int n_src, const double* src, int nrhs,
 #define RW_MODE_DIRECT 0      /* Algorithm 1 solve, FP64                     */
 #define RW_MODE_GMRES_FP32 1  /* FGMRES (FP64) on A~ + L R, preconditioned by
                                  Algorithm 1 with FP32 HBS sweeps (Sec. 4.2) */
+#define RW_MODE_DIRECT_REFINED 2  /* Algorithm 1 solve plus one step of
+                                 iterative refinement against the exact
+                                 refined operator A_nn (on-the-fly N-body
+                                 evaluation); removes the compression error
+                                 amplified by the conditioning of A_nn      */
+
+/* y = A_nn tau with every entry of the refined operator evaluated on the fly
+ * (Sec. 2, Eq. interior_BIE_discretized2 on the refined nodes): the exact
+ * residual of any solve.  tau, y: 2 N_n x nrhs (host or device, no alias). */
+int rw_apply_refined(rw_ref_t r, int nrhs, const double* tau, double* y,
+                     void* stream);
 
 /* s1-s3 (and m1). Solve the refined system for nrhs right-hand sides:
  * g: 2 N_n x nrhs boundary data in refined order; tau: 2 N_n x nrhs density
  * (output, refined order); if n_targets > 0, u: 2 n_targets x nrhs interior
  * velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets (2 x n_targets).
- * info may be NULL. */
+ * info may be NULL (iters = GMRES iterations, or 1 for the refined direct
+ * mode; rel_residual = final GMRES relative residual of the ELS). */
 int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets,
              const double* targets, double* u, int mode, void* stream,
              rw_info* info);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (diagnostics: benchmarks difference it around a timed region). */
+unsigned long long rw_kernel_launches(void);
 
 void rw_ref_free(rw_ref_t r);
 void rw_hbs_free(rw_hbs_t h);

@@ -245,6 +245,19 @@ int rw_ref_nodes(rw_ref_t r, double* out, void* stream) {
   });
 }
 
+int rw_apply_refined(rw_ref_t r, int nrhs, const double* tau, double* y, void* stream) {
+  if (!r || !tau || !y || nrhs < 1) return fail(RW_ERR_INVALID, "rw_apply_refined: bad argument");
+  if (tau == y) return fail(RW_ERR_INVALID, "rw_apply_refined: tau and y may not alias");
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = size_t(2) * r->ref.Nn * nrhs;
+    Arg at(tau, n, true, s), ay(y, n, false, s);
+    rw::apply_exact(r->ref.nn.view(), at.p, ay.p, nrhs, s);
+    ay.finish(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 int rw_stokeslet_data(rw_ref_t r, int n_src, const double* src, int nrhs, const double* f, double* g, void* stream) {
   if (!r || !src || !f || !g || n_src < 1 || nrhs < 1) return fail(RW_ERR_INVALID, "rw_stokeslet_data: bad argument");
   return guarded([&] {
@@ -261,7 +274,8 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
              int mode, void* stream, rw_info* info) {
   if (!r || !g || !tau || nrhs < 1 || n_targets < 0) return fail(RW_ERR_INVALID, "rw_solve: bad argument");
   if (n_targets > 0 && (!targets || !u)) return fail(RW_ERR_INVALID, "rw_solve: targets and u required");
-  if (mode != RW_MODE_DIRECT && mode != RW_MODE_GMRES_FP32) return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
+  if (mode != RW_MODE_DIRECT && mode != RW_MODE_GMRES_FP32 && mode != RW_MODE_DIRECT_REFINED)
+    return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
   int iters = 0;
   double relres = 0.0;
   int rc = guarded([&] {
@@ -271,6 +285,9 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     Arg ag(g, n, true, s), at(tau, n, false, s);
     if (mode == RW_MODE_DIRECT) {
       f.solve_direct(ag.p, at.p, nrhs, s);
+    } else if (mode == RW_MODE_DIRECT_REFINED) {
+      f.solve_refined(ag.p, at.p, nrhs, 1, s);
+      iters = 1;
     } else {
       f.solve_gmres(ag.p, at.p, nrhs, s, &iters, &relres);
     }
@@ -281,12 +298,14 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     }
     at.finish(s);
     RW_CUDA(cudaStreamSynchronize(s));
-    if (mode != RW_MODE_DIRECT && relres > f.wall->opts.gmres_tol)
+    if (mode == RW_MODE_GMRES_FP32 && relres > f.wall->opts.gmres_tol)
       throw rw::Error(RW_ERR_NOT_CONVERGED, "rw_solve: GMRES stopped at relative residual " + std::to_string(relres));
   });
   if (info) { info->iters = iters; info->rel_residual = relres; }
   return rc;
 }
+
+unsigned long long rw_kernel_launches(void) { return rw::g_launches; }
 
 void rw_ref_free(rw_ref_t r) { delete r; }
 void rw_hbs_free(rw_hbs_t h) { delete h; }

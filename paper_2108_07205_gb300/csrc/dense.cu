@@ -5,8 +5,34 @@
 #include "dense.cuh"
 #include <algorithm>
 #include <cmath>
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+#include <chrono>
+#include <cstdlib>
 
 namespace rw {
+
+unsigned long long g_launches = 0;
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+Trace::Trace(cudaStream_t st, const char* w) : s(st), what(w) {
+  const char* e = std::getenv("RW_TRACE");
+  on = e && e[0] == '1';
+  if (on) { cudaStreamSynchronize(s); t0 = now_s(); }
+}
+
+void Trace::mark(const char* phase) {
+  if (!on) return;
+  cudaStreamSynchronize(s);
+  const double t = now_s();
+  std::fprintf(stderr, "[rw trace] %s %-28s %8.3f ms\n", what, phase, 1e3 * (t - t0));
+  t0 = t;
+}
 
 namespace {
 
@@ -23,22 +49,31 @@ __device__ __forceinline__ int find_problem(const int* offs, int nprob, int tile
 // ------------------------------------------------------------------ GEMM
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
-__global__ void __launch_bounds__(256) k_gemm(const GemmProb* probs, const int* offs, int nprob) {
+struct GemmWork {
+  GemmProb p;
+  int tilesM, tilesN, nsplit, kchunk;
+  long long scratch_off;  // partial sums (nsplit x m x n) when nsplit > 1
+};
+
+__global__ void __launch_bounds__(256) k_gemm(const GemmWork* work, const int* offs, int nprob, double* scratch) {
   __shared__ double As[GBK][GBM + 1];
   __shared__ double Bs[GBK][GBN + 1];
   const int tile = blockIdx.x;
   const int b = find_problem(offs, nprob, tile);
-  const GemmProb P = probs[b];
-  const int tilesM = (P.m + GBM - 1) / GBM;
+  const GemmWork Wk = work[b];
+  const GemmProb& P = Wk.p;
+  const int tilesM = Wk.tilesM, tilesMN = Wk.tilesM * Wk.tilesN;
   const int t = tile - offs[b];
-  const int m0 = (t % tilesM) * GBM, n0 = (t / tilesM) * GBN;
+  const int split = t / tilesMN, tt = t % tilesMN;
+  const int m0 = (tt % tilesM) * GBM, n0 = (tt / tilesM) * GBN;
+  const int kb = split * Wk.kchunk, ke = min(P.k, kb + Wk.kchunk);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < P.k; k0 += GBK) {
+  for (int k0 = kb; k0 < ke; k0 += GBK) {
     // load op(A)[m0 : m0+64, k0 : k0+16]
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -47,7 +82,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* probs, const int* 
       if (!P.ta) { i = e & 63; kk = e >> 6; } else { kk = e & 15; i = e >> 4; }
       int gi = m0 + i, gk = k0 + kk;
       double v = 0.0;
-      if (gi < P.m && gk < P.k)
+      if (gi < P.m && gk < ke)
         v = P.ta ? P.A[gk + size_t(gi) * P.lda] : P.A[gi + size_t(gk) * P.lda];
       As[kk][i] = v;
     }
@@ -58,7 +93,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* probs, const int* 
       if (!P.tb) { kk = e & 15; j = e >> 4; } else { j = e & 63; kk = e >> 6; }
       int gj = n0 + j, gk = k0 + kk;
       double v = 0.0;
-      if (gj < P.n && gk < P.k)
+      if (gj < P.n && gk < ke)
         v = P.tb ? P.B[gj + size_t(gk) * P.ldb] : P.B[gk + size_t(gj) * P.ldb];
       Bs[kk][j] = v;
     }
@@ -85,11 +120,32 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* probs, const int* 
     for (int j = 0; j < 4; ++j) {
       int gj = n0 + tx + 16 * j;
       if (gj >= P.n) continue;
-      double* c = P.C + gi + size_t(gj) * P.ldc;
-      double v = P.alpha * acc[i][j];
-      if (P.beta != 0.0) v += P.beta * *c;
-      *c = v;
+      if (Wk.nsplit > 1) {
+        scratch[Wk.scratch_off + (size_t(split) * P.n + gj) * P.m + gi] = acc[i][j];
+      } else {
+        double* c = P.C + gi + size_t(gj) * P.ldc;
+        double v = P.alpha * acc[i][j];
+        if (P.beta != 0.0) v += P.beta * *c;
+        *c = v;
+      }
     }
+  }
+}
+
+// C = alpha * sum_s partial_s + beta C for split problems (fixed order).
+__global__ void k_gemm_reduce(const GemmWork* work, const double* scratch) {
+  const GemmWork Wk = work[blockIdx.y];
+  if (Wk.nsplit <= 1) return;
+  const GemmProb& P = Wk.p;
+  const long long tot = (long long)P.m * P.n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = int(e % P.m), j = int(e / P.m);
+    double s = 0.0;
+    for (int q = 0; q < Wk.nsplit; ++q) s += scratch[Wk.scratch_off + (size_t(q) * P.n + j) * P.m + i];
+    double* c = P.C + i + size_t(j) * P.ldc;
+    double v = P.alpha * s;
+    if (P.beta != 0.0) v += P.beta * *c;
+    *c = v;
   }
 }
 
@@ -229,21 +285,24 @@ __device__ double block_reduce_sum(double v, double* sbuf) {
 }
 
 __global__ void __launch_bounds__(512) k_inverse(const InvProb* probs) {
+  // In-place Gauss-Jordan with partial (row) pivoting on a copy of A in Ainv;
+  // the row interchanges are undone as column interchanges at the end.
   const InvProb P = probs[blockIdx.x];
   const int n = P.n, tid = threadIdx.x, nt = blockDim.x;
-  double* W = P.W;  // ld = n
-  double* X = P.Ainv;
+  double* M = P.Ainv;
+  const int ld = P.ldinv;
   __shared__ double sval[32];
   __shared__ int sidx[32];
   __shared__ int s_flag;
-  extern __shared__ double colc[];  // pivot column multipliers (n)
+  extern __shared__ double colc[];  // multipliers of the pivot column (n)
+  int* ipiv = reinterpret_cast<int*>(P.W);  // n pivot rows (work buffer)
   if (tid == 0) s_flag = 0;
+  for (int c = tid; c < n; c += nt) ipiv[c] = c;
   double amax = 0.0;
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e % n, j = e / n;
-    double v = P.A[i + size_t(j) * P.lda];
-    W[e] = v;
-    X[i + size_t(j) * P.ldinv] = (i == j) ? 1.0 : 0.0;
+  for (long long e = tid; e < (long long)n * n; e += nt) {
+    const int i = int(e % n), j = int(e / n);
+    const double v = P.A[i + size_t(j) * P.lda];
+    M[i + size_t(j) * ld] = v;
     amax = fmax(amax, fabs(v));
   }
   int dummy;
@@ -253,57 +312,90 @@ __global__ void __launch_bounds__(512) k_inverse(const InvProb* probs) {
     double v = -1.0;
     int idx = 0x7fffffff;
     for (int r = c + tid; r < n; r += nt) {
-      double a = fabs(W[r + size_t(c) * n]);
+      const double a = fabs(M[r + size_t(c) * ld]);
       if (a > v) { v = a; idx = r; }
     }
     int p;
-    double pv = block_reduce_max_abs_arg(v, idx, &p, sval, sidx);
-    if (!(pv > tiny)) { if (tid == 0) s_flag = 1; if (pv == 0.0) { __syncthreads(); break; } }
+    const double pv = block_reduce_max_abs_arg(v, idx, &p, sval, sidx);
+    if (!(pv > tiny)) {
+      if (tid == 0) s_flag = 1;
+      if (pv == 0.0) { __syncthreads(); break; }
+    }
+    if (tid == 0) ipiv[c] = p;
     if (p != c) {
       for (int j = tid; j < n; j += nt) {
-        double t1 = W[c + size_t(j) * n]; W[c + size_t(j) * n] = W[p + size_t(j) * n]; W[p + size_t(j) * n] = t1;
-        double t2 = X[c + size_t(j) * P.ldinv]; X[c + size_t(j) * P.ldinv] = X[p + size_t(j) * P.ldinv]; X[p + size_t(j) * P.ldinv] = t2;
+        const double t = M[c + size_t(j) * ld];
+        M[c + size_t(j) * ld] = M[p + size_t(j) * ld];
+        M[p + size_t(j) * ld] = t;
       }
       __syncthreads();
     }
-    const double inv = 1.0 / W[c + size_t(c) * n];
+    const double invp = 1.0 / M[c + size_t(c) * ld];
+    for (int r = tid; r < n; r += nt) colc[r] = (r == c) ? 0.0 : M[r + size_t(c) * ld];
     __syncthreads();
-    // scale pivot row; save multipliers
-    for (int j = tid; j < n; j += nt) {
-      W[c + size_t(j) * n] *= inv;
-      X[c + size_t(j) * P.ldinv] *= inv;
-    }
-    for (int r = tid; r < n; r += nt) colc[r] = (r == c) ? 0.0 : W[r + size_t(c) * n];
+    for (int j = tid; j < n; j += nt) M[c + size_t(j) * ld] = (j == c) ? invp : M[c + size_t(j) * ld] * invp;
     __syncthreads();
-    // eliminate column c from every other row (rows fastest: coalesced)
-    const int ncw = n - c - 1;
-    for (int e = tid; e < n * ncw; e += nt) {
-      const int r = e % n, j = c + 1 + e / n;
-      if (r != c) W[r + size_t(j) * n] -= colc[r] * W[c + size_t(j) * n];
+    for (long long e = tid; e < (long long)n * n; e += nt) {
+      const int r = int(e % n), j = int(e / n);
+      if (r == c) continue;
+      if (j == c) M[r + size_t(j) * ld] = -colc[r] * invp;
+      else M[r + size_t(j) * ld] -= colc[r] * M[c + size_t(j) * ld];
     }
-    for (int e = tid; e < n * n; e += nt) {
-      const int r = e % n, j = e / n;
-      if (r != c) X[r + size_t(j) * P.ldinv] -= colc[r] * X[c + size_t(j) * P.ldinv];
-    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int c = n - 1; c >= 0; --c) {
+    const int p = ipiv[c];
+    if (p != c)
+      for (int r = tid; r < n; r += nt) {
+        const double t = M[r + size_t(c) * ld];
+        M[r + size_t(c) * ld] = M[r + size_t(p) * ld];
+        M[r + size_t(p) * ld] = t;
+      }
     __syncthreads();
   }
   if (tid == 0 && P.flag) *P.flag = s_flag;
 }
 
 // ------------------------------------------------------------------ ID
-__global__ void __launch_bounds__(256) k_cpqr_id(const IdProb* probs) {
-  const IdProb P = probs[blockIdx.x];
+// Column-pivoted Householder QR of W (nr x nc) with early stop, then
+// T = R11^{-1} R12.  SM = true: W is staged in shared memory (small
+// problems); else W stays in global memory and the current Householder
+// vector is cached in shared memory.
+template <bool SM>
+__global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_base) {
+  const IdProb P = probs[nprob_base + blockIdx.x];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int nr = P.nr, nc = P.nc, ld = P.ldw;
-  double* W = P.W;
+  const int nr = P.nr, nc = P.nc;
+  extern __shared__ double smem[];
+  double* W;
+  int ld;
+  double* vcache;
+  if (SM) {
+    W = smem;
+    ld = nr;
+    vcache = nullptr;
+    for (long long e = tid; e < (long long)nr * nc; e += nt) {
+      const int i = int(e % nr), j = int(e / nr);
+      W[e] = P.W[i + size_t(j) * P.ldw];
+    }
+  } else {
+    W = P.W;
+    ld = P.ldw;
+    vcache = smem;
+  }
   double* nrm = P.norms;
   double* nrm0 = P.norms + nc;
   int* piv = P.piv;
   __shared__ double sval[32];
   __shared__ int sidx[32];
-  __shared__ double s_tau;
-  if (nr <= 0 || nc <= 0) { if (tid == 0) *P.rank = 0; return; }
+  __shared__ double s_tau, s_scale;
+  if (nr <= 0 || nc <= 0) {
+    if (tid == 0) { *P.rank = 0; if (nc > 0) { P.norms[2 * nc] = 0.0; P.norms[2 * nc + 3] = 0.0; } }
+    return;
+  }
   for (int j = tid; j < nc; j += nt) piv[j] = j;
+  __syncthreads();
   for (int j = warp; j < nc; j += nw) {
     double s = 0.0;
     for (int i = lane; i < nr; i += 32) { double v = W[i + size_t(j) * ld]; s += v * v; }
@@ -335,7 +427,6 @@ __global__ void __launch_bounds__(256) k_cpqr_id(const IdProb* probs) {
       }
       __syncthreads();
     }
-    // Householder vector for W[s:nr, s]
     double* col = W + size_t(s) * ld;
     double part = 0.0;
     for (int i = s + 1 + tid; i < nr; i += nt) part += col[i] * col[i];
@@ -343,36 +434,41 @@ __global__ void __launch_bounds__(256) k_cpqr_id(const IdProb* probs) {
     const double alpha = col[s];
     if (tid == 0) {
       if (xn2 == 0.0) {
-        s_tau = 0.0;  // already triangular in this column
+        s_tau = 0.0;
+        s_scale = 0.0;
       } else {
         double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
         s_tau = (beta - alpha) / beta;
-        sval[1] = 1.0 / (alpha - beta);
+        s_scale = 1.0 / (alpha - beta);
         col[s] = beta;
       }
     }
     __syncthreads();
     const double tau = s_tau;
+    const double* vv = col;
     if (tau != 0.0) {
-      const double sc = sval[1];
-      for (int i = s + 1 + tid; i < nr; i += nt) col[i] *= sc;
+      const double sc = s_scale;
+      for (int i = s + 1 + tid; i < nr; i += nt) {
+        const double x = col[i] * sc;
+        col[i] = x;
+        if (!SM) vcache[i] = x;
+      }
+      if (!SM) vv = vcache;
     }
     __syncthreads();
-    // apply H = I - tau v v^T (v_s = 1) to columns s+1..nc-1, update norms
     for (int j = s + 1 + warp; j < nc; j += nw) {
       double* cj = W + size_t(j) * ld;
       if (tau != 0.0) {
         double d = 0.0;
-        for (int i = s + 1 + lane; i < nr; i += 32) d += col[i] * cj[i];
+        for (int i = s + 1 + lane; i < nr; i += 32) d += vv[i] * cj[i];
         for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
         d = __shfl_sync(0xffffffffu, d, 0);
         d = tau * (d + cj[s]);
-        for (int i = s + 1 + lane; i < nr; i += 32) cj[i] -= d * col[i];
+        for (int i = s + 1 + lane; i < nr; i += 32) cj[i] -= d * vv[i];
         __syncwarp();
         if (lane == 0) cj[s] -= d;
         __syncwarp();
       }
-      // norm downdate (LAPACK xLAQP2 scheme)
       double nj = nrm[j];
       int recompute = 0;
       if (nj != 0.0) {
@@ -399,8 +495,7 @@ __global__ void __launch_bounds__(256) k_cpqr_id(const IdProb* probs) {
   int keff = s;
   for (int i = 0; i < s; ++i)
     if (!(fabs(W[i + size_t(i) * ld]) > 1e-15 * ref)) { keff = i; break; }
-  // T = R11^{-1} R12 over the first keff pivots, in place in W[0:keff, k:nc];
-  // rows keff..k-1 of T are zero.
+  // T = R11^{-1} R12 over the first keff pivots, in place in W[0:keff, k:nc]
   for (int j = k + tid; j < nc; j += nt) {
     double* cj = W + size_t(j) * ld;
     for (int i = keff - 1; i >= 0; --i) {
@@ -408,10 +503,16 @@ __global__ void __launch_bounds__(256) k_cpqr_id(const IdProb* probs) {
       for (int l = i + 1; l < keff; ++l) acc -= W[i + size_t(l) * ld] * cj[l];
       cj[i] = acc / W[i + size_t(i) * ld];
     }
-    for (int i = keff; i < k && i < nr; ++i) cj[i] = 0.0;
   }
-  if (tid == 0) { *P.rank = k; P.norms[0] = double(keff); }
   __syncthreads();
+  if (tid == 0) { *P.rank = k; P.norms[2 * nc] = double(keff); P.norms[2 * nc + 3] = 0.0; }
+  if (SM) {
+    // the finished factorisation (R and T) goes back for k_id_interp
+    for (long long e = tid; e < (long long)nr * nc; e += nt) {
+      const int i = int(e % nr), j = int(e / nr);
+      if (i < keff) P.W[i + size_t(j) * P.ldw] = W[e];
+    }
+  }
   if (P.P) {
     for (int e = tid; e < nc * k; e += nt) {
       int j = e % nc, c = e / nc;
@@ -423,17 +524,231 @@ __global__ void __launch_bounds__(256) k_cpqr_id(const IdProb* probs) {
   }
 }
 
+// Cluster variant (thread-block cluster of CS CTAs per problem): CTA r of
+// the cluster keeps candidate columns [r cw, (r+1) cw) of W in its shared
+// memory.  Per pivot step: every CTA publishes its local column-norm maximum,
+// cluster barrier, all CTAs agree on the pivot; the owner forms the
+// Householder vector in its shared memory, cluster barrier, every CTA copies
+// it through distributed shared memory and updates its own columns.  Columns
+// are not swapped: column q keeps its data, piv[] records the pivot order,
+// and the factorisation is written back to global memory in this "no-swap"
+// layout (R(l, i) = W[l, piv[i]]; T for a non-pivot candidate q in column q).
+__global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int base, int CS) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = int(cluster.block_rank());
+  const IdProb P = probs[base + blockIdx.x / CS];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int nr = P.nr, nc = P.nc;
+  const int cw = (nc + CS - 1) / CS;
+  const int c0 = crank * cw, c1 = min(nc, c0 + cw), ncl = max(0, c1 - c0);
+  extern __shared__ double smem[];
+  double* Wl = smem;                  // nr x cw
+  double* vbuf = Wl + size_t(nr) * cw;  // published Householder vector (owner)
+  double* vloc = vbuf + nr;           // local copy
+  double* nrm = vloc + nr;            // cw
+  double* nrm0 = nrm + cw;            // cw
+  __shared__ double pub_val, pub_tau, g_val;
+  __shared__ int pub_idx, g_idx;
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  __shared__ int s_done[1];
+  (void)s_done;
+  // load owned columns, norms
+  for (long long e = tid; e < (long long)nr * ncl; e += nt) {
+    const int i = int(e % nr), j = int(e / nr);
+    Wl[i + size_t(j) * nr] = P.W[i + size_t(c0 + j) * P.ldw];
+  }
+  __syncthreads();
+  for (int j = warp; j < ncl; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < nr; i += 32) { double v = Wl[i + size_t(j) * nr]; s += v * v; }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) { nrm[j] = sqrt(s); nrm0[j] = nrm[j]; }
+  }
+  __syncthreads();
+  const int maxsteps = (nr <= 0 || nc <= 0) ? 0 : min(min(nr, nc), P.max_rank);
+  const double tol3z = sqrt(2.220446049250313e-16);
+  int G = 32;
+  while (G > 1 && (nt / G) < ncl) G >>= 1;
+  const int gl = tid & (G - 1);
+  const int ncl_pad = (ncl + (nt / G) - 1) / (nt / G) * (nt / G);
+  double ref = 0.0;
+  int s = 0;
+  for (; s < maxsteps; ++s) {
+    // local argmax over remaining owned columns (done columns have norm -1)
+    double v = -1.0;
+    int idx = 0x7fffffff;
+    for (int j = tid; j < ncl; j += nt) if (nrm[j] > v) { v = nrm[j]; idx = c0 + j; }
+    int p;
+    double lm = block_reduce_max_abs_arg(v, idx, &p, sval, sidx);
+    if (tid == 0) { pub_val = lm; pub_idx = p; }
+    cluster.sync();
+    if (warp == 0) {
+      // lane r reads CTA r's slot; warp arg-max (smallest index on ties)
+      double bv = -1.0;
+      int bi = 0x7fffffff;
+      if (lane < CS) {
+        bv = *cluster.map_shared_rank(&pub_val, lane);
+        bi = *cluster.map_shared_rank(&pub_idx, lane);
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) { g_val = bv; g_idx = bi; }
+    }
+    __syncthreads();
+    const double vmax = g_val;
+    const int pg = g_idx;
+    if (s == 0) ref = vmax;
+    const double thr = fmax(P.tol_abs, P.tol_rel * ref);
+    if (vmax <= 0.0 || (s >= P.min_rank && vmax <= thr)) break;
+    const int owner = pg / cw;
+    if (crank == 0 && tid == 0) P.piv[s] = pg;
+    if (crank == owner) {
+      const int jl = pg - c0;
+      double* col = Wl + size_t(jl) * nr;
+      double part = 0.0;
+      for (int i = s + 1 + tid; i < nr; i += nt) part += col[i] * col[i];
+      const double xn2 = block_reduce_sum(part, sval);
+      const double alpha = col[s];
+      double tau = 0.0, sc = 0.0;
+      if (xn2 != 0.0) {
+        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        tau = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+      }
+      __syncthreads();
+      for (int i = s + 1 + tid; i < nr; i += nt) {
+        const double x = col[i] * sc;
+        col[i] = x;
+        vbuf[i] = x;
+      }
+      if (tid == 0) {
+        if (xn2 != 0.0) col[s] = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        pub_tau = tau;
+        nrm[jl] = -1.0;  // done
+      }
+    }
+    cluster.sync();
+    const double* rv = cluster.map_shared_rank(vbuf, owner);
+    const double tau = *cluster.map_shared_rank(&pub_tau, owner);
+    for (int i = s + 1 + tid; i < nr; i += nt) vloc[i] = rv[i];
+    __syncthreads();
+    // G threads (a power of two <= 32, within one warp) per local column
+    for (int jb = tid / G; jb < ncl_pad; jb += nt / G) {
+      const int j = jb;
+      const bool live = j < ncl && nrm[j] >= 0.0;
+      double* cj = Wl + size_t(live ? j : 0) * nr;
+      double dd = 0.0;
+      if (live && tau != 0.0)
+        for (int i = s + 1 + gl; i < nr; i += G) dd += vloc[i] * cj[i];
+      for (int off = G / 2; off > 0; off >>= 1) dd += __shfl_down_sync(0xffffffffu, dd, off, G);
+      dd = __shfl_sync(0xffffffffu, dd, 0, G);
+      double q = 0.0;
+      if (live) {
+        if (tau != 0.0) {
+          dd = tau * (dd + cj[s]);
+          for (int i = s + 1 + gl; i < nr; i += G) {
+            const double x = cj[i] - dd * vloc[i];
+            cj[i] = x;
+            q += x * x;
+          }
+        } else {
+          for (int i = s + 1 + gl; i < nr; i += G) q += cj[i] * cj[i];
+        }
+      }
+      for (int off = G / 2; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off, G);
+      if (live && gl == 0) {
+        if (tau != 0.0) cj[s] -= dd;
+        nrm[j] = sqrt(q);  // exact norm of rows s+1.. (summed in the update pass)
+      }
+    }
+    __syncthreads();
+  }
+  // every CTA leaves the loop at the same s (same data, same decisions)
+  for (long long e = tid; e < (long long)nr * ncl; e += nt) {
+    const int i = int(e % nr), j = int(e / nr);
+    P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * nr];
+  }
+  // done flags for the remaining-pivot bookkeeping: mark in global norms
+  for (int j = tid; j < ncl; j += nt) P.norms[nc + c0 + j] = (nrm[j] < 0.0) ? -1.0 : 1.0;
+  if (crank == 0 && tid == 0) { P.norms[2 * nc + 1] = double(s); P.norms[2 * nc + 2] = ref; P.norms[2 * nc + 3] = 1.0; }
+  cluster.sync();  // keep shared memory alive until remote readers are done
+}
+
+// Completes a no-swap factorisation (one thread per problem): appends the
+// non-pivot candidates to piv (increasing index), pads fixed-rank requests
+// and counts the usable pivots.
+__global__ void k_id_prep(const IdProb* probs, int base, int n) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const IdProb P = probs[base + b];
+  const int nc = P.nc;
+  const int s = int(P.norms[2 * nc + 1]);
+  const double ref = P.norms[2 * nc + 2];
+  const int k = max(s, min(P.min_rank, nc));
+  int q = s;
+  for (int j = 0; j < nc; ++j) if (P.norms[nc + j] >= 0.0) P.piv[q++] = j;
+  int keff = s;
+  for (int i = 0; i < s; ++i)
+    if (!(fabs(P.W[i + size_t(P.piv[i]) * P.ldw]) > 1e-15 * ref)) { keff = i; break; }
+  *P.rank = k;
+  P.norms[2 * nc] = double(keff);
+}
+
+// T = R11^{-1} R12 for no-swap factorisations: blockIdx.y = problem,
+// blockIdx.x = chunk of 64 non-skeleton candidates; R11 (pivot order) staged
+// in shared memory when it fits, one warp per candidate column.
+constexpr int TS_COLS = 64;
+__global__ void __launch_bounds__(256) k_id_tsolve(const IdProb* probs, int base, int rmax) {
+  const IdProb P = probs[base + blockIdx.y];
+  const int nc = P.nc, k = *P.rank, keff = int(P.norms[2 * nc]);
+  const int q0 = k + blockIdx.x * TS_COLS;
+  if (q0 >= nc || keff == 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  extern __shared__ double sm[];
+  const bool inR = keff <= rmax;
+  double* R = sm;                                        // keff x keff (if inR)
+  double* bb = sm + (inR ? size_t(keff) * keff : 0);     // nw x keff
+  if (inR) {
+    for (long long e = tid; e < (long long)keff * keff; e += blockDim.x) {
+      const int l = int(e % keff), i = int(e / keff);
+      R[e] = (l <= i) ? P.W[l + size_t(P.piv[i]) * P.ldw] : 0.0;
+    }
+  }
+  __syncthreads();
+  double* b = bb + size_t(warp) * keff;
+  for (int q = q0 + warp; q < min(nc, q0 + TS_COLS); q += nw) {
+    double* cj = P.W + size_t(P.piv[q]) * P.ldw;
+    for (int i = lane; i < keff; i += 32) b[i] = cj[i];
+    __syncwarp();
+    for (int i = keff - 1; i >= 0; --i) {
+      const double* Ri = inR ? R + size_t(i) * keff : P.W + size_t(P.piv[i]) * P.ldw;
+      const double ti = b[i] / Ri[i];
+      __syncwarp();
+      for (int l = lane; l < i; l += 32) b[l] -= Ri[l] * ti;
+      if (lane == 0) b[i] = ti;
+      __syncwarp();
+    }
+    for (int i = lane; i < keff; i += 32) cj[i] = b[i];
+    __syncwarp();
+  }
+}
+
 // Interpolation matrix from a finished factorisation (rank in *rank, number
 // of usable pivots in norms[0]).
 __global__ void k_id_interp(const IdProb* probs) {
   const IdProb P = probs[blockIdx.y];
-  const int k = *P.rank, keff = int(P.norms[0]), nc = P.nc;
+  const int nc = P.nc, k = *P.rank, keff = int(P.norms[2 * nc]);
+  const bool noswap = P.norms[2 * nc + 3] != 0.0;
   const long long tot = (long long)nc * k;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int j = int(e % nc), c = int(e / nc);
     double v;
     if (j < k) v = (j == c) ? 1.0 : 0.0;
-    else v = (c < keff) ? P.W[c + size_t(j) * P.ldw] : 0.0;
+    else v = (c < keff) ? P.W[c + size_t(noswap ? P.piv[j] : j) * P.ldw] : 0.0;
     P.P[P.piv[j] + size_t(c) * P.ldp] = v;
   }
 }
@@ -448,6 +763,10 @@ __global__ void k_rademacher(double* out, size_t n, unsigned long long seed) {
   }
 }
 
+__global__ void k_axpby(const double* x, double* y, size_t n, double a, double b) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) y[i] = a * x[i] + b * y[i];
+}
+
 __global__ void k_fill_zero(double* p, size_t n) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) p[i] = 0.0;
 }
@@ -460,20 +779,52 @@ int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, 152 * 16))
 }  // namespace
 
 void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
-  std::vector<GemmProb> ps;
+  std::vector<GemmWork> ws;
   std::vector<int> offs(1, 0);
+  long long tiles_all = 0;
   for (const auto& p : probs) {
     if (p.m <= 0 || p.n <= 0) continue;
-    ps.push_back(p);
-    int tiles = ceil_div(p.m, GBM) * ceil_div(p.n, GBN);
-    offs.push_back(offs.back() + tiles);
+    GemmWork w;
+    w.p = p;
+    w.tilesM = ceil_div(p.m, GBM);
+    w.tilesN = ceil_div(p.n, GBN);
+    w.nsplit = 1;
+    w.kchunk = std::max(p.k, 1);
+    w.scratch_off = 0;
+    ws.push_back(w);
+    tiles_all += (long long)w.tilesM * w.tilesN;
   }
-  if (ps.empty()) return;
-  // k == 0 problems still need C = beta C: handled by the kernel (loop skipped)
-  auto dp = to_device_tmp(ps, s);
+  if (ws.empty()) return;
+  // Split long inner dimensions when the output tiles alone cannot fill the
+  // GPU (two CTAs per SM); partial sums are added in a fixed order.
+  size_t scratch = 0;
+  const long long target = 2 * 152;
+  for (auto& w : ws) {
+    const long long tiles = (long long)w.tilesM * w.tilesN;
+    if (tiles_all < target && w.p.k >= 1024) {
+      int ns = int(std::min<long long>(std::max<long long>(1, target / std::max<long long>(tiles_all, 1)),
+                                       (w.p.k + 511) / 512));
+      ns = std::min(ns, 64);
+      if (ns > 1) {
+        w.kchunk = ((w.p.k + ns - 1) / ns + GBK - 1) / GBK * GBK;
+        w.nsplit = (w.p.k + w.kchunk - 1) / w.kchunk;
+        w.scratch_off = (long long)scratch;
+        scratch += size_t(w.nsplit) * w.p.m * w.p.n;
+      }
+    }
+    offs.push_back(offs.back() + int(tiles * w.nsplit));
+  }
+  TBuf<double> sc(scratch, s);
+  auto dw = to_device_tmp(ws, s);
   auto doff = to_device_tmp(offs, s);
-  k_gemm<<<offs.back(), 256, 0, s>>>(dp.p, doff.p, int(ps.size()));
+  k_gemm<<<offs.back(), 256, 0, s>>>(dw.p, doff.p, int(ws.size()), sc.p);
   RW_CHECK_LAUNCH();
+  if (scratch) {
+    long long mx = 0;
+    for (auto& w : ws) mx = std::max(mx, (long long)w.p.m * w.p.n);
+    k_gemm_reduce<<<dim3(std::min(ceil_div(mx, 256), 1024), int(ws.size())), 256, 0, s>>>(dw.p, sc.p);
+    RW_CHECK_LAUNCH();
+  }
 }
 
 template <class T>
@@ -576,11 +927,78 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
   RW_CHECK_LAUNCH();
 }
 
-void batched_id(const std::vector<IdProb>& probs, cudaStream_t s) {
-  if (probs.empty()) return;
-  auto dp = to_device_tmp(probs, s);
-  k_cpqr_id<<<int(probs.size()), 256, 0, s>>>(dp.p);
-  RW_CHECK_LAUNCH();
+void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
+  if (probs_in.empty()) return;
+  // Route each problem: a thread-block cluster of CS in {1, 2, 4, 8} CTAs
+  // whose shared memory holds the matrix, or the global-memory kernel.
+  const size_t cap = 200 * 1024;
+  std::vector<IdProb> grp[4], gl;
+  const int sizes[4] = {1, 2, 4, 8};
+  for (IdProb p : probs_in) {
+    int g = -1;
+    for (int q = 0; q < 4 && g < 0; ++q) {
+      const int cw = (p.nc + sizes[q] - 1) / sizes[q];
+      const size_t b = (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double);
+      if (b <= cap && (q == 0 || p.nc >= 2 * sizes[q])) g = q;
+    }
+    if (g >= 0) grp[g].push_back(p);
+    else gl.push_back(p);
+  }
+  std::vector<IdProb> all;
+  std::vector<int> base(5, 0);
+  for (int q = 0; q < 4; ++q) { base[q] = int(all.size()); all.insert(all.end(), grp[q].begin(), grp[q].end()); }
+  base[4] = int(all.size());
+  all.insert(all.end(), gl.begin(), gl.end());
+  auto dp = to_device_tmp(all, s);
+  for (int q = 0; q < 4; ++q) {
+    if (grp[q].empty()) continue;
+    const int CS = sizes[q];
+    size_t smem = 0;
+    int maxnr = 0;
+    for (auto& p : grp[q]) {
+      const int cw = (p.nc + CS - 1) / CS;
+      smem = std::max(smem, (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double));
+      maxnr = std::max(maxnr, p.nr);
+    }
+    RW_CUDA(cudaFuncSetAttribute(k_cpqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cap + 1024)));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grp[q].size() * CS));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_cluster, (const IdProb*)dp.p, base[q], CS));
+    RW_CHECK_LAUNCH();
+    int maxk = 0, maxnc = 0;
+    for (auto& p : grp[q]) {
+      maxk = std::max(maxk, std::min(std::min(p.nr, p.nc), p.max_rank));
+      maxnc = std::max(maxnc, p.nc);
+    }
+    const int ng = int(grp[q].size());
+    k_id_prep<<<ceil_div(ng, 128), 128, 0, s>>>(dp.p, base[q], ng);
+    RW_CHECK_LAUNCH();
+    const int rmax = 150;  // R11 in shared memory up to 150 x 150
+    const int kk = std::max(maxk, 1);
+    const size_t tsm = ((kk <= rmax ? size_t(kk) * kk : 0) + 8 * size_t(kk)) * sizeof(double);
+    RW_CUDA(cudaFuncSetAttribute(k_id_tsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(std::max<size_t>(tsm, 48 * 1024))));
+    k_id_tsolve<<<dim3(ceil_div(maxnc, TS_COLS), ng), 256, tsm, s>>>(dp.p, base[q], kk <= rmax ? rmax : 0);
+    RW_CHECK_LAUNCH();
+  }
+  if (!gl.empty()) {
+    size_t gl_bytes = 0;
+    for (auto& p : gl) gl_bytes = std::max(gl_bytes, size_t(p.nr) * sizeof(double));
+    require(gl_bytes <= cap, "batched_id: more than 25600 feature rows");
+    if (gl_bytes > 48 * 1024)
+      RW_CUDA(cudaFuncSetAttribute(k_cpqr_id<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gl_bytes)));
+    k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, s>>>(dp.p, base[4]);
+    RW_CHECK_LAUNCH();
+  }
 }
 
 void batched_id_interp(const std::vector<IdProb>& probs, int max_elems, cudaStream_t s) {
@@ -593,6 +1011,11 @@ void batched_id_interp(const std::vector<IdProb>& probs, int max_elems, cudaStre
 void fill_rademacher(double* out, size_t n, unsigned long long seed, cudaStream_t s) {
   if (!n) return;
   k_rademacher<<<grid_for(n), 256, 0, s>>>(out, n, seed);
+  RW_CHECK_LAUNCH();
+}
+void axpby(const double* x, double* y, size_t n, double a, double b, cudaStream_t s) {
+  if (!n) return;
+  k_axpby<<<grid_for(n), 256, 0, s>>>(x, y, n, a, b);
   RW_CHECK_LAUNCH();
 }
 void fill_zero(double* p, size_t n, cudaStream_t s) {

@@ -67,8 +67,8 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s);
 // stop when the largest remaining column norm is <= max(tol_abs,
 // tol_rel * first pivot norm) once at least min_rank steps were taken, or at
 // max_rank.  A min_rank above the numerical rank is met by taking further
-// candidates in pivot order as skeletons with zero coefficients.  norms[0]
-// returns the number of numerically nonzero pivots.  Outputs rank k, the pivot order piv (nc), and the interpolation
+// candidates in pivot order as skeletons with zero coefficients.  The last
+// four norms entries hold the number of usable pivots and the layout.  Outputs rank k, the pivot order piv (nc), and the interpolation
 // matrix P (nc x k, column-major, leading dimension ldp) with
 // Y ~= P Y(piv[0:k], :) and P(piv[i], :) = e_i.
 struct IdProb {
@@ -77,11 +77,13 @@ struct IdProb {
   double tol_abs, tol_rel;
   int min_rank, max_rank;
   int* piv;
-  double* norms;  // 2 * nc work
+  double* norms;  // id_norms_elems(nc) work entries
   double* P;
   int ldp;
   int* rank;
 };
+// Work entries needed in IdProb::norms for a problem with nc candidates.
+inline size_t id_norms_elems(int nc) { return 2 * size_t(nc) + 4; }
 void batched_id(const std::vector<IdProb>& probs, cudaStream_t s);
 
 // Writes P (nc x rank) for factorisations finished by batched_id (P may have
@@ -94,6 +96,7 @@ void fill_rademacher(double* out, size_t n, unsigned long long seed, cudaStream_
 
 // Elementwise helpers.
 void fill_zero(double* p, size_t n, cudaStream_t s);
+void axpby(const double* x, double* y, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
 void copy_d2f(const double* in, float* out, size_t n, cudaStream_t s);
 
 }  // namespace rw

@@ -186,21 +186,30 @@ __global__ void k_copy(const CopyProb* probs) {
 }
 
 __global__ void k_velocity(NodesView nd, const double* tau, int nrhs, int nt, const double* tg, double* u) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
-  if (t >= nt) return;
+  // one CTA per (target, right-hand side); sources split over the threads
+  const int t = blockIdx.x, r = blockIdx.y;
   const double x = tg[2 * t], y = tg[2 * t + 1];
   const double* tr = tau + size_t(r) * 2 * nd.n;
   double ux = 0.0, uy = 0.0;
-  for (int j = 0; j < nd.n; ++j) {
+  for (int j = threadIdx.x; j < nd.n; j += blockDim.x) {
     const double rx = x - nd.x[j], ry = y - nd.y[j], r2 = rx * rx + ry * ry;
     const double fac = nd.w[j] * (rx * nd.nx[j] + ry * nd.ny[j]) / (kPi * r2 * r2);
     const double rt = rx * tr[2 * j] + ry * tr[2 * j + 1];
     ux += fac * rx * rt;
     uy += fac * ry * rt;
   }
-  u[size_t(r) * 2 * nt + 2 * t] = ux;
-  u[size_t(r) * 2 * nt + 2 * t + 1] = uy;
+  __shared__ double sx[256], sy[256];
+  sx[threadIdx.x] = ux;
+  sy[threadIdx.x] = uy;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) { sx[threadIdx.x] += sx[threadIdx.x + w]; sy[threadIdx.x] += sy[threadIdx.x + w]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    u[size_t(r) * 2 * nt + 2 * t] = sx[0];
+    u[size_t(r) * 2 * nt + 2 * t + 1] = sy[0];
+  }
 }
 
 __global__ void k_stokeslets(NodesView nd, int ns, const double* src, int nrhs, const double* f, double* g) {
@@ -238,6 +247,64 @@ __global__ void k_gather_scatter(const double* in, int ldi, const int* ii, doubl
     const int a = ii ? ii[i] : i, b = io ? io[i] : i;
     out[b + size_t(r) * ldo] = in[a + size_t(r) * ldi];
   }
+}
+
+// y = A x for A = -1/2 I + D + N on one node set, evaluated on the fly
+// (exact refined operator).  One thread per target point, source points
+// staged through shared memory in tiles; the rank-one N term is added from
+// the flux sum_j w_j n_j . x_j computed by k_flux.
+constexpr int NB_T = 128, NB_S = 128;
+__global__ void __launch_bounds__(NB_T) k_apply_exact(NodesView nd, const double* x, int ldx, double* y, int ldy,
+                                                       const double* flux) {
+  const int i = blockIdx.x * NB_T + threadIdx.x;
+  const int r = blockIdx.y;
+  const double* xr = x + size_t(r) * ldx;
+  __shared__ double sx[NB_S], sy[NB_S], snx[NB_S], sny[NB_S], sw[NB_S], stx[NB_S], sty[NB_S];
+  const bool act = i < nd.n;
+  const double xi = act ? nd.x[i] : 0.0, yi = act ? nd.y[i] : 0.0;
+  double ux = 0.0, uy = 0.0;
+  for (int j0 = 0; j0 < nd.n; j0 += NB_S) {
+    const int nj = min(NB_S, nd.n - j0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nj; q += NB_T) {
+      const int j = j0 + q;
+      sx[q] = nd.x[j]; sy[q] = nd.y[j]; snx[q] = nd.nx[j]; sny[q] = nd.ny[j]; sw[q] = nd.w[j];
+      stx[q] = xr[2 * j]; sty[q] = xr[2 * j + 1];
+    }
+    __syncthreads();
+    if (act) {
+      for (int q = 0; q < nj; ++q) {
+        if (j0 + q == i) continue;
+        const double rx = xi - sx[q], ry = yi - sy[q], r2 = rx * rx + ry * ry;
+        const double fac = sw[q] * (rx * snx[q] + ry * sny[q]) / (kPi * r2 * r2);
+        const double rt = rx * stx[q] + ry * sty[q];
+        ux = fma(fac * rx, rt, ux);
+        uy = fma(fac * ry, rt, uy);
+      }
+    }
+  }
+  if (!act) return;
+  const double nxi = nd.nx[i], nyi = nd.ny[i], txi = -nyi, tyi = nxi;
+  const double taux = xr[2 * i], tauy = xr[2 * i + 1];
+  const double dk = -nd.kappa[i] * nd.w[i] * (0.5 / kPi) * (txi * taux + tyi * tauy);
+  const double fl = flux[r];
+  y[size_t(r) * ldy + 2 * i] = ux + dk * txi + nxi * fl - 0.5 * taux;
+  y[size_t(r) * ldy + 2 * i + 1] = uy + dk * tyi + nyi * fl - 0.5 * tauy;
+}
+
+__global__ void k_flux(NodesView nd, const double* x, int ldx, double* flux) {
+  const int r = blockIdx.x;
+  const double* xr = x + size_t(r) * ldx;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < nd.n; j += blockDim.x) s += nd.w[j] * (nd.nx[j] * xr[2 * j] + nd.ny[j] * xr[2 * j + 1]);
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) flux[r] = red[0];
 }
 
 int grid1(long long n) { return int(std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096))); }
@@ -312,7 +379,7 @@ void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s) {
 void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* u,
                    cudaStream_t s) {
   if (nt <= 0 || nrhs <= 0) return;
-  k_velocity<<<dim3(ceil_div(nt, 128), nrhs), 128, 0, s>>>(nodes, tau, nrhs, nt, targets, u);
+  k_velocity<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, nrhs, nt, targets, u);
   RW_CHECK_LAUNCH();
 }
 
@@ -320,6 +387,14 @@ void eval_stokeslets(const NodesView& nodes, int ns, const double* src, int nrhs
                      cudaStream_t s) {
   if (nodes.n <= 0 || nrhs <= 0) return;
   k_stokeslets<<<dim3(ceil_div(nodes.n, 128), nrhs), 128, 0, s>>>(nodes, ns, src, nrhs, f, g);
+  RW_CHECK_LAUNCH();
+}
+
+void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, cudaStream_t s) {
+  if (nodes.n <= 0 || nrhs <= 0) return;
+  TBuf<double> flux(nrhs, s);
+  k_flux<<<nrhs, 256, 0, s>>>(nodes, x, 2 * nodes.n, flux.p);
+  k_apply_exact<<<dim3(ceil_div(nodes.n, NB_T), nrhs), NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p);
   RW_CHECK_LAUNCH();
 }
 

@@ -95,6 +95,10 @@ void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt,
 void eval_stokeslets(const NodesView& nodes, int ns, const double* src,
                      int nrhs, const double* f, double* g, cudaStream_t s);
 
+// y = A x with A = -1/2 I + D + N on a node set, every entry evaluated on
+// the fly (the exact Nystrom operator of Sec. 2).  x, y: 2N x nrhs, ld 2N.
+void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, cudaStream_t s);
+
 // Row-norm maximum of a column-major W (nr x nc): max_j ||W[:, j]|| into out.
 void max_colnorm(const double* W, int nr, int nc, int ld, double* out,
                  cudaStream_t s);

@@ -32,15 +32,17 @@ void IdBatch::run(const NodesView& S, const NodesView& E1, bool e1s, const Nodes
                   unsigned long long seed, cudaStream_t s) {
   const int nj = int(jobs.size());
   if (!W.p) {
-    size_t w = 0, m = 0;
+    size_t w = 0, m = 0, nm = 0;
     for (auto& j : jobs) {
       j.woff = w;
       j.moff = m;
+      j.noff = nm;
       w += size_t(j.nr) * j.spec.m;
       m += j.spec.m;
+      nm += id_norms_elems(j.spec.m);
     }
     W.alloc(std::max<size_t>(w, 1));
-    norms.alloc(std::max<size_t>(2 * m, 1));
+    norms.alloc(std::max<size_t>(nm, 1));
     piv.alloc(std::max<size_t>(m, 1));
     rank.alloc(std::max(nj, 1));
     h_rank.assign(nj, 0);
@@ -83,7 +85,7 @@ void IdBatch::run(const NodesView& S, const NodesView& E1, bool e1s, const Nodes
   std::vector<IdProb> ip;
   for (int id : subset) {
     Job& j = jobs[id];
-    IdProb q;
+    IdProb q{};
     q.W = W.p + j.woff;
     q.ldw = j.nr;
     q.nr = j.nr;
@@ -93,7 +95,7 @@ void IdBatch::run(const NodesView& S, const NodesView& E1, bool e1s, const Nodes
     q.min_rank = min_rank.empty() ? 0 : min_rank[id];
     q.max_rank = max_rank.empty() ? j.spec.m : max_rank[id];
     q.piv = piv.p + j.moff;
-    q.norms = norms.p + 2 * j.moff;
+    q.norms = norms.p + j.noff;
     q.P = nullptr;
     q.ldp = j.spec.m;
     q.rank = rank.p + id;
@@ -116,7 +118,7 @@ void IdBatch::interp(const std::vector<double*>& P, const std::vector<int>& ldp,
     q.nr = j.nr;
     q.nc = j.spec.m;
     q.piv = piv.p + j.moff;
-    q.norms = norms.p + 2 * j.moff;
+    q.norms = norms.p + j.noff;
     q.P = P[id];
     q.ldp = ldp[id];
     q.rank = rank.p + id;
@@ -145,6 +147,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
   TreeId out;
   const int mt = int(rows.size());
   if (mt == 0) return out;
+  Trace tr(s, "  tree-id");
   auto drows = to_device_tmp(rows, s);
   IdMatProb sp = colspec;
   sp.kind = 0;
@@ -173,6 +176,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
   RW_CUDA(cudaMemcpyAsync(&hmx, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   RW_CUDA(cudaStreamSynchronize(s));
   const double tol_abs = tol * hmx;
+  tr.mark("eval (+sketch)");
 
   // level structure: each job has candidate positions (into rows) and the
   // indices of its child jobs in the previous level
@@ -190,7 +194,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
     for (auto& j : cur) cand_all.insert(cand_all.end(), j.cand.begin(), j.cand.end());
     auto dcand = to_device_tmp(cand_all, s);
     TBuf<double> Wl(size_t(nr) * cand_all.size(), s);
-    TBuf<double> nrm(2 * cand_all.size(), s);
+    TBuf<double> nrm(2 * cand_all.size() + 4 * cur.size(), s);
     TBuf<int> piv(cand_all.size(), s), rk(cur.size(), s);
     k_gather_cols<<<std::min(ceil_div((long long)nr * cand_all.size(), 256), 4096), 256, 0, s>>>(
         Z, nr, dcand.p, int(cand_all.size()), Wl.p);
@@ -208,7 +212,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
       q.min_rank = 0;
       q.max_rank = q.nc;
       q.piv = piv.p + off;
-      q.norms = nrm.p + 2 * off;
+      q.norms = nrm.p + 2 * off + 4 * b;
       q.P = nullptr;
       q.ldp = q.nc;
       q.rank = rk.p + b;
@@ -240,6 +244,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
     batched_id_interp(ip, mxe, s);
     Pl.push_back(std::move(P));
     levels.push_back(cur);
+    tr.mark(cur.size() == 1 ? "level (root)" : "level");
     if (cur.size() == 1) break;
     std::vector<TJob> nxt;
     for (size_t b = 0; b < cur.size(); b += 2) {
@@ -304,6 +309,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
   }
   // keep buffers alive until the stream has consumed them
   RW_CUDA(cudaStreamSynchronize(s));
+  tr.mark("top-down interpolation");
   return out;
 }
 
@@ -326,6 +332,7 @@ Geo node_geo(const std::vector<double>& x, const std::vector<double>& y, int lo,
 
 void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
   nodes_ = &nodes;
+  Trace tr(s, "hbs");
   N = nodes.n;
   require(N >= 1, "HBS: empty node set");
   L = 0;
@@ -454,6 +461,7 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
     RW_CUDA(cudaStreamSynchronize(s));
   }
 
+  tr.mark("compression (IDs)");
   // ---------------------------------------------------------- B and D blocks
   {
     std::vector<int> idx;
@@ -505,6 +513,7 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
     RW_CUDA(cudaStreamSynchronize(s));
   }
 
+  tr.mark("B, D blocks");
   // ---------------------------------------------------------- inverse
   // Per node: D~ (leaf: D; parent: [Dh_a B12; B21 Dh_b]); Dinv = D~^{-1};
   // Dh = (V* Dinv U)^{-1}; E = Dinv U Dh; F* = Dh V* Dinv; G = Dinv - E V* Dinv.
@@ -588,13 +597,13 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
       g4.push_back(GemmProb{LV.E.p + oT[t], T2.p + oT[t], LV.G.p + LV.oG[t], n, n, k, n, k, n, 0, 0, -1.0, 1.0});
     }
     batched_gemm(g4, s);
-    RW_CUDA(cudaStreamSynchronize(s));
     Dh_prev = std::move(Dh);
     oDh_prev = oK;
   }
   auto hf = flags.download(s);
   for (int f : hf) require(f == 0, "HBS inverse: singular diagonal block", RW_ERR_SINGULAR);
 
+  tr.mark("inverse");
   // ---------------------------------------------------------- statistics
   inv_elems = fwd_elems = 0;
   bytes = 0;

@@ -35,7 +35,7 @@ class IdBatch {
     IdMatProb spec;
     int sk_width = 0;  // 0: no sketch; else rows of the sketched W
     int nr = 0;        // rows of W handed to the QR
-    size_t woff = 0, moff = 0;
+    size_t woff = 0, moff = 0, noff = 0;
   };
   std::vector<Job> jobs;
   DBuf<double> W, norms;

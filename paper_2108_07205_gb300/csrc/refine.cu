@@ -40,6 +40,7 @@ __global__ void k_zero_cols(double* A, int ld, int nrows, const int* cols, int n
 
 void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::vector<int>& lvl, cudaStream_t s) {
   wall = &w;
+  Trace tr(s, "refine");
   const Opts& o = w.opts;
   const int P = w.n_panels;
   require(!pan.empty() && pan.size() == lvl.size(), "refine: need one level per cut panel");
@@ -119,6 +120,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     dc = to_device(dcv, s);
     RW_CUDA(cudaStreamSynchronize(s));
   }
+  tr.mark("nodes+maps");
   // Gamma_r: centre and radius of the cut and added points
   double cx = 0, cy = 0;
   for (int i : Ic) { cx += w.nodes.hx[i]; cy += w.nodes.hy[i]; }
@@ -145,6 +147,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     hpp.build(pn, opp, s);
     hpp.make_fp32(s);
   }
+  tr.mark("A_pp inverse (HBS)");
 
   const NodesView VW = w.nodes.view(), VP = pn.view();
   // a3: far rows of I_k against P^bas (shared by A_kc and A_kp)
@@ -152,8 +155,9 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   {
     IdMatProb cs{};
     cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
-    tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s);
+    tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 64, s);
   }
+  tr.mark("far ID");
   // near rows of I_k: [A_kc^near | A_kp^near]
   DBuf<int> dall_p;
   {
@@ -162,8 +166,9 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     dall_p = to_device(pd, s);
     IdMatProb cs{};
     cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
-    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
+    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 64, s);
   }
+  tr.mark("near ID");
   // A_pk: rows of [A_{p,div} | A_pk^near | n_p]
   DBuf<int> dnear;
   {
@@ -172,8 +177,9 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
     IdMatProb cs{};
     cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
-    tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s);
+    tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 64, s);
   }
+  tr.mark("pk ID");
   kf = tf.k; kn = tn.k; kpk = tp.k; kk = kf + kn; k = kk + kpk;
 
   // L_o (2No x kk) and L_p (2Np x kpk)
@@ -203,11 +209,13 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     k_zero_cols<<<ceil_div((long long)kpk * 2 * Nc, 256), 256, 0, s>>>(Rpk.p, kpk, kpk, dc.p, 2 * Nc);
     RW_CHECK_LAUNCH();
   }
+  tr.mark("L, R assembly");
   // a5: X = A~^{-1} L
   Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
   Xp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
   if (kk) w.hbs.apply_inverse(Lo.p, Xo.p, kk, s);
   if (kpk) hpp.apply_inverse(Lp.p, Xp.p, kpk, s);
+  tr.mark("X = A~^-1 L");
   // a6: W = I + R X and its inverse
   {
     TBuf<double> W(size_t(k) * k, s), Ww(size_t(k) * k, s), Xc(size_t(2) * Nc * std::max(kk, 1), s);
@@ -226,6 +234,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     auto hf = flag.download(s);
     require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
   }
+  tr.mark("W, W^-1");
   bytes = Lo.bytes() + Lp.bytes() + Rkc.bytes() + Rkp.bytes() + Rpk.bytes() + Xo.bytes() + Xp.bytes() + Winv.bytes() +
           hpp.bytes + pn.buf.bytes() + nn.buf.bytes();
 }
@@ -260,6 +269,20 @@ void Refinement::solve_direct(const double* g, double* tau, int nrhs, cudaStream
   woodbury_correct(yo.p, yp.p, nrhs, s);
   gather_scatter(yo.p, 2 * No, n_to_o.p, tau, 2 * Nn, n_from_o.p, nko, nrhs, s);
   gather_scatter(yp.p, 2 * Np, n_to_p.p, tau, 2 * Nn, n_from_p.p, nkp, nrhs, s);
+}
+
+void Refinement::solve_refined(const double* g, double* tau, int nrhs, int steps, cudaStream_t s) const {
+  solve_direct(g, tau, nrhs, s);
+  if (steps <= 0) return;
+  const size_t n = size_t(2) * Nn * nrhs;
+  TBuf<double> r(n, s), d(n, s);
+  for (int it = 0; it < steps; ++it) {
+    apply_exact(nn.view(), tau, r.p, nrhs, s);
+    // r = g - A tau ; tau += A_ext^{-1} r
+    axpby(g, r.p, n, 1.0, -1.0, s);
+    solve_direct(r.p, d.p, nrhs, s);
+    axpby(d.p, tau, n, 1.0, 1.0, s);
+  }
 }
 
 void Refinement::apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const {

@@ -34,6 +34,9 @@ struct Refinement {
   void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s);
   // Direct solve, device buffers: g, tau (2Nn x nrhs).
   void solve_direct(const double* g, double* tau, int nrhs, cudaStream_t s) const;
+  // Direct solve followed by `steps` rounds of iterative refinement against
+  // the exact refined operator (on-the-fly N-body evaluation of A_nn).
+  void solve_refined(const double* g, double* tau, int nrhs, int steps, cudaStream_t s) const;
   // Woodbury apply in ext space: (yo, yp) <- Ainv_ext (yo, yp), yo/yp hold
   // A~^{-1} g on entry (ld 2No / 2Np).
   void woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t s) const;

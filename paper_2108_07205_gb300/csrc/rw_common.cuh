@@ -26,7 +26,13 @@ struct Error : std::runtime_error {
                                          cudaGetErrorString(e_));            \
   } while (0)
 
-#define RW_CHECK_LAUNCH() RW_CUDA(cudaGetLastError())
+// Every kernel launch site ends with RW_CHECK_LAUNCH(), which also counts it.
+extern unsigned long long g_launches;
+#define RW_CHECK_LAUNCH()       \
+  do {                          \
+    ++::rw::g_launches;         \
+    RW_CUDA(cudaGetLastError()); \
+  } while (0)
 
 inline void require(bool ok, const std::string& msg, int code = RW_ERR_INVALID) {
   if (!ok) throw Error(code, msg);
@@ -181,5 +187,16 @@ struct StreamGuard {
 };
 
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
+
+// Phase timer for the refinement and build (enabled by RW_TRACE=1): prints
+// wall-clock time per phase, synchronising the stream at each mark.
+struct Trace {
+  cudaStream_t s;
+  bool on;
+  double t0;
+  const char* what;
+  explicit Trace(cudaStream_t st, const char* w);
+  void mark(const char* phase);
+};
 
 }  // namespace rw

@@ -19,7 +19,7 @@ RW_OK = 0
 ERRORS = {-1: "RW_ERR_INVALID", -2: "RW_ERR_OOM", -3: "RW_ERR_SINGULAR",
           -4: "RW_ERR_NOT_CONVERGED", -5: "RW_ERR_TIMEOUT", -6: "RW_ERR_CUDA"}
 CURVE_STAR, CURVE_CHANNEL = 0, 1
-MODE_DIRECT, MODE_GMRES_FP32 = 0, 1
+MODE_DIRECT, MODE_GMRES_FP32, MODE_DIRECT_REFINED = 0, 1, 2
 
 
 class RWError(RuntimeError):
@@ -58,8 +58,9 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
-           "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_stokeslet_data",
-           "rw_solve", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
+           "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
+           "rw_stokeslet_data",
+           "rw_solve", "rw_kernel_launches", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
 
 _lib = None
 
@@ -90,13 +91,16 @@ def load(build_if_missing=False):
     L.rw_refine_factor.argtypes = [vp, ctypes.c_int, ip, ip, vp, ctypes.POINTER(vp)]
     L.rw_ref_stats_get.argtypes = [vp, ctypes.POINTER(RefStats)]
     L.rw_ref_nodes.argtypes = [vp, dp, vp]
+    L.rw_apply_refined.argtypes = [vp, ctypes.c_int, dp, dp, vp]
     L.rw_stokeslet_data.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, dp, dp, vp]
     L.rw_solve.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int, vp, ctypes.POINTER(Info)]
     L.rw_ref_free.argtypes = [vp]
     L.rw_hbs_free.argtypes = [vp]
     L.rw_last_error.restype = ctypes.c_char_p
+    L.rw_kernel_launches.argtypes = []
+    L.rw_kernel_launches.restype = ctypes.c_ulonglong
     for name in EXPORTS:
-        if name not in ("rw_last_error", "rw_ref_free", "rw_hbs_free"):
+        if name not in ("rw_last_error", "rw_ref_free", "rw_hbs_free", "rw_kernel_launches"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -135,6 +139,11 @@ def _ptr(a, writable=False):
     if writable and not a.flags["WRITEABLE"]:
         raise TypeError("output array is read-only")
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def kernel_launches():
+    """Kernels launched by the library so far in this process."""
+    return int(load().rw_kernel_launches())
 
 
 def default_opts(**kw):
@@ -219,6 +228,11 @@ class Refinement:
         out = np.empty((6, n))
         _check(load().rw_ref_nodes(self.h, _ptr(out, True), _stream(stream)))
         return dict(zip(("x", "y", "nx", "ny", "w", "kappa"), out))
+
+    def apply_refined(self, tau, y, nrhs=1, stream=None):
+        """y = A_nn tau with the exact refined operator."""
+        _check(load().rw_apply_refined(self.h, nrhs, _ptr(tau), _ptr(y, True), _stream(stream)))
+        return y
 
     def stokeslet_data(self, src, f, g, nrhs=1, stream=None):
         """g = boundary data from point forces: src (n_src, 2), f (nrhs, n_src, 2)."""
