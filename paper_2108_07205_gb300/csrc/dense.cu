@@ -9,12 +9,14 @@
 
 namespace cg = cooperative_groups;
 
+#include <atomic>
 #include <chrono>
+#include <mutex>
 #include <cstdlib>
 
 namespace rw {
 
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -137,9 +139,8 @@ __global__ void k_gemm_reduce(const GemmWork* work, const double* scratch) {
   const GemmWork Wk = work[blockIdx.y];
   if (Wk.nsplit <= 1) return;
   const GemmProb& P = Wk.p;
-  const long long tot = (long long)P.m * P.n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int i = int(e % P.m), j = int(e / P.m);
+  for (int j = blockIdx.x; j < P.n; j += gridDim.x)
+  for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
     double s = 0.0;
     for (int q = 0; q < Wk.nsplit; ++q) s += scratch[Wk.scratch_off + (size_t(q) * P.n + j) * P.m + i];
     double* c = P.C + i + size_t(j) * P.ldc;
@@ -299,12 +300,12 @@ __global__ void __launch_bounds__(512) k_inverse(const InvProb* probs) {
   if (tid == 0) s_flag = 0;
   for (int c = tid; c < n; c += nt) ipiv[c] = c;
   double amax = 0.0;
-  for (long long e = tid; e < (long long)n * n; e += nt) {
-    const int i = int(e % n), j = int(e / n);
-    const double v = P.A[i + size_t(j) * P.lda];
-    M[i + size_t(j) * ld] = v;
-    amax = fmax(amax, fabs(v));
-  }
+  for (int j = tid >> 5; j < n; j += nt >> 5)
+    for (int i = tid & 31; i < n; i += 32) {
+      const double v = P.A[i + size_t(j) * P.lda];
+      M[i + size_t(j) * ld] = v;
+      amax = fmax(amax, fabs(v));
+    }
   int dummy;
   amax = block_reduce_max_abs_arg(amax, 0, &dummy, sval, sidx);
   const double tiny = 1e-14 * amax;
@@ -335,11 +336,33 @@ __global__ void __launch_bounds__(512) k_inverse(const InvProb* probs) {
     __syncthreads();
     for (int j = tid; j < n; j += nt) M[c + size_t(j) * ld] = (j == c) ? invp : M[c + size_t(j) * ld] * invp;
     __syncthreads();
-    for (long long e = tid; e < (long long)n * n; e += nt) {
-      const int r = int(e % n), j = int(e / n);
-      if (r == c) continue;
-      if (j == c) M[r + size_t(j) * ld] = -colc[r] * invp;
-      else M[r + size_t(j) * ld] -= colc[r] * M[c + size_t(j) * ld];
+    {
+      // warps over columns, lanes over rows (coalesced, no index division)
+      const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+      for (int j = warp; j < n; j += nw) {
+        double* mj = M + size_t(j) * ld;
+        if (j == c) {
+          for (int r = lane; r < n; r += 32) if (r != c) mj[r] = -colc[r] * invp;
+        } else {
+          const double pj = mj[c];
+          if (pj != 0.0) {
+            // 8 rows per lane in flight: loads first, then the updates
+            for (int r0 = 0; r0 < n; r0 += 256) {
+              double v[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int r = r0 + lane + 32 * u;
+                v[u] = (r < n) ? mj[r] : 0.0;
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int r = r0 + lane + 32 * u;
+                if (r < n && r != c) mj[r] = v[u] - colc[r] * pj;
+              }
+            }
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -554,8 +577,8 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
   __shared__ int s_done[1];
   (void)s_done;
   // load owned columns, norms
-  for (long long e = tid; e < (long long)nr * ncl; e += nt) {
-    const int i = int(e % nr), j = int(e / nr);
+  for (int e = tid; e < nr * ncl; e += nt) {
+    const int i = e % nr, j = e / nr;
     Wl[i + size_t(j) * nr] = P.W[i + size_t(c0 + j) * P.ldw];
   }
   __syncthreads();
@@ -668,8 +691,8 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
     __syncthreads();
   }
   // every CTA leaves the loop at the same s (same data, same decisions)
-  for (long long e = tid; e < (long long)nr * ncl; e += nt) {
-    const int i = int(e % nr), j = int(e / nr);
+  for (int e = tid; e < nr * ncl; e += nt) {
+    const int i = e % nr, j = e / nr;
     P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * nr];
   }
   // done flags for the remaining-pivot bookkeeping: mark in global norms
@@ -713,8 +736,8 @@ __global__ void __launch_bounds__(256) k_id_tsolve(const IdProb* probs, int base
   double* R = sm;                                        // keff x keff (if inR)
   double* bb = sm + (inR ? size_t(keff) * keff : 0);     // nw x keff
   if (inR) {
-    for (long long e = tid; e < (long long)keff * keff; e += blockDim.x) {
-      const int l = int(e % keff), i = int(e / keff);
+    for (int e = tid; e < keff * keff; e += blockDim.x) {
+      const int l = e % keff, i = e / keff;
       R[e] = (l <= i) ? P.W[l + size_t(P.piv[i]) * P.ldw] : 0.0;
     }
   }
@@ -743,9 +766,8 @@ __global__ void k_id_interp(const IdProb* probs) {
   const IdProb P = probs[blockIdx.y];
   const int nc = P.nc, k = *P.rank, keff = int(P.norms[2 * nc]);
   const bool noswap = P.norms[2 * nc + 3] != 0.0;
-  const long long tot = (long long)nc * k;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int j = int(e % nc), c = int(e / nc);
+  for (int c = blockIdx.x; c < k; c += gridDim.x)
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
     double v;
     if (j < k) v = (j == c) ? 1.0 : 0.0;
     else v = (c < keff) ? P.W[c + size_t(noswap ? P.piv[j] : j) * P.ldw] : 0.0;
@@ -777,6 +799,25 @@ __global__ void k_d2f(const double* in, float* out, size_t n) {
 int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, 152 * 16)); }
 
 }  // namespace
+
+// Raise the dynamic shared-memory limit of every kernel that uses more than
+// 48 KB, once per process, to the largest size any launch asks
+// for.  Done once (not per launch) because the limit is a per-function
+// setting shared by all host threads.
+static void init_smem_limits() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    const int lim = 210 * 1024;
+    cudaError_t e[4];
+    e[0] = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e[1] = cudaFuncSetAttribute(k_cpqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e[2] = cudaFuncSetAttribute(k_id_tsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e[3] = cudaFuncSetAttribute(k_cpqr_id<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    for (cudaError_t x : e) if (x != cudaSuccess) err = x;
+  });
+  if (err != cudaSuccess) throw Error(RW_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
+}
 
 void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
   std::vector<GemmWork> ws;
@@ -822,7 +863,10 @@ void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
   if (scratch) {
     long long mx = 0;
     for (auto& w : ws) mx = std::max(mx, (long long)w.p.m * w.p.n);
-    k_gemm_reduce<<<dim3(std::min(ceil_div(mx, 256), 1024), int(ws.size())), 256, 0, s>>>(dw.p, sc.p);
+    int mn = 0;
+    for (auto& w : ws) mn = std::max(mn, w.p.n);
+    k_gemm_reduce<<<dim3(std::min(mn, 1024), int(ws.size())), 256, 0, s>>>(dw.p, sc.p);
+    (void)mx;
     RW_CHECK_LAUNCH();
   }
 }
@@ -921,8 +965,7 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
   auto dp = to_device_tmp(ps, s);
   size_t smem = size_t(maxn) * sizeof(double);
   require(smem <= 200 * 1024, "batched_inverse: matrix too large");
-  if (smem > 48 * 1024)
-    RW_CUDA(cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  init_smem_limits();
   k_inverse<<<int(ps.size()), 512, smem, s>>>(dp.p);
   RW_CHECK_LAUNCH();
 }
@@ -949,6 +992,7 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
   for (int q = 0; q < 4; ++q) { base[q] = int(all.size()); all.insert(all.end(), grp[q].begin(), grp[q].end()); }
   base[4] = int(all.size());
   all.insert(all.end(), gl.begin(), gl.end());
+  init_smem_limits();
   auto dp = to_device_tmp(all, s);
   for (int q = 0; q < 4; ++q) {
     if (grp[q].empty()) continue;
@@ -960,7 +1004,6 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
       smem = std::max(smem, (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double));
       maxnr = std::max(maxnr, p.nr);
     }
-    RW_CUDA(cudaFuncSetAttribute(k_cpqr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cap + 1024)));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grp[q].size() * CS));
     cfg.blockDim = dim3(256);
@@ -986,7 +1029,6 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
     const int rmax = 150;  // R11 in shared memory up to 150 x 150
     const int kk = std::max(maxk, 1);
     const size_t tsm = ((kk <= rmax ? size_t(kk) * kk : 0) + 8 * size_t(kk)) * sizeof(double);
-    RW_CUDA(cudaFuncSetAttribute(k_id_tsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(std::max<size_t>(tsm, 48 * 1024))));
     k_id_tsolve<<<dim3(ceil_div(maxnc, TS_COLS), ng), 256, tsm, s>>>(dp.p, base[q], kk <= rmax ? rmax : 0);
     RW_CHECK_LAUNCH();
   }
@@ -994,8 +1036,6 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
     size_t gl_bytes = 0;
     for (auto& p : gl) gl_bytes = std::max(gl_bytes, size_t(p.nr) * sizeof(double));
     require(gl_bytes <= cap, "batched_id: more than 25600 feature rows");
-    if (gl_bytes > 48 * 1024)
-      RW_CUDA(cudaFuncSetAttribute(k_cpqr_id<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gl_bytes)));
     k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, s>>>(dp.p, base[4]);
     RW_CHECK_LAUNCH();
   }

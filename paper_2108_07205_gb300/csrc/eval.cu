@@ -146,11 +146,10 @@ __device__ __forceinline__ double idmat_value(const IdMatProb& P, int c, int i, 
 
 __global__ void k_idmat(const IdMatProb* probs, NodesView S, NodesView E1, bool e1s, NodesView E2, bool e2s) {
   const IdMatProb P = probs[blockIdx.y];
-  const long long tot = (long long)P.ncol * P.m;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int c = int(e % P.ncol), i = int(e / P.ncol);
-    P.W[c + size_t(i) * P.ldw] = idmat_value(P, c, i, S, E1, e1s, E2, e2s);
-  }
+  // rows of W (features) over x-threads, candidates over the grid
+  for (int i = blockIdx.x; i < P.m; i += gridDim.x)
+    for (int c = threadIdx.x; c < P.ncol; c += blockDim.x)
+      P.W[c + size_t(i) * P.ldw] = idmat_value(P, c, i, S, E1, e1s, E2, e2s);
 }
 
 __global__ void k_blocks(const BlockProb* probs, NodesView s0, NodesView s1) {
@@ -158,31 +157,25 @@ __global__ void k_blocks(const BlockProb* probs, NodesView s0, NodesView s1) {
   const NodesView& R = P.rset ? s1 : s0;
   const NodesView& C = P.cset ? s1 : s0;
   const bool same = P.rset == P.cset;
-  const long long tot = (long long)P.mr * P.mc;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int r = int(e % P.mr), c = int(e / P.mr);
-    const int dr = P.rows ? P.rows[r] : P.r0 + r;
+  for (int c = blockIdx.x; c < P.mc; c += gridDim.x) {
     const int dc = P.cols ? P.cols[c] : P.c0 + c;
-    P.out[r + size_t(c) * P.ld] = P.scale * a_entry(R, dr >> 1, dr & 1, C, dc >> 1, dc & 1, same);
+    for (int r = threadIdx.x; r < P.mr; r += blockDim.x) {
+      const int dr = P.rows ? P.rows[r] : P.r0 + r;
+      P.out[r + size_t(c) * P.ld] = P.scale * a_entry(R, dr >> 1, dr & 1, C, dc >> 1, dc & 1, same);
+    }
   }
 }
 
 __global__ void k_transpose(const TransProb* probs) {
   const TransProb P = probs[blockIdx.y];
-  const long long tot = (long long)P.m * P.n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int i = int(e % P.n), j = int(e / P.n);  // out(i, j) = in(j, i)
-    P.out[i + size_t(j) * P.ldo] = P.in[j + size_t(i) * P.ldi];
-  }
+  for (int j = blockIdx.x; j < P.m; j += gridDim.x)  // out(i, j) = in(j, i)
+    for (int i = threadIdx.x; i < P.n; i += blockDim.x) P.out[i + size_t(j) * P.ldo] = P.in[j + size_t(i) * P.ldi];
 }
 
 __global__ void k_copy(const CopyProb* probs) {
   const CopyProb P = probs[blockIdx.y];
-  const long long tot = (long long)P.m * P.n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int i = int(e % P.m), j = int(e / P.m);
-    P.out[i + size_t(j) * P.ldo] = P.in[i + size_t(j) * P.ldi];
-  }
+  for (int j = blockIdx.x; j < P.n; j += gridDim.x)
+    for (int i = threadIdx.x; i < P.m; i += blockDim.x) P.out[i + size_t(j) * P.ldo] = P.in[i + size_t(j) * P.ldi];
 }
 
 __global__ void k_velocity(NodesView nd, const double* tau, int nrhs, int nt, const double* tg, double* u) {

@@ -133,11 +133,8 @@ std::vector<int> IdBatch::pivots(cudaStream_t s) const { return piv.download(s);
 // ====================================================================== tree ID
 namespace {
 __global__ void k_gather_cols(const double* Z, int nr, const int* cand, int n, double* W) {
-  const long long tot = (long long)nr * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int r = int(e % nr), c = int(e / nr);
-    W[e] = Z[r + size_t(cand[c]) * nr];
-  }
+  for (int c = blockIdx.x; c < n; c += gridDim.x)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) W[r + size_t(c) * nr] = Z[r + size_t(cand[c]) * nr];
 }
 }  // namespace
 

@@ -19,6 +19,8 @@
 #include "refine.cuh"
 #include <algorithm>
 #include <cmath>
+#include <exception>
+#include <thread>
 
 namespace rw {
 
@@ -139,47 +141,64 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     v.push_back(2 * i + 1);
   }
 
-  // a2: A_pp^{-1} (dense below the threshold: a single-leaf HBS is the dense inverse)
-  {
-    Opts opp = o;
-    pp_dense = Np <= o.dense_pp_max_points;
-    if (pp_dense) opp.leaf_points = Np;
-    hpp.build(pn, opp, s);
-    hpp.make_fp32(s);
-  }
-  tr.mark("A_pp inverse (HBS)");
-
+  // a2 and a3 are independent: A_pp^{-1} (dense below the threshold: a
+  // single-leaf HBS is the dense inverse), the far-field ID and the near and
+  // A_pk IDs run concurrently on three streams driven by three host threads.
   const NodesView VW = w.nodes.view(), VP = pn.view();
-  // a3: far rows of I_k against P^bas (shared by A_kc and A_kp)
   TreeId tf, tn, tp;
-  {
-    IdMatProb cs{};
-    cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
-    tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 64, s);
-  }
-  tr.mark("far ID");
-  // near rows of I_k: [A_kc^near | A_kp^near]
-  DBuf<int> dall_p;
+  DBuf<int> dall_p, dnear;
   {
     std::vector<int> pd(2 * Np);
     for (int i = 0; i < 2 * Np; ++i) pd[i] = i;
     dall_p = to_device(pd, s);
-    IdMatProb cs{};
-    cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
-    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 64, s);
-  }
-  tr.mark("near ID");
-  // A_pk: rows of [A_{p,div} | A_pk^near | n_p]
-  DBuf<int> dnear;
-  {
     dnear = to_device(near_d, s);
-    std::vector<int> prow(2 * Np);
-    for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
-    IdMatProb cs{};
-    cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
-    tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 64, s);
+    RW_CUDA(cudaStreamSynchronize(s));
   }
-  tr.mark("pk ID");
+  cudaStream_t s1 = nullptr, s2 = nullptr;
+  RW_CUDA(cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking));
+  RW_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+  std::exception_ptr e1, e2;
+  std::thread th1([&] {
+    try {
+      Opts opp = o;
+      pp_dense = Np <= o.dense_pp_max_points;
+      if (pp_dense) opp.leaf_points = Np;
+      hpp.build(pn, opp, s1);
+      hpp.make_fp32(s1);
+      RW_CUDA(cudaStreamSynchronize(s1));
+    } catch (...) { e1 = std::current_exception(); }
+  });
+  std::thread th2([&] {
+    try {
+      // far rows of I_k against P^bas (shared by A_kc and A_kp)
+      IdMatProb cs{};
+      cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
+      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 64, s2);
+    } catch (...) { e2 = std::current_exception(); }
+  });
+  std::exception_ptr e0;
+  try {
+    // near rows of I_k: [A_kc^near | A_kp^near]
+    {
+      IdMatProb cs{};
+      cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
+      tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 64, s);
+    }
+    // A_pk: rows of [A_{p,div} | A_pk^near | n_p]
+    {
+      std::vector<int> prow(2 * Np);
+      for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
+      IdMatProb cs{};
+      cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
+      tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 64, s);
+    }
+  } catch (...) { e0 = std::current_exception(); }
+  th1.join();
+  th2.join();
+  cudaStreamDestroy(s1);
+  cudaStreamDestroy(s2);
+  for (auto& e : {e0, e1, e2}) if (e) std::rethrow_exception(e);
+  tr.mark("A_pp inverse + IDs (concurrent)");
   kf = tf.k; kn = tn.k; kpk = tp.k; kk = kf + kn; k = kk + kpk;
 
   // L_o (2No x kk) and L_p (2Np x kpk)

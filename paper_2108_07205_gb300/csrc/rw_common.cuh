@@ -2,6 +2,7 @@
 // buffers, node sets and the Stokes kernel entries of Sec. 2.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -27,11 +28,11 @@ struct Error : std::runtime_error {
   } while (0)
 
 // Every kernel launch site ends with RW_CHECK_LAUNCH(), which also counts it.
-extern unsigned long long g_launches;
-#define RW_CHECK_LAUNCH()       \
-  do {                          \
-    ++::rw::g_launches;         \
-    RW_CUDA(cudaGetLastError()); \
+extern std::atomic<unsigned long long> g_launches;
+#define RW_CHECK_LAUNCH()                                              \
+  do {                                                                 \
+    ::rw::g_launches.fetch_add(1, std::memory_order_relaxed);          \
+    RW_CUDA(cudaGetLastError());                                       \
   } while (0)
 
 inline void require(bool ok, const std::string& msg, int code = RW_ERR_INVALID) {
