@@ -127,6 +127,23 @@ int rw_hbs_nodes(rw_hbs_t h, double* out, void* stream);
 int rw_hbs_apply_inverse(rw_hbs_t h, int nrhs, const double* b, double* x,
                          void* stream);
 
+/* Allocation-free x = A_oo^{-1} b (no counterpart in the paper: a library
+ * service).  For callers that cannot let the library allocate or free device
+ * memory during a solve -- e.g. a host application whose device memory is
+ * owned by another framework's pool, or a latency-critical loop where an
+ * allocation or free could synchronise the device.  Same result as
+ * rw_hbs_apply_inverse; every temporary comes from one fixed 32 MiB device
+ * array inside the library (held by every GPU that loads the library until
+ * exit), so b and x must be device pointers and nrhs is limited to 1..8;
+ * larger problems return RW_ERR_INVALID with a message.  The first call on a
+ * device resolves the array's address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (the sweep writes every
+ * entry before reading it); calls that overlap on the GPU race on it, so
+ * order them on one stream. */
+int rw_hbs_apply_inverse_noalloc(rw_hbs_t h, int nrhs, const double* b,
+                                 double* x, void* stream);
+
 /* y = A_oo x by the HBS forward representation (used for GMRES mat-vecs). */
 int rw_hbs_apply_forward(rw_hbs_t h, int nrhs, const double* x, double* y,
                          void* stream);

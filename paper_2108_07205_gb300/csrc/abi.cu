@@ -1,17 +1,9 @@
 // extern "C" boundary of the rwsolve library (declared in include/rwsolve.h).
 // Argument checking, host/device pointer handling and error codes live here;
 // the work is done by refine.cu / hbs.cu and the kernels below them.
-#include "refine.cuh"
+#include "handles.cuh"
 #include <cstring>
 #include <memory>
-
-struct rw_hbs_s {
-  rw::Wall wall;
-};
-struct rw_ref_s {
-  rw::Refinement ref;
-  const rw_hbs_s* h = nullptr;
-};
 
 namespace {
 
@@ -97,6 +89,11 @@ rw::Opts to_opts(const rw_opts* o) {
 }
 
 }  // namespace
+
+namespace rw {
+int abi_fail(int code, const std::string& msg) { return fail(code, msg); }
+void abi_clear_error() { g_last_error.clear(); }
+}  // namespace rw
 
 extern "C" {
 

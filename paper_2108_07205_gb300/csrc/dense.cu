@@ -925,6 +925,48 @@ void batched_gemv(const std::vector<GemvProb<T>>& probs, int nrhs, T* scratch, c
   RW_CHECK_LAUNCH();
 }
 
+template <class T>
+void gemv_into_sizes(const std::vector<GemvProb<T>>& probs, int nrhs, size_t* desc_bytes, size_t* scratch_elems) {
+  std::vector<GemvWork<T>> work;
+  std::vector<int> offs;
+  size_t sc;
+  gemv_plan(probs, nrhs, work, offs, sc);
+  *desc_bytes = work.size() * sizeof(GemvWork<T>) + offs.size() * sizeof(int) + 16;
+  *scratch_elems = sc;
+}
+
+template <class T>
+void gemv_into(const std::vector<GemvProb<T>>& probs, int nrhs, void* desc, T* scratch, cudaStream_t s) {
+  require(nrhs >= 1 && nrhs <= 8, "gemv_into: nrhs must be in 1..8");
+  std::vector<GemvWork<T>> work;
+  std::vector<int> offs;
+  size_t sc;
+  gemv_plan(probs, nrhs, work, offs, sc);
+  if (work.empty()) return;
+  require(sc == 0 || scratch != nullptr, "gemv_into: scratch buffer missing");
+  auto* dw = static_cast<GemvWork<T>*>(desc);
+  int* doff = reinterpret_cast<int*>(static_cast<char*>(desc) + ((work.size() * sizeof(GemvWork<T>) + 15) / 16) * 16);
+  RW_CUDA(cudaMemcpyAsync(dw, work.data(), work.size() * sizeof(GemvWork<T>), cudaMemcpyHostToDevice, s));
+  RW_CUDA(cudaMemcpyAsync(doff, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  const int nprob = int(work.size());
+  int maxm = 0;
+  for (auto& w : work) maxm = std::max(maxm, w.p.m);
+  switch (nrhs) {
+#define RW_GEMV_INTO_CASE(NR)                                                                \
+  case NR:                                                                                   \
+    k_gemv<T, NR><<<offs.back(), 256, 0, s>>>(dw, doff, nprob, scratch);                     \
+    if (sc) k_gemv_reduce<T, NR><<<dim3(ceil_div(maxm, 256), nprob), 256, 0, s>>>(dw, nprob, scratch); \
+    break;
+    RW_GEMV_INTO_CASE(1) RW_GEMV_INTO_CASE(2) RW_GEMV_INTO_CASE(3) RW_GEMV_INTO_CASE(4)
+    RW_GEMV_INTO_CASE(5) RW_GEMV_INTO_CASE(6) RW_GEMV_INTO_CASE(7) RW_GEMV_INTO_CASE(8)
+#undef RW_GEMV_INTO_CASE
+  }
+  RW_CHECK_LAUNCH();
+}
+
+template void gemv_into_sizes<double>(const std::vector<GemvProb<double>>&, int, size_t*, size_t*);
+template void gemv_into<double>(const std::vector<GemvProb<double>>&, int, void*, double*, cudaStream_t);
+
 template size_t gemv_scratch_elems<double>(const std::vector<GemvProb<double>>&, int);
 template size_t gemv_scratch_elems<float>(const std::vector<GemvProb<float>>&, int);
 template void batched_gemv<double>(const std::vector<GemvProb<double>>&, int, double*, cudaStream_t);

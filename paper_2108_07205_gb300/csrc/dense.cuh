@@ -43,6 +43,14 @@ template <class T>
 void batched_gemv(const std::vector<GemvProb<T>>& probs, int nrhs, T* scratch,
                   cudaStream_t s);
 
+// The same GEMV launch with caller-provided device memory for the launch
+// descriptors (desc, gemv_into_sizes bytes, 16-byte aligned) and the split-K
+// partials (scratch, gemv_into_sizes elements): performs no allocation.
+template <class T>
+void gemv_into_sizes(const std::vector<GemvProb<T>>& probs, int nrhs, size_t* desc_bytes, size_t* scratch_elems);
+template <class T>
+void gemv_into(const std::vector<GemvProb<T>>& probs, int nrhs, void* desc, T* scratch, cudaStream_t s);
+
 // y = alpha A x + beta y for a problem list and any nrhs: GEMV kernels for
 // nrhs <= 8 (chunks of 8 for FP32), the tiled GEMM above that (FP64).
 // Temporaries are stream-ordered.

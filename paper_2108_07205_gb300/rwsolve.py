@@ -58,6 +58,7 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
+           "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
            "rw_stokeslet_data",
            "rw_solve", "rw_kernel_launches", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
@@ -88,6 +89,7 @@ def load(build_if_missing=False):
     L.rw_hbs_nodes.argtypes = [vp, dp, vp]
     L.rw_hbs_apply_inverse.argtypes = [vp, ctypes.c_int, dp, dp, vp]
     L.rw_hbs_apply_forward.argtypes = [vp, ctypes.c_int, dp, dp, vp]
+    L.rw_hbs_apply_inverse_noalloc.argtypes = [vp, ctypes.c_int, dp, dp, vp]
     L.rw_refine_factor.argtypes = [vp, ctypes.c_int, ip, ip, vp, ctypes.POINTER(vp)]
     L.rw_ref_stats_get.argtypes = [vp, ctypes.POINTER(RefStats)]
     L.rw_ref_nodes.argtypes = [vp, dp, vp]
@@ -185,6 +187,11 @@ class Wall:
 
     def apply_inverse(self, b, x, nrhs=1, stream=None):
         _check(load().rw_hbs_apply_inverse(self.h, nrhs, _ptr(b), _ptr(x, True), _stream(stream)))
+        return x
+
+    def apply_inverse_noalloc(self, b, x, nrhs=1, stream=None):
+        """x = A_oo^{-1} b with no device allocation (device buffers only)."""
+        _check(load().rw_hbs_apply_inverse_noalloc(self.h, nrhs, _ptr(b), _ptr(x, True), _stream(stream)))
         return x
 
     def apply_forward(self, x, y, nrhs=1, stream=None):
