@@ -46,10 +46,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", 1))
-    local = int(os.environ.get("LOCAL_RANK", 0))
-    return rank, world, local
+    from paper_2108_07205_gb300 import replicas
+    return replicas.rank_info()
 
 
 class Clocks:
@@ -106,7 +104,7 @@ def stokeslet_inputs(step, rank):
 
 def run_ours(args, rank, world, local):
     import torch
-    from paper_2108_07205_gb300 import rwsolve, inputs
+    from paper_2108_07205_gb300 import rwsolve, inputs, replicas
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -119,7 +117,7 @@ def run_ours(args, rank, world, local):
     build_s = time.time() - t0
     hst = wall.stats()
     total = args.warmup + args.steps
-    sched = inputs.time_schedule(17 + rank, P_PANELS, 2 * total + 1)
+    sched = inputs.time_schedule(replicas.schedule_seed(rank), P_PANELS, 2 * total + 1)
     # device-resident inputs for every step
     dev_in = []
     host_in = []
@@ -156,8 +154,7 @@ def run_ours(args, rank, world, local):
     def timed(offset, host):
         for w in range(args.warmup):
             step(offset + w, host)
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
         lat = []
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -180,24 +177,27 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         launches = rwsolve.kernel_launches() - n_launch0
         clocks = clk.stop()
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         ms = ev0.elapsed_time(ev1)
         lats = [a.elapsed_time(b) for a, b in lat]
         return ms, lats, stats, clocks, launches
 
     ms, lats, stats, clocks, launches = timed(0, host=False)
     ms_e2e, lats_e2e, _, _, _ = timed(total, host=True)
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    # profiled repeat of the device-input steps: per-kernel-class CUDA-event
+    # durations (on each launch's stream) and algorithmic flops
+    rwsolve.profile(True)
+    for i in range(args.steps):
+        step(args.warmup + i, False)
+    prof = rwsolve.profile_read()
+    rwsolve.profile(False)
+    ms, ms_e2e = replicas.max_over_ranks([ms, ms_e2e])
     ks = [s[0]["k"] for s in stats]
     nps = [s[0]["n_p"] for s in stats]
     out = {
         "ms": ms, "ms_e2e": ms_e2e, "lat": lats, "lat_e2e": lats_e2e, "clocks": clocks,
         "build_s": build_s, "hbs": hst, "k_mean": float(np.mean(ks)), "np_range": [min(nps), max(nps)],
-        "iters": [s[1]["iters"] for s in stats], "launches": launches,
+        "iters": [s[1]["iters"] for s in stats], "launches": launches, "prof": prof,
     }
     # solve-only rate on one refinement (same shapes), and the sweep kernel roofline
     panels, levels = sched[0]
@@ -326,7 +326,30 @@ def main():
     hbm = peaks.get("hbm_gbs", 6800.0)
     value = world * args.steps / (out["ms"] / 1e3)
     e2e = world * args.steps / (out["ms_e2e"] / 1e3)
+    # FP64 ALU peak: 152 SMs x 4 FP64 flop/clk (nominal 1.25 TFLOP/s at the
+    # 2070 MHz maximum clock), evaluated at the median SM clock under load
+    sm_mhz = (out["clocks"] or {}).get("sm_mhz") or 2070.0
+    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
+    prof = out["prof"]
+    dom = max(prof, key=lambda c: prof[c]["ms"])
+    dp = prof[dom]
+    dom_names = {"id": "column-pivoted QR (thread-block cluster, FP64)", "gemm": "batched tiled GEMM (FP64)",
+                 "gemv": "batched GEMV / HBS sweeps (FP64)", "inverse": "batched Gauss-Jordan inverse (FP64)",
+                 "eval": "kernel-entry evaluation (FP64)", "other": "bookkeeping kernels"}
+    if dom in ("id", "gemm", "inverse", "eval"):
+        ach = dp["flops"] / (dp["ms"] / 1e3) / 1e12
+        roof = {"kernel": dom_names[dom], "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None, "launches_per_step": dp["launches"] / args.steps,
+                "avg_launch_ms": dp["ms"] / max(dp["launches"], 1),
+                "peak_source": "derived FP64 peak (152 SMs x 4 flop/clk x median SM clock)"}
+    else:
+        ach = dp["bytes"] / (dp["ms"] / 1e3) / 1e9
+        roof = {"kernel": dom_names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "launches_per_step": dp["launches"] / args.steps,
+                "avg_launch_ms": dp["ms"] / max(dp["launches"], 1), "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     achieved = out["sweep_bytes"] / (out["sweep_ms"] / 1e3) / 1e9
+    sweep_flops = 2.0 * out["hbs"]["inv_elems"]
+    share = {c: round(prof[c]["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9), 4) for c in prof}
     line = {
         "metric": "refined-wall solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps,
@@ -339,9 +362,12 @@ def main():
         "e2e": {"value": e2e, "unit": "solves/s",
                 "h2d_bytes_per_step": 8 * (2 * N_SRC + 2 * N_SRC + 2 * TARGETS),
                 "d2h_bytes_per_step": 8 * (2 * TARGETS) + 8 * 2 * 16 * P_PANELS},
-        "roofline": {"kernel": "HBS inverse sweep (s1, FP64, 1 RHS)", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "roofline": roof,
+        "kernel_time_share": share,
+        "roofline_sweep": {"kernel": "HBS inverse sweep (s1, FP64, 1 RHS, L2 flushed)", "ms": out["sweep_ms"],
+                           "hbm_achieved_gbs": achieved, "hbm_frac": achieved / hbm,
+                           "fp64_achieved_tflops": sweep_flops / (out["sweep_ms"] / 1e3) / 1e12,
+                           "fp64_frac": sweep_flops / (out["sweep_ms"] / 1e3) / 1e12 / fp64_peak},
         "clocks": out["clocks"],
         "gpu_launches": out["launches"],
     }

@@ -197,6 +197,30 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets,
  * (diagnostics: benchmarks difference it around a timed region). */
 unsigned long long rw_kernel_launches(void);
 
+/* Opt-in kernel profiler (diagnostics, no counterpart in the paper).
+ * rw_profile(1) clears the records and starts recording a pair of CUDA events
+ * around every kernel launch of this library, on the stream of that launch,
+ * with the launch's algorithmic flops and bytes (GEMM 2mnk, GEMV 2mn*nrhs,
+ * Gauss-Jordan 2n^3, column-pivoted QR 4 flops per trailing entry per pivot
+ * step, counted on the device).  rw_profile(0) stops.  rw_profile_read
+ * synchronises the device and fills out[RW_KCLASS_COUNT] with per-class
+ * launch counts, summed event durations (ms), flops and bytes. */
+#define RW_KCLASS_ID 0       /* column-pivoted QR / interpolative decomposition */
+#define RW_KCLASS_GEMM 1     /* batched tiled GEMM (FP64)                        */
+#define RW_KCLASS_GEMV 2     /* batched GEMV: the HBS sweeps and Woodbury apply  */
+#define RW_KCLASS_INVERSE 3  /* batched Gauss-Jordan inverse                     */
+#define RW_KCLASS_EVAL 4     /* kernel-entry, proxy, node and N-body evaluation  */
+#define RW_KCLASS_OTHER 5    /* copies, gathers, ID bookkeeping                  */
+#define RW_KCLASS_COUNT 6
+typedef struct {
+  long long launches;
+  double ms;
+  double flops;
+  double bytes;
+} rw_kernel_stat;
+int rw_profile(int enable);
+int rw_profile_read(rw_kernel_stat* out, int n);
+
 void rw_ref_free(rw_ref_t r);
 void rw_hbs_free(rw_hbs_t h);
 const char* rw_last_error(void);

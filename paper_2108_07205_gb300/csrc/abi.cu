@@ -304,6 +304,25 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
 
 unsigned long long rw_kernel_launches(void) { return rw::g_launches; }
 
+int rw_profile(int enable) {
+  return guarded([&] { rw::profile_enable(enable != 0); });
+}
+
+int rw_profile_read(rw_kernel_stat* out, int n) {
+  if (!out || n < RW_KCLASS_COUNT) return fail(RW_ERR_INVALID, "rw_profile_read: need RW_KCLASS_COUNT entries");
+  return guarded([&] {
+    long long l[rw::KC_COUNT];
+    double ms[rw::KC_COUNT], fl[rw::KC_COUNT], by[rw::KC_COUNT];
+    rw::profile_read(l, ms, fl, by);
+    for (int c = 0; c < RW_KCLASS_COUNT; ++c) {
+      out[c].launches = l[c];
+      out[c].ms = ms[c];
+      out[c].flops = fl[c];
+      out[c].bytes = by[c];
+    }
+  });
+}
+
 void rw_ref_free(rw_ref_t r) { delete r; }
 void rw_hbs_free(rw_hbs_t h) { delete h; }
 const char* rw_last_error(void) { return g_last_error.c_str(); }

@@ -36,6 +36,67 @@ void Trace::mark(const char* phase) {
   t0 = t;
 }
 
+// ------------------------------------------------------------------ profiler
+namespace {
+struct ProfRec { cudaEvent_t a, b; int cls; double flops, bytes; };
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof;
+std::atomic<bool> g_prof_on{false};
+__device__ double g_id_flops;
+}  // namespace
+
+bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
+
+double* id_flops_counter() {
+  if (!prof_enabled()) return nullptr;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_id_flops) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return static_cast<double*>(p);
+}
+
+ProfScope::ProfScope(int cls_, cudaStream_t st, double fl, double by)
+    : on(prof_enabled()), cls(cls_), s(st), flops(fl), bytes(by) {
+  if (!on) return;
+  cudaEventCreate(&a);
+  cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope() {
+  if (!on) return;
+  cudaEvent_t b;
+  cudaEventCreate(&b);
+  cudaEventRecord(b, s);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back(ProfRec{a, b, cls, flops, bytes});
+}
+
+void profile_enable(bool on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaDeviceSynchronize();
+  for (auto& r : g_prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  g_prof.clear();
+  double z = 0.0;
+  cudaMemcpyToSymbol(g_id_flops, &z, sizeof(double));
+  g_prof_on.store(on);
+}
+
+void profile_read(long long* launches, double* ms, double* flops, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaDeviceSynchronize();
+  for (int c = 0; c < KC_COUNT; ++c) { launches[c] = 0; ms[c] = 0; flops[c] = 0; bytes[c] = 0; }
+  for (auto& r : g_prof) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    launches[r.cls] += 1;
+    ms[r.cls] += t;
+    flops[r.cls] += r.flops;
+    bytes[r.cls] += r.bytes;
+  }
+  double idf = 0.0;
+  cudaMemcpyFromSymbol(&idf, g_id_flops, sizeof(double));
+  flops[KC_ID] += idf;
+}
+
 namespace {
 
 __device__ __forceinline__ int find_problem(const int* offs, int nprob, int tile) {
@@ -386,7 +447,7 @@ __global__ void __launch_bounds__(512) k_inverse(const InvProb* probs) {
 // problems); else W stays in global memory and the current Householder
 // vector is cached in shared memory.
 template <bool SM>
-__global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_base) {
+__global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_base, double* flops_out) {
   const IdProb P = probs[nprob_base + blockIdx.x];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int nr = P.nr, nc = P.nc;
@@ -528,7 +589,14 @@ __global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_
     }
   }
   __syncthreads();
-  if (tid == 0) { *P.rank = k; P.norms[2 * nc] = double(keff); P.norms[2 * nc + 3] = 0.0; }
+  if (tid == 0) {
+    *P.rank = k; P.norms[2 * nc] = double(keff); P.norms[2 * nc + 3] = 0.0;
+    if (flops_out) {
+      double f = 0.0;
+      for (int q = 0; q < s; ++q) f += 4.0 * double(nr - q) * double(nc - q - 1);
+      atomicAdd(flops_out, f);
+    }
+  }
   if (SM) {
     // the finished factorisation (R and T) goes back for k_id_interp
     for (long long e = tid; e < (long long)nr * nc; e += nt) {
@@ -556,7 +624,7 @@ __global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_
 // are not swapped: column q keeps its data, piv[] records the pivot order,
 // and the factorisation is written back to global memory in this "no-swap"
 // layout (R(l, i) = W[l, piv[i]]; T for a non-pivot candidate q in column q).
-__global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int base, int CS) {
+__global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int base, int CS, double* flops_out) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = int(cluster.block_rank());
   const IdProb P = probs[base + blockIdx.x / CS];
@@ -697,7 +765,16 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
   }
   // done flags for the remaining-pivot bookkeeping: mark in global norms
   for (int j = tid; j < ncl; j += nt) P.norms[nc + c0 + j] = (nrm[j] < 0.0) ? -1.0 : 1.0;
-  if (crank == 0 && tid == 0) { P.norms[2 * nc + 1] = double(s); P.norms[2 * nc + 2] = ref; P.norms[2 * nc + 3] = 1.0; }
+  if (crank == 0 && tid == 0) {
+    P.norms[2 * nc + 1] = double(s); P.norms[2 * nc + 2] = ref; P.norms[2 * nc + 3] = 1.0;
+    if (flops_out) {
+      // Householder QR with column pivoting: dot + update = 4 flops per
+      // trailing entry per step
+      double f = 0.0;
+      for (int q = 0; q < s; ++q) f += 4.0 * double(nr - q) * double(nc - q - 1);
+      atomicAdd(flops_out, f);
+    }
+  }
   cluster.sync();  // keep shared memory alive until remote readers are done
 }
 
@@ -858,6 +935,12 @@ void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
   TBuf<double> sc(scratch, s);
   auto dw = to_device_tmp(ws, s);
   auto doff = to_device_tmp(offs, s);
+  double fl = 0.0, by = 0.0;
+  for (auto& w : ws) {
+    fl += 2.0 * w.p.m * w.p.n * double(w.p.k);
+    by += 8.0 * (double(w.p.m) * w.p.k + double(w.p.k) * w.p.n + 2.0 * w.p.m * w.p.n);
+  }
+  ProfScope ps(KC_GEMM, s, fl, by);
   k_gemm<<<offs.back(), 256, 0, s>>>(dw.p, doff.p, int(ws.size()), sc.p);
   RW_CHECK_LAUNCH();
   if (scratch) {
@@ -911,7 +994,13 @@ void batched_gemv(const std::vector<GemvProb<T>>& probs, int nrhs, T* scratch, c
   auto doff = to_device_tmp(offs, s);
   const int nprob = int(work.size());
   int maxm = 0;
-  for (auto& w : work) maxm = std::max(maxm, w.p.m);
+  double fl = 0.0, by = 0.0;
+  for (auto& w : work) {
+    maxm = std::max(maxm, w.p.m);
+    fl += 2.0 * w.p.m * double(w.p.n) * nrhs;
+    by += double(sizeof(T)) * (double(w.p.m) * w.p.n + double(nrhs) * (w.p.n + 2.0 * w.p.m));
+  }
+  ProfScope ps(KC_GEMV, s, fl, by);
   switch (nrhs) {
 #define RW_GEMV_CASE(NR)                                                                   \
   case NR:                                                                                 \
@@ -1008,6 +1097,9 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
   size_t smem = size_t(maxn) * sizeof(double);
   require(smem <= 200 * 1024, "batched_inverse: matrix too large");
   init_smem_limits();
+  double fl = 0.0;
+  for (auto& p : ps) fl += 2.0 * double(p.n) * p.n * p.n;
+  ProfScope prof(KC_INVERSE, s, fl, 0.0);
   k_inverse<<<int(ps.size()), 512, smem, s>>>(dp.p);
   RW_CHECK_LAUNCH();
 }
@@ -1058,14 +1150,18 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_cluster, (const IdProb*)dp.p, base[q], CS));
-    RW_CHECK_LAUNCH();
+    {
+      ProfScope ps(KC_ID, s);
+      RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_cluster, (const IdProb*)dp.p, base[q], CS, id_flops_counter()));
+      RW_CHECK_LAUNCH();
+    }
     int maxk = 0, maxnc = 0;
     for (auto& p : grp[q]) {
       maxk = std::max(maxk, std::min(std::min(p.nr, p.nc), p.max_rank));
       maxnc = std::max(maxnc, p.nc);
     }
     const int ng = int(grp[q].size());
+    ProfScope pf(KC_OTHER, s);
     k_id_prep<<<ceil_div(ng, 128), 128, 0, s>>>(dp.p, base[q], ng);
     RW_CHECK_LAUNCH();
     const int rmax = 150;  // R11 in shared memory up to 150 x 150
@@ -1078,7 +1174,8 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
     size_t gl_bytes = 0;
     for (auto& p : gl) gl_bytes = std::max(gl_bytes, size_t(p.nr) * sizeof(double));
     require(gl_bytes <= cap, "batched_id: more than 25600 feature rows");
-    k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, s>>>(dp.p, base[4]);
+    ProfScope pg(KC_ID, s);
+    k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, s>>>(dp.p, base[4], id_flops_counter());
     RW_CHECK_LAUNCH();
   }
 }

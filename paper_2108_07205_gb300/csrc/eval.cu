@@ -319,6 +319,7 @@ void eval_nodes(const Curve& c, const double* ta, const double* tb, int n_int, d
                 cudaStream_t s) {
   if (n_int <= 0) return;
   ensure_gl();
+  ProfScope prof_(KC_EVAL, s);
   k_nodes<<<ceil_div(16LL * n_int, 128), 128, 0, s>>>(c, ta, tb, n_int, out, ld);
   RW_CHECK_LAUNCH();
 }
@@ -331,6 +332,7 @@ void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S, const N
   if (mx == 0) return;
   auto d = to_device_tmp(probs, s);
   dim3 grid(std::min(grid1(mx), 1024), int(probs.size()));
+  ProfScope prof_(KC_EVAL, s);
   k_idmat<<<grid, 256, 0, s>>>(d.p, S, E1, e1_same, E2, e2_same);
   RW_CHECK_LAUNCH();
 }
@@ -343,6 +345,7 @@ void eval_blocks(const std::vector<BlockProb>& probs, const NodesView& set0, con
   if (ps.empty()) return;
   auto d = to_device_tmp(ps, s);
   dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
+  ProfScope prof_(KC_EVAL, s);
   k_blocks<<<grid, 256, 0, s>>>(d.p, set0, set1);
   RW_CHECK_LAUNCH();
 }
@@ -354,6 +357,7 @@ void batched_transpose(const std::vector<TransProb>& probs, cudaStream_t s) {
   if (ps.empty()) return;
   auto d = to_device_tmp(ps, s);
   dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
+  ProfScope prof_(KC_OTHER, s);
   k_transpose<<<grid, 256, 0, s>>>(d.p);
   RW_CHECK_LAUNCH();
 }
@@ -365,6 +369,7 @@ void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s) {
   if (ps.empty()) return;
   auto d = to_device_tmp(ps, s);
   dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
+  ProfScope prof_(KC_OTHER, s);
   k_copy<<<grid, 256, 0, s>>>(d.p);
   RW_CHECK_LAUNCH();
 }
@@ -372,6 +377,7 @@ void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s) {
 void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* u,
                    cudaStream_t s) {
   if (nt <= 0 || nrhs <= 0) return;
+  ProfScope prof_(KC_EVAL, s);
   k_velocity<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, nrhs, nt, targets, u);
   RW_CHECK_LAUNCH();
 }
@@ -379,6 +385,7 @@ void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, 
 void eval_stokeslets(const NodesView& nodes, int ns, const double* src, int nrhs, const double* f, double* g,
                      cudaStream_t s) {
   if (nodes.n <= 0 || nrhs <= 0) return;
+  ProfScope prof_(KC_EVAL, s);
   k_stokeslets<<<dim3(ceil_div(nodes.n, 128), nrhs), 128, 0, s>>>(nodes, ns, src, nrhs, f, g);
   RW_CHECK_LAUNCH();
 }
@@ -386,6 +393,7 @@ void eval_stokeslets(const NodesView& nodes, int ns, const double* src, int nrhs
 void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, cudaStream_t s) {
   if (nodes.n <= 0 || nrhs <= 0) return;
   TBuf<double> flux(nrhs, s);
+  ProfScope prof_(KC_EVAL, s);
   k_flux<<<nrhs, 256, 0, s>>>(nodes, x, 2 * nodes.n, flux.p);
   k_apply_exact<<<dim3(ceil_div(nodes.n, NB_T), nrhs), NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p);
   RW_CHECK_LAUNCH();
@@ -405,6 +413,7 @@ void max_colnorm(const double* W, int nr, int nc, int ld, double* out, cudaStrea
 void gather_scatter(const double* in, int ldi, const int* idx_in, double* out, int ldo, const int* idx_out, int n,
                     int nrhs, cudaStream_t s) {
   if (n <= 0 || nrhs <= 0) return;
+  ProfScope prof_(KC_OTHER, s);
   k_gather_scatter<<<dim3(std::min(ceil_div(n, 256), 1024), nrhs), 256, 0, s>>>(in, ldi, idx_in, out, ldo, idx_out, n);
   RW_CHECK_LAUNCH();
 }

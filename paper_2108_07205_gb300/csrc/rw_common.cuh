@@ -189,6 +189,25 @@ struct StreamGuard {
 
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 
+// Opt-in kernel profiler (rw_profile / rw_profile_read): when enabled, each
+// launch site records CUDA events on its own stream around its launches and
+// adds its algorithmic flops and bytes to a per-class total.
+enum KClass { KC_ID = 0, KC_GEMM, KC_GEMV, KC_INVERSE, KC_EVAL, KC_OTHER, KC_COUNT };
+bool prof_enabled();
+struct ProfScope {
+  bool on;
+  int cls;
+  cudaStream_t s;
+  double flops, bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(int cls_, cudaStream_t st, double fl = 0.0, double by = 0.0);
+  ~ProfScope();
+};
+// Device counter of column-pivoted QR flops (added by the kernels).
+double* id_flops_counter();
+void profile_enable(bool on);
+void profile_read(long long* launches, double* ms, double* flops, double* bytes);
+
 // Phase timer for the refinement and build (enabled by RW_TRACE=1): prints
 // wall-clock time per phase, synchronising the stream at each mark.
 struct Trace {

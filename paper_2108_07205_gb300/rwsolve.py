@@ -53,6 +53,14 @@ class RefStats(ctypes.Structure):
                 ("pp_levels", ctypes.c_int), ("bytes", ctypes.c_longlong)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+KCLASSES = ["id", "gemm", "gemv", "inverse", "eval", "other"]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double)]
 
@@ -61,7 +69,7 @@ EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_stats_get", "rw_hbs_nodes"
            "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
            "rw_stokeslet_data",
-           "rw_solve", "rw_kernel_launches", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
+           "rw_solve", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
 
 _lib = None
 
@@ -99,6 +107,8 @@ def load(build_if_missing=False):
     L.rw_ref_free.argtypes = [vp]
     L.rw_hbs_free.argtypes = [vp]
     L.rw_last_error.restype = ctypes.c_char_p
+    L.rw_profile.argtypes = [ctypes.c_int]
+    L.rw_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int]
     L.rw_kernel_launches.argtypes = []
     L.rw_kernel_launches.restype = ctypes.c_ulonglong
     for name in EXPORTS:
@@ -146,6 +156,19 @@ def _ptr(a, writable=False):
 def kernel_launches():
     """Kernels launched by the library so far in this process."""
     return int(load().rw_kernel_launches())
+
+
+def profile(enable):
+    """Start (True, clearing old records) or stop the kernel profiler."""
+    _check(load().rw_profile(1 if enable else 0))
+
+
+def profile_read():
+    """Per kernel class: launches, summed CUDA-event ms, algorithmic flops, bytes."""
+    arr = (KernelStat * len(KCLASSES))()
+    _check(load().rw_profile_read(arr, len(KCLASSES)))
+    return {name: {"launches": s.launches, "ms": s.ms, "flops": s.flops, "bytes": s.bytes}
+            for name, s in zip(KCLASSES, arr)}
 
 
 def default_opts(**kw):
