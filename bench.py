@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="direct", choices=["direct", "gmres", "refined"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refine-probe", type=int, default=0,
+                    help="profiling driver: build the wall, run this many refinement steps, print their times")
     return ap.parse_args()
 
 
@@ -306,8 +308,26 @@ def workload_config(args):
             "mode": args.mode, "hbs_leaf": 64, "id_tol": 1e-12, "l2": "flushed (256 MB write) before each step"}
 
 
+def refine_probe(k):
+    import torch
+    from paper_2108_07205_gb300 import rwsolve, inputs
+    rwsolve.load(build_if_missing=True)
+    wall = rwsolve.Wall("channel", P_PANELS)
+    torch.cuda.synchronize()
+    for panels, levels in inputs.time_schedule(17, P_PANELS, k):
+        t0 = time.time()
+        ref = wall.refine(panels, levels)
+        torch.cuda.synchronize()
+        print(json.dumps({"level": levels[0], "refine_ms": 1e3 * (time.time() - t0), **ref.stats()}))
+        ref.close()
+    wall.close()
+
+
 def main():
     args = parse()
+    if args.refine_probe:
+        refine_probe(args.refine_probe)
+        return
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as td

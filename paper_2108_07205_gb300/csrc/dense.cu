@@ -782,7 +782,11 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
 // non-pivot candidates to piv (increasing index), pads fixed-rank requests
 // and counts the usable pivots.
 __global__ void k_id_prep(const IdProb* probs, int base, int n) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per problem: ballot-compacted append of the non-pivot
+  // candidates (increasing index) and a parallel search for the first
+  // numerically zero pivot
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (b >= n) return;
   const IdProb P = probs[base + b];
   const int nc = P.nc;
@@ -790,12 +794,21 @@ __global__ void k_id_prep(const IdProb* probs, int base, int n) {
   const double ref = P.norms[2 * nc + 2];
   const int k = max(s, min(P.min_rank, nc));
   int q = s;
-  for (int j = 0; j < nc; ++j) if (P.norms[nc + j] >= 0.0) P.piv[q++] = j;
-  int keff = s;
-  for (int i = 0; i < s; ++i)
-    if (!(fabs(P.W[i + size_t(P.piv[i]) * P.ldw]) > 1e-15 * ref)) { keff = i; break; }
-  *P.rank = k;
-  P.norms[2 * nc] = double(keff);
+  for (int j0 = 0; j0 < nc; j0 += 32) {
+    const int j = j0 + lane;
+    const bool keep = j < nc && P.norms[nc + j] >= 0.0;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) P.piv[q + __popc(m & ((1u << lane) - 1u))] = j;
+    q += __popc(m);
+  }
+  int first = s;
+  for (int i = lane; i < s; i += 32)
+    if (!(fabs(P.W[i + size_t(P.piv[i]) * P.ldw]) > 1e-15 * ref)) { first = i; break; }
+  for (int off = 16; off > 0; off >>= 1) first = min(first, __shfl_down_sync(0xffffffffu, first, off));
+  if (lane == 0) {
+    *P.rank = k;
+    P.norms[2 * nc] = double(first);
+  }
 }
 
 // T = R11^{-1} R12 for no-swap factorisations: blockIdx.y = problem,
@@ -1162,7 +1175,7 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
     }
     const int ng = int(grp[q].size());
     ProfScope pf(KC_OTHER, s);
-    k_id_prep<<<ceil_div(ng, 128), 128, 0, s>>>(dp.p, base[q], ng);
+    k_id_prep<<<ceil_div(32LL * ng, 128), 128, 0, s>>>(dp.p, base[q], ng);
     RW_CHECK_LAUNCH();
     const int rmax = 150;  // R11 in shared memory up to 150 x 150
     const int kk = std::max(maxk, 1);
