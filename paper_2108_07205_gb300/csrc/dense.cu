@@ -438,7 +438,157 @@ __global__ void __launch_bounds__(512) k_inverse(const InvProb* probs) {
       }
     __syncthreads();
   }
-  if (tid == 0 && P.flag) *P.flag = s_flag;
+  if (tid == 0 && P.flag && s_flag) atomicOr(P.flag, 1);  // flags are only ever raised
+}
+
+// Cluster Gauss-Jordan (partial row pivoting): CTA r of a CS-CTA cluster
+// owns columns [r cw, (r+1) cw), in shared memory (SM) or in place in Ainv.
+// Per pivot column c: the owner finds the pivot row and publishes it;
+// cluster barrier; every CTA swaps the two rows in its columns; the owner
+// publishes the multiplier column and 1/pivot; cluster barrier; every CTA
+// copies them through distributed shared memory and eliminates its columns.
+// The row interchanges become a column permutation applied on write-back
+// (through the work buffer W).
+template <bool SM>
+__global__ void __launch_bounds__(256) k_inverse_cluster(const InvProb* probs, int base, int CS) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = int(cluster.block_rank());
+  const InvProb P = probs[base + blockIdx.x / CS];
+  const int n = P.n, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int cw = (n + CS - 1) / CS;
+  const int c0 = crank * cw, c1 = min(n, c0 + cw), ncl = max(0, c1 - c0);
+  extern __shared__ double smem[];
+  double* colc = smem;                       // n: published multipliers (owner) / local copy
+  double* mine = colc + n;                   // n: local copy of the multipliers
+  int* ipiv = reinterpret_cast<int*>(mine + n);  // n
+  double* Ml = reinterpret_cast<double*>(ipiv + ((n + 1) & ~1));  // n x cw (SM)
+  double* M;
+  int ld;
+  if (SM) { M = Ml; ld = n; } else { M = P.Ainv + size_t(c0) * P.ldinv; ld = P.ldinv; }
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  __shared__ double pub_val, pub_invp;
+  __shared__ int pub_p, g_p, s_flag;
+  if (tid == 0) s_flag = 0;
+  // load my columns, max |A| over my columns
+  double amax = 0.0;
+  for (int j = warp; j < ncl; j += nw)
+    for (int i = lane; i < n; i += 32) {
+      const double v = P.A[i + size_t(c0 + j) * P.lda];
+      M[i + size_t(j) * ld] = v;
+      amax = fmax(amax, fabs(v));
+    }
+  int dummy;
+  amax = block_reduce_max_abs_arg(amax, 0, &dummy, sval, sidx);
+  if (tid == 0) pub_val = amax;
+  cluster.sync();
+  if (tid == 0) {
+    double a = 0.0;
+    for (int r = 0; r < CS; ++r) a = fmax(a, *cluster.map_shared_rank(&pub_val, r));
+    sval[31] = a;
+  }
+  __syncthreads();
+  const double tiny = 1e-14 * sval[31];
+  cluster.sync();  // pub_val is reused below
+  for (int c = 0; c < n; ++c) {
+    const int owner = c / cw;
+    if (crank == owner) {
+      const int jl = c - c0;
+      double v = -1.0;
+      int idx = 0x7fffffff;
+      for (int r = c + tid; r < n; r += nt) {
+        const double a = fabs(M[r + size_t(jl) * ld]);
+        if (a > v) { v = a; idx = r; }
+      }
+      int p;
+      const double pv = block_reduce_max_abs_arg(v, idx, &p, sval, sidx);
+      if (tid == 0) { pub_p = p; pub_val = pv; }
+    }
+    cluster.sync();
+    if (tid == 0) {
+      g_p = *cluster.map_shared_rank(&pub_p, owner);
+      const double pv = *cluster.map_shared_rank(&pub_val, owner);
+      if (!(pv > tiny)) s_flag = 1;
+      ipiv[c] = g_p;
+    }
+    __syncthreads();
+    const int p = g_p;
+    if (p != c)
+      for (int j = tid; j < ncl; j += nt) {
+        double* mj = M + size_t(j) * ld;
+        const double t = mj[c];
+        mj[c] = mj[p];
+        mj[p] = t;
+      }
+    __syncthreads();
+    if (crank == owner) {
+      const int jl = c - c0;
+      const double* mc = M + size_t(jl) * ld;
+      for (int r = tid; r < n; r += nt) colc[r] = (r == c) ? 0.0 : mc[r];
+      if (tid == 0) pub_invp = 1.0 / mc[c];
+    }
+    cluster.sync();
+    {
+      const double* rc = cluster.map_shared_rank(colc, owner);
+      for (int r = tid; r < n; r += nt) mine[r] = rc[r];
+    }
+    const double invp = *cluster.map_shared_rank(&pub_invp, owner);
+    __syncthreads();
+    for (int j = warp; j < ncl; j += nw) {
+      double* mj = M + size_t(j) * ld;
+      if (c0 + j == c) {
+        for (int r = lane; r < n; r += 32) mj[r] = (r == c) ? invp : -mine[r] * invp;
+      } else {
+        const double pj = mj[c] * invp;
+        if (pj != 0.0) {
+          for (int r0 = 0; r0 < n; r0 += 256) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int r = r0 + lane + 32 * u;
+              v[u] = (r < n) ? mj[r] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int r = r0 + lane + 32 * u;
+              if (r < n) mj[r] = (r == c) ? pj : v[u] - mine[r] * pj;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0 && pj == 0.0) mj[c] = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  // column permutation from the row interchanges (last first); the barrier
+  // keeps colc alive until every CTA has copied the last multipliers
+  cluster.sync();
+  int* perm = ipiv;
+  if (tid == 0) {
+    // sigma[j]: original column that ends up at position j
+    // computed in place over a temporary in colc's memory (as ints)
+    int* sigma = reinterpret_cast<int*>(colc);
+    for (int j = 0; j < n; ++j) sigma[j] = j;
+    for (int c = n - 1; c >= 0; --c) {
+      const int q = perm[c];
+      if (q != c) { const int t = sigma[c]; sigma[c] = sigma[q]; sigma[q] = t; }
+    }
+  }
+  // write my columns to the work buffer (W, ld n), then gather by sigma
+  for (int j = warp; j < ncl; j += nw)
+    for (int i = lane; i < n; i += 32) P.W[i + size_t(c0 + j) * n] = M[i + size_t(j) * ld];
+  __threadfence();
+  cluster.sync();
+  {
+    const int* sigma = reinterpret_cast<const int*>(colc);
+    for (int j = warp; j < ncl; j += nw) {
+      const int src = sigma[c0 + j];
+      for (int i = lane; i < n; i += 32) P.Ainv[i + size_t(c0 + j) * P.ldinv] = P.W[i + size_t(src) * n];
+    }
+  }
+  if (tid == 0 && s_flag && P.flag) atomicOr(P.flag, 1);
+  cluster.sync();
 }
 
 // ------------------------------------------------------------------ ID
@@ -905,6 +1055,10 @@ static void init_smem_limits() {
     e[2] = cudaFuncSetAttribute(k_id_tsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     e[3] = cudaFuncSetAttribute(k_cpqr_id<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     for (cudaError_t x : e) if (x != cudaSuccess) err = x;
+    cudaError_t f0 = cudaFuncSetAttribute(k_inverse_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaError_t f1 = cudaFuncSetAttribute(k_inverse_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (f0 != cudaSuccess) err = f0;
+    if (f1 != cudaSuccess) err = f1;
   });
   if (err != cudaSuccess) throw Error(RW_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
 }
@@ -1102,19 +1256,61 @@ void matvec<float>(const std::vector<GemvProb<float>>& probs, int nrhs, cudaStre
 }
 
 void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
-  std::vector<InvProb> ps;
-  int maxn = 0;
-  for (auto& p : probs) if (p.n > 0) { ps.push_back(p); maxn = std::max(maxn, p.n); }
-  if (ps.empty()) return;
-  auto dp = to_device_tmp(ps, s);
-  size_t smem = size_t(maxn) * sizeof(double);
-  require(smem <= 200 * 1024, "batched_inverse: matrix too large");
+  // small matrices: one CTA each; larger: a cluster of up to 8 CTAs with the
+  // columns in shared memory when they fit, else in place in global memory
+  std::vector<InvProb> small, cl_sm[4], cl_gl[4];
+  const int sizes[4] = {1, 2, 4, 8};
+  const size_t cap = 200 * 1024;
+  for (const auto& p : probs) {
+    if (p.n <= 0) continue;
+    if (p.n < 48) { small.push_back(p); continue; }
+    const int q = p.n >= 192 ? 3 : p.n >= 96 ? 2 : 1;
+    const int CS = sizes[q];
+    const int cw = (p.n + CS - 1) / CS;
+    const size_t need = (2 * size_t(p.n) + size_t(p.n) * cw) * sizeof(double) + size_t(p.n + 2) * sizeof(int);
+    if (need <= cap) cl_sm[q].push_back(p); else cl_gl[q].push_back(p);
+  }
   init_smem_limits();
-  double fl = 0.0;
-  for (auto& p : ps) fl += 2.0 * double(p.n) * p.n * p.n;
-  ProfScope prof(KC_INVERSE, s, fl, 0.0);
-  k_inverse<<<int(ps.size()), 512, smem, s>>>(dp.p);
-  RW_CHECK_LAUNCH();
+  if (!small.empty()) {
+    auto dp = to_device_tmp(small, s);
+    int maxn = 0;
+    double fl = 0.0;
+    for (auto& p : small) { maxn = std::max(maxn, p.n); fl += 2.0 * double(p.n) * p.n * p.n; }
+    ProfScope prof(KC_INVERSE, s, fl, 0.0);
+    k_inverse<<<int(small.size()), 512, size_t(maxn) * sizeof(double), s>>>(dp.p);
+    RW_CHECK_LAUNCH();
+  }
+  for (int sm = 0; sm < 2; ++sm)
+    for (int q = 0; q < 4; ++q) {
+      auto& g = sm ? cl_sm[q] : cl_gl[q];
+      if (g.empty()) continue;
+      const int CS = sizes[q];
+      size_t smem = 0;
+      double fl = 0.0;
+      for (auto& p : g) {
+        const int cw = (p.n + CS - 1) / CS;
+        smem = std::max(smem, (2 * size_t(p.n) + (sm ? size_t(p.n) * cw : 0)) * sizeof(double) +
+                                  size_t(p.n + 2) * sizeof(int));
+        fl += 2.0 * double(p.n) * p.n * p.n;
+      }
+      auto dp = to_device_tmp(g, s);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(g.size() * CS));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CS;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      ProfScope prof(KC_INVERSE, s, fl, 0.0);
+      if (sm) RW_CUDA(cudaLaunchKernelEx(&cfg, k_inverse_cluster<true>, (const InvProb*)dp.p, 0, CS));
+      else RW_CUDA(cudaLaunchKernelEx(&cfg, k_inverse_cluster<false>, (const InvProb*)dp.p, 0, CS));
+      RW_CHECK_LAUNCH();
+    }
 }
 
 void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {

@@ -708,7 +708,84 @@ void Hbs::sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const {
   }
 }
 
-void Hbs::apply_inverse(const double* b, double* x, int nrhs, cudaStream_t s) const { sweep_inverse<double>(b, x, nrhs, s); }
+void Hbs::apply_inverse(const double* b, double* x, int nrhs, cudaStream_t s) const {
+  if (nrhs <= 8) apply_inverse_program(b, x, nrhs, s);
+  else sweep_inverse<double>(b, x, nrhs, s);
+}
+
+int Hbs::emit_inverse_sweep(Program& P, int p0, int in_b, long long in_o, int in_ld, int out_b, long long out_o,
+                            int out_ld) const {
+  constexpr int WS = 2;  // workspace base
+  if (L == 0) {
+    P.gemv(p0, lev[0].G.p, 2 * N, 2 * N, 2 * N, in_b, in_o, in_ld, out_b, out_o, out_ld, 1.0, 0.0);
+    return p0 + 1;
+  }
+  std::vector<long long> uh(L + 1), qh(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    uh[l] = P.ws_alloc(lev[l].koff.back());
+    qh[l] = P.ws_alloc(lev[l].koff.back());
+  }
+  int p = p0;
+  {  // leaves: u^ = F* u, x = G u
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      P.gemv(p, LV.F.p + LV.oF[t], nd.k, n, nd.k, in_b, in_o + 2 * nd.lo, in_ld, WS, uh[l] + LV.koff[t], -1, 1.0, 0.0);
+      P.gemv(p, LV.G.p + LV.oG[t], n, n, n, in_b, in_o + 2 * nd.lo, in_ld, out_b, out_o + 2 * nd.lo, out_ld, 1.0, 0.0);
+    }
+    ++p;
+  }
+  for (int l = L - 1; l >= 1; --l, ++p) {
+    const int h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const long long in = uh[l + 1] + LC.koff[2 * t];
+      P.gemv(p, LV.F.p + LV.oF[t], nd.k, nd.m, nd.k, WS, in, -1, WS, uh[l] + LV.koff[t], -1, 1.0, 0.0);
+      P.gemv(p, LV.G.p + LV.oG[t], nd.m, nd.m, nd.m, WS, in, -1, WS, qh[l + 1] + LC.koff[2 * t], -1, 1.0, 0.0);
+    }
+  }
+  {
+    const int K1 = lev[1].koff.back();
+    P.gemv(p++, lev[0].G.p, K1, K1, K1, WS, uh[1], -1, WS, qh[1], -1, 1.0, 0.0);
+  }
+  for (int l = 1; l <= L - 1; ++l, ++p) {
+    const int h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      P.gemv(p, LV.E.p + LV.oE[t], nd.m, nd.k, nd.m, WS, qh[l] + LV.koff[t], -1, WS, qh[l + 1] + LC.koff[2 * t], -1,
+             1.0, 1.0);
+    }
+  }
+  {
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      P.gemv(p, LV.E.p + LV.oE[t], n, nd.k, n, WS, qh[l] + LV.koff[t], -1, out_b, out_o + 2 * nd.lo, out_ld, 1.0, 1.0);
+    }
+    ++p;
+  }
+  return p;
+}
+
+void Hbs::apply_inverse_program(const double* b, double* x, int nrhs, cudaStream_t s) const {
+  if (!inv_prog_built) {
+    emit_inverse_sweep(inv_prog, 0, 0, 0, 2 * N, 1, 0, 2 * N);
+    inv_prog.finalize(s);
+    inv_prog_built = true;
+  }
+  const size_t need = size_t(std::max<long long>(inv_prog.ws_per_rhs(), 1)) * nrhs;
+  if (prog_ws.n < need) prog_ws.alloc(need);
+  double* bases[kMaxBases] = {const_cast<double*>(b), x, prog_ws.p, nullptr};
+  inv_prog.run(bases, nrhs, s);
+}
 void Hbs::apply_inverse_f32(const float* b, float* x, int nrhs, cudaStream_t s) const {
   require(has_fp32, "HBS: FP32 copies not built");
   sweep_inverse<float>(b, x, nrhs, s);

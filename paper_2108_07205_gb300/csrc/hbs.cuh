@@ -6,6 +6,7 @@
 #pragma once
 #include "dense.cuh"
 #include "eval.cuh"
+#include "program.cuh"
 
 namespace rw {
 
@@ -104,6 +105,16 @@ class Hbs {
   void apply_forward(const double* x, double* y, int nrhs, cudaStream_t s) const;
   void make_fp32(cudaStream_t s);
   bool has_fp32 = false;
+  // Add the inverse sweep x = A^{-1} b to a program, starting at phase p0
+  // (input and output addressed as program vectors); returns the next phase.
+  int emit_inverse_sweep(Program& P, int p0, int in_b, long long in_o, int in_ld, int out_b, long long out_o,
+                         int out_ld) const;
+  // single-launch inverse sweep on a program built on first use (bases:
+  // b, x, workspace); same result as apply_inverse
+  void apply_inverse_program(const double* b, double* x, int nrhs, cudaStream_t s) const;
+  mutable Program inv_prog;
+  mutable bool inv_prog_built = false;
+  mutable DBuf<double> prog_ws;
 
  private:
   template <class T>

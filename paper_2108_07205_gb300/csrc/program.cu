@@ -1,0 +1,273 @@
+// Persistent cooperative executor of GEMV programs (see program.cuh).
+#include "program.cuh"
+#include <algorithm>
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+namespace rw {
+
+namespace {
+
+constexpr int TR = 32;        // GEMV rows per tile (256 threads = 32 rows x 8 column lanes)
+constexpr int TE = 256;       // copy / fill / reduce entries per tile
+constexpr int SPLIT_N = 4096; // GEMVs wider than this with few row tiles are split
+
+struct Bases { double* p[kMaxBases]; };
+
+__device__ __forceinline__ int tiles_of(const GOp& o) {
+  return o.kind == OP_GEMV ? (o.m + TR - 1) / TR : (o.m + TE - 1) / TE;
+}
+
+template <int NR>
+__device__ void do_gemv(const GOp& o, int tile, const Bases& B, int r0, double (*xs)[NR], double (*red)[TR][NR]) {
+  // 256 threads = TR (32) rows x 8 column lanes; each lane keeps 4
+  // independent accumulator chains per right-hand side
+  const int lr = threadIdx.x & (TR - 1), lc = threadIdx.x / TR;
+  const int row = tile * TR + lr;
+  const double* x = B.p[o.xb] + o.xo + size_t(r0) * o.ldx;
+  double* y = B.p[o.yb] + o.yo + size_t(r0) * o.ldy;
+  // UNR independent chains per right-hand side (UNR * NR = 16 accumulators)
+  constexpr int UNR = NR == 1 ? 16 : NR == 2 ? 8 : NR <= 4 ? 4 : 2;
+  double acc[UNR][NR];
+#pragma unroll
+  for (int u = 0; u < UNR; ++u)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[u][r] = 0.0;
+  for (int cb = 0; cb < o.n; cb += 256) {
+    const int ncur = min(256, o.n - cb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ncur; e += 256)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) xs[e][r] = x[cb + e + size_t(r) * o.ldx];
+    __syncthreads();
+    if (row < o.m) {
+      const double* a = o.A + row + size_t(cb) * o.lda;
+      int j = lc;
+      for (; j + 8 * (UNR - 1) < ncur; j += 8 * UNR) {
+        double v[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) v[u] = a[size_t(j + 8 * u) * o.lda];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) acc[u][r] = fma(v[u], xs[j + 8 * u][r], acc[u][r]);
+      }
+      for (; j < ncur; j += 8) {
+        const double v = a[size_t(j) * o.lda];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[0][r] = fma(v, xs[j][r], acc[0][r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) s += acc[u][r];
+    red[lc][lr][r] = s;
+  }
+  __syncthreads();
+  if (lc == 0 && row < o.m) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += red[q][lr][r];
+      double* yp = y + row + size_t(r) * o.ldy;
+      double v = o.alpha * s;
+      if (o.beta != 0.0) v += o.beta * *yp;
+      *yp = v;
+    }
+  }
+  __syncthreads();
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256, 2) k_program(const GOp* ops, const int* tile0, const int* phase, int nphases,
+                                                 Bases B, int r0) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double xs[256][NR];
+  __shared__ double red[8][TR][NR];
+  for (int ph = 0; ph < nphases; ++ph) {
+    const int o0 = phase[ph], o1 = phase[ph + 1];
+    const int t0 = tile0[o0], t1 = tile0[o1];
+    for (int t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+      int lo = o0, hi = o1;  // op with tile0[op] <= t < tile0[op + 1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tile0[mid] <= t) lo = mid; else hi = mid;
+      }
+      const GOp& o = ops[lo];
+      const int tile = t - tile0[lo];
+      if (o.kind == OP_GEMV) {
+        do_gemv<NR>(o, tile, B, r0, xs, red);
+      } else {
+        const int i = tile * TE + threadIdx.x;
+        if (i < o.m) {
+          const double* x = (o.kind == OP_ZERO) ? nullptr : B.p[o.xb] + o.xo + size_t(r0) * o.ldx;
+          double* y = B.p[o.yb] + o.yo + size_t(r0) * o.ldy;
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            if (o.kind == OP_COPY) {
+              y[(o.iy ? o.iy[i] : i) + size_t(r) * o.ldy] = x[(o.ix ? o.ix[i] : i) + size_t(r) * o.ldx];
+            } else if (o.kind == OP_ZERO) {
+              y[(o.iy ? o.iy[i] : i) + size_t(r) * o.ldy] = 0.0;
+            } else {  // REDUCE: parts are m apart in x
+              double s = 0.0;
+              for (int q = 0; q < o.n; ++q) s += x[i + size_t(q) * o.m + size_t(r) * o.ldx];
+              double* yp = y + i + size_t(r) * o.ldy;
+              double v = o.alpha * s;
+              if (o.beta != 0.0) v += o.beta * *yp;
+              *yp = v;
+            }
+          }
+        }
+      }
+    }
+    grid.sync();
+  }
+}
+
+template <int NR>
+const void* kernel_ptr() { return reinterpret_cast<const void*>(&k_program<NR>); }
+
+int host_tiles(const GOp& o) { return o.kind == OP_GEMV ? (o.m + TR - 1) / TR : (o.m + TE - 1) / TE; }
+
+}  // namespace
+
+static std::vector<GOp>& phase_at(std::vector<std::vector<GOp>>& ph, int p) {
+  if (int(ph.size()) <= p) ph.resize(p + 1);
+  return ph[p];
+}
+
+void Program::gemv(int p, const double* A, int m, int n, int lda, int xb, long long xo, int ldx, int yb,
+                   long long yo, int ldy, double alpha, double beta) {
+  if (m <= 0) return;
+  GOp o{};
+  o.kind = OP_GEMV;
+  o.m = m; o.n = n; o.A = A; o.lda = lda;
+  o.xb = xb; o.xo = xo; o.ldx = ldx; o.yb = yb; o.yo = yo; o.ldy = ldy;
+  o.alpha = alpha; o.beta = beta;
+  phase_at(phases_, p).push_back(o);
+  mat_elems_ += (long long)m * n;
+}
+
+void Program::copy(int p, int n, int xb, long long xo, int ldx, const int* ix, int yb, long long yo, int ldy,
+                   const int* iy) {
+  if (n <= 0) return;
+  GOp o{};
+  o.kind = OP_COPY;
+  o.m = n; o.xb = xb; o.xo = xo; o.ldx = ldx; o.ix = ix; o.yb = yb; o.yo = yo; o.ldy = ldy; o.iy = iy;
+  phase_at(phases_, p).push_back(o);
+}
+
+void Program::zero(int p, int n, int yb, long long yo, int ldy, const int* iy) {
+  if (n <= 0) return;
+  GOp o{};
+  o.kind = OP_ZERO;
+  o.m = n; o.yb = yb; o.yo = yo; o.ldy = ldy; o.iy = iy;
+  phase_at(phases_, p).push_back(o);
+}
+
+long long Program::ws_alloc(long long elems) {
+  const long long o = ws_;
+  ws_ += (elems + 31) / 32 * 32;
+  return o;
+}
+
+void Program::finalize(cudaStream_t s) {
+  // split wide GEMVs (few row tiles, many columns) into column-chunk partial
+  // products in the workspace and a reduce op in an extra phase
+  std::vector<std::vector<GOp>> out;
+  const int wsb = 2;  // workspace base index (by convention)
+  for (auto& ph : phases_) {
+    std::vector<GOp> cur, red;
+    for (const GOp& o : ph) {
+      if (o.kind == OP_GEMV && o.n > SPLIT_N && host_tiles(o) < 38) {
+        const int parts = (o.n + SPLIT_N - 1) / SPLIT_N;
+        const long long pw = ws_alloc((long long)parts * o.m);
+        for (int q = 0; q < parts; ++q) {
+          GOp g = o;
+          const int c0 = q * SPLIT_N, c1 = std::min(o.n, c0 + SPLIT_N);
+          g.A = o.A + size_t(c0) * o.lda;
+          g.n = c1 - c0;
+          g.xo = o.xo + c0;
+          g.yb = wsb; g.yo = pw + (long long)q * o.m; g.ldy = -1;  // ld patched at run (workspace ld)
+          g.alpha = 1.0; g.beta = 0.0;
+          cur.push_back(g);
+        }
+        GOp r{};
+        r.kind = OP_REDUCE;
+        r.m = o.m; r.n = parts;
+        r.xb = wsb; r.xo = pw; r.ldx = -1;
+        r.yb = o.yb; r.yo = o.yo; r.ldy = o.ldy;
+        r.alpha = o.alpha; r.beta = o.beta;
+        red.push_back(r);
+      } else {
+        cur.push_back(o);
+      }
+    }
+    out.push_back(cur);
+    if (!red.empty()) out.push_back(red);
+  }
+  // workspace leading dimension: the per-RHS block size
+  for (auto& ph : out)
+    for (GOp& o : ph) {
+      if (o.ldx == -1) o.ldx = int(ws_);
+      if (o.ldy == -1) o.ldy = int(ws_);
+    }
+  std::vector<GOp> flat;
+  std::vector<int> phase(1, 0), tile0(1, 0);
+  int maxt = 1;
+  for (auto& ph : out) {
+    int tph = 0;
+    for (const GOp& o : ph) {
+      flat.push_back(o);
+      tph += host_tiles(o);
+      tile0.push_back(tile0.back() + host_tiles(o));
+    }
+    phase.push_back(int(flat.size()));
+    maxt = std::max(maxt, tph);
+  }
+  nph_ = int(out.size());
+  d_ops_ = to_device(flat, s);
+  d_tile_ = to_device(tile0, s);
+  d_phase_ = to_device(phase, s);
+  RW_CUDA(cudaStreamSynchronize(s));
+  int dev = 0, nsm = 0, per = 0;
+  RW_CUDA(cudaGetDevice(&dev));
+  RW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  RW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_program<8>, 256, 0));
+  grid_ = std::max(1, std::min(maxt, nsm * std::max(per, 1)));
+}
+
+void Program::run(double* const* bases, int nrhs, cudaStream_t s) const {
+  if (nph_ == 0) return;
+  Bases B;
+  for (int i = 0; i < kMaxBases; ++i) B.p[i] = bases[i];
+  const GOp* ops = d_ops_.p;
+  const int* t0 = d_tile_.p;
+  const int* ph = d_phase_.p;
+  int nphases = nph_;
+  for (int r0 = 0; r0 < nrhs; r0 += 8) {
+    const int nr = std::min(8, nrhs - r0);
+    void* args[] = {(void*)&ops, (void*)&t0, (void*)&ph, (void*)&nphases, (void*)&B, (void*)&r0};
+    const void* fn = nullptr;
+    switch (nr) {
+      case 1: fn = kernel_ptr<1>(); break;
+      case 2: fn = kernel_ptr<2>(); break;
+      case 3: fn = kernel_ptr<3>(); break;
+      case 4: fn = kernel_ptr<4>(); break;
+      case 5: fn = kernel_ptr<5>(); break;
+      case 6: fn = kernel_ptr<6>(); break;
+      case 7: fn = kernel_ptr<7>(); break;
+      default: fn = kernel_ptr<8>(); break;
+    }
+    ProfScope prof(KC_GEMV, s, 0.0, 0.0);
+    RW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid_), dim3(256), args, 0, s));
+    RW_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace rw

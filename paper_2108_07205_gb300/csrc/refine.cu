@@ -254,6 +254,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
   }
   tr.mark("W, W^-1");
+  build_solve_program(s);
   bytes = Lo.bytes() + Lp.bytes() + Rkc.bytes() + Rkp.bytes() + Rpk.bytes() + Xo.bytes() + Xp.bytes() + Winv.bytes() +
           hpp.bytes + pn.buf.bytes() + nn.buf.bytes();
 }
@@ -277,7 +278,43 @@ void Refinement::woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t
   matvec<double>(p2, nrhs, s);
 }
 
+void Refinement::build_solve_program(cudaStream_t s) {
+  // bases: 0 = g (2Nn x nrhs), 1 = tau (2Nn x nrhs), 2 = workspace (ld -1 = per-RHS block)
+  Program& P = solve_prog;
+  const int WS = 2, ldn = 2 * Nn;
+  const long long go = P.ws_alloc(2LL * No), gp = P.ws_alloc(2LL * Np);
+  const long long yo = P.ws_alloc(2LL * No), yp = P.ws_alloc(2LL * Np);
+  P.zero(0, 2 * No, WS, go, -1, nullptr);
+  P.copy(0, nkp, 0, 0, ldn, n_from_p.p, WS, gp, -1, n_to_p.p);
+  P.copy(1, nko, 0, 0, ldn, n_from_o.p, WS, go, -1, n_to_o.p);
+  const int pa = wall->hbs.emit_inverse_sweep(P, 2, WS, go, -1, WS, yo, -1);
+  const int pb = hpp.emit_inverse_sweep(P, 2, WS, gp, -1, WS, yp, -1);
+  int p = std::max(pa, pb);
+  if (k > 0) {
+    const long long yc = P.ws_alloc(2LL * Nc), r = P.ws_alloc(k), z = P.ws_alloc(k);
+    P.copy(p++, 2 * Nc, WS, yo, -1, dc.p, WS, yc, -1, nullptr);
+    if (kk) P.gemv(p, Rkc.p, kk, 2 * Nc, kk, WS, yc, -1, WS, r, -1, 1.0, 0.0);
+    if (kpk) P.gemv(p, Rpk.p, kpk, 2 * No, kpk, WS, yo, -1, WS, r + kk, -1, 1.0, 0.0);
+    ++p;
+    if (kk && Np) P.gemv(p++, Rkp.p, kk, 2 * Np, kk, WS, yp, -1, WS, r, -1, 1.0, 1.0);
+    P.gemv(p++, Winv.p, k, k, k, WS, r, -1, WS, z, -1, 1.0, 0.0);
+    if (kk) P.gemv(p, Xo.p, 2 * No, kk, 2 * No, WS, z, -1, WS, yo, -1, -1.0, 1.0);
+    if (kpk) P.gemv(p, Xp.p, 2 * Np, kpk, 2 * Np, WS, z + kk, -1, WS, yp, -1, -1.0, 1.0);
+    ++p;
+  }
+  P.copy(p, nko, WS, yo, -1, n_to_o.p, 1, 0, ldn, n_from_o.p);
+  P.copy(p, nkp, WS, yp, -1, n_to_p.p, 1, 0, ldn, n_from_p.p);
+  P.finalize(s);
+}
+
 void Refinement::solve_direct(const double* g, double* tau, int nrhs, cudaStream_t s) const {
+  const size_t need = size_t(std::max<long long>(solve_prog.ws_per_rhs(), 1)) * nrhs;
+  if (solve_ws.n < need) solve_ws.alloc(need);
+  double* bases[kMaxBases] = {const_cast<double*>(g), tau, solve_ws.p, nullptr};
+  solve_prog.run(bases, nrhs, s);
+}
+
+void Refinement::solve_direct_levels(const double* g, double* tau, int nrhs, cudaStream_t s) const {
   TBuf<double> go(size_t(2) * No * nrhs, s), gp(size_t(2) * Np * nrhs, s);
   TBuf<double> yo(size_t(2) * No * nrhs, s), yp(size_t(2) * Np * nrhs, s);
   fill_zero(go.p, go.n, s);

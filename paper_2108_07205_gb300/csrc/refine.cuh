@@ -31,9 +31,16 @@ struct Refinement {
   int nko = 0, nkp = 0;
   size_t bytes = 0;
 
+  // The direct solve as one persistent program (bases: g, tau, workspace).
+  Program solve_prog;
+  mutable DBuf<double> solve_ws;
+  void build_solve_program(cudaStream_t s);
   void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s);
-  // Direct solve, device buffers: g, tau (2Nn x nrhs).
+  // Direct solve, device buffers: g, tau (2Nn x nrhs): one persistent launch
+  // per 8 right-hand sides.  solve_direct_levels is the same computation as
+  // a sequence of per-level launches.
   void solve_direct(const double* g, double* tau, int nrhs, cudaStream_t s) const;
+  void solve_direct_levels(const double* g, double* tau, int nrhs, cudaStream_t s) const;
   // Direct solve followed by `steps` rounds of iterative refinement against
   // the exact refined operator (on-the-fly N-body evaluation of A_nn).
   void solve_refined(const double* g, double* tau, int nrhs, int steps, cudaStream_t s) const;
