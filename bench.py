@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 P_PANELS = 1024
 TARGETS = 16
 N_SRC = 5
+NRHS = 1
 
 
 def parse():
@@ -42,6 +43,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="direct", choices=["direct", "gmres", "refined"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=48, help="serving workload: number of requests per phase")
+    ap.add_argument("--workload", default="channel1024", choices=["channel1024", "mixed2048", "serving"],
+                    help="channel1024: 1 RHS per step (default); mixed2048: 2048-panel channel, 64 RHS per "
+                         "step from Stokeslet pairs")
     ap.add_argument("--refine-probe", type=int, default=0,
                     help="profiling driver: build the wall, run this many refinement steps, print their times")
     return ap.parse_args()
@@ -96,7 +101,10 @@ class Clocks:
 
 def stokeslet_inputs(step, rank):
     from paper_2108_07205_gb300 import inputs
-    sx, sy, f = inputs.stokeslets_channel(1000 * rank + step, nrhs=1, n=N_SRC)
+    if NRHS == 1:
+        sx, sy, f = inputs.stokeslets_channel(1000 * rank + step, nrhs=1, n=N_SRC)
+    else:
+        sx, sy, f = inputs.stokeslet_pairs_channel(1000 * rank + step, NRHS)
     src = np.ascontiguousarray(np.stack([sx, sy], 1))
     fd = np.ascontiguousarray(np.transpose(f, (2, 0, 1)))
     tx, ty = inputs.targets_channel(7 + step, TARGETS)
@@ -137,18 +145,18 @@ def run_ours(args, rank, world, local):
         n_n = ref.stats()["n_n"]
         if host:
             src, fd, tg = host_in[s]
-            g = torch.empty(2 * n_n, dtype=torch.float64, device=dev)
-            ref.stokeslet_data(src.numpy(), fd.numpy(), g, stream=stream)
-            tau = np.empty(2 * n_n)
-            u = np.empty(2 * TARGETS)
-            info = ref.solve(g, tau, targets=tg.numpy(), u=u, mode=mode, stream=stream)
+            g = torch.empty((NRHS, 2 * n_n), dtype=torch.float64, device=dev)
+            ref.stokeslet_data(src.numpy(), fd.numpy(), g, nrhs=NRHS, stream=stream)
+            tau = np.empty((NRHS, 2 * n_n))
+            u = np.empty((NRHS, 2 * TARGETS))
+            info = ref.solve(g, tau, nrhs=NRHS, targets=tg.numpy(), u=u, mode=mode, stream=stream)
         else:
             src, fd, tg = dev_in[s]
-            g = torch.empty(2 * n_n, dtype=torch.float64, device=dev)
-            ref.stokeslet_data(src, fd, g, stream=stream)
+            g = torch.empty((NRHS, 2 * n_n), dtype=torch.float64, device=dev)
+            ref.stokeslet_data(src, fd, g, nrhs=NRHS, stream=stream)
             tau = torch.empty_like(g)
-            u = torch.empty(2 * TARGETS, dtype=torch.float64, device=dev)
-            info = ref.solve(g, tau, targets=tg, u=u, mode=mode, stream=stream)
+            u = torch.empty((NRHS, 2 * TARGETS), dtype=torch.float64, device=dev)
+            info = ref.solve(g, tau, nrhs=NRHS, targets=tg, u=u, mode=mode, stream=stream)
         st = ref.stats()
         ref.close()
         return st, info
@@ -206,18 +214,18 @@ def run_ours(args, rank, world, local):
     ref = wall.refine(panels, levels, stream=stream)
     n_n = ref.stats()["n_n"]
     src, fd, tg = dev_in[0]
-    g = torch.empty(2 * n_n, dtype=torch.float64, device=dev)
-    ref.stokeslet_data(src, fd, g, stream=stream)
+    g = torch.empty((NRHS, 2 * n_n), dtype=torch.float64, device=dev)
+    ref.stokeslet_data(src, fd, g, nrhs=NRHS, stream=stream)
     tau = torch.empty_like(g)
     for _ in range(5):
-        ref.solve(g, tau, mode=mode, stream=stream)
+        ref.solve(g, tau, nrhs=NRHS, mode=mode, stream=stream)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     nsolve = 50
     e0.record(stream)
     for _ in range(nsolve):
-        ref.solve(g, tau, mode=mode, stream=stream)
+        ref.solve(g, tau, nrhs=NRHS, mode=mode, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     out["solve_ms"] = e0.elapsed_time(e1) / nsolve
@@ -303,6 +311,10 @@ def run_reference(args, rank, world):
 
 
 def workload_config(args):
+    if args.workload == "mixed2048":
+        return {"workload": "channel 2048 panels x 16 nodes (65536 unknowns), moving 8-panel window refined "
+                            "2-5 levels, refine + data + solve + velocity per step, 64 RHS from Stokeslet pairs",
+                "mode": args.mode, "hbs_leaf": 64, "id_tol": 1e-12, "l2": "flushed (256 MB write) before each step"}
     return {"workload": "channel 1024 panels x 16 nodes (32768 unknowns), moving 8-panel window refined "
                         "2-5 levels, refine + data + solve + velocity per step, 1 RHS",
             "mode": args.mode, "hbs_leaf": 64, "id_tol": 1e-12, "l2": "flushed (256 MB write) before each step"}
@@ -323,10 +335,83 @@ def refine_probe(k):
     wall.close()
 
 
+def run_serving(args):
+    """Serving workload: resident walls (channel 512/1024/2048 panels, star 1024
+    panels); each request refines 1-64 contiguous panels by 2-6 levels and
+    carries 1-32 right-hand sides from exterior point forces.  Closed loop
+    (all requests at once) gives the saturation rate; an open loop with
+    Poisson arrivals at 0.8 x that rate gives p50/p99 latency."""
+    import torch
+    from paper_2108_07205_gb300 import rwsolve, inputs
+    rwsolve.load(build_if_missing=True)
+    walls = [rwsolve.Wall("channel", 512), rwsolve.Wall("channel", 1024), rwsolve.Wall("channel", 2048),
+             rwsolve.Wall("star", 1024, (0.3, 5, 1.0))]
+    torch.cuda.synchronize()
+
+    def make(seed):
+        g = inputs.rng(seed)
+        w = walls[int(g.integers(0, len(walls)))]
+        m = int(g.integers(1, 65))
+        L = int(g.integers(2, 7))
+        nrhs = int(g.integers(1, 33))
+        panels, _ = inputs.refinement_window(seed, w.n_panels, m, L, L)
+        if w is walls[3]:
+            sx, sy, f = inputs.stokeslets_star(seed, nrhs=nrhs)
+            tx, ty = inputs.targets_star(seed, 16)
+        else:
+            sx, sy, f = inputs.stokeslets_channel(seed, nrhs=nrhs)
+            tx, ty = inputs.targets_channel(seed, 16)
+        return (w, panels, [L] * m, np.stack([sx, sy], 1), np.transpose(f, (2, 0, 1)).copy(), nrhs,
+                np.stack([tx, ty], 1))
+
+    sv = rwsolve.Server(n_workers=4, max_device_bytes=200 << 30)
+    warm = [sv.submit(*make(10 ** 6 + i)[:5], nrhs=1)[0] for i in range(2)]
+    for t in warm:
+        sv.wait(t)
+    reqs = [make(i) for i in range(args.requests)]
+    t0 = time.time()
+    tk = [sv.submit(w, p, l, s, f, nrhs=n, targets=tg)[0] for (w, p, l, s, f, n, tg) in reqs]
+    lat_closed = [sv.wait(t) for t in tk]
+    t_closed = time.time() - t0
+    nsolves = sum(r[5] for r in reqs)
+    sat = args.requests / t_closed
+    lam = 0.8 * sat
+    g = inputs.rng(4242)
+    gaps = g.exponential(1.0 / lam, size=args.requests)
+    reqs2 = [make(10 ** 5 + i) for i in range(args.requests)]
+    t0 = time.time()
+    tk2 = []
+    for gap, (w, p, l, s, f, n, tg) in zip(gaps, reqs2):
+        time.sleep(gap)
+        tk2.append(sv.submit(w, p, l, s, f, nrhs=n, targets=tg)[0])
+    lat_open = [sv.wait(t) for t in tk2]
+    t_open = time.time() - t0
+    nsolves2 = sum(r[5] for r in reqs2)
+    sv.close()
+    line = {"metric": "refined-wall solves/s (serving, open loop at 0.8 x saturation)",
+            "value": nsolves2 / t_open, "unit": "solves/s", "n_gpus": 1, "steps": args.requests, "warmup": 2,
+            "ms_per_step": 1e3 * t_open / args.requests, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serving: walls channel 512/1024/2048 + star 1024 panels; requests refine "
+                                   "1-64 panels by 2-6 levels with 1-32 RHS; 4 workers, 200 GB budget"},
+            "p50_ms": float(np.percentile(lat_open, 50)), "p99_ms": float(np.percentile(lat_open, 99)),
+            "saturation": {"requests_per_s": sat, "solves_per_s": nsolves / t_closed,
+                           "p50_ms": float(np.percentile(lat_closed, 50)),
+                           "p99_ms": float(np.percentile(lat_closed, 99))},
+            "arrival_rate_per_s": lam}
+    print(json.dumps(line))
+
+
 def main():
+    global P_PANELS, NRHS
     args = parse()
+    if args.workload == "mixed2048":
+        P_PANELS, NRHS = 2048, 64
     if args.refine_probe:
         refine_probe(args.refine_probe)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     rank, world, local = dist_env()
     if world > 1:
@@ -344,8 +429,8 @@ def main():
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    value = world * args.steps / (out["ms"] / 1e3)
-    e2e = world * args.steps / (out["ms_e2e"] / 1e3)
+    value = world * args.steps * NRHS / (out["ms"] / 1e3)
+    e2e = world * args.steps * NRHS / (out["ms_e2e"] / 1e3)
     # FP64 ALU peak: 152 SMs x 4 FP64 flop/clk (nominal 1.25 TFLOP/s at the
     # 2070 MHz maximum clock), evaluated at the median SM clock under load
     sm_mhz = (out["clocks"] or {}).get("sm_mhz") or 2070.0
@@ -377,11 +462,12 @@ def main():
         "dtype": "f64" if args.mode != "gmres" else "f64+f32", "data": "synthetic",
         "config": workload_config(args),
         "p50_ms": float(np.percentile(out["lat"], 50)), "p99_ms": float(np.percentile(out["lat"], 99)),
-        "solve_only_per_s": 1e3 / out["solve_ms"], "k_mean": out["k_mean"], "n_p_range": out["np_range"],
+        "solve_only_per_s": NRHS * 1e3 / out["solve_ms"], "k_mean": out["k_mean"], "n_p_range": out["np_range"],
         "hbs_build_s": out["build_s"], "gmres_iters": out["iters"] if args.mode == "gmres" else None,
         "e2e": {"value": e2e, "unit": "solves/s",
-                "h2d_bytes_per_step": 8 * (2 * N_SRC + 2 * N_SRC + 2 * TARGETS),
-                "d2h_bytes_per_step": 8 * (2 * TARGETS) + 8 * 2 * 16 * P_PANELS},
+                "h2d_bytes_per_step": 8 * (2 * N_SRC + 2 * N_SRC * NRHS + 2 * TARGETS) if NRHS == 1 else
+                8 * (4 * NRHS + 4 * NRHS * NRHS + 2 * TARGETS),
+                "d2h_bytes_per_step": 8 * NRHS * (2 * TARGETS + 2 * 16 * P_PANELS)},
         "roofline": roof,
         "kernel_time_share": share,
         "roofline_sweep": {"kernel": "HBS inverse sweep (s1, FP64, 1 RHS, L2 flushed)", "ms": out["sweep_ms"],

@@ -153,7 +153,9 @@ int rw_hbs_apply_forward(rw_hbs_t h, int nrhs, const double* x, double* y,
  * and replace panel_ids[i] by 2^levels[i] equal sub-panels; build the added
  * nodes, A_pp^{-1}, the row-ID factors Q ~= L R, X = A~^{-1} L and the LU
  * factors of W = I + R X.  panel_ids and levels are host arrays.
- * The handle borrows h, which must outlive it. */
+ * The handle borrows h, which must outlive it.  Its device memory is
+ * allocated in stream order on `stream`, which must stay valid until
+ * rw_ref_free. */
 int rw_refine_factor(rw_hbs_t h, int n_cut, const int* panel_ids,
                      const int* levels, void* stream, rw_ref_t* out);
 
@@ -196,6 +198,43 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets,
 /* Number of CUDA kernels this library has launched in this process so far
  * (diagnostics: benchmarks difference it around a timed region). */
 unsigned long long rw_kernel_launches(void);
+
+/* Serving loop (SURVEY configuration 4; the paper has no serving layer):
+ * continuous batching of refined-wall solve requests against resident walls.
+ * rw_server_create starts n_workers host threads, each with its own CUDA
+ * stream on the current device; requests queue FIFO and are admitted while
+ * the estimated device memory of the admitted requests stays within
+ * max_device_bytes (a request is always admitted when nothing else runs), so
+ * requests arriving while others run start as memory frees up and their
+ * kernels overlap on the device.  A request runs rw_refine_factor, boundary
+ * data from point forces (rw_stokeslet_data), rw_solve and the velocity at
+ * targets, and copies tau (2 N_n x nrhs) and u (2 n_targets x nrhs) to the
+ * caller's host buffers, which must stay valid until the request completes.
+ * Inputs are copied at submission.  Each result depends only on its own
+ * request.  rw_server_wait blocks and returns the request's status;
+ * rw_server_destroy finishes every queued request first. */
+typedef struct rw_server_s* rw_server_t;
+typedef struct {
+  rw_hbs_t wall;
+  int n_cut;
+  const int* panel_ids;   /* host, n_cut (as rw_refine_factor)              */
+  const int* levels;      /* host, n_cut                                    */
+  int nrhs;
+  int n_src;
+  const double* src;      /* host, 2 x n_src                                */
+  const double* f;        /* host, 2 x n_src x nrhs                         */
+  int n_targets;
+  const double* targets;  /* host, 2 x n_targets (may be NULL if none)      */
+  double* tau;            /* host output, 2 N_n x nrhs                      */
+  double* u;              /* host output, 2 n_targets x nrhs (or NULL)      */
+  int mode;               /* RW_MODE_*                                      */
+} rw_request;
+int rw_server_create(int n_workers, long long max_device_bytes, rw_server_t* out);
+int rw_server_submit(rw_server_t s, const rw_request* req, long long* ticket);
+/* status: 1 queued or running, 0 done, < 0 the request's error code. */
+int rw_server_poll(rw_server_t s, long long ticket, int* status, double* latency_ms);
+int rw_server_wait(rw_server_t s, long long ticket, double* latency_ms);
+int rw_server_destroy(rw_server_t s);
 
 /* Opt-in kernel profiler (diagnostics, no counterpart in the paper).
  * rw_profile(1) clears the records and starts recording a pair of CUDA events

@@ -17,6 +17,7 @@ namespace cg = cooperative_groups;
 namespace rw {
 
 std::atomic<unsigned long long> g_launches{0};
+thread_local cudaStream_t tl_alloc_stream = nullptr;
 
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();

@@ -212,6 +212,7 @@ __global__ void k_stokeslets(NodesView nd, int ns, const double* src, int nrhs, 
   const double* fr = f + size_t(r) * 2 * ns;
   double gx = 0.0, gy = 0.0;
   for (int s = 0; s < ns; ++s) {
+    if (fr[2 * s] == 0.0 && fr[2 * s + 1] == 0.0) continue;  // no force on this right-hand side
     const double rx = nd.x[i] - src[2 * s], ry = nd.y[i] - src[2 * s + 1], r2 = rx * rx + ry * ry;
     const double lg = -0.5 * log(r2);
     const double rf = (rx * fr[2 * s] + ry * fr[2 * s + 1]) / r2;
@@ -247,22 +248,29 @@ __global__ void k_gather_scatter(const double* in, int ldi, const int* ii, doubl
 // staged through shared memory in tiles; the rank-one N term is added from
 // the flux sum_j w_j n_j . x_j computed by k_flux.
 constexpr int NB_T = 128, NB_S = 128;
+template <int NR>
 __global__ void __launch_bounds__(NB_T) k_apply_exact(NodesView nd, const double* x, int ldx, double* y, int ldy,
-                                                       const double* flux) {
+                                                       const double* flux, int r0) {
+  // one thread per target point, up to NR right-hand sides per pass: each
+  // kernel entry is evaluated once and applied to all of them
   const int i = blockIdx.x * NB_T + threadIdx.x;
-  const int r = blockIdx.y;
-  const double* xr = x + size_t(r) * ldx;
-  __shared__ double sx[NB_S], sy[NB_S], snx[NB_S], sny[NB_S], sw[NB_S], stx[NB_S], sty[NB_S];
+  __shared__ double sx[NB_S], sy[NB_S], snx[NB_S], sny[NB_S], sw[NB_S], st[NB_S][2 * NR];
   const bool act = i < nd.n;
   const double xi = act ? nd.x[i] : 0.0, yi = act ? nd.y[i] : 0.0;
-  double ux = 0.0, uy = 0.0;
+  double ux[NR], uy[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) { ux[r] = 0.0; uy[r] = 0.0; }
   for (int j0 = 0; j0 < nd.n; j0 += NB_S) {
     const int nj = min(NB_S, nd.n - j0);
     __syncthreads();
     for (int q = threadIdx.x; q < nj; q += NB_T) {
       const int j = j0 + q;
       sx[q] = nd.x[j]; sy[q] = nd.y[j]; snx[q] = nd.nx[j]; sny[q] = nd.ny[j]; sw[q] = nd.w[j];
-      stx[q] = xr[2 * j]; sty[q] = xr[2 * j + 1];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        st[q][2 * r] = x[size_t(r0 + r) * ldx + 2 * j];
+        st[q][2 * r + 1] = x[size_t(r0 + r) * ldx + 2 * j + 1];
+      }
     }
     __syncthreads();
     if (act) {
@@ -270,19 +278,28 @@ __global__ void __launch_bounds__(NB_T) k_apply_exact(NodesView nd, const double
         if (j0 + q == i) continue;
         const double rx = xi - sx[q], ry = yi - sy[q], r2 = rx * rx + ry * ry;
         const double fac = sw[q] * (rx * snx[q] + ry * sny[q]) / (kPi * r2 * r2);
-        const double rt = rx * stx[q] + ry * sty[q];
-        ux = fma(fac * rx, rt, ux);
-        uy = fma(fac * ry, rt, uy);
+        const double fx = fac * rx, fy = fac * ry;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const double rt = rx * st[q][2 * r] + ry * st[q][2 * r + 1];
+          ux[r] = fma(fx, rt, ux[r]);
+          uy[r] = fma(fy, rt, uy[r]);
+        }
       }
     }
   }
   if (!act) return;
   const double nxi = nd.nx[i], nyi = nd.ny[i], txi = -nyi, tyi = nxi;
-  const double taux = xr[2 * i], tauy = xr[2 * i + 1];
-  const double dk = -nd.kappa[i] * nd.w[i] * (0.5 / kPi) * (txi * taux + tyi * tauy);
-  const double fl = flux[r];
-  y[size_t(r) * ldy + 2 * i] = ux + dk * txi + nxi * fl - 0.5 * taux;
-  y[size_t(r) * ldy + 2 * i + 1] = uy + dk * tyi + nyi * fl - 0.5 * tauy;
+  const double dkw = -nd.kappa[i] * nd.w[i] * (0.5 / kPi);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const double* xr = x + size_t(r0 + r) * ldx;
+    const double taux = xr[2 * i], tauy = xr[2 * i + 1];
+    const double dk = dkw * (txi * taux + tyi * tauy);
+    const double fl = flux[r0 + r];
+    y[size_t(r0 + r) * ldy + 2 * i] = ux[r] + dk * txi + nxi * fl - 0.5 * taux;
+    y[size_t(r0 + r) * ldy + 2 * i + 1] = uy[r] + dk * tyi + nyi * fl - 0.5 * tauy;
+  }
 }
 
 __global__ void k_flux(NodesView nd, const double* x, int ldx, double* flux) {
@@ -395,8 +412,18 @@ void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, c
   TBuf<double> flux(nrhs, s);
   ProfScope prof_(KC_EVAL, s);
   k_flux<<<nrhs, 256, 0, s>>>(nodes, x, 2 * nodes.n, flux.p);
-  k_apply_exact<<<dim3(ceil_div(nodes.n, NB_T), nrhs), NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p);
   RW_CHECK_LAUNCH();
+  for (int r0 = 0; r0 < nrhs; r0 += 4) {
+    const int nr = std::min(4, nrhs - r0);
+    const dim3 grid(ceil_div(nodes.n, NB_T));
+    switch (nr) {
+      case 1: k_apply_exact<1><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
+      case 2: k_apply_exact<2><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
+      case 3: k_apply_exact<3><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
+      default: k_apply_exact<4><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
+    }
+    RW_CHECK_LAUNCH();
+  }
 }
 
 void max_colnorm(const double* W, int nr, int nc, int ld, double* out, cudaStream_t s) {

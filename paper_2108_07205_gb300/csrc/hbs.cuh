@@ -100,6 +100,11 @@ class Hbs {
   void build(const Nodes& nodes, const Opts& o, cudaStream_t s);
   // x = A^{-1} b, b and x: 2N x nrhs (ld 2N).  Template on the sweep type.
   void apply_inverse(const double* b, double* x, int nrhs, cudaStream_t s) const;
+  // the same as a sequence of per-level launches with per-call temporaries
+  // (safe to call concurrently on one handle)
+  void apply_inverse_levels(const double* b, double* x, int nrhs, cudaStream_t s) const {
+    sweep_inverse<double>(b, x, nrhs, s);
+  }
   void apply_inverse_f32(const float* b, float* x, int nrhs, cudaStream_t s) const;
   // y = A x via the forward representation.
   void apply_forward(const double* x, double* y, int nrhs, cudaStream_t s) const;

@@ -40,8 +40,29 @@ __global__ void k_zero_cols(double* A, int ld, int nrows, const int* cols, int n
 
 }  // namespace
 
+SideStreams::~SideStreams() {
+  // every buffer of the refinement has been released (stream ordered) by now
+  for (cudaStream_t t : {s1, s2}) if (t) { cudaStreamSynchronize(t); cudaStreamDestroy(t); }
+}
+
+Refinement::~Refinement() {
+  // order the frees on the side streams after all work queued on the main
+  // stream (the members are released after this body, the streams last)
+  if (streams.main && (streams.s1 || streams.s2)) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(ev, streams.main);
+      if (streams.s1) cudaStreamWaitEvent(streams.s1, ev, 0);
+      if (streams.s2) cudaStreamWaitEvent(streams.s2, ev, 0);
+      cudaEventDestroy(ev);
+    }
+  }
+}
+
 void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::vector<int>& lvl, cudaStream_t s) {
   wall = &w;
+  streams.main = s;
+  AllocStreamScope alloc_scope(s);
   Trace tr(s, "refine");
   const Opts& o = w.opts;
   const int P = w.n_panels;
@@ -154,11 +175,12 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     dnear = to_device(near_d, s);
     RW_CUDA(cudaStreamSynchronize(s));
   }
-  cudaStream_t s1 = nullptr, s2 = nullptr;
-  RW_CUDA(cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking));
-  RW_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+  RW_CUDA(cudaStreamCreateWithFlags(&streams.s1, cudaStreamNonBlocking));
+  RW_CUDA(cudaStreamCreateWithFlags(&streams.s2, cudaStreamNonBlocking));
+  cudaStream_t s1 = streams.s1, s2 = streams.s2;
   std::exception_ptr e1, e2;
   std::thread th1([&] {
+    AllocStreamScope scope1(s1);
     try {
       Opts opp = o;
       pp_dense = Np <= o.dense_pp_max_points;
@@ -169,6 +191,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     } catch (...) { e1 = std::current_exception(); }
   });
   std::thread th2([&] {
+    AllocStreamScope scope2(s2);
     try {
       // far rows of I_k against P^bas (shared by A_kc and A_kp)
       IdMatProb cs{};
@@ -195,8 +218,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   } catch (...) { e0 = std::current_exception(); }
   th1.join();
   th2.join();
-  cudaStreamDestroy(s1);
-  cudaStreamDestroy(s2);
+  RW_CUDA(cudaStreamSynchronize(s1));
+  RW_CUDA(cudaStreamSynchronize(s2));
   for (auto& e : {e0, e1, e2}) if (e) std::rethrow_exception(e);
   tr.mark("A_pp inverse + IDs (concurrent)");
   kf = tf.k; kn = tn.k; kpk = tp.k; kk = kf + kn; k = kk + kpk;
@@ -232,8 +255,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   // a5: X = A~^{-1} L
   Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
   Xp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
-  if (kk) w.hbs.apply_inverse(Lo.p, Xo.p, kk, s);
-  if (kpk) hpp.apply_inverse(Lp.p, Xp.p, kpk, s);
+  if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
+  if (kpk) hpp.apply_inverse_levels(Lp.p, Xp.p, kpk, s);
   tr.mark("X = A~^-1 L");
   // a6: W = I + R X and its inverse
   {
@@ -320,8 +343,8 @@ void Refinement::solve_direct_levels(const double* g, double* tau, int nrhs, cud
   fill_zero(go.p, go.n, s);
   gather_scatter(g, 2 * Nn, n_from_o.p, go.p, 2 * No, n_to_o.p, nko, nrhs, s);
   gather_scatter(g, 2 * Nn, n_from_p.p, gp.p, 2 * Np, n_to_p.p, nkp, nrhs, s);
-  wall->hbs.apply_inverse(go.p, yo.p, nrhs, s);
-  hpp.apply_inverse(gp.p, yp.p, nrhs, s);
+  wall->hbs.apply_inverse_levels(go.p, yo.p, nrhs, s);
+  hpp.apply_inverse_levels(gp.p, yp.p, nrhs, s);
   woodbury_correct(yo.p, yp.p, nrhs, s);
   gather_scatter(yo.p, 2 * No, n_to_o.p, tau, 2 * Nn, n_from_o.p, nko, nrhs, s);
   gather_scatter(yp.p, 2 * Np, n_to_p.p, tau, 2 * Nn, n_from_p.p, nkp, nrhs, s);

@@ -13,7 +13,15 @@ struct Wall {
   Hbs hbs;      // A_oo
 };
 
+// Side streams of one refinement: created by factor(), destroyed last (after
+// every buffer allocated on them has been released).
+struct SideStreams {
+  cudaStream_t main = nullptr, s1 = nullptr, s2 = nullptr;
+  ~SideStreams();
+};
+
 struct Refinement {
+  SideStreams streams;  // first member: destroyed last
   const Wall* wall = nullptr;
   std::vector<int> panels, levels;     // cut panels (window order) and levels
   int No = 0, Nk = 0, Nc = 0, Np = 0, Nn = 0;
@@ -51,6 +59,7 @@ struct Refinement {
   void solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres) const;
   // ext-space operator y = (A~ + L R) x (FP64)
   void apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
+  ~Refinement();
 };
 
 }  // namespace rw

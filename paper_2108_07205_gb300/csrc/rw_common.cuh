@@ -40,19 +40,31 @@ inline void require(bool ok, const std::string& msg, int code = RW_ERR_INVALID) 
 }
 
 // ---------------------------------------------------------------- memory
-// Owning device buffer (cudaMallocAsync/cudaFreeAsync on the given stream is
-// avoided: handles outlive streams).  Moves only.
+// Allocation stream of the calling host thread: when set, DBuf allocations
+// are stream ordered on it (cudaMallocAsync / cudaFreeAsync), so freeing a
+// handle's memory does not synchronise the whole device.  Unset (the
+// default), DBuf uses cudaMalloc / cudaFree.
+extern thread_local cudaStream_t tl_alloc_stream;
+struct AllocStreamScope {
+  cudaStream_t prev;
+  explicit AllocStreamScope(cudaStream_t s) : prev(tl_alloc_stream) { tl_alloc_stream = s; }
+  ~AllocStreamScope() { tl_alloc_stream = prev; }
+};
+
+// Owning device buffer.  Moves only.
 template <class T>
 struct DBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t as = nullptr;
+  bool async = false;
   DBuf() = default;
   explicit DBuf(size_t count) { alloc(count); }
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
-  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), as(o.as), async(o.async) { o.p = nullptr; o.n = 0; }
   DBuf& operator=(DBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) { release(); p = o.p; n = o.n; as = o.as; async = o.async; o.p = nullptr; o.n = 0; }
     return *this;
   }
   ~DBuf() { release(); }
@@ -60,15 +72,25 @@ struct DBuf {
     release();
     n = count;
     if (count) {
-      cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+      cudaError_t e;
+      if (tl_alloc_stream) {
+        as = tl_alloc_stream;
+        async = true;
+        e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), as);
+      } else {
+        async = false;
+        e = cudaMalloc(&p, count * sizeof(T));
+      }
       if (e != cudaSuccess) {
         p = nullptr; n = 0;
-        throw Error(RW_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        throw Error(RW_ERR_OOM, std::string("device allocation: ") + cudaGetErrorString(e));
       }
     }
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (async) cudaFreeAsync(p, as); else cudaFree(p);
+    }
     p = nullptr; n = 0;
   }
   size_t bytes() const { return n * sizeof(T); }

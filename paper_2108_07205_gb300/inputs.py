@@ -67,6 +67,19 @@ def stokeslets_channel(seed, nrhs=1, n=5):
     return sx, sy, f
 
 
+def stokeslet_pairs_channel(seed, nrhs):
+    """One pair of exterior point forces per right-hand side (positions and
+    strengths drawn per pair): positions (2 nrhs,), (2 nrhs,) and strengths
+    (2 nrhs, 2, nrhs) with right-hand side r driven only by its own pair."""
+    g = rng(seed)
+    sx = g.uniform(-10.0, 10.0, size=2 * nrhs)
+    sy = g.uniform(1.0, 3.0, size=2 * nrhs) * np.where(g.uniform(size=2 * nrhs) < 0.5, -1.0, 1.0)
+    f = np.zeros((2 * nrhs, 2, nrhs))
+    for r in range(nrhs):
+        f[2 * r:2 * r + 2, :, r] = g.standard_normal(size=(2, 2))
+    return sx, sy, f
+
+
 def targets_star(seed, n=16):
     g = rng(seed)
     r = g.uniform(0.0, 0.5, size=n)

@@ -61,6 +61,14 @@ class KernelStat(ctypes.Structure):
 KCLASSES = ["id", "gemm", "gemv", "inverse", "eval", "other"]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("wall", ctypes.c_void_p), ("n_cut", ctypes.c_int), ("panel_ids", ctypes.POINTER(ctypes.c_int)),
+                ("levels", ctypes.POINTER(ctypes.c_int)), ("nrhs", ctypes.c_int), ("n_src", ctypes.c_int),
+                ("src", ctypes.c_void_p), ("f", ctypes.c_void_p), ("n_targets", ctypes.c_int),
+                ("targets", ctypes.c_void_p), ("tau", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("mode", ctypes.c_int)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double)]
 
@@ -69,7 +77,8 @@ EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_stats_get", "rw_hbs_nodes"
            "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
            "rw_stokeslet_data",
-           "rw_solve", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
+           "rw_solve", "rw_server_create", "rw_server_submit", "rw_server_poll", "rw_server_wait",
+           "rw_server_destroy", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
 
 _lib = None
 
@@ -107,6 +116,11 @@ def load(build_if_missing=False):
     L.rw_ref_free.argtypes = [vp]
     L.rw_hbs_free.argtypes = [vp]
     L.rw_last_error.restype = ctypes.c_char_p
+    L.rw_server_create.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(vp)]
+    L.rw_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]
+    L.rw_server_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.rw_server_wait.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
+    L.rw_server_destroy.argtypes = [vp]
     L.rw_profile.argtypes = [ctypes.c_int]
     L.rw_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int]
     L.rw_kernel_launches.argtypes = []
@@ -287,3 +301,63 @@ class Refinement:
             self.close()
         except Exception:
             pass
+
+
+def refined_points(n_panels, levels):
+    """N_n for a refinement of a wall with n_panels panels."""
+    return 16 * (n_panels - len(levels)) + sum(16 << int(L) for L in levels)
+
+
+class Server:
+    """Continuous-batching server over resident walls (C ABI rw_server_*)."""
+
+    def __init__(self, n_workers=4, max_device_bytes=64 << 30):
+        h = ctypes.c_void_p()
+        _check(load().rw_server_create(int(n_workers), int(max_device_bytes), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, wall, panels, levels, src, f, nrhs=1, targets=None, mode=MODE_DIRECT):
+        """Queue one request; returns (ticket, tau, u) with tau, u filled on completion.
+        src: (n_src, 2); f: (nrhs, n_src, 2) host arrays."""
+        src = np.ascontiguousarray(src, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        nn = refined_points(wall.n_panels, levels)
+        tau = np.empty((nrhs, 2 * nn))
+        nt = 0 if targets is None else len(targets)
+        tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.float64)
+        u = np.empty((nrhs, 2 * nt)) if nt else None
+        p = (ctypes.c_int * len(panels))(*[int(v) for v in panels])
+        lv = (ctypes.c_int * len(levels))(*[int(v) for v in levels])
+        q = Request(wall.h, len(panels), p, lv, int(nrhs), src.shape[0], src.ctypes.data, f.ctypes.data, nt,
+                    tg.ctypes.data if nt else None, tau.ctypes.data, u.ctypes.data if nt else None, int(mode))
+        t = ctypes.c_longlong()
+        _check(load().rw_server_submit(self.h, ctypes.byref(q), ctypes.byref(t)))
+        self._keep[t.value] = (tau, u, src, f, tg, p, lv)
+        return t.value, tau, u
+
+    def poll(self, ticket):
+        st = ctypes.c_int()
+        lat = ctypes.c_double(0.0)
+        _check(load().rw_server_poll(self.h, ticket, ctypes.byref(st), ctypes.byref(lat)))
+        return st.value, lat.value
+
+    def wait(self, ticket):
+        """Block until the request is done; returns its latency in ms."""
+        lat = ctypes.c_double(0.0)
+        rc = load().rw_server_wait(self.h, ticket, ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        _check(rc)
+        return lat.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rw_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
