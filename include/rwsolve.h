@@ -236,6 +236,25 @@ int rw_server_poll(rw_server_t s, long long ticket, int* status, double* latency
 int rw_server_wait(rw_server_t s, long long ticket, double* latency_ms);
 int rw_server_destroy(rw_server_t s);
 
+/* Batched solve of many refined walls (SURVEY configuration 5; the paper
+ * solves one wall at a time): the direct solves (Algorithm 1, s1-s3) of n
+ * refinements, each on its own wall, run as one persistent cooperative launch
+ * per 8 right-hand sides with phases aligned across the instances.  The
+ * refinements must outlive the batch.  Right-hand sides of all instances are
+ * stacked: g and tau are G x nrhs column-major (host or device), where
+ * instance i occupies rows offsets[i] .. offsets[i+1]-1 (rw_batch_rows fills
+ * offsets[0..n], offsets[n] = G) in its refined order.  use_graph != 0
+ * captures the launch in a CUDA graph on first use per nrhs and replays it.
+ * rw_batch_autotune times GEMV tiles of 16, 32 and 64 rows on the batch and
+ * keeps the fastest (appended to the file named by RW_AUTOTUNE_CACHE, if set,
+ * and read back by later batches of the same shape). */
+typedef struct rw_batch_s* rw_batch_t;
+int rw_batch_create(int n, const rw_ref_t* refs, void* stream, rw_batch_t* out);
+int rw_batch_rows(rw_batch_t b, long long* offsets);
+int rw_batch_autotune(rw_batch_t b, int nrhs, void* stream, int* tile_rows, float* ms);
+int rw_batch_solve(rw_batch_t b, int nrhs, const double* g, double* tau, int use_graph, void* stream);
+void rw_batch_free(rw_batch_t b);
+
 /* Opt-in kernel profiler (diagnostics, no counterpart in the paper).
  * rw_profile(1) clears the records and starts recording a pair of CUDA events
  * around every kernel launch of this library, on the stream of that launch,

@@ -9,21 +9,17 @@ namespace rw {
 
 namespace {
 
-constexpr int TR = 32;        // GEMV rows per tile (256 threads = 32 rows x 8 column lanes)
 constexpr int TE = 256;       // copy / fill / reduce entries per tile
 constexpr int SPLIT_N = 4096; // GEMVs wider than this with few row tiles are split
 
 struct Bases { double* p[kMaxBases]; };
 
-__device__ __forceinline__ int tiles_of(const GOp& o) {
-  return o.kind == OP_GEMV ? (o.m + TR - 1) / TR : (o.m + TE - 1) / TE;
-}
-
-template <int NR>
+template <int NR, int TR>
 __device__ void do_gemv(const GOp& o, int tile, const Bases& B, int r0, double (*xs)[NR], double (*red)[TR][NR]) {
-  // 256 threads = TR (32) rows x 8 column lanes; each lane keeps 4
+  // 256 threads = TR rows x LANES column lanes; each lane keeps UNR
   // independent accumulator chains per right-hand side
-  const int lr = threadIdx.x & (TR - 1), lc = threadIdx.x / TR;
+  constexpr int LANES = 256 / TR;
+  const int lr = threadIdx.x % TR, lc = threadIdx.x / TR;
   const int row = tile * TR + lr;
   const double* x = B.p[o.xb] + o.xo + size_t(r0) * o.ldx;
   double* y = B.p[o.yb] + o.yo + size_t(r0) * o.ldy;
@@ -44,16 +40,16 @@ __device__ void do_gemv(const GOp& o, int tile, const Bases& B, int r0, double (
     if (row < o.m) {
       const double* a = o.A + row + size_t(cb) * o.lda;
       int j = lc;
-      for (; j + 8 * (UNR - 1) < ncur; j += 8 * UNR) {
+      for (; j + LANES * (UNR - 1) < ncur; j += LANES * UNR) {
         double v[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) v[u] = a[size_t(j + 8 * u) * o.lda];
+        for (int u = 0; u < UNR; ++u) v[u] = a[size_t(j + LANES * u) * o.lda];
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
 #pragma unroll
-          for (int r = 0; r < NR; ++r) acc[u][r] = fma(v[u], xs[j + 8 * u][r], acc[u][r]);
+          for (int r = 0; r < NR; ++r) acc[u][r] = fma(v[u], xs[j + LANES * u][r], acc[u][r]);
       }
-      for (; j < ncur; j += 8) {
+      for (; j < ncur; j += LANES) {
         const double v = a[size_t(j) * o.lda];
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[0][r] = fma(v, xs[j][r], acc[0][r]);
@@ -73,7 +69,7 @@ __device__ void do_gemv(const GOp& o, int tile, const Bases& B, int r0, double (
     for (int r = 0; r < NR; ++r) {
       double s = 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s += red[q][lr][r];
+      for (int q = 0; q < LANES; ++q) s += red[q][lr][r];
       double* yp = y + row + size_t(r) * o.ldy;
       double v = o.alpha * s;
       if (o.beta != 0.0) v += o.beta * *yp;
@@ -83,12 +79,12 @@ __device__ void do_gemv(const GOp& o, int tile, const Bases& B, int r0, double (
   __syncthreads();
 }
 
-template <int NR>
+template <int NR, int TR>
 __global__ void __launch_bounds__(256, 2) k_program(const GOp* ops, const int* tile0, const int* phase, int nphases,
                                                  Bases B, int r0) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double xs[256][NR];
-  __shared__ double red[8][TR][NR];
+  __shared__ double red[256 / TR][TR][NR];
   for (int ph = 0; ph < nphases; ++ph) {
     const int o0 = phase[ph], o1 = phase[ph + 1];
     const int t0 = tile0[o0], t1 = tile0[o1];
@@ -101,7 +97,7 @@ __global__ void __launch_bounds__(256, 2) k_program(const GOp* ops, const int* t
       const GOp& o = ops[lo];
       const int tile = t - tile0[lo];
       if (o.kind == OP_GEMV) {
-        do_gemv<NR>(o, tile, B, r0, xs, red);
+        do_gemv<NR, TR>(o, tile, B, r0, xs, red);
       } else {
         const int i = tile * TE + threadIdx.x;
         if (i < o.m) {
@@ -129,10 +125,25 @@ __global__ void __launch_bounds__(256, 2) k_program(const GOp* ops, const int* t
   }
 }
 
-template <int NR>
-const void* kernel_ptr() { return reinterpret_cast<const void*>(&k_program<NR>); }
+template <int TR>
+const void* kernel_ptr(int nr) {
+  switch (nr) {
+    case 1: return reinterpret_cast<const void*>(&k_program<1, TR>);
+    case 2: return reinterpret_cast<const void*>(&k_program<2, TR>);
+    case 3: return reinterpret_cast<const void*>(&k_program<3, TR>);
+    case 4: return reinterpret_cast<const void*>(&k_program<4, TR>);
+    case 5: return reinterpret_cast<const void*>(&k_program<5, TR>);
+    case 6: return reinterpret_cast<const void*>(&k_program<6, TR>);
+    case 7: return reinterpret_cast<const void*>(&k_program<7, TR>);
+    default: return reinterpret_cast<const void*>(&k_program<8, TR>);
+  }
+}
 
-int host_tiles(const GOp& o) { return o.kind == OP_GEMV ? (o.m + TR - 1) / TR : (o.m + TE - 1) / TE; }
+const void* kernel_for(int tr, int nr) {
+  return tr == 16 ? kernel_ptr<16>(nr) : tr == 64 ? kernel_ptr<64>(nr) : kernel_ptr<32>(nr);
+}
+
+int host_tiles(const GOp& o, int tr) { return o.kind == OP_GEMV ? (o.m + tr - 1) / tr : (o.m + TE - 1) / TE; }
 
 }  // namespace
 
@@ -184,7 +195,7 @@ void Program::finalize(cudaStream_t s) {
   for (auto& ph : phases_) {
     std::vector<GOp> cur, red;
     for (const GOp& o : ph) {
-      if (o.kind == OP_GEMV && o.n > SPLIT_N && host_tiles(o) < 38) {
+      if (o.kind == OP_GEMV && o.n > SPLIT_N && host_tiles(o, 32) < 38) {
         const int parts = (o.n + SPLIT_N - 1) / SPLIT_N;
         const long long pw = ws_alloc((long long)parts * o.m);
         for (int q = 0; q < parts; ++q) {
@@ -218,56 +229,94 @@ void Program::finalize(cudaStream_t s) {
       if (o.ldy == -1) o.ldy = int(ws_);
     }
   std::vector<GOp> flat;
-  std::vector<int> phase(1, 0), tile0(1, 0);
-  int maxt = 1;
+  std::vector<int> phase(1, 0);
   for (auto& ph : out) {
-    int tph = 0;
-    for (const GOp& o : ph) {
-      flat.push_back(o);
-      tph += host_tiles(o);
-      tile0.push_back(tile0.back() + host_tiles(o));
-    }
+    for (const GOp& o : ph) flat.push_back(o);
     phase.push_back(int(flat.size()));
-    maxt = std::max(maxt, tph);
   }
   nph_ = int(out.size());
   d_ops_ = to_device(flat, s);
-  d_tile_ = to_device(tile0, s);
   d_phase_ = to_device(phase, s);
-  RW_CUDA(cudaStreamSynchronize(s));
-  int dev = 0, nsm = 0, per = 0;
+  int dev = 0, nsm = 0;
   RW_CUDA(cudaGetDevice(&dev));
   RW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  RW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_program<8>, 256, 0));
-  grid_ = std::max(1, std::min(maxt, nsm * std::max(per, 1)));
+  const int trs[3] = {16, 32, 64};
+  for (int v = 0; v < 3; ++v) {
+    std::vector<int> tile0(1, 0);
+    int maxt = 1;
+    size_t o0 = 0;
+    for (auto& ph : out) {
+      int tph = 0;
+      for (const GOp& o : ph) {
+        const int t = host_tiles(o, trs[v]);
+        tph += t;
+        tile0.push_back(tile0.back() + t);
+      }
+      maxt = std::max(maxt, tph);
+      o0 += ph.size();
+    }
+    d_tile_[v] = to_device(tile0, s);
+    int per = 0;
+    RW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(trs[v], 8), 256, 0));
+    grid_[v] = std::max(1, std::min(maxt, nsm * std::max(per, 1)));
+  }
+  RW_CUDA(cudaStreamSynchronize(s));
 }
 
 void Program::run(double* const* bases, int nrhs, cudaStream_t s) const {
   if (nph_ == 0) return;
   Bases B;
   for (int i = 0; i < kMaxBases; ++i) B.p[i] = bases[i];
+  const int v = tr_index_;
+  const int trs[3] = {16, 32, 64};
   const GOp* ops = d_ops_.p;
-  const int* t0 = d_tile_.p;
+  const int* t0 = d_tile_[v].p;
   const int* ph = d_phase_.p;
   int nphases = nph_;
   for (int r0 = 0; r0 < nrhs; r0 += 8) {
     const int nr = std::min(8, nrhs - r0);
     void* args[] = {(void*)&ops, (void*)&t0, (void*)&ph, (void*)&nphases, (void*)&B, (void*)&r0};
-    const void* fn = nullptr;
-    switch (nr) {
-      case 1: fn = kernel_ptr<1>(); break;
-      case 2: fn = kernel_ptr<2>(); break;
-      case 3: fn = kernel_ptr<3>(); break;
-      case 4: fn = kernel_ptr<4>(); break;
-      case 5: fn = kernel_ptr<5>(); break;
-      case 6: fn = kernel_ptr<6>(); break;
-      case 7: fn = kernel_ptr<7>(); break;
-      default: fn = kernel_ptr<8>(); break;
-    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_[v]);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     ProfScope prof(KC_GEMV, s, 0.0, 0.0);
-    RW_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid_), dim3(256), args, 0, s));
+    RW_CUDA(cudaLaunchKernelExC(&cfg, kernel_for(trs[v], nr), args));
     RW_CHECK_LAUNCH();
   }
+}
+
+float Program::autotune(double* const* bases, int nrhs, cudaStream_t s) {
+  // time each tile height (best of 3 after one warm-up run) and keep the fastest
+  cudaEvent_t a, b;
+  RW_CUDA(cudaEventCreate(&a));
+  RW_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  int bestv = 1;
+  for (int v = 0; v < 3; ++v) {
+    tr_index_ = v;
+    run(bases, nrhs, s);
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      RW_CUDA(cudaEventRecord(a, s));
+      run(bases, nrhs, s);
+      RW_CUDA(cudaEventRecord(b, s));
+      RW_CUDA(cudaEventSynchronize(b));
+      float ms = 0.f;
+      RW_CUDA(cudaEventElapsedTime(&ms, a, b));
+      tmin = std::min(tmin, ms);
+    }
+    if (tmin < best) { best = tmin; bestv = v; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  tr_index_ = bestv;
+  return best;
 }
 
 }  // namespace rw

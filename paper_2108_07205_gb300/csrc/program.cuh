@@ -48,13 +48,20 @@ class Program {
   void run(double* const* bases, int nrhs, cudaStream_t s) const;
   long long matrix_elems() const { return mat_elems_; }
   int launches_per_run(int nrhs) const { return (nrhs + 7) / 8; }
+  // Autotuner: times the three GEMV tile heights (16, 32, 64 rows) on these
+  // bases and keeps the fastest; returns its time (ms).
+  float autotune(double* const* bases, int nrhs, cudaStream_t s);
+  int tile_rows() const { return tr_index_ == 0 ? 16 : tr_index_ == 2 ? 64 : 32; }
+  void set_tile_rows(int tr) { tr_index_ = tr == 16 ? 0 : tr == 64 ? 2 : 1; }
 
  private:
   std::vector<std::vector<GOp>> phases_;
   long long ws_ = 0, mat_elems_ = 0;
-  int nph_ = 0, grid_ = 0;
+  int nph_ = 0;
+  int grid_[3] = {0, 0, 0};
+  int tr_index_ = 1;
   DBuf<GOp> d_ops_;
-  DBuf<int> d_tile_, d_phase_;
+  DBuf<int> d_tile_[3], d_phase_;
 };
 
 }  // namespace rw

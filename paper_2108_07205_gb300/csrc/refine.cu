@@ -301,15 +301,13 @@ void Refinement::woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t
   matvec<double>(p2, nrhs, s);
 }
 
-void Refinement::build_solve_program(cudaStream_t s) {
-  // bases: 0 = g (2Nn x nrhs), 1 = tau (2Nn x nrhs), 2 = workspace (ld -1 = per-RHS block)
-  Program& P = solve_prog;
-  const int WS = 2, ldn = 2 * Nn;
+void Refinement::emit_solve(Program& P, int gb, long long g_off, int ldg, int tb, long long t_off, int ldt) const {
+  const int WS = 2;  // workspace base (ld -1: per-RHS block)
   const long long go = P.ws_alloc(2LL * No), gp = P.ws_alloc(2LL * Np);
   const long long yo = P.ws_alloc(2LL * No), yp = P.ws_alloc(2LL * Np);
   P.zero(0, 2 * No, WS, go, -1, nullptr);
-  P.copy(0, nkp, 0, 0, ldn, n_from_p.p, WS, gp, -1, n_to_p.p);
-  P.copy(1, nko, 0, 0, ldn, n_from_o.p, WS, go, -1, n_to_o.p);
+  P.copy(0, nkp, gb, g_off, ldg, n_from_p.p, WS, gp, -1, n_to_p.p);
+  P.copy(1, nko, gb, g_off, ldg, n_from_o.p, WS, go, -1, n_to_o.p);
   const int pa = wall->hbs.emit_inverse_sweep(P, 2, WS, go, -1, WS, yo, -1);
   const int pb = hpp.emit_inverse_sweep(P, 2, WS, gp, -1, WS, yp, -1);
   int p = std::max(pa, pb);
@@ -325,9 +323,14 @@ void Refinement::build_solve_program(cudaStream_t s) {
     if (kpk) P.gemv(p, Xp.p, 2 * Np, kpk, 2 * Np, WS, z + kk, -1, WS, yp, -1, -1.0, 1.0);
     ++p;
   }
-  P.copy(p, nko, WS, yo, -1, n_to_o.p, 1, 0, ldn, n_from_o.p);
-  P.copy(p, nkp, WS, yp, -1, n_to_p.p, 1, 0, ldn, n_from_p.p);
-  P.finalize(s);
+  P.copy(p, nko, WS, yo, -1, n_to_o.p, tb, t_off, ldt, n_from_o.p);
+  P.copy(p, nkp, WS, yp, -1, n_to_p.p, tb, t_off, ldt, n_from_p.p);
+}
+
+void Refinement::build_solve_program(cudaStream_t s) {
+  // bases: 0 = g (2Nn x nrhs), 1 = tau (2Nn x nrhs), 2 = workspace
+  emit_solve(solve_prog, 0, 0, 2 * Nn, 1, 0, 2 * Nn);
+  solve_prog.finalize(s);
 }
 
 void Refinement::solve_direct(const double* g, double* tau, int nrhs, cudaStream_t s) const {

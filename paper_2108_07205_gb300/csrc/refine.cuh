@@ -43,6 +43,9 @@ struct Refinement {
   Program solve_prog;
   mutable DBuf<double> solve_ws;
   void build_solve_program(cudaStream_t s);
+  // Append this refinement's direct solve to a program: g = base gb + g_off
+  // (ld ldg), tau = base tb + t_off (ld ldt), temporaries in base 2.
+  void emit_solve(Program& P, int gb, long long g_off, int ldg, int tb, long long t_off, int ldt) const;
   void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s);
   // Direct solve, device buffers: g, tau (2Nn x nrhs): one persistent launch
   // per 8 right-hand sides.  solve_direct_levels is the same computation as

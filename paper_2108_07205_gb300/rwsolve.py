@@ -77,7 +77,8 @@ EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_stats_get", "rw_hbs_nodes"
            "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
            "rw_stokeslet_data",
-           "rw_solve", "rw_server_create", "rw_server_submit", "rw_server_poll", "rw_server_wait",
+           "rw_solve", "rw_batch_create", "rw_batch_rows", "rw_batch_autotune", "rw_batch_solve",
+           "rw_batch_free", "rw_server_create", "rw_server_submit", "rw_server_poll", "rw_server_wait",
            "rw_server_destroy", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
 
 _lib = None
@@ -116,6 +117,11 @@ def load(build_if_missing=False):
     L.rw_ref_free.argtypes = [vp]
     L.rw_hbs_free.argtypes = [vp]
     L.rw_last_error.restype = ctypes.c_char_p
+    L.rw_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), vp, ctypes.POINTER(vp)]
+    L.rw_batch_rows.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.rw_batch_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+    L.rw_batch_solve.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_int, vp]
+    L.rw_batch_free.argtypes = [vp]
     L.rw_server_create.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(vp)]
     L.rw_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]
     L.rw_server_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -126,7 +132,7 @@ def load(build_if_missing=False):
     L.rw_kernel_launches.argtypes = []
     L.rw_kernel_launches.restype = ctypes.c_ulonglong
     for name in EXPORTS:
-        if name not in ("rw_last_error", "rw_ref_free", "rw_hbs_free", "rw_kernel_launches"):
+        if name not in ("rw_last_error", "rw_ref_free", "rw_hbs_free", "rw_kernel_launches", "rw_batch_free"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -353,6 +359,41 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             load().rw_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched single-launch solve over many refinements (C ABI rw_batch_*)."""
+
+    def __init__(self, refs, stream=None):
+        arr = (ctypes.c_void_p * len(refs))(*[r.h.value for r in refs])
+        h = ctypes.c_void_p()
+        _check(load().rw_batch_create(len(refs), arr, _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.refs = list(refs)
+        off = (ctypes.c_longlong * (len(refs) + 1))()
+        _check(load().rw_batch_rows(self.h, off))
+        self.offsets = list(off)
+
+    def autotune(self, nrhs=1, stream=None):
+        tr = ctypes.c_int()
+        ms = ctypes.c_float()
+        _check(load().rw_batch_autotune(self.h, nrhs, _stream(stream), ctypes.byref(tr), ctypes.byref(ms)))
+        return tr.value, ms.value
+
+    def solve(self, g, tau, nrhs=1, use_graph=True, stream=None):
+        _check(load().rw_batch_solve(self.h, nrhs, _ptr(g), _ptr(tau, True), 1 if use_graph else 0, _stream(stream)))
+        return tau
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rw_batch_free(self.h)
             self.h = None
 
     def __del__(self):
