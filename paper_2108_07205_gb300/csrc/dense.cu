@@ -766,6 +766,53 @@ __global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_
   }
 }
 
+// One pivot step's update of a CTA's candidate columns (shared memory, nr
+// rows each) by the Householder reflector I - tau v v^T (v(s) = 1, v(i) =
+// vloc(i) below): G threads (a power of two <= 32, within one warp) per
+// column compute the dot product and the update, then the column norm is
+// downdated (LAPACK xLAQP2 scheme) and recomputed exactly when cancellation
+// makes the downdate unreliable.  Done columns carry a negative norm.
+__device__ __forceinline__ void cpqr_update_columns(double* Wl, int nr, int ncl, int ncl_pad, int G, int s,
+                                                    double tau, const double* vloc, double* nrm, double* nrm0,
+                                                    double tol3z) {
+  const int tid = threadIdx.x, nt = blockDim.x, gl = tid & (G - 1);
+  for (int j = tid / G; j < ncl_pad; j += nt / G) {
+    const bool live = j < ncl && nrm[j] >= 0.0;
+    double* cj = Wl + size_t(live ? j : 0) * nr;
+    double dd = 0.0;
+    if (live && tau != 0.0)
+      for (int i = s + 1 + gl; i < nr; i += G) dd += vloc[i] * cj[i];
+    for (int off = G / 2; off > 0; off >>= 1) dd += __shfl_down_sync(0xffffffffu, dd, off, G);
+    dd = __shfl_sync(0xffffffffu, dd, 0, G);
+    int recompute = 0;
+    if (live) {
+      if (tau != 0.0) {
+        dd = tau * (dd + cj[s]);
+        for (int i = s + 1 + gl; i < nr; i += G) cj[i] -= dd * vloc[i];
+      }
+      const double rs = (tau != 0.0) ? cj[s] - dd : cj[s];
+      const double nj = nrm[j];
+      if (nj != 0.0) {
+        double t = fabs(rs) / nj;
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        const double r = nj / nrm0[j];
+        if (t * r * r <= tol3z) recompute = 1;
+        else if (gl == 0) nrm[j] = nj * sqrt(t);
+      }
+    }
+    // recompute decisions differ between groups: every lane joins the
+    // shuffles, lanes of groups without a recompute add zeros
+    double q = 0.0;
+    if (live && recompute)
+      for (int i = s + 1 + gl; i < nr; i += G) q += cj[i] * cj[i];
+    for (int off = G / 2; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off, G);
+    if (live && gl == 0) {
+      if (tau != 0.0) cj[s] -= dd;
+      if (recompute) { nrm[j] = sqrt(q); nrm0[j] = nrm[j]; }
+    }
+  }
+}
+
 // Cluster variant (thread-block cluster of CS CTAs per problem): CTA r of
 // the cluster keeps candidate columns [r cw, (r+1) cw) of W in its shared
 // memory.  Per pivot step: every CTA publishes its local column-norm maximum,
@@ -775,26 +822,35 @@ __global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_
 // are not swapped: column q keeps its data, piv[] records the pivot order,
 // and the factorisation is written back to global memory in this "no-swap"
 // layout (R(l, i) = W[l, piv[i]]; T for a non-pivot candidate q in column q).
-__global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int base, int CS, double* flops_out) {
+//
+// Paired mode (paired = 1): a cluster of 2 CS CTAs factors problems 2c and
+// 2c+1 side by side (CTAs [0, CS) and [CS, 2 CS)) with a joint stopping
+// rule: both continue while either has not met its tolerance, so both end
+// with the larger of the two ranks (the common rank of a node's row and
+// column IDs) in one pass.  A problem that runs out of candidates or of
+// nonzero columns stops on its own while its partner continues.
+__global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int base, int CS, int paired,
+                                                      double* flops_out) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = int(cluster.block_rank());
-  const IdProb P = probs[base + blockIdx.x / CS];
+  const int np = paired ? 2 : 1;
+  const int half = crank / CS, lr = crank % CS;
+  const int pidx = base + (blockIdx.x / (CS * np)) * np + half;
+  const IdProb P = probs[pidx];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int nr = P.nr, nc = P.nc;
   const int cw = (nc + CS - 1) / CS;
-  const int c0 = crank * cw, c1 = min(nc, c0 + cw), ncl = max(0, c1 - c0);
+  const int c0 = min(nc, lr * cw), c1 = min(nc, c0 + cw), ncl = max(0, c1 - c0);
   extern __shared__ double smem[];
   double* Wl = smem;                  // nr x cw
   double* vbuf = Wl + size_t(nr) * cw;  // published Householder vector (owner)
   double* vloc = vbuf + nr;           // local copy
   double* nrm = vloc + nr;            // cw
   double* nrm0 = nrm + cw;            // cw
-  __shared__ double pub_val, pub_tau, g_val;
+  __shared__ double pub_val, pub_tau, g_val, g_val_o;
   __shared__ int pub_idx, g_idx;
   __shared__ double sval[32];
   __shared__ int sidx[32];
-  __shared__ int s_done[1];
-  (void)s_done;
   // load owned columns, norms
   for (int e = tid; e < nr * ncl; e += nt) {
     const int i = e % nr, j = e / nr;
@@ -809,114 +865,111 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
   }
   __syncthreads();
   const int maxsteps = (nr <= 0 || nc <= 0) ? 0 : min(min(nr, nc), P.max_rank);
+  // the partner's stopping parameters (paired mode)
+  int maxsteps_o = 0, minrank_o = 0;
+  double tabs_o = 0.0, trel_o = 0.0;
+  if (paired) {
+    const IdProb& Q = probs[pidx + (half == 0 ? 1 : -1)];
+    maxsteps_o = (Q.nr <= 0 || Q.nc <= 0) ? 0 : min(min(Q.nr, Q.nc), Q.max_rank);
+    minrank_o = Q.min_rank;
+    tabs_o = Q.tol_abs;
+    trel_o = Q.tol_rel;
+  }
   const double tol3z = sqrt(2.220446049250313e-16);
   int G = 32;
   while (G > 1 && (nt / G) < ncl) G >>= 1;
-  const int gl = tid & (G - 1);
   const int ncl_pad = (ncl + (nt / G) - 1) / (nt / G) * (nt / G);
-  double ref = 0.0;
-  int s = 0;
-  for (; s < maxsteps; ++s) {
+  double ref = 0.0, ref_o = 0.0;
+  bool done = false, done_o = !paired;
+  int s = 0;  // steps taken by this CTA's problem
+  for (int it = 0;; ++it) {
     // local argmax over remaining owned columns (done columns have norm -1)
     double v = -1.0;
     int idx = 0x7fffffff;
-    for (int j = tid; j < ncl; j += nt) if (nrm[j] > v) { v = nrm[j]; idx = c0 + j; }
+    if (!done)
+      for (int j = tid; j < ncl; j += nt) if (nrm[j] > v) { v = nrm[j]; idx = c0 + j; }
     int p;
     double lm = block_reduce_max_abs_arg(v, idx, &p, sval, sidx);
     if (tid == 0) { pub_val = lm; pub_idx = p; }
     cluster.sync();
     if (warp == 0) {
-      // lane r reads CTA r's slot; warp arg-max (smallest index on ties)
-      double bv = -1.0;
+      // lane r reads CTA r's slot; warp arg-max over this problem's CTAs
+      // (smallest index on ties) and the partner's maximum
+      double bv = -1.0, ov_o = -1.0;
       int bi = 0x7fffffff;
-      if (lane < CS) {
-        bv = *cluster.map_shared_rank(&pub_val, lane);
-        bi = *cluster.map_shared_rank(&pub_idx, lane);
+      if (lane < CS * np) {
+        const double x = *cluster.map_shared_rank(&pub_val, lane);
+        const int xi = *cluster.map_shared_rank(&pub_idx, lane);
+        if (lane / CS == half) { bv = x; bi = xi; }
+        else ov_o = x;
       }
       for (int off = 16; off > 0; off >>= 1) {
         const double ov = __shfl_down_sync(0xffffffffu, bv, off);
         const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        ov_o = fmax(ov_o, __shfl_down_sync(0xffffffffu, ov_o, off));
         if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
       }
-      if (lane == 0) { g_val = bv; g_idx = bi; }
+      if (lane == 0) { g_val = bv; g_idx = bi; g_val_o = ov_o; }
     }
     __syncthreads();
-    const double vmax = g_val;
+    const double vmax = g_val, vmax_o = g_val_o;
     const int pg = g_idx;
-    if (s == 0) ref = vmax;
-    const double thr = fmax(P.tol_abs, P.tol_rel * ref);
-    if (vmax <= 0.0 || (s >= P.min_rank && vmax <= thr)) break;
-    const int owner = pg / cw;
-    if (crank == 0 && tid == 0) P.piv[s] = pg;
-    if (crank == owner) {
-      const int jl = pg - c0;
-      double* col = Wl + size_t(jl) * nr;
-      double part = 0.0;
-      for (int i = s + 1 + tid; i < nr; i += nt) part += col[i] * col[i];
-      const double xn2 = block_reduce_sum(part, sval);
-      const double alpha = col[s];
-      double tau = 0.0, sc = 0.0;
-      if (xn2 != 0.0) {
-        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-        tau = (beta - alpha) / beta;
-        sc = 1.0 / (alpha - beta);
-      }
-      __syncthreads();
-      for (int i = s + 1 + tid; i < nr; i += nt) {
-        const double x = col[i] * sc;
-        col[i] = x;
-        vbuf[i] = x;
-      }
-      if (tid == 0) {
-        if (xn2 != 0.0) col[s] = -copysign(sqrt(alpha * alpha + xn2), alpha);
-        pub_tau = tau;
-        nrm[jl] = -1.0;  // done
+    if (it == 0) { ref = vmax; ref_o = vmax_o; }
+    // the same decisions in every CTA of the cluster (same published data)
+    const bool hard = done || it >= maxsteps || vmax <= 0.0;
+    const bool soft = hard || (it >= P.min_rank && vmax <= fmax(P.tol_abs, P.tol_rel * ref));
+    const bool hard_o = done_o || it >= maxsteps_o || vmax_o <= 0.0;
+    const bool soft_o = hard_o || (it >= minrank_o && vmax_o <= fmax(tabs_o, trel_o * ref_o));
+    if (soft && soft_o) break;
+    done = hard;
+    done_o = hard_o;
+    const int owner = half * CS + pg / cw;
+    if (!done) {
+      if (lr == 0 && tid == 0) P.piv[s] = pg;
+      if (crank == owner) {
+        const int jl = pg - c0;
+        double* col = Wl + size_t(jl) * nr;
+        double part = 0.0;
+        for (int i = s + 1 + tid; i < nr; i += nt) part += col[i] * col[i];
+        const double xn2 = block_reduce_sum(part, sval);
+        const double alpha = col[s];
+        double tau = 0.0, sc = 0.0;
+        if (xn2 != 0.0) {
+          const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+          tau = (beta - alpha) / beta;
+          sc = 1.0 / (alpha - beta);
+        }
+        __syncthreads();
+        for (int i = s + 1 + tid; i < nr; i += nt) {
+          const double x = col[i] * sc;
+          col[i] = x;
+          vbuf[i] = x;
+        }
+        if (tid == 0) {
+          if (xn2 != 0.0) col[s] = -copysign(sqrt(alpha * alpha + xn2), alpha);
+          pub_tau = tau;
+          nrm[jl] = -1.0;  // done
+        }
       }
     }
     cluster.sync();
-    const double* rv = cluster.map_shared_rank(vbuf, owner);
-    const double tau = *cluster.map_shared_rank(&pub_tau, owner);
-    for (int i = s + 1 + tid; i < nr; i += nt) vloc[i] = rv[i];
-    __syncthreads();
-    // G threads (a power of two <= 32, within one warp) per local column
-    for (int jb = tid / G; jb < ncl_pad; jb += nt / G) {
-      const int j = jb;
-      const bool live = j < ncl && nrm[j] >= 0.0;
-      double* cj = Wl + size_t(live ? j : 0) * nr;
-      double dd = 0.0;
-      if (live && tau != 0.0)
-        for (int i = s + 1 + gl; i < nr; i += G) dd += vloc[i] * cj[i];
-      for (int off = G / 2; off > 0; off >>= 1) dd += __shfl_down_sync(0xffffffffu, dd, off, G);
-      dd = __shfl_sync(0xffffffffu, dd, 0, G);
-      double q = 0.0;
-      if (live) {
-        if (tau != 0.0) {
-          dd = tau * (dd + cj[s]);
-          for (int i = s + 1 + gl; i < nr; i += G) {
-            const double x = cj[i] - dd * vloc[i];
-            cj[i] = x;
-            q += x * x;
-          }
-        } else {
-          for (int i = s + 1 + gl; i < nr; i += G) q += cj[i] * cj[i];
-        }
-      }
-      for (int off = G / 2; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off, G);
-      if (live && gl == 0) {
-        if (tau != 0.0) cj[s] -= dd;
-        nrm[j] = sqrt(q);  // exact norm of rows s+1.. (summed in the update pass)
-      }
+    if (!done) {
+      const double* rv = cluster.map_shared_rank(vbuf, owner);
+      const double tau = *cluster.map_shared_rank(&pub_tau, owner);
+      for (int i = s + 1 + tid; i < nr; i += nt) vloc[i] = rv[i];
+      __syncthreads();
+      cpqr_update_columns(Wl, nr, ncl, ncl_pad, G, s, tau, vloc, nrm, nrm0, tol3z);
+      ++s;
     }
     __syncthreads();
   }
-  // every CTA leaves the loop at the same s (same data, same decisions)
   for (int e = tid; e < nr * ncl; e += nt) {
     const int i = e % nr, j = e / nr;
     P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * nr];
   }
   // done flags for the remaining-pivot bookkeeping: mark in global norms
   for (int j = tid; j < ncl; j += nt) P.norms[nc + c0 + j] = (nrm[j] < 0.0) ? -1.0 : 1.0;
-  if (crank == 0 && tid == 0) {
+  if (lr == 0 && tid == 0) {
     P.norms[2 * nc + 1] = double(s); P.norms[2 * nc + 2] = ref; P.norms[2 * nc + 3] = 1.0;
     if (flops_out) {
       // Householder QR with column pivoting: dot + update = 4 flops per
@@ -927,6 +980,131 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
     }
   }
   cluster.sync();  // keep shared memory alive until remote readers are done
+}
+
+// Grid-wide variant for one wide problem (hundreds to thousands of
+// candidates): a cooperative grid of G CTAs, CTA b keeping candidate columns
+// [b cw, (b+1) cw) in its shared memory.  One grid barrier per pivot step:
+// every CTA publishes its local norm maximum together with that column
+// (double-buffered by step parity), the barrier makes them visible, and every
+// CTA then picks the same global pivot, forms the same Householder vector from
+// the published column and updates its own columns.  Same no-swap layout and
+// outputs as the cluster variant.  pub holds 4 G + 2 G nr doubles.
+__global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int idx, double* pub, double* flops_out) {
+  cg::grid_group grid = cg::this_grid();
+  const IdProb P = probs[idx];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int nr = P.nr, nc = P.nc;
+  const int cw = (nc + G - 1) / G;
+  const int c0 = min(nc, b * cw), c1 = min(nc, c0 + cw), ncl = max(0, c1 - c0);
+  extern __shared__ double smem[];
+  double* Wl = smem;                    // nr x cw
+  double* vloc = Wl + size_t(nr) * cw;  // nr
+  double* nrm = vloc + nr;              // cw
+  double* nrm0 = nrm + cw;              // cw
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  __shared__ double g_val;
+  __shared__ int g_idx, g_blk;
+  for (int e = tid; e < nr * ncl; e += nt) {
+    const int i = e % nr, j = e / nr;
+    Wl[i + size_t(j) * nr] = P.W[i + size_t(c0 + j) * P.ldw];
+  }
+  __syncthreads();
+  for (int j = warp; j < ncl; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < nr; i += 32) { double v = Wl[i + size_t(j) * nr]; s += v * v; }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) { nrm[j] = sqrt(s); nrm0[j] = nrm[j]; }
+  }
+  __syncthreads();
+  const int maxsteps = (nr <= 0 || nc <= 0) ? 0 : min(min(nr, nc), P.max_rank);
+  const double tol3z = sqrt(2.220446049250313e-16);
+  int G2 = 32;
+  while (G2 > 1 && (nt / G2) < ncl) G2 >>= 1;
+  const int ncl_pad = (ncl + (nt / G2) - 1) / (nt / G2) * (nt / G2);
+  double ref = 0.0;
+  int s = 0;
+  for (; s < maxsteps; ++s) {
+    const int par = s & 1;
+    double* pv = pub + size_t(par) * G;
+    double* pi = pub + 2 * size_t(G) + size_t(par) * G;
+    double* pcol = pub + 4 * size_t(G) + (size_t(par) * G + b) * nr;
+    double v = -1.0;
+    int id = 0x7fffffff;
+    for (int j = tid; j < ncl; j += nt) if (nrm[j] > v) { v = nrm[j]; id = c0 + j; }
+    int p;
+    const double lm = block_reduce_max_abs_arg(v, id, &p, sval, sidx);
+    if (lm >= 0.0) {
+      const double* src = Wl + size_t(p - c0) * nr;
+      for (int i = s + tid; i < nr; i += nt) pcol[i] = src[i];
+    }
+    if (tid == 0) { pv[b] = lm; pi[b] = double(lm >= 0.0 ? p : 0x7fffffff); }
+    __threadfence();
+    grid.sync();
+    if (warp == 0) {
+      double bv = -1.0;
+      int bi = 0x7fffffff, bb = 0;
+      for (int q = lane; q < G; q += 32) {
+        const double ov = __ldcg(pv + q);
+        const int oi = int(__ldcg(pi + q));
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bb = q; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        const int ob = __shfl_down_sync(0xffffffffu, bb, off);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bb = ob; }
+      }
+      if (lane == 0) { g_val = bv; g_idx = bi; g_blk = bb; }
+    }
+    __syncthreads();
+    const double vmax = g_val;
+    const int pg = g_idx, owner = g_blk;
+    if (s == 0) ref = vmax;
+    const double thr = fmax(P.tol_abs, P.tol_rel * ref);
+    if (vmax <= 0.0 || (s >= P.min_rank && vmax <= thr)) break;
+    if (b == 0 && tid == 0) P.piv[s] = pg;
+    // Householder vector of the published pivot column (the same arithmetic
+    // in every CTA, so every CTA holds the same reflector)
+    const double* col = pub + 4 * size_t(G) + (size_t(par) * G + owner) * nr;
+    double part = 0.0;
+    for (int i = s + 1 + tid; i < nr; i += nt) { const double x = __ldcg(col + i); part += x * x; }
+    const double xn2 = block_reduce_sum(part, sval);
+    const double alpha = __ldcg(col + s);
+    double tau = 0.0, sc = 0.0, beta = alpha;
+    if (xn2 != 0.0) {
+      beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+      tau = (beta - alpha) / beta;
+      sc = 1.0 / (alpha - beta);
+    }
+    for (int i = s + 1 + tid; i < nr; i += nt) vloc[i] = __ldcg(col + i) * sc;
+    __syncthreads();
+    if (b == owner) {
+      const int jl = pg - c0;
+      double* cp = Wl + size_t(jl) * nr;
+      for (int i = s + 1 + tid; i < nr; i += nt) cp[i] = vloc[i];
+      if (tid == 0) { cp[s] = beta; nrm[jl] = -1.0; }
+      __syncthreads();
+    }
+    cpqr_update_columns(Wl, nr, ncl, ncl_pad, G2, s, tau, vloc, nrm, nrm0, tol3z);
+    __syncthreads();
+  }
+  // every CTA leaves the loop at the same s (same published data, same decisions)
+  for (int e = tid; e < nr * ncl; e += nt) {
+    const int i = e % nr, j = e / nr;
+    P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * nr];
+  }
+  for (int j = tid; j < ncl; j += nt) P.norms[nc + c0 + j] = (nrm[j] < 0.0) ? -1.0 : 1.0;
+  if (b == 0 && tid == 0) {
+    P.norms[2 * nc + 1] = double(s); P.norms[2 * nc + 2] = ref; P.norms[2 * nc + 3] = 1.0;
+    if (flops_out) {
+      double f = 0.0;
+      for (int q = 0; q < s; ++q) f += 4.0 * double(nr - q) * double(nc - q - 1);
+      atomicAdd(flops_out, f);
+    }
+  }
 }
 
 // Completes a no-swap factorisation (one thread per problem): appends the
@@ -963,41 +1141,46 @@ __global__ void k_id_prep(const IdProb* probs, int base, int n) {
 }
 
 // T = R11^{-1} R12 for no-swap factorisations: blockIdx.y = problem,
-// blockIdx.x = chunk of 64 non-skeleton candidates; R11 (pivot order) staged
-// in shared memory when it fits, one warp per candidate column.
-constexpr int TS_COLS = 64;
+// blockIdx.x = chunk of TS_COLS non-skeleton candidates.  Column-parallel
+// back substitution: the chunk's right-hand sides sit in shared memory, and
+// at step i (from keff-1 down) every thread scales its column's entry i by
+// 1 / R(i, i) and updates its share of rows l < i.  R11 (pivot order) is
+// staged in shared memory as a packed upper triangle when keff <= rmax, else
+// read from global memory.
+constexpr int TS_COLS = 16;
 __global__ void __launch_bounds__(256) k_id_tsolve(const IdProb* probs, int base, int rmax) {
   const IdProb P = probs[base + blockIdx.y];
   const int nc = P.nc, k = *P.rank, keff = int(P.norms[2 * nc]);
   const int q0 = k + blockIdx.x * TS_COLS;
   if (q0 >= nc || keff == 0) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int ncols = min(TS_COLS, nc - q0);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int c = tid % TS_COLS, rg = tid / TS_COLS, nrg = nt / TS_COLS;
   extern __shared__ double sm[];
   const bool inR = keff <= rmax;
-  double* R = sm;                                        // keff x keff (if inR)
-  double* bb = sm + (inR ? size_t(keff) * keff : 0);     // nw x keff
-  if (inR) {
-    for (int e = tid; e < keff * keff; e += blockDim.x) {
-      const int l = e % keff, i = e / keff;
-      R[e] = (l <= i) ? P.W[l + size_t(P.piv[i]) * P.ldw] : 0.0;
+  double* R = sm;                                                   // packed, column i at i(i+1)/2
+  double* B = sm + (inR ? size_t(keff) * (keff + 1) / 2 : 0);       // keff x TS_COLS, B[l TS_COLS + c]
+  double* dinv = B + size_t(keff) * TS_COLS;                        // keff
+  if (inR)
+    for (int i = warp; i < keff; i += nw) {
+      const double* src = P.W + size_t(P.piv[i]) * P.ldw;
+      double* dst = R + size_t(i) * (i + 1) / 2;
+      for (int l = lane; l <= i; l += 32) dst[l] = src[l];
     }
+  for (int i = tid; i < keff; i += nt) dinv[i] = 1.0 / P.W[i + size_t(P.piv[i]) * P.ldw];
+  for (int e = tid; e < keff * TS_COLS; e += nt) {
+    const int l = e % keff, cc = e / keff;
+    B[size_t(l) * TS_COLS + cc] = cc < ncols ? P.W[l + size_t(P.piv[q0 + cc]) * P.ldw] : 0.0;
   }
   __syncthreads();
-  double* b = bb + size_t(warp) * keff;
-  for (int q = q0 + warp; q < min(nc, q0 + TS_COLS); q += nw) {
-    double* cj = P.W + size_t(P.piv[q]) * P.ldw;
-    for (int i = lane; i < keff; i += 32) b[i] = cj[i];
-    __syncwarp();
-    for (int i = keff - 1; i >= 0; --i) {
-      const double* Ri = inR ? R + size_t(i) * keff : P.W + size_t(P.piv[i]) * P.ldw;
-      const double ti = b[i] / Ri[i];
-      __syncwarp();
-      for (int l = lane; l < i; l += 32) b[l] -= Ri[l] * ti;
-      if (lane == 0) b[i] = ti;
-      __syncwarp();
-    }
-    for (int i = lane; i < keff; i += 32) cj[i] = b[i];
-    __syncwarp();
+  double* out = P.W + size_t(P.piv[q0 + min(c, ncols - 1)]) * P.ldw;
+  const bool act = c < ncols;
+  for (int i = keff - 1; i >= 0; --i) {
+    const double ti = B[size_t(i) * TS_COLS + c] * dinv[i];
+    const double* Ri = inR ? R + size_t(i) * (i + 1) / 2 : P.W + size_t(P.piv[i]) * P.ldw;
+    for (int l = rg; l < i; l += nrg) B[size_t(l) * TS_COLS + c] -= Ri[l] * ti;
+    if (act && rg == i % nrg) out[i] = ti;
+    __syncthreads();
   }
 }
 
@@ -1056,6 +1239,8 @@ static void init_smem_limits() {
     e[2] = cudaFuncSetAttribute(k_id_tsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     e[3] = cudaFuncSetAttribute(k_cpqr_id<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     for (cudaError_t x : e) if (x != cudaSuccess) err = x;
+    cudaError_t g0 = cudaFuncSetAttribute(k_cpqr_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (g0 != cudaSuccess) err = g0;
     cudaError_t f0 = cudaFuncSetAttribute(k_inverse_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaError_t f1 = cudaFuncSetAttribute(k_inverse_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (f0 != cudaSuccess) err = f0;
@@ -1063,6 +1248,8 @@ static void init_smem_limits() {
   });
   if (err != cudaSuccess) throw Error(RW_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
 }
+
+namespace { int sm_count(); }
 
 void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
   std::vector<GemmWork> ws;
@@ -1082,14 +1269,15 @@ void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
   }
   if (ws.empty()) return;
   // Split long inner dimensions when the output tiles alone cannot fill the
-  // GPU (two CTAs per SM); partial sums are added in a fixed order.
+  // GPU (three CTAs per SM: one CTA runs at the SM's FP64 rate, so a launch
+  // with fewer CTAs than SMs leaves FP64 units idle); chunks of at least 64,
+  // partial sums added in a fixed order.
   size_t scratch = 0;
-  const long long target = 2 * 152;
+  const long long target = 3LL * sm_count();
   for (auto& w : ws) {
     const long long tiles = (long long)w.tilesM * w.tilesN;
-    if (tiles_all < target && w.p.k >= 1024) {
-      int ns = int(std::min<long long>(std::max<long long>(1, target / std::max<long long>(tiles_all, 1)),
-                                       (w.p.k + 511) / 512));
+    if (tiles_all < target && w.p.k >= 128) {
+      int ns = int(std::min<long long>((target + tiles_all - 1) / std::max<long long>(tiles_all, 1), w.p.k / 64));
       ns = std::min(ns, 64);
       if (ns > 1) {
         w.kchunk = ((w.p.k + ns - 1) / ns + GBK - 1) / GBK * GBK;
@@ -1314,78 +1502,170 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
     }
 }
 
-void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s) {
+namespace {
+int sm_count() {
+  static std::once_flag once;
+  static int n = 0;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+  });
+  if (n <= 0) throw Error(RW_ERR_CUDA, "cannot query the number of SMs");
+  return n;
+}
+
+// Finishes a no-swap factorisation of ng problems at probs[base..): pivot
+// bookkeeping and the interpolation coefficients T.
+void id_finish(const IdProb* dprobs, int base, const std::vector<IdProb>& ps, cudaStream_t s) {
+  int maxk = 0, maxnc = 0;
+  for (auto& p : ps) {
+    maxk = std::max(maxk, std::min(std::min(p.nr, p.nc), p.max_rank));
+    maxnc = std::max(maxnc, p.nc);
+  }
+  const int ng = int(ps.size());
+  ProfScope pf(KC_OTHER, s);
+  k_id_prep<<<ceil_div(32LL * ng, 128), 128, 0, s>>>(dprobs, base, ng);
+  RW_CHECK_LAUNCH();
+  // R11 in shared memory (packed) when the rank found is at most rmax
+  const int kk = std::max(maxk, 1);
+  const int rmax = std::min(kk, 200);
+  const size_t in_sm = size_t(rmax) * (rmax + 1) / 2 + size_t(rmax) * (TS_COLS + 1);
+  const size_t out_sm = size_t(kk) * (TS_COLS + 1);
+  const size_t tsm = std::max(in_sm, out_sm) * sizeof(double);
+  k_id_tsolve<<<dim3(ceil_div(maxnc, TS_COLS), ng), 256, tsm, s>>>(dprobs, base, rmax);
+  RW_CHECK_LAUNCH();
+}
+
+// Grid-wide plan for one problem: CTAs and columns per CTA, or false when
+// the columns cannot be spread over the SMs within the shared-memory cap.
+bool grid_id_plan(const IdProb& p, size_t cap, int* G, size_t* smem) {
+  const int nsm = sm_count();
+  if (std::min(p.nr, p.nc) > 1500) return false;  // T-solve staging bound
+  const int cw = ceil_div(p.nc, nsm);
+  const size_t b = (size_t(p.nr) * cw + size_t(p.nr) + 2 * size_t(cw)) * sizeof(double);
+  if (b > cap) return false;
+  *G = ceil_div(p.nc, cw);
+  *smem = b;
+  return true;
+}
+}  // namespace
+
+// A single problem with at least this many candidates goes to the grid-wide
+// factorisation (every SM works on it) instead of one thread-block cluster.
+constexpr int kGridIdMinCols = 256;
+
+bool grid_id_fits(int nr, int nc) {
+  IdProb p{};
+  p.nr = nr;
+  p.nc = nc;
+  int G = 0;
+  size_t smem = 0;
+  return nc >= kGridIdMinCols && nr > 0 && grid_id_plan(p, 200 * 1024, &G, &smem);
+}
+
+void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired) {
   if (probs_in.empty()) return;
+  if (probs_in.size() == 1 && probs_in[0].nc >= kGridIdMinCols && probs_in[0].nr > 0) {
+    int G = 0;
+    size_t smem = 0;
+    if (grid_id_plan(probs_in[0], 200 * 1024, &G, &smem)) {
+      init_smem_limits();
+      auto dp = to_device_tmp(probs_in, s);
+      TBuf<double> pub(4 * size_t(G) + 2 * size_t(G) * probs_in[0].nr, s);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(G));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      {
+        ProfScope ps(KC_ID, s);
+        RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_grid, (const IdProb*)dp.p, 0, pub.p, id_flops_counter()));
+        RW_CHECK_LAUNCH();
+      }
+      id_finish(dp.p, 0, probs_in, s);
+      return;
+    }
+  }
   // Route each problem: a thread-block cluster of CS in {1, 2, 4, 8} CTAs
   // whose shared memory holds the matrix, or the global-memory kernel.
+  // Pairs (paired: problems 2i and 2i+1) share one cluster of 2 CS <= 8 CTAs
+  // when both fit; otherwise they are routed one by one.
   const size_t cap = 200 * 1024;
-  std::vector<IdProb> grp[4], gl;
   const int sizes[4] = {1, 2, 4, 8};
-  for (IdProb p : probs_in) {
-    int g = -1;
-    for (int q = 0; q < 4 && g < 0; ++q) {
+  auto fitq = [&](const IdProb& p) {
+    for (int q = 0; q < 4; ++q) {
       const int cw = (p.nc + sizes[q] - 1) / sizes[q];
       const size_t b = (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double);
-      if (b <= cap && (q == 0 || p.nc >= 2 * sizes[q])) g = q;
+      if (b <= cap && (q == 0 || p.nc >= 2 * sizes[q])) return q;
     }
-    if (g >= 0) grp[g].push_back(p);
-    else gl.push_back(p);
+    return -1;
+  };
+  std::vector<IdProb> grp[4], pgrp[3], gl;
+  const size_t n = probs_in.size();
+  for (size_t i = 0; i < n;) {
+    if (paired && i + 1 < n) {
+      const int qa = fitq(probs_in[i]), qb = fitq(probs_in[i + 1]);
+      const int q = std::max(qa, qb);
+      if (qa >= 0 && qb >= 0 && q <= 2) {
+        pgrp[q].push_back(probs_in[i]);
+        pgrp[q].push_back(probs_in[i + 1]);
+        i += 2;
+        continue;
+      }
+    }
+    const int q = fitq(probs_in[i]);
+    if (q >= 0) grp[q].push_back(probs_in[i]);
+    else gl.push_back(probs_in[i]);
+    ++i;
   }
   std::vector<IdProb> all;
-  std::vector<int> base(5, 0);
+  std::vector<int> base(4, 0), pbase(3, 0);
   for (int q = 0; q < 4; ++q) { base[q] = int(all.size()); all.insert(all.end(), grp[q].begin(), grp[q].end()); }
-  base[4] = int(all.size());
+  for (int q = 0; q < 3; ++q) { pbase[q] = int(all.size()); all.insert(all.end(), pgrp[q].begin(), pgrp[q].end()); }
+  const int gbase = int(all.size());
   all.insert(all.end(), gl.begin(), gl.end());
   init_smem_limits();
   auto dp = to_device_tmp(all, s);
-  for (int q = 0; q < 4; ++q) {
-    if (grp[q].empty()) continue;
-    const int CS = sizes[q];
+  auto launch = [&](const std::vector<IdProb>& g, int b0, int CS, int pr) {
+    if (g.empty()) return;
     size_t smem = 0;
-    int maxnr = 0;
-    for (auto& p : grp[q]) {
+    for (auto& p : g) {
       const int cw = (p.nc + CS - 1) / CS;
       smem = std::max(smem, (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double));
-      maxnr = std::max(maxnr, p.nr);
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(grp[q].size() * CS));
+    cfg.gridDim = dim3(unsigned(g.size() * CS));
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.x = CS * (pr ? 2 : 1);
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     {
       ProfScope ps(KC_ID, s);
-      RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_cluster, (const IdProb*)dp.p, base[q], CS, id_flops_counter()));
+      RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_cluster, (const IdProb*)dp.p, b0, CS, pr, id_flops_counter()));
       RW_CHECK_LAUNCH();
     }
-    int maxk = 0, maxnc = 0;
-    for (auto& p : grp[q]) {
-      maxk = std::max(maxk, std::min(std::min(p.nr, p.nc), p.max_rank));
-      maxnc = std::max(maxnc, p.nc);
-    }
-    const int ng = int(grp[q].size());
-    ProfScope pf(KC_OTHER, s);
-    k_id_prep<<<ceil_div(32LL * ng, 128), 128, 0, s>>>(dp.p, base[q], ng);
-    RW_CHECK_LAUNCH();
-    const int rmax = 150;  // R11 in shared memory up to 150 x 150
-    const int kk = std::max(maxk, 1);
-    const size_t tsm = ((kk <= rmax ? size_t(kk) * kk : 0) + 8 * size_t(kk)) * sizeof(double);
-    k_id_tsolve<<<dim3(ceil_div(maxnc, TS_COLS), ng), 256, tsm, s>>>(dp.p, base[q], kk <= rmax ? rmax : 0);
-    RW_CHECK_LAUNCH();
-  }
+    id_finish(dp.p, b0, g, s);
+  };
+  for (int q = 0; q < 4; ++q) launch(grp[q], base[q], sizes[q], 0);
+  for (int q = 0; q < 3; ++q) launch(pgrp[q], pbase[q], sizes[q], 1);
   if (!gl.empty()) {
     size_t gl_bytes = 0;
     for (auto& p : gl) gl_bytes = std::max(gl_bytes, size_t(p.nr) * sizeof(double));
     require(gl_bytes <= cap, "batched_id: more than 25600 feature rows");
     ProfScope pg(KC_ID, s);
-    k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, s>>>(dp.p, base[4], id_flops_counter());
+    k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, s>>>(dp.p, gbase, id_flops_counter());
     RW_CHECK_LAUNCH();
   }
 }

@@ -92,7 +92,12 @@ struct IdProb {
 };
 // Work entries needed in IdProb::norms for a problem with nc candidates.
 inline size_t id_norms_elems(int nc) { return 2 * size_t(nc) + 4; }
-void batched_id(const std::vector<IdProb>& probs, cudaStream_t s);
+// paired: probs[2i] and probs[2i+1] are factorised together with a joint
+// stopping rule (both end at the larger of their two ranks).
+void batched_id(const std::vector<IdProb>& probs, cudaStream_t s, bool paired = false);
+// True when one problem of nr x nc goes to the grid-wide factorisation
+// (batched_id with a single problem).
+bool grid_id_fits(int nr, int nc);
 
 // Writes P (nc x rank) for factorisations finished by batched_id (P may have
 // been null there).  max_elems bounds nc * rank over the list.

@@ -101,7 +101,7 @@ void IdBatch::run(const NodesView& S, const NodesView& E1, bool e1s, const Nodes
     q.rank = rank.p + id;
     ip.push_back(q);
   }
-  batched_id(ip, s);
+  batched_id(ip, s, paired && subset_in.empty());
   h_rank = rank.download(s);
   h_rank.resize(nj);
 }
@@ -131,6 +131,8 @@ void IdBatch::interp(const std::vector<double*>& P, const std::vector<int>& ldp,
 std::vector<int> IdBatch::pivots(cudaStream_t s) const { return piv.download(s); }
 
 // ====================================================================== tree ID
+// Largest level (number of problems) that is merged into a single root.
+constexpr int kRootMergeJobs = 256;
 namespace {
 __global__ void k_gather_cols(const double* Z, int nr, const int* cand, int n, double* W) {
   for (int c = blockIdx.x; c < n; c += gridDim.x)
@@ -177,7 +179,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
 
   // level structure: each job has candidate positions (into rows) and the
   // indices of its child jobs in the previous level
-  struct TJob { std::vector<int> cand; int c0 = -1, c1 = -1; int k = 0; std::vector<int> skel; size_t poff = 0; };
+  struct TJob { std::vector<int> cand; std::vector<int> ch; int k = 0; std::vector<int> skel; size_t poff = 0; };
   std::vector<std::vector<TJob>> levels;
   std::vector<DBuf<double>> Pl;  // per level: interpolation matrices (m_j x k_j, ld m_j)
   std::vector<TJob> cur;
@@ -243,14 +245,32 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
     levels.push_back(cur);
     tr.mark(cur.size() == 1 ? "level (root)" : "level");
     if (cur.size() == 1) break;
+    // Next level: pairwise merges while the level has enough problems to
+    // occupy the GPU; once it has few, one root over every remaining
+    // skeleton (one wide problem that the grid-wide factorisation spreads
+    // over all SMs) replaces the remaining levels of narrow problems.
+    size_t nsk = 0;
+    for (auto& j : cur) nsk += j.skel.size();
+    const bool wide_root = cur.size() > 2 && cur.size() <= size_t(kRootMergeJobs) && grid_id_fits(nr, int(nsk));
     std::vector<TJob> nxt;
-    for (size_t b = 0; b < cur.size(); b += 2) {
+    if (wide_root) {
       TJob j;
-      j.c0 = int(b);
-      j.c1 = (b + 1 < cur.size()) ? int(b + 1) : -1;
-      j.cand = cur[b].skel;
-      if (j.c1 >= 0) j.cand.insert(j.cand.end(), cur[b + 1].skel.begin(), cur[b + 1].skel.end());
+      for (size_t b = 0; b < cur.size(); ++b) {
+        j.ch.push_back(int(b));
+        j.cand.insert(j.cand.end(), cur[b].skel.begin(), cur[b].skel.end());
+      }
       nxt.push_back(j);
+    } else {
+      for (size_t b = 0; b < cur.size(); b += 2) {
+        TJob j;
+        j.ch.push_back(int(b));
+        j.cand = cur[b].skel;
+        if (b + 1 < cur.size()) {
+          j.ch.push_back(int(b + 1));
+          j.cand.insert(j.cand.end(), cur[b + 1].skel.begin(), cur[b + 1].skel.end());
+        }
+        nxt.push_back(j);
+      }
     }
     // keep the (small) sync-free guard: wait for this level's buffers before reuse
     cur = nxt;
@@ -285,8 +305,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
     for (size_t pb = 0; pb < par.size(); ++pb) {
       const int mp = int(par[pb].cand.size());
       int slice = 0;
-      for (int cidx : {par[pb].c0, par[pb].c1}) {
-        if (cidx < 0) continue;
+      for (int cidx : par[pb].ch) {
         const TJob& c = ch[cidx];
         const double* M = Wm[lv].p + wpar[pb] + slice;  // rows slice of the parent's map, ld mp
         double* C;
@@ -388,6 +407,7 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
     }
     DBuf<int> didx = to_device(idx, s);
     IdBatch batch;
+    batch.paired = true;
     for (int t = 0; t < nn; ++t) {
       const double R = o.proxy_ratio * geo[t].rad;
       for (int kind = 0; kind < 2; ++kind) {
@@ -408,6 +428,7 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
       }
     }
     batch.run(V, V, true, V, true, o.id_tol, {}, {}, {}, {}, o.seed + l, s);
+    tr.mark("  level IDs");
     std::vector<int> kfix(2 * nn), redo, minr(2 * nn, 0), maxr(2 * nn);
     for (int t = 0; t < nn; ++t) {
       int k = std::max(batch.h_rank[2 * t], batch.h_rank[2 * t + 1]);
@@ -420,6 +441,7 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
       }
     }
     if (!redo.empty()) batch.run(V, V, true, V, true, 0.0, {}, redo, minr, maxr, o.seed + l, s);
+    tr.mark("  level IDs at the common rank");
     // storage for U (m x k), V (m x k -> transposed to Vt)
     Level& LV = lev[l];
     LV.oU.resize(nn); LV.oVt.resize(nn);

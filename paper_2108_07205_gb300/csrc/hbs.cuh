@@ -42,6 +42,9 @@ class IdBatch {
   DBuf<double> W, norms;
   DBuf<int> piv, rank;
   std::vector<int> h_rank;
+  // Jobs 2i and 2i+1 are a node's row and column IDs: a run over all jobs
+  // factors each pair with a joint stopping rule (both at the larger rank).
+  bool paired = false;
 
   int add(const IdMatProb& spec, int sketch_cols, int sketch_width);
   // Evaluate (all jobs, or the listed subset) and factor.  min_rank/max_rank
@@ -60,7 +63,9 @@ class IdBatch {
 // columns given by a column spec as in IdMatProb): chunks of `chunk` rows are
 // decomposed independently and merged pairwise up a binary tree, so that the
 // cost stays linear in the number of rows (Sec. 3.3, the hierarchical ID of the
-// far field).  Absolute tolerance = tol * max row norm of Y (Def. 3.1 with
+// far field); once a level has few problems, one root over all of their
+// skeletons (a single wide problem for the grid-wide factorisation) ends the
+// tree.  Absolute tolerance = tol * max row norm of Y (Def. 3.1 with
 // ||Y|| bounded below by its largest row norm).
 struct TreeId {
   int k = 0;

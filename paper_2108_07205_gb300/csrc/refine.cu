@@ -19,6 +19,7 @@
 #include "refine.cuh"
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <exception>
 #include <thread>
 
@@ -179,7 +180,10 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   RW_CUDA(cudaStreamCreateWithFlags(&streams.s2, cudaStreamNonBlocking));
   cudaStream_t s1 = streams.s1, s2 = streams.s2;
   std::exception_ptr e1, e2;
-  std::thread th1([&] {
+  // RW_SERIAL_REFINE=1 (diagnostics): run the three tasks one after another
+  const char* ser = std::getenv("RW_SERIAL_REFINE");
+  const bool serial = ser && ser[0] == '1';
+  auto task1 = [&] {
     AllocStreamScope scope1(s1);
     try {
       Opts opp = o;
@@ -189,8 +193,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       hpp.make_fp32(s1);
       RW_CUDA(cudaStreamSynchronize(s1));
     } catch (...) { e1 = std::current_exception(); }
-  });
-  std::thread th2([&] {
+  };
+  auto task2 = [&] {
     AllocStreamScope scope2(s2);
     try {
       // far rows of I_k against P^bas (shared by A_kc and A_kp)
@@ -198,7 +202,22 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
       tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 64, s2);
     } catch (...) { e2 = std::current_exception(); }
-  });
+  };
+  std::thread th1, th2;
+  // every exit from here on (including a throw) waits for the side threads
+  struct Joiner {
+    std::thread& t;
+    ~Joiner() { if (t.joinable()) t.join(); }
+  } join1{th1}, join2{th2};
+  if (serial) {
+    task1();
+    tr.mark("  A_pp inverse (HBS)");
+    task2();
+    tr.mark("  far ID");
+  } else {
+    th1 = std::thread(task1);
+    th2 = std::thread(task2);
+  }
   std::exception_ptr e0;
   try {
     // near rows of I_k: [A_kc^near | A_kp^near]
@@ -216,12 +235,13 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 64, s);
     }
   } catch (...) { e0 = std::current_exception(); }
-  th1.join();
-  th2.join();
-  RW_CUDA(cudaStreamSynchronize(s1));
+  if (serial) tr.mark("  near + A_pk IDs");
+  // X_o = A_oo^{-1} L_o needs only the far and near IDs: it runs on the main
+  // stream while A_pp^{-1} may still be in construction on its own stream
+  if (th2.joinable()) th2.join();
   RW_CUDA(cudaStreamSynchronize(s2));
-  for (auto& e : {e0, e1, e2}) if (e) std::rethrow_exception(e);
-  tr.mark("A_pp inverse + IDs (concurrent)");
+  for (auto& e : {e0, e2}) if (e) std::rethrow_exception(e);
+  tr.mark("IDs (concurrent with A_pp)");
   kf = tf.k; kn = tn.k; kpk = tp.k; kk = kf + kn; k = kk + kpk;
 
   // L_o (2No x kk) and L_p (2Np x kpk)
@@ -234,6 +254,9 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     Lp = std::move(tp.P);
     RW_CUDA(cudaStreamSynchronize(s));
   }
+  // a5 (o part): X_o = A_oo^{-1} L_o
+  Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
+  if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
   // skeleton DOFs
   std::vector<int> Jk, Jpk;
   for (int i : tf.skel) Jk.push_back(far_d[i]);
@@ -251,13 +274,15 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     k_zero_cols<<<ceil_div((long long)kpk * 2 * Nc, 256), 256, 0, s>>>(Rpk.p, kpk, kpk, dc.p, 2 * Nc);
     RW_CHECK_LAUNCH();
   }
-  tr.mark("L, R assembly");
-  // a5: X = A~^{-1} L
-  Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
+  tr.mark("L, R assembly, X_o");
+  // a5 (p part): X_p = A_pp^{-1} L_p once A_pp^{-1} is built
+  if (th1.joinable()) th1.join();
+  RW_CUDA(cudaStreamSynchronize(s1));
+  if (e1) std::rethrow_exception(e1);
+  tr.mark("A_pp inverse (joined)");
   Xp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
-  if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
   if (kpk) hpp.apply_inverse_levels(Lp.p, Xp.p, kpk, s);
-  tr.mark("X = A~^-1 L");
+  tr.mark("X_p = A_pp^-1 L_p");
   // a6: W = I + R X and its inverse
   {
     TBuf<double> W(size_t(k) * k, s), Ww(size_t(k) * k, s), Xc(size_t(2) * Nc * std::max(kk, 1), s);
