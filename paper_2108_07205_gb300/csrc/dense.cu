@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(256) k_inverse_cluster(const InvProb* probs, i
   const int cw = (n + CS - 1) / CS;
   const int c0 = crank * cw, c1 = min(n, c0 + cw), ncl = max(0, c1 - c0);
   extern __shared__ double smem[];
-  double* colc = smem;                       // n: published multipliers (owner) / local copy
-  double* mine = colc + n;                   // n: local copy of the multipliers
+  double* colc = smem;                       // 2 x n: published pivot column (owner), by step parity
+  double* mine = colc + 2 * n;               // n: local copy of the multipliers
   int* ipiv = reinterpret_cast<int*>(mine + n);  // n
   double* Ml = reinterpret_cast<double*>(ipiv + ((n + 1) & ~1));  // n x cw (SM)
   double* M;
@@ -468,8 +468,8 @@ __global__ void __launch_bounds__(256) k_inverse_cluster(const InvProb* probs, i
   if (SM) { M = Ml; ld = n; } else { M = P.Ainv + size_t(c0) * P.ldinv; ld = P.ldinv; }
   __shared__ double sval[32];
   __shared__ int sidx[32];
-  __shared__ double pub_val, pub_invp;
-  __shared__ int pub_p, g_p, s_flag;
+  __shared__ double pub_val, pub_pv[2];
+  __shared__ int pub_p[2], g_p, s_flag;
   if (tid == 0) s_flag = 0;
   // load my columns, max |A| over my columns
   double amax = 0.0;
@@ -491,29 +491,35 @@ __global__ void __launch_bounds__(256) k_inverse_cluster(const InvProb* probs, i
   __syncthreads();
   const double tiny = 1e-14 * sval[31];
   cluster.sync();  // pub_val is reused below
+  // One cluster barrier per column: the owner publishes the column as it
+  // is (before the row interchange) with its pivot row, double-buffered by
+  // step parity; every CTA applies the interchange while copying it.
   for (int c = 0; c < n; ++c) {
-    const int owner = c / cw;
+    const int owner = c / cw, par = c & 1;
     if (crank == owner) {
       const int jl = c - c0;
+      const double* mc = M + size_t(jl) * ld;
       double v = -1.0;
       int idx = 0x7fffffff;
       for (int r = c + tid; r < n; r += nt) {
-        const double a = fabs(M[r + size_t(jl) * ld]);
+        const double a = fabs(mc[r]);
         if (a > v) { v = a; idx = r; }
       }
       int p;
       const double pv = block_reduce_max_abs_arg(v, idx, &p, sval, sidx);
-      if (tid == 0) { pub_p = p; pub_val = pv; }
+      double* pub = colc + size_t(par) * n;
+      for (int r = tid; r < n; r += nt) pub[r] = mc[r];
+      if (tid == 0) { pub_p[par] = p; pub_pv[par] = pv; }
     }
     cluster.sync();
+    const int p = *cluster.map_shared_rank(&pub_p[par], owner);
     if (tid == 0) {
-      g_p = *cluster.map_shared_rank(&pub_p, owner);
-      const double pv = *cluster.map_shared_rank(&pub_val, owner);
-      if (!(pv > tiny)) s_flag = 1;
-      ipiv[c] = g_p;
+      if (!(*cluster.map_shared_rank(&pub_pv[par], owner) > tiny)) s_flag = 1;
+      ipiv[c] = p;
     }
-    __syncthreads();
-    const int p = g_p;
+    const double* rc = cluster.map_shared_rank(colc + size_t(par) * n, owner);
+    const double invp = 1.0 / rc[p];
+    for (int r = tid; r < n; r += nt) mine[r] = (r == c) ? 0.0 : rc[r == p ? c : r];
     if (p != c)
       for (int j = tid; j < ncl; j += nt) {
         double* mj = M + size_t(j) * ld;
@@ -521,19 +527,6 @@ __global__ void __launch_bounds__(256) k_inverse_cluster(const InvProb* probs, i
         mj[c] = mj[p];
         mj[p] = t;
       }
-    __syncthreads();
-    if (crank == owner) {
-      const int jl = c - c0;
-      const double* mc = M + size_t(jl) * ld;
-      for (int r = tid; r < n; r += nt) colc[r] = (r == c) ? 0.0 : mc[r];
-      if (tid == 0) pub_invp = 1.0 / mc[c];
-    }
-    cluster.sync();
-    {
-      const double* rc = cluster.map_shared_rank(colc, owner);
-      for (int r = tid; r < n; r += nt) mine[r] = rc[r];
-    }
-    const double invp = *cluster.map_shared_rank(&pub_invp, owner);
     __syncthreads();
     for (int j = warp; j < ncl; j += nw) {
       double* mj = M + size_t(j) * ld;
@@ -982,31 +975,57 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
   cluster.sync();  // keep shared memory alive until remote readers are done
 }
 
-// Grid-wide variant for one wide problem (hundreds to thousands of
-// candidates): a cooperative grid of G CTAs, CTA b keeping candidate columns
-// [b cw, (b+1) cw) in its shared memory.  One grid barrier per pivot step:
-// every CTA publishes its local norm maximum together with that column
-// (double-buffered by step parity), the barrier makes them visible, and every
-// CTA then picks the same global pivot, forms the same Householder vector from
-// the published column and updates its own columns.  Same no-swap layout and
-// outputs as the cluster variant.  pub holds 4 G + 2 G nr doubles.
-__global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int idx, double* pub, double* flops_out) {
+// Grid-wide variant for a few problems (one to a few dozen, hundreds to
+// thousands of candidates each): one cooperative grid, problem p owning the
+// CTAs [b0_p, b0_p + G_p); CTA b keeps candidate columns [r cw_p,
+// (r+1) cw_p) of its problem (r = b - b0_p) in shared memory.  One grid
+// barrier per pivot step: every CTA publishes its local norm maximum
+// together with that column (double-buffered by step parity); after the
+// barrier every CTA reads all published maxima, so every CTA takes the same
+// decisions for every problem, forms its problem's Householder vector from
+// the published pivot column and updates its own columns.  Paired mode:
+// problems 2i and 2i+1 stop jointly, as in the cluster variant.  Same
+// no-swap layout and outputs.  pub holds 4 G + 2 G nr_max doubles.
+constexpr int kGridIdMaxProbs = 64;
+constexpr int kGridIdMaxCtas = 256;
+__global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int base, int np, const int* parts,
+                                                   int paired, int nr_max, double* pub, double* flops_out) {
   cg::grid_group grid = cg::this_grid();
-  const IdProb P = probs[idx];
   const int G = gridDim.x, b = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  __shared__ int s_b0[kGridIdMaxProbs], s_G[kGridIdMaxProbs], s_s[kGridIdMaxProbs], s_own[kGridIdMaxProbs];
+  __shared__ int s_idx[kGridIdMaxProbs], s_act[kGridIdMaxProbs], s_soft[kGridIdMaxProbs], s_hard[kGridIdMaxProbs];
+  __shared__ int s_mx[kGridIdMaxProbs], s_minr[kGridIdMaxProbs];
+  __shared__ double s_val[kGridIdMaxProbs], s_ref[kGridIdMaxProbs], s_tabs[kGridIdMaxProbs], s_trel[kGridIdMaxProbs];
+  __shared__ double slot_v[kGridIdMaxCtas];
+  __shared__ int slot_i[kGridIdMaxCtas];
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  for (int q = tid; q < np; q += nt) {
+    const IdProb& Q = probs[base + q];
+    s_b0[q] = parts[2 * q];
+    s_G[q] = parts[2 * q + 1];
+    s_s[q] = 0;
+    s_act[q] = 1;
+    s_ref[q] = 0.0;
+    s_mx[q] = (Q.nr <= 0 || Q.nc <= 0) ? 0 : min(min(Q.nr, Q.nc), Q.max_rank);
+    s_minr[q] = Q.min_rank;
+    s_tabs[q] = Q.tol_abs;
+    s_trel[q] = Q.tol_rel;
+  }
+  __syncthreads();
+  int me = 0;
+  while (me + 1 < np && b >= s_b0[me + 1]) ++me;
+  const IdProb P = probs[base + me];
+  const int Gp = s_G[me], lr = b - s_b0[me];
   const int nr = P.nr, nc = P.nc;
-  const int cw = (nc + G - 1) / G;
-  const int c0 = min(nc, b * cw), c1 = min(nc, c0 + cw), ncl = max(0, c1 - c0);
+  const int cw = (nc + Gp - 1) / Gp;
+  const int c0 = min(nc, lr * cw), c1 = min(nc, c0 + cw), ncl = max(0, c1 - c0);
   extern __shared__ double smem[];
   double* Wl = smem;                    // nr x cw
   double* vloc = Wl + size_t(nr) * cw;  // nr
   double* nrm = vloc + nr;              // cw
   double* nrm0 = nrm + cw;              // cw
-  __shared__ double sval[32];
-  __shared__ int sidx[32];
-  __shared__ double g_val;
-  __shared__ int g_idx, g_blk;
   for (int e = tid; e < nr * ncl; e += nt) {
     const int i = e % nr, j = e / nr;
     Wl[i + size_t(j) * nr] = P.W[i + size_t(c0 + j) * P.ldw];
@@ -1019,21 +1038,21 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int idx,
     if (lane == 0) { nrm[j] = sqrt(s); nrm0[j] = nrm[j]; }
   }
   __syncthreads();
-  const int maxsteps = (nr <= 0 || nc <= 0) ? 0 : min(min(nr, nc), P.max_rank);
   const double tol3z = sqrt(2.220446049250313e-16);
   int G2 = 32;
   while (G2 > 1 && (nt / G2) < ncl) G2 >>= 1;
   const int ncl_pad = (ncl + (nt / G2) - 1) / (nt / G2) * (nt / G2);
-  double ref = 0.0;
-  int s = 0;
-  for (; s < maxsteps; ++s) {
-    const int par = s & 1;
+  for (int it = 0;; ++it) {
+    const int par = it & 1;
     double* pv = pub + size_t(par) * G;
     double* pi = pub + 2 * size_t(G) + size_t(par) * G;
-    double* pcol = pub + 4 * size_t(G) + (size_t(par) * G + b) * nr;
+    double* pcol = pub + 4 * size_t(G) + (size_t(par) * G + b) * nr_max;
+    const bool act = s_act[me] != 0;
+    const int s = s_s[me];
     double v = -1.0;
     int id = 0x7fffffff;
-    for (int j = tid; j < ncl; j += nt) if (nrm[j] > v) { v = nrm[j]; id = c0 + j; }
+    if (act)
+      for (int j = tid; j < ncl; j += nt) if (nrm[j] > v) { v = nrm[j]; id = c0 + j; }
     int p;
     const double lm = block_reduce_max_abs_arg(v, id, &p, sval, sidx);
     if (lm >= 0.0) {
@@ -1043,13 +1062,21 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int idx,
     if (tid == 0) { pv[b] = lm; pi[b] = double(lm >= 0.0 ? p : 0x7fffffff); }
     __threadfence();
     grid.sync();
-    if (warp == 0) {
+    // every CTA's published maximum into shared memory (one pass), then
+    // every problem's maximum (warp q % nw reduces problem q)
+    for (int q = tid; q < G; q += nt) {
+      slot_v[q] = __ldcg(pv + q);
+      slot_i[q] = int(__ldcg(pi + q));
+    }
+    __syncthreads();
+    for (int q = warp; q < np; q += nw) {
       double bv = -1.0;
       int bi = 0x7fffffff, bb = 0;
-      for (int q = lane; q < G; q += 32) {
-        const double ov = __ldcg(pv + q);
-        const int oi = int(__ldcg(pi + q));
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bb = q; }
+      for (int r = lane; r < s_G[q]; r += 32) {
+        const int slot = s_b0[q] + r;
+        const double ov = slot_v[slot];
+        const int oi = slot_i[slot];
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bb = slot; }
       }
       for (int off = 16; off > 0; off >>= 1) {
         const double ov = __shfl_down_sync(0xffffffffu, bv, off);
@@ -1057,48 +1084,65 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int idx,
         const int ob = __shfl_down_sync(0xffffffffu, bb, off);
         if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bb = ob; }
       }
-      if (lane == 0) { g_val = bv; g_idx = bi; g_blk = bb; }
+      if (lane == 0) { s_val[q] = bv; s_idx[q] = bi; s_own[q] = bb; }
     }
     __syncthreads();
-    const double vmax = g_val;
-    const int pg = g_idx, owner = g_blk;
-    if (s == 0) ref = vmax;
-    const double thr = fmax(P.tol_abs, P.tol_rel * ref);
-    if (vmax <= 0.0 || (s >= P.min_rank && vmax <= thr)) break;
-    if (b == 0 && tid == 0) P.piv[s] = pg;
-    // Householder vector of the published pivot column (the same arithmetic
-    // in every CTA, so every CTA holds the same reflector)
-    const double* col = pub + 4 * size_t(G) + (size_t(par) * G + owner) * nr;
-    double part = 0.0;
-    for (int i = s + 1 + tid; i < nr; i += nt) { const double x = __ldcg(col + i); part += x * x; }
-    const double xn2 = block_reduce_sum(part, sval);
-    const double alpha = __ldcg(col + s);
-    double tau = 0.0, sc = 0.0, beta = alpha;
-    if (xn2 != 0.0) {
-      beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-      tau = (beta - alpha) / beta;
-      sc = 1.0 / (alpha - beta);
+    // the same decisions in every CTA: soft = tolerance met (or no further
+    // step possible), hard = no further step possible
+    if (tid < np) {
+      const int q = tid;
+      if (it == 0) s_ref[q] = s_val[q];
+      const bool hard = !s_act[q] || s_s[q] >= s_mx[q] || s_val[q] <= 0.0;
+      s_hard[q] = hard;
+      s_soft[q] = hard || (s_s[q] >= s_minr[q] && s_val[q] <= fmax(s_tabs[q], s_trel[q] * s_ref[q]));
     }
-    for (int i = s + 1 + tid; i < nr; i += nt) vloc[i] = __ldcg(col + i) * sc;
     __syncthreads();
-    if (b == owner) {
-      const int jl = pg - c0;
-      double* cp = Wl + size_t(jl) * nr;
-      for (int i = s + 1 + tid; i < nr; i += nt) cp[i] = vloc[i];
-      if (tid == 0) { cp[s] = beta; nrm[jl] = -1.0; }
+    int act_q = 0;
+    if (tid < np) {
+      const int q = tid, qp = ((q ^ 1) < np) ? (q ^ 1) : q;
+      const bool stop = paired ? (s_soft[q] && s_soft[qp]) : s_soft[q];
+      act_q = !(stop || s_hard[q]);
+    }
+    __syncthreads();
+    if (tid < np) s_act[tid] = act_q;
+    if (!__syncthreads_or(act_q)) break;
+    if (s_act[me]) {
+      const int pg = s_idx[me], owner = s_own[me];
+      if (lr == 0 && tid == 0) P.piv[s] = pg;
+      const double* col = pub + 4 * size_t(G) + (size_t(par) * G + owner) * nr_max;
+      double part = 0.0;
+      for (int i = s + 1 + tid; i < nr; i += nt) { const double x = __ldcg(col + i); part += x * x; }
+      const double xn2 = block_reduce_sum(part, sval);
+      const double alpha = __ldcg(col + s);
+      double tau = 0.0, sc = 0.0, beta = alpha;
+      if (xn2 != 0.0) {
+        beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        tau = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+      }
+      for (int i = s + 1 + tid; i < nr; i += nt) vloc[i] = __ldcg(col + i) * sc;
       __syncthreads();
+      if (b == owner) {
+        const int jl = pg - c0;
+        double* cp = Wl + size_t(jl) * nr;
+        for (int i = s + 1 + tid; i < nr; i += nt) cp[i] = vloc[i];
+        if (tid == 0) { cp[s] = beta; nrm[jl] = -1.0; }
+        __syncthreads();
+      }
+      cpqr_update_columns(Wl, nr, ncl, ncl_pad, G2, s, tau, vloc, nrm, nrm0, tol3z);
     }
-    cpqr_update_columns(Wl, nr, ncl, ncl_pad, G2, s, tau, vloc, nrm, nrm0, tol3z);
+    __syncthreads();
+    if (tid < np && s_act[tid]) s_s[tid] += 1;
     __syncthreads();
   }
-  // every CTA leaves the loop at the same s (same published data, same decisions)
+  const int s = s_s[me];
   for (int e = tid; e < nr * ncl; e += nt) {
     const int i = e % nr, j = e / nr;
     P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * nr];
   }
   for (int j = tid; j < ncl; j += nt) P.norms[nc + c0 + j] = (nrm[j] < 0.0) ? -1.0 : 1.0;
-  if (b == 0 && tid == 0) {
-    P.norms[2 * nc + 1] = double(s); P.norms[2 * nc + 2] = ref; P.norms[2 * nc + 3] = 1.0;
+  if (lr == 0 && tid == 0) {
+    P.norms[2 * nc + 1] = double(s); P.norms[2 * nc + 2] = s_ref[me]; P.norms[2 * nc + 3] = 1.0;
     if (flops_out) {
       double f = 0.0;
       for (int q = 0; q < s; ++q) f += 4.0 * double(nr - q) * double(nc - q - 1);
@@ -1272,13 +1316,18 @@ void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
   // GPU (three CTAs per SM: one CTA runs at the SM's FP64 rate, so a launch
   // with fewer CTAs than SMs leaves FP64 units idle); chunks of at least 64,
   // partial sums added in a fixed order.
+  // The chunk count of each problem follows its share of the work (tiles x
+  // inner dimension), so that the CTAs of one launch carry similar work.
   size_t scratch = 0;
   const long long target = 3LL * sm_count();
+  double tile_k = 0.0;
+  for (auto& w : ws) tile_k += double(w.tilesM) * w.tilesN * std::max(w.p.k, 1);
+  const double per_cta = tile_k / double(target);
   for (auto& w : ws) {
     const long long tiles = (long long)w.tilesM * w.tilesN;
     if (tiles_all < target && w.p.k >= 128) {
-      int ns = int(std::min<long long>((target + tiles_all - 1) / std::max<long long>(tiles_all, 1), w.p.k / 64));
-      ns = std::min(ns, 64);
+      int ns = int(std::min<double>(std::ceil(double(w.p.k) / std::max(per_cta, 1.0)), double(w.p.k / 64)));
+      ns = std::min(ns, 128);
       if (ns > 1) {
         w.kchunk = ((w.p.k + ns - 1) / ns + GBK - 1) / GBK * GBK;
         w.nsplit = (w.p.k + w.kchunk - 1) / w.kchunk;
@@ -1456,7 +1505,7 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
     const int q = p.n >= 192 ? 3 : p.n >= 96 ? 2 : 1;
     const int CS = sizes[q];
     const int cw = (p.n + CS - 1) / CS;
-    const size_t need = (2 * size_t(p.n) + size_t(p.n) * cw) * sizeof(double) + size_t(p.n + 2) * sizeof(int);
+    const size_t need = (3 * size_t(p.n) + size_t(p.n) * cw) * sizeof(double) + size_t(p.n + 2) * sizeof(int);
     if (need <= cap) cl_sm[q].push_back(p); else cl_gl[q].push_back(p);
   }
   init_smem_limits();
@@ -1478,7 +1527,7 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
       double fl = 0.0;
       for (auto& p : g) {
         const int cw = (p.n + CS - 1) / CS;
-        smem = std::max(smem, (2 * size_t(p.n) + (sm ? size_t(p.n) * cw : 0)) * sizeof(double) +
+        smem = std::max(smem, (3 * size_t(p.n) + (sm ? size_t(p.n) * cw : 0)) * sizeof(double) +
                                   size_t(p.n + 2) * sizeof(int));
         fl += 2.0 * double(p.n) * p.n * p.n;
       }
@@ -1537,58 +1586,115 @@ void id_finish(const IdProb* dprobs, int base, const std::vector<IdProb>& ps, cu
   RW_CHECK_LAUNCH();
 }
 
-// Grid-wide plan for one problem: CTAs and columns per CTA, or false when
-// the columns cannot be spread over the SMs within the shared-memory cap.
-bool grid_id_plan(const IdProb& p, size_t cap, int* G, size_t* smem) {
+// Grid-wide plan for a few problems: CTA ranges (b0, G_p) per problem, the
+// CTAs first covering each problem's shared-memory need and the rest shared
+// out in proportion to the problems' sizes; false when the problems do not
+// fit on the SMs within the shared-memory cap.
+bool grid_id_plan(const std::vector<IdProb>& ps, size_t cap, std::vector<int>& parts, int* G, size_t* smem,
+                  int* nr_max) {
+  const int np = int(ps.size());
+  if (np < 1 || np > kGridIdMaxProbs) return false;
   const int nsm = sm_count();
-  if (std::min(p.nr, p.nc) > 1500) return false;  // T-solve staging bound
-  const int cw = ceil_div(p.nc, nsm);
-  const size_t b = (size_t(p.nr) * cw + size_t(p.nr) + 2 * size_t(cw)) * sizeof(double);
-  if (b > cap) return false;
-  *G = ceil_div(p.nc, cw);
-  *smem = b;
-  return true;
+  std::vector<int> g(np);
+  long long need = 0;
+  double work = 0.0;
+  for (int q = 0; q < np; ++q) {
+    const IdProb& p = ps[q];
+    if (p.nr <= 0 || p.nc <= 0 || std::min(p.nr, p.nc) > 1500) return false;  // T-solve staging bound
+    const long long room = (long long)(cap / sizeof(double)) - p.nr;
+    const long long cwmax = room / (p.nr + 2);
+    if (cwmax < 1) return false;
+    g[q] = ceil_div(p.nc, cwmax);
+    need += g[q];
+    work += double(p.nr) * p.nc;
+  }
+  if (need > nsm || nsm > kGridIdMaxCtas) return false;
+  const long long spare = nsm - need;
+  for (int q = 0; q < np; ++q) {
+    const long long extra = (long long)(double(spare) * double(ps[q].nr) * ps[q].nc / work);
+    g[q] = int(std::min<long long>(g[q] + extra, ps[q].nc));
+  }
+  parts.assign(2 * np, 0);
+  int b0 = 0;
+  size_t sm = 0;
+  int nrm = 0;
+  for (int q = 0; q < np; ++q) {
+    const IdProb& p = ps[q];
+    const int cw = ceil_div(p.nc, g[q]);
+    g[q] = ceil_div(p.nc, cw);  // no CTA without columns
+    parts[2 * q] = b0;
+    parts[2 * q + 1] = g[q];
+    b0 += g[q];
+    sm = std::max(sm, (size_t(p.nr) * cw + size_t(p.nr) + 2 * size_t(cw)) * sizeof(double));
+    nrm = std::max(nrm, p.nr);
+  }
+  *G = b0;
+  *smem = sm;
+  *nr_max = nrm;
+  return sm <= cap;
+}
+
+void grid_id_run(const std::vector<IdProb>& ps, bool paired, const std::vector<int>& parts, int G, size_t smem,
+                 int nr_max, cudaStream_t s) {
+  init_smem_limits();
+  auto dp = to_device_tmp(ps, s);
+  auto dparts = to_device_tmp(parts, s);
+  TBuf<double> pub(4 * size_t(G) + 2 * size_t(G) * nr_max, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(G));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  {
+    ProfScope pr(KC_ID, s);
+    RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_grid, (const IdProb*)dp.p, 0, int(ps.size()), (const int*)dparts.p,
+                               paired ? 1 : 0, nr_max, pub.p, id_flops_counter()));
+    RW_CHECK_LAUNCH();
+  }
+  id_finish(dp.p, 0, ps, s);
 }
 }  // namespace
 
-// A single problem with at least this many candidates goes to the grid-wide
-// factorisation (every SM works on it) instead of one thread-block cluster.
-constexpr int kGridIdMinCols = 256;
+// Up to this many problems (with enough work between them to matter) go to
+// the grid-wide factorisation, every SM working on one of them, instead of
+// one thread-block cluster each.
+constexpr int kGridIdProbs = 32;
+constexpr double kGridIdMinWork = 32768.0;
+
+// RW_ID_GRID=0 (diagnostics) keeps every problem on thread-block clusters.
+static bool grid_id_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("RW_ID_GRID");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 
 bool grid_id_fits(int nr, int nc) {
   IdProb p{};
   p.nr = nr;
   p.nc = nc;
-  int G = 0;
+  std::vector<int> parts;
+  int G = 0, nrm = 0;
   size_t smem = 0;
-  return nc >= kGridIdMinCols && nr > 0 && grid_id_plan(p, 200 * 1024, &G, &smem);
+  return grid_id_enabled() && double(nr) * nc >= kGridIdMinWork && grid_id_plan({p}, 200 * 1024, parts, &G, &smem, &nrm);
 }
 
 void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired) {
   if (probs_in.empty()) return;
-  if (probs_in.size() == 1 && probs_in[0].nc >= kGridIdMinCols && probs_in[0].nr > 0) {
-    int G = 0;
+  if (int(probs_in.size()) <= kGridIdProbs && grid_id_enabled()) {
+    double work = 0.0;
+    for (auto& p : probs_in) work += double(p.nr) * p.nc;
+    std::vector<int> parts;
+    int G = 0, nrm = 0;
     size_t smem = 0;
-    if (grid_id_plan(probs_in[0], 200 * 1024, &G, &smem)) {
-      init_smem_limits();
-      auto dp = to_device_tmp(probs_in, s);
-      TBuf<double> pub(4 * size_t(G) + 2 * size_t(G) * probs_in[0].nr, s);
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(unsigned(G));
-      cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = s;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeCooperative;
-      attr[0].val.cooperative = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      {
-        ProfScope ps(KC_ID, s);
-        RW_CUDA(cudaLaunchKernelEx(&cfg, k_cpqr_grid, (const IdProb*)dp.p, 0, pub.p, id_flops_counter()));
-        RW_CHECK_LAUNCH();
-      }
-      id_finish(dp.p, 0, probs_in, s);
+    if (work >= kGridIdMinWork && grid_id_plan(probs_in, 200 * 1024, parts, &G, &smem, &nrm)) {
+      grid_id_run(probs_in, paired, parts, G, smem, nrm, s);
       return;
     }
   }

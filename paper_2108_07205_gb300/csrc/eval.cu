@@ -99,57 +99,118 @@ __global__ void k_nodes(Curve c, const double* ta, const double* tb, int n_int, 
   out[i + 5 * size_t(ld)] = (g.dx * g.ddy - g.dy * g.ddx) / (sp * sp * sp);
 }
 
-__device__ __forceinline__ double idmat_value(const IdMatProb& P, int c, int i, const NodesView& S,
-                                              const NodesView& E1, bool e1s, const NodesView& E2, bool e2s) {
-  const int d = P.cand[i];
-  const int ip = d >> 1, ia = d & 1;
-  if (c < P.n1) {
-    const int e = P.e1[c];
-    return P.kind == 0 ? a_entry(S, ip, ia, E1, e >> 1, e & 1, e1s) : a_entry(E1, e >> 1, e & 1, S, ip, ia, e1s);
+// The 2 x 2 block of A between a target point t and a source point s
+// (A(t a, s b) for a, b in {0, 1}): one distance, one division.
+struct Blk2 { double v[2][2]; };
+__device__ __forceinline__ Blk2 a_block(const NodesView& T, int t, const NodesView& Sv, int s, bool same_point) {
+  Blk2 o;
+  const double ntx = T.nx[t], nty = T.ny[t], nsx = Sv.nx[s], nsy = Sv.ny[s], ws = Sv.w[s];
+  const double nt[2] = {ntx, nty}, ns[2] = {nsx, nsy};
+  if (same_point) {
+    const double ta[2] = {-nty, ntx};
+    const double kap = T.kappa[t] * ws * (0.5 / kPi);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) o.v[a][b] = nt[a] * ns[b] * ws - kap * ta[a] * ta[b] - (a == b ? 0.5 : 0.0);
+  } else {
+    const double rx = T.x[t] - Sv.x[s], ry = T.y[t] - Sv.y[s];
+    const double inv = 1.0 / (rx * rx + ry * ry);
+    const double fac = ws * (rx * nsx + ry * nsy) * inv * inv * (1.0 / kPi);
+    const double r[2] = {rx, ry};
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) o.v[a][b] = nt[a] * ns[b] * ws + fac * r[a] * r[b];
   }
-  c -= P.n1;
-  if (c < P.n2) {
-    const int e = P.e2[c];
-    return P.kind == 0 ? a_entry(S, ip, ia, E2, e >> 1, e & 1, e2s) : a_entry(E2, e >> 1, e & 1, S, ip, ia, e2s);
-  }
-  c -= P.n2;
-  const int per = P.kind == 0 ? 4 : 2;
-  if (c < per * P.M) {
-    const int q = c / per, sub = c % per;
-    double sn, cs;
-    sincospi(2.0 * q / P.M, &sn, &cs);
-    const double zx = P.cx + P.R * cs, zy = P.cy + P.R * sn;
-    if (P.kind == 0) {
-      // field at x_i of a unit source at z_q: Stokeslet (sub 0, 1) or double
-      // layer with the circle's outward normal (sub 2, 3), component b
-      const double rx = S.x[ip] - zx, ry = S.y[ip] - zy, r2 = rx * rx + ry * ry;
-      const double ra = ia ? ry : rx;
-      if (sub < 2) {
-        const double rb = sub ? ry : rx;
-        return (1.0 / (4.0 * kPi)) * ((ia == sub ? -0.5 * log(r2) : 0.0) + ra * rb / r2);
-      }
-      const double rb = (sub - 2) ? ry : rx;
-      const double rdn = rx * cs + ry * sn;
-      return ra * rb * rdn / (kPi * r2 * r2);
-    } else {
-      // field at z_q, component a' = sub, of a unit density at x_i component ia
-      const double rx = zx - S.x[ip], ry = zy - S.y[ip], r2 = rx * rx + ry * ry;
-      const double rdn = rx * S.nx[ip] + ry * S.ny[ip];
-      const double fac = S.w[ip] * rdn / (kPi * r2 * r2);
-      return fac * (sub ? ry : rx) * (ia ? ry : rx);
-    }
-  }
-  // normal column
-  const double n = ia ? S.ny[ip] : S.nx[ip];
-  return P.kind == 0 ? n : n * S.w[ip];
+  return o;
 }
 
-__global__ void k_idmat(const IdMatProb* probs, NodesView S, NodesView E1, bool e1s, NodesView E2, bool e2s) {
+// Feature list section (entries of A against the DOFs e[0..n)): pairs of
+// consecutive entries that are the two components of one point share one
+// 2 x 2 block evaluation.
+__device__ __forceinline__ void idmat_section(const IdMatProb& P, double* Wc, int ip, int ia, const NodesView& S,
+                                              const int* e, int n, const NodesView& E, bool es) {
+  for (int cp = threadIdx.x; 2 * cp < n; cp += blockDim.x) {
+    const int c = 2 * cp;
+    const int e0 = e[c];
+    const bool pair = c + 1 < n && (e0 & 1) == 0 && e[c + 1] == e0 + 1;
+    if (pair) {
+      const int j = e0 >> 1;
+      const bool same = es && j == ip;
+      if (P.kind == 0) {
+        const Blk2 B = a_block(S, ip, E, j, same);
+        Wc[c] = B.v[ia][0];
+        Wc[c + 1] = B.v[ia][1];
+      } else {
+        const Blk2 B = a_block(E, j, S, ip, same);
+        Wc[c] = B.v[0][ia];
+        Wc[c + 1] = B.v[1][ia];
+      }
+    } else {
+      for (int q = c; q < min(n, c + 2); ++q) {
+        const int eq = e[q];
+        Wc[q] = P.kind == 0 ? a_entry(S, ip, ia, E, eq >> 1, eq & 1, es) : a_entry(E, eq >> 1, eq & 1, S, ip, ia, es);
+      }
+    }
+  }
+}
+
+// Rows of W (features) for the candidates of one problem per blockIdx.y:
+// near-field sections, then the proxy section (points tabulated once per
+// block; one distance, one division and at most one logarithm per proxy
+// point), then the normal column.
+__global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesView E1, bool e1s, NodesView E2,
+                        bool e2s) {
   const IdMatProb P = probs[blockIdx.y];
-  // rows of W (features) over x-threads, candidates over the grid
-  for (int i = blockIdx.x; i < P.m; i += gridDim.x)
-    for (int c = threadIdx.x; c < P.ncol; c += blockDim.x)
-      P.W[c + size_t(i) * P.ldw] = idmat_value(P, c, i, S, E1, e1s, E2, e2s);
+  extern __shared__ double ztab[];  // 4 x max_M
+  double* zx = ztab;
+  double* zy = ztab + max_M;
+  double* zc = ztab + 2 * max_M;
+  double* zs = ztab + 3 * max_M;
+  const int M = P.M;
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * q / M, &sn, &cs);
+    zx[q] = P.cx + P.R * cs;
+    zy[q] = P.cy + P.R * sn;
+    zc[q] = cs;
+    zs[q] = sn;
+  }
+  __syncthreads();
+  const int base = P.n1 + P.n2;
+  for (int i = blockIdx.x; i < P.m; i += gridDim.x) {
+    double* Wc = P.W + size_t(i) * P.ldw;
+    const int d = P.cand[i];
+    const int ip = d >> 1, ia = d & 1;
+    idmat_section(P, Wc, ip, ia, S, P.e1, P.n1, E1, e1s);
+    idmat_section(P, Wc + P.n1, ip, ia, S, P.e2, P.n2, E2, e2s);
+    const double xi = S.x[ip], yi = S.y[ip];
+    if (P.kind == 0) {
+      // field at x_i of unit sources at z_q: Stokeslet (columns 4q, 4q+1)
+      // and double layer with the circle's outward normal (4q+2, 4q+3)
+      for (int q = threadIdx.x; q < M; q += blockDim.x) {
+        const double rx = xi - zx[q], ry = yi - zy[q], r2 = rx * rx + ry * ry;
+        const double inv = 1.0 / r2, lg = -0.5 * log(r2), ra = ia ? ry : rx;
+        const double f = (rx * zc[q] + ry * zs[q]) * inv * inv * (1.0 / kPi);
+        double* w = Wc + base + 4 * q;
+        w[0] = (1.0 / (4.0 * kPi)) * ((ia == 0 ? lg : 0.0) + ra * rx * inv);
+        w[1] = (1.0 / (4.0 * kPi)) * ((ia == 1 ? lg : 0.0) + ra * ry * inv);
+        w[2] = ra * rx * f;
+        w[3] = ra * ry * f;
+      }
+    } else {
+      // field at z_q (components 2q, 2q+1) of a unit density at x_i
+      const double nxi = S.nx[ip], nyi = S.ny[ip], wi = S.w[ip];
+      for (int q = threadIdx.x; q < M; q += blockDim.x) {
+        const double rx = zx[q] - xi, ry = zy[q] - yi;
+        const double inv = 1.0 / (rx * rx + ry * ry);
+        const double fac = wi * (rx * nxi + ry * nyi) * inv * inv * (1.0 / kPi) * (ia ? ry : rx);
+        Wc[base + 2 * q] = fac * rx;
+        Wc[base + 2 * q + 1] = fac * ry;
+      }
+    }
+    if (P.normal && threadIdx.x == 0) {
+      const double n = ia ? S.ny[ip] : S.nx[ip];
+      Wc[P.ncol - 1] = P.kind == 0 ? n : n * S.w[ip];
+    }
+  }
 }
 
 __global__ void k_blocks(const BlockProb* probs, NodesView s0, NodesView s1) {
@@ -347,10 +408,15 @@ void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S, const N
   long long mx = 0;
   for (auto& p : probs) mx = std::max(mx, (long long)p.ncol * p.m);
   if (mx == 0) return;
+  int max_M = 1;
+  for (auto& p : probs) {
+    require(p.M >= 0 && p.M <= 1024, "eval_idmat: at most 1024 proxy points");
+    max_M = std::max(max_M, p.M);
+  }
   auto d = to_device_tmp(probs, s);
   dim3 grid(std::min(grid1(mx), 1024), int(probs.size()));
   ProfScope prof_(KC_EVAL, s);
-  k_idmat<<<grid, 256, 0, s>>>(d.p, S, E1, e1_same, E2, e2_same);
+  k_idmat<<<grid, 256, 4 * size_t(max_M) * sizeof(double), s>>>(d.p, max_M, S, E1, e1_same, E2, e2_same);
   RW_CHECK_LAUNCH();
 }
 

@@ -6,6 +6,7 @@
 #include "hbs.cuh"
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <numeric>
 #include <type_traits>
 
@@ -131,8 +132,16 @@ void IdBatch::interp(const std::vector<double*>& P, const std::vector<int>& ldp,
 std::vector<int> IdBatch::pivots(cudaStream_t s) const { return piv.download(s); }
 
 // ====================================================================== tree ID
-// Largest level (number of problems) that is merged into a single root.
-constexpr int kRootMergeJobs = 256;
+// Largest level (number of problems) that is merged into a single root
+// (RW_ROOT_MERGE overrides it, for tuning).
+int root_merge_jobs() {
+  static const int v = [] {
+    const char* e = std::getenv("RW_ROOT_MERGE");
+    const int x = e ? std::atoi(e) : 0;
+    return x > 0 ? x : 256;
+  }();
+  return v;
+}
 namespace {
 __global__ void k_gather_cols(const double* Z, int nr, const int* cand, int n, double* W) {
   for (int c = blockIdx.x; c < n; c += gridDim.x)
@@ -183,6 +192,10 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
   std::vector<std::vector<TJob>> levels;
   std::vector<DBuf<double>> Pl;  // per level: interpolation matrices (m_j x k_j, ld m_j)
   std::vector<TJob> cur;
+  if (const char* e = std::getenv("RW_TREE_CHUNK")) {
+    const int x = std::atoi(e);
+    if (x >= 16 && x <= 1024) chunk = x;
+  }
   for (int r0 = 0; r0 < mt; r0 += chunk) {
     TJob j;
     for (int r = r0; r < std::min(mt, r0 + chunk); ++r) j.cand.push_back(r);
@@ -251,7 +264,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
     // over all SMs) replaces the remaining levels of narrow problems.
     size_t nsk = 0;
     for (auto& j : cur) nsk += j.skel.size();
-    const bool wide_root = cur.size() > 2 && cur.size() <= size_t(kRootMergeJobs) && grid_id_fits(nr, int(nsk));
+    const bool wide_root = cur.size() > 2 && cur.size() <= size_t(root_merge_jobs()) && grid_id_fits(nr, int(nsk));
     std::vector<TJob> nxt;
     if (wide_root) {
       TJob j;

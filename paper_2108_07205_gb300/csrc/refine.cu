@@ -200,7 +200,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       // far rows of I_k against P^bas (shared by A_kc and A_kp)
       IdMatProb cs{};
       cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
-      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 64, s2);
+      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
     } catch (...) { e2 = std::current_exception(); }
   };
   std::thread th1, th2;
@@ -224,7 +224,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     {
       IdMatProb cs{};
       cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
-      tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 64, s);
+      tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
     }
     // A_pk: rows of [A_{p,div} | A_pk^near | n_p]
     {
@@ -232,7 +232,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
       IdMatProb cs{};
       cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
-      tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 64, s);
+      tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s);
     }
   } catch (...) { e0 = std::current_exception(); }
   if (serial) tr.mark("  near + A_pk IDs");
