@@ -61,7 +61,12 @@ class Program {
   int grid_[3] = {0, 0, 0};
   int tr_index_ = 1;
   DBuf<GOp> d_ops_;
-  DBuf<int> d_tile_[3], d_phase_;
+  DBuf<int> d_tile_[3], d_top_[3], d_phase_;
+  // L2 prefetch list: contiguous byte ranges of every phase's matrices
+  // (16-byte aligned, at most kPrefetchChunk bytes each), phase p's ranges at
+  // [d_pf_off_[p], d_pf_off_[p+1])
+  DBuf<const char*> d_pf_addr_;
+  DBuf<int> d_pf_bytes_, d_pf_off_;
 };
 
 }  // namespace rw
