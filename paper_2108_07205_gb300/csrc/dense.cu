@@ -1609,7 +1609,14 @@ bool grid_id_plan(const std::vector<IdProb>& ps, size_t cap, std::vector<int>& p
     work += double(p.nr) * p.nc;
   }
   if (need > nsm || nsm > kGridIdMaxCtas) return false;
-  const long long spare = nsm - need;
+  // CTAs beyond the shared-memory need are shared out up to the SM count, or
+  // up to RW_ID_GRID_CTAS (tuning: leaves SMs to the other streams)
+  static const int cap_ctas = [] {
+    const char* e = std::getenv("RW_ID_GRID_CTAS");
+    return e ? std::atoi(e) : 0;
+  }();
+  const long long budget = cap_ctas > 0 ? std::max<long long>(need, std::min(cap_ctas, nsm)) : nsm;
+  const long long spare = budget - need;
   for (int q = 0; q < np; ++q) {
     const long long extra = (long long)(double(spare) * double(ps[q].nr) * ps[q].nc / work);
     g[q] = int(std::min<long long>(g[q] + extra, ps[q].nc));

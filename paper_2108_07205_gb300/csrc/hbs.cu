@@ -149,9 +149,32 @@ __global__ void k_gather_cols(const double* Z, int nr, const int* cand, int n, d
 }
 }  // namespace
 
+namespace {
+TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
+                     const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
+                     int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s);
+}  // namespace
+
+// Sketched problems first try a narrow sketch (kSketchTry rows) and keep it
+// when the rank found leaves kSketchMargin rows of oversampling; otherwise
+// they are redone at the full sketch width.
+constexpr int kSketchTry = 96, kSketchMargin = 16;
+
 TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
                    const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
                    int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s) {
+  const int ncol = idmat_ncol(0, colspec.n1, colspec.n2, colspec.M, colspec.normal);
+  if (ncol > sketch_cols && sketch_width > kSketchTry && ncol > kSketchTry) {
+    TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, kSketchTry, seed, chunk, s);
+    if (t.k <= kSketchTry - kSketchMargin) return t;
+  }
+  return tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, sketch_width, seed, chunk, s);
+}
+
+namespace {
+TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
+                     const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
+                     int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s) {
   TreeId out;
   const int mt = int(rows.size());
   if (mt == 0) return out;
@@ -341,6 +364,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
   tr.mark("top-down interpolation");
   return out;
 }
+}  // namespace
 
 // ====================================================================== HBS build
 namespace {

@@ -298,11 +298,13 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     DBuf<int> flag(1);
     flag.zero(s);
     batched_inverse({InvProb{W.p, Winv.p, Ww.p, k, k, k, flag.p}}, s);
+    // the solve program depends on the buffers, not on their values: the host
+    // builds it while the GPU forms W and W^-1
+    build_solve_program(s);
     auto hf = flag.download(s);
     require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
   }
-  tr.mark("W, W^-1");
-  build_solve_program(s);
+  tr.mark("W, W^-1, solve program");
   bytes = Lo.bytes() + Lp.bytes() + Rkc.bytes() + Rkp.bytes() + Rpk.bytes() + Xo.bytes() + Xp.bytes() + Winv.bytes() +
           hpp.bytes + pn.buf.bytes() + nn.buf.bytes();
 }
