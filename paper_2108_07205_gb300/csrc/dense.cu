@@ -1289,6 +1289,11 @@ static void init_smem_limits() {
     cudaError_t f1 = cudaFuncSetAttribute(k_inverse_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (f0 != cudaSuccess) err = f0;
     if (f1 != cudaSuccess) err = f1;
+    // 16-CTA clusters are only used when asked for (RW_GJ_CS=16): a part that
+    // refuses the attribute keeps working with portable sizes
+    cudaFuncSetAttribute(k_inverse_cluster<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_inverse_cluster<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
   });
   if (err != cudaSuccess) throw Error(RW_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
 }
@@ -1496,13 +1501,21 @@ void matvec<float>(const std::vector<GemvProb<float>>& probs, int nrhs, cudaStre
 void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
   // small matrices: one CTA each; larger: a cluster of up to 8 CTAs with the
   // columns in shared memory when they fit, else in place in global memory
-  std::vector<InvProb> small, cl_sm[4], cl_gl[4];
-  const int sizes[4] = {1, 2, 4, 8};
+  std::vector<InvProb> small, cl_sm[5], cl_gl[5];
+  const int sizes[5] = {1, 2, 4, 8, 16};
   const size_t cap = 200 * 1024;
   for (const auto& p : probs) {
     if (p.n <= 0) continue;
     if (p.n < 48) { small.push_back(p); continue; }
-    const int q = p.n >= 192 ? 3 : p.n >= 96 ? 2 : 1;
+    // eight CTAs per matrix (measured fastest from n = 48 up: the pivot
+    // steps are latency bound, more SMs shorten each elimination);
+    // RW_GJ_CS (tuning) fixes another size: 1, 2, 4, 8 or 16 (non-portable)
+    static const int fixed_cs = [] {
+      const char* e = std::getenv("RW_GJ_CS");
+      const int v = e ? std::atoi(e) : 0;
+      return v == 1 ? 0 : v == 2 ? 1 : v == 4 ? 2 : v == 8 ? 3 : v == 16 ? 4 : 3;
+    }();
+    const int q = fixed_cs;
     const int CS = sizes[q];
     const int cw = (p.n + CS - 1) / CS;
     const size_t need = (3 * size_t(p.n) + size_t(p.n) * cw) * sizeof(double) + size_t(p.n + 2) * sizeof(int);
@@ -1519,7 +1532,7 @@ void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
     RW_CHECK_LAUNCH();
   }
   for (int sm = 0; sm < 2; ++sm)
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 5; ++q) {
       auto& g = sm ? cl_sm[q] : cl_gl[q];
       if (g.empty()) continue;
       const int CS = sizes[q];
@@ -1711,11 +1724,17 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired
   // when both fit; otherwise they are routed one by one.
   const size_t cap = 200 * 1024;
   const int sizes[4] = {1, 2, 4, 8};
+  // RW_ID_CS_MIN (tuning): smallest cluster size tried (1, 2, 4 or 8)
+  static const int q_min = [] {
+    const char* e = std::getenv("RW_ID_CS_MIN");
+    const int v = e ? std::atoi(e) : 1;
+    return v >= 8 ? 3 : v >= 4 ? 2 : v >= 2 ? 1 : 0;
+  }();
   auto fitq = [&](const IdProb& p) {
-    for (int q = 0; q < 4; ++q) {
+    for (int q = q_min; q < 4; ++q) {
       const int cw = (p.nc + sizes[q] - 1) / sizes[q];
       const size_t b = (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double);
-      if (b <= cap && (q == 0 || p.nc >= 2 * sizes[q])) return q;
+      if (b <= cap && (q == q_min || p.nc >= 2 * sizes[q])) return q;
     }
     return -1;
   };
