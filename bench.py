@@ -523,7 +523,7 @@ def main():
     prof = out["prof"]
     dom = max(prof, key=lambda c: prof[c]["ms"])
     dp = prof[dom]
-    dom_names = {"id": "column-pivoted QR (thread-block cluster, FP64)", "gemm": "batched tiled GEMM (FP64)",
+    dom_names = {"id": "column-pivoted QR (cluster and grid-wide kernels, FP64)", "gemm": "batched tiled GEMM (FP64)",
                  "gemv": "batched GEMV / HBS sweeps (FP64)", "inverse": "batched Gauss-Jordan inverse (FP64)",
                  "eval": "kernel-entry evaluation (FP64)", "other": "bookkeeping kernels"}
     if dom in ("id", "gemm", "inverse", "eval"):

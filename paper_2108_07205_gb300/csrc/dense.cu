@@ -762,9 +762,12 @@ __global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_
 // One pivot step's update of a CTA's candidate columns (shared memory, nr
 // rows each) by the Householder reflector I - tau v v^T (v(s) = 1, v(i) =
 // vloc(i) below): G threads (a power of two <= 32, within one warp) per
-// column compute the dot product and the update, then the column norm is
-// downdated (LAPACK xLAQP2 scheme) and recomputed exactly when cancellation
-// makes the downdate unreliable.  Done columns carry a negative norm.
+// column compute the dot product and the update, then the column's squared
+// norm is downdated by the square of the entry leaving it and recomputed
+// exactly when cancellation makes the downdate unreliable (remaining square
+// <= sqrt(eps) x the square at the last exact computation: LAPACK xLAQP2's
+// test, stated on squares, which needs no division or square root).  Done
+// columns carry a negative value.
 __device__ __forceinline__ void cpqr_update_columns(double* Wl, int nr, int ncl, int ncl_pad, int G, int s,
                                                     double tau, const double* vloc, double* nrm, double* nrm0,
                                                     double tol3z) {
@@ -784,13 +787,11 @@ __device__ __forceinline__ void cpqr_update_columns(double* Wl, int nr, int ncl,
         for (int i = s + 1 + gl; i < nr; i += G) cj[i] -= dd * vloc[i];
       }
       const double rs = (tau != 0.0) ? cj[s] - dd : cj[s];
-      const double nj = nrm[j];
-      if (nj != 0.0) {
-        double t = fabs(rs) / nj;
-        t = fmax(0.0, (1.0 + t) * (1.0 - t));
-        const double r = nj / nrm0[j];
-        if (t * r * r <= tol3z) recompute = 1;
-        else if (gl == 0) nrm[j] = nj * sqrt(t);
+      const double nj2 = nrm[j];
+      if (nj2 != 0.0) {
+        const double t2 = fmax(0.0, fma(-rs, rs, nj2));
+        if (t2 <= tol3z * nrm0[j]) recompute = 1;
+        else if (gl == 0) nrm[j] = t2;
       }
     }
     // recompute decisions differ between groups: every lane joins the
@@ -801,7 +802,7 @@ __device__ __forceinline__ void cpqr_update_columns(double* Wl, int nr, int ncl,
     for (int off = G / 2; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off, G);
     if (live && gl == 0) {
       if (tau != 0.0) cj[s] -= dd;
-      if (recompute) { nrm[j] = sqrt(q); nrm0[j] = nrm[j]; }
+      if (recompute) { nrm[j] = q; nrm0[j] = q; }
     }
   }
 }
@@ -854,7 +855,7 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
     double s = 0.0;
     for (int i = lane; i < nr; i += 32) { double v = Wl[i + size_t(j) * nr]; s += v * v; }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) { nrm[j] = sqrt(s); nrm0[j] = nrm[j]; }
+    if (lane == 0) { nrm[j] = s; nrm0[j] = s; }
   }
   __syncthreads();
   const int maxsteps = (nr <= 0 || nc <= 0) ? 0 : min(min(nr, nc), P.max_rank);
@@ -905,14 +906,16 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
       if (lane == 0) { g_val = bv; g_idx = bi; g_val_o = ov_o; }
     }
     __syncthreads();
+    // squared norms are published; ref is the first pivot norm itself
     const double vmax = g_val, vmax_o = g_val_o;
     const int pg = g_idx;
-    if (it == 0) { ref = vmax; ref_o = vmax_o; }
+    if (it == 0) { ref = sqrt(fmax(vmax, 0.0)); ref_o = sqrt(fmax(vmax_o, 0.0)); }
+    const double thr = fmax(P.tol_abs, P.tol_rel * ref), thr_o = fmax(tabs_o, trel_o * ref_o);
     // the same decisions in every CTA of the cluster (same published data)
     const bool hard = done || it >= maxsteps || vmax <= 0.0;
-    const bool soft = hard || (it >= P.min_rank && vmax <= fmax(P.tol_abs, P.tol_rel * ref));
+    const bool soft = hard || (it >= P.min_rank && vmax <= thr * thr);
     const bool hard_o = done_o || it >= maxsteps_o || vmax_o <= 0.0;
-    const bool soft_o = hard_o || (it >= minrank_o && vmax_o <= fmax(tabs_o, trel_o * ref_o));
+    const bool soft_o = hard_o || (it >= minrank_o && vmax_o <= thr_o * thr_o);
     if (soft && soft_o) break;
     done = hard;
     done_o = hard_o;
@@ -1035,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int base
     double s = 0.0;
     for (int i = lane; i < nr; i += 32) { double v = Wl[i + size_t(j) * nr]; s += v * v; }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) { nrm[j] = sqrt(s); nrm0[j] = nrm[j]; }
+    if (lane == 0) { nrm[j] = s; nrm0[j] = s; }
   }
   __syncthreads();
   const double tol3z = sqrt(2.220446049250313e-16);
@@ -1091,10 +1094,12 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int base
     // step possible), hard = no further step possible
     if (tid < np) {
       const int q = tid;
-      if (it == 0) s_ref[q] = s_val[q];
+      // squared norms are published; s_ref is the first pivot norm itself
+      if (it == 0) s_ref[q] = sqrt(fmax(s_val[q], 0.0));
+      const double thr = fmax(s_tabs[q], s_trel[q] * s_ref[q]);
       const bool hard = !s_act[q] || s_s[q] >= s_mx[q] || s_val[q] <= 0.0;
       s_hard[q] = hard;
-      s_soft[q] = hard || (s_s[q] >= s_minr[q] && s_val[q] <= fmax(s_tabs[q], s_trel[q] * s_ref[q]));
+      s_soft[q] = hard || (s_s[q] >= s_minr[q] && s_val[q] <= thr * thr);
     }
     __syncthreads();
     int act_q = 0;
