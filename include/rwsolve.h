@@ -199,7 +199,7 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets,
  * (diagnostics: benchmarks difference it around a timed region). */
 unsigned long long rw_kernel_launches(void);
 
-/* Serving loop (SURVEY configuration 4; the paper has no serving layer):
+/* Serving loop (the paper has no serving layer):
  * continuous batching of refined-wall solve requests against resident walls.
  * rw_server_create starts n_workers host threads, each with its own CUDA
  * stream on the current device; requests queue FIFO and are admitted while
@@ -236,7 +236,7 @@ int rw_server_poll(rw_server_t s, long long ticket, int* status, double* latency
 int rw_server_wait(rw_server_t s, long long ticket, double* latency_ms);
 int rw_server_destroy(rw_server_t s);
 
-/* Batched solve of many refined walls (SURVEY configuration 5; the paper
+/* Batched solve of many refined walls (the paper
  * solves one wall at a time): the direct solves (Algorithm 1, s1-s3) of n
  * refinements, each on its own wall, run as one persistent cooperative launch
  * per 8 right-hand sides with phases aligned across the instances.  The

@@ -1,4 +1,4 @@
-// Batched solve of many refined walls (SURVEY configuration 5): the direct
+// Batched solve of many refined walls: the direct
 // solves of n refinements, each on its own wall, are merged into one GEMV
 // program (phases aligned by index: scatter, sweeps leaf to root to leaf,
 // Woodbury, gather) and executed by one persistent cooperative launch per 8

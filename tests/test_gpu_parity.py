@@ -4,7 +4,7 @@ Tolerances (relative 2-norm unless stated), from the arithmetic:
 * nodes, boundary data: 1e-13 (same formulas, different rounding order);
 * HBS inverse vs dense solve: 1e-10 (compression tolerance 1e-12 times
   kappa(A_oo) ~ 3e2 on the star wall);
-* refined density, RW_MODE_DIRECT_REFINED: 1e-10 (the spec bar for the
+* refined density, RW_MODE_DIRECT_REFINED: 1e-10 (the parity bar for the
   FP64 path); RW_MODE_DIRECT alone: 1e-9 (1e-12 compression amplified by
   kappa(A_nn) ~ 5e2, measured 1.7e-10);
 * mixed path (FP32 sweeps inside FP64 FGMRES): ELS residual <= 1e-10 and
