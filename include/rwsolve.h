@@ -52,6 +52,7 @@ extern "C" {
  *                    the paper's spline channel (Sec. 5.1). */
 #define RW_CURVE_STAR 0
 #define RW_CURVE_CHANNEL 1
+#define RW_CURVE_NODES 2   /* wall given by explicit nodes (rw_hbs_build_nodes) */
 
 typedef struct {
   int curve_kind;     /* RW_CURVE_*                                          */
@@ -71,7 +72,7 @@ typedef struct {
                                points, else by an HBS of the refined arc
                                (Alg. 1 step 2; default = leaf_points)         */
   int sketch_cols;          /* ID matrices wider than this are compressed by
-                               a random +-1 sketch first (default 1024)       */
+                               a random +-1 sketch first (default 2048)       */
   double gmres_tol;         /* relative residual target (default 1e-10)      */
   int gmres_maxit;          /* iterations per restart cycle (default 30)     */
   int gmres_restarts;       /* restart cycles (default 4)                    */
@@ -100,7 +101,20 @@ typedef struct {
 typedef struct {
   int iters;             /* GMRES iterations (0 for the direct path)         */
   double rel_residual;   /* GMRES: final relative residual of the ELS        */
+  int k_woodbury;        /* Woodbury size k of the refinement                */
+  double cond_w;         /* 1-norm condition estimate of W = I + R X:
+                            ||W||_1 ||W^-1||_1 (computed at factorisation)   */
 } rw_info;
+
+/* A wall given by explicit nodes: n = 16 P points in panel order (P panels of
+ * 16 Gauss-Legendre points, counter-clockwise), with unit outward normals
+ * (nx, ny), quadrature weights w (Gauss-Legendre weight times |x'(t)| times
+ * the panel's half-width in t) and signed curvature kappa.  Each array holds
+ * n values, host or device. */
+typedef struct {
+  int n;
+  const double *x, *y, *nx, *ny, *w, *kappa;
+} rw_nodes;
 
 typedef struct rw_hbs_s* rw_hbs_t;   /* reference wall: HBS forward + inverse */
 typedef struct rw_ref_s* rw_ref_t;   /* one refinement: Woodbury factors       */
@@ -115,6 +129,21 @@ int rw_default_opts(rw_opts* o);
  * opts may be NULL (defaults).  On success *out owns all device memory. */
 int rw_hbs_build(const rw_wall_desc* wall, const rw_opts* opts, void* stream,
                  rw_hbs_t* out);
+
+/* a0 for a wall given by its nodes (any geometry: the paper's spline
+ * channel, fish or tube discretised elsewhere).  Checks n = 16 P >= 16,
+ * finite values, positive weights and unit normals (|n| within 1e-8 of 1),
+ * else RW_ERR_INVALID.  Such a wall has no curve: refine it with
+ * rw_refine_factor_nodes. */
+int rw_hbs_build_nodes(const rw_nodes* nodes, const rw_opts* opts, void* stream, rw_hbs_t* out);
+
+/* Checkpoint and restore of a built wall (nodes, curve, options, HBS
+ * forward and inverse factors) in a binary file, little-endian, for the same
+ * library version; a restored handle gives the same results as the one saved.
+ * Load allocates on the current device.  Errors: RW_ERR_INVALID for an
+ * unreadable, truncated or foreign file. */
+int rw_hbs_save(rw_hbs_t h, const char* path);
+int rw_hbs_load(const char* path, void* stream, rw_hbs_t* out);
 
 int rw_hbs_stats_get(rw_hbs_t h, rw_hbs_stats* s);
 
@@ -159,6 +188,13 @@ int rw_hbs_apply_forward(rw_hbs_t h, int nrhs, const double* x, double* y,
 int rw_refine_factor(rw_hbs_t h, int n_cut, const int* panel_ids,
                      const int* levels, void* stream, rw_ref_t* out);
 
+/* As rw_refine_factor with the added nodes given by the caller (any wall,
+ * required for walls built from nodes): added holds the 16 x 2^levels[i]
+ * nodes of each cut panel's sub-panels, cut panels in window order, points
+ * in parameter order within each (same checks as rw_hbs_build_nodes). */
+int rw_refine_factor_nodes(rw_hbs_t h, int n_cut, const int* panel_ids, const int* levels,
+                           const rw_nodes* added, void* stream, rw_ref_t* out);
+
 int rw_ref_stats_get(rw_ref_t r, rw_ref_stats* s);
 
 /* Copy the refined nodes in refined order (6 x N_n, as rw_hbs_nodes). */
@@ -190,7 +226,8 @@ int rw_apply_refined(rw_ref_t r, int nrhs, const double* tau, double* y,
  * (output, refined order); if n_targets > 0, u: 2 n_targets x nrhs interior
  * velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets (2 x n_targets).
  * info may be NULL (iters = GMRES iterations, or 1 for the refined direct
- * mode; rel_residual = final GMRES relative residual of the ELS). */
+ * mode; rel_residual = final GMRES relative residual of the ELS; k_woodbury
+ * and cond_w describe the refinement's Woodbury operator). */
 int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets,
              const double* targets, double* u, int mode, void* stream,
              rw_info* info);

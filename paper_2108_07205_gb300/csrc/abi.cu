@@ -2,6 +2,7 @@
 // Argument checking, host/device pointer handling and error codes live here;
 // the work is done by refine.cu / hbs.cu and the kernels below them.
 #include "handles.cuh"
+#include <cmath>
 #include <cstring>
 #include <memory>
 
@@ -88,6 +89,31 @@ rw::Opts to_opts(const rw_opts* o) {
   return r;
 }
 
+// Copies the six arrays of an rw_nodes (host or device) into one host
+// array, 6 x n column-major (x, y, nx, ny, w, kappa), and checks them.
+std::vector<double> stage_nodes(const rw_nodes* nd, int n_expected, const char* what, cudaStream_t s) {
+  rw::require(nd != nullptr, std::string(what) + ": null nodes");
+  const int n = nd->n;
+  rw::require(n >= 16 && n % 16 == 0, std::string(what) + ": n must be a positive multiple of 16");
+  rw::require(n_expected < 0 || n == n_expected,
+              std::string(what) + ": expected " + std::to_string(n_expected) + " nodes, got " + std::to_string(n));
+  const double* src[6] = {nd->x, nd->y, nd->nx, nd->ny, nd->w, nd->kappa};
+  std::vector<double> h(6 * size_t(n));
+  for (int c = 0; c < 6; ++c) {
+    rw::require(src[c] != nullptr, std::string(what) + ": null node array");
+    RW_CUDA(cudaMemcpyAsync(h.data() + size_t(c) * n, src[c], size_t(n) * sizeof(double), cudaMemcpyDefault, s));
+  }
+  RW_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) {
+    for (int c = 0; c < 6; ++c)
+      rw::require(std::isfinite(h[size_t(c) * n + i]), std::string(what) + ": non-finite node data");
+    const double nx = h[2 * size_t(n) + i], ny = h[3 * size_t(n) + i];
+    rw::require(std::fabs(nx * nx + ny * ny - 1.0) <= 1e-8, std::string(what) + ": normals must have unit length");
+    rw::require(h[4 * size_t(n) + i] > 0.0, std::string(what) + ": weights must be positive");
+  }
+  return h;
+}
+
 }  // namespace
 
 namespace rw {
@@ -158,6 +184,32 @@ int rw_hbs_build(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_h
   return rc;
 }
 
+int rw_hbs_build_nodes(const rw_nodes* nodes, const rw_opts* opts, void* stream, rw_hbs_t* out) {
+  if (!nodes || !out) return fail(RW_ERR_INVALID, "rw_hbs_build_nodes: null argument");
+  *out = nullptr;
+  std::unique_ptr<rw_hbs_s> h(new rw_hbs_s);
+  int rc = guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rw::Wall& w = h->wall;
+    w.opts = to_opts(opts);
+    const std::vector<double> hn = stage_nodes(nodes, -1, "rw_hbs_build_nodes", s);
+    const int n = nodes->n;
+    rw::require(n / 16 <= (1 << 20), "rw_hbs_build_nodes: at most 2^20 panels");
+    w.n_panels = n / 16;
+    w.curve.kind = RW_CURVE_NODES;
+    for (int i = 0; i < 8; ++i) w.curve.p[i] = 0.0;
+    w.nodes.alloc(n);
+    RW_CUDA(cudaMemcpyAsync(w.nodes.buf.p, hn.data(), hn.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    w.nodes.hx.assign(hn.begin(), hn.begin() + n);
+    w.nodes.hy.assign(hn.begin() + n, hn.begin() + 2 * size_t(n));
+    w.hbs.build(w.nodes, w.opts, s);
+    w.hbs.make_fp32(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+  if (rc == RW_OK) *out = h.release();
+  return rc;
+}
+
 int rw_hbs_stats_get(rw_hbs_t h, rw_hbs_stats* st) {
   if (!h || !st) return fail(RW_ERR_INVALID, "rw_hbs_stats_get: null argument");
   const rw::Hbs& b = h->wall.hbs;
@@ -213,8 +265,34 @@ int rw_refine_factor(rw_hbs_t h, int n_cut, const int* panel_ids, const int* lev
   r->h = h;
   int rc = guarded([&] {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rw::require(h->wall.curve.kind != RW_CURVE_NODES,
+                "rw_refine_factor: this wall was built from nodes; give the added nodes (rw_refine_factor_nodes)");
     std::vector<int> pan(panel_ids, panel_ids + n_cut), lv(levels, levels + n_cut);
     r->ref.factor(h->wall, pan, lv, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+  if (rc == RW_OK) *out = r.release();
+  return rc;
+}
+
+int rw_refine_factor_nodes(rw_hbs_t h, int n_cut, const int* panel_ids, const int* levels, const rw_nodes* added,
+                           void* stream, rw_ref_t* out) {
+  if (!h || !panel_ids || !levels || !added || !out || n_cut < 1)
+    return fail(RW_ERR_INVALID, "rw_refine_factor_nodes: bad argument");
+  *out = nullptr;
+  std::unique_ptr<rw_ref_s> r(new rw_ref_s);
+  r->h = h;
+  int rc = guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int> pan(panel_ids, panel_ids + n_cut), lv(levels, levels + n_cut);
+    long long np = 0;
+    for (int L : lv) {
+      rw::require(L >= 0 && L <= 12, "rw_refine_factor_nodes: level must be in 0..12");
+      np += 16LL << L;
+    }
+    rw::require(np <= (1LL << 30), "rw_refine_factor_nodes: too many added nodes");
+    const std::vector<double> hn = stage_nodes(added, int(np), "rw_refine_factor_nodes", s);
+    r->ref.factor(h->wall, pan, lv, s, &hn);
     RW_CUDA(cudaStreamSynchronize(s));
   });
   if (rc == RW_OK) *out = r.release();
@@ -298,7 +376,12 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     if (mode == RW_MODE_GMRES_FP32 && relres > f.wall->opts.gmres_tol)
       throw rw::Error(RW_ERR_NOT_CONVERGED, "rw_solve: GMRES stopped at relative residual " + std::to_string(relres));
   });
-  if (info) { info->iters = iters; info->rel_residual = relres; }
+  if (info) {
+    info->iters = iters;
+    info->rel_residual = relres;
+    info->k_woodbury = r->ref.k;
+    info->cond_w = r->ref.cond_w;
+  }
   return rc;
 }
 

@@ -384,7 +384,6 @@ Geo node_geo(const std::vector<double>& x, const std::vector<double>& y, int lo,
 }  // namespace
 
 void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
-  nodes_ = &nodes;
   Trace tr(s, "hbs");
   N = nodes.n;
   require(N >= 1, "HBS: empty node set");

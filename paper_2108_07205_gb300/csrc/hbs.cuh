@@ -90,8 +90,7 @@ class Hbs {
   std::vector<HbsNode> node;  // heap order, index 1 .. 2^{L+1}-1
   // per-level storage (index = level)
   struct Level {
-    DBuf<double> U, Vt, E, F, G, B, D, Gf, Ef, Ff;  // F holds F* (k x m); *f: FP32 copies
-    DBuf<float> U32;  // unused placeholder for symmetry
+    DBuf<double> U, Vt, E, F, G, B, D;  // F holds F* (k x m)
     std::vector<size_t> oU, oVt, oE, oF, oG, oB12, oB21, oD;
     std::vector<int> koff;  // prefix sums of ranks at this level (size nn+1)
     DBuf<float> G32, E32, F32;
@@ -129,7 +128,6 @@ class Hbs {
  private:
   template <class T>
   void sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const;
-  const Nodes* nodes_ = nullptr;
 };
 
 }  // namespace rw

@@ -32,6 +32,20 @@ __global__ void k_identity(double* W, int n) {
     W[e] = (e % n == e / n) ? 1.0 : 0.0;
 }
 
+// out[slot] = max(out[slot], max_j sum_i |A(i, j)|) for n x n column-major A:
+// one warp per column; the maximum of non-negative doubles is taken on their
+// bit patterns, which order the same way (out[slot] starts at 0).
+__global__ void k_norm1(const double* A, int n, double* out, int slot) {
+  const int lane = threadIdx.x & 31;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += fabs(A[i + size_t(j) * n]);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(out + slot), static_cast<unsigned long long>(__double_as_longlong(s)));
+}
+
 __global__ void k_zero_cols(double* A, int ld, int nrows, const int* cols, int ncols) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nrows * ncols; e += gridDim.x * blockDim.x) {
     const int r = e % nrows, c = e / nrows;
@@ -60,7 +74,8 @@ Refinement::~Refinement() {
   }
 }
 
-void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::vector<int>& lvl, cudaStream_t s) {
+void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::vector<int>& lvl, cudaStream_t s,
+                        const std::vector<double>* added) {
   wall = &w;
   streams.main = s;
   AllocStreamScope alloc_scope(s);
@@ -103,7 +118,14 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   }
   Np = np;
   Nn = Nk + Np;
-  {
+  if (added) {
+    // the caller's nodes for the sub-panels (window order)
+    require(added->size() == size_t(6) * Np, "refine: added nodes do not match the cut panels and levels");
+    pn.alloc(Np);
+    RW_CUDA(cudaMemcpyAsync(pn.buf.p, added->data(), added->size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    pn.hx.assign(added->begin(), added->begin() + Np);
+    pn.hy.assign(added->begin() + Np, added->begin() + 2 * size_t(Np));
+  } else {
     auto dta = to_device_tmp(ta, s), dtb = to_device_tmp(tb, s);
     pn.alloc(Np);
     eval_nodes(w.curve, dta.p, dtb.p, int(ta.size()), pn.buf.p, Np, s);
@@ -296,13 +318,25 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     batched_gemm(g, s);
     Winv.alloc(std::max<size_t>(size_t(k) * k, 1));
     DBuf<int> flag(1);
+    DBuf<double> norms(2);
     flag.zero(s);
+    norms.zero(s);
+    if (k) {
+      k_norm1<<<ceil_div(32LL * k, 256), 256, 0, s>>>(W.p, k, norms.p, 0);
+      RW_CHECK_LAUNCH();
+    }
     batched_inverse({InvProb{W.p, Winv.p, Ww.p, k, k, k, flag.p}}, s);
+    if (k) {
+      k_norm1<<<ceil_div(32LL * k, 256), 256, 0, s>>>(Winv.p, k, norms.p, 1);
+      RW_CHECK_LAUNCH();
+    }
     // the solve program depends on the buffers, not on their values: the host
     // builds it while the GPU forms W and W^-1
     build_solve_program(s);
     auto hf = flag.download(s);
     require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
+    const auto hn = norms.download(s);
+    cond_w = hn[0] * hn[1];
   }
   tr.mark("W, W^-1, solve program");
   bytes = Lo.bytes() + Lp.bytes() + Rkc.bytes() + Rkp.bytes() + Rpk.bytes() + Xo.bytes() + Xp.bytes() + Winv.bytes() +

@@ -31,6 +31,7 @@ struct Refinement {
   Hbs hpp;                             // A_pp (single leaf = dense inverse)
   bool pp_dense = false;
   int kf = 0, kn = 0, kpk = 0, kk = 0, k = 0;
+  double cond_w = 0.0;                 // ||W||_1 ||W^-1||_1
   // factors: L_o (2No x kk), L_p (2Np x kpk); R blocks; X = A~^{-1} L; W^{-1}
   DBuf<double> Lo, Lp, Rkc, Rkp, Rpk, Xo, Xp, Winv;
   DBuf<int> dc;                  // c DOFs (2Nc) in o numbering
@@ -46,7 +47,10 @@ struct Refinement {
   // Append this refinement's direct solve to a program: g = base gb + g_off
   // (ld ldg), tau = base tb + t_off (ld ldt), temporaries in base 2.
   void emit_solve(Program& P, int gb, long long g_off, int ldg, int tb, long long t_off, int ldt) const;
-  void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s);
+  // added (optional): the added nodes, 6 x N_p host array (x, y, nx, ny, w,
+  // kappa) in window order; without it they are evaluated on the wall's curve
+  void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s,
+              const std::vector<double>* added = nullptr);
   // Direct solve, device buffers: g, tau (2Nn x nrhs): one persistent launch
   // per 8 right-hand sides.  solve_direct_levels is the same computation as
   // a sequence of per-level launches.

@@ -18,7 +18,7 @@ from . import build as _build
 RW_OK = 0
 ERRORS = {-1: "RW_ERR_INVALID", -2: "RW_ERR_OOM", -3: "RW_ERR_SINGULAR",
           -4: "RW_ERR_NOT_CONVERGED", -5: "RW_ERR_TIMEOUT", -6: "RW_ERR_CUDA"}
-CURVE_STAR, CURVE_CHANNEL = 0, 1
+CURVE_STAR, CURVE_CHANNEL, CURVE_NODES = 0, 1, 2
 MODE_DIRECT, MODE_GMRES_FP32, MODE_DIRECT_REFINED = 0, 1, 2
 
 
@@ -70,10 +70,18 @@ class Request(ctypes.Structure):
 
 
 class Info(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+    _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double), ("k_woodbury", ctypes.c_int),
+                ("cond_w", ctypes.c_double)]
 
 
-EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
+class NodesDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("nx", ctypes.c_void_p),
+                ("ny", ctypes.c_void_p), ("w", ctypes.c_void_p), ("kappa", ctypes.c_void_p)]
+
+
+EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_build_nodes", "rw_hbs_save", "rw_hbs_load",
+           "rw_refine_factor_nodes",
+           "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
            "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
            "rw_stokeslet_data",
@@ -109,6 +117,10 @@ def load(build_if_missing=False):
     L.rw_hbs_apply_forward.argtypes = [vp, ctypes.c_int, dp, dp, vp]
     L.rw_hbs_apply_inverse_noalloc.argtypes = [vp, ctypes.c_int, dp, dp, vp]
     L.rw_refine_factor.argtypes = [vp, ctypes.c_int, ip, ip, vp, ctypes.POINTER(vp)]
+    L.rw_hbs_build_nodes.argtypes = [ctypes.POINTER(NodesDesc), ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    L.rw_refine_factor_nodes.argtypes = [vp, ctypes.c_int, ip, ip, ctypes.POINTER(NodesDesc), vp, ctypes.POINTER(vp)]
+    L.rw_hbs_save.argtypes = [vp, ctypes.c_char_p]
+    L.rw_hbs_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
     L.rw_ref_stats_get.argtypes = [vp, ctypes.POINTER(RefStats)]
     L.rw_ref_nodes.argtypes = [vp, dp, vp]
     L.rw_apply_refined.argtypes = [vp, ctypes.c_int, dp, dp, vp]
@@ -201,10 +213,33 @@ def default_opts(**kw):
     return o
 
 
+def _nodes_desc(nodes):
+    """rw_nodes from a dict of six equal-length arrays (numpy or CUDA tensors);
+    returns the descriptor and the arrays it points into (kept alive)."""
+    keep = []
+    ptrs = []
+    n = None
+    for key in ("x", "y", "nx", "ny", "w", "kappa"):
+        a = nodes[key]
+        if not hasattr(a, "data_ptr"):
+            a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        keep.append(a)
+        ptrs.append(_ptr(a))
+        m = a.numel() if hasattr(a, "numel") else a.size
+        if n is not None and m != n:
+            raise ValueError("node arrays must have equal lengths")
+        n = m
+    return NodesDesc(int(n), *ptrs), keep
+
+
 class Wall:
     """Reference wall: nodes, HBS forward representation and HBS inverse."""
 
-    def __init__(self, kind, n_panels, params=(), opts=None, stream=None):
+    def __init__(self, kind, n_panels=0, params=(), opts=None, stream=None, _handle=None):
+        if _handle is not None:
+            self.h = _handle
+            self.n_panels = self.stats()["n_points"] // 16
+            return
         L = load()
         d = WallDesc()
         d.curve_kind = {"star": CURVE_STAR, "channel": CURVE_CHANNEL}.get(kind, kind)
@@ -216,6 +251,27 @@ class Wall:
         _check(L.rw_hbs_build(ctypes.byref(d), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self.h = h
         self.n_panels = int(n_panels)
+
+    @classmethod
+    def from_nodes(cls, nodes, opts=None, stream=None):
+        """Wall from explicit nodes: dict x, y, nx, ny, w, kappa (16 per panel,
+        panel order, counter-clockwise)."""
+        desc, keep = _nodes_desc(nodes)
+        o = opts if opts is not None else default_opts()
+        h = ctypes.c_void_p()
+        _check(load().rw_hbs_build_nodes(ctypes.byref(desc), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        del keep
+        return cls(None, _handle=h)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """Restore a wall written by save()."""
+        h = ctypes.c_void_p()
+        _check(load().rw_hbs_load(os.fsencode(path), _stream(stream), ctypes.byref(h)))
+        return cls(None, _handle=h)
+
+    def save(self, path):
+        _check(load().rw_hbs_save(self.h, os.fsencode(path)))
 
     def stats(self):
         s = HbsStats()
@@ -241,8 +297,10 @@ class Wall:
         _check(load().rw_hbs_apply_forward(self.h, nrhs, _ptr(x), _ptr(y, True), _stream(stream)))
         return y
 
-    def refine(self, panels, levels, stream=None):
-        return Refinement(self, panels, levels, stream)
+    def refine(self, panels, levels, stream=None, added=None):
+        """Refinement of the cut panels; added = the sub-panels' nodes (dict as
+        for from_nodes, window order) instead of evaluating the wall's curve."""
+        return Refinement(self, panels, levels, stream, added)
 
     def close(self):
         if getattr(self, "h", None):
@@ -259,12 +317,18 @@ class Wall:
 class Refinement:
     """Algorithm 1 pre-computation for one local refinement of a Wall."""
 
-    def __init__(self, wall, panels, levels, stream=None):
+    def __init__(self, wall, panels, levels, stream=None, added=None):
         L = load()
         p = (ctypes.c_int * len(panels))(*[int(v) for v in panels])
         lv = (ctypes.c_int * len(levels))(*[int(v) for v in levels])
         h = ctypes.c_void_p()
-        _check(L.rw_refine_factor(wall.h, len(panels), p, lv, _stream(stream), ctypes.byref(h)))
+        if added is None:
+            _check(L.rw_refine_factor(wall.h, len(panels), p, lv, _stream(stream), ctypes.byref(h)))
+        else:
+            desc, keep = _nodes_desc(added)
+            _check(L.rw_refine_factor_nodes(wall.h, len(panels), p, lv, ctypes.byref(desc), _stream(stream),
+                                            ctypes.byref(h)))
+            del keep
         self.h = h
         self.wall = wall  # the wall must outlive the refinement
 
@@ -295,7 +359,8 @@ class Refinement:
         nt = 0 if targets is None else (targets.shape[0] if hasattr(targets, "shape") else len(targets) // 2)
         _check(load().rw_solve(self.h, nrhs, _ptr(g), _ptr(tau, True), nt, _ptr(targets), _ptr(u, True),
                                mode, _stream(stream), ctypes.byref(info)))
-        return {"iters": info.iters, "rel_residual": info.rel_residual}
+        return {"iters": info.iters, "rel_residual": info.rel_residual, "k_woodbury": info.k_woodbury,
+                "cond_w": info.cond_w}
 
     def close(self):
         if getattr(self, "h", None):

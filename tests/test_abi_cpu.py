@@ -52,6 +52,23 @@ def test_default_opts_and_validation_without_gpu():
         rwsolve._ptr(np.zeros(3, dtype=np.float32))
 
 
+def test_nodes_and_checkpoint_validation_without_gpu(tmp_path):
+    L = rwsolve.load(build_if_missing=True)
+    h = ctypes.c_void_p()
+    assert L.rw_hbs_build_nodes(None, None, None, ctypes.byref(h)) == -1
+    nd = rwsolve.NodesDesc(5, None, None, None, None, None, None)
+    assert L.rw_hbs_build_nodes(ctypes.byref(nd), None, None, ctypes.byref(h)) == -1
+    assert b"multiple of 16" in L.rw_last_error()
+    assert L.rw_refine_factor_nodes(None, 1, None, None, None, None, ctypes.byref(h)) == -1
+    assert L.rw_hbs_load(os.fsencode(str(tmp_path / "missing.rw")), None, ctypes.byref(h)) == -1
+    assert b"cannot open" in L.rw_last_error()
+    junk = tmp_path / "junk.rw"
+    junk.write_bytes(b"not a wall file at all")
+    assert L.rw_hbs_load(os.fsencode(str(junk)), None, ctypes.byref(h)) == -1
+    assert b"not a wall file" in L.rw_last_error()
+    assert L.rw_hbs_save(None, b"x.rw") == -1
+
+
 def test_inputs_are_seeded():
     a = inputs.refinement_window(3, 64, 4, 2, 5)
     b = inputs.refinement_window(3, 64, 4, 2, 5)
