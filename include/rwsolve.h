@@ -232,6 +232,15 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets,
              const double* targets, double* u, int mode, void* stream,
              rw_info* info);
 
+/* Interior pressure matching the double-layer velocity (Sec. 2):
+ * p(x) = sum_j w_j P(x, y_j) . tau_j with P_j(x, y) = (1/pi)(-n_j(y) / r^2 +
+ * 2 r_j (r . n(y)) / r^4), mu = 1, for a refined density tau (2 N_n x nrhs,
+ * refined order) at targets (2 x n_targets); p: n_targets x nrhs.  The
+ * pressure of an interior flow is fixed up to a constant; this is the
+ * representation's.  All host or device. */
+int rw_pressure(rw_ref_t r, int nrhs, const double* tau, int n_targets, const double* targets, double* p,
+                void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (diagnostics: benchmarks difference it around a timed region). */
 unsigned long long rw_kernel_launches(void);

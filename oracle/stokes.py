@@ -16,6 +16,9 @@ Nystrom discretisation (readings where the paper is silent):
 * degrees of freedom interleaved: (x-component, y-component) per point.
 
 Interior velocity (Sec. 2.1): u(x) = sum_j w_j D(x, y_j) tau_j (no N term).
+Pressure (Sec. 2): the double-layer velocity's pressure
+p(x) = sum_j w_j P(x, y_j) . tau_j, P_j = (1/pi)(-n_j / r^2 + 2 r_j (r . n) / r^4);
+the Stokeslet's pressure kernel is Q_j = r_j / (2 pi r^2).
 """
 import numpy as np
 
@@ -39,6 +42,23 @@ def stokeslet_velocity(tx, ty, sx, sy, f):
     uy = c * np.sum(lg[:, :, None] * fy[None] + ry[:, :, None] * rdotf / r2[:, :, None], axis=1)
     u = np.stack([ux, uy], axis=1)
     return u[:, :, 0] if squeeze else u
+
+
+def stokeslet_pressure(tx, ty, sx, sy, f):
+    """Pressure at targets of the point forces of stokeslet_velocity: the
+    single-layer pressure kernel Q_j(x, y) = r_j / (2 pi r^2) of Sec. 2
+    applied to the forces.  Returns (nt,) or (nt, nrhs)."""
+    f = np.asarray(f, dtype=np.float64)
+    squeeze = f.ndim == 2
+    if squeeze:
+        f = f[:, :, None]
+    rx = np.asarray(tx)[:, None] - np.asarray(sx)[None, :]
+    ry = np.asarray(ty)[:, None] - np.asarray(sy)[None, :]
+    r2 = rx * rx + ry * ry
+    fx, fy = f[:, 0, :], f[:, 1, :]
+    rdotf = rx[:, :, None] * fx[None] + ry[:, :, None] * fy[None]
+    p = np.sum(rdotf / r2[:, :, None], axis=1) / (2.0 * np.pi)
+    return p[:, 0] if squeeze else p
 
 
 def boundary_data(nodes, sx, sy, f):
@@ -114,6 +134,30 @@ def velocity(nodes, tau, tx, ty):
     uy = np.einsum("ij,ijr->ir", fac * ry, rdt)
     u = np.stack([ux, uy], axis=1)
     return u[:, :, 0] if squeeze else u
+
+
+def pressure(nodes, tau, tx, ty):
+    """Interior pressure matching the double-layer velocity (Sec. 2):
+    p(x) = sum_j w_j P(x, y_j) . tau_j with
+    P_j(x, y) = (mu / pi) (-n_j(y) / r^2 + 2 r_j (r . n(y)) / r^4), mu = 1.
+    tau: interleaved (2N) or (2N x nrhs).  Returns (nt,) or (nt, nrhs)."""
+    tau = np.asarray(tau, dtype=np.float64)
+    squeeze = tau.ndim == 1
+    if squeeze:
+        tau = tau[:, None]
+    rx = np.asarray(tx)[:, None] - nodes["x"][None, :]
+    ry = np.asarray(ty)[:, None] - nodes["y"][None, :]
+    r2 = rx * rx + ry * ry
+    nx, ny = nodes["nx"][None, :], nodes["ny"][None, :]
+    rdn = rx * nx + ry * ny
+    tx_, ty_ = tau[0::2, :], tau[1::2, :]
+    # P . tau = (1/pi) ( -(n . tau) / r^2 + 2 (r . tau)(r . n) / r^4 )
+    ndt = nx[:, :, None] * tx_[None] + ny[:, :, None] * ty_[None]
+    rdt = rx[:, :, None] * tx_[None] + ry[:, :, None] * ty_[None]
+    w = nodes["w"][None, :, None]
+    term = w * (-ndt / r2[:, :, None] + 2.0 * rdt * rdn[:, :, None] / (r2 * r2)[:, :, None]) / np.pi
+    p = np.sum(term, axis=1)
+    return p[:, 0] if squeeze else p
 
 
 def apply_rows(nodes, tau, rows):

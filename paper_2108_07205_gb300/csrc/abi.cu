@@ -385,6 +385,20 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
   return rc;
 }
 
+int rw_pressure(rw_ref_t r, int nrhs, const double* tau, int n_targets, const double* targets, double* p,
+                void* stream) {
+  if (!r || !tau || !targets || !p || nrhs < 1 || n_targets < 1) return fail(RW_ERR_INVALID, "rw_pressure: bad argument");
+  return guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const rw::Refinement& f = r->ref;
+    Arg at(tau, size_t(2) * f.Nn * nrhs, true, s), ax(targets, size_t(2) * n_targets, true, s);
+    Arg ap(p, size_t(n_targets) * nrhs, false, s);
+    rw::eval_pressure(f.nn.view(), at.p, nrhs, n_targets, ax.p, ap.p, s);
+    ap.finish(s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 unsigned long long rw_kernel_launches(void) { return rw::g_launches; }
 
 int rw_profile(int enable) {

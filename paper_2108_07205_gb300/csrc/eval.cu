@@ -266,6 +266,32 @@ __global__ void k_velocity(NodesView nd, const double* tau, int nrhs, int nt, co
   }
 }
 
+// Pressure of the double-layer velocity (Sec. 2): p(x) = sum_j w_j P(x, y_j)
+// . tau_j, P_j = (1/pi)(-n_j / r^2 + 2 r_j (r . n) / r^4), mu = 1; one CTA per
+// (target, right-hand side), sources split over the threads.
+__global__ void k_pressure(NodesView nd, const double* tau, int nt, const double* tg, double* p) {
+  const int t = blockIdx.x, r = blockIdx.y;
+  const double x = tg[2 * t], y = tg[2 * t + 1];
+  const double* tr = tau + size_t(r) * 2 * nd.n;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < nd.n; j += blockDim.x) {
+    const double rx = x - nd.x[j], ry = y - nd.y[j];
+    const double inv = 1.0 / (rx * rx + ry * ry);
+    const double ndt = nd.nx[j] * tr[2 * j] + nd.ny[j] * tr[2 * j + 1];
+    const double rdt = rx * tr[2 * j] + ry * tr[2 * j + 1];
+    const double rdn = rx * nd.nx[j] + ry * nd.ny[j];
+    acc += nd.w[j] * inv * (2.0 * rdt * rdn * inv - ndt);
+  }
+  __shared__ double sp[256];
+  sp[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sp[threadIdx.x] += sp[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) p[size_t(r) * nt + t] = sp[0] * (1.0 / kPi);
+}
+
 __global__ void k_stokeslets(NodesView nd, int ns, const double* src, int nrhs, const double* f, double* g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
@@ -462,6 +488,14 @@ void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, 
   if (nt <= 0 || nrhs <= 0) return;
   ProfScope prof_(KC_EVAL, s);
   k_velocity<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, nrhs, nt, targets, u);
+  RW_CHECK_LAUNCH();
+}
+
+void eval_pressure(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* p,
+                   cudaStream_t s) {
+  if (nt <= 0 || nrhs <= 0) return;
+  ProfScope prof_(KC_EVAL, s);
+  k_pressure<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, nt, targets, p);
   RW_CHECK_LAUNCH();
 }
 

@@ -90,6 +90,10 @@ void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s);
 void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt,
                    const double* targets, double* u, cudaStream_t s);
 
+// Pressure of the double-layer velocity at targets (Sec. 2): p (nt x nrhs).
+void eval_pressure(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* p,
+                   cudaStream_t s);
+
 // g(x_i) = sum_s S(x_i, y_s) f_s (Eq. stokeslet, mu = 1) at every node.
 // src: 2 x ns; f: 2 x ns x nrhs; g: 2N x nrhs.
 void eval_stokeslets(const NodesView& nodes, int ns, const double* src,

@@ -84,7 +84,7 @@ EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_build_nodes", "rw_hbs_save
            "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
            "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
-           "rw_stokeslet_data",
+           "rw_stokeslet_data", "rw_pressure",
            "rw_solve", "rw_batch_create", "rw_batch_rows", "rw_batch_autotune", "rw_batch_solve",
            "rw_batch_free", "rw_server_create", "rw_server_submit", "rw_server_poll", "rw_server_wait",
            "rw_server_destroy", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
@@ -125,6 +125,7 @@ def load(build_if_missing=False):
     L.rw_ref_nodes.argtypes = [vp, dp, vp]
     L.rw_apply_refined.argtypes = [vp, ctypes.c_int, dp, dp, vp]
     L.rw_stokeslet_data.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, dp, dp, vp]
+    L.rw_pressure.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, dp, dp, vp]
     L.rw_solve.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int, vp, ctypes.POINTER(Info)]
     L.rw_ref_free.argtypes = [vp]
     L.rw_hbs_free.argtypes = [vp]
@@ -353,6 +354,13 @@ class Refinement:
         n_src = src.shape[0] if hasattr(src, "shape") else len(src) // 2
         _check(load().rw_stokeslet_data(self.h, n_src, _ptr(src), nrhs, _ptr(f), _ptr(g, True), _stream(stream)))
         return g
+
+    def pressure(self, tau, targets, p, nrhs=1, stream=None):
+        """p = pressure of the double-layer velocity of tau at targets (nt, 2);
+        p: (nrhs, nt)."""
+        nt = targets.shape[0] if hasattr(targets, "shape") else len(targets) // 2
+        _check(load().rw_pressure(self.h, nrhs, _ptr(tau), nt, _ptr(targets), _ptr(p, True), _stream(stream)))
+        return p
 
     def solve(self, g, tau, nrhs=1, targets=None, u=None, mode=MODE_DIRECT, stream=None):
         info = Info()

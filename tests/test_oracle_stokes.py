@@ -8,6 +8,10 @@
 * closed form: the interior velocity of the solved density equals the
   Stokeslet field that made the data (Sec. 5 preamble), with spectral decay
   of the error under panel refinement;
+* closed form for the pressure: the double-layer pressure of the solved
+  density equals the Stokeslet pressure up to one constant (pressure is
+  fixed up to a constant by the velocity), with spectral decay; a sign error
+  in either term of the pressure kernel breaks the constant offset;
 * the row-at-a-time residual agrees with the dense matrix;
 * ELS equivalence (Eq. extendedlLinearSystem), Woodbury exactness for Q = L R
   (Eq. wood), truncated-SVD Woodbury accuracy, Lemma 3.1's bound, and the
@@ -94,6 +98,56 @@ def test_closed_form_refined_star():
     u = S.velocity(ref["n"], tau, tx, ty)
     ue = S.stokeslet_velocity(tx, ty, sx, sy, f)
     assert np.abs(u - ue).max() / np.abs(ue).max() < 1e-12
+
+
+def _pressure_offset_spread(nodes, sx, sy, f, tx, ty, kernel=None):
+    """Spread of p_DLP(tau) - p_exact over the targets, relative to the
+    spread of p_exact (zero when they differ by one constant)."""
+    g = S.boundary_data(nodes, sx, sy, f)
+    tau = np.linalg.solve(S.matrix(nodes), g)
+    p = (kernel or S.pressure)(nodes, tau, tx, ty)
+    pe = S.stokeslet_pressure(tx, ty, sx, sy, f)
+    diff = p - pe
+    return np.abs(diff - diff.mean(axis=0)).max() / np.abs(pe - pe.mean(axis=0)).max()
+
+
+def test_pressure_closed_form_up_to_a_constant():
+    sx, sy, f = I.stokeslets_star(0, nrhs=2)
+    tx, ty = I.targets_star(1)
+    spreads = [_pressure_offset_spread(D.wall_nodes("star", STAR, P), sx, sy, f, tx, ty) for P in (8, 16, 64)]
+    assert spreads[-1] < 1e-11
+    assert spreads[0] > spreads[1] > spreads[2]
+    # refined wall: the refined density's pressure meets the same closed form
+    ref = D.refine("star", STAR, 64, [62, 63, 0, 1], [3] * 4)
+    tau = DN.solve_refined(ref, S.boundary_data(ref["n"], sx, sy, f))
+    dp = S.pressure(ref["n"], tau, tx, ty) - S.stokeslet_pressure(tx, ty, sx, sy, f)
+    assert np.abs(dp - dp.mean(axis=0)).max() < 1e-10
+
+
+def test_pressure_pins_catch_sign_errors():
+    n = D.wall_nodes("star", STAR, 64)
+    sx, sy, f = I.stokeslets_star(0, nrhs=1)
+    tx, ty = I.targets_star(1)
+
+    def flipped(which):
+        def k(nodes, tau, tx_, ty_):
+            # the same sum with one term's sign flipped (a planted mistake)
+            tau = np.asarray(tau)[:, None] if np.ndim(tau) == 1 else np.asarray(tau)
+            rx = np.asarray(tx_)[:, None] - nodes["x"][None, :]
+            ry = np.asarray(ty_)[:, None] - nodes["y"][None, :]
+            r2 = rx * rx + ry * ry
+            rdn = rx * nodes["nx"][None, :] + ry * nodes["ny"][None, :]
+            ndt = nodes["nx"][None, :, None] * tau[0::2][None] + nodes["ny"][None, :, None] * tau[1::2][None]
+            rdt = rx[:, :, None] * tau[0::2][None] + ry[:, :, None] * tau[1::2][None]
+            a = -ndt / r2[:, :, None]
+            b = 2.0 * rdt * rdn[:, :, None] / (r2 * r2)[:, :, None]
+            s = (-a + b) if which == 0 else (a - b)
+            return np.sum(nodes["w"][None, :, None] * s, axis=1)[:, 0] / np.pi
+        return k
+
+    assert _pressure_offset_spread(n, sx, sy, f, tx, ty) < 1e-11
+    for which in (0, 1):
+        assert _pressure_offset_spread(n, sx, sy, f, tx, ty, flipped(which)) > 1e-3
 
 
 def test_apply_rows_matches_matrix():
