@@ -280,6 +280,16 @@ int rw_server_submit(rw_server_t s, const rw_request* req, long long* ticket);
 /* status: 1 queued or running, 0 done, < 0 the request's error code. */
 int rw_server_poll(rw_server_t s, long long ticket, int* status, double* latency_ms);
 int rw_server_wait(rw_server_t s, long long ticket, double* latency_ms);
+/* Factor reuse across requests: keep each request's refinement
+ * pre-computation (a1-a6) after it completes, up to max_bytes of device
+ * memory counted in the server's budget, keyed by (wall, panel_ids, levels);
+ * a request with the same key skips rw_refine_factor's work.  Least recently
+ * used entries are evicted beyond max_bytes or when a waiting request needs
+ * the memory.  0 (the default) disables the cache and frees its unused
+ * entries.  With a cache, walls must outlive the server. */
+int rw_server_set_cache(rw_server_t s, long long max_bytes);
+/* Cache hits and misses so far and the device bytes the cache holds. */
+int rw_server_stats(rw_server_t s, long long* hits, long long* misses, long long* cache_bytes);
 int rw_server_destroy(rw_server_t s);
 
 /* Batched solve of many refined walls (the paper

@@ -118,6 +118,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   }
   Np = np;
   Nn = Nk + Np;
+  require(added || w.curve.kind != RW_CURVE_NODES,
+          "refine: this wall was built from nodes; the added nodes must be given");
   if (added) {
     // the caller's nodes for the sub-panels (window order)
     require(added->size() == size_t(6) * Np, "refine: added nodes do not match the cut panels and levels");

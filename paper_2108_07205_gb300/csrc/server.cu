@@ -4,18 +4,27 @@
 // solve for nrhs right-hand sides and the velocity at targets.
 //
 // Requests wait in a FIFO queue and are admitted while the estimated device
-// memory of the admitted requests stays within the server's budget; each of
-// n_workers host threads owns a CUDA stream and runs admitted requests end to
-// end, so the kernels of different requests overlap on the device.  When a
-// request finishes, its memory is released (stream ordered) and waiting
-// requests are admitted.  Every request's result depends only on its own
-// inputs (deterministic kernels and seeds), so it is the same alone and in
-// the mix.
+// memory of the admitted requests and of the factor cache stays within the
+// server's budget; each of n_workers host threads runs admitted requests end
+// to end on its own CUDA stream (owned by the server), so the kernels of
+// different requests overlap on the device.  When a request finishes, its
+// memory is released (stream ordered) and waiting requests are admitted.
+// Every request's result depends only on its own inputs (deterministic
+// kernels and seeds), so it is the same alone and in the mix.
+//
+// Factor cache (optional, rw_server_set_cache): the pre-computation of a
+// refinement is kept after its request, keyed by (wall, cut panels, levels),
+// and a later request with the same key skips it (factor reuse across steps).
+// Entries are evicted least recently used when the cache exceeds its
+// capacity or when a waiting request needs the memory; solves on one cached
+// refinement are serialised (they share its solve workspace).
 #include "handles.cuh"
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <string>
+#include <memory>
 #include <mutex>
 #include <thread>
 
@@ -39,6 +48,14 @@ struct Req {
 
 }  // namespace
 
+struct CachedRef {
+  std::unique_ptr<rw::Refinement> ref;
+  std::mutex solve_mu;  // one solve at a time on a cached refinement
+  long long bytes = 0;
+  int users = 0;
+  unsigned long long last = 0;
+};
+
 struct rw_server_s {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -48,9 +65,26 @@ struct rw_server_s {
   long long budget = 0, in_use = 0;
   bool stopping = false;
   std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;  // one per worker; destroyed after the cache
   long long completed = 0;
+  // factor cache
+  long long cache_cap = 0, cache_bytes = 0, hits = 0, misses = 0;
+  unsigned long long tick = 0;
+  std::map<std::string, std::shared_ptr<CachedRef>> cache;
 
-  void worker_loop();
+  void worker_loop(int w);
+  // Moves the least recently used entry without users into `out`; false if
+  // there is none.  mu held.
+  bool evict_one(std::vector<std::shared_ptr<CachedRef>>& out) {
+    auto best = cache.end();
+    for (auto it = cache.begin(); it != cache.end(); ++it)
+      if (it->second->users == 0 && (best == cache.end() || it->second->last < best->second->last)) best = it;
+    if (best == cache.end()) return false;
+    cache_bytes -= best->second->bytes;
+    out.push_back(best->second);
+    cache.erase(best);
+    return true;
+  }
 };
 
 namespace {
@@ -72,33 +106,73 @@ long long estimate_bytes(const rw_hbs_s* h, const std::vector<int>& levels, int 
   return 8 * d + (64LL << 20);
 }
 
+std::string cache_key(const Req& r) {
+  std::string k = std::to_string(reinterpret_cast<uintptr_t>(r.wall)) + "|";
+  for (size_t i = 0; i < r.panels.size(); ++i) k += std::to_string(r.panels[i]) + ":" + std::to_string(r.levels[i]) + ",";
+  return k;
+}
+
 }  // namespace
 
-void rw_server_s::worker_loop() {
-  cudaStream_t s = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+void rw_server_s::worker_loop(int wi) {
+  const cudaStream_t s = streams[wi];
+  rw::AllocStreamScope alloc_scope(s);  // every allocation of a request is stream ordered
   for (;;) {
     long long t = 0;
     Req* r = nullptr;
+    std::vector<std::shared_ptr<CachedRef>> evicted;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] {
-        if (stopping && queue.empty()) return true;
-        if (queue.empty()) return false;
-        const Req& head = reqs[queue.front()];
-        return in_use + head.est_bytes <= budget || in_use == 0;  // FIFO; one request always fits
-      });
+      for (;;) {
+        if (!queue.empty()) {
+          const Req& head = reqs[queue.front()];
+          // FIFO; cached factors give way to a waiting request; one request
+          // always fits when nothing else runs
+          while (in_use + cache_bytes + head.est_bytes > budget && evict_one(evicted)) {}
+          if (in_use + cache_bytes + head.est_bytes <= budget || in_use == 0) break;
+        } else if (stopping) {
+          break;
+        }
+        cv_work.wait(lk);
+      }
       if (queue.empty()) break;
       t = queue.front();
       queue.pop_front();
       r = &reqs[t];
       in_use += r->est_bytes;
     }
+    evicted.clear();  // cached refinements freed outside the lock
     int status = RW_OK;
     std::string err;
+    std::shared_ptr<CachedRef> ce;
+    const std::string key = cache_key(*r);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (cache_cap > 0) {
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+          ce = it->second;
+          ++ce->users;
+          ce->last = ++tick;
+          ++hits;
+        } else {
+          ++misses;
+        }
+      }
+    }
+    std::unique_ptr<rw::Refinement> own;
     try {
-      rw::Refinement ref;
-      ref.factor(r->wall->wall, r->panels, r->levels, s);
+      const rw::Refinement* refp = nullptr;
+      if (ce) {
+        refp = ce->ref.get();
+      } else {
+        own.reset(new rw::Refinement);
+        own->factor(r->wall->wall, r->panels, r->levels, s);
+        refp = own.get();
+      }
+      const rw::Refinement& ref = *refp;
+      std::unique_lock<std::mutex> solve_lock;
+      if (ce) solve_lock = std::unique_lock<std::mutex>(ce->solve_mu);
       const int Nn = ref.Nn;
       rw::TBuf<double> dsrc(r->src.size(), s), df(r->f.size(), s), dtg(std::max<size_t>(r->targets.size(), 1), s);
       RW_CUDA(cudaMemcpyAsync(dsrc.p, r->src.data(), r->src.size() * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -127,20 +201,33 @@ void rw_server_s::worker_loop() {
       status = RW_ERR_INVALID;
       err = e.what();
     }
-    // the refinement's memory is released (stream ordered) when `ref` leaves scope above
     cudaStreamSynchronize(s);
     {
       std::lock_guard<std::mutex> lk(mu);
+      if (ce) --ce->users;
+      // a new factorisation that fits joins the cache
+      if (own && status == RW_OK && cache_cap > 0 && (long long)own->bytes <= cache_cap && !cache.count(key)) {
+        auto e = std::make_shared<CachedRef>();
+        e->bytes = (long long)own->bytes;
+        e->ref = std::move(own);
+        e->last = ++tick;
+        cache_bytes += e->bytes;
+        cache.emplace(key, e);
+        while (cache_bytes > cache_cap && evict_one(evicted)) {}
+      }
       r->status = status;
       r->err = err;
       r->t_done = Clock::now();
       in_use -= r->est_bytes;
       ++completed;
     }
+    // the request's own refinement (if not cached) and evicted entries are
+    // released here, stream ordered, outside the lock
+    own.reset();
+    evicted.clear();
     cv_done.notify_all();
     cv_work.notify_all();
   }
-  cudaStreamDestroy(s);
 }
 
 namespace {
@@ -156,13 +243,45 @@ int rw_server_create(int n_workers, long long max_device_bytes, rw_server_t* out
   sv->budget = max_device_bytes;
   int dev = 0;
   cudaGetDevice(&dev);
+  for (int i = 0; i < n_workers; ++i) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
+      delete sv;
+      return sfail(RW_ERR_CUDA, "rw_server_create: cannot create a worker stream");
+    }
+    sv->streams.push_back(st);
+  }
   for (int i = 0; i < n_workers; ++i)
-    sv->workers.emplace_back([sv, dev] {
+    sv->workers.emplace_back([sv, dev, i] {
       cudaSetDevice(dev);
-      sv->worker_loop();
+      sv->worker_loop(i);
     });
   *out = sv;
   rw::abi_clear_error();
+  return RW_OK;
+}
+
+int rw_server_set_cache(rw_server_t sv, long long max_bytes) {
+  if (!sv || max_bytes < 0) return sfail(RW_ERR_INVALID, "rw_server_set_cache: bad argument");
+  std::vector<std::shared_ptr<CachedRef>> evicted;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->cache_cap = max_bytes;
+    while (sv->cache_bytes > sv->cache_cap && sv->evict_one(evicted)) {}
+  }
+  evicted.clear();
+  sv->cv_work.notify_all();
+  rw::abi_clear_error();
+  return RW_OK;
+}
+
+int rw_server_stats(rw_server_t sv, long long* hits, long long* misses, long long* cache_bytes) {
+  if (!sv) return sfail(RW_ERR_INVALID, "rw_server_stats: null server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (hits) *hits = sv->hits;
+  if (misses) *misses = sv->misses;
+  if (cache_bytes) *cache_bytes = sv->cache_bytes;
   return RW_OK;
 }
 
@@ -237,6 +356,12 @@ int rw_server_destroy(rw_server_t sv) {
   }
   sv->cv_work.notify_all();
   for (auto& t : sv->workers) t.join();
+  // cached refinements release their memory on the worker streams, which go last
+  sv->cache.clear();
+  for (cudaStream_t st : sv->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
   delete sv;
   return RW_OK;
 }

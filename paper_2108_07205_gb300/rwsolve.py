@@ -87,7 +87,7 @@ EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_build_nodes", "rw_hbs_save
            "rw_stokeslet_data", "rw_pressure",
            "rw_solve", "rw_batch_create", "rw_batch_rows", "rw_batch_autotune", "rw_batch_solve",
            "rw_batch_free", "rw_server_create", "rw_server_submit", "rw_server_poll", "rw_server_wait",
-           "rw_server_destroy", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
+           "rw_server_destroy", "rw_server_set_cache", "rw_server_stats", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
 
 _lib = None
 
@@ -140,6 +140,9 @@ def load(build_if_missing=False):
     L.rw_server_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.rw_server_wait.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
     L.rw_server_destroy.argtypes = [vp]
+    L.rw_server_set_cache.argtypes = [vp, ctypes.c_longlong]
+    L.rw_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_longlong)]
     L.rw_profile.argtypes = [ctypes.c_int]
     L.rw_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int]
     L.rw_kernel_launches.argtypes = []
@@ -390,11 +393,22 @@ def refined_points(n_panels, levels):
 class Server:
     """Continuous-batching server over resident walls (C ABI rw_server_*)."""
 
-    def __init__(self, n_workers=4, max_device_bytes=64 << 30):
+    def __init__(self, n_workers=4, max_device_bytes=64 << 30, cache_bytes=0):
         h = ctypes.c_void_p()
         _check(load().rw_server_create(int(n_workers), int(max_device_bytes), ctypes.byref(h)))
         self.h = h
         self._keep = {}
+        if cache_bytes:
+            self.set_cache(cache_bytes)
+
+    def set_cache(self, max_bytes):
+        """Keep refinement factors for reuse by later requests (0 disables)."""
+        _check(load().rw_server_set_cache(self.h, int(max_bytes)))
+
+    def stats(self):
+        h, m, b = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().rw_server_stats(self.h, ctypes.byref(h), ctypes.byref(m), ctypes.byref(b)))
+        return {"hits": h.value, "misses": m.value, "cache_bytes": b.value}
 
     def submit(self, wall, panels, levels, src, f, nrhs=1, targets=None, mode=MODE_DIRECT):
         """Queue one request; returns (ticket, tau, u) with tau, u filled on completion.

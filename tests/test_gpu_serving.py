@@ -77,3 +77,34 @@ def test_tiny_budget_serves_one_at_a_time(walls):
         sv.wait(t)
         assert sv.poll(t)[0] == 0
     sv.close()
+
+
+def test_factor_cache_reuse(walls):
+    """A repeated (wall, panels, levels) request reuses the cached factors:
+    the same result as the first request, and a cache hit."""
+    a, b = walls
+    src, f = forces(3, 2)
+    src2, f2 = forces(4, 2)
+    sv = rwsolve.Server(n_workers=2, max_device_bytes=32 << 30, cache_bytes=8 << 30)
+    t1, tau1, _ = sv.submit(a, [5, 6, 7], [2, 3, 2], src, f, nrhs=2)
+    sv.wait(t1)
+    t2, tau2, _ = sv.submit(a, [5, 6, 7], [2, 3, 2], src, f, nrhs=2)       # same key, same data
+    t3, tau3, _ = sv.submit(a, [5, 6, 7], [2, 3, 2], src2, f2, nrhs=2)     # same key, new data
+    t4, tau4, _ = sv.submit(b, [5, 6, 7], [2, 3, 2], src, f, nrhs=2)       # other wall: a miss
+    for t in (t2, t3, t4):
+        sv.wait(t)
+    st = sv.stats()
+    assert st["hits"] == 2 and st["misses"] == 2 and st["cache_bytes"] > 0
+    assert np.array_equal(tau1, tau2)
+    # the cached factors solve new data like a fresh factorisation
+    r = a.refine([5, 6, 7], [2, 3, 2])
+    g = np.empty((2, 2 * r.stats()["n_n"]))
+    r.stokeslet_data(np.ascontiguousarray(src2), np.ascontiguousarray(f2), g, nrhs=2)
+    tau_ref = np.empty_like(g)
+    r.solve(g, tau_ref, nrhs=2)
+    assert rel(tau3, tau_ref) <= 1e-13
+    r.close()
+    # disabling the cache frees it
+    sv.set_cache(0)
+    assert sv.stats()["cache_bytes"] == 0
+    sv.close()
