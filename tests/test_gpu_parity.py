@@ -167,6 +167,23 @@ def test_exact_operator_and_multi_rhs_consistency(star64):
     ref.close()
 
 
+def test_many_rhs_take_the_gemm_sweeps(star64):
+    """From 16 right-hand sides the direct solve sweeps level by level with
+    batched GEMMs instead of the GEMV program: same bar against the oracle,
+    and the same solution as the program path (which sums in another order)."""
+    panels, levels = inputs.refinement_window(0, 64, 4, 3, 3)
+    ref = star64.refine(panels, levels)
+    o = D.refine("star", STAR, 64, panels, levels)
+    g, g_or, _ = data(ref, o, 11, 20)
+    tau = np.empty_like(g)
+    ref.solve(g, tau, nrhs=20)
+    assert rel(tau, DN.solve_refined(o, g_or.T).T) < 1e-9
+    tau8 = np.empty((8, g.shape[1]))
+    ref.solve(np.ascontiguousarray(g[:8]), tau8, nrhs=8)
+    assert rel(tau[:8], tau8) < 1e-11
+    ref.close()
+
+
 def test_invalid_refinements_rejected(star64):
     for panels, levels in (([3, 5], [2, 2]), ([64], [1]), ([1, 2], [2, 13]), ([4, 4], [1, 1])):
         with pytest.raises(rwsolve.RWError) as e:
