@@ -19,6 +19,8 @@ Modules
   stokes      Stokeslet, double-layer matrix with the N correction (Sec. 2,
               Remark 2.1), velocity evaluation.
   dense       dense solve of the refined system; ELS and Woodbury (Sec. 3.2-3.4).
+  holes       the wall with added holes (App. B): combined-field operator of
+              Eq. exterior_BIE on the holes with a graded singular rule.
 
 Parity status of each function is stated in its module docstring; every
 function here is pinned by ``tests/test_oracle_*.py`` against closed forms,

@@ -14,6 +14,14 @@ Workload recipes (the paper's geometries are not available, Sec. 5):
   targets x ~ U[-8, 8], |y| <= 0.1 (inside the 0.4-wide constriction).
 * time stepping: an 8-panel window starting at a seeded j0 that advances one
   panel per step (modulo P), levels ~ U{2..5} per step.
+* added holes (App. B, Sec. 5.2: three circles of 10 panels in the channel,
+  two below the centre line and one above; data from 5 exterior Stokeslets
+  plus 2, 2 and 1 Stokeslets inside the holes): circles of radius 0.12 at
+  (-7.5, -0.15), (6.5, -0.15), (8, 0.15), each x jittered by U[-0.3, 0.3];
+  in the star wall, circles of radius 0.1 at distance 0.35 from the centre,
+  angles 2 pi i / 3 + U[0, 0.4].  Stokeslets inside a hole sit within 0.4 R
+  of its centre; fluid targets are the wall's targets with those closer
+  than 2 R to a hole centre redrawn.
 """
 import numpy as np
 
@@ -90,3 +98,52 @@ def targets_star(seed, n=16):
 def targets_channel(seed, n=16):
     g = rng(seed)
     return g.uniform(-8.0, 8.0, size=n), g.uniform(-0.1, 0.1, size=n)
+
+
+def holes_channel(seed, n_panels=10, radius=0.12):
+    """Three circular holes in the constricted channel: list of dicts
+    (cx, cy, R, a, k, P)."""
+    g = rng(seed)
+    base = [(-7.5, -0.15), (6.5, -0.15), (8.0, 0.15)]
+    return [dict(cx=x + float(g.uniform(-0.3, 0.3)), cy=y, R=radius, a=0.0, k=1, P=n_panels) for x, y in base]
+
+
+def holes_star(seed, n_panels=10, radius=0.1, n=3, a=0.0, k=1):
+    """n holes inside the star wall at distance 0.35 from its centre."""
+    g = rng(seed)
+    out = []
+    for i in range(n):
+        th = 2.0 * np.pi * i / n + float(g.uniform(0.0, 0.4))
+        out.append(dict(cx=0.35 * np.cos(th), cy=0.35 * np.sin(th), R=radius, a=a, k=k, P=n_panels))
+    return out
+
+
+def stokeslets_in_holes(seed, holes, counts, nrhs=1):
+    """Point forces inside the holes (counts[i] in hole i, within 0.4 R of its
+    centre): positions (n,), (n,) and strengths (n, 2, nrhs)."""
+    g = rng(seed)
+    sx, sy = [], []
+    for h, c in zip(holes, counts):
+        for _ in range(c):
+            rad = 0.4 * h["R"] * np.sqrt(g.uniform())
+            th = g.uniform(0.0, 2.0 * np.pi)
+            sx.append(h["cx"] + rad * np.cos(th))
+            sy.append(h["cy"] + rad * np.sin(th))
+    f = g.standard_normal(size=(len(sx), 2, nrhs))
+    return np.asarray(sx), np.asarray(sy), f
+
+
+def targets_fluid(seed, holes, kind="channel", n=16):
+    """Targets of the wall's recipe, redrawn while closer than 2 R to a hole
+    centre."""
+    draw = targets_channel if kind == "channel" else targets_star
+    tx, ty = [], []
+    s = seed
+    while len(tx) < n:
+        x, y = draw(s, n)
+        s += 7919
+        for a, b in zip(x, y):
+            if all((a - h["cx"]) ** 2 + (b - h["cy"]) ** 2 >= (2.0 * h["R"]) ** 2 for h in holes) and len(tx) < n:
+                tx.append(a)
+                ty.append(b)
+    return np.asarray(tx), np.asarray(ty)
