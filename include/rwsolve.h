@@ -195,6 +195,38 @@ int rw_refine_factor(rw_hbs_t h, int n_cut, const int* panel_ids,
 int rw_refine_factor_nodes(rw_hbs_t h, int n_cut, const int* panel_ids, const int* levels,
                            const rw_nodes* added, void* stream, rw_ref_t* out);
 
+/* One hole added inside the wall (App. B): the closed curve
+ * x(t) = (cx, cy) + radius (1 + a cos(k t)) (cos t, sin t), t in [0, 2 pi),
+ * counter-clockwise, cut into n_panels panels equal in t with 16
+ * Gauss-Legendre points each (the paper's holes are circles, a = 0, with 10
+ * panels, Sec. 5.2).  Requirements: radius > 0, 0 <= a < 1, 0 <= k <= 64,
+ * 3 <= n_panels <= 256; the holes lie inside the wall's fluid region, apart
+ * from the wall and from one another (the library checks only that the
+ * holes' enclosing circles do not overlap). */
+typedef struct {
+  double cx, cy, radius, a;
+  int k;
+  int n_panels;
+} rw_hole;
+
+/* App. B (Eq. simple_ext) with the combined-field BIE of Eq. exterior_BIE on
+ * the holes: factor the wall with n_holes (1..8, at most 1024 hole points
+ * in all) holes added, nothing cut.  Unknowns: the wall's points (panel
+ * order) then the holes' points (hole by hole, panel by panel), interleaved
+ * (x, y) per point; N_c = 0, N_p = hole points.  The system is
+ *   [A_kk  A_kp] with A_kk = -1/2 I + D + N (the wall operator, N on the
+ *   [A_pk  A_pp]      wall only), A_pp = 1/2 I + D + S on the holes
+ * (log-singular single layer by product integration on each target's own
+ * panel and its neighbours), A_kp = the holes' combined field w_j (D + S) on
+ * the wall, A_pk = the wall's double layer w_j D on the holes.  The velocity
+ * (rw_solve targets) is the wall's double layer plus the holes' combined
+ * field; rw_pressure likewise.  The returned handle works with every rw_ref_t
+ * call (rw_solve in all modes, rw_apply_refined, rw_stokeslet_data,
+ * rw_pressure, rw_ref_nodes, batches); it borrows the wall, which must
+ * outlive it.  Errors: RW_ERR_INVALID (arguments, overlapping holes),
+ * RW_ERR_SINGULAR (A_pp or W not invertible), RW_ERR_OOM, RW_ERR_CUDA. */
+int rw_holes_factor(rw_hbs_t wall, int n_holes, const rw_hole* holes, void* stream, rw_ref_t* out);
+
 int rw_ref_stats_get(rw_ref_t r, rw_ref_stats* s);
 
 /* Copy the refined nodes in refined order (6 x N_n, as rw_hbs_nodes). */

@@ -299,6 +299,23 @@ int rw_refine_factor_nodes(rw_hbs_t h, int n_cut, const int* panel_ids, const in
   return rc;
 }
 
+int rw_holes_factor(rw_hbs_t h, int n_holes, const rw_hole* holes, void* stream, rw_ref_t* out) {
+  if (!h || !holes || !out || n_holes < 1) return fail(RW_ERR_INVALID, "rw_holes_factor: bad argument");
+  *out = nullptr;
+  std::unique_ptr<rw_ref_s> r(new rw_ref_s);
+  r->h = h;
+  int rc = guarded([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<rw::HoleSpec> hs;
+    for (int i = 0; i < n_holes; ++i)
+      hs.push_back(rw::HoleSpec{holes[i].cx, holes[i].cy, holes[i].radius, holes[i].a, holes[i].k, holes[i].n_panels});
+    r->ref.factor_holes(h->wall, hs, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  });
+  if (rc == RW_OK) *out = r.release();
+  return rc;
+}
+
 int rw_ref_stats_get(rw_ref_t r, rw_ref_stats* st) {
   if (!r || !st) return fail(RW_ERR_INVALID, "rw_ref_stats_get: null argument");
   const rw::Refinement& f = r->ref;
@@ -327,7 +344,7 @@ int rw_apply_refined(rw_ref_t r, int nrhs, const double* tau, double* y, void* s
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = size_t(2) * r->ref.Nn * nrhs;
     Arg at(tau, n, true, s), ay(y, n, false, s);
-    rw::apply_exact(r->ref.nn.view(), at.p, ay.p, nrhs, s);
+    r->ref.apply_nn(at.p, ay.p, nrhs, s);
     ay.finish(s);
     RW_CUDA(cudaStreamSynchronize(s));
   });
@@ -368,7 +385,7 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     }
     if (n_targets > 0) {
       Arg ax(targets, size_t(2) * n_targets, true, s), au(u, size_t(2) * n_targets * nrhs, false, s);
-      rw::eval_velocity(f.nn.view(), at.p, nrhs, n_targets, ax.p, au.p, s);
+      f.velocity(at.p, nrhs, n_targets, ax.p, au.p, s);
       au.finish(s);
     }
     at.finish(s);
@@ -393,7 +410,7 @@ int rw_pressure(rw_ref_t r, int nrhs, const double* tau, int n_targets, const do
     const rw::Refinement& f = r->ref;
     Arg at(tau, size_t(2) * f.Nn * nrhs, true, s), ax(targets, size_t(2) * n_targets, true, s);
     Arg ap(p, size_t(n_targets) * nrhs, false, s);
-    rw::eval_pressure(f.nn.view(), at.p, nrhs, n_targets, ax.p, ap.p, s);
+    f.pressure(at.p, nrhs, n_targets, ax.p, ap.p, s);
     ap.finish(s);
     RW_CUDA(cudaStreamSynchronize(s));
   });

@@ -1,5 +1,6 @@
 // Geometry and kernel-matrix evaluation kernels (Sec. 2, Sec. 3.1, Sec. 3.3).
 #include "eval.cuh"
+#include "dense.cuh"
 #include <algorithm>
 #include <cmath>
 
@@ -43,7 +44,7 @@ struct Pt { double x, y, dx, dy, ddx, ddy; };
 
 __device__ Pt curve_eval(const Curve& c, double t) {
   Pt q;
-  if (c.kind == RW_CURVE_STAR) {
+  if (c.kind == RW_CURVE_STAR || c.kind == kCurveHole) {
     const double a = c.p[0], k = c.p[1], sc = c.p[2];
     double ct, st, ck, sk;
     sincos(t, &st, &ct);
@@ -53,6 +54,7 @@ __device__ Pt curve_eval(const Curve& c, double t) {
     q.dx = r1 * ct - r * st; q.dy = r1 * st + r * ct;
     q.ddx = r2 * ct - 2.0 * r1 * st - r * ct;
     q.ddy = r2 * st + 2.0 * r1 * ct - r * st;
+    if (c.kind == kCurveHole) { q.x += c.p[3]; q.y += c.p[4]; }
   } else {
     // superellipse (A cos t, B sin t) (cos^p + sin^p)^(-1/p), y squeezed by
     // q(x) = 1 - delta (1 + cos(pi x / A)) / 2
@@ -104,7 +106,20 @@ __global__ void k_nodes(Curve c, const double* ta, const double* tb, int n_int, 
 struct Blk2 { double v[2][2]; };
 __device__ __forceinline__ Blk2 a_block(const NodesView& T, int t, const NodesView& Sv, int s, bool same_point) {
   Blk2 o;
-  const double ntx = T.nx[t], nty = T.ny[t], nsx = Sv.nx[s], nsy = Sv.ny[s], ws = Sv.w[s];
+  const double ws = Sv.w[s];
+  if (T.kind | Sv.kind) {
+    // a hole is involved (App. B): combined field of a hole source, double
+    // layer of a wall source at a hole point; never the same point
+    const double rx = T.x[t] - Sv.x[s], ry = T.y[t] - Sv.y[s];
+    const double r2 = rx * rx + ry * ry, inv = 1.0 / r2;
+    const double fac = ws * (rx * Sv.nx[s] + ry * Sv.ny[s]) * inv * inv * (1.0 / kPi);
+    const double sl = Sv.kind ? ws * (0.25 / kPi) : 0.0, lg = Sv.kind ? -0.5 * log(r2) : 0.0;
+    const double r[2] = {rx, ry};
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) o.v[a][b] = fac * r[a] * r[b] + sl * ((a == b ? lg : 0.0) + r[a] * r[b] * inv);
+    return o;
+  }
+  const double ntx = T.nx[t], nty = T.ny[t], nsx = Sv.nx[s], nsy = Sv.ny[s];
   const double nt[2] = {ntx, nty}, ns[2] = {nsx, nsy};
   if (same_point) {
     const double ta[2] = {-nty, ntx};
@@ -164,12 +179,16 @@ __global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesVie
   double* zy = ztab + max_M;
   double* zc = ztab + 2 * max_M;
   double* zs = ztab + 3 * max_M;
-  const int M = P.M;
+  const int M = P.M * (P.ncirc > 1 ? P.ncirc : 1);
   for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    const int c = q / P.M, qq = q - c * P.M;
+    const double ccx = P.ncirc > 1 ? P.circ[3 * c] : P.cx;
+    const double ccy = P.ncirc > 1 ? P.circ[3 * c + 1] : P.cy;
+    const double cR = P.ncirc > 1 ? P.circ[3 * c + 2] : P.R;
     double sn, cs;
-    sincospi(2.0 * q / M, &sn, &cs);
-    zx[q] = P.cx + P.R * cs;
-    zy[q] = P.cy + P.R * sn;
+    sincospi(2.0 * qq / P.M, &sn, &cs);
+    zx[q] = ccx + cR * cs;
+    zy[q] = ccy + cR * sn;
     zc[q] = cs;
     zs[q] = sn;
   }
@@ -239,11 +258,13 @@ __global__ void k_copy(const CopyProb* probs) {
     for (int i = threadIdx.x; i < P.m; i += blockDim.x) P.out[i + size_t(j) * P.ldo] = P.in[i + size_t(j) * P.ldi];
 }
 
-__global__ void k_velocity(NodesView nd, const double* tau, int nrhs, int nt, const double* tg, double* u) {
-  // one CTA per (target, right-hand side); sources split over the threads
+__global__ void k_velocity(NodesView nd, const double* tau, int ldt, int nt, const double* tg, double* u, int acc) {
+  // one CTA per (target, right-hand side); sources split over the threads.
+  // Wall sources carry the double layer; hole sources (kind 1) the combined
+  // field, whose single layer adds w_j S(x, y_j) tau_j.
   const int t = blockIdx.x, r = blockIdx.y;
   const double x = tg[2 * t], y = tg[2 * t + 1];
-  const double* tr = tau + size_t(r) * 2 * nd.n;
+  const double* tr = tau + size_t(r) * ldt;
   double ux = 0.0, uy = 0.0;
   for (int j = threadIdx.x; j < nd.n; j += blockDim.x) {
     const double rx = x - nd.x[j], ry = y - nd.y[j], r2 = rx * rx + ry * ry;
@@ -251,6 +272,11 @@ __global__ void k_velocity(NodesView nd, const double* tau, int nrhs, int nt, co
     const double rt = rx * tr[2 * j] + ry * tr[2 * j + 1];
     ux += fac * rx * rt;
     uy += fac * ry * rt;
+    if (nd.kind) {
+      const double c = nd.w[j] * (0.25 / kPi), lg = -0.5 * log(r2), q = rt / r2;
+      ux += c * (lg * tr[2 * j] + rx * q);
+      uy += c * (lg * tr[2 * j + 1] + ry * q);
+    }
   }
   __shared__ double sx[256], sy[256];
   sx[threadIdx.x] = ux;
@@ -261,35 +287,41 @@ __global__ void k_velocity(NodesView nd, const double* tau, int nrhs, int nt, co
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    u[size_t(r) * 2 * nt + 2 * t] = sx[0];
-    u[size_t(r) * 2 * nt + 2 * t + 1] = sy[0];
+    double* ur = u + size_t(r) * 2 * nt;
+    ur[2 * t] = (acc ? ur[2 * t] : 0.0) + sx[0];
+    ur[2 * t + 1] = (acc ? ur[2 * t + 1] : 0.0) + sy[0];
   }
 }
 
 // Pressure of the double-layer velocity (Sec. 2): p(x) = sum_j w_j P(x, y_j)
-// . tau_j, P_j = (1/pi)(-n_j / r^2 + 2 r_j (r . n) / r^4), mu = 1; one CTA per
-// (target, right-hand side), sources split over the threads.
-__global__ void k_pressure(NodesView nd, const double* tau, int nt, const double* tg, double* p) {
+// . tau_j, P_j = (1/pi)(-n_j / r^2 + 2 r_j (r . n) / r^4), mu = 1; hole
+// sources (kind 1) add the single layer's pressure w_j (r . tau_j) / (2 pi
+// r^2).  One CTA per (target, right-hand side), sources split over threads.
+__global__ void k_pressure(NodesView nd, const double* tau, int ldt, int nt, const double* tg, double* p, int acc) {
   const int t = blockIdx.x, r = blockIdx.y;
   const double x = tg[2 * t], y = tg[2 * t + 1];
-  const double* tr = tau + size_t(r) * 2 * nd.n;
-  double acc = 0.0;
+  const double* tr = tau + size_t(r) * ldt;
+  double dl = 0.0, sl = 0.0;
   for (int j = threadIdx.x; j < nd.n; j += blockDim.x) {
     const double rx = x - nd.x[j], ry = y - nd.y[j];
     const double inv = 1.0 / (rx * rx + ry * ry);
     const double ndt = nd.nx[j] * tr[2 * j] + nd.ny[j] * tr[2 * j + 1];
     const double rdt = rx * tr[2 * j] + ry * tr[2 * j + 1];
     const double rdn = rx * nd.nx[j] + ry * nd.ny[j];
-    acc += nd.w[j] * inv * (2.0 * rdt * rdn * inv - ndt);
+    dl += nd.w[j] * inv * (2.0 * rdt * rdn * inv - ndt);
+    if (nd.kind) sl += nd.w[j] * rdt * inv;
   }
   __shared__ double sp[256];
-  sp[threadIdx.x] = acc;
+  sp[threadIdx.x] = dl * (1.0 / kPi) + sl * (0.5 / kPi);
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) sp[threadIdx.x] += sp[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) p[size_t(r) * nt + t] = sp[0] * (1.0 / kPi);
+  if (threadIdx.x == 0) {
+    double* pr = p + size_t(r) * nt;
+    pr[t] = (acc ? pr[t] : 0.0) + sp[0];
+  }
 }
 
 __global__ void k_stokeslets(NodesView nd, int ns, const double* src, int nrhs, const double* f, double* g) {
@@ -404,6 +436,152 @@ __global__ void k_flux(NodesView nd, const double* x, int ldx, double* flux) {
   if (threadIdx.x == 0) flux[r] = red[0];
 }
 
+// y[T rows] (+)= A(T, S) x for two disjoint node sets, every 2 x 2 block
+// evaluated on the fly (App. B: the hole columns seen on the wall, the wall
+// columns seen on the holes).  One thread per (target point, right-hand side).
+__global__ void k_apply_cross(NodesView T, NodesView Sv, const double* x, int ldx, double* y, int ldy, int acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (i >= T.n) return;
+  const double* xr = x + size_t(r) * ldx;
+  double ux = 0.0, uy = 0.0;
+  for (int j = 0; j < Sv.n; ++j) {
+    const Blk2 B = a_block(T, i, Sv, j, false);
+    const double a = xr[2 * j], b = xr[2 * j + 1];
+    ux += B.v[0][0] * a + B.v[0][1] * b;
+    uy += B.v[1][0] * a + B.v[1][1] * b;
+  }
+  double* yr = y + size_t(r) * ldy;
+  yr[2 * i] = (acc ? yr[2 * i] : 0.0) + ux;
+  yr[2 * i + 1] = (acc ? yr[2 * i + 1] : 0.0) + uy;
+}
+
+// Moments M_n(t) = int_{-1}^{1} P_n(s) log|t - s| ds, n = 0..15, of the
+// Legendre polynomials against the logarithm.  Integration by parts with
+// P_n = (P_{n+1}' - P_{n-1}') / (2n + 1) gives M_n = 2 (Q_{n+1}(t) -
+// Q_{n-1}(t)) / (2n + 1), where Q_m(t) = (1/2) int P_m(s) / (t - s) ds (a
+// principal value for |t| < 1) obeys the Legendre three-term recurrence from
+// Q_0 = (1/2) log|(1 + t) / (1 - t)|, Q_1 = t Q_0 - 1.  For |t| < 1 the
+// recurrence runs forward; for |t| > 1, where Q_m is the recurrence's
+// minimal solution, it runs backward from a start index past which the
+// neglected dominant part is below rounding (Miller's algorithm) and is
+// normalised by Q_0.  M_0 is the elementary integral.
+__device__ void log_moments16(double t, double* M) {
+  double Q[17];
+  const double at = fabs(t);
+  if (at < 1.0) {
+    Q[0] = 0.5 * log((1.0 + t) / (1.0 - t));
+    Q[1] = t * Q[0] - 1.0;
+    for (int n = 1; n < 16; ++n) Q[n + 1] = ((2.0 * n + 1.0) * t * Q[n] - n * Q[n - 1]) / (n + 1.0);
+  } else {
+    const double rho = at + sqrt((at - 1.0) * (at + 1.0));
+    int n0 = 17 + int(ceil(40.0 / log(rho)));
+    n0 = min(n0, 20000);
+    double qn1 = 0.0, qn = 1.0;  // Q_{n+1}, Q_n up to a common factor
+    for (int n = n0; n >= 1; --n) {
+      const double qm = ((2.0 * n + 1.0) * t * qn - (n + 1.0) * qn1) / n;
+      qn1 = qn;
+      qn = qm;
+      if (n - 1 <= 16) Q[n - 1] = qn;
+      if (fabs(qn) > 1e200) {
+        qn *= 1e-200;
+        qn1 *= 1e-200;
+        for (int m = n - 1; m <= 16; ++m)
+          if (m >= 0) Q[m] *= 1e-200;
+      }
+    }
+    const double sc = 0.5 * log((t + 1.0) / (t - 1.0)) / Q[0];
+    for (int m = 0; m <= 16; ++m) Q[m] *= sc;
+  }
+  M[0] = (t + 1.0) * log(fabs(t + 1.0)) - (t - 1.0) * log(fabs(t - 1.0)) - 2.0;
+  for (int n = 1; n < 16; ++n) M[n] = 2.0 * (Q[n + 1] - Q[n - 1]) / (2.0 * n + 1.0);
+}
+
+// Dense A_pp = 1/2 I + D + S on the holes (App. B; Eq. exterior_BIE), column
+// major, ld = 2 N_p.  One CTA per target point i.  The double layer and the
+// r r^T / |r|^2 part of the Stokeslet are smooth along a hole: plain panel
+// rule (curvature and tangent limits on the diagonal).  The logarithm is
+// singular: on the target's own panel and its two neighbours (panels equal
+// in t, at least three per hole) its weights come from product integration
+// of the panel's degree-15 interpolant (Legendre form),
+//   int log|x_i - y(s)| f(s) ds ~ sum_j f_j [h |x'_j| lam_j(t) + w_j phi_j],
+//   lam_j(t) = omega_j sum_n (2n+1)/2 P_n(s_j) M_n(t),
+// with t the target's coordinate in the source panel's [-1, 1], h the
+// panel's half-width in t and phi_j = log|x_i - y_j| - log|t - s_j| (the
+// smooth remainder; log(h |x'_i|) at the target itself).
+constexpr int kMaxHoles = 8;
+struct HoleSet {
+  int nh;
+  int off[kMaxHoles + 1];
+  int P[kMaxHoles];
+};
+
+__global__ void __launch_bounds__(128) k_hole_matrix(NodesView hv, HoleSet hs, double* A, int ld) {
+  const int i = blockIdx.x;
+  int h = 0;
+  while (h + 1 < hs.nh && i >= hs.off[h + 1]) ++h;
+  const int P = hs.P[h], li = i - hs.off[h], qi = li >> 4, si = li & 15;
+  const double hw = kPi / P;  // half-width of a panel in t
+  __shared__ double Mn[3][16], lam[3][16];
+  if (threadIdx.x < 3) {
+    const int d = int(threadIdx.x) - 1;   // source panel q_i + d
+    log_moments16(c_glx[si] - 2.0 * d, Mn[threadIdx.x]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 48) {
+    const int pd = threadIdx.x >> 4, j = threadIdx.x & 15;
+    const double sj = c_glx[j];
+    double p0 = 1.0, p1 = sj, acc = 0.5 * Mn[pd][0] + 1.5 * sj * Mn[pd][1];
+    for (int n = 1; n < 15; ++n) {
+      const double p2 = ((2.0 * n + 1.0) * sj * p1 - n * p0) / (n + 1.0);
+      p0 = p1;
+      p1 = p2;
+      acc += (n + 1.5) * p2 * Mn[pd][n + 1];
+    }
+    lam[pd][j] = c_glw[j] * acc;
+  }
+  __syncthreads();
+  const double xi = hv.x[i], yi = hv.y[i];
+  const double c4 = 0.25 / kPi;
+  for (int j = threadIdx.x; j < hv.n; j += blockDim.x) {
+    const double wj = hv.w[j];
+    double b[2][2];
+    double wlog;  // weight of log|r| in the single layer
+    const int lj = j - hs.off[h];
+    int d = 2;
+    if (lj >= 0 && lj < 16 * P) {
+      d = (lj >> 4) - qi;
+      if (d > P / 2) d -= P;
+      if (d < -P / 2) d += P;
+    }
+    const int sj = lj & 15;
+    if (j == i) {
+      const double tx = -hv.ny[i], ty = hv.nx[i], t[2] = {tx, ty};
+      const double sp = wj / (c_glw[si] * hw);
+      wlog = hw * sp * lam[1][si] + wj * log(hw * sp);
+      const double kap = -hv.kappa[i] * wj * (0.5 / kPi);
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c)
+          b[a][c] = kap * t[a] * t[c] + c4 * wj * t[a] * t[c] + (a == c ? 0.5 - c4 * wlog : 0.0);
+    } else {
+      const double rx = xi - hv.x[j], ry = yi - hv.y[j], r2 = rx * rx + ry * ry, inv = 1.0 / r2;
+      const double r[2] = {rx, ry};
+      const double fac = wj * (rx * hv.nx[j] + ry * hv.ny[j]) * inv * inv * (1.0 / kPi);
+      if (d >= -1 && d <= 1) {
+        const double tloc = c_glx[si] - 2.0 * d;
+        const double sp = wj / (c_glw[sj] * hw);
+        wlog = hw * sp * lam[d + 1][sj] + wj * (0.5 * log(r2) - log(fabs(tloc - c_glx[sj])));
+      } else {
+        wlog = wj * 0.5 * log(r2);
+      }
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c)
+          b[a][c] = fac * r[a] * r[c] + c4 * wj * r[a] * r[c] * inv - (a == c ? c4 * wlog : 0.0);
+    }
+    for (int a = 0; a < 2; ++a)
+      for (int c = 0; c < 2; ++c) A[(2 * size_t(i) + a) + (2 * size_t(j) + c) * ld] = b[a][c];
+  }
+}
+
 int grid1(long long n) { return int(std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096))); }
 
 bool g_gl_ready = false;
@@ -436,8 +614,9 @@ void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S, const N
   if (mx == 0) return;
   int max_M = 1;
   for (auto& p : probs) {
-    require(p.M >= 0 && p.M <= 1024, "eval_idmat: at most 1024 proxy points");
-    max_M = std::max(max_M, p.M);
+    require(p.M >= 0 && idmat_nproxy(p) <= 1024, "eval_idmat: at most 1024 proxy points");
+    require(p.ncirc <= 1 || p.circ, "eval_idmat: circle list missing");
+    max_M = std::max(max_M, idmat_nproxy(p));
   }
   auto d = to_device_tmp(probs, s);
   dim3 grid(std::min(grid1(mx), 1024), int(probs.size()));
@@ -484,18 +663,55 @@ void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s) {
 }
 
 void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* u,
-                   cudaStream_t s) {
+                   cudaStream_t s, int ldt, bool accumulate) {
   if (nt <= 0 || nrhs <= 0) return;
+  if (nodes.n <= 0) {
+    if (!accumulate) fill_zero(u, size_t(2) * nt * nrhs, s);
+    return;
+  }
   ProfScope prof_(KC_EVAL, s);
-  k_velocity<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, nrhs, nt, targets, u);
+  k_velocity<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, ldt > 0 ? ldt : 2 * nodes.n, nt, targets, u, accumulate);
   RW_CHECK_LAUNCH();
 }
 
 void eval_pressure(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* p,
-                   cudaStream_t s) {
+                   cudaStream_t s, int ldt, bool accumulate) {
   if (nt <= 0 || nrhs <= 0) return;
+  if (nodes.n <= 0) {
+    if (!accumulate) fill_zero(p, size_t(nt) * nrhs, s);
+    return;
+  }
   ProfScope prof_(KC_EVAL, s);
-  k_pressure<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, nt, targets, p);
+  k_pressure<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, ldt > 0 ? ldt : 2 * nodes.n, nt, targets, p, accumulate);
+  RW_CHECK_LAUNCH();
+}
+
+void apply_cross(const NodesView& T, const NodesView& Sv, const double* x, int ldx, double* y, int ldy, int nrhs,
+                 bool accumulate, cudaStream_t s) {
+  if (T.n <= 0 || nrhs <= 0) return;
+  require(T.kind != Sv.kind, "apply_cross: the node sets must be a wall and holes");
+  ProfScope prof_(KC_EVAL, s);
+  k_apply_cross<<<dim3(ceil_div(T.n, 128), nrhs), 128, 0, s>>>(T, Sv, x, ldx, y, ldy, accumulate);
+  RW_CHECK_LAUNCH();
+}
+
+void eval_hole_matrix(const NodesView& holes, const std::vector<int>& panels, double* A, cudaStream_t s) {
+  require(!panels.empty() && int(panels.size()) <= kMaxHoles, "hole matrix: 1 to 8 holes");
+  require(holes.kind == 1, "hole matrix: node set is not a hole set");
+  ensure_gl();
+  HoleSet hs{};
+  hs.nh = int(panels.size());
+  int off = 0;
+  for (int h = 0; h < hs.nh; ++h) {
+    require(panels[h] >= 3, "hole matrix: at least three panels per hole");
+    hs.off[h] = off;
+    hs.P[h] = panels[h];
+    off += 16 * panels[h];
+  }
+  hs.off[hs.nh] = off;
+  require(off == holes.n, "hole matrix: panel counts do not match the nodes");
+  ProfScope prof_(KC_EVAL, s);
+  k_hole_matrix<<<holes.n, 128, 0, s>>>(holes, hs, A, 2 * holes.n);
   RW_CHECK_LAUNCH();
 }
 
@@ -507,20 +723,22 @@ void eval_stokeslets(const NodesView& nodes, int ns, const double* src, int nrhs
   RW_CHECK_LAUNCH();
 }
 
-void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, cudaStream_t s) {
+void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, cudaStream_t s, int ldx, int ldy) {
   if (nodes.n <= 0 || nrhs <= 0) return;
+  if (ldx <= 0) ldx = 2 * nodes.n;
+  if (ldy <= 0) ldy = 2 * nodes.n;
   TBuf<double> flux(nrhs, s);
   ProfScope prof_(KC_EVAL, s);
-  k_flux<<<nrhs, 256, 0, s>>>(nodes, x, 2 * nodes.n, flux.p);
+  k_flux<<<nrhs, 256, 0, s>>>(nodes, x, ldx, flux.p);
   RW_CHECK_LAUNCH();
   for (int r0 = 0; r0 < nrhs; r0 += 4) {
     const int nr = std::min(4, nrhs - r0);
     const dim3 grid(ceil_div(nodes.n, NB_T));
     switch (nr) {
-      case 1: k_apply_exact<1><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
-      case 2: k_apply_exact<2><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
-      case 3: k_apply_exact<3><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
-      default: k_apply_exact<4><<<grid, NB_T, 0, s>>>(nodes, x, 2 * nodes.n, y, 2 * nodes.n, flux.p, r0); break;
+      case 1: k_apply_exact<1><<<grid, NB_T, 0, s>>>(nodes, x, ldx, y, ldy, flux.p, r0); break;
+      case 2: k_apply_exact<2><<<grid, NB_T, 0, s>>>(nodes, x, ldx, y, ldy, flux.p, r0); break;
+      case 3: k_apply_exact<3><<<grid, NB_T, 0, s>>>(nodes, x, ldx, y, ldy, flux.p, r0); break;
+      default: k_apply_exact<4><<<grid, NB_T, 0, s>>>(nodes, x, ldx, y, ldy, flux.p, r0); break;
     }
     RW_CHECK_LAUNCH();
   }

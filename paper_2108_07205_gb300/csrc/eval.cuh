@@ -22,13 +22,19 @@ void gauss_legendre16(double* x, double* w);
 void eval_nodes(const Curve& c, const double* ta, const double* tb, int n_int,
                 double* out, int ld, cudaStream_t s);
 
+// Internal curve kind of a hole: x(t) = c + R (1 + a cos(k t)) (cos t, sin t),
+// p = {a, k, R, cx, cy} (counter-clockwise; the normal points into the fluid).
+constexpr int kCurveHole = 100;
+
 // Columns of an ID matrix, written transposed: W (ncol x m) holds Y^T.
 // kind 0 ("outgoing", rows of A): Y[i, :] = [A(cand_i, e1) | A(cand_i, e2) |
 //   S(x_i, z_q) e_b, D(x_i, z_q) e_b for proxy points z_q | n_i]
 // kind 1 ("incoming", columns of A): Y[i, :] = [A(e1, cand_i)^T |
 //   A(e2, cand_i)^T | w_i D(z_q, x_i)[a', .] for proxy points | w_i n_i].
 // Candidates live in node set S; e1 in E1 and e2 in E2.  Proxy points are
-// z_q = c + R (cos 2 pi q / M, sin 2 pi q / M) with outward normal.
+// z_q = c + R (cos 2 pi q / M, sin 2 pi q / M) with outward normal; with
+// ncirc > 1 the proxies are the union of M points on each of the circles
+// circ[3 c .. 3 c + 2] = (cx, cy, R) (device array), as for several holes.
 struct IdMatProb {
   int kind;
   int m;
@@ -43,7 +49,10 @@ struct IdMatProb {
   double* W;
   int ldw;
   int ncol;
+  int ncirc;
+  const double* circ;
 };
+inline int idmat_nproxy(const IdMatProb& p) { return p.M * (p.ncirc > 1 ? p.ncirc : 1); }
 inline int idmat_ncol(int kind, int n1, int n2, int M, int normal) {
   return n1 + n2 + (kind == 0 ? 4 * M : 2 * M) + (normal ? 1 : 0);
 }
@@ -85,14 +94,25 @@ struct CopyProb {
 };
 void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s);
 
-// Velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets (Sec. 2.1).
-// targets: 2 x nt; tau: 2N x nrhs (ld 2N); u: 2nt x nrhs (ld 2nt).
+// Velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets (Sec. 2.1); a hole
+// set (kind 1) adds its single layer sum_j w_j S(x, y_j) tau_j (App. B).
+// targets: 2 x nt; tau: 2N x nrhs (ld ldt, default 2N); u: 2nt x nrhs (ld
+// 2nt), overwritten or accumulated into.
 void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt,
-                   const double* targets, double* u, cudaStream_t s);
+                   const double* targets, double* u, cudaStream_t s, int ldt = 0, bool accumulate = false);
 
-// Pressure of the double-layer velocity at targets (Sec. 2): p (nt x nrhs).
+// Pressure of the same representation at targets (Sec. 2): p (nt x nrhs).
 void eval_pressure(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* p,
-                   cudaStream_t s);
+                   cudaStream_t s, int ldt = 0, bool accumulate = false);
+
+// y[T] (+)= A(T, S) x between a wall set and a hole set (either order),
+// entries evaluated on the fly; x: 2 S.n x nrhs (ld ldx), y: 2 T.n x nrhs.
+void apply_cross(const NodesView& T, const NodesView& S, const double* x, int ldx, double* y, int ldy, int nrhs,
+                 bool accumulate, cudaStream_t s);
+
+// Dense A_pp = 1/2 I + D + S on a hole set whose hole h has panels[h] equal
+// panels in t (16 points each, in order): A is 2N x 2N column major.
+void eval_hole_matrix(const NodesView& holes, const std::vector<int>& panels, double* A, cudaStream_t s);
 
 // g(x_i) = sum_s S(x_i, y_s) f_s (Eq. stokeslet, mu = 1) at every node.
 // src: 2 x ns; f: 2 x ns x nrhs; g: 2N x nrhs.
@@ -101,7 +121,8 @@ void eval_stokeslets(const NodesView& nodes, int ns, const double* src,
 
 // y = A x with A = -1/2 I + D + N on a node set, every entry evaluated on
 // the fly (the exact Nystrom operator of Sec. 2).  x, y: 2N x nrhs, ld 2N.
-void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, cudaStream_t s);
+void apply_exact(const NodesView& nodes, const double* x, double* y, int nrhs, cudaStream_t s, int ldx = 0,
+                 int ldy = 0);
 
 // Row-norm maximum of a column-major W (nr x nc): max_j ||W[:, j]|| into out.
 void max_colnorm(const double* W, int nr, int nc, int ld, double* out,

@@ -16,7 +16,7 @@ namespace rw {
 int IdBatch::add(const IdMatProb& spec, int sketch_cols, int sketch_width) {
   Job j;
   j.spec = spec;
-  j.spec.ncol = idmat_ncol(spec.kind, spec.n1, spec.n2, spec.M, spec.normal);
+  j.spec.ncol = idmat_ncol(spec.kind, spec.n1, spec.n2, idmat_nproxy(spec), spec.normal);
   if (j.spec.ncol > sketch_cols && sketch_width < j.spec.ncol) {
     j.sk_width = sketch_width;
     j.nr = sketch_width;
@@ -163,7 +163,7 @@ constexpr int kSketchTry = 96, kSketchMargin = 16;
 TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
                    const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
                    int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s) {
-  const int ncol = idmat_ncol(0, colspec.n1, colspec.n2, colspec.M, colspec.normal);
+  const int ncol = idmat_ncol(0, colspec.n1, colspec.n2, idmat_nproxy(colspec), colspec.normal);
   if (ncol > sketch_cols && sketch_width > kSketchTry && ncol > kSketchTry) {
     TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, kSketchTry, seed, chunk, s);
     if (t.k <= kSketchTry - kSketchMargin) return t;
@@ -184,7 +184,7 @@ TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdM
   sp.kind = 0;
   sp.m = mt;
   sp.cand = drows.p;
-  sp.ncol = idmat_ncol(0, sp.n1, sp.n2, sp.M, sp.normal);
+  sp.ncol = idmat_ncol(0, sp.n1, sp.n2, idmat_nproxy(sp), sp.normal);
   // Y^T for all rows, optionally sketched
   int nr = sp.ncol;
   TBuf<double> Yt(size_t(sp.ncol) * mt, s);
@@ -668,6 +668,35 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
     fwd_elems += (long long)LV.U.n * (l > 0) + (long long)LV.Vt.n * (l > 0) + (long long)LV.B.n * (l < L) + (long long)LV.D.n;
     bytes += LV.U.bytes() + LV.Vt.bytes() + LV.E.bytes() + LV.F.bytes() + LV.G.bytes() + LV.B.bytes() + LV.D.bytes();
   }
+}
+
+void Hbs::build_dense(DBuf<double>&& A, int npts, cudaStream_t s) {
+  N = npts;
+  require(N >= 1, "HBS: empty node set");
+  const int n = 2 * N;
+  require(A.n >= size_t(n) * n, "HBS: dense matrix too small");
+  L = 0;
+  node.assign(2, HbsNode());
+  node[1].lo = 0;
+  node[1].hi = N;
+  lev.clear();
+  lev.resize(1);
+  Level& LV = lev[0];
+  LV.D = std::move(A);
+  LV.oD = {0};
+  LV.oG = {0};
+  LV.G.alloc(size_t(n) * n);
+  TBuf<double> Dt(size_t(n) * n, s), Wk(size_t(n) * n, s);
+  batched_copy({CopyProb{LV.D.p, n, n, n, Dt.p, n}}, s);
+  DBuf<int> flag(1);
+  flag.zero(s);
+  batched_inverse({InvProb{Dt.p, LV.G.p, Wk.p, n, n, n, flag.p}}, s);
+  const auto hf = flag.download(s);
+  require(hf[0] == 0, "HBS inverse: singular dense block", RW_ERR_SINGULAR);
+  max_rank = 0;
+  inv_elems = (long long)LV.G.n;
+  fwd_elems = (long long)LV.D.n;
+  bytes = LV.G.bytes() + LV.D.bytes();
 }
 
 void Hbs::make_fp32(cudaStream_t s) {

@@ -102,6 +102,10 @@ class Hbs {
 
   // Build from a node set (positions on host in `nodes.hx/hy` for planning).
   void build(const Nodes& nodes, const Opts& o, cudaStream_t s);
+  // Single-leaf representation of a dense matrix A (2 npts x 2 npts, column
+  // major; the handle takes it over): the forward apply uses A, the inverse
+  // sweeps its inverse.  Throws RW_ERR_SINGULAR if A cannot be inverted.
+  void build_dense(DBuf<double>&& A, int npts, cudaStream_t s);
   // x = A^{-1} b, b and x: 2N x nrhs (ld 2N).  Template on the sweep type.
   void apply_inverse(const double* b, double* x, int nrhs, cudaStream_t s) const;
   // the same as a sequence of per-level launches with per-call temporaries

@@ -307,54 +307,56 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   Xp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
   if (kpk) hpp.apply_inverse_levels(Lp.p, Xp.p, kpk, s);
   tr.mark("X_p = A_pp^-1 L_p");
-  // a6: W = I + R X and its inverse
-  {
-    TBuf<double> W(size_t(k) * k, s), Ww(size_t(k) * k, s), Xc(size_t(2) * Nc * std::max(kk, 1), s);
-    k_identity<<<ceil_div((long long)k * k, 256), 256, 0, s>>>(W.p, k);
-    RW_CHECK_LAUNCH();
-    if (kk) gather_scatter(Xo.p, 2 * No, dc.p, Xc.p, 2 * Nc, nullptr, 2 * Nc, kk, s);
-    std::vector<GemmProb> g;
-    if (kk) g.push_back(GemmProb{Rkc.p, Xc.p, W.p, kk, kk, 2 * Nc, kk, 2 * Nc, k, 0, 0, 1.0, 1.0});
-    if (kk && kpk) g.push_back(GemmProb{Rkp.p, Xp.p, W.p + size_t(kk) * k, kk, kpk, 2 * Np, kk, 2 * Np, k, 0, 0, 1.0, 1.0});
-    if (kk && kpk) g.push_back(GemmProb{Rpk.p, Xo.p, W.p + kk, kpk, kk, 2 * No, kpk, 2 * No, k, 0, 0, 1.0, 1.0});
-    batched_gemm(g, s);
-    Winv.alloc(std::max<size_t>(size_t(k) * k, 1));
-    DBuf<int> flag(1);
-    DBuf<double> norms(2);
-    flag.zero(s);
-    norms.zero(s);
-    if (k) {
-      k_norm1<<<ceil_div(32LL * k, 256), 256, 0, s>>>(W.p, k, norms.p, 0);
-      RW_CHECK_LAUNCH();
-    }
-    batched_inverse({InvProb{W.p, Winv.p, Ww.p, k, k, k, flag.p}}, s);
-    if (k) {
-      k_norm1<<<ceil_div(32LL * k, 256), 256, 0, s>>>(Winv.p, k, norms.p, 1);
-      RW_CHECK_LAUNCH();
-    }
-    // the solve program depends on the buffers, not on their values: the host
-    // builds it while the GPU forms W and W^-1
-    build_solve_program(s);
-    auto hf = flag.download(s);
-    require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
-    const auto hn = norms.download(s);
-    cond_w = hn[0] * hn[1];
-  }
+  form_w(s);
   tr.mark("W, W^-1, solve program");
   bytes = Lo.bytes() + Lp.bytes() + Rkc.bytes() + Rkp.bytes() + Rpk.bytes() + Xo.bytes() + Xp.bytes() + Winv.bytes() +
           hpp.bytes + pn.buf.bytes() + nn.buf.bytes();
 }
 
+void Refinement::form_w(cudaStream_t s) {
+  TBuf<double> W(size_t(k) * k, s), Ww(size_t(k) * k, s), Xc(size_t(2) * Nc * std::max(kk, 1), s);
+  k_identity<<<ceil_div((long long)k * k, 256), 256, 0, s>>>(W.p, k);
+  RW_CHECK_LAUNCH();
+  if (kk && Nc) gather_scatter(Xo.p, 2 * No, dc.p, Xc.p, 2 * Nc, nullptr, 2 * Nc, kk, s);
+  std::vector<GemmProb> g;
+  if (kk && Nc) g.push_back(GemmProb{Rkc.p, Xc.p, W.p, kk, kk, 2 * Nc, kk, 2 * Nc, k, 0, 0, 1.0, 1.0});
+  if (kk && kpk) g.push_back(GemmProb{Rkp.p, Xp.p, W.p + size_t(kk) * k, kk, kpk, 2 * Np, kk, 2 * Np, k, 0, 0, 1.0, 1.0});
+  if (kk && kpk) g.push_back(GemmProb{Rpk.p, Xo.p, W.p + kk, kpk, kk, 2 * No, kpk, 2 * No, k, 0, 0, 1.0, 1.0});
+  batched_gemm(g, s);
+  Winv.alloc(std::max<size_t>(size_t(k) * k, 1));
+  DBuf<int> flag(1);
+  DBuf<double> norms(2);
+  flag.zero(s);
+  norms.zero(s);
+  if (k) {
+    k_norm1<<<ceil_div(32LL * k, 256), 256, 0, s>>>(W.p, k, norms.p, 0);
+    RW_CHECK_LAUNCH();
+  }
+  batched_inverse({InvProb{W.p, Winv.p, Ww.p, k, k, k, flag.p}}, s);
+  if (k) {
+    k_norm1<<<ceil_div(32LL * k, 256), 256, 0, s>>>(Winv.p, k, norms.p, 1);
+    RW_CHECK_LAUNCH();
+  }
+  // the solve program depends on the buffers, not on their values: the host
+  // builds it while the GPU forms W and W^-1
+  build_solve_program(s);
+  auto hf = flag.download(s);
+  require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
+  const auto hn = norms.download(s);
+  cond_w = hn[0] * hn[1];
+}
+
 void Refinement::woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t s) const {
   if (k == 0) return;
   TBuf<double> yc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s), z(size_t(k) * nrhs, s);
-  gather_scatter(yo, 2 * No, dc.p, yc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
-  // r = R y
+  if (Nc) gather_scatter(yo, 2 * No, dc.p, yc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
+  // r = R y (with nothing cut, the k rows of R are R_kp alone)
   std::vector<GemvProb<double>> p1;
-  if (kk) p1.push_back(GemvProb<double>{Rkc.p, yc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
+  if (kk && Nc) p1.push_back(GemvProb<double>{Rkc.p, yc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
   if (kpk) p1.push_back(GemvProb<double>{Rpk.p, yo, r.p + kk, kpk, 2 * No, kpk, 2 * No, k, 1.0, 0.0});
   matvec<double>(p1, nrhs, s);
-  if (kk && Np) matvec<double>({GemvProb<double>{Rkp.p, yp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, 1.0}}, nrhs, s);
+  if (kk && Np)
+    matvec<double>({GemvProb<double>{Rkp.p, yp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, Nc ? 1.0 : 0.0}}, nrhs, s);
   // z = W^{-1} r
   matvec<double>({GemvProb<double>{Winv.p, r.p, z.p, k, k, k, k, k, 1.0, 0.0}}, nrhs, s);
   // y -= X z
@@ -375,12 +377,14 @@ void Refinement::emit_solve(Program& P, int gb, long long g_off, int ldg, int tb
   const int pb = hpp.emit_inverse_sweep(P, 2, WS, gp, -1, WS, yp, -1);
   int p = std::max(pa, pb);
   if (k > 0) {
-    const long long yc = P.ws_alloc(2LL * Nc), r = P.ws_alloc(k), z = P.ws_alloc(k);
-    P.copy(p++, 2 * Nc, WS, yo, -1, dc.p, WS, yc, -1, nullptr);
-    if (kk) P.gemv(p, Rkc.p, kk, 2 * Nc, kk, WS, yc, -1, WS, r, -1, 1.0, 0.0);
+    const long long yc = P.ws_alloc(std::max(2LL * Nc, 1LL)), r = P.ws_alloc(k), z = P.ws_alloc(k);
+    if (Nc) {
+      P.copy(p++, 2 * Nc, WS, yo, -1, dc.p, WS, yc, -1, nullptr);
+      if (kk) P.gemv(p, Rkc.p, kk, 2 * Nc, kk, WS, yc, -1, WS, r, -1, 1.0, 0.0);
+    }
     if (kpk) P.gemv(p, Rpk.p, kpk, 2 * No, kpk, WS, yo, -1, WS, r + kk, -1, 1.0, 0.0);
-    ++p;
-    if (kk && Np) P.gemv(p++, Rkp.p, kk, 2 * Np, kk, WS, yp, -1, WS, r, -1, 1.0, 1.0);
+    if (kk && Np) P.gemv(p + 1, Rkp.p, kk, 2 * Np, kk, WS, yp, -1, WS, r, -1, 1.0, Nc ? 1.0 : 0.0);
+    p += 2;
     P.gemv(p++, Winv.p, k, k, k, WS, r, -1, WS, z, -1, 1.0, 0.0);
     if (kk) P.gemv(p, Xo.p, 2 * No, kk, 2 * No, WS, z, -1, WS, yo, -1, -1.0, 1.0);
     if (kpk) P.gemv(p, Xp.p, 2 * Np, kpk, 2 * Np, WS, z + kk, -1, WS, yp, -1, -1.0, 1.0);
@@ -435,7 +439,7 @@ void Refinement::solve_refined(const double* g, double* tau, int nrhs, int steps
   const size_t n = size_t(2) * Nn * nrhs;
   TBuf<double> r(n, s), d(n, s);
   for (int it = 0; it < steps; ++it) {
-    apply_exact(nn.view(), tau, r.p, nrhs, s);
+    apply_nn(tau, r.p, nrhs, s);
     // r = g - A tau ; tau += A_ext^{-1} r
     axpby(g, r.p, n, 1.0, -1.0, s);
     solve_direct(r.p, d.p, nrhs, s);
@@ -443,17 +447,52 @@ void Refinement::solve_refined(const double* g, double* tau, int nrhs, int steps
   }
 }
 
+void Refinement::apply_nn(const double* x, double* y, int nrhs, cudaStream_t s) const {
+  if (!holes) {
+    apply_exact(nn.view(), x, y, nrhs, s);
+    return;
+  }
+  // [y_k; y_p] = [A_kk x_k + A_kp x_p; A_pk x_k + A_pp x_p]; wall rows first
+  const int ld = 2 * Nn, ko = 2 * No;
+  const NodesView VW = wall->nodes.view(), VP = pn.view();
+  apply_exact(VW, x, y, nrhs, s, ld, ld);
+  apply_cross(VW, VP, x + ko, ld, y, ld, nrhs, true, s);
+  apply_cross(VP, VW, x, ld, y + ko, ld, nrhs, false, s);
+  matvec<double>({GemvProb<double>{hpp.lev[0].D.p, x + ko, y + ko, 2 * Np, 2 * Np, 2 * Np, ld, ld, 1.0, 1.0}}, nrhs, s);
+}
+
+void Refinement::velocity(const double* tau, int nrhs, int nt, const double* targets, double* u,
+                          cudaStream_t s) const {
+  if (!holes) {
+    eval_velocity(nn.view(), tau, nrhs, nt, targets, u, s);
+    return;
+  }
+  eval_velocity(wall->nodes.view(), tau, nrhs, nt, targets, u, s, 2 * Nn, false);
+  eval_velocity(pn.view(), tau + 2 * No, nrhs, nt, targets, u, s, 2 * Nn, true);
+}
+
+void Refinement::pressure(const double* tau, int nrhs, int nt, const double* targets, double* p,
+                          cudaStream_t s) const {
+  if (!holes) {
+    eval_pressure(nn.view(), tau, nrhs, nt, targets, p, s);
+    return;
+  }
+  eval_pressure(wall->nodes.view(), tau, nrhs, nt, targets, p, s, 2 * Nn, false);
+  eval_pressure(pn.view(), tau + 2 * No, nrhs, nt, targets, p, s, 2 * Nn, true);
+}
+
 void Refinement::apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const {
   wall->hbs.apply_forward(xo, yo, nrhs, s);
   hpp.apply_forward(xp, yp, nrhs, s);
   if (k == 0) return;
   TBuf<double> xc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s);
-  gather_scatter(xo, 2 * No, dc.p, xc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
+  if (Nc) gather_scatter(xo, 2 * No, dc.p, xc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
   std::vector<GemvProb<double>> p1;
-  if (kk) p1.push_back(GemvProb<double>{Rkc.p, xc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
+  if (kk && Nc) p1.push_back(GemvProb<double>{Rkc.p, xc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
   if (kpk) p1.push_back(GemvProb<double>{Rpk.p, xo, r.p + kk, kpk, 2 * No, kpk, 2 * No, k, 1.0, 0.0});
   matvec<double>(p1, nrhs, s);
-  if (kk && Np) matvec<double>({GemvProb<double>{Rkp.p, xp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, 1.0}}, nrhs, s);
+  if (kk && Np)
+    matvec<double>({GemvProb<double>{Rkp.p, xp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, Nc ? 1.0 : 0.0}}, nrhs, s);
   std::vector<GemvProb<double>> p2;
   if (kk) p2.push_back(GemvProb<double>{Lo.p, r.p, yo, 2 * No, kk, 2 * No, k, 2 * No, 1.0, 1.0});
   if (kpk) p2.push_back(GemvProb<double>{Lp.p, r.p + kk, yp, 2 * Np, kpk, 2 * Np, k, 2 * Np, 1.0, 1.0});

@@ -20,9 +20,18 @@ struct SideStreams {
   ~SideStreams();
 };
 
+// One added hole (App. B): x(t) = c + R (1 + a cos(k t)) (cos t, sin t),
+// P panels equal in t.
+struct HoleSpec {
+  double cx, cy, R, a;
+  int k, P;
+};
+
 struct Refinement {
   SideStreams streams;  // first member: destroyed last
   const Wall* wall = nullptr;
+  bool holes = false;                  // App. B: holes added, nothing cut
+  std::vector<HoleSpec> hole_specs;
   std::vector<int> panels, levels;     // cut panels (window order) and levels
   int No = 0, Nk = 0, Nc = 0, Np = 0, Nn = 0;
   std::vector<int> Ic, Ik;             // point indices into the wall
@@ -51,6 +60,17 @@ struct Refinement {
   // kappa) in window order; without it they are evaluated on the wall's curve
   void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s,
               const std::vector<double>* added = nullptr);
+  // App. B: holes added inside the wall (no point cut).  The system is
+  // [A_kk A_kp; A_pk A_pp] with A_pp = 1/2 I + D + S on the holes (dense,
+  // singular rule), A_kp the holes' combined field on the wall and A_pk the
+  // wall's double layer on the holes; Q = [0 A_kp; A_pk 0] ~ L R.
+  void factor_holes(const Wall& w, const std::vector<HoleSpec>& holes, cudaStream_t s);
+  // y = A_nn x, the exact refined (or holed) operator, entries on the fly
+  // (the dense hole block from its stored matrix).  x, y: 2Nn x nrhs.
+  void apply_nn(const double* x, double* y, int nrhs, cudaStream_t s) const;
+  // Velocity / pressure of a density tau (2Nn x nrhs) at targets (2 x nt).
+  void velocity(const double* tau, int nrhs, int nt, const double* targets, double* u, cudaStream_t s) const;
+  void pressure(const double* tau, int nrhs, int nt, const double* targets, double* p, cudaStream_t s) const;
   // Direct solve, device buffers: g, tau (2Nn x nrhs): one persistent launch
   // per 8 right-hand sides.  solve_direct_levels is the same computation as
   // a sequence of per-level launches.
@@ -67,6 +87,11 @@ struct Refinement {
   // ext-space operator y = (A~ + L R) x (FP64)
   void apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
   ~Refinement();
+
+ private:
+  // a6 and the solve program, shared by both factorisations: W = I + R X,
+  // W^{-1}, its condition estimate, and the persistent solve program.
+  void form_w(cudaStream_t s);
 };
 
 }  // namespace rw

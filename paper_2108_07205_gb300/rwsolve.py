@@ -74,13 +74,18 @@ class Info(ctypes.Structure):
                 ("cond_w", ctypes.c_double)]
 
 
+class HoleDesc(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("radius", ctypes.c_double), ("a", ctypes.c_double),
+                ("k", ctypes.c_int), ("n_panels", ctypes.c_int)]
+
+
 class NodesDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("nx", ctypes.c_void_p),
                 ("ny", ctypes.c_void_p), ("w", ctypes.c_void_p), ("kappa", ctypes.c_void_p)]
 
 
 EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_build_nodes", "rw_hbs_save", "rw_hbs_load",
-           "rw_refine_factor_nodes",
+           "rw_refine_factor_nodes", "rw_holes_factor",
            "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
            "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
@@ -119,6 +124,7 @@ def load(build_if_missing=False):
     L.rw_refine_factor.argtypes = [vp, ctypes.c_int, ip, ip, vp, ctypes.POINTER(vp)]
     L.rw_hbs_build_nodes.argtypes = [ctypes.POINTER(NodesDesc), ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     L.rw_refine_factor_nodes.argtypes = [vp, ctypes.c_int, ip, ip, ctypes.POINTER(NodesDesc), vp, ctypes.POINTER(vp)]
+    L.rw_holes_factor.argtypes = [vp, ctypes.c_int, ctypes.POINTER(HoleDesc), vp, ctypes.POINTER(vp)]
     L.rw_hbs_save.argtypes = [vp, ctypes.c_char_p]
     L.rw_hbs_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
     L.rw_ref_stats_get.argtypes = [vp, ctypes.POINTER(RefStats)]
@@ -306,6 +312,12 @@ class Wall:
         for from_nodes, window order) instead of evaluating the wall's curve."""
         return Refinement(self, panels, levels, stream, added)
 
+    def add_holes(self, holes, stream=None):
+        """Factor the wall with holes added (App. B): holes is a list of dicts
+        with cx, cy, R and optionally a, k (shape r = R (1 + a cos(k t))) and
+        P (panels, default 10).  Returns a Refinement handle."""
+        return Refinement(self, None, None, stream, holes=holes)
+
     def close(self):
         if getattr(self, "h", None):
             load().rw_hbs_free(self.h)
@@ -321,11 +333,19 @@ class Wall:
 class Refinement:
     """Algorithm 1 pre-computation for one local refinement of a Wall."""
 
-    def __init__(self, wall, panels, levels, stream=None, added=None):
+    def __init__(self, wall, panels, levels, stream=None, added=None, holes=None):
         L = load()
+        h = ctypes.c_void_p()
+        if holes is not None:
+            arr = (HoleDesc * len(holes))(*[HoleDesc(float(d["cx"]), float(d["cy"]), float(d["R"]),
+                                                       float(d.get("a", 0.0)), int(d.get("k", 1)),
+                                                       int(d.get("P", 10))) for d in holes])
+            _check(L.rw_holes_factor(wall.h, len(holes), arr, _stream(stream), ctypes.byref(h)))
+            self.h = h
+            self.wall = wall
+            return
         p = (ctypes.c_int * len(panels))(*[int(v) for v in panels])
         lv = (ctypes.c_int * len(levels))(*[int(v) for v in levels])
-        h = ctypes.c_void_p()
         if added is None:
             _check(L.rw_refine_factor(wall.h, len(panels), p, lv, _stream(stream), ctypes.byref(h)))
         else:

@@ -60,6 +60,9 @@ def test_nodes_and_checkpoint_validation_without_gpu(tmp_path):
     assert L.rw_hbs_build_nodes(ctypes.byref(nd), None, None, ctypes.byref(h)) == -1
     assert b"multiple of 16" in L.rw_last_error()
     assert L.rw_refine_factor_nodes(None, 1, None, None, None, None, ctypes.byref(h)) == -1
+    hole = rwsolve.HoleDesc(0.3, 0.0, 0.1, 0.0, 1, 10)
+    assert L.rw_holes_factor(None, 1, ctypes.byref(hole), None, ctypes.byref(h)) == -1
+    assert L.rw_holes_factor(None, 0, None, None, ctypes.byref(h)) == -1
     assert L.rw_hbs_load(os.fsencode(str(tmp_path / "missing.rw")), None, ctypes.byref(h)) == -1
     assert b"cannot open" in L.rw_last_error()
     junk = tmp_path / "junk.rw"
