@@ -200,7 +200,7 @@ int rw_refine_factor_nodes(rw_hbs_t h, int n_cut, const int* panel_ids, const in
  * counter-clockwise, cut into n_panels panels equal in t with 16
  * Gauss-Legendre points each (the paper's holes are circles, a = 0, with 10
  * panels, Sec. 5.2).  Requirements: radius > 0, 0 <= a < 1, 0 <= k <= 64,
- * 3 <= n_panels <= 256; the holes lie inside the wall's fluid region, apart
+ * 5 <= n_panels <= 256; the holes lie inside the wall's fluid region, apart
  * from the wall and from one another (the library checks only that the
  * holes' enclosing circles do not overlap). */
 typedef struct {
@@ -216,8 +216,8 @@ typedef struct {
  * (x, y) per point; N_c = 0, N_p = hole points.  The system is
  *   [A_kk  A_kp] with A_kk = -1/2 I + D + N (the wall operator, N on the
  *   [A_pk  A_pp]      wall only), A_pp = 1/2 I + D + S on the holes
- * (log-singular single layer by product integration on each target's own
- * panel and its neighbours), A_kp = the holes' combined field w_j (D + S) on
+ * (log-singular single layer by product integration of the density's
+ * interpolant on each target's own panel and two panels on either side), A_kp = the holes' combined field w_j (D + S) on
  * the wall, A_pk = the wall's double layer w_j D on the holes.  The velocity
  * (rw_solve targets) is the wall's double layer plus the holes' combined
  * field; rw_pressure likewise.  The returned handle works with every rw_ref_t

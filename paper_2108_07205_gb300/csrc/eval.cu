@@ -7,8 +7,9 @@
 namespace rw {
 
 // ------------------------------------------------------------ quadrature
-void gauss_legendre16(double* x, double* w) {
-  const int n = 16;
+void gauss_legendre16(double* x, double* w) { gauss_legendre_n(16, x, w); }
+
+void gauss_legendre_n(int n, double* x, double* w) {
   for (int i = 0; i < n; ++i) {
     // Chebyshev-like initial guess, Newton on P_n via the three-term recurrence
     double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
@@ -39,6 +40,10 @@ void gauss_legendre16(double* x, double* w) {
 namespace {
 
 __constant__ double c_glx[16], c_glw[16];
+// auxiliary 32-point rule of the hole matrix and the values l_j(u_f) of the
+// 16-point Lagrange basis at its nodes (c_lag[f][j])
+constexpr int kAux = 32;
+__constant__ double c_ux[kAux], c_uw[kAux], c_lag[kAux][16];
 
 struct Pt { double x, y, dx, dy, ddx, ddy; };
 
@@ -455,7 +460,7 @@ __global__ void k_apply_cross(NodesView T, NodesView Sv, const double* x, int ld
   yr[2 * i + 1] = (acc ? yr[2 * i + 1] : 0.0) + uy;
 }
 
-// Moments M_n(t) = int_{-1}^{1} P_n(s) log|t - s| ds, n = 0..15, of the
+// Moments M_n(t) = int_{-1}^{1} P_n(s) log|t - s| ds, n = 0..NM-1, of the
 // Legendre polynomials against the logarithm.  Integration by parts with
 // P_n = (P_{n+1}' - P_{n-1}') / (2n + 1) gives M_n = 2 (Q_{n+1}(t) -
 // Q_{n-1}(t)) / (2n + 1), where Q_m(t) = (1/2) int P_m(s) / (t - s) ds (a
@@ -465,117 +470,154 @@ __global__ void k_apply_cross(NodesView T, NodesView Sv, const double* x, int ld
 // minimal solution, it runs backward from a start index past which the
 // neglected dominant part is below rounding (Miller's algorithm) and is
 // normalised by Q_0.  M_0 is the elementary integral.
-__device__ void log_moments16(double t, double* M) {
-  double Q[17];
+template <int NM>
+__device__ void log_moments(double t, double* M) {
+  double Q[NM + 1];
   const double at = fabs(t);
   if (at < 1.0) {
     Q[0] = 0.5 * log((1.0 + t) / (1.0 - t));
     Q[1] = t * Q[0] - 1.0;
-    for (int n = 1; n < 16; ++n) Q[n + 1] = ((2.0 * n + 1.0) * t * Q[n] - n * Q[n - 1]) / (n + 1.0);
+    for (int n = 1; n < NM; ++n) Q[n + 1] = ((2.0 * n + 1.0) * t * Q[n] - n * Q[n - 1]) / (n + 1.0);
   } else {
     const double rho = at + sqrt((at - 1.0) * (at + 1.0));
-    int n0 = 17 + int(ceil(40.0 / log(rho)));
-    n0 = min(n0, 20000);
+    const int n0 = min(NM + 1 + int(ceil(40.0 / log(rho))), 20000);
     double qn1 = 0.0, qn = 1.0;  // Q_{n+1}, Q_n up to a common factor
     for (int n = n0; n >= 1; --n) {
       const double qm = ((2.0 * n + 1.0) * t * qn - (n + 1.0) * qn1) / n;
       qn1 = qn;
       qn = qm;
-      if (n - 1 <= 16) Q[n - 1] = qn;
+      if (n - 1 <= NM) Q[n - 1] = qn;
       if (fabs(qn) > 1e200) {
         qn *= 1e-200;
         qn1 *= 1e-200;
-        for (int m = n - 1; m <= 16; ++m)
-          if (m >= 0) Q[m] *= 1e-200;
+        for (int m = max(n - 1, 0); m <= NM; ++m) Q[m] *= 1e-200;
       }
     }
     const double sc = 0.5 * log((t + 1.0) / (t - 1.0)) / Q[0];
-    for (int m = 0; m <= 16; ++m) Q[m] *= sc;
+    for (int m = 0; m <= NM; ++m) Q[m] *= sc;
   }
   M[0] = (t + 1.0) * log(fabs(t + 1.0)) - (t - 1.0) * log(fabs(t - 1.0)) - 2.0;
-  for (int n = 1; n < 16; ++n) M[n] = 2.0 * (Q[n + 1] - Q[n - 1]) / (2.0 * n + 1.0);
+  for (int n = 1; n < NM; ++n) M[n] = 2.0 * (Q[n + 1] - Q[n - 1]) / (2.0 * n + 1.0);
 }
 
 // Dense A_pp = 1/2 I + D + S on the holes (App. B; Eq. exterior_BIE), column
-// major, ld = 2 N_p.  One CTA per target point i.  The double layer and the
-// r r^T / |r|^2 part of the Stokeslet are smooth along a hole: plain panel
-// rule (curvature and tangent limits on the diagonal).  The logarithm is
-// singular: on the target's own panel and its two neighbours (panels equal
-// in t, at least three per hole) its weights come from product integration
-// of the panel's degree-15 interpolant (Legendre form),
-//   int log|x_i - y(s)| f(s) ds ~ sum_j f_j [h |x'_j| lam_j(t) + w_j phi_j],
-//   lam_j(t) = omega_j sum_n (2n+1)/2 P_n(s_j) M_n(t),
-// with t the target's coordinate in the source panel's [-1, 1], h the
-// panel's half-width in t and phi_j = log|x_i - y_j| - log|t - s_j| (the
-// smooth remainder; log(h |x'_i|) at the target itself).
+// major, ld = 2 N_p.  One CTA per target point i.  The double layer is
+// smooth along a hole: plain panel rule with the curvature limit on the
+// diagonal.  The Stokeslet is integrated against the degree-15 interpolant
+// of the density on the target's own panel and two panels on either side
+// (panels equal in t, at least five per hole), with the geometry exact: a 32-point
+// auxiliary Gauss rule (u_f, nu_f) on the source panel, the curve evaluated
+// at its nodes, the interpolant through l_j(u_f), and for the logarithm
+// Legendre product integration (generalised Gaussian quadrature corrections
+// in the sense of Sec. 5: exact for the density's interpolant):
+//   int log|x_i - y(s)| l_j(s) |y'(s)| ds
+//     ~ sum_f [Lam_f(t) + nu_f phi(u_f)] |y'(u_f)| l_j(u_f),
+//   Lam_f(t) = nu_f sum_{n<32} (2n+1)/2 P_n(u_f) M_n(t),
+//   phi(s) = log|x_i - y(s)| - log|t - s|  (smooth),
+// with t the target's coordinate in the source panel's [-1, 1] (the panel's
+// half-width h in t scales every weight); r r^T / |r|^2 takes the auxiliary
+// rule alone.  Every other pair uses the plain panel rule.
 constexpr int kMaxHoles = 8;
+constexpr int kNearHole = 2;  // corrected panels: cyclic distance <= 2
 struct HoleSet {
   int nh;
   int off[kMaxHoles + 1];
   int P[kMaxHoles];
+  double geo[kMaxHoles][5];  // a, k, R, cx, cy
 };
 
 __global__ void __launch_bounds__(128) k_hole_matrix(NodesView hv, HoleSet hs, double* A, int ld) {
+  constexpr int ND = 2 * kNearHole + 1;  // corrected source panels q_i - 2 .. q_i + 2
   const int i = blockIdx.x;
   int h = 0;
   while (h + 1 < hs.nh && i >= hs.off[h + 1]) ++h;
   const int P = hs.P[h], li = i - hs.off[h], qi = li >> 4, si = li & 15;
   const double hw = kPi / P;  // half-width of a panel in t
-  __shared__ double Mn[3][16], lam[3][16];
-  if (threadIdx.x < 3) {
-    const int d = int(threadIdx.x) - 1;   // source panel q_i + d
-    log_moments16(c_glx[si] - 2.0 * d, Mn[threadIdx.x]);
+  __shared__ double Mn[ND][kAux], lam[ND][kAux], ux[ND][kAux], uy[ND][kAux], usp[ND][kAux];
+  __shared__ double wl[ND][16], tab[ND][3][16];  // log weights; r r^T / r^2 (xx, xy, yy)
+  const double xi = hv.x[i], yi = hv.y[i];
+  if (threadIdx.x < ND) log_moments<kAux>(c_glx[si] - 2.0 * (int(threadIdx.x) - kNearHole), Mn[threadIdx.x]);
+  for (int e = threadIdx.x; e < ND * kAux; e += blockDim.x) {
+    const int pd = e / kAux, f = e % kAux;
+    const int q = ((qi + pd - kNearHole) % P + P) % P;
+    Curve c;
+    c.kind = kCurveHole;
+    for (int m = 0; m < 5; ++m) c.p[m] = hs.geo[h][m];
+    const Pt g = curve_eval(c, (2.0 * q + 1.0 + c_ux[f]) * hw);
+    ux[pd][f] = g.x;
+    uy[pd][f] = g.y;
+    usp[pd][f] = sqrt(g.dx * g.dx + g.dy * g.dy);
   }
   __syncthreads();
-  if (threadIdx.x < 48) {
-    const int pd = threadIdx.x >> 4, j = threadIdx.x & 15;
-    const double sj = c_glx[j];
-    double p0 = 1.0, p1 = sj, acc = 0.5 * Mn[pd][0] + 1.5 * sj * Mn[pd][1];
-    for (int n = 1; n < 15; ++n) {
-      const double p2 = ((2.0 * n + 1.0) * sj * p1 - n * p0) / (n + 1.0);
+  for (int e = threadIdx.x; e < ND * kAux; e += blockDim.x) {
+    const int pd = e / kAux, f = e % kAux;
+    const double u = c_ux[f];
+    double p0 = 1.0, p1 = u, acc = 0.5 * Mn[pd][0] + 1.5 * u * Mn[pd][1];
+    for (int n = 1; n < kAux - 1; ++n) {
+      const double p2 = ((2.0 * n + 1.0) * u * p1 - n * p0) / (n + 1.0);
       p0 = p1;
       p1 = p2;
       acc += (n + 1.5) * p2 * Mn[pd][n + 1];
     }
-    lam[pd][j] = c_glw[j] * acc;
+    lam[pd][f] = c_uw[f] * acc;
   }
   __syncthreads();
-  const double xi = hv.x[i], yi = hv.y[i];
+  for (int e = threadIdx.x; e < ND * 16; e += blockDim.x) {
+    const int pd = e >> 4, j = e & 15;
+    const double t = c_glx[si] - 2.0 * (pd - kNearHole);
+    double sl = 0.0, sxx = 0.0, sxy = 0.0, syy = 0.0;
+    for (int f = 0; f < kAux; ++f) {
+      const double rx = xi - ux[pd][f], ry = yi - uy[pd][f], r2 = rx * rx + ry * ry;
+      const double g = usp[pd][f] * c_lag[f][j];
+      const double phi = 0.5 * log(r2) - log(fabs(t - c_ux[f]));
+      sl += (lam[pd][f] + c_uw[f] * phi) * g;
+      const double wg = c_uw[f] * g / r2;
+      sxx += wg * rx * rx;
+      sxy += wg * rx * ry;
+      syy += wg * ry * ry;
+    }
+    wl[pd][j] = hw * sl;
+    tab[pd][0][j] = hw * sxx;
+    tab[pd][1][j] = hw * sxy;
+    tab[pd][2][j] = hw * syy;
+  }
+  __syncthreads();
   const double c4 = 0.25 / kPi;
   for (int j = threadIdx.x; j < hv.n; j += blockDim.x) {
     const double wj = hv.w[j];
-    double b[2][2];
-    double wlog;  // weight of log|r| in the single layer
     const int lj = j - hs.off[h];
-    int d = 2;
+    int d = kNearHole + 1;  // not corrected
     if (lj >= 0 && lj < 16 * P) {
       d = (lj >> 4) - qi;
       if (d > P / 2) d -= P;
       if (d < -P / 2) d += P;
     }
-    const int sj = lj & 15;
+    double b[2][2];
+    // double layer (plain rule; curvature limit at the target itself)
     if (j == i) {
-      const double tx = -hv.ny[i], ty = hv.nx[i], t[2] = {tx, ty};
-      const double sp = wj / (c_glw[si] * hw);
-      wlog = hw * sp * lam[1][si] + wj * log(hw * sp);
+      const double t[2] = {-hv.ny[i], hv.nx[i]};
       const double kap = -hv.kappa[i] * wj * (0.5 / kPi);
       for (int a = 0; a < 2; ++a)
-        for (int c = 0; c < 2; ++c)
-          b[a][c] = kap * t[a] * t[c] + c4 * wj * t[a] * t[c] + (a == c ? 0.5 - c4 * wlog : 0.0);
+        for (int c = 0; c < 2; ++c) b[a][c] = kap * t[a] * t[c] + (a == c ? 0.5 : 0.0);
+    } else {
+      const double rx = xi - hv.x[j], ry = yi - hv.y[j], inv = 1.0 / (rx * rx + ry * ry);
+      const double r[2] = {rx, ry};
+      const double fac = wj * (rx * hv.nx[j] + ry * hv.ny[j]) * inv * inv * (1.0 / kPi);
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) b[a][c] = fac * r[a] * r[c];
+    }
+    // single layer
+    if (d >= -kNearHole && d <= kNearHole) {
+      const int pd = d + kNearHole, sj = lj & 15;
+      const double txy[2][2] = {{tab[pd][0][sj], tab[pd][1][sj]}, {tab[pd][1][sj], tab[pd][2][sj]}};
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) b[a][c] += c4 * (txy[a][c] - (a == c ? wl[pd][sj] : 0.0));
     } else {
       const double rx = xi - hv.x[j], ry = yi - hv.y[j], r2 = rx * rx + ry * ry, inv = 1.0 / r2;
       const double r[2] = {rx, ry};
-      const double fac = wj * (rx * hv.nx[j] + ry * hv.ny[j]) * inv * inv * (1.0 / kPi);
-      if (d >= -1 && d <= 1) {
-        const double tloc = c_glx[si] - 2.0 * d;
-        const double sp = wj / (c_glw[sj] * hw);
-        wlog = hw * sp * lam[d + 1][sj] + wj * (0.5 * log(r2) - log(fabs(tloc - c_glx[sj])));
-      } else {
-        wlog = wj * 0.5 * log(r2);
-      }
+      const double lg = 0.5 * log(r2);
       for (int a = 0; a < 2; ++a)
-        for (int c = 0; c < 2; ++c)
-          b[a][c] = fac * r[a] * r[c] + c4 * wj * r[a] * r[c] * inv - (a == c ? c4 * wlog : 0.0);
+        for (int c = 0; c < 2; ++c) b[a][c] += c4 * wj * (r[a] * r[c] * inv - (a == c ? lg : 0.0));
     }
     for (int a = 0; a < 2; ++a)
       for (int c = 0; c < 2; ++c) A[(2 * size_t(i) + a) + (2 * size_t(j) + c) * ld] = b[a][c];
@@ -592,6 +634,24 @@ void ensure_gl() {
   gauss_legendre16(x, w);
   RW_CUDA(cudaMemcpyToSymbol(c_glx, x, sizeof(x)));
   RW_CUDA(cudaMemcpyToSymbol(c_glw, w, sizeof(w)));
+  double ux[kAux], uw[kAux], lag[kAux][16];
+  gauss_legendre_n(kAux, ux, uw);
+  // barycentric weights of the 16 nodes, then the Lagrange basis at u_f
+  double bw[16];
+  for (int j = 0; j < 16; ++j) {
+    double pr = 1.0;
+    for (int m = 0; m < 16; ++m)
+      if (m != j) pr *= x[j] - x[m];
+    bw[j] = 1.0 / pr;
+  }
+  for (int f = 0; f < kAux; ++f) {
+    double den = 0.0;
+    for (int j = 0; j < 16; ++j) den += bw[j] / (ux[f] - x[j]);
+    for (int j = 0; j < 16; ++j) lag[f][j] = bw[j] / (ux[f] - x[j]) / den;
+  }
+  RW_CUDA(cudaMemcpyToSymbol(c_ux, ux, sizeof(ux)));
+  RW_CUDA(cudaMemcpyToSymbol(c_uw, uw, sizeof(uw)));
+  RW_CUDA(cudaMemcpyToSymbol(c_lag, lag, sizeof(lag)));
   g_gl_ready = true;
 }
 
@@ -695,17 +755,20 @@ void apply_cross(const NodesView& T, const NodesView& Sv, const double* x, int l
   RW_CHECK_LAUNCH();
 }
 
-void eval_hole_matrix(const NodesView& holes, const std::vector<int>& panels, double* A, cudaStream_t s) {
+void eval_hole_matrix(const NodesView& holes, const std::vector<int>& panels, const std::vector<double>& geo,
+                      double* A, cudaStream_t s) {
   require(!panels.empty() && int(panels.size()) <= kMaxHoles, "hole matrix: 1 to 8 holes");
+  require(geo.size() == 5 * panels.size(), "hole matrix: five shape parameters per hole");
   require(holes.kind == 1, "hole matrix: node set is not a hole set");
   ensure_gl();
   HoleSet hs{};
   hs.nh = int(panels.size());
   int off = 0;
   for (int h = 0; h < hs.nh; ++h) {
-    require(panels[h] >= 3, "hole matrix: at least three panels per hole");
+    require(panels[h] >= 2 * kNearHole + 1, "hole matrix: at least five panels per hole");
     hs.off[h] = off;
     hs.P[h] = panels[h];
+    for (int e = 0; e < 5; ++e) hs.geo[h][e] = geo[5 * h + e];
     off += 16 * panels[h];
   }
   hs.off[hs.nh] = off;

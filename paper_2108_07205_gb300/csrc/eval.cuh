@@ -16,6 +16,7 @@ struct Curve {
 // Gauss-Legendre nodes/weights of the 16-point rule on [-1, 1] (host table,
 // Newton iteration on the Legendre recurrence).
 void gauss_legendre16(double* x, double* w);
+void gauss_legendre_n(int n, double* x, double* w);
 
 // Nodes on t-intervals [ta[i], tb[i]] (16 Gauss-Legendre points each) into
 // `out` (6 x 16 n_int, see Nodes).  ta/tb are device arrays.
@@ -111,8 +112,10 @@ void apply_cross(const NodesView& T, const NodesView& S, const double* x, int ld
                  bool accumulate, cudaStream_t s);
 
 // Dense A_pp = 1/2 I + D + S on a hole set whose hole h has panels[h] equal
-// panels in t (16 points each, in order): A is 2N x 2N column major.
-void eval_hole_matrix(const NodesView& holes, const std::vector<int>& panels, double* A, cudaStream_t s);
+// panels in t (16 points each, in order) and shape geo[5h .. 5h+4] = (a, k,
+// R, cx, cy) (kCurveHole): A is 2N x 2N column major.
+void eval_hole_matrix(const NodesView& holes, const std::vector<int>& panels, const std::vector<double>& geo,
+                      double* A, cudaStream_t s);
 
 // g(x_i) = sum_s S(x_i, y_s) f_s (Eq. stokeslet, mu = 1) at every node.
 // src: 2 x ns; f: 2 x ns x nrhs; g: 2N x nrhs.

@@ -38,7 +38,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
     require(h.R > 0.0, "holes: radius must be positive");
     require(h.a >= 0.0 && h.a < 1.0, "holes: shape amplitude a must be in [0, 1)");
     require(h.k >= 0 && h.k <= 64, "holes: shape frequency k must be in 0..64");
-    require(h.P >= 3 && h.P <= 256, "holes: 3 to 256 panels per hole");
+    require(h.P >= 5 && h.P <= 256, "holes: 5 to 256 panels per hole");
     np += 16 * h.P;
   }
   require(np <= 1024, "holes: at most 1024 hole points (A_pp is inverted densely)");
@@ -159,8 +159,12 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
     try {
       DBuf<double> A(size_t(4) * Np * Np);
       std::vector<int> pan(nh);
-      for (int h = 0; h < nh; ++h) pan[h] = hs[h].P;
-      eval_hole_matrix(VP, pan, A.p, s1);
+      std::vector<double> geo;
+      for (int h = 0; h < nh; ++h) {
+        pan[h] = hs[h].P;
+        geo.insert(geo.end(), {hs[h].a, double(hs[h].k), hs[h].R, hs[h].cx, hs[h].cy});
+      }
+      eval_hole_matrix(VP, pan, geo, A.p, s1);
       hpp.build_dense(std::move(A), Np, s1);
       hpp.make_fp32(s1);
       pp_dense = true;

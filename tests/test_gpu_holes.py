@@ -1,9 +1,11 @@
 """Oracle parity of the wall with added holes (App. B) through the C ABI.
 
 * the exact operator A_nn (rw_apply_refined) against the oracle's dense
-  system, entry by entry through random vectors: the holes' combined field
-  with its singular rule (product integration here, graded Gauss there), the
-  cross blocks and the wall block, <= 1e-13 relative;
+  system, entry by entry through random vectors, with the paper's circles
+  and with star-shaped holes: the holes' combined field with its singular
+  rule (Legendre product integration on a 32-point auxiliary rule here,
+  graded Gauss there, both exact for the density's interpolant), the cross
+  blocks and the wall block, <= 1e-13 relative;
 * densities from the three solve modes against the oracle's dense LU solve
   on the star wall with circular and star-shaped holes and on the channel:
   RW_MODE_DIRECT_REFINED and FGMRES at <= 1e-10 relative (the FP64 parity
@@ -60,8 +62,9 @@ def _device_data(r, src, nrhs):
     return g
 
 
-def test_operator_matches_oracle(lib):
-    w, wall_o, hl, src = _case("star", 24, 6, hole_a=0.2, hole_k=3)
+@pytest.mark.parametrize("PH,a,k", [(10, 0.0, 1), (12, 0.2, 3)])
+def test_operator_matches_oracle(lib, PH, a, k):
+    w, wall_o, hl, src = _case("star", 24, PH, hole_a=a, hole_k=k)
     r = w.add_holes(hl)
     hn = H.hole_nodes(hl)
     A = H.system(wall_o, hn, hl)
@@ -173,7 +176,7 @@ def test_batch_mixes_holes_and_refinements(lib):
 
 @pytest.mark.parametrize("bad", [
     [dict(cx=0.3, cy=0.0, R=0.2, P=6), dict(cx=0.45, cy=0.0, R=0.2, P=6)],   # overlapping
-    [dict(cx=0.3, cy=0.0, R=0.1, P=2)],                                       # too few panels
+    [dict(cx=0.3, cy=0.0, R=0.1, P=4)],                                       # too few panels
     [dict(cx=0.3, cy=0.0, R=-0.1, P=6)],                                      # negative radius
     [dict(cx=0.3, cy=0.0, R=0.1, a=1.2, k=3, P=6)],                           # self-intersecting shape
     [dict(cx=0.3, cy=0.0, R=0.1, P=70)],                                      # more than 1024 points
