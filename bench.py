@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=48, help="serving workload: number of requests per phase")
     ap.add_argument("--walls", type=int, default=32, help="batched workload: number of walls")
-    ap.add_argument("--workload", default="channel1024", choices=["channel1024", "mixed2048", "serving", "batched"],
+    ap.add_argument("--workload", default="channel1024",
+                    choices=["channel1024", "mixed2048", "serving", "batched", "holes"],
                     help="channel1024: 1 RHS per step (default); mixed2048: 2048-panel channel, 64 RHS per "
                          "step from Stokeslet pairs")
     ap.add_argument("--refine-probe", type=int, default=0,
@@ -484,6 +485,96 @@ def run_batched(args):
     b.close()
 
 
+def run_holes(args):
+    """Channel with three added holes (App. B; Sec. 5.2, Tab. holes): the
+    channel at the paper's three sizes (2N = 30720, 61440, 122880: 960, 1920
+    and 3840 panels) with three circular holes of 10 panels (960 hole
+    unknowns), data from 5 exterior Stokeslets and 2 + 2 + 1 inside the holes.
+    Per size: the wall's HBS build (static), the holes factorisation
+    (T_ELS,comp + T_ELS,inv of the paper; median of --steps runs after the
+    warm-up), and the direct and refined solves of one right-hand side (CUDA
+    events, L2 flushed before each), with the velocity error at fluid targets
+    against the closed-form Stokeslet field.  One JSON line per size."""
+    import torch
+    from paper_2108_07205_gb300 import rwsolve, inputs
+    rwsolve.load(build_if_missing=True)
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for P in (960, 1920, 3840):
+        t0 = time.time()
+        w = rwsolve.Wall("channel", P)
+        build_s = time.time() - t0
+        hl = inputs.holes_channel(3, n_panels=10)
+        sx, sy, f = inputs.stokeslets_channel(0, nrhs=1)
+        hx, hy, hf = inputs.stokeslets_in_holes(1, hl, [2, 2, 1], nrhs=1)
+        src = np.ascontiguousarray(np.stack([np.concatenate([sx, hx]), np.concatenate([sy, hy])], 1))
+        fd = np.ascontiguousarray(np.transpose(np.concatenate([f, hf]), (2, 0, 1)))
+        for _ in range(max(1, args.warmup)):
+            w.add_holes(hl).close()
+        torch.cuda.synchronize()
+        fac = []
+        for _ in range(max(1, args.steps)):
+            t0 = time.time()
+            r = w.add_holes(hl)
+            torch.cuda.synchronize()
+            fac.append(time.time() - t0)
+            if _ < args.steps - 1:
+                r.close()
+        st = r.stats()
+        n = 2 * st["n_n"]
+        g = torch.empty(n, dtype=torch.float64, device=dev)
+        r.stokeslet_data(torch.from_numpy(src).to(dev), torch.from_numpy(fd).to(dev), g)
+        tau = torch.empty_like(g)
+        out = {}
+        for name, mode in (("direct", rwsolve.MODE_DIRECT), ("refined", rwsolve.MODE_DIRECT_REFINED)):
+            for _ in range(3):
+                r.solve(g, tau, mode=mode, stream=stream)
+            ts = []
+            for _ in range(max(3, args.steps)):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.solve(g, tau, mode=mode, stream=stream)
+                e1.record(stream)
+                ts.append((e0, e1))
+            torch.cuda.synchronize()
+            out[name] = float(np.median([a.elapsed_time(b) for a, b in ts]))
+        tx, ty = inputs.targets_fluid(4, hl, "channel", 32)
+        tg = torch.from_numpy(np.ascontiguousarray(np.stack([tx, ty], 1))).to(dev)
+        u = torch.empty(2 * tx.size, dtype=torch.float64, device=dev)
+        r.solve(g, tau, targets=tg, u=u, mode=rwsolve.MODE_DIRECT_REFINED, stream=stream)
+        ue = _stokeslet_field(tx, ty, src, fd[0])
+        err = float(np.abs(u.cpu().numpy().reshape(-1, 2) - ue).max() / np.abs(ue).max())
+        line = {"metric": "holed-wall solves/s (direct, 1 RHS)", "value": 1e3 / out["direct"], "unit": "solves/s",
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["direct"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": f"channel {P} panels (2N = {32 * P}) + 3 circular holes x 10 panels "
+                                       "(960 hole unknowns), App. B", "l2": "flushed before each solve"},
+                "factor_ms": 1e3 * float(np.median(fac)), "hbs_build_s": build_s,
+                "refined_solve_ms": out["refined"], "k_woodbury": st["k"], "k_far": st["k_far"],
+                "k_near": st["k_near"], "k_pk": st["k_pk"], "ref_bytes": st["bytes"],
+                "velocity_rel_error_closed_form": err}
+        print(json.dumps(line))
+        r.close()
+        w.close()
+
+
+def _stokeslet_field(tx, ty, src, f):
+    """Closed-form velocity of point forces f (ns x 2) at src (ns x 2), mu = 1
+    (Eq. stokeslet), for the error column of the holes workload."""
+    rx = tx[:, None] - src[None, :, 0]
+    ry = ty[:, None] - src[None, :, 1]
+    r2 = rx * rx + ry * ry
+    rf = (rx * f[None, :, 0] + ry * f[None, :, 1]) / r2
+    lg = -0.5 * np.log(r2)
+    ux = ((lg * f[None, :, 0] + rx * rf).sum(1)) / (4.0 * np.pi)
+    uy = ((lg * f[None, :, 1] + ry * rf).sum(1)) / (4.0 * np.pi)
+    return np.stack([ux, uy], 1)
+
+
 def main():
     global P_PANELS, NRHS
     args = parse()
@@ -497,6 +588,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "holes":
+        run_holes(args)
         return
     rank, world, local = dist_env()
     if world > 1:
