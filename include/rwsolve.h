@@ -92,7 +92,9 @@ typedef struct {
   int n_k, n_c, n_p;   /* points kept, cut and added (Sec. 3.1)              */
   int n_n, n_ext;      /* N_n = N_k + N_p, N_ext = N_k + N_c + N_p           */
   int k_far, k_near, k_pk;  /* ranks of the far, near and A_pk row IDs       */
-  int k;               /* Woodbury size k = k_far + k_near + k_pk            */
+  int k;               /* Woodbury size k <= k_far + k_near + k_pk after the
+                          recompression of Sec. 3.4 (row IDs of the skeleton
+                          blocks of R)                                       */
   int pp_dense;        /* 1 if A_pp was inverted densely                     */
   int pp_levels;       /* tree depth of the refined-arc HBS (0 if dense)     */
   long long bytes;     /* device bytes held by the handle                    */

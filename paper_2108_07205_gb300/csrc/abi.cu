@@ -320,7 +320,7 @@ int rw_ref_stats_get(rw_ref_t r, rw_ref_stats* st) {
   if (!r || !st) return fail(RW_ERR_INVALID, "rw_ref_stats_get: null argument");
   const rw::Refinement& f = r->ref;
   st->n_k = f.Nk; st->n_c = f.Nc; st->n_p = f.Np; st->n_n = f.Nn; st->n_ext = f.Nk + f.Nc + f.Np;
-  st->k_far = f.kf; st->k_near = f.kn; st->k_pk = f.kpk; st->k = f.k;
+  st->k_far = f.kf; st->k_near = f.kn; st->k_pk = f.kpk_id; st->k = f.k;
   st->pp_dense = f.pp_dense ? 1 : 0;
   st->pp_levels = f.pp_dense ? 0 : f.hpp.L;
   st->bytes = (long long)f.bytes;

@@ -10,12 +10,14 @@
 //  * A_pk, hole by hole: a hierarchical ID of the hole's rows of
 //    [A_{p,div} | A_pk^near] with that hole's P^div circle and the wall
 //    points inside it; L_pk = blkdiag over the holes.
-// so L = blkdiag(L_k, L_pk), R = [[0, A(J_k, I_p)], [A(J_pk, I_k), 0]].
+// so L = blkdiag(L_k, L_pk), R = [[0, A(J_k, I_p)], [A(J_pk, I_k), 0]],
+// then recompressed by row IDs of the two skeleton blocks (Sec. 3.4).
 // A_pp = 1/2 I + D + S is assembled densely with the singular rule of the
 // hole matrix kernel and inverted (single-leaf HBS).
 #include "refine.cuh"
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <exception>
 #include <thread>
 
@@ -217,6 +219,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
   for (int h = 0; h < nh; ++h) kpk += tp[h].k;
   kk = kf + kn;
   k = kk + kpk;
+  kpk_id = kpk;
 
   // L_o (2No x kk) and L_p = blkdiag of the holes' interpolation matrices
   Lo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
@@ -240,11 +243,27 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
     batched_copy(cp, s);
     RW_CUDA(cudaStreamSynchronize(s));
   }
+  for (int i : tf.skel) Jk.push_back(far_d[i]);
+  for (int i : tn.skel) Jk.push_back(near_d[i]);
+  // a4, recompression (Sec. 3.4): row IDs of the skeleton blocks
+  // R_k = A(J_k, I_p) and R_pk = A(J_pk, I_k) (see recompress_rows)
+  const double rtol = 0.1 * o.id_tol;
+  if (recompress_enabled()) {
+    IdMatProb ck{};
+    ck.n2 = 2 * Np; ck.e2 = dall_p.p;
+    recompress_rows(VW, Jk, ck, VW, true, VP, false, Lo, 2 * No, kk, rtol, o.seed + 404, s);
+    std::vector<int> od(2 * No);
+    for (int d = 0; d < 2 * No; ++d) od[d] = d;
+    auto dall_o = to_device_tmp(od, s);
+    IdMatProb cp{};
+    cp.n1 = 2 * No; cp.e1 = dall_o.p;
+    recompress_rows(VP, Jpk, cp, VW, false, VW, false, Lp, 2 * Np, kpk, rtol, o.seed + 505, s);
+    k = kk + kpk;
+    tr.mark("recompression");
+  }
   // a5 (wall part): X_o = A_kk^{-1} L_o
   Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
   if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
-  for (int i : tf.skel) Jk.push_back(far_d[i]);
-  for (int i : tn.skel) Jk.push_back(near_d[i]);
   auto dJk = to_device_tmp(Jk, s), dJpk = to_device_tmp(Jpk, s);
   Rkp.alloc(std::max<size_t>(size_t(kk) * 2 * Np, 1));
   Rpk.alloc(std::max<size_t>(size_t(kpk) * 2 * No, 1));

@@ -12,10 +12,14 @@
 //  * near rows of I_k: one direct ID of [A_kc^near | A_kp^near];
 //  * A_pk: one hierarchical ID of the rows of [A_{p,div} | A_pk^near];
 //  so L = blkdiag(L_k, L_pk) with L_k = [P_far ; P_near] on the k rows and
-//  R = [[0, -A(J_k, I_c), A(J_k, I_p)], [A(J_pk, I_k), 0, 0]].
-//  This is the row ID of the blockwise factor L_1 (whose kc and kp column
-//  blocks share their far and near interpolation matrices), i.e. the
-//  recompressed factorisation of Sec. 3.4 reached without duplicated columns.
+//  R = [[0, -A(J_k, I_c), A(J_k, I_p)], [A(J_pk, I_k), 0, 0]]: the row ID of
+//  the blockwise factor L_1, whose kc and kp column blocks share their far
+//  and near interpolation matrices (no duplicated columns).
+//  Recompression (Sec. 3.4): the proxies stand for every possible source
+//  near Gamma_r, so these ranks exceed those of the blocks themselves; row IDs
+//  of the skeleton blocks R_k = [A(J_k, I_c), A(J_k, I_p)] and R_pk =
+//  A(J_pk, I_k) (sketched when wide) fold into L and thin J (recompress_rows):
+//  226 -> 81 on the 1024-panel channel (the paper's k_opt ~ 79, Sec. 3.4).
 #include "refine.cuh"
 #include <algorithm>
 #include <cmath>
@@ -54,6 +58,35 @@ __global__ void k_zero_cols(double* A, int ld, int nrows, const int* cols, int n
 }
 
 }  // namespace
+
+bool recompress_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("RW_RECOMPRESS");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+void recompress_rows(const NodesView& S, std::vector<int>& J, const IdMatProb& cols, const NodesView& E1, bool e1s,
+                     const NodesView& E2, bool e2s, DBuf<double>& L, int m, int& k, double tol,
+                     unsigned long long seed, cudaStream_t s) {
+  if (k == 0 || J.empty()) return;
+  IdMatProb cs = cols;
+  cs.M = 0;
+  cs.normal = 0;
+  cs.ncirc = 0;
+  cs.circ = nullptr;
+  const Opts o;
+  TreeId t = tree_row_id(S, J, cs, E1, e1s, E2, e2s, tol, o.sketch_cols, o.sketch_width, seed, 128, s);
+  if (t.k >= k) return;
+  DBuf<double> L2(std::max<size_t>(size_t(m) * t.k, 1));
+  if (t.k) batched_gemm({GemmProb{L.p, t.P.p, L2.p, m, t.k, k, m, k, m, 0, 0, 1.0, 0.0}}, s);
+  L = std::move(L2);
+  std::vector<int> J2;
+  for (int i : t.skel) J2.push_back(J[i]);
+  J = J2;
+  k = t.k;
+}
 
 SideStreams::~SideStreams() {
   // every buffer of the refinement has been released (stream ordered) by now
@@ -267,6 +300,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   for (auto& e : {e0, e2}) if (e) std::rethrow_exception(e);
   tr.mark("IDs (concurrent with A_pp)");
   kf = tf.k; kn = tn.k; kpk = tp.k; kk = kf + kn; k = kk + kpk;
+  kpk_id = kpk;
 
   // L_o (2No x kk) and L_p (2Np x kpk)
   Lo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
@@ -278,14 +312,29 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     Lp = std::move(tp.P);
     RW_CUDA(cudaStreamSynchronize(s));
   }
-  // a5 (o part): X_o = A_oo^{-1} L_o
-  Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
-  if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
   // skeleton DOFs
   std::vector<int> Jk, Jpk;
   for (int i : tf.skel) Jk.push_back(far_d[i]);
   for (int i : tn.skel) Jk.push_back(near_d[i]);
   for (int i : tp.skel) Jpk.push_back(i);
+  if (recompress_enabled()) {
+    // row IDs of R_k = [A(J_k, I_c), A(J_k, I_p)] and R_pk = A(J_pk, I_k)
+    const double rtol = 0.1 * o.id_tol;
+    IdMatProb ck{};
+    ck.n1 = 2 * Nc; ck.e1 = dc.p; ck.n2 = 2 * Np; ck.e2 = dall_p.p;
+    recompress_rows(VW, Jk, ck, VW, true, VP, false, Lo, 2 * No, kk, rtol, o.seed + 404, s);
+    std::vector<int> kd;
+    for (int i : Ik) { kd.push_back(2 * i); kd.push_back(2 * i + 1); }
+    auto dkd = to_device_tmp(kd, s);
+    IdMatProb cp{};
+    cp.n1 = int(kd.size()); cp.e1 = dkd.p;
+    recompress_rows(VP, Jpk, cp, VW, false, VW, false, Lp, 2 * Np, kpk, rtol, o.seed + 505, s);
+    k = kk + kpk;
+    tr.mark("recompression");
+  }
+  // a5 (o part): X_o = A_oo^{-1} L_o
+  Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
+  if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
   auto dJk = to_device_tmp(Jk, s), dJpk = to_device_tmp(Jpk, s);
   Rkc.alloc(std::max<size_t>(size_t(kk) * 2 * Nc, 1));
   Rkp.alloc(std::max<size_t>(size_t(kk) * 2 * Np, 1));

@@ -27,6 +27,20 @@ struct HoleSpec {
   int k, P;
 };
 
+// Recompression of one block of Q's low-rank factors (Sec. 3.4).  The
+// blockwise IDs bound a block of Q through proxies that stand for every
+// possible source or target near the modification, so their ranks can exceed
+// the block's own.  A row ID of the skeleton block A(J, cols) (sketched when
+// wide) gives A(J, cols) ~ T A(J[J'], cols), so L A(J, cols) ~ (L T)
+// A(J[J'], cols): L (m x k, column major) takes the product and J the
+// surviving skeleton rows; k shrinks to the new rank.  cols: the explicit
+// column lists of an IdMatProb (n1/e1 in E1, n2/e2 in E2).
+void recompress_rows(const NodesView& S, std::vector<int>& J, const IdMatProb& cols, const NodesView& E1, bool e1s,
+                     const NodesView& E2, bool e2s, DBuf<double>& L, int m, int& k, double tol,
+                     unsigned long long seed, cudaStream_t s);
+// RW_RECOMPRESS=0 (diagnostics) keeps the blockwise ranks.
+bool recompress_enabled();
+
 struct Refinement {
   SideStreams streams;  // first member: destroyed last
   const Wall* wall = nullptr;
@@ -40,6 +54,7 @@ struct Refinement {
   Hbs hpp;                             // A_pp (single leaf = dense inverse)
   bool pp_dense = false;
   int kf = 0, kn = 0, kpk = 0, kk = 0, k = 0;
+  int kpk_id = 0;                      // rank of the A_pk ID(s) before recompression
   double cond_w = 0.0;                 // ||W||_1 ||W^-1||_1
   // factors: L_o (2No x kk), L_p (2Np x kpk); R blocks; X = A~^{-1} L; W^{-1}
   DBuf<double> Lo, Lp, Rkc, Rkp, Rpk, Xo, Xp, Winv;

@@ -10,10 +10,11 @@
   on the star wall with circular and star-shaped holes and on the channel:
   RW_MODE_DIRECT_REFINED at <= 1e-10 relative (the FP64 parity bar),
   RW_MODE_DIRECT at <= 1e-8 (one compressed solve: 1e-12 IDs times the
-  conditioning of the holed system); FGMRES, which stops on the residual
-  (relative residual <= 1e-10 against the oracle's dense operator, as for
-  the refined channel), at <= 1e-10 times the oracle's condition estimate
-  of A_nn for the density;
+  conditioning of the holed system); FGMRES, which stops on the residual of
+  the compressed (ELS) operator: that residual <= 1e-10 (as for the refined
+  channel), the residual of the oracle's dense operator <= 1e-9 (the ELS
+  operator carries the 1e-12 compression) and the density within 1e-10
+  times the oracle's condition estimate of A_nn;
 * the velocity and pressure in the fluid against the oracle's evaluation and
   the closed-form Stokeslet field;
 * on the 1024-panel channel with the paper's three holes of 10 panels
@@ -118,7 +119,9 @@ def test_solve_modes_match_oracle(lib, kind, P, PH, a, k):
               f"cond(A_nn) {kappa:.1e}, iters {info['iters']}")
         assert err <= bar, (mode, err)
         if mode == rwsolve.MODE_GMRES_FP32:
-            assert info["rel_residual"] <= 1e-10 and res <= 1e-10
+            # FGMRES stops on the ELS residual; the exact operator differs from
+            # the ELS one by the 1e-12 compression
+            assert info["rel_residual"] <= 1e-10 and res <= 1e-9
         uu = u.reshape(nrhs, -1, 2).transpose(1, 2, 0)
         u_or = H.velocity(wall_o, hn, tau.T, *tg)
         assert np.abs(uu - u_or).max() <= 1e-12 * np.abs(u_or).max()
