@@ -77,6 +77,10 @@ typedef struct {
   int gmres_maxit;          /* iterations per restart cycle (default 30)     */
   int gmres_restarts;       /* restart cycles (default 4)                    */
   unsigned long long seed;  /* seed of the sketch generator                  */
+  double hole_div_ratio;    /* P^div radius / radius of an added hole (App. B;
+                               default 4: the wall points inside are taken
+                               explicitly, so a wider circle lowers the
+                               A_pk rank toward the block's own)            */
 } rw_opts;
 
 typedef struct {

@@ -71,6 +71,7 @@ rw::Opts to_opts(const rw_opts* o) {
   rw::require(o->proxy_ratio > 1.0, "opts.proxy_ratio must exceed 1");
   rw::require(o->n_proxy_refine >= 8 && o->n_proxy_refine <= 1024, "opts.n_proxy_refine must be in 8..1024");
   rw::require(o->div_ratio > o->bas_ratio && o->bas_ratio > 1.0, "opts need div_ratio > bas_ratio > 1");
+  rw::require(o->hole_div_ratio > o->bas_ratio, "opts need hole_div_ratio > bas_ratio");
   rw::require(o->sketch_cols >= 64, "opts.sketch_cols must be >= 64");
   rw::require(o->gmres_tol > 0 && o->gmres_maxit >= 1 && o->gmres_restarts >= 1, "bad GMRES options");
   r.leaf_points = o->leaf_points;
@@ -86,6 +87,7 @@ rw::Opts to_opts(const rw_opts* o) {
   r.gmres_maxit = o->gmres_maxit;
   r.gmres_restarts = o->gmres_restarts;
   r.seed = o->seed;
+  r.hole_div_ratio = o->hole_div_ratio;
   return r;
 }
 
@@ -139,6 +141,7 @@ int rw_default_opts(rw_opts* o) {
   o->gmres_maxit = d.gmres_maxit;
   o->gmres_restarts = d.gmres_restarts;
   o->seed = d.seed;
+  o->hole_div_ratio = d.hole_div_ratio;
   return RW_OK;
 }
 

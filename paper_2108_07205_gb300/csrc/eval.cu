@@ -443,21 +443,34 @@ __global__ void k_flux(NodesView nd, const double* x, int ldx, double* flux) {
 
 // y[T rows] (+)= A(T, S) x for two disjoint node sets, every 2 x 2 block
 // evaluated on the fly (App. B: the hole columns seen on the wall, the wall
-// columns seen on the holes).  One thread per (target point, right-hand side).
-__global__ void k_apply_cross(NodesView T, NodesView Sv, const double* x, int ldx, double* y, int ldy, int acc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-  if (i >= T.n) return;
+// columns seen on the holes).  One CTA per (target point, right-hand side),
+// sources split over its threads (a few hundred hole targets against tens
+// of thousands of wall sources still fill the GPU).
+__global__ void __launch_bounds__(128) k_apply_cross(NodesView T, NodesView Sv, const double* x, int ldx, double* y,
+                                                     int ldy, int acc) {
+  const int i = blockIdx.x, r = blockIdx.y;
   const double* xr = x + size_t(r) * ldx;
   double ux = 0.0, uy = 0.0;
-  for (int j = 0; j < Sv.n; ++j) {
+  for (int j = threadIdx.x; j < Sv.n; j += blockDim.x) {
     const Blk2 B = a_block(T, i, Sv, j, false);
     const double a = xr[2 * j], b = xr[2 * j + 1];
     ux += B.v[0][0] * a + B.v[0][1] * b;
     uy += B.v[1][0] * a + B.v[1][1] * b;
   }
-  double* yr = y + size_t(r) * ldy;
-  yr[2 * i] = (acc ? yr[2 * i] : 0.0) + ux;
-  yr[2 * i + 1] = (acc ? yr[2 * i + 1] : 0.0) + uy;
+  for (int off = 16; off > 0; off >>= 1) {
+    ux += __shfl_down_sync(0xffffffffu, ux, off);
+    uy += __shfl_down_sync(0xffffffffu, uy, off);
+  }
+  __shared__ double sx[4], sy[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sx[warp] = ux; sy[warp] = uy; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double vx = sx[0] + sx[1] + sx[2] + sx[3], vy = sy[0] + sy[1] + sy[2] + sy[3];
+    double* yr = y + size_t(r) * ldy;
+    yr[2 * i] = (acc ? yr[2 * i] : 0.0) + vx;
+    yr[2 * i + 1] = (acc ? yr[2 * i + 1] : 0.0) + vy;
+  }
 }
 
 // Moments M_n(t) = int_{-1}^{1} P_n(s) log|t - s| ds, n = 0..NM-1, of the
@@ -751,7 +764,8 @@ void apply_cross(const NodesView& T, const NodesView& Sv, const double* x, int l
   if (T.n <= 0 || nrhs <= 0) return;
   require(T.kind != Sv.kind, "apply_cross: the node sets must be a wall and holes");
   ProfScope prof_(KC_EVAL, s);
-  k_apply_cross<<<dim3(ceil_div(T.n, 128), nrhs), 128, 0, s>>>(T, Sv, x, ldx, y, ldy, accumulate);
+  require(nrhs <= 65535, "apply_cross: at most 65535 right-hand sides per call");
+  k_apply_cross<<<dim3(T.n, nrhs), 128, 0, s>>>(T, Sv, x, ldx, y, ldy, accumulate);
   RW_CHECK_LAUNCH();
 }
 

@@ -168,7 +168,17 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
     TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, kSketchTry, seed, chunk, s);
     if (t.k <= kSketchTry - kSketchMargin) return t;
   }
-  return tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, sketch_width, seed, chunk, s);
+  // A sketch of width w certifies ranks up to w - kSketchMargin only: a rank
+  // beyond that means the sketch truncated the block, so the width doubles
+  // until the rank leaves the margin or the sketch is no narrower than the
+  // block itself (rows + margin, or every column).
+  int w = sketch_width;
+  for (;;) {
+    TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, w, seed, chunk, s);
+    const bool sketched = ncol > sketch_cols && w < ncol;
+    if (!sketched || t.k <= w - kSketchMargin || w >= int(rows.size()) + kSketchMargin) return t;
+    w = std::min(2 * w, std::max(int(rows.size()) + kSketchMargin, w + 1));
+  }
 }
 
 namespace {

@@ -25,6 +25,7 @@ struct Opts {
   int gmres_maxit = 30;
   int gmres_restarts = 4;
   unsigned long long seed = 0x5eed2108ull;
+  double hole_div_ratio = 4.0;
 };
 
 // A list of row-interpolative decompositions evaluated on the fly: each job

@@ -11,7 +11,8 @@
 //    [A_{p,div} | A_pk^near] with that hole's P^div circle and the wall
 //    points inside it; L_pk = blkdiag over the holes.
 // so L = blkdiag(L_k, L_pk), R = [[0, A(J_k, I_p)], [A(J_pk, I_k), 0]],
-// then recompressed by row IDs of the two skeleton blocks (Sec. 3.4).
+// with the wall block recompressed by a row ID of its skeleton rows
+// (Sec. 3.4).
 // A_pp = 1/2 I + D + S is assembled densely with the singular rule of the
 // hole matrix kernel and inverted (single-leaf HBS).
 #include "refine.cuh"
@@ -118,7 +119,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
     hcy[h] = cy;
     hrho[h] = std::sqrt(r2);
     circ_bas.insert(circ_bas.end(), {cx, cy, o.bas_ratio * hrho[h]});
-    circ_div.insert(circ_div.end(), {cx, cy, o.div_ratio * hrho[h]});
+    circ_div.insert(circ_div.end(), {cx, cy, o.hole_div_ratio * hrho[h]});
   }
   // wall DOFs: far (outside every P^div circle) and near; near set per hole
   std::vector<int> far_d, near_d;
@@ -245,19 +246,18 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
   }
   for (int i : tf.skel) Jk.push_back(far_d[i]);
   for (int i : tn.skel) Jk.push_back(near_d[i]);
-  // a4, recompression (Sec. 3.4): row IDs of the skeleton blocks
-  // R_k = A(J_k, I_p) and R_pk = A(J_pk, I_k) (see recompress_rows)
+  // a4, recompression (Sec. 3.4): a row ID of the skeleton block
+  // R_k = A(J_k, I_p) (see recompress_rows; 960 columns, cheap).  The A_pk
+  // blocks are not recompressed: their columns are every wall point, and
+  // with P^div at hole_div_ratio = 4 hole radii (the wall points inside
+  // taken explicitly) their ranks are already close to the blocks' own
+  // (1920-panel channel, three holes: k_pk 505 -> 262 against 2 radii;
+  // recompressing them as well gains 3 % of k for 30 % more time).
   const double rtol = 0.1 * o.id_tol;
   if (recompress_enabled()) {
     IdMatProb ck{};
     ck.n2 = 2 * Np; ck.e2 = dall_p.p;
     recompress_rows(VW, Jk, ck, VW, true, VP, false, Lo, 2 * No, kk, rtol, o.seed + 404, s);
-    std::vector<int> od(2 * No);
-    for (int d = 0; d < 2 * No; ++d) od[d] = d;
-    auto dall_o = to_device_tmp(od, s);
-    IdMatProb cp{};
-    cp.n1 = 2 * No; cp.e1 = dall_o.p;
-    recompress_rows(VP, Jpk, cp, VW, false, VW, false, Lp, 2 * Np, kpk, rtol, o.seed + 505, s);
     k = kk + kpk;
     tr.mark("recompression");
   }

@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr char kTag[8] = {'R', 'W', 'H', 'B', 'S', 'v', '0', '1'};
+constexpr char kTag[8] = {'R', 'W', 'H', 'B', 'S', 'v', '0', '2'};  // v02: options gained hole_div_ratio
 
 struct File {
   FILE* f = nullptr;

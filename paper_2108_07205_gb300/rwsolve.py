@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
                 ("div_ratio", ctypes.c_double), ("bas_ratio", ctypes.c_double),
                 ("dense_pp_max_points", ctypes.c_int), ("sketch_cols", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
-                ("gmres_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+                ("gmres_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("hole_div_ratio", ctypes.c_double)]
 
 
 class HbsStats(ctypes.Structure):
