@@ -18,6 +18,7 @@ the host cores on the same workload family (see cpu_baseline.sample).
 Multi-GPU: replicas only (independent walls and windows per rank).
 """
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -60,7 +61,12 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons (background)."""
+    """nvidia-smi sampling of SM clocks and throttle reasons (background).
+
+    The sampler starts before the warm-up, so that nvidia-smi's own start-up
+    (slow on a fresh machine) stays out of the timed region, and stop() keeps
+    only the samples stamped inside [t0, t1] (host wall clock of the timed
+    region)."""
 
     def __init__(self, index):
         self.index = index
@@ -68,7 +74,7 @@ class Clocks:
 
     def start(self):
         cmd = ["nvidia-smi", f"--id={self.index}",
-               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+               "--query-gpu=timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
                "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
                "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"]
         try:
@@ -76,7 +82,7 @@ class Clocks:
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -85,8 +91,16 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 7:
+            if len(f) < 8:
                 continue
+            if t0 is not None:
+                try:
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                if ts < t0 or ts > t1:
+                    continue
+            f = f[1:]
             try:
                 sm.append(float(f[0]))
                 mx.append(float(f[1]))
@@ -164,7 +178,10 @@ def run_ours(args, rank, world, local):
         return st, info
 
     def timed(offset, host):
+        clk = Clocks(local)
+        clk.start()
         for w in range(args.warmup):
+            flush.zero_()
             step(offset + w, host)
         replicas.barrier()
         torch.cuda.synchronize()
@@ -172,8 +189,7 @@ def run_ours(args, rank, world, local):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         stats = []
-        clk = Clocks(local)
-        clk.start()
+        t_start = time.time()
         n_launch0 = rwsolve.kernel_launches()
         ev0.record(stream)
         for i in range(args.steps):
@@ -187,8 +203,9 @@ def run_ours(args, rank, world, local):
             lat.append((e0, e1))
         ev1.record(stream)
         torch.cuda.synchronize()
+        t_end = time.time()
         launches = rwsolve.kernel_launches() - n_launch0
-        clocks = clk.stop()
+        clocks = clk.stop(t_start, t_end)
         replicas.barrier()
         ms = ev0.elapsed_time(ev1)
         lats = [a.elapsed_time(b) for a, b in lat]

@@ -19,6 +19,30 @@ namespace rw {
 std::atomic<unsigned long long> g_launches{0};
 thread_local cudaStream_t tl_alloc_stream = nullptr;
 
+void pool_retain_once() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<bool> done[kMaxDev];
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) { cudaGetLastError(); return; }
+  if (done[dev].load(std::memory_order_acquire)) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev].load(std::memory_order_relaxed)) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long keep = 0;
+    if (const char* e = std::getenv("RW_POOL_RETAIN_BYTES")) {
+      keep = std::strtoull(e, nullptr, 10);
+    } else {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) keep = tot / 4;
+    }
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();  // a refusal leaves the default behaviour
+  done[dev].store(true, std::memory_order_release);
+}
+
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }

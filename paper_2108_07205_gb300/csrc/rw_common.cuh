@@ -45,6 +45,12 @@ inline void require(bool ok, const std::string& msg, int code = RW_ERR_INVALID) 
 // handle's memory does not synchronise the whole device.  Unset (the
 // default), DBuf uses cudaMalloc / cudaFree.
 extern thread_local cudaStream_t tl_alloc_stream;
+// Once per device, before its first stream-ordered allocation: the default
+// memory pool keeps freed memory (up to a quarter of the device, or
+// RW_POOL_RETAIN_BYTES) instead of returning it to the driver at every
+// synchronisation, so a refinement's temporaries and factors are recycled
+// from one time step to the next instead of being mapped afresh.
+void pool_retain_once();
 struct AllocStreamScope {
   cudaStream_t prev;
   explicit AllocStreamScope(cudaStream_t s) : prev(tl_alloc_stream) { tl_alloc_stream = s; }
@@ -76,6 +82,7 @@ struct DBuf {
       if (tl_alloc_stream) {
         as = tl_alloc_stream;
         async = true;
+        pool_retain_once();
         e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), as);
       } else {
         async = false;
@@ -120,6 +127,7 @@ struct TBuf {
   TBuf(size_t count, cudaStream_t st) : s(st) {
     n = count;
     if (count) {
+      pool_retain_once();
       cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
       if (e != cudaSuccess) {
         p = nullptr; n = 0;
