@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="direct", choices=["direct", "gmres", "refined"])
+    ap.add_argument("--mode", default="direct", choices=["direct", "gmres", "gmres_bf16", "refined"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=48, help="serving workload: number of requests per phase")
     ap.add_argument("--walls", type=int, default=32, help="batched workload: number of walls")
@@ -136,7 +136,7 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
     rwsolve.load(build_if_missing=True)
     mode = {"direct": rwsolve.MODE_DIRECT, "gmres": rwsolve.MODE_GMRES_FP32,
-            "refined": rwsolve.MODE_DIRECT_REFINED}[args.mode]
+            "refined": rwsolve.MODE_DIRECT_REFINED, "gmres_bf16": rwsolve.MODE_GMRES_BF16}[args.mode]
     t0 = time.time()
     wall = rwsolve.Wall("channel", P_PANELS)
     torch.cuda.synchronize()
@@ -180,30 +180,34 @@ def run_ours(args, rank, world, local):
     def timed(offset, host):
         clk = Clocks(local)
         clk.start()
-        for w in range(args.warmup):
-            flush.zero_()
-            step(offset + w, host)
-        replicas.barrier()
-        torch.cuda.synchronize()
-        lat = []
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        stats = []
-        t_start = time.time()
-        n_launch0 = rwsolve.kernel_launches()
-        ev0.record(stream)
-        for i in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st, info = step(offset + args.warmup + i, host)
-            e1.record(stream)
-            stats.append((st, info))
-            lat.append((e0, e1))
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        t_end = time.time()
+        try:
+            for w in range(args.warmup):
+                flush.zero_()
+                step(offset + w, host)
+            replicas.barrier()
+            torch.cuda.synchronize()
+            lat = []
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            stats = []
+            t_start = time.time()
+            n_launch0 = rwsolve.kernel_launches()
+            ev0.record(stream)
+            for i in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, info = step(offset + args.warmup + i, host)
+                e1.record(stream)
+                stats.append((st, info))
+                lat.append((e0, e1))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t_end = time.time()
+        except BaseException:
+            clk.stop()   # never leave the sampler running
+            raise
         launches = rwsolve.kernel_launches() - n_launch0
         clocks = clk.stop(t_start, t_end)
         replicas.barrier()
@@ -211,7 +215,19 @@ def run_ours(args, rank, world, local):
         lats = [a.elapsed_time(b) for a, b in lat]
         return ms, lats, stats, clocks, launches
 
-    ms, lats, stats, clocks, launches = timed(0, host=False)
+    try:
+        ms, lats, stats, clocks, launches = timed(0, host=False)
+    except rwsolve.RWError as e:
+        if args.mode != "gmres_bf16" or e.code != -4:
+            raise
+        # BF16 sweeps as the preconditioner do not converge on this wall: the
+        # BF16 rounding of the inverse times the wall's conditioning exceeds one
+        if rank == 0:
+            print(json.dumps({"metric": "refined-wall solves/s", "value": None, "unit": "solves/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16", "data": "synthetic",
+                              "config": workload_config(args), "not_converged": str(e)}))
+        return
     ms_e2e, lats_e2e, _, _, _ = timed(total, host=True)
     # profiled repeat of the device-input steps: per-kernel-class CUDA-event
     # durations (on each launch's stream) and algorithmic flops
@@ -655,11 +671,11 @@ def main():
         "metric": "refined-wall solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.mode != "gmres" else "f64+f32", "data": "synthetic",
+        "dtype": {"gmres": "f64+f32", "gmres_bf16": "f64+bf16"}.get(args.mode, "f64"), "data": "synthetic",
         "config": workload_config(args),
         "p50_ms": float(np.percentile(out["lat"], 50)), "p99_ms": float(np.percentile(out["lat"], 99)),
         "solve_only_per_s": NRHS * 1e3 / out["solve_ms"], "k_mean": out["k_mean"], "n_p_range": out["np_range"],
-        "hbs_build_s": out["build_s"], "gmres_iters": out["iters"] if args.mode == "gmres" else None,
+        "hbs_build_s": out["build_s"], "gmres_iters": out["iters"] if args.mode in ("gmres", "gmres_bf16") else None,
         "e2e": {"value": e2e, "unit": "solves/s",
                 "h2d_bytes_per_step": 8 * (2 * N_SRC + 2 * N_SRC * NRHS + 2 * TARGETS) if NRHS == 1 else
                 8 * (4 * NRHS + 4 * NRHS * NRHS + 2 * TARGETS),

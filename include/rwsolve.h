@@ -252,6 +252,12 @@ int rw_stokeslet_data(rw_ref_t r, int n_src, const double* src, int nrhs,
                                  refined operator A_nn (on-the-fly N-body
                                  evaluation); removes the compression error
                                  amplified by the conditioning of A_nn      */
+#define RW_MODE_GMRES_BF16 3  /* as RW_MODE_GMRES_FP32 with the HBS sweeps'
+                                 matrices in BF16 (FP32 vectors and
+                                 accumulation, Sec. 4.2): converges on
+                                 well-conditioned walls in more iterations;
+                                 RW_ERR_NOT_CONVERGED where the BF16 rounding
+                                 times the conditioning of A_oo exceeds one */
 
 /* y = A_nn tau with every entry of the refined operator evaluated on the fly
  * (Sec. 2, Eq. interior_BIE_discretized2 on the refined nodes): the exact

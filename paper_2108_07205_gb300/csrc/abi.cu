@@ -181,6 +181,7 @@ int rw_hbs_build(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_h
     w.nodes.hy.assign(all.begin() + 16 * P, all.begin() + 32 * P);
     w.hbs.build(w.nodes, w.opts, s);
     w.hbs.make_fp32(s);
+    w.hbs.make_bf16(s);
     RW_CUDA(cudaStreamSynchronize(s));
   });
   if (rc == RW_OK) *out = h.release();
@@ -207,6 +208,7 @@ int rw_hbs_build_nodes(const rw_nodes* nodes, const rw_opts* opts, void* stream,
     w.nodes.hy.assign(hn.begin() + n, hn.begin() + 2 * size_t(n));
     w.hbs.build(w.nodes, w.opts, s);
     w.hbs.make_fp32(s);
+    w.hbs.make_bf16(s);
     RW_CUDA(cudaStreamSynchronize(s));
   });
   if (rc == RW_OK) *out = h.release();
@@ -369,7 +371,8 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
              int mode, void* stream, rw_info* info) {
   if (!r || !g || !tau || nrhs < 1 || n_targets < 0) return fail(RW_ERR_INVALID, "rw_solve: bad argument");
   if (n_targets > 0 && (!targets || !u)) return fail(RW_ERR_INVALID, "rw_solve: targets and u required");
-  if (mode != RW_MODE_DIRECT && mode != RW_MODE_GMRES_FP32 && mode != RW_MODE_DIRECT_REFINED)
+  if (mode != RW_MODE_DIRECT && mode != RW_MODE_GMRES_FP32 && mode != RW_MODE_DIRECT_REFINED &&
+      mode != RW_MODE_GMRES_BF16)
     return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
   int iters = 0;
   double relres = 0.0;
@@ -384,7 +387,7 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
       f.solve_refined(ag.p, at.p, nrhs, 1, s);
       iters = 1;
     } else {
-      f.solve_gmres(ag.p, at.p, nrhs, s, &iters, &relres);
+      f.solve_gmres(ag.p, at.p, nrhs, s, &iters, &relres, mode == RW_MODE_GMRES_BF16);
     }
     if (n_targets > 0) {
       Arg ax(targets, size_t(2) * n_targets, true, s), au(u, size_t(2) * n_targets * nrhs, false, s);
@@ -393,7 +396,7 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     }
     at.finish(s);
     RW_CUDA(cudaStreamSynchronize(s));
-    if (mode == RW_MODE_GMRES_FP32 && relres > f.wall->opts.gmres_tol)
+    if ((mode == RW_MODE_GMRES_FP32 || mode == RW_MODE_GMRES_BF16) && relres > f.wall->opts.gmres_tol)
       throw rw::Error(RW_ERR_NOT_CONVERGED, "rw_solve: GMRES stopped at relative residual " + std::to_string(relres));
   });
   if (info) {

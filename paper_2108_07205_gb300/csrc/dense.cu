@@ -241,9 +241,9 @@ __global__ void k_gemm_reduce(const GemmWork* work, const double* scratch) {
 constexpr int VR = 64;
 constexpr int VCHUNK = 2048;  // columns per split-K chunk
 
-template <class T>
+template <class T, class MT = T>
 struct GemvWork {  // device-side descriptor (adds split-K bookkeeping)
-  GemvProb<T> p;
+  GemvProb<T, MT> p;
   int tilesM, nchunk;
   long long scratch_off;  // offset of this problem's partials (elements)
 };
@@ -251,14 +251,14 @@ struct GemvWork {  // device-side descriptor (adds split-K bookkeeping)
 template <class T> struct Acc { typedef double type; };
 template <> struct Acc<float> { typedef float type; };
 
-template <class T, int NR>
-__global__ void __launch_bounds__(256) k_gemv(const GemvWork<T>* work, const int* offs, int nprob,
+template <class T, class MT, int NR>
+__global__ void __launch_bounds__(256) k_gemv(const GemvWork<T, MT>* work, const int* offs, int nprob,
                                               T* scratch) {
   typedef typename Acc<T>::type A_t;
   const int tile = blockIdx.x;
   const int b = find_problem(offs, nprob, tile);
-  const GemvWork<T> W = work[b];
-  const GemvProb<T>& P = W.p;
+  const GemvWork<T, MT> W = work[b];
+  const GemvProb<T, MT>& P = W.p;
   const int t = tile - offs[b];
   const int mt = t % W.tilesM, chunk = t / W.tilesM;
   const int r0 = mt * VR;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvWork<T>* work, const int
       for (int r = 0; r < NR; ++r) xs[e][r] = A_t(P.x[cb + e + size_t(r) * P.ldx]);
     __syncthreads();
     if (row < P.m) {
-      const T* a = P.A + row + size_t(cb) * P.lda;
+      const MT* a = P.A + row + size_t(cb) * P.lda;
       for (int j = lc; j < ncur; j += 4) {
         const A_t v = A_t(a[size_t(j) * P.lda]);
 #pragma unroll
@@ -305,13 +305,13 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvWork<T>* work, const int
   }
 }
 
-template <class T, int NR>
-__global__ void k_gemv_reduce(const GemvWork<T>* work, int nprob, const T* scratch) {
+template <class T, class MT, int NR>
+__global__ void k_gemv_reduce(const GemvWork<T, MT>* work, int nprob, const T* scratch) {
   typedef typename Acc<T>::type A_t;
   const int b = blockIdx.y;
-  const GemvWork<T> W = work[b];
+  const GemvWork<T, MT> W = work[b];
   if (W.nchunk == 1) return;
-  const GemvProb<T>& P = W.p;
+  const GemvProb<T, MT>& P = W.p;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < P.m; row += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -1393,14 +1393,14 @@ void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s) {
   }
 }
 
-template <class T>
-static void gemv_plan(const std::vector<GemvProb<T>>& probs, int nrhs, std::vector<GemvWork<T>>& work,
+template <class T, class MT>
+static void gemv_plan(const std::vector<GemvProb<T, MT>>& probs, int nrhs, std::vector<GemvWork<T, MT>>& work,
                       std::vector<int>& offs, size_t& scratch) {
   offs.assign(1, 0);
   scratch = 0;
   for (const auto& p : probs) {
     if (p.m <= 0) continue;
-    GemvWork<T> w;
+    GemvWork<T, MT> w;
     w.p = p;
     w.tilesM = ceil_div(p.m, VR);
     w.nchunk = std::max(1, ceil_div(std::max(p.n, 1), VCHUNK));
@@ -1411,19 +1411,19 @@ static void gemv_plan(const std::vector<GemvProb<T>>& probs, int nrhs, std::vect
   }
 }
 
-template <class T>
-size_t gemv_scratch_elems(const std::vector<GemvProb<T>>& probs, int nrhs) {
-  std::vector<GemvWork<T>> w;
+template <class T, class MT>
+size_t gemv_scratch_elems(const std::vector<GemvProb<T, MT>>& probs, int nrhs) {
+  std::vector<GemvWork<T, MT>> w;
   std::vector<int> o;
   size_t sc;
   gemv_plan(probs, nrhs, w, o, sc);
   return sc;
 }
 
-template <class T>
-void batched_gemv(const std::vector<GemvProb<T>>& probs, int nrhs, T* scratch, cudaStream_t s) {
+template <class T, class MT>
+void batched_gemv(const std::vector<GemvProb<T, MT>>& probs, int nrhs, T* scratch, cudaStream_t s) {
   require(nrhs >= 1 && nrhs <= 8, "batched_gemv: nrhs must be in 1..8");
-  std::vector<GemvWork<T>> work;
+  std::vector<GemvWork<T, MT>> work;
   std::vector<int> offs;
   size_t sc;
   gemv_plan(probs, nrhs, work, offs, sc);
@@ -1437,14 +1437,14 @@ void batched_gemv(const std::vector<GemvProb<T>>& probs, int nrhs, T* scratch, c
   for (auto& w : work) {
     maxm = std::max(maxm, w.p.m);
     fl += 2.0 * w.p.m * double(w.p.n) * nrhs;
-    by += double(sizeof(T)) * (double(w.p.m) * w.p.n + double(nrhs) * (w.p.n + 2.0 * w.p.m));
+    by += double(sizeof(MT)) * double(w.p.m) * w.p.n + double(sizeof(T)) * double(nrhs) * (w.p.n + 2.0 * w.p.m);
   }
   ProfScope ps(KC_GEMV, s, fl, by);
   switch (nrhs) {
 #define RW_GEMV_CASE(NR)                                                                   \
   case NR:                                                                                 \
-    k_gemv<T, NR><<<offs.back(), 256, 0, s>>>(dw.p, doff.p, nprob, scratch);               \
-    if (sc) k_gemv_reduce<T, NR><<<dim3(ceil_div(maxm, 256), nprob), 256, 0, s>>>(dw.p, nprob, scratch); \
+    k_gemv<T, MT, NR><<<offs.back(), 256, 0, s>>>(dw.p, doff.p, nprob, scratch);           \
+    if (sc) k_gemv_reduce<T, MT, NR><<<dim3(ceil_div(maxm, 256), nprob), 256, 0, s>>>(dw.p, nprob, scratch); \
     break;
     RW_GEMV_CASE(1) RW_GEMV_CASE(2) RW_GEMV_CASE(3) RW_GEMV_CASE(4)
     RW_GEMV_CASE(5) RW_GEMV_CASE(6) RW_GEMV_CASE(7) RW_GEMV_CASE(8)
@@ -1482,8 +1482,8 @@ void gemv_into(const std::vector<GemvProb<T>>& probs, int nrhs, void* desc, T* s
   switch (nrhs) {
 #define RW_GEMV_INTO_CASE(NR)                                                                \
   case NR:                                                                                   \
-    k_gemv<T, NR><<<offs.back(), 256, 0, s>>>(dw, doff, nprob, scratch);                     \
-    if (sc) k_gemv_reduce<T, NR><<<dim3(ceil_div(maxm, 256), nprob), 256, 0, s>>>(dw, nprob, scratch); \
+    k_gemv<T, T, NR><<<offs.back(), 256, 0, s>>>(dw, doff, nprob, scratch);                  \
+    if (sc) k_gemv_reduce<T, T, NR><<<dim3(ceil_div(maxm, 256), nprob), 256, 0, s>>>(dw, nprob, scratch); \
     break;
     RW_GEMV_INTO_CASE(1) RW_GEMV_INTO_CASE(2) RW_GEMV_INTO_CASE(3) RW_GEMV_INTO_CASE(4)
     RW_GEMV_INTO_CASE(5) RW_GEMV_INTO_CASE(6) RW_GEMV_INTO_CASE(7) RW_GEMV_INTO_CASE(8)
@@ -1497,11 +1497,14 @@ template void gemv_into<double>(const std::vector<GemvProb<double>>&, int, void*
 
 template size_t gemv_scratch_elems<double>(const std::vector<GemvProb<double>>&, int);
 template size_t gemv_scratch_elems<float>(const std::vector<GemvProb<float>>&, int);
+template size_t gemv_scratch_elems<float, __nv_bfloat16>(const std::vector<GemvProb<float, __nv_bfloat16>>&, int);
 template void batched_gemv<double>(const std::vector<GemvProb<double>>&, int, double*, cudaStream_t);
 template void batched_gemv<float>(const std::vector<GemvProb<float>>&, int, float*, cudaStream_t);
+template void batched_gemv<float, __nv_bfloat16>(const std::vector<GemvProb<float, __nv_bfloat16>>&, int, float*,
+                                                 cudaStream_t);
 
 template <>
-void matvec<double>(const std::vector<GemvProb<double>>& probs, int nrhs, cudaStream_t s) {
+void matvec<double, double>(const std::vector<GemvProb<double>>& probs, int nrhs, cudaStream_t s) {
   if (probs.empty() || nrhs <= 0) return;
   if (nrhs <= 8) {
     size_t sc = gemv_scratch_elems(probs, nrhs);
@@ -1514,17 +1517,28 @@ void matvec<double>(const std::vector<GemvProb<double>>& probs, int nrhs, cudaSt
   }
 }
 
-template <>
-void matvec<float>(const std::vector<GemvProb<float>>& probs, int nrhs, cudaStream_t s) {
+template <class MT>
+static void matvec_f32(const std::vector<GemvProb<float, MT>>& probs, int nrhs, cudaStream_t s) {
   if (probs.empty() || nrhs <= 0) return;
   for (int r0 = 0; r0 < nrhs; r0 += 8) {
     const int nr = std::min(8, nrhs - r0);
-    std::vector<GemvProb<float>> ps = probs;
+    std::vector<GemvProb<float, MT>> ps = probs;
     for (auto& p : ps) { p.x += size_t(r0) * p.ldx; p.y += size_t(r0) * p.ldy; }
     size_t sc = gemv_scratch_elems(ps, nr);
     TBuf<float> scratch(sc, s);
     batched_gemv(ps, nr, scratch.p, s);
   }
+}
+
+template <>
+void matvec<float, float>(const std::vector<GemvProb<float>>& probs, int nrhs, cudaStream_t s) {
+  matvec_f32(probs, nrhs, s);
+}
+
+template <>
+void matvec<float, __nv_bfloat16>(const std::vector<GemvProb<float, __nv_bfloat16>>& probs, int nrhs,
+                                  cudaStream_t s) {
+  matvec_f32(probs, nrhs, s);
 }
 
 void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
@@ -1853,6 +1867,17 @@ void fill_zero(double* p, size_t n, cudaStream_t s) {
   k_fill_zero<<<grid_for(n), 256, 0, s>>>(p, n);
   RW_CHECK_LAUNCH();
 }
+__global__ void k_d2bf(const double* in, __nv_bfloat16* out, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    out[i] = __double2bfloat16(in[i]);
+}
+
+void copy_d2bf(const double* in, __nv_bfloat16* out, size_t n, cudaStream_t s) {
+  if (n == 0) return;
+  k_d2bf<<<grid_for(n), 256, 0, s>>>(in, out, n);
+  RW_CHECK_LAUNCH();
+}
+
 void copy_d2f(const double* in, float* out, size_t n, cudaStream_t s) {
   if (!n) return;
   k_d2f<<<grid_for(n), 256, 0, s>>>(in, out, n);

@@ -2,6 +2,7 @@
 // Every routine takes a list of independent problems of varying size and
 // runs them in one launch; matrices are column-major.
 #pragma once
+#include <cuda_bf16.h>
 #include "rw_common.cuh"
 
 namespace rw {
@@ -19,14 +20,14 @@ struct GemmProb {
 void batched_gemm(const std::vector<GemmProb>& probs, cudaStream_t s);
 
 // y (m x nrhs) = alpha A x + beta y for column-major A (m x n) and a few
-// right-hand sides (nrhs <= 8).  Matrix and vector element types are
-// templated (double or float); accumulation is in double for double
-// matrices and float for float matrices.  When a problem is wide (n large
-// and m small) the columns are split into chunks whose partial sums go to a
-// scratch buffer and are added in a fixed order (deterministic).
-template <class T>
+// right-hand sides (nrhs <= 8).  Vector type T (double or float) and matrix
+// type MT (T, or __nv_bfloat16 with float vectors); accumulation is in T.
+// When a problem is wide (n large and m small) the columns are split into
+// chunks whose partial sums go to a scratch buffer and are added in a fixed
+// order (deterministic).
+template <class T, class MT = T>
 struct GemvProb {
-  const T* A;
+  const MT* A;
   const T* x;
   T* y;
   int m, n, lda, ldx, ldy;
@@ -34,13 +35,13 @@ struct GemvProb {
 };
 
 // Scratch needed by batched_gemv for a problem list (in elements of T).
-template <class T>
-size_t gemv_scratch_elems(const std::vector<GemvProb<T>>& probs, int nrhs);
+template <class T, class MT = T>
+size_t gemv_scratch_elems(const std::vector<GemvProb<T, MT>>& probs, int nrhs);
 
 // Runs the problems; `scratch` must hold gemv_scratch_elems() elements (may
 // be null when that is 0).
-template <class T>
-void batched_gemv(const std::vector<GemvProb<T>>& probs, int nrhs, T* scratch,
+template <class T, class MT = T>
+void batched_gemv(const std::vector<GemvProb<T, MT>>& probs, int nrhs, T* scratch,
                   cudaStream_t s);
 
 // The same GEMV launch with caller-provided device memory for the launch
@@ -54,8 +55,8 @@ void gemv_into(const std::vector<GemvProb<T>>& probs, int nrhs, void* desc, T* s
 // y = alpha A x + beta y for a problem list and any nrhs: GEMV kernels for
 // nrhs <= 8 (chunks of 8 for FP32), the tiled GEMM above that (FP64).
 // Temporaries are stream-ordered.
-template <class T>
-void matvec(const std::vector<GemvProb<T>>& probs, int nrhs, cudaStream_t s);
+template <class T, class MT = T>
+void matvec(const std::vector<GemvProb<T, MT>>& probs, int nrhs, cudaStream_t s);
 
 // Inverse of square matrices by Gauss-Jordan elimination with partial
 // pivoting (the pivot sequence of LU with partial pivoting).  A is read, Ainv
@@ -111,5 +112,7 @@ void fill_rademacher(double* out, size_t n, unsigned long long seed, cudaStream_
 void fill_zero(double* p, size_t n, cudaStream_t s);
 void axpby(const double* x, double* y, size_t n, double a, double b, cudaStream_t s);  // y = a x + b y
 void copy_d2f(const double* in, float* out, size_t n, cudaStream_t s);
+// out = bf16(in), round to nearest even
+void copy_d2bf(const double* in, __nv_bfloat16* out, size_t n, cudaStream_t s);
 
 }  // namespace rw

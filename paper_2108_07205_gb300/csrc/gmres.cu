@@ -2,7 +2,8 @@
 // system (A~ + L R) tau_ext = g_ext (Eq. ELS_approximate), with A~ applied by
 // the FP64 HBS forward representations of A_oo and A_pp and L R by the FP64
 // factors.  The preconditioner is the Woodbury inverse of Sec. 4.2 whose
-// A~^{-1} applications are HBS inverse sweeps in FP32; X and W^{-1} stay FP64.
+// A~^{-1} applications are HBS inverse sweeps in FP32 (or with the matrices
+// in BF16, FP32 accumulation); X and W^{-1} stay FP64.
 // Right preconditioning keeps the monitored residual equal to the true one.
 // Every right-hand side runs its own Krylov space; the columns advance in
 // lockstep and stop together once all have converged.
@@ -65,9 +66,10 @@ int g1(long long n) { return int(std::max<long long>(1, std::min<long long>((n +
 }  // namespace
 
 void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters_out,
-                             double* relres_out) const {
+                             double* relres_out, bool bf16) const {
   const Opts& o = wall->opts;
   require(wall->hbs.has_fp32 && hpp.has_fp32, "GMRES path: FP32 sweep data missing");
+  require(!bf16 || (wall->hbs.has_bf16 && hpp.has_bf16), "GMRES path: BF16 sweep data missing");
   const int m = o.gmres_maxit;
   const int no = 2 * No, np = 2 * Np;
   // Krylov bases V (m+1 vectors) and Z (m vectors), o and p parts separately
@@ -108,8 +110,13 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
     k_d2f_v<<<g1(size_t(no) * nrhs), 256, 0, s>>>(vo, fo_in.p, size_t(no) * nrhs);
     k_d2f_v<<<g1(size_t(np) * nrhs), 256, 0, s>>>(vp, fp_in.p, size_t(np) * nrhs);
     RW_CHECK_LAUNCH();
-    wall->hbs.apply_inverse_f32(fo_in.p, fo_out.p, nrhs, s);
-    hpp.apply_inverse_f32(fp_in.p, fp_out.p, nrhs, s);
+    if (bf16) {
+      wall->hbs.apply_inverse_bf16(fo_in.p, fo_out.p, nrhs, s);
+      hpp.apply_inverse_bf16(fp_in.p, fp_out.p, nrhs, s);
+    } else {
+      wall->hbs.apply_inverse_f32(fo_in.p, fo_out.p, nrhs, s);
+      hpp.apply_inverse_f32(fp_in.p, fp_out.p, nrhs, s);
+    }
     k_f2d_v<<<g1(size_t(no) * nrhs), 256, 0, s>>>(fo_out.p, zo, size_t(no) * nrhs);
     k_f2d_v<<<g1(size_t(np) * nrhs), 256, 0, s>>>(fp_out.p, zp, size_t(np) * nrhs);
     RW_CHECK_LAUNCH();

@@ -709,6 +709,18 @@ void Hbs::build_dense(DBuf<double>&& A, int npts, cudaStream_t s) {
   bytes = LV.G.bytes() + LV.D.bytes();
 }
 
+void Hbs::make_bf16(cudaStream_t s) {
+  for (int l = 0; l <= L; ++l) {
+    Level& LV = lev[l];
+    LV.G16.alloc(LV.G.n); copy_d2bf(LV.G.p, LV.G16.p, LV.G.n, s);
+    if (l > 0) {
+      LV.E16.alloc(LV.E.n); copy_d2bf(LV.E.p, LV.E16.p, LV.E.n, s);
+      LV.F16.alloc(LV.F.n); copy_d2bf(LV.F.p, LV.F16.p, LV.F.n, s);
+    }
+  }
+  has_bf16 = true;
+}
+
 void Hbs::make_fp32(cudaStream_t s) {
   for (int l = 0; l <= L; ++l) {
     Level& LV = lev[l];
@@ -722,20 +734,20 @@ void Hbs::make_fp32(cudaStream_t s) {
 }
 
 // ====================================================================== sweeps
-template <class T>
+template <class T, class MT>
 void Hbs::sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const {
   const int ld = 2 * N;
-  auto Gp = [&](const Level& LV) -> const T* {
-    if constexpr (std::is_same<T, double>::value) return LV.G.p; else return LV.G32.p;
+  // matrices in MT: the FP64 factors, or their FP32 / BF16 copies
+  auto pick = [](const DBuf<double>& d, const DBuf<float>& f, const DBuf<__nv_bfloat16>& h) -> const MT* {
+    if constexpr (std::is_same<MT, double>::value) return d.p;
+    else if constexpr (std::is_same<MT, float>::value) return f.p;
+    else return h.p;
   };
-  auto Ep = [&](const Level& LV) -> const T* {
-    if constexpr (std::is_same<T, double>::value) return LV.E.p; else return LV.E32.p;
-  };
-  auto Fp = [&](const Level& LV) -> const T* {
-    if constexpr (std::is_same<T, double>::value) return LV.F.p; else return LV.F32.p;
-  };
+  auto Gp = [&](const Level& LV) -> const MT* { return pick(LV.G, LV.G32, LV.G16); };
+  auto Ep = [&](const Level& LV) -> const MT* { return pick(LV.E, LV.E32, LV.E16); };
+  auto Fp = [&](const Level& LV) -> const MT* { return pick(LV.F, LV.F32, LV.F16); };
   if (L == 0) {
-    matvec<T>({GemvProb<T>{Gp(lev[0]), b, x, ld, ld, ld, ld, ld, 1.0, 0.0}}, nrhs, s);
+    matvec<T, MT>({GemvProb<T, MT>{Gp(lev[0]), b, x, ld, ld, ld, ld, ld, 1.0, 0.0}}, nrhs, s);
     return;
   }
   // per-level vectors uh (K_l x nrhs) and qh (K_l x nrhs)
@@ -750,64 +762,64 @@ void Hbs::sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const {
     const int l = L, h0 = 1 << l, nn = 1 << l;
     const Level& LV = lev[l];
     const int K = LV.koff.back();
-    std::vector<GemvProb<T>> ps;
+    std::vector<GemvProb<T, MT>> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& nd = node[h0 + t];
       const int n = 2 * (nd.hi - nd.lo), k = nd.k;
       const T* in = b + 2 * nd.lo;
-      ps.push_back(GemvProb<T>{Fp(LV) + LV.oF[t], in, uh[l].p + LV.koff[t], k, n, k, ld, K, 1.0, 0.0});
-      ps.push_back(GemvProb<T>{Gp(LV) + LV.oG[t], in, x + 2 * nd.lo, n, n, n, ld, ld, 1.0, 0.0});
+      ps.push_back(GemvProb<T, MT>{Fp(LV) + LV.oF[t], in, uh[l].p + LV.koff[t], k, n, k, ld, K, 1.0, 0.0});
+      ps.push_back(GemvProb<T, MT>{Gp(LV) + LV.oG[t], in, x + 2 * nd.lo, n, n, n, ld, ld, 1.0, 0.0});
     }
-    matvec<T>(ps, nrhs, s);
+    matvec<T, MT>(ps, nrhs, s);
   }
   for (int l = L - 1; l >= 1; --l) {
     const int h0 = 1 << l, nn = 1 << l;
     const Level& LV = lev[l];
     const Level& LC = lev[l + 1];
     const int K = LV.koff.back(), KC = LC.koff.back();
-    std::vector<GemvProb<T>> ps;
+    std::vector<GemvProb<T, MT>> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& nd = node[h0 + t];
       const int n = nd.m, k = nd.k;
       const T* in = uh[l + 1].p + LC.koff[2 * t];
-      ps.push_back(GemvProb<T>{Fp(LV) + LV.oF[t], in, uh[l].p + LV.koff[t], k, n, k, KC, K, 1.0, 0.0});
-      ps.push_back(GemvProb<T>{Gp(LV) + LV.oG[t], in, qh[l + 1].p + LC.koff[2 * t], n, n, n, KC, KC, 1.0, 0.0});
+      ps.push_back(GemvProb<T, MT>{Fp(LV) + LV.oF[t], in, uh[l].p + LV.koff[t], k, n, k, KC, K, 1.0, 0.0});
+      ps.push_back(GemvProb<T, MT>{Gp(LV) + LV.oG[t], in, qh[l + 1].p + LC.koff[2 * t], n, n, n, KC, KC, 1.0, 0.0});
     }
-    matvec<T>(ps, nrhs, s);
+    matvec<T, MT>(ps, nrhs, s);
   }
   {
     const int K1 = lev[1].koff.back();
-    matvec<T>({GemvProb<T>{Gp(lev[0]), uh[1].p, qh[1].p, K1, K1, K1, K1, K1, 1.0, 0.0}}, nrhs, s);
+    matvec<T, MT>({GemvProb<T, MT>{Gp(lev[0]), uh[1].p, qh[1].p, K1, K1, K1, K1, K1, 1.0, 0.0}}, nrhs, s);
   }
   for (int l = 1; l <= L - 1; ++l) {
     const int h0 = 1 << l, nn = 1 << l;
     const Level& LV = lev[l];
     const Level& LC = lev[l + 1];
     const int K = LV.koff.back(), KC = LC.koff.back();
-    std::vector<GemvProb<T>> ps;
+    std::vector<GemvProb<T, MT>> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& nd = node[h0 + t];
-      ps.push_back(GemvProb<T>{Ep(LV) + LV.oE[t], qh[l].p + LV.koff[t], qh[l + 1].p + LC.koff[2 * t], nd.m, nd.k, nd.m, K, KC, 1.0, 1.0});
+      ps.push_back(GemvProb<T, MT>{Ep(LV) + LV.oE[t], qh[l].p + LV.koff[t], qh[l + 1].p + LC.koff[2 * t], nd.m, nd.k, nd.m, K, KC, 1.0, 1.0});
     }
-    matvec<T>(ps, nrhs, s);
+    matvec<T, MT>(ps, nrhs, s);
   }
   {
     const int l = L, h0 = 1 << l, nn = 1 << l;
     const Level& LV = lev[l];
     const int K = LV.koff.back();
-    std::vector<GemvProb<T>> ps;
+    std::vector<GemvProb<T, MT>> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& nd = node[h0 + t];
       const int n = 2 * (nd.hi - nd.lo);
-      ps.push_back(GemvProb<T>{Ep(LV) + LV.oE[t], qh[l].p + LV.koff[t], x + 2 * nd.lo, n, nd.k, n, K, ld, 1.0, 1.0});
+      ps.push_back(GemvProb<T, MT>{Ep(LV) + LV.oE[t], qh[l].p + LV.koff[t], x + 2 * nd.lo, n, nd.k, n, K, ld, 1.0, 1.0});
     }
-    matvec<T>(ps, nrhs, s);
+    matvec<T, MT>(ps, nrhs, s);
   }
 }
 
 void Hbs::apply_inverse(const double* b, double* x, int nrhs, cudaStream_t s) const {
   if (nrhs <= 8) apply_inverse_program(b, x, nrhs, s);
-  else sweep_inverse<double>(b, x, nrhs, s);
+  else sweep_inverse<double, double>(b, x, nrhs, s);
 }
 
 int Hbs::emit_inverse_sweep(Program& P, int p0, int in_b, long long in_o, int in_ld, int out_b, long long out_o,
@@ -885,7 +897,12 @@ void Hbs::apply_inverse_program(const double* b, double* x, int nrhs, cudaStream
 }
 void Hbs::apply_inverse_f32(const float* b, float* x, int nrhs, cudaStream_t s) const {
   require(has_fp32, "HBS: FP32 copies not built");
-  sweep_inverse<float>(b, x, nrhs, s);
+  sweep_inverse<float, float>(b, x, nrhs, s);
+}
+
+void Hbs::apply_inverse_bf16(const float* b, float* x, int nrhs, cudaStream_t s) const {
+  require(has_bf16, "HBS: BF16 copies not built");
+  sweep_inverse<float, __nv_bfloat16>(b, x, nrhs, s);
 }
 
 void Hbs::apply_forward(const double* xin, double* y, int nrhs, cudaStream_t s) const {

@@ -95,6 +95,7 @@ class Hbs {
     std::vector<size_t> oU, oVt, oE, oF, oG, oB12, oB21, oD;
     std::vector<int> koff;  // prefix sums of ranks at this level (size nn+1)
     DBuf<float> G32, E32, F32;
+    DBuf<__nv_bfloat16> G16, E16, F16;  // BF16 copies (preconditioner sweeps)
   };
   std::vector<Level> lev;
   long long inv_elems = 0, fwd_elems = 0;
@@ -115,10 +116,13 @@ class Hbs {
     sweep_inverse<double>(b, x, nrhs, s);
   }
   void apply_inverse_f32(const float* b, float* x, int nrhs, cudaStream_t s) const;
+  // BF16 matrices, FP32 vectors and accumulation (make_bf16 first)
+  void apply_inverse_bf16(const float* b, float* x, int nrhs, cudaStream_t s) const;
   // y = A x via the forward representation.
   void apply_forward(const double* x, double* y, int nrhs, cudaStream_t s) const;
   void make_fp32(cudaStream_t s);
-  bool has_fp32 = false;
+  void make_bf16(cudaStream_t s);
+  bool has_fp32 = false, has_bf16 = false;
   // Add the inverse sweep x = A^{-1} b to a program, starting at phase p0
   // (input and output addressed as program vectors); returns the next phase.
   int emit_inverse_sweep(Program& P, int p0, int in_b, long long in_o, int in_ld, int out_b, long long out_o,
@@ -131,7 +135,7 @@ class Hbs {
   mutable DBuf<double> prog_ws;
 
  private:
-  template <class T>
+  template <class T, class MT = T>
   void sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const;
 };
 

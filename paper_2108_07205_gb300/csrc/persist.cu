@@ -138,6 +138,7 @@ void load_wall(rw::Wall& w, Reader& in, cudaStream_t s) {
   in.raw(tag, sizeof(tag));
   rw::require(std::memcmp(tag, kTag, sizeof(tag)) == 0, "rw_hbs_load: corrupt trailer");
   H.make_fp32(s);
+  H.make_bf16(s);
   RW_CUDA(cudaStreamSynchronize(s));
 }
 

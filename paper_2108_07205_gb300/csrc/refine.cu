@@ -248,6 +248,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       if (pp_dense) opp.leaf_points = Np;
       hpp.build(pn, opp, s1);
       hpp.make_fp32(s1);
+      hpp.make_bf16(s1);
       RW_CUDA(cudaStreamSynchronize(s1));
     } catch (...) { e1 = std::current_exception(); }
   };

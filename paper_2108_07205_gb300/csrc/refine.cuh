@@ -97,8 +97,10 @@ struct Refinement {
   // Woodbury apply in ext space: (yo, yp) <- Ainv_ext (yo, yp), yo/yp hold
   // A~^{-1} g on entry (ld 2No / 2Np).
   void woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t s) const;
-  // FGMRES on A~ + L R with the FP32-sweep Woodbury preconditioner.
-  void solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres) const;
+  // FGMRES on A~ + L R with the Woodbury preconditioner, its HBS sweeps in
+  // FP32 (or with BF16 matrices when bf16 is set).
+  void solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres,
+                   bool bf16 = false) const;
   // ext-space operator y = (A~ + L R) x (FP64)
   void apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
   ~Refinement();

@@ -19,7 +19,7 @@ RW_OK = 0
 ERRORS = {-1: "RW_ERR_INVALID", -2: "RW_ERR_OOM", -3: "RW_ERR_SINGULAR",
           -4: "RW_ERR_NOT_CONVERGED", -5: "RW_ERR_TIMEOUT", -6: "RW_ERR_CUDA"}
 CURVE_STAR, CURVE_CHANNEL, CURVE_NODES = 0, 1, 2
-MODE_DIRECT, MODE_GMRES_FP32, MODE_DIRECT_REFINED = 0, 1, 2
+MODE_DIRECT, MODE_GMRES_FP32, MODE_DIRECT_REFINED, MODE_GMRES_BF16 = 0, 1, 2, 3
 
 
 class RWError(RuntimeError):

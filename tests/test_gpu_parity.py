@@ -9,7 +9,8 @@ Tolerances (relative 2-norm unless stated), from the arithmetic:
   kappa(A_nn) ~ 5e2, measured 1.7e-10);
 * mixed path (FP32 sweeps inside FP64 FGMRES): ELS residual <= 1e-10 and
   density within 1e-9 of the oracle (the ELS operator itself carries the
-  1e-12 compression);
+  1e-12 compression); the same with BF16 sweep matrices on the star wall,
+  in more iterations than FP32;
 * full-size channel (32768 unknowns): residual of the exact refined operator
   on 64 sampled rows computed one by one by the oracle, <= 1e-8 relative to
   max |g| (kappa(A) ~ 1e6 on this wall), and the interior velocity against the
@@ -139,6 +140,23 @@ def test_mixed_gmres_fp32(star64):
     assert info["rel_residual"] <= 1e-10
     assert 1 <= info["iters"] <= 10
     assert rel(tau, DN.solve_refined(o, g_or.T).T) < 1e-9
+    ref.close()
+
+
+def test_mixed_gmres_bf16(star64):
+    # BF16 matrices in the preconditioner's sweeps (FP32 vectors and sums):
+    # on this wall (kappa ~ 4e2) the preconditioned operator stays within
+    # ~5e-2 of the identity, so FGMRES still reaches 1e-10, in more iterations
+    panels, levels = inputs.refinement_window(0, 64, 4, 3, 3)
+    ref = star64.refine(panels, levels)
+    o = D.refine("star", STAR, 64, panels, levels)
+    g, g_or, _ = data(ref, o, 1, 4)
+    tau32, tau16 = np.empty_like(g), np.empty_like(g)
+    i32 = ref.solve(g, tau32, nrhs=4, mode=rwsolve.MODE_GMRES_FP32)
+    i16 = ref.solve(g, tau16, nrhs=4, mode=rwsolve.MODE_GMRES_BF16)
+    assert i16["rel_residual"] <= 1e-10
+    assert i32["iters"] < i16["iters"] <= 30
+    assert rel(tau16, DN.solve_refined(o, g_or.T).T) < 1e-9
     ref.close()
 
 
