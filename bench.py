@@ -633,7 +633,7 @@ def main():
         run_reference(args, rank, world)
         return
     out = run_ours(args, rank, world, local)
-    if rank != 0:
+    if rank != 0 or out is None:
         return
     peaks = {}
     try:
