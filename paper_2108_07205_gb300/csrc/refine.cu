@@ -90,18 +90,19 @@ void recompress_rows(const NodesView& S, std::vector<int>& J, const IdMatProb& c
 
 SideStreams::~SideStreams() {
   // every buffer of the refinement has been released (stream ordered) by now
-  for (cudaStream_t t : {s1, s2}) if (t) { cudaStreamSynchronize(t); cudaStreamDestroy(t); }
+  for (cudaStream_t t : {s1, s2, s3}) if (t) { cudaStreamSynchronize(t); cudaStreamDestroy(t); }
 }
 
 Refinement::~Refinement() {
   // order the frees on the side streams after all work queued on the main
   // stream (the members are released after this body, the streams last)
-  if (streams.main && (streams.s1 || streams.s2)) {
+  if (streams.main && (streams.s1 || streams.s2 || streams.s3)) {
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
       cudaEventRecord(ev, streams.main);
       if (streams.s1) cudaStreamWaitEvent(streams.s1, ev, 0);
       if (streams.s2) cudaStreamWaitEvent(streams.s2, ev, 0);
+      if (streams.s3) cudaStreamWaitEvent(streams.s3, ev, 0);
       cudaEventDestroy(ev);
     }
   }
@@ -224,7 +225,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   // single-leaf HBS is the dense inverse), the far-field ID and the near and
   // A_pk IDs run concurrently on three streams driven by three host threads.
   const NodesView VW = w.nodes.view(), VP = pn.view();
-  TreeId tf, tn, tp;
+  TreeId tf, tn;
   DBuf<int> dall_p, dnear;
   {
     std::vector<int> pd(2 * Np);
@@ -235,9 +236,12 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   }
   RW_CUDA(cudaStreamCreateWithFlags(&streams.s1, cudaStreamNonBlocking));
   RW_CUDA(cudaStreamCreateWithFlags(&streams.s2, cudaStreamNonBlocking));
-  cudaStream_t s1 = streams.s1, s2 = streams.s2;
-  std::exception_ptr e1, e2;
-  // RW_SERIAL_REFINE=1 (diagnostics): run the three tasks one after another
+  RW_CUDA(cudaStreamCreateWithFlags(&streams.s3, cudaStreamNonBlocking));
+  cudaStream_t s1 = streams.s1, s2 = streams.s2, s3 = streams.s3;
+  std::exception_ptr e1, e2, e3;
+  const bool recompress = recompress_enabled();
+  const double rtol = 0.1 * o.id_tol;  // recompression tolerance (see recompress_rows)
+  // RW_SERIAL_REFINE=1 (diagnostics): run the four tasks one after another
   const char* ser = std::getenv("RW_SERIAL_REFINE");
   const bool serial = ser && ser[0] == '1';
   auto task1 = [&] {
@@ -261,93 +265,105 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
     } catch (...) { e2 = std::current_exception(); }
   };
-  std::thread th1, th2;
+  // A_pk: rows of [A_{p,div} | A_pk^near | n_p], then (recompression) a row
+  // ID of R_pk = A(J_pk, I_k); needs neither the far nor the near ID
+  std::vector<int> Jpk;
+  auto task3 = [&] {
+    AllocStreamScope scope3(s3);
+    try {
+      std::vector<int> prow(2 * Np);
+      for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
+      IdMatProb cs{};
+      cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
+      TreeId tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s3);
+      kpk = kpk_id = tp.k;
+      Lp = std::move(tp.P);
+      for (int i : tp.skel) Jpk.push_back(i);
+      if (recompress) {
+        std::vector<int> kd;
+        for (int i : Ik) { kd.push_back(2 * i); kd.push_back(2 * i + 1); }
+        auto dkd = to_device_tmp(kd, s3);
+        IdMatProb cp{};
+        cp.n1 = int(kd.size()); cp.e1 = dkd.p;
+        recompress_rows(VP, Jpk, cp, VW, false, VW, false, Lp, 2 * Np, kpk, rtol, o.seed + 505, s3);
+      }
+      // R_pk = A(J_pk, I_o) with the cut columns zeroed
+      auto dJpk = to_device_tmp(Jpk, s3);
+      Rpk.alloc(std::max<size_t>(size_t(kpk) * 2 * No, 1));
+      eval_blocks({BlockProb{kpk, 2 * No, dJpk.p, nullptr, 0, 0, 1, 0, 1.0, Rpk.p, kpk}}, VW, VP, s3);
+      if (kpk) {
+        k_zero_cols<<<ceil_div((long long)kpk * 2 * Nc, 256), 256, 0, s3>>>(Rpk.p, kpk, kpk, dc.p, 2 * Nc);
+        RW_CHECK_LAUNCH();
+      }
+      RW_CUDA(cudaStreamSynchronize(s3));
+    } catch (...) { e3 = std::current_exception(); }
+  };
+  std::thread th1, th2, th3;
   // every exit from here on (including a throw) waits for the side threads
   struct Joiner {
     std::thread& t;
     ~Joiner() { if (t.joinable()) t.join(); }
-  } join1{th1}, join2{th2};
+  } join1{th1}, join2{th2}, join3{th3};
   if (serial) {
     task1();
     tr.mark("  A_pp inverse (HBS)");
     task2();
     tr.mark("  far ID");
+    task3();
+    tr.mark("  A_pk ID (+ recompression)");
   } else {
     th1 = std::thread(task1);
     th2 = std::thread(task2);
+    th3 = std::thread(task3);
   }
   std::exception_ptr e0;
   try {
     // near rows of I_k: [A_kc^near | A_kp^near]
-    {
-      IdMatProb cs{};
-      cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
-      tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
-    }
-    // A_pk: rows of [A_{p,div} | A_pk^near | n_p]
-    {
-      std::vector<int> prow(2 * Np);
-      for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
-      IdMatProb cs{};
-      cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
-      tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s);
-    }
+    IdMatProb cs{};
+    cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
+    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
   } catch (...) { e0 = std::current_exception(); }
-  if (serial) tr.mark("  near + A_pk IDs");
+  if (serial) tr.mark("  near ID");
   // X_o = A_oo^{-1} L_o needs only the far and near IDs: it runs on the main
   // stream while A_pp^{-1} may still be in construction on its own stream
   if (th2.joinable()) th2.join();
   RW_CUDA(cudaStreamSynchronize(s2));
   for (auto& e : {e0, e2}) if (e) std::rethrow_exception(e);
   tr.mark("IDs (concurrent with A_pp)");
-  kf = tf.k; kn = tn.k; kpk = tp.k; kk = kf + kn; k = kk + kpk;
-  kpk_id = kpk;
+  kf = tf.k; kn = tn.k; kk = kf + kn;
 
-  // L_o (2No x kk) and L_p (2Np x kpk)
+  // L_o (2No x kk)
   Lo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
   Lo.zero(s);
   {
     auto dfar = to_device_tmp(far_d, s);
     if (kf) gather_scatter(tf.P.p, int(far_d.size()), nullptr, Lo.p, 2 * No, dfar.p, int(far_d.size()), kf, s);
     if (kn) gather_scatter(tn.P.p, int(near_d.size()), nullptr, Lo.p + size_t(2) * No * kf, 2 * No, dnear.p, int(near_d.size()), kn, s);
-    Lp = std::move(tp.P);
     RW_CUDA(cudaStreamSynchronize(s));
   }
   // skeleton DOFs
-  std::vector<int> Jk, Jpk;
+  std::vector<int> Jk;
   for (int i : tf.skel) Jk.push_back(far_d[i]);
   for (int i : tn.skel) Jk.push_back(near_d[i]);
-  for (int i : tp.skel) Jpk.push_back(i);
-  if (recompress_enabled()) {
-    // row IDs of R_k = [A(J_k, I_c), A(J_k, I_p)] and R_pk = A(J_pk, I_k)
-    const double rtol = 0.1 * o.id_tol;
+  if (recompress) {
+    // row ID of R_k = [A(J_k, I_c), A(J_k, I_p)]
     IdMatProb ck{};
     ck.n1 = 2 * Nc; ck.e1 = dc.p; ck.n2 = 2 * Np; ck.e2 = dall_p.p;
     recompress_rows(VW, Jk, ck, VW, true, VP, false, Lo, 2 * No, kk, rtol, o.seed + 404, s);
-    std::vector<int> kd;
-    for (int i : Ik) { kd.push_back(2 * i); kd.push_back(2 * i + 1); }
-    auto dkd = to_device_tmp(kd, s);
-    IdMatProb cp{};
-    cp.n1 = int(kd.size()); cp.e1 = dkd.p;
-    recompress_rows(VP, Jpk, cp, VW, false, VW, false, Lp, 2 * Np, kpk, rtol, o.seed + 505, s);
-    k = kk + kpk;
-    tr.mark("recompression");
+    tr.mark("recompression (wall rows)");
   }
+  if (th3.joinable()) th3.join();
+  if (e3) std::rethrow_exception(e3);
+  k = kk + kpk;
   // a5 (o part): X_o = A_oo^{-1} L_o
   Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
   if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
-  auto dJk = to_device_tmp(Jk, s), dJpk = to_device_tmp(Jpk, s);
+  auto dJk = to_device_tmp(Jk, s);
   Rkc.alloc(std::max<size_t>(size_t(kk) * 2 * Nc, 1));
   Rkp.alloc(std::max<size_t>(size_t(kk) * 2 * Np, 1));
-  Rpk.alloc(std::max<size_t>(size_t(kpk) * 2 * No, 1));
   eval_blocks({BlockProb{kk, 2 * Nc, dJk.p, dc.p, 0, 0, 0, 0, -1.0, Rkc.p, kk},
-               BlockProb{kk, 2 * Np, dJk.p, nullptr, 0, 0, 0, 1, 1.0, Rkp.p, kk},
-               BlockProb{kpk, 2 * No, dJpk.p, nullptr, 0, 0, 1, 0, 1.0, Rpk.p, kpk}},
+               BlockProb{kk, 2 * Np, dJk.p, nullptr, 0, 0, 0, 1, 1.0, Rkp.p, kk}},
               VW, VP, s);
-  if (kpk) {
-    k_zero_cols<<<ceil_div((long long)kpk * 2 * Nc, 256), 256, 0, s>>>(Rpk.p, kpk, kpk, dc.p, 2 * Nc);
-    RW_CHECK_LAUNCH();
-  }
   tr.mark("L, R assembly, X_o");
   // a5 (p part): X_p = A_pp^{-1} L_p once A_pp^{-1} is built
   if (th1.joinable()) th1.join();

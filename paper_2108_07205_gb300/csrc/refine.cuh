@@ -16,7 +16,7 @@ struct Wall {
 // Side streams of one refinement: created by factor(), destroyed last (after
 // every buffer allocated on them has been released).
 struct SideStreams {
-  cudaStream_t main = nullptr, s1 = nullptr, s2 = nullptr;
+  cudaStream_t main = nullptr, s1 = nullptr, s2 = nullptr, s3 = nullptr;
   ~SideStreams();
 };
 
