@@ -1541,6 +1541,35 @@ void matvec<float, __nv_bfloat16>(const std::vector<GemvProb<float, __nv_bfloat1
   matvec_f32(probs, nrhs, s);
 }
 
+void block_inverse(const double* A, double* Ainv, int n, int nb, int* flag, cudaStream_t s) {
+  require(n >= 1 && nb >= 1, "block_inverse: bad size");
+  nb = std::min(nb, n);
+  double* M = Ainv;  // worked on in place
+  RW_CUDA(cudaMemcpyAsync(M, A, sizeof(double) * size_t(n) * n, cudaMemcpyDeviceToDevice, s));
+  TBuf<double> C(size_t(n) * nb, s), T(size_t(nb) * n, s), P(size_t(nb) * nb, s), Wk(size_t(nb) * nb, s);
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int b = std::min(nb, n - j0), j1 = j0 + b;
+    // C = M[:, J]; P = M[J, J]^{-1}
+    RW_CUDA(cudaMemcpyAsync(C.p, M + size_t(j0) * n, sizeof(double) * size_t(n) * b, cudaMemcpyDeviceToDevice, s));
+    batched_inverse({InvProb{C.p + j0, P.p, Wk.p, b, n, b, flag}}, s);
+    // T = P M[J, :], with T[:, J] = P; then M[J, :] = T
+    batched_gemm({GemmProb{P.p, M + j0, T.p, b, n, b, b, n, b, 0, 0, 1.0, 0.0}}, s);
+    RW_CUDA(cudaMemcpy2DAsync(T.p + size_t(j0) * b, sizeof(double) * b, P.p, sizeof(double) * b,
+                              sizeof(double) * b, b, cudaMemcpyDeviceToDevice, s));
+    RW_CUDA(cudaMemcpy2DAsync(M + j0, sizeof(double) * n, T.p, sizeof(double) * b, sizeof(double) * b, n,
+                              cudaMemcpyDeviceToDevice, s));
+    // other rows: M[I, J] = 0, then M[I, :] -= C[I, :] T (so M[I, J] = -C[I] P)
+    if (j0 > 0)
+      RW_CUDA(cudaMemset2DAsync(M + size_t(j0) * n, sizeof(double) * n, 0, sizeof(double) * j0, b, s));
+    if (j1 < n)
+      RW_CUDA(cudaMemset2DAsync(M + j1 + size_t(j0) * n, sizeof(double) * n, 0, sizeof(double) * (n - j1), b, s));
+    std::vector<GemmProb> g;
+    if (j0 > 0) g.push_back(GemmProb{C.p, T.p, M, j0, n, b, n, b, n, 0, 0, -1.0, 1.0});
+    if (j1 < n) g.push_back(GemmProb{C.p + j1, T.p, M + j1, n - j1, n, b, n, b, n, 0, 0, -1.0, 1.0});
+    batched_gemm(g, s);
+  }
+}
+
 void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s) {
   // small matrices: one CTA each; larger: a cluster of up to 8 CTAs with the
   // columns in shared memory when they fit, else in place in global memory

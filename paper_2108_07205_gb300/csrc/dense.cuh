@@ -71,6 +71,15 @@ struct InvProb {
 };
 void batched_inverse(const std::vector<InvProb>& probs, cudaStream_t s);
 
+// Inverse of one large square matrix (n x n, column major, ld n) by block
+// Gauss-Jordan elimination: for each diagonal block of at most nb rows, its
+// inverse (Gauss-Jordan with partial pivoting inside the block) scales the
+// block row and GEMMs eliminate the block column from every other row.  No
+// pivoting across blocks: meant for matrices whose diagonal blocks and their
+// Schur complements stay well conditioned (second-kind operators such as the
+// dense hole matrix).  A is not modified; flag is set if a pivot is tiny.
+void block_inverse(const double* A, double* Ainv, int n, int nb, int* flag, cudaStream_t s);
+
 // Interpolative decomposition on the columns of W (the rows of Y = W^T) by
 // column-pivoted Householder QR (Def. 3.1): W (nr x nc) is overwritten;
 // stop when the largest remaining column norm is <= max(tol_abs,

@@ -680,6 +680,10 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
   }
 }
 
+// dense single-leaf inverses above this size use block Gauss-Jordan with
+// diagonal blocks of kBlockInverseNb rows (each inverted in shared memory)
+constexpr int kBlockInverseMin = 512, kBlockInverseNb = 320;
+
 void Hbs::build_dense(DBuf<double>&& A, int npts, cudaStream_t s) {
   N = npts;
   require(N >= 1, "HBS: empty node set");
@@ -696,11 +700,16 @@ void Hbs::build_dense(DBuf<double>&& A, int npts, cudaStream_t s) {
   LV.oD = {0};
   LV.oG = {0};
   LV.G.alloc(size_t(n) * n);
-  TBuf<double> Dt(size_t(n) * n, s), Wk(size_t(n) * n, s);
-  batched_copy({CopyProb{LV.D.p, n, n, n, Dt.p, n}}, s);
   DBuf<int> flag(1);
   flag.zero(s);
-  batched_inverse({InvProb{Dt.p, LV.G.p, Wk.p, n, n, n, flag.p}}, s);
+  if (n > kBlockInverseMin) {
+    // beyond one shared-memory cluster: block Gauss-Jordan on GEMMs
+    block_inverse(LV.D.p, LV.G.p, n, kBlockInverseNb, flag.p, s);
+  } else {
+    TBuf<double> Dt(size_t(n) * n, s), Wk(size_t(n) * n, s);
+    batched_copy({CopyProb{LV.D.p, n, n, n, Dt.p, n}}, s);
+    batched_inverse({InvProb{Dt.p, LV.G.p, Wk.p, n, n, n, flag.p}}, s);
+  }
   const auto hf = flag.download(s);
   require(hf[0] == 0, "HBS inverse: singular dense block", RW_ERR_SINGULAR);
   max_rank = 0;
