@@ -4,7 +4,8 @@ The tuning switches change only how the same factorisations are scheduled:
 - the cluster-only QR instead of the grid-wide one;
 - other Gauss-Jordan cluster sizes and smallest QR clusters;
 - a deep binary far-field tree (64-row chunks, pairwise merges to the top);
-- no L2 prefetch in the solve program.
+- no L2 prefetch in the solve program;
+- no recompression (the blockwise ranks kept).
 
 Each configuration must still meet the FP64 parity bar against the oracle's
 dense LU solve of the refined system: 1e-10 relative with one refinement
@@ -70,6 +71,7 @@ def tau_oracle():
     {"RW_ID_CS_MIN": "8"},
     {"RW_TREE_CHUNK": "64", "RW_ROOT_MERGE": "2"},
     {"RW_PROG_PREFETCH": "0"},
+    {"RW_RECOMPRESS": "0"},
 ], ids=lambda e: ",".join(f"{k}={v}" for k, v in e.items()) or "default")
 def test_route_matches_oracle(tau_oracle, env, tmp_path):
     out = tmp_path / "tau.npy"
