@@ -14,7 +14,8 @@ Tolerances (relative 2-norm unless stated), from the arithmetic:
 * full-size channel (32768 unknowns): residual of the exact refined operator
   on 64 sampled rows computed one by one by the oracle, <= 1e-8 relative to
   max |g| (kappa(A) ~ 1e6 on this wall), and the interior velocity against the
-  closed-form Stokeslet field <= 1e-8.
+  closed-form Stokeslet field <= 1e-8; the same bars on the 2048-panel
+  channel (65536 unknowns) with 64 right-hand sides, direct and FGMRES.
 """
 import numpy as np
 import pytest
@@ -235,5 +236,44 @@ def test_channel_full_size(lib, level):
     tau2 = np.empty_like(g)
     info = ref.solve(g, tau2, mode=rwsolve.MODE_GMRES_FP32)
     assert info["rel_residual"] <= 1e-10
+    ref.close()
+    w.close()
+
+
+def test_mixed_config_full_size(lib):
+    # the 2048-panel channel (65536 unknowns) with 64 right-hand sides, one
+    # Stokeslet pair each, as the mixed-precision workload runs it: the direct
+    # solve (level-by-level GEMM sweeps) and FP32-preconditioned FGMRES, both
+    # checked on 24 rows of the exact refined operator written out by the
+    # oracle, for every right-hand side, and on the closed-form velocity
+    nrhs = 64
+    w = rwsolve.Wall("channel", 2048)
+    panels, levels = inputs.time_schedule(11, 2048, 1, level_lo=4, level_hi=4)[0]
+    ref = w.refine(panels, levels)
+    o = D.refine("channel", {}, 2048, panels, levels)
+    sx, sy, f = inputs.stokeslet_pairs_channel(5, nrhs)
+    g = np.empty((nrhs, 2 * ref.stats()["n_n"]))
+    ref.stokeslet_data(np.ascontiguousarray(np.stack([sx, sy], 1)),
+                       np.ascontiguousarray(np.transpose(f, (2, 0, 1))), g, nrhs=nrhs)
+    rows = inputs.rng(21).choice(g.shape[1], 24, replace=False)
+    # the oracle's data at the sampled rows only (every node x 128 sources x
+    # 64 right-hand sides would not fit a test's memory)
+    pts = rows // 2
+    ur = S.stokeslet_velocity(o["n"]["x"][pts], o["n"]["y"][pts], sx, sy, f)   # (24, 2, nrhs)
+    gr = ur[np.arange(rows.size), rows % 2, :]                                 # (24, nrhs)
+    gmax = np.abs(g).max()
+    assert np.abs(gr.T - g[:, rows]).max() <= 1e-13 * gmax
+    tx, ty = inputs.targets_channel(4, 8)
+    ue = S.stokeslet_velocity(tx, ty, sx, sy, f)                     # (nt, 2, nrhs)
+    for mode in (rwsolve.MODE_DIRECT, rwsolve.MODE_GMRES_FP32):
+        tau = np.empty_like(g)
+        u = np.empty((nrhs, 2 * tx.size))
+        info = ref.solve(g, tau, nrhs=nrhs, targets=np.ascontiguousarray(np.stack([tx, ty], 1)), u=u, mode=mode)
+        res = S.apply_rows(o["n"], tau.T, rows) - gr
+        assert np.abs(res).max() <= 1e-8 * gmax, mode
+        uu = u.reshape(nrhs, -1, 2).transpose(1, 2, 0)
+        assert np.abs(uu - ue).max() <= 1e-8 * np.abs(ue).max(), mode
+        if mode == rwsolve.MODE_GMRES_FP32:
+            assert info["rel_residual"] <= 1e-10
     ref.close()
     w.close()
