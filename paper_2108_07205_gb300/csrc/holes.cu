@@ -27,7 +27,6 @@ namespace rw {
 void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cudaStream_t s) {
   wall = &w;
   holes = true;
-  hole_specs = hs;
   streams.main = s;
   AllocStreamScope alloc_scope(s);
   Trace tr(s, "holes");

@@ -45,7 +45,6 @@ struct Refinement {
   SideStreams streams;  // first member: destroyed last
   const Wall* wall = nullptr;
   bool holes = false;                  // App. B: holes added, nothing cut
-  std::vector<HoleSpec> hole_specs;
   std::vector<int> panels, levels;     // cut panels (window order) and levels
   int No = 0, Nk = 0, Nc = 0, Np = 0, Nn = 0;
   std::vector<int> Ic, Ik;             // point indices into the wall
