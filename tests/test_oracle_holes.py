@@ -162,3 +162,24 @@ def test_apply_rows_matches_dense_system():
                            2 * wall["x"].size + I.rng(7).choice(2 * hn["x"].size, 7, replace=False)])
     got = H.apply_rows(wall, hn, hl, x, rows)
     assert np.abs(got - (A @ x)[rows]).max() < 1e-13 * np.abs(A @ x).max()
+
+
+@pytest.mark.parametrize("kind", ["channel", "star"])
+def test_seeded_hole_layouts_are_valid(kind):
+    # every seeded layout keeps its holes inside the wall, at least one hole
+    # radius away from it, and apart from one another (the input recipe)
+    from oracle.curves import evaluate
+    t = np.linspace(0.0, 2.0 * np.pi, 20001)
+    wall = evaluate("channel", t) if kind == "channel" else evaluate("star", t, a=0.3, k=5)
+    for seed in range(20):
+        hl = I.holes_channel(seed) if kind == "channel" else I.holes_star(seed)
+        for i, h in enumerate(hl):
+            d = np.hypot(wall["x"] - h["cx"], wall["y"] - h["cy"]).min()
+            assert d >= 2.0 * h["R"], (seed, i, d)
+            # inside: a ray to the right from the centre crosses the wall an odd number of times
+            ys = wall["y"] - h["cy"]
+            cross = (np.sign(ys[:-1]) != np.sign(ys[1:])) & (wall["x"][:-1] > h["cx"])
+            assert cross.sum() % 2 == 1, (seed, i)
+            for j in range(i):
+                g = hl[j]
+                assert np.hypot(h["cx"] - g["cx"], h["cy"] - g["cy"]) > 3.0 * max(h["R"], g["R"])
