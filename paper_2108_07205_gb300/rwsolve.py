@@ -331,7 +331,11 @@ class Wall:
 
 
 class Refinement:
-    """Algorithm 1 pre-computation for one local refinement of a Wall."""
+    """Algorithm 1 pre-computation for one modification of a Wall: a local
+    refinement (cut panels split into sub-panels, Sec. 3.1) or, through
+    Wall.add_holes, holes added inside the wall (App. B).  Both give the same
+    handle: solve (MODE_DIRECT, MODE_DIRECT_REFINED, MODE_GMRES_FP32,
+    MODE_GMRES_BF16), apply_refined, stokeslet_data, pressure, nodes, Batch."""
 
     def __init__(self, wall, panels, levels, stream=None, added=None, holes=None):
         L = load()
@@ -379,8 +383,8 @@ class Refinement:
         return g
 
     def pressure(self, tau, targets, p, nrhs=1, stream=None):
-        """p = pressure of the double-layer velocity of tau at targets (nt, 2);
-        p: (nrhs, nt)."""
+        """p = pressure of the velocity represented by tau (the double layer;
+        for holes also their single layer) at targets (nt, 2); p: (nrhs, nt)."""
         nt = targets.shape[0] if hasattr(targets, "shape") else len(targets) // 2
         _check(load().rw_pressure(self.h, nrhs, _ptr(tau), nt, _ptr(targets), _ptr(p, True), _stream(stream)))
         return p
