@@ -345,7 +345,6 @@ TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdM
     const bool bottom = (lv - 1 == 0);
     if (!bottom) Wm[lv - 1].alloc(std::max<size_t>(sz, 1));
     std::vector<GemmProb> gm;
-    size_t poff_in_parent = 0;
     std::vector<size_t> wpar(par.size());
     { size_t o = 0; for (size_t b = 0; b < par.size(); ++b) { wpar[b] = o; o += par[b].cand.size() * size_t(out.k); } }
     for (size_t pb = 0; pb < par.size(); ++pb) {
@@ -362,7 +361,6 @@ TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdM
         slice += c.k;
       }
     }
-    (void)poff_in_parent;
     batched_gemm(gm, s);
   }
   if (top == 0) {
@@ -417,6 +415,164 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
   max_rank = 0;
   bytes = 0;
 
+  // ---------------------------------------------------------- leaf D blocks
+  {
+    Level& LL = lev[L];
+    const int nl = 1 << L;
+    LL.oD.resize(nl);
+    size_t sd = 0;
+    for (int t = 0; t < nl; ++t) { const HbsNode& nd = node[nl + t]; LL.oD[t] = sd; sd += size_t(4) * (nd.hi - nd.lo) * (nd.hi - nd.lo); }
+    LL.D.alloc(sd);
+    std::vector<BlockProb> bp;
+    for (int t = 0; t < nl; ++t) {
+      const HbsNode& nd = node[nl + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      bp.push_back(BlockProb{n, n, nullptr, nullptr, 2 * nd.lo, 2 * nd.lo, 0, 0, 1.0, LL.D.p + LL.oD[t], n});
+    }
+    eval_blocks(bp, V, V, s);
+  }
+  // ---------------------------------------------------------- inverse (pipelined)
+  // Per node: D~ (leaf: D; parent: [Dh_a B12; B21 Dh_b]); Dinv = D~^{-1};
+  // Dh = (V* Dinv U)^{-1}; E = Dinv U Dh; F* = Dh V* Dinv; G = Dinv - E V* Dinv.
+  // Level l needs its own U, V* (compression of level l), its B blocks (the
+  // skeletons of level l + 1) and the children's Dh (inverse of level l + 1):
+  // it runs on its own stream as soon as level l is compressed, while the
+  // host goes on compressing level l - 1.  Buffers that outlive the build are
+  // allocated on the build's stream and handed over through an event; the
+  // inverse's temporaries (the children's Dh included) live on its stream.
+  // declaration order = reverse destruction order: on any exit the inverse
+  // stream is synchronised (done) after its own temporaries are released and
+  // before anything it reads (flags, index lists) is
+  DBuf<int> flags(size_t(2) << L);
+  flags.zero(s);
+  std::vector<DBuf<int>> keep_idx;  // B-block index lists, alive until the inverse stream is done
+  cudaStream_t si = nullptr;
+  cudaEvent_t ev_alloc = nullptr;
+  struct StreamDone {
+    cudaStream_t& st;
+    cudaEvent_t& ev;
+    ~StreamDone() {
+      if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+      if (ev) cudaEventDestroy(ev);
+    }
+  } done{si, ev_alloc};
+  RW_CUDA(cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking));
+  RW_CUDA(cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming));
+  TBuf<double> Dh_prev;  // Dh of the level below (children), offsets koff^2, on si
+  std::vector<size_t> oDh_prev;
+  auto order_after_alloc = [&] {
+    RW_CUDA(cudaEventRecord(ev_alloc, s));
+    RW_CUDA(cudaStreamWaitEvent(si, ev_alloc, 0));
+  };
+  auto invert_level = [&](int l) {
+    const int h0 = 1 << l, nn = 1 << l;
+    Level& LV = lev[l];
+    if (l < L) {
+      // B blocks between the children of every node of level l
+      LV.oB12.resize(nn); LV.oB21.resize(nn);
+      size_t sb = 0;
+      std::vector<int> idx;
+      std::vector<size_t> pos;
+      for (int t = 0; t < nn; ++t) {
+        const HbsNode& a = node[2 * (h0 + t)];
+        const HbsNode& b = node[2 * (h0 + t) + 1];
+        LV.oB12[t] = sb; sb += size_t(a.k) * b.k;
+        LV.oB21[t] = sb; sb += size_t(b.k) * a.k;
+        for (const std::vector<int>* v : {&a.skr, &b.skc, &b.skr, &a.skc}) { pos.push_back(idx.size()); idx.insert(idx.end(), v->begin(), v->end()); }
+      }
+      LV.B.alloc(std::max<size_t>(sb, 1));
+      keep_idx.push_back(to_device(idx, s));
+      order_after_alloc();
+      const int* di = keep_idx.back().p;
+      std::vector<BlockProb> bp;
+      for (int t = 0; t < nn; ++t) {
+        const HbsNode& a = node[2 * (h0 + t)];
+        const HbsNode& b = node[2 * (h0 + t) + 1];
+        bp.push_back(BlockProb{a.k, b.k, di + pos[4 * t], di + pos[4 * t + 1], 0, 0, 0, 0, 1.0, LV.B.p + LV.oB12[t], a.k});
+        bp.push_back(BlockProb{b.k, a.k, di + pos[4 * t + 2], di + pos[4 * t + 3], 0, 0, 0, 0, 1.0, LV.B.p + LV.oB21[t], b.k});
+      }
+      eval_blocks(bp, V, V, si);
+    } else {
+      order_after_alloc();  // the leaf D blocks and this level's U, V*
+    }
+    std::vector<int> mm(nn);
+    size_t sG = 0;
+    LV.oG.resize(nn);
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      mm[t] = (l == L) ? 2 * (nd.hi - nd.lo) : node[2 * (h0 + t)].k + node[2 * (h0 + t) + 1].k;
+      if (l > 0) require(mm[t] == nd.m, "HBS: inconsistent candidate count");
+      LV.oG[t] = sG;
+      sG += size_t(mm[t]) * mm[t];
+    }
+    LV.G.alloc(sG);
+    order_after_alloc();
+    TBuf<double> Dt(sG, si), Wk(sG, si);
+    // assemble D~
+    std::vector<CopyProb> cp;
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t];
+      double* dst = Dt.p + LV.oG[t];
+      if (l == L) {
+        cp.push_back(CopyProb{LV.D.p + LV.oD[t], n, n, n, dst, n});
+      } else {
+        const HbsNode& a = node[2 * (h0 + t)];
+        const HbsNode& b = node[2 * (h0 + t) + 1];
+        const int ca = 2 * t, cb = 2 * t + 1;  // child positions in the level below
+        cp.push_back(CopyProb{Dh_prev.p + oDh_prev[ca], a.k, a.k, a.k, dst, n});
+        cp.push_back(CopyProb{Dh_prev.p + oDh_prev[cb], b.k, b.k, b.k, dst + a.k + size_t(a.k) * n, n});
+        cp.push_back(CopyProb{LV.B.p + LV.oB12[t], a.k, b.k, a.k, dst + size_t(a.k) * n, n});
+        cp.push_back(CopyProb{LV.B.p + LV.oB21[t], b.k, a.k, b.k, dst + a.k, n});
+      }
+    }
+    batched_copy(cp, si);
+    // Dinv into G (root: final)
+    std::vector<InvProb> inv;
+    for (int t = 0; t < nn; ++t)
+      inv.push_back(InvProb{Dt.p + LV.oG[t], LV.G.p + LV.oG[t], Wk.p + LV.oG[t], mm[t], mm[t], mm[t], flags.p + h0 + t});
+    batched_inverse(inv, si);
+    if (l == 0) return;
+    // T1 = Dinv U (m x k), T2 = Vt Dinv (k x m), M = Vt T1 (k x k)
+    size_t sk = 0, skk = 0;
+    std::vector<size_t> oT(nn), oK(nn);
+    for (int t = 0; t < nn; ++t) { oT[t] = sk; sk += size_t(mm[t]) * node[h0 + t].k; oK[t] = skk; skk += size_t(node[h0 + t].k) * node[h0 + t].k; }
+    LV.E.alloc(sk); LV.F.alloc(sk);
+    order_after_alloc();
+    TBuf<double> T1(sk, si), T2(sk, si), M(skk, si), Mw(skk, si);
+    TBuf<double> Dh(std::max<size_t>(skk, 1), si);
+    LV.oE = oT; LV.oF = oT;
+    std::vector<GemmProb> g1, g2;
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      const double* Di = LV.G.p + LV.oG[t];
+      g1.push_back(GemmProb{Di, LV.U.p + LV.oU[t], T1.p + oT[t], n, k, n, n, n, n, 0, 0, 1.0, 0.0});
+      g1.push_back(GemmProb{LV.Vt.p + LV.oVt[t], Di, T2.p + oT[t], k, n, n, k, n, k, 0, 0, 1.0, 0.0});
+    }
+    batched_gemm(g1, si);
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      g2.push_back(GemmProb{LV.Vt.p + LV.oVt[t], T1.p + oT[t], M.p + oK[t], k, k, n, k, n, k, 0, 0, 1.0, 0.0});
+    }
+    batched_gemm(g2, si);
+    std::vector<InvProb> inv2;
+    for (int t = 0; t < nn; ++t)
+      inv2.push_back(InvProb{M.p + oK[t], Dh.p + oK[t], Mw.p + oK[t], node[h0 + t].k, node[h0 + t].k, node[h0 + t].k, flags.p + h0 + t});
+    batched_inverse(inv2, si);
+    std::vector<GemmProb> g3, g4;
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      g3.push_back(GemmProb{T1.p + oT[t], Dh.p + oK[t], LV.E.p + oT[t], n, k, k, n, k, n, 0, 0, 1.0, 0.0});
+      g3.push_back(GemmProb{Dh.p + oK[t], T2.p + oT[t], LV.F.p + oT[t], k, n, k, k, k, k, 0, 0, 1.0, 0.0});
+    }
+    batched_gemm(g3, si);
+    for (int t = 0; t < nn; ++t) {
+      const int n = mm[t], k = node[h0 + t].k;
+      g4.push_back(GemmProb{LV.E.p + oT[t], T2.p + oT[t], LV.G.p + LV.oG[t], n, n, k, n, k, n, 0, 0, -1.0, 1.0});
+    }
+    batched_gemm(g4, si);
+    Dh_prev = std::move(Dh);
+    oDh_prev = oK;
+  };
   // ---------------------------------------------------------- compression
   for (int l = L; l >= 1; --l) {
     const int h0 = 1 << l, nn = 1 << l;
@@ -524,147 +680,13 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
       }
     }
     RW_CUDA(cudaStreamSynchronize(s));
+    invert_level(l);
   }
 
-  tr.mark("compression (IDs)");
-  // ---------------------------------------------------------- B and D blocks
-  {
-    std::vector<int> idx;
-    std::vector<BlockProb> bp;
-    for (int l = 0; l < L; ++l) {
-      const int h0 = 1 << l, nn = 1 << l;
-      Level& LV = lev[l];
-      LV.oB12.resize(nn); LV.oB21.resize(nn);
-      size_t sb = 0;
-      for (int t = 0; t < nn; ++t) {
-        const HbsNode& a = node[2 * (h0 + t)];
-        const HbsNode& b = node[2 * (h0 + t) + 1];
-        LV.oB12[t] = sb; sb += size_t(a.k) * b.k;
-        LV.oB21[t] = sb; sb += size_t(b.k) * a.k;
-      }
-      LV.B.alloc(std::max<size_t>(sb, 1));
-    }
-    // index lists first (device copy), then block problems
-    std::vector<size_t> pos;
-    for (int l = 0; l < L; ++l)
-      for (int t = 0; t < (1 << l); ++t) {
-        const HbsNode& a = node[2 * ((1 << l) + t)];
-        const HbsNode& b = node[2 * ((1 << l) + t) + 1];
-        for (const std::vector<int>* v : {&a.skr, &b.skc, &b.skr, &a.skc}) { pos.push_back(idx.size()); idx.insert(idx.end(), v->begin(), v->end()); }
-      }
-    DBuf<int> didx = to_device(idx, s);
-    size_t q = 0;
-    for (int l = 0; l < L; ++l)
-      for (int t = 0; t < (1 << l); ++t) {
-        const HbsNode& a = node[2 * ((1 << l) + t)];
-        const HbsNode& b = node[2 * ((1 << l) + t) + 1];
-        Level& LV = lev[l];
-        bp.push_back(BlockProb{a.k, b.k, didx.p + pos[q], didx.p + pos[q + 1], 0, 0, 0, 0, 1.0, LV.B.p + LV.oB12[t], a.k});
-        bp.push_back(BlockProb{b.k, a.k, didx.p + pos[q + 2], didx.p + pos[q + 3], 0, 0, 0, 0, 1.0, LV.B.p + LV.oB21[t], b.k});
-        q += 4;
-      }
-    Level& LL = lev[L];
-    const int nl = 1 << L;
-    LL.oD.resize(nl);
-    size_t sd = 0;
-    for (int t = 0; t < nl; ++t) { const HbsNode& nd = node[nl + t]; LL.oD[t] = sd; sd += size_t(4) * (nd.hi - nd.lo) * (nd.hi - nd.lo); }
-    LL.D.alloc(sd);
-    for (int t = 0; t < nl; ++t) {
-      const HbsNode& nd = node[nl + t];
-      const int n = 2 * (nd.hi - nd.lo);
-      bp.push_back(BlockProb{n, n, nullptr, nullptr, 2 * nd.lo, 2 * nd.lo, 0, 0, 1.0, LL.D.p + LL.oD[t], n});
-    }
-    eval_blocks(bp, V, V, s);
-    RW_CUDA(cudaStreamSynchronize(s));
-  }
-
-  tr.mark("B, D blocks");
-  // ---------------------------------------------------------- inverse
-  // Per node: D~ (leaf: D; parent: [Dh_a B12; B21 Dh_b]); Dinv = D~^{-1};
-  // Dh = (V* Dinv U)^{-1}; E = Dinv U Dh; F* = Dh V* Dinv; G = Dinv - E V* Dinv.
-  DBuf<double> Dh_prev;  // Dh of the level below (children), offsets koff^2
-  std::vector<size_t> oDh_prev;
-  DBuf<int> flags(size_t(2) << L);
-  flags.zero(s);
-  for (int l = L; l >= 0; --l) {
-    const int h0 = 1 << l, nn = 1 << l;
-    Level& LV = lev[l];
-    std::vector<int> mm(nn);
-    size_t sG = 0;
-    LV.oG.resize(nn);
-    for (int t = 0; t < nn; ++t) {
-      const HbsNode& nd = node[h0 + t];
-      mm[t] = (l == L) ? 2 * (nd.hi - nd.lo) : node[2 * (h0 + t)].k + node[2 * (h0 + t) + 1].k;
-      if (l > 0) require(mm[t] == nd.m, "HBS: inconsistent candidate count");
-      LV.oG[t] = sG;
-      sG += size_t(mm[t]) * mm[t];
-    }
-    TBuf<double> Dt(sG, s), Wk(sG, s);
-    LV.G.alloc(sG);
-    // assemble D~
-    std::vector<CopyProb> cp;
-    for (int t = 0; t < nn; ++t) {
-      const int n = mm[t];
-      double* dst = Dt.p + LV.oG[t];
-      if (l == L) {
-        cp.push_back(CopyProb{LV.D.p + LV.oD[t], n, n, n, dst, n});
-      } else {
-        const HbsNode& a = node[2 * (h0 + t)];
-        const HbsNode& b = node[2 * (h0 + t) + 1];
-        const int ca = 2 * t, cb = 2 * t + 1;  // child positions in the level below
-        cp.push_back(CopyProb{Dh_prev.p + oDh_prev[ca], a.k, a.k, a.k, dst, n});
-        cp.push_back(CopyProb{Dh_prev.p + oDh_prev[cb], b.k, b.k, b.k, dst + a.k + size_t(a.k) * n, n});
-        cp.push_back(CopyProb{LV.B.p + LV.oB12[t], a.k, b.k, a.k, dst + size_t(a.k) * n, n});
-        cp.push_back(CopyProb{LV.B.p + LV.oB21[t], b.k, a.k, b.k, dst + a.k, n});
-      }
-    }
-    batched_copy(cp, s);
-    // Dinv into G (root: final)
-    std::vector<InvProb> inv;
-    for (int t = 0; t < nn; ++t)
-      inv.push_back(InvProb{Dt.p + LV.oG[t], LV.G.p + LV.oG[t], Wk.p + LV.oG[t], mm[t], mm[t], mm[t], flags.p + h0 + t});
-    batched_inverse(inv, s);
-    if (l == 0) break;
-    // T1 = Dinv U (m x k), T2 = Vt Dinv (k x m), M = Vt T1 (k x k)
-    size_t sk = 0, skk = 0;
-    std::vector<size_t> oT(nn), oK(nn);
-    for (int t = 0; t < nn; ++t) { oT[t] = sk; sk += size_t(mm[t]) * node[h0 + t].k; oK[t] = skk; skk += size_t(node[h0 + t].k) * node[h0 + t].k; }
-    TBuf<double> T1(sk, s), T2(sk, s), M(skk, s), Mw(skk, s);
-    DBuf<double> Dh(std::max<size_t>(skk, 1));
-    LV.E.alloc(sk); LV.F.alloc(sk);
-    LV.oE = oT; LV.oF = oT;
-    std::vector<GemmProb> g1, g2;
-    for (int t = 0; t < nn; ++t) {
-      const int n = mm[t], k = node[h0 + t].k;
-      const double* Di = LV.G.p + LV.oG[t];
-      g1.push_back(GemmProb{Di, LV.U.p + LV.oU[t], T1.p + oT[t], n, k, n, n, n, n, 0, 0, 1.0, 0.0});
-      g1.push_back(GemmProb{LV.Vt.p + LV.oVt[t], Di, T2.p + oT[t], k, n, n, k, n, k, 0, 0, 1.0, 0.0});
-    }
-    batched_gemm(g1, s);
-    for (int t = 0; t < nn; ++t) {
-      const int n = mm[t], k = node[h0 + t].k;
-      g2.push_back(GemmProb{LV.Vt.p + LV.oVt[t], T1.p + oT[t], M.p + oK[t], k, k, n, k, n, k, 0, 0, 1.0, 0.0});
-    }
-    batched_gemm(g2, s);
-    std::vector<InvProb> inv2;
-    for (int t = 0; t < nn; ++t)
-      inv2.push_back(InvProb{M.p + oK[t], Dh.p + oK[t], Mw.p + oK[t], node[h0 + t].k, node[h0 + t].k, node[h0 + t].k, flags.p + h0 + t});
-    batched_inverse(inv2, s);
-    std::vector<GemmProb> g3, g4;
-    for (int t = 0; t < nn; ++t) {
-      const int n = mm[t], k = node[h0 + t].k;
-      g3.push_back(GemmProb{T1.p + oT[t], Dh.p + oK[t], LV.E.p + oT[t], n, k, k, n, k, n, 0, 0, 1.0, 0.0});
-      g3.push_back(GemmProb{Dh.p + oK[t], T2.p + oT[t], LV.F.p + oT[t], k, n, k, k, k, k, 0, 0, 1.0, 0.0});
-    }
-    batched_gemm(g3, s);
-    for (int t = 0; t < nn; ++t) {
-      const int n = mm[t], k = node[h0 + t].k;
-      g4.push_back(GemmProb{LV.E.p + oT[t], T2.p + oT[t], LV.G.p + LV.oG[t], n, n, k, n, k, n, 0, 0, -1.0, 1.0});
-    }
-    batched_gemm(g4, s);
-    Dh_prev = std::move(Dh);
-    oDh_prev = oK;
-  }
+  tr.mark("compression (IDs), inverse overlapped");
+  invert_level(0);
+  Dh_prev = TBuf<double>();
+  RW_CUDA(cudaStreamSynchronize(si));
   auto hf = flags.download(s);
   for (int f : hf) require(f == 0, "HBS inverse: singular diagonal block", RW_ERR_SINGULAR);
 
