@@ -33,6 +33,16 @@ def test_default_opts_and_validation_without_gpu():
     L = rwsolve.load(build_if_missing=True)
     o = rwsolve.default_opts()
     assert o.leaf_points == 64 and o.id_tol == 1e-12 and o.gmres_tol == 1e-10
+    # the last field of rw_opts: a layout mismatch between the header and the
+    # binding would leave it unset or shifted
+    assert o.hole_div_ratio == 4.0 and o.seed == 0x5eed2108
+    bad = rwsolve.default_opts(hole_div_ratio=1.2)   # must exceed bas_ratio (1.5)
+    d0 = rwsolve.WallDesc()
+    d0.curve_kind = rwsolve.CURVE_STAR
+    d0.n_panels = 8
+    h0 = ctypes.c_void_p()
+    assert L.rw_hbs_build(ctypes.byref(d0), ctypes.byref(bad), None, ctypes.byref(h0)) == -1
+    assert b"hole_div_ratio" in L.rw_last_error()
     d = rwsolve.WallDesc()
     d.curve_kind = 7
     d.n_panels = 4
