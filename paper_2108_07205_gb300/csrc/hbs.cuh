@@ -102,7 +102,9 @@ class Hbs {
   size_t bytes = 0;
   int max_rank = 0;
 
-  // Build from a node set (positions on host in `nodes.hx/hy` for planning).
+  // Build from a node set (positions on host in `nodes.hx/hy` for planning):
+  // compression level by level on s, each level's inverse on a second stream
+  // as soon as that level is compressed (synchronised before returning).
   void build(const Nodes& nodes, const Opts& o, cudaStream_t s);
   // Single-leaf representation of a dense matrix A (2 npts x 2 npts, column
   // major; the handle takes it over): the forward apply uses A, the inverse
