@@ -1,20 +1,36 @@
-"""Benchmark: refined-wall solves per second on the constricted channel.
+"""Benchmark: refined-wall solves per second at a certified relative residual
+of 1e-10, mixed precision against FP64, on the constricted channel.
 
-Workload (one GPU): the 1024-panel channel wall (16384 points, 32768
-unknowns, HBS leaf 64, ID tolerance 1e-12).  One step = one time step of the
-moving-window schedule: an 8-panel window advancing one panel per step,
-refined 2-5 levels (seeded), so each step runs the whole hot path:
-refinement factorisation (added nodes, A_pp^{-1}, row IDs, X, W^{-1}),
-boundary data from 5 exterior Stokeslets at the refined nodes, the Woodbury
-solve for the density, and the interior velocity at 16 targets.  The
+Default workload (one GPU): the 2048-panel channel wall (32768 points,
+65536 unknowns, HBS leaf 64, ID tolerance 1e-12, operator tolerance 1e-14).
+One step = one time step of the moving-window schedule: an 8-panel window
+advancing one panel per step, refined 2-5 levels (seeded), 64 right-hand
+sides from seeded pairs of exterior Stokeslets.  Each step runs the whole hot
+path: refinement factorisation (added nodes, A_pp and its inverse, row IDs,
+X, W^{-1}), boundary data at the refined nodes, the solve of all 64
+right-hand sides to a relative residual <= 1e-10 of the extended system
+against the operator at 1e-14, and the interior velocity at 16 targets.  The
 reference wall's HBS (built once) is static and excluded, as the paper's
 T_static.
 
-`value`: steps per second with the Stokeslet inputs resident on the device.
-`e2e`: the same through host buffers (inputs copied in and density and
-velocity copied out inside the timed region).
+Two arms run the same steps:
+  * the headline, RW_MODE_GMRES_MIXED: FP64 FGMRES whose preconditioner is
+    Algorithm 1 with FP32 HBS sweeps and an FP32 Woodbury correction (W^{-1}
+    in FP64) and whose operator products run in double-FP32;
+  * "fp64_arm", RW_MODE_DIRECT_IR: Algorithm 1 in FP64 plus FP64 iterative
+    refinement against the same operator, the plain FP64 path to the same
+    certified residual.
+After the timed steps, sampled steps of each arm are re-run and their
+density checked against the exact refined operator A_nn (every entry
+evaluated on the fly): the true relative residual is printed per arm.
+
+`value`: solves per second (steps x right-hand sides / time) with the
+Stokeslet inputs resident on the device.  `e2e`: the same through host
+buffers (inputs copied in and density and velocity copied out inside the
+timed region).
 --impl reference: the CPU oracle (dense Nystrom assembly + LAPACK LU) timed on
-the host cores on the same workload family (see cpu_baseline.sample).
+the host cores on a bounded sample of the same workload family (see
+cpu_baseline.sample).
 Multi-GPU: replicas only (independent walls and windows per rank).
 """
 import argparse
@@ -30,10 +46,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-P_PANELS = 1024
 TARGETS = 16
 N_SRC = 5
-NRHS = 1
+OP_TOL = 1e-14
+
+# workload -> panels, right-hand sides per step, data kind
+WORKLOADS = {
+    "mixed2048": dict(P=2048, nrhs=64, pairs=True),
+    "channel1024": dict(P=1024, nrhs=1, pairs=False),
+}
+P_PANELS = 2048
+NRHS = 64
+PAIRS = True
 
 
 def parse():
@@ -42,17 +66,32 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="direct", choices=["direct", "gmres", "gmres_bf16", "refined"])
+    ap.add_argument("--mode", default="mixed",
+                    choices=["mixed", "fp64_ir", "direct", "gmres", "gmres_bf16", "refined"])
+    ap.add_argument("--compare", default="fp64_ir", choices=["fp64_ir", "direct", "gmres", "none"],
+                    help="second arm timed on the same steps (none: skip)")
+    ap.add_argument("--verify-steps", type=int, default=3, help="steps of each arm re-run and checked against A_nn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=48, help="serving workload: number of requests per phase")
     ap.add_argument("--walls", type=int, default=32, help="batched workload: number of walls")
-    ap.add_argument("--workload", default="channel1024",
-                    choices=["channel1024", "mixed2048", "serving", "batched", "holes"],
-                    help="channel1024: 1 RHS per step (default); mixed2048: 2048-panel channel, 64 RHS per "
-                         "step from Stokeslet pairs")
+    ap.add_argument("--workload", default="mixed2048",
+                    choices=["mixed2048", "channel1024", "serving", "batched", "holes"],
+                    help="mixed2048: 2048-panel channel, 64 RHS per step from Stokeslet pairs (default); "
+                         "channel1024: 1024-panel channel, 1 RHS per step")
     ap.add_argument("--refine-probe", type=int, default=0,
                     help="profiling driver: build the wall, run this many refinement steps, print their times")
     return ap.parse_args()
+
+
+MODE_NAMES = {"mixed": "MODE_GMRES_MIXED", "fp64_ir": "MODE_DIRECT_IR", "direct": "MODE_DIRECT",
+              "gmres": "MODE_GMRES_FP32", "gmres_bf16": "MODE_GMRES_BF16", "refined": "MODE_DIRECT_REFINED"}
+MODE_DTYPE = {"mixed": "f64+f32", "fp64_ir": "f64", "direct": "f64", "gmres": "f64+f32", "gmres_bf16": "f64+bf16",
+              "refined": "f64"}
+
+
+def mode_id(name):
+    from paper_2108_07205_gb300 import rwsolve
+    return getattr(rwsolve, MODE_NAMES[name])
 
 
 def dist_env():
@@ -117,8 +156,8 @@ class Clocks:
 
 def stokeslet_inputs(step, rank):
     from paper_2108_07205_gb300 import inputs
-    if NRHS == 1:
-        sx, sy, f = inputs.stokeslets_channel(1000 * rank + step, nrhs=1, n=N_SRC)
+    if not PAIRS:
+        sx, sy, f = inputs.stokeslets_channel(1000 * rank + step, nrhs=NRHS, n=N_SRC)
     else:
         sx, sy, f = inputs.stokeslet_pairs_channel(1000 * rank + step, NRHS)
     src = np.ascontiguousarray(np.stack([sx, sy], 1))
@@ -128,34 +167,18 @@ def stokeslet_inputs(step, rank):
     return src, fd, tg
 
 
-def run_ours(args, rank, world, local):
+def run_arm(args, wall, mode_name, sched, dev_in, host_in, flush, local, profile=False, verify=0):
+    """Time one solve mode on the step schedule: W warm-up steps, then K timed
+    steps with device inputs and K with host inputs; optionally a profiled
+    repeat and a re-run of sampled steps checked against the exact operator."""
     import torch
-    from paper_2108_07205_gb300 import rwsolve, inputs, replicas
-    torch.cuda.set_device(local)
+    from paper_2108_07205_gb300 import rwsolve, replicas
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    rwsolve.load(build_if_missing=True)
-    mode = {"direct": rwsolve.MODE_DIRECT, "gmres": rwsolve.MODE_GMRES_FP32,
-            "refined": rwsolve.MODE_DIRECT_REFINED, "gmres_bf16": rwsolve.MODE_GMRES_BF16}[args.mode]
-    t0 = time.time()
-    wall = rwsolve.Wall("channel", P_PANELS)
-    torch.cuda.synchronize()
-    build_s = time.time() - t0
-    hst = wall.stats()
+    mode = mode_id(mode_name)
     total = args.warmup + args.steps
-    sched = inputs.time_schedule(replicas.schedule_seed(rank), P_PANELS, 2 * total + 1)
-    # device-resident inputs for every step
-    dev_in = []
-    host_in = []
-    for s in range(2 * total + 1):
-        src, fd, tg = stokeslet_inputs(s, rank)
-        host_in.append((torch.from_numpy(src).pin_memory(), torch.from_numpy(fd).pin_memory(),
-                        torch.from_numpy(tg).pin_memory()))
-        dev_in.append(tuple(x.to(dev) for x in (torch.from_numpy(src), torch.from_numpy(fd), torch.from_numpy(tg))))
-    # L2 flush buffer (> 129 MB L2)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(s, host):
+    def step(s, host, keep=False):
         panels, levels = sched[s]
         ref = wall.refine(panels, levels, stream=stream)
         n_n = ref.stats()["n_n"]
@@ -174,6 +197,8 @@ def run_ours(args, rank, world, local):
             u = torch.empty((NRHS, 2 * TARGETS), dtype=torch.float64, device=dev)
             info = ref.solve(g, tau, nrhs=NRHS, targets=tg, u=u, mode=mode, stream=stream)
         st = ref.stats()
+        if keep:
+            return ref, g, tau, st, info
         ref.close()
         return st, info
 
@@ -215,49 +240,29 @@ def run_ours(args, rank, world, local):
         lats = [a.elapsed_time(b) for a, b in lat]
         return ms, lats, stats, clocks, launches
 
-    try:
-        ms, lats, stats, clocks, launches = timed(0, host=False)
-    except rwsolve.RWError as e:
-        if args.mode != "gmres_bf16" or e.code != -4:
-            raise
-        # BF16 sweeps as the preconditioner do not converge on this wall: the
-        # BF16 rounding of the inverse times the wall's conditioning exceeds one
-        if rank == 0:
-            print(json.dumps({"metric": "refined-wall solves/s", "value": None, "unit": "solves/s", "n_gpus": world,
-                              "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-                              "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16", "data": "synthetic",
-                              "config": workload_config(args), "not_converged": str(e)}))
-        return
+    ms, lats, stats, clocks, launches = timed(0, host=False)
     ms_e2e, lats_e2e, _, _, _ = timed(total, host=True)
-    # profiled repeat of the device-input steps: per-kernel-class CUDA-event
-    # durations (on each launch's stream) and algorithmic flops
-    rwsolve.profile(True)
-    for i in range(args.steps):
-        step(args.warmup + i, False)
-    prof = rwsolve.profile_read()
-    rwsolve.profile(False)
-    ms, ms_e2e = replicas.max_over_ranks([ms, ms_e2e])
-    ks = [s[0]["k"] for s in stats]
-    nps = [s[0]["n_p"] for s in stats]
-    out = {
-        "ms": ms, "ms_e2e": ms_e2e, "lat": lats, "lat_e2e": lats_e2e, "clocks": clocks,
-        "build_s": build_s, "hbs": hst, "k_mean": float(np.mean(ks)), "np_range": [min(nps), max(nps)],
-        "iters": [s[1]["iters"] for s in stats], "launches": launches, "prof": prof,
-    }
-    # solve-only rate on one refinement (same shapes), and the sweep kernel roofline
-    panels, levels = sched[0]
-    ref = wall.refine(panels, levels, stream=stream)
-    n_n = ref.stats()["n_n"]
-    src, fd, tg = dev_in[0]
-    g = torch.empty((NRHS, 2 * n_n), dtype=torch.float64, device=dev)
-    ref.stokeslet_data(src, fd, g, nrhs=NRHS, stream=stream)
-    tau = torch.empty_like(g)
-    for _ in range(5):
+    out = {"mode": mode_name, "ms": ms, "ms_e2e": ms_e2e, "lat": lats, "lat_e2e": lats_e2e, "clocks": clocks,
+           "launches": launches, "k_mean": float(np.mean([s[0]["k"] for s in stats])),
+           "np_range": [min(s[0]["n_p"] for s in stats), max(s[0]["n_p"] for s in stats)],
+           "iters": [s[1]["iters"] for s in stats], "relres": max(s[1]["rel_residual"] for s in stats),
+           "nn_mean": float(np.mean([s[0]["n_n"] for s in stats]))}
+    if profile:
+        # profiled repeat of the device-input steps: per-kernel-class CUDA-event
+        # durations (on each launch's stream) and algorithmic flops
+        rwsolve.profile(True)
+        for i in range(args.steps):
+            step(args.warmup + i, False)
+        out["prof"] = rwsolve.profile_read()
+        rwsolve.profile(False)
+    # solve-only rate on one refinement (same shapes)
+    ref, g, tau, _, _ = step(0, False, keep=True)
+    for _ in range(2):
         ref.solve(g, tau, nrhs=NRHS, mode=mode, stream=stream)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    nsolve = 50
+    nsolve = 10 if NRHS > 8 else 50
     e0.record(stream)
     for _ in range(nsolve):
         ref.solve(g, tau, nrhs=NRHS, mode=mode, stream=stream)
@@ -265,37 +270,34 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     out["solve_ms"] = e0.elapsed_time(e1) / nsolve
     ref.close()
-    # HBS inverse sweep alone (s1 on the reference wall): algorithmic bytes =
-    # matrix entries read (FP64) + vectors
-    b = torch.randn(2 * hst["n_points"], dtype=torch.float64, device=dev)
-    x = torch.empty_like(b)
-    for _ in range(5):
-        wall.apply_inverse(b, x, stream=stream)
-    torch.cuda.synchronize()
-    nsw = 50
-    times = []
-    for _ in range(nsw):
-        flush.zero_()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        wall.apply_inverse(b, x, stream=stream)
-        a1.record(stream)
-        times.append((a0, a1))
-    torch.cuda.synchronize()
-    sweep_ms = float(np.mean([a.elapsed_time(c) for a, c in times]))
-    out["sweep_ms"] = sweep_ms
-    out["sweep_bytes"] = 8 * hst["inv_elems"] + 8 * 4 * 2 * hst["n_points"]
-    wall.close()
+    # accuracy: re-run sampled timed steps (same inputs, same kernels) and
+    # apply the exact refined operator A_nn to the density
+    checks, taus = [], {}
+    for i in np.linspace(0, args.steps - 1, max(verify, 0)).astype(int) if verify else []:
+        s = args.warmup + int(i)
+        ref, g, tau, _, info = step(s, False, keep=True)
+        y = torch.empty_like(g)
+        ref.apply_refined(tau, y, nrhs=NRHS, stream=stream)
+        res = ((y - g).norm(dim=1) / g.norm(dim=1)).max().item()
+        checks.append({"step": s, "true_rel_residual_max": res, "solver_rel_residual": info["rel_residual"],
+                       "iters": info["iters"]})
+        taus[s] = tau.cpu()
+        ref.close()
+    out["verify"] = checks
+    out["taus"] = taus
     return out
 
 
-def cpu_baseline(budget_s=25.0):
+def cpu_baseline(budget_s=25.0, single_thread=True):
     """Oracle (dense assembly + LAPACK LU) on the host cores on a bounded
-    sample of the workload: one moving-window step on the same channel family
-    at 256 panels (the dense solve of the 1024-panel step does not fit the
-    time budget); the rate is scaled to the full-size step by the LU flop
-    ratio (n_sample / n_full)^3."""
+    sample of the workload: moving-window steps on the same channel family at
+    256 panels, one right-hand side each (the dense solve of a full-size step,
+    2N_n ~ 70000, needs about 40 GB for the matrix and several times that for
+    the assembly's temporaries); each measured time is scaled to the full-size
+    step by the LU flop ratio (2N_n / 2N_full)^3 and the step's right-hand
+    sides share the factorisation, so solves/s = nrhs / scaled time.  The
+    single-thread figure repeats one sample step in a child process with every
+    BLAS pool held to one thread."""
     from oracle import discretize as D, stokes as S, dense as DN
     from paper_2108_07205_gb300 import inputs
     cores = os.cpu_count()
@@ -317,42 +319,85 @@ def cpu_baseline(budget_s=25.0):
     n_full = 2 * (16 * P_PANELS - 16 * len(full[0]) + 16 * sum(2 ** L for L in full[1]))
     # the measured steps have varying sizes: scale each to the full step
     scaled = [t * (n_full / n) ** 3 for t, n in zip(times, ns)]
-    v = 1.0 / float(np.mean(scaled))
-    return {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(times)} steps of the 256-panel channel window schedule "
-                      f"(2N_n {min(ns)}-{max(ns)}), dense assembly + LAPACK LU, time scaled by "
-                      f"(2N_n / {n_full})^3 to the 1024-panel step; raw mean {np.mean(times):.3f} s/solve"}
+    v = NRHS / float(np.mean(scaled))
+    out = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "blas_threads": _blas_threads(),
+           "sample": f"{len(times)} steps of the 256-panel channel window schedule "
+                     f"(2N_n {min(ns)}-{max(ns)}), dense assembly + LAPACK LU, 1 RHS; time scaled by "
+                     f"(2N_n / {n_full})^3 to the full-size step, {NRHS} RHS sharing it; "
+                     f"raw mean {np.mean(times):.3f} s per sample step",
+           "sample_s_per_step": float(np.mean(times))}
+    if single_thread:
+        out["single_thread"] = _single_thread_sample(n_full)
+    return out
+
+
+def _blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return f"{k}={os.environ[k]}"
+    return f"default (BLAS pool sized to the {os.cpu_count()} host cores)"
+
+
+def _single_thread_sample(n_full):
+    """One 256-panel sample step of the oracle with one BLAS thread, scaled as
+    cpu_baseline scales its steps; run in a child process (the thread count of
+    a BLAS pool is fixed when it starts)."""
+    code = ("import sys, time, json; sys.path.insert(0, %r)\n"
+            "from oracle import discretize as D, stokes as S, dense as DN\n"
+            "from paper_2108_07205_gb300 import inputs\n"
+            "panels, levels = inputs.time_schedule(17, 256, 1)[0]\n"
+            "o = D.refine('channel', {}, 256, panels, levels)\n"
+            "sx, sy, f = inputs.stokeslets_channel(0)\n"
+            "t0 = time.time(); g = S.boundary_data(o['n'], sx, sy, f)[:, 0]; DN.solve_refined(o, g)\n"
+            "print(json.dumps({'s': time.time() - t0, 'n': 2 * o['n']['x'].size}))\n" % ROOT)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": NRHS / (d["s"] * (n_full / d["n"]) ** 3), "unit": "solves/s", "cores": 1,
+            "sample_s": d["s"], "sample_2n": d["n"]}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is one bounded sample
+    (cpu_baseline's scaling to the full-size step); ms_per_step is the time
+    the samples actually took, value the scaled solves/s."""
     if rank != 0:
         return
-    t_all = []
+    rates, took = [], []
     budget = 150.0 / max(1, args.steps + args.warmup)
     cb = None
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(budget_s=budget)
+        t0 = time.time()
+        cb = cpu_baseline(budget_s=budget, single_thread=False)
         if i >= args.warmup:
-            t_all.append(1.0 / cb["value"])
-    v = 1.0 / float(np.mean(t_all))
-    line = {"impl": "reference", "metric": "refined-wall solves/s", "value": v, "unit": "solves/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            rates.append(cb["value"])
+            took.append(time.time() - t0)
+    v = 1.0 / float(np.mean([1.0 / r for r in rates]))
+    line = {"impl": "reference", "metric": "refined-wall solves/s at rel. residual 1e-10", "value": v,
+            "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(took)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
-                             "unit": "solves/s"},
+                             "unit": "solves/s", "blas_threads": cb["blas_threads"]},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def workload_config(args):
-    if args.workload == "mixed2048":
-        return {"workload": "channel 2048 panels x 16 nodes (65536 unknowns), moving 8-panel window refined "
-                            "2-5 levels, refine + data + solve + velocity per step, 64 RHS from Stokeslet pairs",
-                "mode": args.mode, "hbs_leaf": 64, "id_tol": 1e-12, "l2": "flushed (256 MB write) before each step"}
-    return {"workload": "channel 1024 panels x 16 nodes (32768 unknowns), moving 8-panel window refined "
-                        "2-5 levels, refine + data + solve + velocity per step, 1 RHS",
-            "mode": args.mode, "hbs_leaf": 64, "id_tol": 1e-12, "l2": "flushed (256 MB write) before each step"}
+    w = {"mixed2048": "channel 2048 panels x 16 nodes (65536 unknowns), moving 8-panel window refined 2-5 levels, "
+                      "64 RHS from Stokeslet pairs per step; refine + data + solve to relative residual <= 1e-10 + "
+                      "velocity at 16 targets",
+         "channel1024": "channel 1024 panels x 16 nodes (32768 unknowns), moving 8-panel window refined 2-5 levels, "
+                        "1 RHS from 5 Stokeslets per step; refine + data + solve + velocity at 16 targets"}
+    return {"workload": w.get(args.workload, args.workload), "mode": MODE_NAMES[args.mode],
+            "compare": None if args.compare == "none" else MODE_NAMES[args.compare],
+            "hbs_leaf": 64, "id_tol": 1e-12, "op_tol": OP_TOL, "residual_tol": 1e-10,
+            "l2": "flushed (256 MB write) before each step"}
 
 
 def refine_probe(k):
@@ -608,11 +653,121 @@ def _stokeslet_field(tx, ty, src, f):
     return np.stack([ux, uy], 1)
 
 
+def run_ours(args, rank, world, local):
+    """Build the wall, the schedule and the inputs, then time each arm."""
+    import torch
+    from paper_2108_07205_gb300 import rwsolve, inputs, replicas
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    rwsolve.load(build_if_missing=True)
+    t0 = time.time()
+    wall = rwsolve.Wall("channel", P_PANELS, opts=rwsolve.default_opts(op_tol=OP_TOL))
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    hst = wall.stats()
+    total = args.warmup + args.steps
+    sched = inputs.time_schedule(replicas.schedule_seed(rank), P_PANELS, 2 * total + 1)
+    dev_in, host_in = [], []
+    for s in range(2 * total + 1):
+        src, fd, tg = stokeslet_inputs(s, rank)
+        host_in.append((torch.from_numpy(src).pin_memory(), torch.from_numpy(fd).pin_memory(),
+                        torch.from_numpy(tg).pin_memory()))
+        dev_in.append(tuple(x.to(dev) for x in (torch.from_numpy(src), torch.from_numpy(fd), torch.from_numpy(tg))))
+    # L2 flush buffer (> 129 MB L2)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    arms = [args.mode] + ([args.compare] if args.compare not in ("none", args.mode) else [])
+    res = {}
+    for i, m in enumerate(arms):
+        try:
+            res[m] = run_arm(args, wall, m, sched, dev_in, host_in, flush, local, profile=(i == 0),
+                             verify=args.verify_steps)
+        except rwsolve.RWError as e:
+            res[m] = {"error": str(e)}
+    # HBS inverse sweep alone (s1 on the reference wall, 1 RHS): algorithmic
+    # bytes = matrix entries read (FP64) + vectors
+    b = torch.randn(2 * hst["n_points"], dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    for _ in range(5):
+        wall.apply_inverse(b, x, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(50):
+        flush.zero_()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        wall.apply_inverse(b, x, stream=stream)
+        a1.record(stream)
+        times.append((a0, a1))
+    torch.cuda.synchronize()
+    sweep = {"ms": float(np.mean([a.elapsed_time(c) for a, c in times])),
+             "bytes": 8 * hst["inv_elems"] + 8 * 4 * 2 * hst["n_points"]}
+    wall.close()
+    for m in res:
+        if "ms" in res[m]:
+            res[m]["ms"], res[m]["ms_e2e"] = replicas.max_over_ranks([res[m]["ms"], res[m]["ms_e2e"]])
+    h2d = int(sum(x.numel() * x.element_size() for x in host_in[0]))
+    return {"arms": res, "order": arms, "build_s": build_s, "hbs": hst, "sweep": sweep, "h2d": h2d}
+
+
+# Peaks of the ALU-bound kernel classes, from the unit counts and the SM clock
+# sampled under load: 152 SMs; FP64 4 flop/clk/SM; FP32 128 lanes x 2
+# flop/clk/SM; double-FP32 products take 12 FP32 lane operations per
+# multiply-add (2 FP64-equivalent flops).
+def alu_peak_tflops(cls, sm_mhz):
+    clk = sm_mhz * 1e6
+    if cls == "gemm_f32":
+        return 152 * 256 * clk / 1e12, "FP32: 152 SMs x 128 lanes x 2 flop/clk x median SM clock"
+    if cls == "gemm_df":
+        return 152 * 128 * 2 / 12 * clk / 1e12, ("double-FP32: 152 SMs x 128 FP32 lanes / 12 lane-ops per "
+                                                  "multiply-add x 2 flop x median SM clock")
+    return 152 * 4 * clk / 1e12, "FP64: 152 SMs x 4 flop/clk x median SM clock"
+
+
+KCLASS_NAMES = {"id": "column-pivoted QR (cluster and grid-wide kernels, FP64)", "gemm": "batched tiled GEMM (FP64)",
+                "gemv": "batched GEMV / HBS sweeps", "inverse": "batched Gauss-Jordan inverse (FP64)",
+                "eval": "kernel-entry evaluation (FP64)", "other": "bookkeeping kernels",
+                "gemm_f32": "batched GEMM, FP32 accumulation (preconditioner sweeps)",
+                "gemm_df": "batched double-FP32 GEMM (FP64-accurate operator products)"}
+
+
+def roofline_of(prof, steps, sm_mhz, hbm, hbm_src):
+    dom = max(prof, key=lambda c: prof[c]["ms"])
+    dp = prof[dom]
+    if dom == "gemv" or dom == "other":
+        ach = dp["bytes"] / (dp["ms"] / 1e3) / 1e9
+        return {"kernel": KCLASS_NAMES[dom], "class": dom, "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "launches_per_step": dp["launches"] / steps,
+                "avg_launch_ms": dp["ms"] / max(dp["launches"], 1), "peak_source": hbm_src}
+    peak, src = alu_peak_tflops(dom, sm_mhz)
+    ach = dp["flops"] / (dp["ms"] / 1e3) / 1e12
+    return {"kernel": KCLASS_NAMES[dom], "class": dom, "bound": "alu", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches_per_step": dp["launches"] / steps,
+            "avg_launch_ms": dp["ms"] / max(dp["launches"], 1), "peak_source": "derived " + src}
+
+
+def arm_summary(a, args, world):
+    if "error" in a:
+        return {"mode": a.get("mode"), "error": a["error"]}
+    v = world * args.steps * NRHS / (a["ms"] / 1e3)
+    checks = a["verify"]
+    return {"mode": MODE_NAMES[a["mode"]], "value": v, "unit": "solves/s", "ms_per_step": a["ms"] / args.steps,
+            "e2e": world * args.steps * NRHS / (a["ms_e2e"] / 1e3),
+            "p50_ms": float(np.percentile(a["lat"], 50)), "p99_ms": float(np.percentile(a["lat"], 99)),
+            "solve_only_per_s": NRHS * 1e3 / a["solve_ms"], "solve_only_ms": a["solve_ms"],
+            "iters": a["iters"], "solver_rel_residual_max": a["relres"], "k_mean": a["k_mean"],
+            "true_rel_residual_max": max((c["true_rel_residual_max"] for c in checks), default=None),
+            "verified_steps": [c["step"] for c in checks], "dtype": MODE_DTYPE[a["mode"]],
+            "gpu_launches": a["launches"]}
+
+
 def main():
-    global P_PANELS, NRHS
+    global P_PANELS, NRHS, PAIRS
     args = parse()
-    if args.workload == "mixed2048":
-        P_PANELS, NRHS = 2048, 64
+    if args.workload in WORKLOADS:
+        wl = WORKLOADS[args.workload]
+        P_PANELS, NRHS, PAIRS = wl["P"], wl["nrhs"], wl["pairs"]
     if args.refine_probe:
         refine_probe(args.refine_probe)
         return
@@ -635,60 +790,71 @@ def main():
     out = run_ours(args, rank, world, local)
     if rank != 0 or out is None:
         return
-    peaks = {}
+    peaks, hbm_src = {}, "profiling recipe fallback 6800 GB/s (MEASURED_PEAKS.json absent)"
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
+        hbm_src = "MEASURED_PEAKS.json hbm_gbs"
+    except (OSError, ValueError):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    value = world * args.steps * NRHS / (out["ms"] / 1e3)
-    e2e = world * args.steps * NRHS / (out["ms_e2e"] / 1e3)
-    # FP64 ALU peak: 152 SMs x 4 FP64 flop/clk (nominal 1.25 TFLOP/s at the
-    # 2070 MHz maximum clock), evaluated at the median SM clock under load
-    sm_mhz = (out["clocks"] or {}).get("sm_mhz") or 2070.0
-    fp64_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
-    prof = out["prof"]
-    dom = max(prof, key=lambda c: prof[c]["ms"])
-    dp = prof[dom]
-    dom_names = {"id": "column-pivoted QR (cluster and grid-wide kernels, FP64)", "gemm": "batched tiled GEMM (FP64)",
-                 "gemv": "batched GEMV / HBS sweeps (FP64)", "inverse": "batched Gauss-Jordan inverse (FP64)",
-                 "eval": "kernel-entry evaluation (FP64)", "other": "bookkeeping kernels"}
-    if dom in ("id", "gemm", "inverse", "eval"):
-        ach = dp["flops"] / (dp["ms"] / 1e3) / 1e12
-        roof = {"kernel": dom_names[dom], "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None, "launches_per_step": dp["launches"] / args.steps,
-                "avg_launch_ms": dp["ms"] / max(dp["launches"], 1),
-                "peak_source": "derived FP64 peak (152 SMs x 4 flop/clk x median SM clock)"}
-    else:
-        ach = dp["bytes"] / (dp["ms"] / 1e3) / 1e9
-        roof = {"kernel": dom_names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "launches_per_step": dp["launches"] / args.steps,
-                "avg_launch_ms": dp["ms"] / max(dp["launches"], 1), "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-    achieved = out["sweep_bytes"] / (out["sweep_ms"] / 1e3) / 1e9
-    sweep_flops = 2.0 * out["hbs"]["inv_elems"]
+    head = out["arms"][out["order"][0]]
+    if "error" in head:
+        print(json.dumps({"metric": "refined-wall solves/s at rel. residual 1e-10", "value": None,
+                          "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": MODE_DTYPE[args.mode], "data": "synthetic", "config": workload_config(args),
+                          "error": head["error"]}))
+        return
+    hs = arm_summary(head, args, world)
+    sm_mhz = (head["clocks"] or {}).get("sm_mhz") or 2070.0
+    prof = head["prof"]
     share = {c: round(prof[c]["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9), 4) for c in prof}
+    roof = roofline_of(prof, args.steps, sm_mhz, hbm, hbm_src)
+    by_class = {}
+    for c in ("gemm_df", "gemm_f32", "gemm", "id"):
+        if prof.get(c, {}).get("launches"):
+            pk, src = alu_peak_tflops(c, sm_mhz)
+            ach = prof[c]["flops"] / (prof[c]["ms"] / 1e3) / 1e12
+            by_class[c] = {"achieved_tflops": ach, "peak_tflops": pk, "frac": ach / pk,
+                           "launches_per_step": prof[c]["launches"] / args.steps}
+    fp64_peak = alu_peak_tflops("gemm", sm_mhz)[0]
+    sw = out["sweep"]
+    sweep_gbs = sw["bytes"] / (sw["ms"] / 1e3) / 1e9
+    sweep_flops = 2.0 * out["hbs"]["inv_elems"]
+    h2d = out["h2d"]   # point forces, their positions and the velocity targets of one step
     line = {
-        "metric": "refined-wall solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"gmres": "f64+f32", "gmres_bf16": "f64+bf16"}.get(args.mode, "f64"), "data": "synthetic",
-        "config": workload_config(args),
-        "p50_ms": float(np.percentile(out["lat"], 50)), "p99_ms": float(np.percentile(out["lat"], 99)),
-        "solve_only_per_s": NRHS * 1e3 / out["solve_ms"], "k_mean": out["k_mean"], "n_p_range": out["np_range"],
-        "hbs_build_s": out["build_s"], "gmres_iters": out["iters"] if args.mode in ("gmres", "gmres_bf16") else None,
-        "e2e": {"value": e2e, "unit": "solves/s",
-                "h2d_bytes_per_step": 8 * (2 * N_SRC + 2 * N_SRC * NRHS + 2 * TARGETS) if NRHS == 1 else
-                8 * (4 * NRHS + 4 * NRHS * NRHS + 2 * TARGETS),
-                "d2h_bytes_per_step": 8 * NRHS * (2 * TARGETS + 2 * 16 * P_PANELS)},
+        "metric": "refined-wall solves/s at rel. residual 1e-10", "value": hs["value"], "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": hs["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": MODE_DTYPE[args.mode],
+        "data": "synthetic", "config": workload_config(args),
+        "p50_ms": hs["p50_ms"], "p99_ms": hs["p99_ms"],
+        "solve_only_per_s": hs["solve_only_per_s"], "iters": hs["iters"],
+        "solver_rel_residual_max": hs["solver_rel_residual_max"],
+        "true_rel_residual_max": hs["true_rel_residual_max"], "verified_steps": hs["verified_steps"],
+        "k_mean": hs["k_mean"], "n_p_range": head["np_range"], "hbs_build_s": out["build_s"],
+        "e2e": {"value": hs["e2e"], "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(8 * NRHS * (2 * TARGETS + 2 * head["nn_mean"]))},
         "roofline": roof,
+        "roofline_by_class": by_class,
         "kernel_time_share": share,
-        "roofline_sweep": {"kernel": "HBS inverse sweep (s1, FP64, 1 RHS, L2 flushed)", "ms": out["sweep_ms"],
-                           "hbm_achieved_gbs": achieved, "hbm_frac": achieved / hbm,
-                           "fp64_achieved_tflops": sweep_flops / (out["sweep_ms"] / 1e3) / 1e12,
-                           "fp64_frac": sweep_flops / (out["sweep_ms"] / 1e3) / 1e12 / fp64_peak},
-        "clocks": out["clocks"],
-        "gpu_launches": out["launches"],
+        "roofline_sweep": {"kernel": "HBS inverse sweep (s1, FP64, 1 RHS, L2 flushed)", "ms": sw["ms"],
+                           "hbm_achieved_gbs": sweep_gbs, "hbm_frac": sweep_gbs / hbm,
+                           "fp64_achieved_tflops": sweep_flops / (sw["ms"] / 1e3) / 1e12,
+                           "fp64_frac": sweep_flops / (sw["ms"] / 1e3) / 1e12 / fp64_peak},
+        "clocks": head["clocks"],
+        "gpu_launches": hs["gpu_launches"],
     }
+    if len(out["order"]) > 1:
+        other = out["arms"][out["order"][1]]
+        line["fp64_arm" if out["order"][1] == "fp64_ir" else "compare_arm"] = arm_summary(other, args, world)
+        if "error" not in other:
+            line["speedup_vs_compare"] = hs["value"] / (world * args.steps * NRHS / (other["ms"] / 1e3))
+            diffs = []
+            for s_, t in head["taus"].items():
+                if s_ in other["taus"]:
+                    o = other["taus"][s_]
+                    diffs.append(float(((t - o).norm(dim=1) / o.norm(dim=1)).max()))
+            line["density_rel_diff_vs_compare"] = max(diffs) if diffs else None
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -81,6 +81,16 @@ typedef struct {
                                default 4: the wall points inside are taken
                                explicitly, so a wider circle lowers the
                                A_pk rank toward the block's own)            */
+  double op_tol;            /* tolerance of the operator representation that
+                               residuals are computed with (FGMRES, iterative
+                               refinement; Sec. 4.2); 0 (default) = id_tol.
+                               When smaller than id_tol, rw_hbs_build keeps a
+                               second forward HBS of A_oo at op_tol beside the
+                               inverse at id_tol, and rw_refine_factor /
+                               rw_holes_factor compute the row IDs of Q and
+                               the representation of A_pp at op_tol, so that
+                               A~ + L R matches A_ext to about op_tol while the
+                               reference wall's inverse stays at id_tol      */
 } rw_opts;
 
 typedef struct {
@@ -90,6 +100,8 @@ typedef struct {
   long long inv_elems; /* matrix entries read by one inverse sweep           */
   long long fwd_elems; /* matrix entries read by one forward apply           */
   long long bytes;     /* device bytes held by the handle                    */
+  long long op_fwd_elems; /* entries read by one forward apply of the operator
+                          representation (= fwd_elems unless op_tol < id_tol) */
 } rw_hbs_stats;
 
 typedef struct {
@@ -258,6 +270,23 @@ int rw_stokeslet_data(rw_ref_t r, int n_src, const double* src, int nrhs,
                                  well-conditioned walls in more iterations;
                                  RW_ERR_NOT_CONVERGED where the BF16 rounding
                                  times the conditioning of A_oo exceeds one */
+#define RW_MODE_DIRECT_IR 4   /* the plain FP64 path to a certified residual:
+                                 Algorithm 1 solve, then FP64 iterative
+                                 refinement tau += A_ext^{-1} (g - (A~ + L R)
+                                 tau) with the operator in its op_tol
+                                 representation, until the relative residual
+                                 is <= gmres_tol (at most gmres_maxit
+                                 corrections; iters = corrections made) */
+#define RW_MODE_GMRES_MIXED 5 /* as RW_MODE_GMRES_FP32, with the operator's
+                                 products for nrhs > 8 in double-FP32: every
+                                 FP64 factor of A~ + L R is held as a pair of
+                                 FP32 numbers (hi + lo) and each product and
+                                 sum is compensated (exact FMA product error,
+                                 two-sum accumulation, FP64 every 128 terms),
+                                 so the residual keeps FP64-level accuracy
+                                 (relative error ~1e-14 per product) from the
+                                 FP32 units; Krylov vectors, Hessenberg
+                                 matrix, X and W^{-1} stay FP64 */
 
 /* y = A_nn tau with every entry of the refined operator evaluated on the fly
  * (Sec. 2, Eq. interior_BIE_discretized2 on the refined nodes): the exact
@@ -369,7 +398,11 @@ void rw_batch_free(rw_batch_t b);
 #define RW_KCLASS_INVERSE 3  /* batched Gauss-Jordan inverse                     */
 #define RW_KCLASS_EVAL 4     /* kernel-entry, proxy, node and N-body evaluation  */
 #define RW_KCLASS_OTHER 5    /* copies, gathers, ID bookkeeping                  */
-#define RW_KCLASS_COUNT 6
+#define RW_KCLASS_GEMM_F32 6 /* batched GEMM with FP32 accumulation (FP32 or BF16
+                                matrices): low-precision sweeps, many RHS       */
+#define RW_KCLASS_GEMM_DF 7  /* double-FP32 GEMM: FP64-accurate operator
+                                products of RW_MODE_GMRES_MIXED                 */
+#define RW_KCLASS_COUNT 8
 typedef struct {
   long long launches;
   double ms;

@@ -96,25 +96,6 @@ def matrix(nodes):
     return A
 
 
-def cross_matrix(rows, cols):
-    """A restricted to rows of one node set and columns of a disjoint one:
-    w_j D(x_i, y_j) + w_j n_i n_j^T (no diagonal terms)."""
-    rx = rows["x"][:, None] - cols["x"][None, :]
-    ry = rows["y"][:, None] - cols["y"][None, :]
-    r2 = rx * rx + ry * ry
-    rdn = rx * cols["nx"][None, :] + ry * cols["ny"][None, :]
-    wj = cols["w"][None, :]
-    fac = wj * rdn / (np.pi * r2 * r2)
-    M = np.empty((2 * rows["x"].size, 2 * cols["x"].size))
-    ni = (rows["nx"][:, None], rows["ny"][:, None])
-    nj = (cols["nx"][None, :], cols["ny"][None, :])
-    rr = (rx, ry)
-    for a in range(2):
-        for b in range(2):
-            M[a::2, b::2] = fac * rr[a] * rr[b] + ni[a] * nj[b] * wj
-    return M
-
-
 def velocity(nodes, tau, tx, ty):
     """Interior velocity u(x) = sum_j w_j D(x, y_j) tau_j at targets.
 

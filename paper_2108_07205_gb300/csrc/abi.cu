@@ -74,6 +74,7 @@ rw::Opts to_opts(const rw_opts* o) {
   rw::require(o->hole_div_ratio > o->bas_ratio, "opts need hole_div_ratio > bas_ratio");
   rw::require(o->sketch_cols >= 64, "opts.sketch_cols must be >= 64");
   rw::require(o->gmres_tol > 0 && o->gmres_maxit >= 1 && o->gmres_restarts >= 1, "bad GMRES options");
+  rw::require(o->op_tol == 0.0 || (o->op_tol > 0 && o->op_tol < 1), "opts.op_tol must be 0 or in (0, 1)");
   r.leaf_points = o->leaf_points;
   r.id_tol = o->id_tol;
   r.n_proxy = o->n_proxy;
@@ -88,6 +89,7 @@ rw::Opts to_opts(const rw_opts* o) {
   r.gmres_restarts = o->gmres_restarts;
   r.seed = o->seed;
   r.hole_div_ratio = o->hole_div_ratio;
+  r.op_tol = o->op_tol;
   return r;
 }
 
@@ -142,6 +144,7 @@ int rw_default_opts(rw_opts* o) {
   o->gmres_restarts = d.gmres_restarts;
   o->seed = d.seed;
   o->hole_div_ratio = d.hole_div_ratio;
+  o->op_tol = d.op_tol;
   return RW_OK;
 }
 
@@ -179,10 +182,7 @@ int rw_hbs_build(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_h
     auto all = w.nodes.buf.download(s);
     w.nodes.hx.assign(all.begin(), all.begin() + 16 * P);
     w.nodes.hy.assign(all.begin() + 16 * P, all.begin() + 32 * P);
-    w.hbs.build(w.nodes, w.opts, s);
-    w.hbs.make_fp32(s);
-    w.hbs.make_bf16(s);
-    RW_CUDA(cudaStreamSynchronize(s));
+    w.build_hbs(s);
   });
   if (rc == RW_OK) *out = h.release();
   return rc;
@@ -206,10 +206,7 @@ int rw_hbs_build_nodes(const rw_nodes* nodes, const rw_opts* opts, void* stream,
     RW_CUDA(cudaMemcpyAsync(w.nodes.buf.p, hn.data(), hn.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     w.nodes.hx.assign(hn.begin(), hn.begin() + n);
     w.nodes.hy.assign(hn.begin() + n, hn.begin() + 2 * size_t(n));
-    w.hbs.build(w.nodes, w.opts, s);
-    w.hbs.make_fp32(s);
-    w.hbs.make_bf16(s);
-    RW_CUDA(cudaStreamSynchronize(s));
+    w.build_hbs(s);
   });
   if (rc == RW_OK) *out = h.release();
   return rc;
@@ -223,7 +220,8 @@ int rw_hbs_stats_get(rw_hbs_t h, rw_hbs_stats* st) {
   st->max_rank = b.max_rank;
   st->inv_elems = b.inv_elems;
   st->fwd_elems = b.fwd_elems;
-  st->bytes = (long long)(b.bytes + h->wall.nodes.buf.bytes());
+  st->bytes = (long long)(b.bytes + h->wall.hbs_op.bytes + h->wall.nodes.buf.bytes());
+  st->op_fwd_elems = h->wall.op().fwd_elems;
   return RW_OK;
 }
 
@@ -371,9 +369,7 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
              int mode, void* stream, rw_info* info) {
   if (!r || !g || !tau || nrhs < 1 || n_targets < 0) return fail(RW_ERR_INVALID, "rw_solve: bad argument");
   if (n_targets > 0 && (!targets || !u)) return fail(RW_ERR_INVALID, "rw_solve: targets and u required");
-  if (mode != RW_MODE_DIRECT && mode != RW_MODE_GMRES_FP32 && mode != RW_MODE_DIRECT_REFINED &&
-      mode != RW_MODE_GMRES_BF16)
-    return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
+  if (mode < RW_MODE_DIRECT || mode > RW_MODE_GMRES_MIXED) return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
   int iters = 0;
   double relres = 0.0;
   int rc = guarded([&] {
@@ -386,8 +382,10 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     } else if (mode == RW_MODE_DIRECT_REFINED) {
       f.solve_refined(ag.p, at.p, nrhs, 1, s);
       iters = 1;
+    } else if (mode == RW_MODE_DIRECT_IR) {
+      f.solve_ir(ag.p, at.p, nrhs, s, &iters, &relres);
     } else {
-      f.solve_gmres(ag.p, at.p, nrhs, s, &iters, &relres, mode == RW_MODE_GMRES_BF16);
+      f.solve_gmres(ag.p, at.p, nrhs, s, &iters, &relres, mode == RW_MODE_GMRES_BF16, mode == RW_MODE_GMRES_MIXED);
     }
     if (n_targets > 0) {
       Arg ax(targets, size_t(2) * n_targets, true, s), au(u, size_t(2) * n_targets * nrhs, false, s);
@@ -396,8 +394,12 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     }
     at.finish(s);
     RW_CUDA(cudaStreamSynchronize(s));
-    if ((mode == RW_MODE_GMRES_FP32 || mode == RW_MODE_GMRES_BF16) && relres > f.wall->opts.gmres_tol)
+    if ((mode == RW_MODE_GMRES_FP32 || mode == RW_MODE_GMRES_BF16 || mode == RW_MODE_GMRES_MIXED) &&
+        relres > f.wall->opts.gmres_tol)
       throw rw::Error(RW_ERR_NOT_CONVERGED, "rw_solve: GMRES stopped at relative residual " + std::to_string(relres));
+    if (mode == RW_MODE_DIRECT_IR && relres > f.wall->opts.gmres_tol)
+      throw rw::Error(RW_ERR_NOT_CONVERGED,
+                      "rw_solve: iterative refinement stopped at relative residual " + std::to_string(relres));
   });
   if (info) {
     info->iters = iters;

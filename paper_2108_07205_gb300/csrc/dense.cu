@@ -1517,30 +1517,6 @@ void matvec<double, double>(const std::vector<GemvProb<double>>& probs, int nrhs
   }
 }
 
-template <class MT>
-static void matvec_f32(const std::vector<GemvProb<float, MT>>& probs, int nrhs, cudaStream_t s) {
-  if (probs.empty() || nrhs <= 0) return;
-  for (int r0 = 0; r0 < nrhs; r0 += 8) {
-    const int nr = std::min(8, nrhs - r0);
-    std::vector<GemvProb<float, MT>> ps = probs;
-    for (auto& p : ps) { p.x += size_t(r0) * p.ldx; p.y += size_t(r0) * p.ldy; }
-    size_t sc = gemv_scratch_elems(ps, nr);
-    TBuf<float> scratch(sc, s);
-    batched_gemv(ps, nr, scratch.p, s);
-  }
-}
-
-template <>
-void matvec<float, float>(const std::vector<GemvProb<float>>& probs, int nrhs, cudaStream_t s) {
-  matvec_f32(probs, nrhs, s);
-}
-
-template <>
-void matvec<float, __nv_bfloat16>(const std::vector<GemvProb<float, __nv_bfloat16>>& probs, int nrhs,
-                                  cudaStream_t s) {
-  matvec_f32(probs, nrhs, s);
-}
-
 void block_inverse(const double* A, double* Ainv, int n, int nb, int* flag, cudaStream_t s) {
   require(n >= 1 && nb >= 1, "block_inverse: bad size");
   nb = std::min(nb, n);

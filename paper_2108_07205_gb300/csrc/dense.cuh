@@ -53,10 +53,49 @@ template <class T>
 void gemv_into(const std::vector<GemvProb<T>>& probs, int nrhs, void* desc, T* scratch, cudaStream_t s);
 
 // y = alpha A x + beta y for a problem list and any nrhs: GEMV kernels for
-// nrhs <= 8 (chunks of 8 for FP32), the tiled GEMM above that (FP64).
+// nrhs <= 8, the tiled GEMMs above that (FP64, FP32 accumulation for FP32 and
+// BF16 matrices, double-FP32 for float2 matrices with FP64 vectors).
 // Temporaries are stream-ordered.
 template <class T, class MT = T>
 void matvec(const std::vector<GemvProb<T, MT>>& probs, int nrhs, cudaStream_t s);
+
+// Batched GEMM with FP32 accumulation for the low-precision sweeps with many
+// right-hand sides: C (m x n, float) = alpha A B + beta C with A column-major
+// in MT (float, or __nv_bfloat16 widened as it is read) and B float.  Same
+// tiling and split-K rule as batched_gemm; split partial sums are added in a
+// fixed order.
+template <class MT>
+struct GemmF32Prob {
+  const MT* A;
+  const float* B;
+  float* C;
+  int m, n, k;
+  int lda, ldb, ldc;
+  float alpha, beta;
+};
+template <class MT>
+void batched_gemm_f32(const std::vector<GemmF32Prob<MT>>& probs, cudaStream_t s);
+
+// Double-FP32 ("df") matrices: an FP64 matrix held as the FP32 pairs
+// (hi, lo) = (fl32(a), fl32(a - hi)), interleaved as float2.  hi + lo carries
+// 48 bits of a's significand (relative error <= 2^-48 ~ 3.6e-15).
+void copy_d2df(const double* in, float2* out, size_t n, cudaStream_t s);
+// C (m x n, FP64) = alpha A B + beta C with A df (column-major) and B FP64
+// (split into df pairs as it is read).  Every product is formed exactly from
+// FP32 operations (the rounding error of hi * hi by an FMA, the cross terms
+// hi * lo by FMAs), sums are compensated (two-sum of the hi products, the
+// errors and cross terms in a second FP32 accumulator) and flushed to FP64
+// every 128 terms of the inner dimension, so the result keeps FP64-level
+// accuracy (~1e-14 relative per product) while running on the FP32 units.
+struct GemmDfProb {
+  const float2* A;
+  const double* B;
+  double* C;
+  int m, n, k;
+  int lda, ldb, ldc;
+  double alpha, beta;
+};
+void batched_gemm_df(const std::vector<GemmDfProb>& probs, cudaStream_t s);
 
 // Inverse of square matrices by Gauss-Jordan elimination with partial
 // pivoting (the pivot sequence of LU with partial pivoting).  A is read, Ainv

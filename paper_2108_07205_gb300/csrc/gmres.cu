@@ -1,12 +1,17 @@
 // Mixed-precision path (Sec. 4.2): flexible GMRES in FP64 on the extended
 // system (A~ + L R) tau_ext = g_ext (Eq. ELS_approximate), with A~ applied by
-// the FP64 HBS forward representations of A_oo and A_pp and L R by the FP64
-// factors.  The preconditioner is the Woodbury inverse of Sec. 4.2 whose
-// A~^{-1} applications are HBS inverse sweeps in FP32 (or with the matrices
-// in BF16, FP32 accumulation); X and W^{-1} stay FP64.
+// the HBS forward representations of A_oo and A_pp and L R by its factors, all
+// at the operator tolerance (op_tol).  The preconditioner is the Woodbury
+// inverse of Sec. 4.2 whose A~^{-1} applications are HBS inverse sweeps in
+// FP32 (or with the matrices in BF16, FP32 accumulation); W^{-1} stays FP64.
+// In the mixed mode the operator's products run in double-FP32 (FP64-level
+// accuracy on the FP32 units) and the preconditioner's Woodbury correction in
+// FP32; otherwise they are FP64.
 // Right preconditioning keeps the monitored residual equal to the true one.
 // Every right-hand side runs its own Krylov space; the columns advance in
 // lockstep and stop together once all have converged.
+// Also the plain FP64 path to a certified residual: Algorithm 1 followed by
+// FP64 iterative refinement against the same operator (solve_ir).
 #include "refine.cuh"
 #include <algorithm>
 #include <cmath>
@@ -63,11 +68,131 @@ __global__ void k_f2d_v(const float* in, double* out, size_t n) {
 
 int g1(long long n) { return int(std::max<long long>(1, std::min<long long>((n + 255) / 256, 2048))); }
 
+// Per-column squared norms (or dot products) of ext-space blocks, on the host.
+std::vector<double> col_dots(const double* ao, const double* ap, const double* bo, const double* bp, int no, int np,
+                             int nrhs, int nb, double* dots, cudaStream_t s) {
+  k_coldot2<<<dim3(nrhs, nb), 256, 0, s>>>(ao, bo, no, no, ap, bp, np, np, nrhs, dots);
+  RW_CHECK_LAUNCH();
+  std::vector<double> h(size_t(nb) * nrhs);
+  RW_CUDA(cudaMemcpyAsync(h.data(), dots, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RW_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
 }  // namespace
 
-void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters_out,
-                             double* relres_out, bool bf16) const {
+void Refinement::make_mixed() const {
+  if (has_mixed) return;
+  cudaStream_t s = streams.main;
+  AllocStreamScope scope(s);
+  for (auto pr : {std::make_pair(&Lo, &Lo2), std::make_pair(&Lp, &Lp2), std::make_pair(&Rkc, &Rkc2),
+                  std::make_pair(&Rkp, &Rkp2), std::make_pair(&Rpk, &Rpk2)}) {
+    pr.second->alloc(pr.first->n);
+    copy_d2df(pr.first->p, pr.second->p, pr.first->n, s);
+  }
+  for (auto pr : {std::make_pair(&Rkc, &Rkc32), std::make_pair(&Rkp, &Rkp32), std::make_pair(&Rpk, &Rpk32),
+                  std::make_pair(&Xo, &Xo32), std::make_pair(&Xp, &Xp32)}) {
+    pr.second->alloc(pr.first->n);
+    copy_d2f(pr.first->p, pr.second->p, pr.first->n, s);
+  }
+  hpp.make_df(s);
+  RW_CUDA(cudaStreamSynchronize(s));
+  has_mixed = true;
+}
+
+void Refinement::apply_els_df(const double* xo, const double* xp, double* yo, double* yp, int nrhs,
+                              cudaStream_t s) const {
+  make_mixed();
+  wall->op().apply_forward_df(xo, yo, nrhs, s);
+  hpp.apply_forward_df(xp, yp, nrhs, s);
+  if (k == 0) return;
+  typedef GemvProb<double, float2> GP;
+  TBuf<double> xc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s);
+  if (Nc) gather_scatter(xo, 2 * No, dc.p, xc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
+  std::vector<GP> p1;
+  if (kk && Nc) p1.push_back(GP{Rkc2.p, xc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
+  if (kpk) p1.push_back(GP{Rpk2.p, xo, r.p + kk, kpk, 2 * No, kpk, 2 * No, k, 1.0, 0.0});
+  matvec<double, float2>(p1, nrhs, s);
+  if (kk && Np) matvec<double, float2>({GP{Rkp2.p, xp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, Nc ? 1.0 : 0.0}}, nrhs, s);
+  std::vector<GP> p2;
+  if (kk) p2.push_back(GP{Lo2.p, r.p, yo, 2 * No, kk, 2 * No, k, 2 * No, 1.0, 1.0});
+  if (kpk) p2.push_back(GP{Lp2.p, r.p + kk, yp, 2 * Np, kpk, 2 * Np, k, 2 * Np, 1.0, 1.0});
+  matvec<double, float2>(p2, nrhs, s);
+}
+
+void Refinement::woodbury_correct_f32(float* yo, float* yp, int nrhs, cudaStream_t s) const {
+  if (k == 0) return;
+  make_mixed();
+  typedef GemvProb<float> GP;
+  TBuf<float> yc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s), z(size_t(k) * nrhs, s);
+  TBuf<double> r64(size_t(k) * nrhs, s), z64(size_t(k) * nrhs, s);
+  if (Nc) gather_scatter_f32(yo, 2 * No, dc.p, yc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
+  std::vector<GP> p1;
+  if (kk && Nc) p1.push_back(GP{Rkc32.p, yc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
+  if (kpk) p1.push_back(GP{Rpk32.p, yo, r.p + kk, kpk, 2 * No, kpk, 2 * No, k, 1.0, 0.0});
+  matvec<float>(p1, nrhs, s);
+  if (kk && Np) matvec<float>({GP{Rkp32.p, yp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, Nc ? 1.0 : 0.0}}, nrhs, s);
+  // z = W^{-1} r in FP64 (the capacitance system stays FP64)
+  k_f2d_v<<<g1(size_t(k) * nrhs), 256, 0, s>>>(r.p, r64.p, size_t(k) * nrhs);
+  RW_CHECK_LAUNCH();
+  matvec<double>({GemvProb<double>{Winv.p, r64.p, z64.p, k, k, k, k, k, 1.0, 0.0}}, nrhs, s);
+  k_d2f_v<<<g1(size_t(k) * nrhs), 256, 0, s>>>(z64.p, z.p, size_t(k) * nrhs);
+  RW_CHECK_LAUNCH();
+  std::vector<GP> p2;
+  if (kk) p2.push_back(GP{Xo32.p, z.p, yo, 2 * No, kk, 2 * No, k, 2 * No, -1.0, 1.0});
+  if (kpk) p2.push_back(GP{Xp32.p, z.p + kk, yp, 2 * Np, kpk, 2 * Np, k, 2 * Np, -1.0, 1.0});
+  matvec<float>(p2, nrhs, s);
+}
+
+void Refinement::solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters_out,
+                          double* relres_out) const {
   const Opts& o = wall->opts;
+  const int no = 2 * No, np = 2 * Np;
+  TBuf<double> go(size_t(no) * nrhs, s), gp(size_t(np) * nrhs, s), xo(size_t(no) * nrhs, s), xp(size_t(np) * nrhs, s);
+  TBuf<double> ro(size_t(no) * nrhs, s), rp(size_t(np) * nrhs, s), dso(size_t(no) * nrhs, s), dsp(size_t(np) * nrhs, s);
+  TBuf<double> dots(size_t(nrhs), s);
+  fill_zero(go.p, go.n, s);
+  gather_scatter(g, 2 * Nn, n_from_o.p, go.p, no, n_to_o.p, nko, nrhs, s);
+  gather_scatter(g, 2 * Nn, n_from_p.p, gp.p, np, n_to_p.p, nkp, nrhs, s);
+  // Algorithm 1 in ext space: y = A~^{-1} v, then the Woodbury correction
+  auto direct = [&](const double* vo, const double* vp, double* yo, double* yp) {
+    wall->hbs.apply_inverse_levels(vo, yo, nrhs, s);
+    hpp.apply_inverse_levels(vp, yp, nrhs, s);
+    woodbury_correct(yo, yp, nrhs, s);
+  };
+  direct(go.p, gp.p, xo.p, xp.p);
+  std::vector<double> gn = col_dots(go.p, gp.p, go.p, gp.p, no, np, nrhs, 1, dots.p, s);
+  int it = 0;
+  double worst = 0.0;
+  for (;; ++it) {
+    // r = g - (A~ + L R) x
+    apply_els(xo.p, xp.p, ro.p, rp.p, nrhs, s);
+    axpby(go.p, ro.p, ro.n, 1.0, -1.0, s);
+    axpby(gp.p, rp.p, rp.n, 1.0, -1.0, s);
+    std::vector<double> rn = col_dots(ro.p, rp.p, ro.p, rp.p, no, np, nrhs, 1, dots.p, s);
+    worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) worst = std::max(worst, gn[c] > 0 ? std::sqrt(rn[c] / gn[c]) : 0.0);
+    if (worst <= o.gmres_tol || it >= o.gmres_maxit) break;
+    direct(ro.p, rp.p, dso.p, dsp.p);
+    axpby(dso.p, xo.p, xo.n, 1.0, 1.0, s);
+    axpby(dsp.p, xp.p, xp.n, 1.0, 1.0, s);
+  }
+  gather_scatter(xo.p, no, n_to_o.p, tau, 2 * Nn, n_from_o.p, nko, nrhs, s);
+  gather_scatter(xp.p, np, n_to_p.p, tau, 2 * Nn, n_from_p.p, nkp, nrhs, s);
+  *iters_out = it;
+  *relres_out = worst;
+}
+
+void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters_out,
+                             double* relres_out, bool bf16, bool mixed) const {
+  const Opts& o = wall->opts;
+  // double-FP32 products only pay off once the right-hand sides fill the
+  // GEMM tiles; below that the mixed mode is the FP32 mode
+  mixed = mixed && nrhs > 8;
+  auto op = [&](const double* xo_, const double* xp_, double* yo_, double* yp_) {
+    if (mixed) apply_els_df(xo_, xp_, yo_, yp_, nrhs, s);
+    else apply_els(xo_, xp_, yo_, yp_, nrhs, s);
+  };
   require(wall->hbs.has_fp32 && hpp.has_fp32, "GMRES path: FP32 sweep data missing");
   require(!bf16 || (wall->hbs.has_bf16 && hpp.has_bf16), "GMRES path: BF16 sweep data missing");
   const int m = o.gmres_maxit;
@@ -117,10 +242,11 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
       wall->hbs.apply_inverse_f32(fo_in.p, fo_out.p, nrhs, s);
       hpp.apply_inverse_f32(fp_in.p, fp_out.p, nrhs, s);
     }
+    if (mixed) woodbury_correct_f32(fo_out.p, fp_out.p, nrhs, s);
     k_f2d_v<<<g1(size_t(no) * nrhs), 256, 0, s>>>(fo_out.p, zo, size_t(no) * nrhs);
     k_f2d_v<<<g1(size_t(np) * nrhs), 256, 0, s>>>(fp_out.p, zp, size_t(np) * nrhs);
     RW_CHECK_LAUNCH();
-    woodbury_correct(zo, zp, nrhs, s);
+    if (!mixed) woodbury_correct(zo, zp, nrhs, s);
   };
 
   std::vector<double> gnorm = coldots(go.p, gp.p, go.p, gp.p, 1);
@@ -129,7 +255,7 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
   double worst = 0.0;
   for (int cycle = 0; cycle < o.gmres_restarts; ++cycle) {
     // r = g - A x
-    apply_els(xo.p, xp.p, wo.p, wp.p, nrhs, s);
+    op(xo.p, xp.p, wo.p, wp.p);
     std::vector<double> minus1(nrhs, -1.0), one(nrhs, 1.0);
     RW_CUDA(cudaMemcpyAsync(ro.p, go.p, go.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RW_CUDA(cudaMemcpyAsync(rp.p, gp.p, gp.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -154,7 +280,7 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
       double* zoj = Zo.p + size_t(j) * no * nrhs;
       double* zpj = Zp.p + size_t(j) * np * nrhs;
       precond(Vo.p + size_t(j) * no * nrhs, Vp.p + size_t(j) * np * nrhs, zoj, zpj);
-      apply_els(zoj, zpj, wo.p, wp.p, nrhs, s);
+      op(zoj, zpj, wo.p, wp.p);
       // classical Gram-Schmidt, twice
       for (int pass = 0; pass < 2; ++pass) {
         std::vector<double> h = coldots(wo.p, wp.p, Vo.p, Vp.p, j + 1);
@@ -204,7 +330,7 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
     if (j > 0) comb(xo.p, xp.p, Zo.p, Zp.p, j, yc);
   }
   // final true residual
-  apply_els(xo.p, xp.p, wo.p, wp.p, nrhs, s);
+  op(xo.p, xp.p, wo.p, wp.p);
   RW_CUDA(cudaMemcpyAsync(ro.p, go.p, go.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   RW_CUDA(cudaMemcpyAsync(rp.p, gp.p, gp.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   comb(ro.p, rp.p, wo.p, wp.p, 1, std::vector<double>(nrhs, -1.0));

@@ -4,6 +4,7 @@
 // matrix entry, factorisation and product is computed by the kernels in
 // dense.cu / eval.cu.
 #include "hbs.cuh"
+#include <mutex>
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -391,7 +392,7 @@ Geo node_geo(const std::vector<double>& x, const std::vector<double>& y, int lo,
 
 }  // namespace
 
-void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
+void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s, bool fwd_only) {
   Trace tr(s, "hbs");
   N = nodes.n;
   require(N >= 1, "HBS: empty node set");
@@ -495,6 +496,7 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s) {
     } else {
       order_after_alloc();  // the leaf D blocks and this level's U, V*
     }
+    if (fwd_only) return;
     std::vector<int> mm(nn);
     size_t sG = 0;
     LV.oG.resize(nn);
@@ -937,9 +939,43 @@ void Hbs::apply_inverse_bf16(const float* b, float* x, int nrhs, cudaStream_t s)
 }
 
 void Hbs::apply_forward(const double* xin, double* y, int nrhs, cudaStream_t s) const {
+  forward_impl<double>(xin, y, nrhs, s);
+}
+
+void Hbs::apply_forward_df(const double* xin, double* y, int nrhs, cudaStream_t s) const {
+  make_df(s);
+  forward_impl<float2>(xin, y, nrhs, s);
+}
+
+void Hbs::make_df(cudaStream_t s) const {
+  // once per representation; the wall's copy may be asked for by several
+  // host threads (serving workers) at the same time
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (has_df) return;
+  for (int l = 0; l <= L; ++l) {
+    const Level& LV = lev[l];
+    for (auto pr : {std::make_pair(&LV.U, &LV.U2), std::make_pair(&LV.Vt, &LV.Vt2), std::make_pair(&LV.B, &LV.B2),
+                    std::make_pair(&LV.D, &LV.D2)}) {
+      pr.second->alloc(pr.first->n);
+      copy_d2df(pr.first->p, pr.second->p, pr.first->n, s);
+    }
+  }
+  RW_CUDA(cudaStreamSynchronize(s));
+  has_df = true;
+}
+
+template <class MT>
+void Hbs::forward_impl(const double* xin, double* y, int nrhs, cudaStream_t s) const {
+  // matrices in MT: the FP64 factors, or their double-FP32 copies
+  auto pick = [](const DBuf<double>& d, const DBuf<float2>& f) -> const MT* {
+    if constexpr (std::is_same<MT, double>::value) return d.p;
+    else return f.p;
+  };
+  typedef GemvProb<double, MT> GP;
   const int ld = 2 * N;
   if (L == 0) {
-    matvec<double>({GemvProb<double>{lev[0].D.p, xin, y, ld, ld, ld, ld, ld, 1.0, 0.0}}, nrhs, s);
+    matvec<double, MT>({GP{pick(lev[0].D, lev[0].D2), xin, y, ld, ld, ld, ld, ld, 1.0, 0.0}}, nrhs, s);
     return;
   }
   std::vector<TBuf<double>> xh(L + 1), yh(L + 1);
@@ -952,26 +988,26 @@ void Hbs::apply_forward(const double* xin, double* y, int nrhs, cudaStream_t s) 
     const int l = L, h0 = 1 << l, nn = 1 << l;
     const Level& LV = lev[l];
     const int K = LV.koff.back();
-    std::vector<GemvProb<double>> ps;
+    std::vector<GP> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& nd = node[h0 + t];
       const int n = 2 * (nd.hi - nd.lo);
-      ps.push_back(GemvProb<double>{LV.Vt.p + LV.oVt[t], xin + 2 * nd.lo, xh[l].p + LV.koff[t], nd.k, n, nd.k, ld, K, 1.0, 0.0});
-      ps.push_back(GemvProb<double>{LV.D.p + LV.oD[t], xin + 2 * nd.lo, y + 2 * nd.lo, n, n, n, ld, ld, 1.0, 0.0});
+      ps.push_back(GP{pick(LV.Vt, LV.Vt2) + LV.oVt[t], xin + 2 * nd.lo, xh[l].p + LV.koff[t], nd.k, n, nd.k, ld, K, 1.0, 0.0});
+      ps.push_back(GP{pick(LV.D, LV.D2) + LV.oD[t], xin + 2 * nd.lo, y + 2 * nd.lo, n, n, n, ld, ld, 1.0, 0.0});
     }
-    matvec<double>(ps, nrhs, s);
+    matvec<double, MT>(ps, nrhs, s);
   }
   for (int l = L - 1; l >= 1; --l) {
     const int h0 = 1 << l, nn = 1 << l;
     const Level& LV = lev[l];
     const Level& LC = lev[l + 1];
     const int K = LV.koff.back(), KC = LC.koff.back();
-    std::vector<GemvProb<double>> ps;
+    std::vector<GP> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& nd = node[h0 + t];
-      ps.push_back(GemvProb<double>{LV.Vt.p + LV.oVt[t], xh[l + 1].p + LC.koff[2 * t], xh[l].p + LV.koff[t], nd.k, nd.m, nd.k, KC, K, 1.0, 0.0});
+      ps.push_back(GP{pick(LV.Vt, LV.Vt2) + LV.oVt[t], xh[l + 1].p + LC.koff[2 * t], xh[l].p + LV.koff[t], nd.k, nd.m, nd.k, KC, K, 1.0, 0.0});
     }
-    matvec<double>(ps, nrhs, s);
+    matvec<double, MT>(ps, nrhs, s);
   }
   // sibling interactions at every parent, then interpolation down
   for (int l = 0; l <= L - 1; ++l) {
@@ -981,35 +1017,35 @@ void Hbs::apply_forward(const double* xin, double* y, int nrhs, cudaStream_t s) 
     const int KC = LC.koff.back();
     if (l >= 1) {
       const int K = LV.koff.back();
-      std::vector<GemvProb<double>> ps;
+      std::vector<GP> ps;
       for (int t = 0; t < nn; ++t) {
         const HbsNode& nd = node[h0 + t];
-        ps.push_back(GemvProb<double>{LV.U.p + LV.oU[t], yh[l].p + LV.koff[t], yh[l + 1].p + LC.koff[2 * t], nd.m, nd.k, nd.m, K, KC, 1.0, 0.0});
+        ps.push_back(GP{pick(LV.U, LV.U2) + LV.oU[t], yh[l].p + LV.koff[t], yh[l + 1].p + LC.koff[2 * t], nd.m, nd.k, nd.m, K, KC, 1.0, 0.0});
       }
-      matvec<double>(ps, nrhs, s);
+      matvec<double, MT>(ps, nrhs, s);
     }
-    std::vector<GemvProb<double>> ps;
+    std::vector<GP> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& a = node[2 * (h0 + t)];
       const HbsNode& b = node[2 * (h0 + t) + 1];
       const int ia = LC.koff[2 * t], ib = LC.koff[2 * t + 1];
       const double beta = (l >= 1) ? 1.0 : 0.0;
-      ps.push_back(GemvProb<double>{LV.B.p + LV.oB12[t], xh[l + 1].p + ib, yh[l + 1].p + ia, a.k, b.k, a.k, KC, KC, 1.0, beta});
-      ps.push_back(GemvProb<double>{LV.B.p + LV.oB21[t], xh[l + 1].p + ia, yh[l + 1].p + ib, b.k, a.k, b.k, KC, KC, 1.0, beta});
+      ps.push_back(GP{pick(LV.B, LV.B2) + LV.oB12[t], xh[l + 1].p + ib, yh[l + 1].p + ia, a.k, b.k, a.k, KC, KC, 1.0, beta});
+      ps.push_back(GP{pick(LV.B, LV.B2) + LV.oB21[t], xh[l + 1].p + ia, yh[l + 1].p + ib, b.k, a.k, b.k, KC, KC, 1.0, beta});
     }
-    matvec<double>(ps, nrhs, s);
+    matvec<double, MT>(ps, nrhs, s);
   }
   {
     const int l = L, h0 = 1 << l, nn = 1 << l;
     const Level& LV = lev[l];
     const int K = LV.koff.back();
-    std::vector<GemvProb<double>> ps;
+    std::vector<GP> ps;
     for (int t = 0; t < nn; ++t) {
       const HbsNode& nd = node[h0 + t];
       const int n = 2 * (nd.hi - nd.lo);
-      ps.push_back(GemvProb<double>{LV.U.p + LV.oU[t], yh[l].p + LV.koff[t], y + 2 * nd.lo, n, nd.k, n, K, ld, 1.0, 1.0});
+      ps.push_back(GP{pick(LV.U, LV.U2) + LV.oU[t], yh[l].p + LV.koff[t], y + 2 * nd.lo, n, nd.k, n, K, ld, 1.0, 1.0});
     }
-    matvec<double>(ps, nrhs, s);
+    matvec<double, MT>(ps, nrhs, s);
   }
 }
 

@@ -26,6 +26,12 @@ struct Opts {
   int gmres_restarts = 4;
   unsigned long long seed = 0x5eed2108ull;
   double hole_div_ratio = 4.0;
+  // Tolerance of the operator used for residuals (FGMRES and iterative
+  // refinement); 0: the same as id_tol.  When tighter, the wall keeps a
+  // second forward representation at op_tol and a refinement's IDs and A_pp
+  // are computed at op_tol.
+  double op_tol = 0.0;
+  double factor_tol() const { return (op_tol > 0.0 && op_tol < id_tol) ? op_tol : id_tol; }
 };
 
 // A list of row-interpolative decompositions evaluated on the fly: each job
@@ -96,6 +102,7 @@ class Hbs {
     std::vector<int> koff;  // prefix sums of ranks at this level (size nn+1)
     DBuf<float> G32, E32, F32;
     DBuf<__nv_bfloat16> G16, E16, F16;  // BF16 copies (preconditioner sweeps)
+    mutable DBuf<float2> U2, Vt2, B2, D2;  // double-FP32 copies of the forward factors (made on first use)
   };
   std::vector<Level> lev;
   long long inv_elems = 0, fwd_elems = 0;
@@ -105,7 +112,8 @@ class Hbs {
   // Build from a node set (positions on host in `nodes.hx/hy` for planning):
   // compression level by level on s, each level's inverse on a second stream
   // as soon as that level is compressed (synchronised before returning).
-  void build(const Nodes& nodes, const Opts& o, cudaStream_t s);
+  // fwd_only: the forward representation (U, V*, B, D) alone, no inverse.
+  void build(const Nodes& nodes, const Opts& o, cudaStream_t s, bool fwd_only = false);
   // Single-leaf representation of a dense matrix A (2 npts x 2 npts, column
   // major; the handle takes it over): the forward apply uses A, the inverse
   // sweeps its inverse.  Throws RW_ERR_SINGULAR if A cannot be inverted.
@@ -122,6 +130,10 @@ class Hbs {
   void apply_inverse_bf16(const float* b, float* x, int nrhs, cudaStream_t s) const;
   // y = A x via the forward representation.
   void apply_forward(const double* x, double* y, int nrhs, cudaStream_t s) const;
+  // The same with the products in double-FP32 (copies made on first use).
+  void apply_forward_df(const double* x, double* y, int nrhs, cudaStream_t s) const;
+  void make_df(cudaStream_t s) const;
+  mutable bool has_df = false;
   void make_fp32(cudaStream_t s);
   void make_bf16(cudaStream_t s);
   bool has_fp32 = false, has_bf16 = false;
@@ -139,6 +151,8 @@ class Hbs {
  private:
   template <class T, class MT = T>
   void sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const;
+  template <class MT>
+  void forward_impl(const double* x, double* y, int nrhs, cudaStream_t s) const;
 };
 
 }  // namespace rw

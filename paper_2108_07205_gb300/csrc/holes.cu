@@ -31,6 +31,9 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
   AllocStreamScope alloc_scope(s);
   Trace tr(s, "holes");
   const Opts& o = w.opts;
+  // IDs (and A_pp) at the operator tolerance when that is tighter: the
+  // factors then serve as the accurate operator for residuals as well
+  const double ftol = o.factor_tol();
   const int nh = int(hs.size());
   require(nh >= 1 && nh <= 8, "holes: 1 to 8 holes");
   int np = 0;
@@ -183,7 +186,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
       cs.ncirc = nh;
       cs.circ = dcirc_bas.p;
       if (nh == 1) { cs.cx = circ_bas[0]; cs.cy = circ_bas[1]; cs.R = circ_bas[2]; cs.ncirc = 0; cs.circ = nullptr; }
-      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
+      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
     } catch (...) { e2 = std::current_exception(); }
   };
   std::thread th1(task1), th2(task2);
@@ -196,7 +199,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
     {
       IdMatProb cs{};
       cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
-      tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
+      tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, ftol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
     }
     // A_pk per hole: rows of [A_{p,div} | A_pk^near]
     for (int h = 0; h < nh; ++h) {
@@ -206,7 +209,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
       cs.n1 = int(near_h[h].size()); cs.e1 = dnear_h[h].p;
       cs.cx = circ_div[3 * h]; cs.cy = circ_div[3 * h + 1]; cs.R = circ_div[3 * h + 2];
       cs.M = o.n_proxy_refine; cs.normal = 0;
-      tp[h] = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width,
+      tp[h] = tree_row_id(VP, prow, cs, VW, false, VW, false, ftol, o.sketch_cols, o.sketch_width,
                           o.seed + 303 + h, 128, s);
     }
   } catch (...) { e0 = std::current_exception(); }
@@ -253,7 +256,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
   // taken explicitly) their ranks are already close to the blocks' own
   // (1920-panel channel, three holes: k_pk 505 -> 262 against 2 radii;
   // recompressing them as well gains 3 % of k for 30 % more time).
-  const double rtol = 0.1 * o.id_tol;
+  const double rtol = 0.1 * ftol;
   if (recompress_enabled()) {
     IdMatProb ck{};
     ck.n2 = 2 * Np; ck.e2 = dall_p.p;

@@ -63,28 +63,17 @@ struct Arena {
   }
 };
 
-void gemv_from_arena(Arena& ar, const std::vector<rw::GemvProb<double>>& ps, int nrhs, cudaStream_t s) {
-  size_t db = 0, se = 0;
-  rw::gemv_into_sizes(ps, nrhs, &db, &se);
-  void* desc = ar.take<char>(db);
-  double* sc = se ? ar.take<double>(se) : nullptr;
-  rw::gemv_into(ps, nrhs, desc, sc, s);
-}
-
-// The level-by-level inverse sweep of the HBS representation (same
-// operations and order as Hbs::sweep_inverse) with scratch from the arena.
-void sweep_noalloc(const rw::Hbs& H, const double* b, double* x, int nrhs, Arena& ar, cudaStream_t s) {
+// The sweep's launches, level by level (same operations and order as
+// Hbs::sweep_inverse), as problem lists over the per-level vectors uh, qh.
+std::vector<std::vector<rw::GemvProb<double>>> sweep_stages(const rw::Hbs& H, const double* b, double* x,
+                                                           const std::vector<double*>& uh,
+                                                           const std::vector<double*>& qh) {
   using rw::GemvProb;
   const int L = H.L, ld = 2 * H.N;
+  std::vector<std::vector<GemvProb<double>>> st;
   if (L == 0) {
-    gemv_from_arena(ar, {GemvProb<double>{H.lev[0].G.p, b, x, ld, ld, ld, ld, ld, 1.0, 0.0}}, nrhs, s);
-    return;
-  }
-  std::vector<double*> uh(L + 1, nullptr), qh(L + 1, nullptr);
-  for (int l = 1; l <= L; ++l) {
-    const int K = H.lev[l].koff.back();
-    uh[l] = ar.take<double>(size_t(K) * nrhs);
-    qh[l] = ar.take<double>(size_t(K) * nrhs);
+    st.push_back({GemvProb<double>{H.lev[0].G.p, b, x, ld, ld, ld, ld, ld, 1.0, 0.0}});
+    return st;
   }
   {
     const int l = L, h0 = 1 << l, nn = 1 << l;
@@ -98,7 +87,7 @@ void sweep_noalloc(const rw::Hbs& H, const double* b, double* x, int nrhs, Arena
       ps.push_back(GemvProb<double>{LV.F.p + LV.oF[t], in, uh[l] + LV.koff[t], k, n, k, ld, K, 1.0, 0.0});
       ps.push_back(GemvProb<double>{LV.G.p + LV.oG[t], in, x + 2 * nd.lo, n, n, n, ld, ld, 1.0, 0.0});
     }
-    gemv_from_arena(ar, ps, nrhs, s);
+    st.push_back(std::move(ps));
   }
   for (int l = L - 1; l >= 1; --l) {
     const int h0 = 1 << l, nn = 1 << l;
@@ -112,11 +101,11 @@ void sweep_noalloc(const rw::Hbs& H, const double* b, double* x, int nrhs, Arena
       ps.push_back(GemvProb<double>{LV.F.p + LV.oF[t], in, uh[l] + LV.koff[t], nd.k, nd.m, nd.k, KC, K, 1.0, 0.0});
       ps.push_back(GemvProb<double>{LV.G.p + LV.oG[t], in, qh[l + 1] + LC.koff[2 * t], nd.m, nd.m, nd.m, KC, KC, 1.0, 0.0});
     }
-    gemv_from_arena(ar, ps, nrhs, s);
+    st.push_back(std::move(ps));
   }
   {
     const int K1 = H.lev[1].koff.back();
-    gemv_from_arena(ar, {GemvProb<double>{H.lev[0].G.p, uh[1], qh[1], K1, K1, K1, K1, K1, 1.0, 0.0}}, nrhs, s);
+    st.push_back({GemvProb<double>{H.lev[0].G.p, uh[1], qh[1], K1, K1, K1, K1, K1, 1.0, 0.0}});
   }
   for (int l = 1; l <= L - 1; ++l) {
     const int h0 = 1 << l, nn = 1 << l;
@@ -128,7 +117,7 @@ void sweep_noalloc(const rw::Hbs& H, const double* b, double* x, int nrhs, Arena
       const auto& nd = H.node[h0 + t];
       ps.push_back(GemvProb<double>{LV.E.p + LV.oE[t], qh[l] + LV.koff[t], qh[l + 1] + LC.koff[2 * t], nd.m, nd.k, nd.m, K, KC, 1.0, 1.0});
     }
-    gemv_from_arena(ar, ps, nrhs, s);
+    st.push_back(std::move(ps));
   }
   {
     const int l = L, h0 = 1 << l, nn = 1 << l;
@@ -140,7 +129,44 @@ void sweep_noalloc(const rw::Hbs& H, const double* b, double* x, int nrhs, Arena
       const int n = 2 * (nd.hi - nd.lo);
       ps.push_back(GemvProb<double>{LV.E.p + LV.oE[t], qh[l] + LV.koff[t], x + 2 * nd.lo, n, nd.k, n, K, ld, 1.0, 1.0});
     }
-    gemv_from_arena(ar, ps, nrhs, s);
+    st.push_back(std::move(ps));
+  }
+  return st;
+}
+
+size_t round256(size_t bytes) { return ((bytes + 255) / 256) * 256; }
+
+// The whole sweep with scratch from the arena.  Every piece (per-level
+// vectors, each launch's descriptors and split-K partials) is sized first and
+// the total checked against the array, so a sweep that does not fit is
+// refused before anything is launched or written.
+void sweep_noalloc(const rw::Hbs& H, const double* b, double* x, int nrhs, Arena& ar, cudaStream_t s) {
+  const int L = H.L;
+  size_t need = 0;
+  for (int l = 1; l <= L; ++l) need += 2 * round256(size_t(H.lev[l].koff.back()) * nrhs * sizeof(double));
+  {
+    const std::vector<double*> none(L + 1, nullptr);
+    for (const auto& ps : sweep_stages(H, b, x, none, none)) {
+      size_t db = 0, se = 0;
+      rw::gemv_into_sizes(ps, nrhs, &db, &se);
+      need += round256(db) + (se ? round256(se * sizeof(double)) : 0);
+    }
+  }
+  rw::require(need <= ar.cap, "rw_hbs_apply_inverse_noalloc: the sweep needs " + std::to_string(need) +
+                                  " bytes of scratch, more than the " + std::to_string(RW_NOALLOC_SCRATCH_BYTES >> 20) +
+                                  " MiB scratch array (reduce nrhs)");
+  std::vector<double*> uh(L + 1, nullptr), qh(L + 1, nullptr);
+  for (int l = 1; l <= L; ++l) {
+    const int K = H.lev[l].koff.back();
+    uh[l] = ar.take<double>(size_t(K) * nrhs);
+    qh[l] = ar.take<double>(size_t(K) * nrhs);
+  }
+  for (const auto& ps : sweep_stages(H, b, x, uh, qh)) {
+    size_t db = 0, se = 0;
+    rw::gemv_into_sizes(ps, nrhs, &db, &se);
+    void* desc = ar.take<char>(db);
+    double* sc = se ? ar.take<double>(se) : nullptr;
+    rw::gemv_into(ps, nrhs, desc, sc, s);
   }
 }
 

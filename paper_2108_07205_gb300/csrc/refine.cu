@@ -88,6 +88,18 @@ void recompress_rows(const NodesView& S, std::vector<int>& J, const IdMatProb& c
   k = t.k;
 }
 
+void Wall::build_hbs(cudaStream_t s) {
+  hbs.build(nodes, opts, s);
+  hbs.make_fp32(s);
+  hbs.make_bf16(s);
+  if (opts.factor_tol() < opts.id_tol) {
+    Opts oo = opts;
+    oo.id_tol = opts.factor_tol();
+    hbs_op.build(nodes, oo, s, true);
+  }
+  RW_CUDA(cudaStreamSynchronize(s));
+}
+
 SideStreams::~SideStreams() {
   // every buffer of the refinement has been released (stream ordered) by now
   for (cudaStream_t t : {s1, s2, s3}) if (t) { cudaStreamSynchronize(t); cudaStreamDestroy(t); }
@@ -115,6 +127,9 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   AllocStreamScope alloc_scope(s);
   Trace tr(s, "refine");
   const Opts& o = w.opts;
+  // IDs (and A_pp) at the operator tolerance when that is tighter: the
+  // factors then serve as the accurate operator for residuals as well
+  const double ftol = o.factor_tol();
   const int P = w.n_panels;
   require(!pan.empty() && pan.size() == lvl.size(), "refine: need one level per cut panel");
   require(int(pan.size()) < P, "refine: cannot cut every panel");
@@ -240,7 +255,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   cudaStream_t s1 = streams.s1, s2 = streams.s2, s3 = streams.s3;
   std::exception_ptr e1, e2, e3;
   const bool recompress = recompress_enabled();
-  const double rtol = 0.1 * o.id_tol;  // recompression tolerance (see recompress_rows)
+  const double rtol = 0.1 * ftol;  // recompression tolerance (see recompress_rows)
   // RW_SERIAL_REFINE=1 (diagnostics): run the four tasks one after another
   const char* ser = std::getenv("RW_SERIAL_REFINE");
   const bool serial = ser && ser[0] == '1';
@@ -249,6 +264,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     try {
       Opts opp = o;
       pp_dense = Np <= o.dense_pp_max_points;
+      opp.id_tol = ftol;
       if (pp_dense) opp.leaf_points = Np;
       hpp.build(pn, opp, s1);
       hpp.make_fp32(s1);
@@ -262,7 +278,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       // far rows of I_k against P^bas (shared by A_kc and A_kp)
       IdMatProb cs{};
       cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
-      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
+      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
     } catch (...) { e2 = std::current_exception(); }
   };
   // A_pk: rows of [A_{p,div} | A_pk^near | n_p], then (recompression) a row
@@ -275,7 +291,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
       IdMatProb cs{};
       cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
-      TreeId tp = tree_row_id(VP, prow, cs, VW, false, VW, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s3);
+      TreeId tp = tree_row_id(VP, prow, cs, VW, false, VW, false, ftol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s3);
       kpk = kpk_id = tp.k;
       Lp = std::move(tp.P);
       for (int i : tp.skel) Jpk.push_back(i);
@@ -321,7 +337,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     // near rows of I_k: [A_kc^near | A_kp^near]
     IdMatProb cs{};
     cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
-    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, o.id_tol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
+    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, ftol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
   } catch (...) { e0 = std::current_exception(); }
   if (serial) tr.mark("  near ID");
   // X_o = A_oo^{-1} L_o needs only the far and near IDs: it runs on the main
@@ -548,7 +564,7 @@ void Refinement::pressure(const double* tau, int nrhs, int nt, const double* tar
 }
 
 void Refinement::apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const {
-  wall->hbs.apply_forward(xo, yo, nrhs, s);
+  wall->op().apply_forward(xo, yo, nrhs, s);
   hpp.apply_forward(xp, yp, nrhs, s);
   if (k == 0) return;
   TBuf<double> xc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s);

@@ -10,7 +10,13 @@ struct Wall {
   int n_panels = 0;
   Opts opts;
   Nodes nodes;  // original discretisation (panel order)
-  Hbs hbs;      // A_oo
+  Hbs hbs;      // A_oo at id_tol: inverse (direct solves, preconditioner) and forward
+  Hbs hbs_op;   // A_oo forward at op_tol when that is tighter (else empty)
+  // The forward representation used for residuals.
+  const Hbs& op() const { return hbs_op.N ? hbs_op : hbs; }
+  // Build hbs (with its FP32 and BF16 copies) and, when op_tol is tighter
+  // than id_tol, hbs_op, on the wall's nodes.
+  void build_hbs(cudaStream_t s);
 };
 
 // Side streams of one refinement: created by factor(), destroyed last (after
@@ -97,11 +103,26 @@ struct Refinement {
   // A~^{-1} g on entry (ld 2No / 2Np).
   void woodbury_correct(double* yo, double* yp, int nrhs, cudaStream_t s) const;
   // FGMRES on A~ + L R with the Woodbury preconditioner, its HBS sweeps in
-  // FP32 (or with BF16 matrices when bf16 is set).
+  // FP32 (or with BF16 matrices when bf16 is set).  mixed: the operator's
+  // products in double-FP32 and the preconditioner's Woodbury correction in
+  // FP32 (W^{-1} in FP64), for nrhs > 8 (RW_MODE_GMRES_MIXED).
   void solve_gmres(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres,
-                   bool bf16 = false) const;
+                   bool bf16 = false, bool mixed = false) const;
   // ext-space operator y = (A~ + L R) x (FP64)
   void apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
+  // the same with every product in double-FP32 (FP64-level accuracy)
+  void apply_els_df(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
+  // Woodbury correction of the low-precision preconditioner: FP32 vectors
+  // (ld 2No / 2Np), R and X in FP32, W^{-1} applied in FP64.
+  void woodbury_correct_f32(float* yo, float* yp, int nrhs, cudaStream_t s) const;
+  // Algorithm 1 solve plus FP64 iterative refinement against apply_els until
+  // the relative residual is <= gmres_tol (RW_MODE_DIRECT_IR).
+  void solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres) const;
+  // double-FP32 copies of L and R, FP32 copies of R and X (made on first use)
+  void make_mixed() const;
+  mutable bool has_mixed = false;
+  mutable DBuf<float2> Lo2, Lp2, Rkc2, Rkp2, Rpk2;
+  mutable DBuf<float> Rkc32, Rkp32, Rpk32, Xo32, Xp32;
   ~Refinement();
 
  private:

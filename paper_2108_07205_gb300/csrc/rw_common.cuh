@@ -239,7 +239,7 @@ inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 // Opt-in kernel profiler (rw_profile / rw_profile_read): when enabled, each
 // launch site records CUDA events on its own stream around its launches and
 // adds its algorithmic flops and bytes to a per-class total.
-enum KClass { KC_ID = 0, KC_GEMM, KC_GEMV, KC_INVERSE, KC_EVAL, KC_OTHER, KC_COUNT };
+enum KClass { KC_ID = 0, KC_GEMM, KC_GEMV, KC_INVERSE, KC_EVAL, KC_OTHER, KC_GEMM_F32, KC_GEMM_DF, KC_COUNT };
 bool prof_enabled();
 struct ProfScope {
   bool on;

@@ -184,8 +184,12 @@ void rw_server_s::worker_loop(int wi) {
       rw::eval_stokeslets(ref.nn.view(), r->n_src, dsrc.p, r->nrhs, df.p, g.p, s);
       int iters = 0;
       double relres = 0.0;
-      const bool gm = r->mode == RW_MODE_GMRES_FP32 || r->mode == RW_MODE_GMRES_BF16;
-      if (gm) ref.solve_gmres(g.p, tau.p, r->nrhs, s, &iters, &relres, r->mode == RW_MODE_GMRES_BF16);
+      const bool gm = r->mode == RW_MODE_GMRES_FP32 || r->mode == RW_MODE_GMRES_BF16 ||
+                      r->mode == RW_MODE_GMRES_MIXED || r->mode == RW_MODE_DIRECT_IR;
+      if (r->mode == RW_MODE_DIRECT_IR) ref.solve_ir(g.p, tau.p, r->nrhs, s, &iters, &relres);
+      else if (gm)
+        ref.solve_gmres(g.p, tau.p, r->nrhs, s, &iters, &relres, r->mode == RW_MODE_GMRES_BF16,
+                        r->mode == RW_MODE_GMRES_MIXED);
       else if (r->mode == RW_MODE_DIRECT_REFINED) ref.solve_refined(g.p, tau.p, r->nrhs, 1, s);
       else ref.solve_direct(g.p, tau.p, r->nrhs, s);
       if (r->n_targets) ref.velocity(tau.p, r->nrhs, r->n_targets, dtg.p, u.p, s);
@@ -194,7 +198,7 @@ void rw_server_s::worker_loop(int wi) {
         RW_CUDA(cudaMemcpyAsync(r->u, u.p, size_t(2) * r->n_targets * r->nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
       RW_CUDA(cudaStreamSynchronize(s));
       if (gm && relres > r->wall->wall.opts.gmres_tol)
-        throw rw::Error(RW_ERR_NOT_CONVERGED, "GMRES stopped at relative residual " + std::to_string(relres));
+        throw rw::Error(RW_ERR_NOT_CONVERGED, "residual stopped at " + std::to_string(relres));
     } catch (const rw::Error& e) {
       status = e.code;
       err = e.what();
@@ -290,8 +294,7 @@ int rw_server_submit(rw_server_t sv, const rw_request* q, long long* ticket) {
   if (!sv || !q || !ticket || !q->wall || q->n_cut < 1 || !q->panel_ids || !q->levels || q->nrhs < 1 ||
       q->n_src < 1 || !q->src || !q->f || !q->tau || q->n_targets < 0 || (q->n_targets > 0 && (!q->targets || !q->u)))
     return sfail(RW_ERR_INVALID, "rw_server_submit: bad request");
-  if (q->mode != RW_MODE_DIRECT && q->mode != RW_MODE_GMRES_FP32 && q->mode != RW_MODE_DIRECT_REFINED &&
-      q->mode != RW_MODE_GMRES_BF16)
+  if (q->mode < RW_MODE_DIRECT || q->mode > RW_MODE_GMRES_MIXED)
     return sfail(RW_ERR_INVALID, "rw_server_submit: unknown mode");
   Req r;
   r.wall = q->wall;

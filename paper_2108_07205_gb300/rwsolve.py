@@ -20,6 +20,7 @@ ERRORS = {-1: "RW_ERR_INVALID", -2: "RW_ERR_OOM", -3: "RW_ERR_SINGULAR",
           -4: "RW_ERR_NOT_CONVERGED", -5: "RW_ERR_TIMEOUT", -6: "RW_ERR_CUDA"}
 CURVE_STAR, CURVE_CHANNEL, CURVE_NODES = 0, 1, 2
 MODE_DIRECT, MODE_GMRES_FP32, MODE_DIRECT_REFINED, MODE_GMRES_BF16 = 0, 1, 2, 3
+MODE_DIRECT_IR, MODE_GMRES_MIXED = 4, 5
 
 
 class RWError(RuntimeError):
@@ -38,12 +39,14 @@ class Opts(ctypes.Structure):
                 ("div_ratio", ctypes.c_double), ("bas_ratio", ctypes.c_double),
                 ("dense_pp_max_points", ctypes.c_int), ("sketch_cols", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
-                ("gmres_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("hole_div_ratio", ctypes.c_double)]
+                ("gmres_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("hole_div_ratio", ctypes.c_double),
+                ("op_tol", ctypes.c_double)]
 
 
 class HbsStats(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int), ("levels", ctypes.c_int), ("max_rank", ctypes.c_int),
-                ("inv_elems", ctypes.c_longlong), ("fwd_elems", ctypes.c_longlong), ("bytes", ctypes.c_longlong)]
+                ("inv_elems", ctypes.c_longlong), ("fwd_elems", ctypes.c_longlong), ("bytes", ctypes.c_longlong),
+                ("op_fwd_elems", ctypes.c_longlong)]
 
 
 class RefStats(ctypes.Structure):
@@ -58,7 +61,7 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-KCLASSES = ["id", "gemm", "gemv", "inverse", "eval", "other"]
+KCLASSES = ["id", "gemm", "gemv", "inverse", "eval", "other", "gemm_f32", "gemm_df"]
 
 
 class Request(ctypes.Structure):
@@ -334,8 +337,9 @@ class Refinement:
     """Algorithm 1 pre-computation for one modification of a Wall: a local
     refinement (cut panels split into sub-panels, Sec. 3.1) or, through
     Wall.add_holes, holes added inside the wall (App. B).  Both give the same
-    handle: solve (MODE_DIRECT, MODE_DIRECT_REFINED, MODE_GMRES_FP32,
-    MODE_GMRES_BF16), apply_refined, stokeslet_data, pressure, nodes, Batch."""
+    handle: solve (MODE_DIRECT, MODE_DIRECT_REFINED, MODE_DIRECT_IR,
+    MODE_GMRES_FP32, MODE_GMRES_BF16, MODE_GMRES_MIXED), apply_refined,
+    stokeslet_data, pressure, nodes, Batch."""
 
     def __init__(self, wall, panels, levels, stream=None, added=None, holes=None):
         L = load()

@@ -35,7 +35,14 @@ def test_default_opts_and_validation_without_gpu():
     assert o.leaf_points == 64 and o.id_tol == 1e-12 and o.gmres_tol == 1e-10
     # the last field of rw_opts: a layout mismatch between the header and the
     # binding would leave it unset or shifted
-    assert o.hole_div_ratio == 4.0 and o.seed == 0x5eed2108
+    assert o.hole_div_ratio == 4.0 and o.seed == 0x5eed2108 and o.op_tol == 0.0
+    bad_op = rwsolve.default_opts(op_tol=-1e-14)
+    d1 = rwsolve.WallDesc()
+    d1.curve_kind = rwsolve.CURVE_STAR
+    d1.n_panels = 8
+    h1 = ctypes.c_void_p()
+    assert L.rw_hbs_build(ctypes.byref(d1), ctypes.byref(bad_op), None, ctypes.byref(h1)) == -1
+    assert b"op_tol" in L.rw_last_error()
     bad = rwsolve.default_opts(hole_div_ratio=1.2)   # must exceed bas_ratio (1.5)
     d0 = rwsolve.WallDesc()
     d0.curve_kind = rwsolve.CURVE_STAR
