@@ -359,8 +359,7 @@ __global__ void k_max_colnorm(const double* W, int nr, int nc, int ld, unsigned 
 
 __global__ void k_to_double(const unsigned long long* in, double* out) { *out = __longlong_as_double(*in); }
 
-template <class T>
-__global__ void k_gather_scatter(const T* in, int ldi, const int* ii, T* out, int ldo, const int* io, int n) {
+__global__ void k_gather_scatter(const double* in, int ldi, const int* ii, double* out, int ldo, const int* io, int n) {
   const int r = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int a = ii ? ii[i] : i, b = io ? io[i] : i;
@@ -837,15 +836,7 @@ void gather_scatter(const double* in, int ldi, const int* idx_in, double* out, i
                     int nrhs, cudaStream_t s) {
   if (n <= 0 || nrhs <= 0) return;
   ProfScope prof_(KC_OTHER, s);
-  k_gather_scatter<double><<<dim3(std::min(ceil_div(n, 256), 1024), nrhs), 256, 0, s>>>(in, ldi, idx_in, out, ldo, idx_out, n);
-  RW_CHECK_LAUNCH();
-}
-
-void gather_scatter_f32(const float* in, int ldi, const int* idx_in, float* out, int ldo, const int* idx_out, int n,
-                        int nrhs, cudaStream_t s) {
-  if (n <= 0 || nrhs <= 0) return;
-  ProfScope prof_(KC_OTHER, s);
-  k_gather_scatter<float><<<dim3(std::min(ceil_div(n, 256), 1024), nrhs), 256, 0, s>>>(in, ldi, idx_in, out, ldo, idx_out, n);
+  k_gather_scatter<<<dim3(std::min(ceil_div(n, 256), 1024), nrhs), 256, 0, s>>>(in, ldi, idx_in, out, ldo, idx_out, n);
   RW_CHECK_LAUNCH();
 }
 

@@ -136,8 +136,5 @@ void max_colnorm(const double* W, int nr, int nc, int ld, double* out,
 void gather_scatter(const double* in, int ldi, const int* idx_in, double* out,
                     int ldo, const int* idx_out, int n, int nrhs,
                     cudaStream_t s);
-void gather_scatter_f32(const float* in, int ldi, const int* idx_in, float* out,
-                        int ldo, const int* idx_out, int n, int nrhs,
-                        cudaStream_t s);
 
 }  // namespace rw

@@ -91,11 +91,13 @@ void Refinement::make_mixed() const {
     copy_d2df(pr.first->p, pr.second->p, pr.first->n, s);
   }
   for (auto pr : {std::make_pair(&Rkc, &Rkc32), std::make_pair(&Rkp, &Rkp32), std::make_pair(&Rpk, &Rpk32),
-                  std::make_pair(&Xo, &Xo32), std::make_pair(&Xp, &Xp32)}) {
+                  std::make_pair(&Xo, &Xo32), std::make_pair(&Xp, &Xp32), std::make_pair(&Lo, &Lo32),
+                  std::make_pair(&Lp, &Lp32)}) {
     pr.second->alloc(pr.first->n);
     copy_d2f(pr.first->p, pr.second->p, pr.first->n, s);
   }
   hpp.make_df(s);
+  hpp.make_fp32_fwd(s);
   RW_CUDA(cudaStreamSynchronize(s));
   has_mixed = true;
 }
@@ -103,6 +105,10 @@ void Refinement::make_mixed() const {
 void Refinement::apply_els_df(const double* xo, const double* xp, double* yo, double* yp, int nrhs,
                               cudaStream_t s) const {
   make_mixed();
+  if (nrhs > 8) {
+    run_prog(els_prog(true, s), xo, xp, yo, yp, (double*)nullptr, nrhs, s);
+    return;
+  }
   wall->op().apply_forward_df(xo, yo, nrhs, s);
   hpp.apply_forward_df(xp, yp, nrhs, s);
   if (k == 0) return;
@@ -120,30 +126,6 @@ void Refinement::apply_els_df(const double* xo, const double* xp, double* yo, do
   matvec<double, float2>(p2, nrhs, s);
 }
 
-void Refinement::woodbury_correct_f32(float* yo, float* yp, int nrhs, cudaStream_t s) const {
-  if (k == 0) return;
-  make_mixed();
-  typedef GemvProb<float> GP;
-  TBuf<float> yc(size_t(2) * Nc * nrhs, s), r(size_t(k) * nrhs, s), z(size_t(k) * nrhs, s);
-  TBuf<double> r64(size_t(k) * nrhs, s), z64(size_t(k) * nrhs, s);
-  if (Nc) gather_scatter_f32(yo, 2 * No, dc.p, yc.p, 2 * Nc, nullptr, 2 * Nc, nrhs, s);
-  std::vector<GP> p1;
-  if (kk && Nc) p1.push_back(GP{Rkc32.p, yc.p, r.p, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 0.0});
-  if (kpk) p1.push_back(GP{Rpk32.p, yo, r.p + kk, kpk, 2 * No, kpk, 2 * No, k, 1.0, 0.0});
-  matvec<float>(p1, nrhs, s);
-  if (kk && Np) matvec<float>({GP{Rkp32.p, yp, r.p, kk, 2 * Np, kk, 2 * Np, k, 1.0, Nc ? 1.0 : 0.0}}, nrhs, s);
-  // z = W^{-1} r in FP64 (the capacitance system stays FP64)
-  k_f2d_v<<<g1(size_t(k) * nrhs), 256, 0, s>>>(r.p, r64.p, size_t(k) * nrhs);
-  RW_CHECK_LAUNCH();
-  matvec<double>({GemvProb<double>{Winv.p, r64.p, z64.p, k, k, k, k, k, 1.0, 0.0}}, nrhs, s);
-  k_d2f_v<<<g1(size_t(k) * nrhs), 256, 0, s>>>(z64.p, z.p, size_t(k) * nrhs);
-  RW_CHECK_LAUNCH();
-  std::vector<GP> p2;
-  if (kk) p2.push_back(GP{Xo32.p, z.p, yo, 2 * No, kk, 2 * No, k, 2 * No, -1.0, 1.0});
-  if (kpk) p2.push_back(GP{Xp32.p, z.p + kk, yp, 2 * Np, kpk, 2 * Np, k, 2 * Np, -1.0, 1.0});
-  matvec<float>(p2, nrhs, s);
-}
-
 void Refinement::solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters_out,
                           double* relres_out) const {
   const Opts& o = wall->opts;
@@ -156,6 +138,10 @@ void Refinement::solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s
   gather_scatter(g, 2 * Nn, n_from_p.p, gp.p, np, n_to_p.p, nkp, nrhs, s);
   // Algorithm 1 in ext space: y = A~^{-1} v, then the Woodbury correction
   auto direct = [&](const double* vo, const double* vp, double* yo, double* yp) {
+    if (nrhs > 8) {
+      run_prog(dir_prog(s), vo, vp, yo, yp, (double*)nullptr, nrhs, s);
+      return;
+    }
     wall->hbs.apply_inverse_levels(vo, yo, nrhs, s);
     hpp.apply_inverse_levels(vp, yp, nrhs, s);
     woodbury_correct(yo, yp, nrhs, s);
@@ -193,6 +179,18 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
     if (mixed) apply_els_df(xo_, xp_, yo_, yp_, nrhs, s);
     else apply_els(xo_, xp_, yo_, yp_, nrhs, s);
   };
+  TBuf<float> o32_in(mixed ? size_t(2 * No) * nrhs : 0, s), o32_out(mixed ? size_t(2 * No) * nrhs : 0, s);
+  TBuf<float> p32_in(mixed ? size_t(2 * Np) * nrhs : 0, s), p32_out(mixed ? size_t(2 * Np) * nrhs : 0, s);
+  // the operator with FP32 factors and vectors (relaxed iterations)
+  auto op32 = [&](const double* xo_, const double* xp_, double* yo_, double* yp_) {
+    k_d2f_v<<<g1(size_t(2 * No) * nrhs), 256, 0, s>>>(xo_, o32_in.p, size_t(2 * No) * nrhs);
+    k_d2f_v<<<g1(size_t(2 * Np) * nrhs), 256, 0, s>>>(xp_, p32_in.p, size_t(2 * Np) * nrhs);
+    RW_CHECK_LAUNCH();
+    run_prog(els_prog32(s), o32_in.p, p32_in.p, o32_out.p, p32_out.p, (float*)nullptr, nrhs, s);
+    k_f2d_v<<<g1(size_t(2 * No) * nrhs), 256, 0, s>>>(o32_out.p, yo_, size_t(2 * No) * nrhs);
+    k_f2d_v<<<g1(size_t(2 * Np) * nrhs), 256, 0, s>>>(p32_out.p, yp_, size_t(2 * Np) * nrhs);
+    RW_CHECK_LAUNCH();
+  };
   require(wall->hbs.has_fp32 && hpp.has_fp32, "GMRES path: FP32 sweep data missing");
   require(!bf16 || (wall->hbs.has_bf16 && hpp.has_bf16), "GMRES path: BF16 sweep data missing");
   const int m = o.gmres_maxit;
@@ -204,6 +202,9 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
   TBuf<double> wo(size_t(no) * nrhs, s), wp(size_t(np) * nrhs, s), go(size_t(no) * nrhs, s), gp(size_t(np) * nrhs, s);
   TBuf<float> fo_in(size_t(no) * nrhs, s), fo_out(size_t(no) * nrhs, s), fp_in(size_t(np) * nrhs, s), fp_out(size_t(np) * nrhs, s);
   TBuf<double> dots(size_t(m + 1) * nrhs, s), coef(size_t(m + 1) * nrhs, s);
+  // preconditioner's Woodbury vectors (mixed mode): r and z in FP32, in FP64
+  TBuf<float> r32(mixed ? size_t(std::max(k, 1)) * nrhs : 0, s);
+  TBuf<double> r64(mixed ? size_t(std::max(k, 1)) * nrhs : 0, s), z64(mixed ? size_t(std::max(k, 1)) * nrhs : 0, s);
   fill_zero(go.p, go.n, s);
   gather_scatter(g, 2 * Nn, n_from_o.p, go.p, no, n_to_o.p, nko, nrhs, s);
   gather_scatter(g, 2 * Nn, n_from_p.p, gp.p, np, n_to_p.p, nkp, nrhs, s);
@@ -235,14 +236,24 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
     k_d2f_v<<<g1(size_t(no) * nrhs), 256, 0, s>>>(vo, fo_in.p, size_t(no) * nrhs);
     k_d2f_v<<<g1(size_t(np) * nrhs), 256, 0, s>>>(vp, fp_in.p, size_t(np) * nrhs);
     RW_CHECK_LAUNCH();
-    if (bf16) {
+    if (mixed) {
+      // sweeps and r = R y in one launch, z = W^{-1} r in FP64, y -= X z
+      run_prog(pre_prog_a(bf16, s), fo_in.p, fp_in.p, fo_out.p, fp_out.p, r32.p, nrhs, s);
+      if (k > 0) {
+        k_f2d_v<<<g1(size_t(k) * nrhs), 256, 0, s>>>(r32.p, r64.p, size_t(k) * nrhs);
+        RW_CHECK_LAUNCH();
+        matvec<double>({GemvProb<double>{Winv.p, r64.p, z64.p, k, k, k, k, k, 1.0, 0.0}}, nrhs, s);
+        k_d2f_v<<<g1(size_t(k) * nrhs), 256, 0, s>>>(z64.p, r32.p, size_t(k) * nrhs);
+        RW_CHECK_LAUNCH();
+        run_prog(pre_prog_b(s), (const float*)nullptr, (const float*)nullptr, fo_out.p, fp_out.p, r32.p, nrhs, s);
+      }
+    } else if (bf16) {
       wall->hbs.apply_inverse_bf16(fo_in.p, fo_out.p, nrhs, s);
       hpp.apply_inverse_bf16(fp_in.p, fp_out.p, nrhs, s);
     } else {
       wall->hbs.apply_inverse_f32(fo_in.p, fo_out.p, nrhs, s);
       hpp.apply_inverse_f32(fp_in.p, fp_out.p, nrhs, s);
     }
-    if (mixed) woodbury_correct_f32(fo_out.p, fp_out.p, nrhs, s);
     k_f2d_v<<<g1(size_t(no) * nrhs), 256, 0, s>>>(fo_out.p, zo, size_t(no) * nrhs);
     k_f2d_v<<<g1(size_t(np) * nrhs), 256, 0, s>>>(fp_out.p, zp, size_t(np) * nrhs);
     RW_CHECK_LAUNCH();
@@ -253,20 +264,32 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
   for (auto& v : gnorm) v = std::sqrt(v);
   int total_it = 0;
   double worst = 0.0;
-  for (int cycle = 0; cycle < o.gmres_restarts; ++cycle) {
-    // r = g - A x
-    op(xo.p, xp.p, wo.p, wp.p);
-    std::vector<double> minus1(nrhs, -1.0), one(nrhs, 1.0);
+  // Inexact (relaxed) products, mixed mode only (Bouras and Fraysse 2005,
+  // Simoncini and Szyld 2003): once the residual estimate is below eta, the
+  // error an operator product may carry without spoiling the final residual
+  // grows as tol / residual, so the rest of the cycle uses the FP32 operator
+  // (relative error ~3e-6, so eta = tol / 3e-6).  Each cycle starts from the
+  // true residual with the accurate operator; a cycle whose true residual
+  // still misses tol after a relaxed cycle runs without relaxation.
+  bool relax = mixed;
+  const double eta = o.gmres_tol / 3e-6;
+  for (int cycle = 0;; ++cycle) {
+    // r = g - A x (x = 0 in the first cycle: r = g)
     RW_CUDA(cudaMemcpyAsync(ro.p, go.p, go.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RW_CUDA(cudaMemcpyAsync(rp.p, gp.p, gp.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    comb(ro.p, rp.p, wo.p, wp.p, 1, minus1);
-    std::vector<double> beta = coldots(ro.p, rp.p, ro.p, rp.p, 1);
-    worst = 0.0;
-    for (int c = 0; c < nrhs; ++c) {
-      beta[c] = std::sqrt(beta[c]);
-      worst = std::max(worst, gnorm[c] > 0 ? beta[c] / gnorm[c] : 0.0);
+    std::vector<double> beta;
+    if (cycle == 0) {
+      beta = gnorm;
+    } else {
+      op(xo.p, xp.p, wo.p, wp.p);
+      comb(ro.p, rp.p, wo.p, wp.p, 1, std::vector<double>(nrhs, -1.0));
+      beta = coldots(ro.p, rp.p, ro.p, rp.p, 1);
+      for (auto& v : beta) v = std::sqrt(v);
     }
-    if (worst <= o.gmres_tol) break;
+    worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) worst = std::max(worst, gnorm[c] > 0 ? beta[c] / gnorm[c] : 0.0);
+    if (worst <= o.gmres_tol || cycle == o.gmres_restarts) break;
+    if (cycle > 0) relax = false;
     std::vector<double> inv(nrhs);
     for (int c = 0; c < nrhs; ++c) inv[c] = beta[c] > 0 ? 1.0 / beta[c] : 0.0;
     scale(ro.p, rp.p, Vo.p, Vp.p, inv);
@@ -280,7 +303,8 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
       double* zoj = Zo.p + size_t(j) * no * nrhs;
       double* zpj = Zp.p + size_t(j) * np * nrhs;
       precond(Vo.p + size_t(j) * no * nrhs, Vp.p + size_t(j) * np * nrhs, zoj, zpj);
-      op(zoj, zpj, wo.p, wp.p);
+      if (relax && worst <= eta) op32(zoj, zpj, wo.p, wp.p);
+      else op(zoj, zpj, wo.p, wp.p);
       // classical Gram-Schmidt, twice
       for (int pass = 0; pass < 2; ++pass) {
         std::vector<double> h = coldots(wo.p, wp.p, Vo.p, Vp.p, j + 1);
@@ -329,14 +353,7 @@ void Refinement::solve_gmres(const double* g, double* tau, int nrhs, cudaStream_
     }
     if (j > 0) comb(xo.p, xp.p, Zo.p, Zp.p, j, yc);
   }
-  // final true residual
-  op(xo.p, xp.p, wo.p, wp.p);
-  RW_CUDA(cudaMemcpyAsync(ro.p, go.p, go.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  RW_CUDA(cudaMemcpyAsync(rp.p, gp.p, gp.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  comb(ro.p, rp.p, wo.p, wp.p, 1, std::vector<double>(nrhs, -1.0));
-  std::vector<double> rn = coldots(ro.p, rp.p, ro.p, rp.p, 1);
-  worst = 0.0;
-  for (int c = 0; c < nrhs; ++c) worst = std::max(worst, gnorm[c] > 0 ? std::sqrt(rn[c]) / gnorm[c] : 0.0);
+  // worst: the true relative residual of the last cycle start (the verified one)
   gather_scatter(xo.p, no, n_to_o.p, tau, 2 * Nn, n_from_o.p, nko, nrhs, s);
   gather_scatter(xp.p, np, n_to_p.p, tau, 2 * Nn, n_from_p.p, nkp, nrhs, s);
   *iters_out = total_it;

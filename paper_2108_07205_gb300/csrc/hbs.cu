@@ -776,6 +776,12 @@ void Hbs::sweep_inverse(const T* b, T* x, int nrhs, cudaStream_t s) const {
     else if constexpr (std::is_same<MT, float>::value) return f.p;
     else return h.p;
   };
+  // many right-hand sides: the cached GEMM program (one launch per 64)
+  if (nrhs > 8) {
+    if constexpr (std::is_same<T, double>::value) inverse_gemm(b, x, nrhs, s);
+    else inverse_gemm_f32(b, x, nrhs, std::is_same<MT, __nv_bfloat16>::value, s);
+    return;
+  }
   auto Gp = [&](const Level& LV) -> const MT* { return pick(LV.G, LV.G32, LV.G16); };
   auto Ep = [&](const Level& LV) -> const MT* { return pick(LV.E, LV.E32, LV.E16); };
   auto Fp = [&](const Level& LV) -> const MT* { return pick(LV.F, LV.F32, LV.F16); };
@@ -939,12 +945,14 @@ void Hbs::apply_inverse_bf16(const float* b, float* x, int nrhs, cudaStream_t s)
 }
 
 void Hbs::apply_forward(const double* xin, double* y, int nrhs, cudaStream_t s) const {
-  forward_impl<double>(xin, y, nrhs, s);
+  if (nrhs > 8) forward_gemm(xin, y, nrhs, false, s);
+  else forward_impl<double>(xin, y, nrhs, s);
 }
 
 void Hbs::apply_forward_df(const double* xin, double* y, int nrhs, cudaStream_t s) const {
   make_df(s);
-  forward_impl<float2>(xin, y, nrhs, s);
+  if (nrhs > 8) forward_gemm(xin, y, nrhs, true, s);
+  else forward_impl<float2>(xin, y, nrhs, s);
 }
 
 void Hbs::make_df(cudaStream_t s) const {
@@ -963,6 +971,22 @@ void Hbs::make_df(cudaStream_t s) const {
   }
   RW_CUDA(cudaStreamSynchronize(s));
   has_df = true;
+}
+
+void Hbs::make_fp32_fwd(cudaStream_t s) const {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (has_fp32_fwd) return;
+  for (int l = 0; l <= L; ++l) {
+    const Level& LV = lev[l];
+    for (auto pr : {std::make_pair(&LV.U, &LV.Uf), std::make_pair(&LV.Vt, &LV.Vtf), std::make_pair(&LV.B, &LV.Bf),
+                    std::make_pair(&LV.D, &LV.Df)}) {
+      pr.second->alloc(pr.first->n);
+      copy_d2f(pr.first->p, pr.second->p, pr.first->n, s);
+    }
+  }
+  RW_CUDA(cudaStreamSynchronize(s));
+  has_fp32_fwd = true;
 }
 
 template <class MT>

@@ -7,6 +7,7 @@
 #include "dense.cuh"
 #include "eval.cuh"
 #include "program.cuh"
+#include "gprogram.cuh"
 
 namespace rw {
 
@@ -103,6 +104,7 @@ class Hbs {
     DBuf<float> G32, E32, F32;
     DBuf<__nv_bfloat16> G16, E16, F16;  // BF16 copies (preconditioner sweeps)
     mutable DBuf<float2> U2, Vt2, B2, D2;  // double-FP32 copies of the forward factors (made on first use)
+    mutable DBuf<float> Uf, Vtf, Bf, Df;   // FP32 copies of the forward factors (made on first use)
   };
   std::vector<Level> lev;
   long long inv_elems = 0, fwd_elems = 0;
@@ -134,6 +136,8 @@ class Hbs {
   void apply_forward_df(const double* x, double* y, int nrhs, cudaStream_t s) const;
   void make_df(cudaStream_t s) const;
   mutable bool has_df = false;
+  void make_fp32_fwd(cudaStream_t s) const;
+  mutable bool has_fp32_fwd = false;
   void make_fp32(cudaStream_t s);
   void make_bf16(cudaStream_t s);
   bool has_fp32 = false, has_bf16 = false;
@@ -147,6 +151,23 @@ class Hbs {
   mutable Program inv_prog;
   mutable bool inv_prog_built = false;
   mutable DBuf<double> prog_ws;
+  // Many right-hand sides: the forward apply and the inverse sweep as GEMM
+  // programs (one persistent launch per 64 right-hand sides), emitted into a
+  // caller's program or cached here.  atype (MA_*) picks the factors: FP64 or
+  // double-FP32 for the forward apply (FP64 vectors), FP64, FP32 or BF16 for
+  // the inverse (the program's vector type must match).  Bases: the input
+  // at (xb, xo, ldx), the output at (yb, yo, ldy), temporaries in the
+  // program's workspace; returns the next free phase.
+  template <class GP>
+  int emit_forward_g(GP& P, int p0, int xb, long long xo, int ldx, int yb, long long yo, int ldy, int atype) const;
+  template <class GP>
+  int emit_inverse_g(GP& P, int p0, int xb, long long xo, int ldx, int yb, long long yo, int ldy, int atype) const;
+  mutable GProgram<double> gfwd64, gfwddf, ginv64;
+  mutable GProgram<float> ginv32, ginv16;
+  // one launch per 64 right-hand sides on the cached programs (built on first use)
+  void forward_gemm(const double* x, double* y, int nrhs, bool df, cudaStream_t s) const;
+  void inverse_gemm(const double* b, double* x, int nrhs, cudaStream_t s) const;
+  void inverse_gemm_f32(const float* b, float* x, int nrhs, bool bf16, cudaStream_t s) const;
 
  private:
   template <class T, class MT = T>

@@ -10,6 +10,7 @@
 // per launch, split-K with partial sums added in a fixed order when the tiles
 // cannot fill the GPU.
 #include "dense.cuh"
+#include "dfarith.cuh"
 #include <algorithm>
 #include <cmath>
 
@@ -177,32 +178,6 @@ struct GemmDfWork {
   int tilesM, tilesN, nsplit, kchunk;
   long long scratch_off;
 };
-
-// (s, c) += a * b for a = ah + al, b = bh + bl: p = fl(ah bh) and its exact
-// rounding error e = ah bh - p (one FMA); the cross terms ah bl + al bh (+ e)
-// go to c with FMAs; p enters s by two-sum, whose exact error also goes to c.
-// The _rn intrinsics keep the compiler from contracting these steps.
-__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float bh, float bl) {
-  const float p = __fmul_rn(ah, bh);
-  const float e = __fmaf_rn(ah, bh, -p);
-  const float t = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
-  const float s1 = __fadd_rn(s, p);
-  const float bb = __fsub_rn(s1, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
-  s = s1;
-  c = __fadd_rn(c, __fadd_rn(err, t));
-}
-
-// (H, L) += (s + c): two-sum of the running pair with the chunk's sum.
-__device__ __forceinline__ void df_flush(float& H, float& L, float& s, float& c) {
-  const float h1 = __fadd_rn(H, s);
-  const float bb = __fsub_rn(h1, H);
-  const float err = __fadd_rn(__fsub_rn(H, __fsub_rn(h1, bb)), __fsub_rn(s, bb));
-  H = h1;
-  L = __fadd_rn(L, __fadd_rn(err, c));
-  s = 0.f;
-  c = 0.f;
-}
 
 __global__ void __launch_bounds__(256) k_gemm_df(const GemmDfWork* work, const int* offs, int nprob,
                                                  double* scratch) {

@@ -508,9 +508,14 @@ void Refinement::solve_direct_levels(const double* g, double* tau, int nrhs, cud
   fill_zero(go.p, go.n, s);
   gather_scatter(g, 2 * Nn, n_from_o.p, go.p, 2 * No, n_to_o.p, nko, nrhs, s);
   gather_scatter(g, 2 * Nn, n_from_p.p, gp.p, 2 * Np, n_to_p.p, nkp, nrhs, s);
-  wall->hbs.apply_inverse_levels(go.p, yo.p, nrhs, s);
-  hpp.apply_inverse_levels(gp.p, yp.p, nrhs, s);
-  woodbury_correct(yo.p, yp.p, nrhs, s);
+  if (nrhs > 8) {
+    // both trees and the Woodbury correction in one launch per 64 RHS
+    run_prog(dir_prog(s), go.p, gp.p, yo.p, yp.p, (double*)nullptr, nrhs, s);
+  } else {
+    wall->hbs.apply_inverse_levels(go.p, yo.p, nrhs, s);
+    hpp.apply_inverse_levels(gp.p, yp.p, nrhs, s);
+    woodbury_correct(yo.p, yp.p, nrhs, s);
+  }
   gather_scatter(yo.p, 2 * No, n_to_o.p, tau, 2 * Nn, n_from_o.p, nko, nrhs, s);
   gather_scatter(yp.p, 2 * Np, n_to_p.p, tau, 2 * Nn, n_from_p.p, nkp, nrhs, s);
 }
@@ -564,6 +569,10 @@ void Refinement::pressure(const double* tau, int nrhs, int nt, const double* tar
 }
 
 void Refinement::apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const {
+  if (nrhs > 8) {
+    run_prog(els_prog(false, s), xo, xp, yo, yp, (double*)nullptr, nrhs, s);
+    return;
+  }
   wall->op().apply_forward(xo, yo, nrhs, s);
   hpp.apply_forward(xp, yp, nrhs, s);
   if (k == 0) return;

@@ -47,6 +47,11 @@ void recompress_rows(const NodesView& S, std::vector<int>& J, const IdMatProb& c
 // RW_RECOMPRESS=0 (diagnostics) keeps the blockwise ranks.
 bool recompress_enabled();
 
+// Runs a refinement program on bases 0, 1 (inputs), 3, 4 (outputs) and 5,
+// with a stream-ordered workspace as base 2.
+template <class T>
+void run_prog(const GProgram<T>& P, const T* b0, const T* b1, T* b3, T* b4, T* b5, int nrhs, cudaStream_t s);
+
 struct Refinement {
   SideStreams streams;  // first member: destroyed last
   const Wall* wall = nullptr;
@@ -112,17 +117,33 @@ struct Refinement {
   void apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
   // the same with every product in double-FP32 (FP64-level accuracy)
   void apply_els_df(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
-  // Woodbury correction of the low-precision preconditioner: FP32 vectors
-  // (ld 2No / 2Np), R and X in FP32, W^{-1} applied in FP64.
-  void woodbury_correct_f32(float* yo, float* yp, int nrhs, cudaStream_t s) const;
   // Algorithm 1 solve plus FP64 iterative refinement against apply_els until
   // the relative residual is <= gmres_tol (RW_MODE_DIRECT_IR).
   void solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres) const;
+  // Many right-hand sides: the whole ELS operator, the whole FP64 direct
+  // solve (Algorithm 1 in ext space) and the low-precision preconditioner as
+  // GEMM programs, the wall's and the refined arc's trees side by side in
+  // the same phases with the Woodbury terms (built on first use).
+  // ELS operator: bases 0 = x_o, 1 = x_p, 2 = workspace, 3 = y_o, 4 = y_p.
+  const GProgram<double>& els_prog(bool df, cudaStream_t s) const;
+  // The same operator with FP32 factors and vectors (the relaxed FGMRES
+  // iterations of the mixed mode): same bases, FP32.
+  const GProgram<float>& els_prog32(cudaStream_t s) const;
+  // Direct solve in ext space: bases 0 = g_o, 1 = g_p, 2 = workspace,
+  // 3 = y_o, 4 = y_p.
+  const GProgram<double>& dir_prog(cudaStream_t s) const;
+  // Preconditioner, FP32 vectors: part a = sweeps and r = R y (bases 0 = v_o,
+  // 1 = v_p, 2 = workspace, 3 = y_o, 4 = y_p, 5 = r, k x nrhs); part b =
+  // y -= X z (bases 3, 4, and 5 = z); W^{-1} is applied in FP64 between them.
+  const GProgram<float>& pre_prog_a(bool bf16, cudaStream_t s) const;
+  const GProgram<float>& pre_prog_b(cudaStream_t s) const;
+  mutable GProgram<double> g_els64, g_elsdf, g_dir64;
+  mutable GProgram<float> g_pre32, g_pre16, g_preb, g_els32;
   // double-FP32 copies of L and R, FP32 copies of R and X (made on first use)
   void make_mixed() const;
   mutable bool has_mixed = false;
   mutable DBuf<float2> Lo2, Lp2, Rkc2, Rkp2, Rpk2;
-  mutable DBuf<float> Rkc32, Rkp32, Rpk32, Xo32, Xp32;
+  mutable DBuf<float> Rkc32, Rkp32, Rpk32, Xo32, Xp32, Lo32, Lp32;
   ~Refinement();
 
  private:
