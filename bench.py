@@ -417,15 +417,20 @@ def refine_probe(k):
 
 def run_serving(args):
     """Serving workload: resident walls (channel 512/1024/2048 panels, star 1024
-    panels); each request refines 1-64 contiguous panels by 2-6 levels and
-    carries 1-32 right-hand sides from exterior point forces.  Closed loop
-    (all requests at once) gives the saturation rate; an open loop with
-    Poisson arrivals at 0.8 x that rate gives p50/p99 latency."""
+    panels, operator tolerance 1e-14); each request refines 1-64 contiguous
+    panels by 2-6 levels and carries 1-32 right-hand sides from exterior point
+    forces, solved in --mode (default the mixed FGMRES to a certified 1e-10).
+    Closed loop (all requests at once) gives the saturation rate; an open loop
+    with Poisson arrivals at 0.8 x that rate gives p50/p99 latency.  Sampled
+    open-loop requests are refactored afterwards and their densities checked
+    against the exact refined operator."""
     import torch
     from paper_2108_07205_gb300 import rwsolve, inputs
     rwsolve.load(build_if_missing=True)
-    walls = [rwsolve.Wall("channel", 512), rwsolve.Wall("channel", 1024), rwsolve.Wall("channel", 2048),
-             rwsolve.Wall("star", 1024, (0.3, 5, 1.0))]
+    mode = mode_id(args.mode)
+    op = rwsolve.default_opts(op_tol=OP_TOL)
+    walls = [rwsolve.Wall("channel", 512, opts=op), rwsolve.Wall("channel", 1024, opts=op),
+             rwsolve.Wall("channel", 2048, opts=op), rwsolve.Wall("star", 1024, (0.3, 5, 1.0), opts=op)]
     torch.cuda.synchronize()
 
     def make(seed):
@@ -450,7 +455,7 @@ def run_serving(args):
         sv.wait(t)
     reqs = [make(i) for i in range(args.requests)]
     t0 = time.time()
-    tk = [sv.submit(w, p, l, s, f, nrhs=n, targets=tg)[0] for (w, p, l, s, f, n, tg) in reqs]
+    tk = [sv.submit(w, p, l, s, f, nrhs=n, targets=tg, mode=mode)[0] for (w, p, l, s, f, n, tg) in reqs]
     lat_closed = [sv.wait(t) for t in tk]
     t_closed = time.time() - t0
     nsolves = sum(r[5] for r in reqs)
@@ -460,20 +465,36 @@ def run_serving(args):
     gaps = g.exponential(1.0 / lam, size=args.requests)
     reqs2 = [make(10 ** 5 + i) for i in range(args.requests)]
     t0 = time.time()
-    tk2 = []
+    tk2, outs = [], []
     for gap, (w, p, l, s, f, n, tg) in zip(gaps, reqs2):
         time.sleep(gap)
-        tk2.append(sv.submit(w, p, l, s, f, nrhs=n, targets=tg)[0])
+        t, tau, _ = sv.submit(w, p, l, s, f, nrhs=n, targets=tg, mode=mode)
+        tk2.append(t)
+        outs.append(tau)
     lat_open = [sv.wait(t) for t in tk2]
     t_open = time.time() - t0
     nsolves2 = sum(r[5] for r in reqs2)
     sv.close()
+    # accuracy of sampled served results against the exact refined operator
+    worst = 0.0
+    sample = inputs.rng(99).choice(args.requests, min(16, args.requests), replace=False)
+    for i in sample:
+        w, p, l, s_, f, n, _ = reqs2[i]
+        ref = w.refine(p, l)
+        g = np.empty((n, 2 * ref.stats()["n_n"]))
+        ref.stokeslet_data(np.ascontiguousarray(s_), f, g, nrhs=n)
+        y = np.empty_like(g)
+        ref.apply_refined(np.ascontiguousarray(outs[i]), y, nrhs=n)
+        worst = max(worst, float((np.linalg.norm(y - g, axis=1) / np.linalg.norm(g, axis=1)).max()))
+        ref.close()
     line = {"metric": "refined-wall solves/s (serving, open loop at 0.8 x saturation)",
             "value": nsolves2 / t_open, "unit": "solves/s", "n_gpus": 1, "steps": args.requests, "warmup": 2,
             "ms_per_step": 1e3 * t_open / args.requests, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "serving: walls channel 512/1024/2048 + star 1024 panels; requests refine "
-                                   "1-64 panels by 2-6 levels with 1-32 RHS; 4 workers, 200 GB budget"},
+            "vs_baseline": None, "dtype": MODE_DTYPE[args.mode], "data": "synthetic",
+            "config": {"workload": "serving: walls channel 512/1024/2048 + star 1024 panels (op_tol 1e-14); "
+                                   "requests refine 1-64 panels by 2-6 levels with 1-32 RHS; 4 workers, "
+                                   "200 GB budget", "mode": MODE_NAMES[args.mode]},
+            "true_rel_residual_max_sampled": worst, "sampled_requests": len(sample),
             "p50_ms": float(np.percentile(lat_open, 50)), "p99_ms": float(np.percentile(lat_open, 99)),
             "saturation": {"requests_per_s": sat, "solves_per_s": nsolves / t_closed,
                            "p50_ms": float(np.percentile(lat_closed, 50)),

@@ -196,10 +196,16 @@ int rw_hbs_apply_forward(rw_hbs_t h, int nrhs, const double* x, double* y,
                          void* stream);
 
 /* a1-a6. Algorithm 1 pre-computation for one local refinement (Sec. 3.1-3.4):
- * cut the n_cut panels panel_ids[] (a contiguous run modulo P, window order)
- * and replace panel_ids[i] by 2^levels[i] equal sub-panels; build the added
- * nodes, A_pp^{-1}, the row-ID factors Q ~= L R, X = A~^{-1} L and the LU
- * factors of W = I + R X.  panel_ids and levels are host arrays.
+ * cut the n_cut panels panel_ids[] and replace panel_ids[i] by 2^levels[i]
+ * equal sub-panels; build the added nodes, A_pp^{-1}, the row-ID factors
+ * Q ~= L R, X = A~^{-1} L and the LU factors of W = I + R X.  panel_ids is one
+ * or more regions, each a contiguous run of panels modulo P given in window
+ * order (consecutive entries i, i+1 with panel_ids[i+1] = panel_ids[i] + 1 mod
+ * P belong to one region), at most 8 regions: several refined regions grouped
+ * in one refinement share one factorisation of Q (Sec. 5.3, the Remark on
+ * grouping two refined regions, e.g. those of two consecutive time steps);
+ * each region gets its own proxy circles.  panel_ids and levels are host
+ * arrays; panels must be distinct, levels in 0..12.
  * The handle borrows h, which must outlive it.  Its device memory is
  * allocated in stream order on `stream`, which must stay valid until
  * rw_ref_free. */

@@ -411,7 +411,11 @@ long long GProgram<T>::ws_alloc(long long elems) {
 }
 
 template <class T>
-void GProgram<T>::finalize(cudaStream_t s) {
+void GProgram<T>::finalize(cudaStream_t s_caller, cudaStream_t alloc) {
+  // uploads on the allocation stream when there is one (the memory is
+  // ordered there), synchronised before returning
+  AllocStreamScope scope(alloc);
+  cudaStream_t s = alloc ? alloc : s_caller;
   int dev = 0, nsm = 0;
   RW_CUDA(cudaGetDevice(&dev));
   RW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -61,8 +61,11 @@ class GProgram {
   int ws_base() const { return wsb_; }
   int nphases() const { return int(phases_.size()); }
   bool finalized() const { return done_; }
-  // split long inner dimensions in thin phases, tile, upload
-  void finalize(cudaStream_t s);
+  // split long inner dimensions, tile, upload.  The program's device tables
+  // are allocated in stream order on `alloc` (the owner's stream, which must
+  // outlive the program), or with plain cudaMalloc when it is null (programs
+  // of a shared wall, which any stream may use and outlive).
+  void finalize(cudaStream_t s, cudaStream_t alloc = nullptr);
   // Execute on bases[0..kGBases) for nrhs right-hand sides (the workspace
   // base must hold ws_per_rhs() * nrhs entries).
   void run(T* const* bases, int nrhs, cudaStream_t s) const;

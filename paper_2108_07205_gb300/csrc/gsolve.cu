@@ -203,12 +203,12 @@ std::mutex g_prog_mu;  // cached programs of a wall may be asked for by several 
 // 2 = workspace.
 template <class T>
 static void run_cached(GProgram<T>& prog, const std::function<void(GProgram<T>&)>& emit, const T* in, T* out,
-                       int nrhs, cudaStream_t s) {
+                       int nrhs, cudaStream_t alloc, cudaStream_t s) {
   {
     std::lock_guard<std::mutex> lock(g_prog_mu);
     if (!prog.finalized()) {
       emit(prog);
-      prog.finalize(s);
+      prog.finalize(s, alloc);
     }
   }
   TBuf<T> ws(size_t(std::max<long long>(prog.ws_per_rhs(), 1)) * nrhs, s);
@@ -221,12 +221,12 @@ void Hbs::forward_gemm(const double* x, double* y, int nrhs, bool df, cudaStream
   GProgram<double>& P = df ? gfwddf : gfwd64;
   run_cached<double>(P, [&](GProgram<double>& G) {
     emit_forward_g(G, 0, 0, 0, 2 * N, 1, 0, 2 * N, df ? MA_DF : MA_F64);
-  }, x, y, nrhs, s);
+  }, x, y, nrhs, own_stream, s);
 }
 
 void Hbs::inverse_gemm(const double* b, double* x, int nrhs, cudaStream_t s) const {
   run_cached<double>(ginv64, [&](GProgram<double>& G) { emit_inverse_g(G, 0, 0, 0, 2 * N, 1, 0, 2 * N, MA_F64); },
-                     b, x, nrhs, s);
+                     b, x, nrhs, own_stream, s);
 }
 
 void Hbs::inverse_gemm_f32(const float* b, float* x, int nrhs, bool bf16, cudaStream_t s) const {
@@ -234,7 +234,7 @@ void Hbs::inverse_gemm_f32(const float* b, float* x, int nrhs, bool bf16, cudaSt
   GProgram<float>& P = bf16 ? ginv16 : ginv32;
   run_cached<float>(P, [&](GProgram<float>& G) {
     emit_inverse_g(G, 0, 0, 0, 2 * N, 1, 0, 2 * N, bf16 ? MA_BF16 : MA_F32);
-  }, b, x, nrhs, s);
+  }, b, x, nrhs, own_stream, s);
 }
 
 }  // namespace rw

@@ -955,12 +955,14 @@ void Hbs::apply_forward_df(const double* xin, double* y, int nrhs, cudaStream_t 
   else forward_impl<float2>(xin, y, nrhs, s);
 }
 
-void Hbs::make_df(cudaStream_t s) const {
+void Hbs::make_df(cudaStream_t s_caller) const {
   // once per representation; the wall's copy may be asked for by several
   // host threads (serving workers) at the same time
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
   if (has_df) return;
+  AllocStreamScope scope(own_stream);
+  cudaStream_t s = own_stream ? own_stream : s_caller;  // copies ordered after the allocation
   for (int l = 0; l <= L; ++l) {
     const Level& LV = lev[l];
     for (auto pr : {std::make_pair(&LV.U, &LV.U2), std::make_pair(&LV.Vt, &LV.Vt2), std::make_pair(&LV.B, &LV.B2),
@@ -973,10 +975,12 @@ void Hbs::make_df(cudaStream_t s) const {
   has_df = true;
 }
 
-void Hbs::make_fp32_fwd(cudaStream_t s) const {
+void Hbs::make_fp32_fwd(cudaStream_t s_caller) const {
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
   if (has_fp32_fwd) return;
+  AllocStreamScope scope(own_stream);
+  cudaStream_t s = own_stream ? own_stream : s_caller;  // copies ordered after the allocation
   for (int l = 0; l <= L; ++l) {
     const Level& LV = lev[l];
     for (auto pr : {std::make_pair(&LV.U, &LV.Uf), std::make_pair(&LV.Vt, &LV.Vtf), std::make_pair(&LV.B, &LV.Bf),

@@ -134,6 +134,11 @@ class Hbs {
   void apply_forward(const double* x, double* y, int nrhs, cudaStream_t s) const;
   // The same with the products in double-FP32 (copies made on first use).
   void apply_forward_df(const double* x, double* y, int nrhs, cudaStream_t s) const;
+  // Copies and programs made after the build are allocated in stream order on
+  // own_stream (a refined arc: its refinement's stream, which outlives it),
+  // or with plain cudaMalloc when it is null (a shared wall, which any stream
+  // may use and outlive).
+  cudaStream_t own_stream = nullptr;
   void make_df(cudaStream_t s) const;
   mutable bool has_df = false;
   void make_fp32_fwd(cudaStream_t s) const;

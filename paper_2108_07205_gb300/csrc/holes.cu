@@ -171,6 +171,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
       }
       eval_hole_matrix(VP, pan, geo, A.p, s1);
       hpp.build_dense(std::move(A), Np, s1);
+      hpp.own_stream = s;   // later copies and programs live on the refinement's stream
       hpp.make_fp32(s1);
       hpp.make_bf16(s1);
       pp_dense = true;

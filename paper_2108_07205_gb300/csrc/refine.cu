@@ -134,13 +134,20 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   require(!pan.empty() && pan.size() == lvl.size(), "refine: need one level per cut panel");
   require(int(pan.size()) < P, "refine: cannot cut every panel");
   std::vector<char> cut(P, 0);
+  // regions: maximal contiguous runs (mod P) of consecutive entries; several
+  // regions grouped in one refinement share one factorisation of Q (Sec. 5.3,
+  // the Remark on grouping refined regions)
+  std::vector<int> rstart;
   for (size_t i = 0; i < pan.size(); ++i) {
     require(pan[i] >= 0 && pan[i] < P, "refine: panel id out of range");
     require(!cut[pan[i]], "refine: cut panels must be distinct");
     require(lvl[i] >= 0 && lvl[i] <= 12, "refine: level must be in 0..12");
-    if (i > 0) require(pan[i] == (pan[i - 1] + 1) % P, "refine: cut panels must be a contiguous run (mod P)");
+    if (i == 0 || pan[i] != (pan[i - 1] + 1) % P) rstart.push_back(int(i));
     cut[pan[i]] = 1;
   }
+  require(rstart.size() <= 8, "refine: at most 8 regions (contiguous runs of cut panels) per refinement");
+  rstart.push_back(int(pan.size()));
+  const int nreg = int(rstart.size()) - 1;
   panels = pan;
   levels = lvl;
   No = w.nodes.n;
@@ -219,19 +226,47 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   }
   tr.mark("nodes+maps");
   // Gamma_r: centre and radius of the cut and added points
-  double cx = 0, cy = 0;
-  for (int i : Ic) { cx += w.nodes.hx[i]; cy += w.nodes.hy[i]; }
-  for (int i = 0; i < Np; ++i) { cx += pn.hx[i]; cy += pn.hy[i]; }
-  cx /= (Nc + Np);
-  cy /= (Nc + Np);
-  double rho2 = 0;
-  for (int i : Ic) rho2 = std::max(rho2, (w.nodes.hx[i] - cx) * (w.nodes.hx[i] - cx) + (w.nodes.hy[i] - cy) * (w.nodes.hy[i] - cy));
-  for (int i = 0; i < Np; ++i) rho2 = std::max(rho2, (pn.hx[i] - cx) * (pn.hx[i] - cx) + (pn.hy[i] - cy) * (pn.hy[i] - cy));
-  const double rho = std::sqrt(rho2), Rdiv = o.div_ratio * rho, Rbas = o.bas_ratio * rho;
+  // per region r: centre and radius rho_r of its cut and added points,
+  // P^div (div_ratio rho_r) and P^bas (bas_ratio rho_r); kept points inside
+  // any P^div are near, the rest far
+  std::vector<int> poff(nreg + 1, 0);
+  for (int r = 0; r < nreg; ++r) {
+    int cnt = 0;
+    for (int i = rstart[r]; i < rstart[r + 1]; ++i) cnt += 16 << lvl[i];
+    poff[r + 1] = poff[r] + cnt;
+  }
+  std::vector<double> circ_div, circ_bas;
+  for (int r = 0; r < nreg; ++r) {
+    std::vector<int> pts;  // wall points cut by this region
+    for (int i = rstart[r]; i < rstart[r + 1]; ++i)
+      for (int q = 0; q < 16; ++q) pts.push_back(16 * pan[i] + q);
+    double cx = 0, cy = 0;
+    for (int i : pts) { cx += w.nodes.hx[i]; cy += w.nodes.hy[i]; }
+    for (int i = poff[r]; i < poff[r + 1]; ++i) { cx += pn.hx[i]; cy += pn.hy[i]; }
+    const double cnt = double(pts.size() + (poff[r + 1] - poff[r]));
+    cx /= cnt;
+    cy /= cnt;
+    double rho2 = 0;
+    for (int i : pts) rho2 = std::max(rho2, (w.nodes.hx[i] - cx) * (w.nodes.hx[i] - cx) + (w.nodes.hy[i] - cy) * (w.nodes.hy[i] - cy));
+    for (int i = poff[r]; i < poff[r + 1]; ++i)
+      rho2 = std::max(rho2, (pn.hx[i] - cx) * (pn.hx[i] - cx) + (pn.hy[i] - cy) * (pn.hy[i] - cy));
+    const double rho = std::sqrt(rho2);
+    circ_div.insert(circ_div.end(), {cx, cy, o.div_ratio * rho});
+    circ_bas.insert(circ_bas.end(), {cx, cy, o.bas_ratio * rho});
+  }
   std::vector<int> far_d, near_d;
+  std::vector<std::vector<int>> near_r(nreg);
   for (int i : Ik) {
-    const double dx = w.nodes.hx[i] - cx, dy = w.nodes.hy[i] - cy;
-    auto& v = (dx * dx + dy * dy >= Rdiv * Rdiv) ? far_d : near_d;
+    bool near = false;
+    for (int r = 0; r < nreg; ++r) {
+      const double dx = w.nodes.hx[i] - circ_div[3 * r], dy = w.nodes.hy[i] - circ_div[3 * r + 1];
+      if (dx * dx + dy * dy < circ_div[3 * r + 2] * circ_div[3 * r + 2]) {
+        near = true;
+        near_r[r].push_back(2 * i);
+        near_r[r].push_back(2 * i + 1);
+      }
+    }
+    auto& v = near ? near_d : far_d;
     v.push_back(2 * i);
     v.push_back(2 * i + 1);
   }
@@ -241,12 +276,15 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   // A_pk IDs run concurrently on three streams driven by three host threads.
   const NodesView VW = w.nodes.view(), VP = pn.view();
   TreeId tf, tn;
-  DBuf<int> dall_p, dnear;
+  DBuf<int> dall_p;
+  std::vector<DBuf<int>> dnear_r(nreg);
+  DBuf<double> dcirc_bas;
   {
     std::vector<int> pd(2 * Np);
     for (int i = 0; i < 2 * Np; ++i) pd[i] = i;
     dall_p = to_device(pd, s);
-    dnear = to_device(near_d, s);
+    for (int r = 0; r < nreg; ++r) dnear_r[r] = to_device(near_r[r], s);
+    dcirc_bas = to_device(circ_bas, s);
     RW_CUDA(cudaStreamSynchronize(s));
   }
   RW_CUDA(cudaStreamCreateWithFlags(&streams.s1, cudaStreamNonBlocking));
@@ -267,6 +305,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       opp.id_tol = ftol;
       if (pp_dense) opp.leaf_points = Np;
       hpp.build(pn, opp, s1);
+      hpp.own_stream = s;   // later copies and programs live on the refinement's stream
       hpp.make_fp32(s1);
       hpp.make_bf16(s1);
       RW_CUDA(cudaStreamSynchronize(s1));
@@ -275,9 +314,12 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   auto task2 = [&] {
     AllocStreamScope scope2(s2);
     try {
-      // far rows of I_k against P^bas (shared by A_kc and A_kp)
+      // far rows of I_k against P^bas (shared by A_kc and A_kp); with several
+      // regions against the union of their P^bas circles (every source lies
+      // inside its own region's circle, every far row outside all of them)
       IdMatProb cs{};
-      cs.cx = cx; cs.cy = cy; cs.R = Rbas; cs.M = o.n_proxy_refine; cs.normal = 1;
+      cs.cx = circ_bas[0]; cs.cy = circ_bas[1]; cs.R = circ_bas[2]; cs.M = o.n_proxy_refine; cs.normal = 1;
+      if (nreg > 1) { cs.ncirc = nreg; cs.circ = dcirc_bas.p; }
       tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
     } catch (...) { e2 = std::current_exception(); }
   };
@@ -287,14 +329,40 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   auto task3 = [&] {
     AllocStreamScope scope3(s3);
     try {
-      std::vector<int> prow(2 * Np);
-      for (int i = 0; i < 2 * Np; ++i) prow[i] = i;
-      IdMatProb cs{};
-      cs.n1 = int(near_d.size()); cs.e1 = dnear.p; cs.cx = cx; cs.cy = cy; cs.R = Rdiv; cs.M = o.n_proxy_refine; cs.normal = 1;
-      TreeId tp = tree_row_id(VP, prow, cs, VW, false, VW, false, ftol, o.sketch_cols, o.sketch_width, o.seed + 303, 128, s3);
-      kpk = kpk_id = tp.k;
-      Lp = std::move(tp.P);
-      for (int i : tp.skel) Jpk.push_back(i);
+      // region by region (its added rows against its P^div circle and the
+      // kept points inside it): L_pk block diagonal over the regions
+      std::vector<TreeId> tp(nreg);
+      kpk = 0;
+      for (int r = 0; r < nreg; ++r) {
+        std::vector<int> prow;
+        for (int d = 2 * poff[r]; d < 2 * poff[r + 1]; ++d) prow.push_back(d);
+        IdMatProb cs{};
+        cs.n1 = int(near_r[r].size()); cs.e1 = dnear_r[r].p;
+        cs.cx = circ_div[3 * r]; cs.cy = circ_div[3 * r + 1]; cs.R = circ_div[3 * r + 2];
+        cs.M = o.n_proxy_refine; cs.normal = 1;
+        tp[r] = tree_row_id(VP, prow, cs, VW, false, VW, false, ftol, o.sketch_cols, o.sketch_width,
+                            o.seed + 303 + 7 * r, 128, s3);
+        kpk += tp[r].k;
+      }
+      kpk_id = kpk;
+      if (nreg == 1) {
+        Lp = std::move(tp[0].P);
+        for (int i : tp[0].skel) Jpk.push_back(i);
+      } else {
+        Lp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
+        Lp.zero(s3);
+        std::vector<CopyProb> cp;
+        int col = 0;
+        for (int r = 0; r < nreg; ++r) {
+          const int m = 2 * (poff[r + 1] - poff[r]);
+          if (tp[r].k)
+            cp.push_back(CopyProb{tp[r].P.p, m, tp[r].k, m, Lp.p + 2 * size_t(poff[r]) + size_t(col) * 2 * Np, 2 * Np});
+          for (int i : tp[r].skel) Jpk.push_back(2 * poff[r] + i);
+          col += tp[r].k;
+        }
+        batched_copy(cp, s3);
+        RW_CUDA(cudaStreamSynchronize(s3));
+      }
       if (recompress) {
         std::vector<int> kd;
         for (int i : Ik) { kd.push_back(2 * i); kd.push_back(2 * i + 1); }
@@ -352,7 +420,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   Lo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
   Lo.zero(s);
   {
-    auto dfar = to_device_tmp(far_d, s);
+    auto dfar = to_device_tmp(far_d, s), dnear = to_device_tmp(near_d, s);
     if (kf) gather_scatter(tf.P.p, int(far_d.size()), nullptr, Lo.p, 2 * No, dfar.p, int(far_d.size()), kf, s);
     if (kn) gather_scatter(tn.P.p, int(near_d.size()), nullptr, Lo.p + size_t(2) * No * kf, 2 * No, dnear.p, int(near_d.size()), kn, s);
     RW_CUDA(cudaStreamSynchronize(s));

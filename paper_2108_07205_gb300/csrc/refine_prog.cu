@@ -53,7 +53,7 @@ const GProgram<double>& Refinement::els_prog(bool df, cudaStream_t s) const {
       if (kpk) P.gemm(q, Lp.p, 2 * Np, kpk, 2 * Np, P.ws_base(), r + kk, -1, 4, 0, 2 * Np, 1.0, 1.0);
     }
   }
-  P.finalize(s);
+  P.finalize(s, streams.main);
   return P;
 }
 
@@ -71,7 +71,7 @@ const GProgram<float>& Refinement::els_prog32(cudaStream_t s) const {
     if (kk) P.gemm(q, Lo32.p, 2 * No, kk, 2 * No, P.ws_base(), r, -1, 3, 0, 2 * No, 1.0, 1.0);
     if (kpk) P.gemm(q, Lp32.p, 2 * Np, kpk, 2 * Np, P.ws_base(), r + kk, -1, 4, 0, 2 * Np, 1.0, 1.0);
   }
-  P.finalize(s);
+  P.finalize(s, streams.main);
   return P;
 }
 
@@ -89,7 +89,7 @@ const GProgram<double>& Refinement::dir_prog(cudaStream_t s) const {
     if (kk) P.gemm(p, Xo.p, 2 * No, kk, 2 * No, W, z, -1, 3, 0, 2 * No, -1.0, 1.0);
     if (kpk) P.gemm(p, Xp.p, 2 * Np, kpk, 2 * Np, W, z + kk, -1, 4, 0, 2 * Np, -1.0, 1.0);
   }
-  P.finalize(s);
+  P.finalize(s, streams.main);
   return P;
 }
 
@@ -102,7 +102,7 @@ const GProgram<float>& Refinement::pre_prog_a(bool bf16, cudaStream_t s) const {
   const int pb = hpp.emit_inverse_g(P, 0, 1, 0, 2 * Np, 4, 0, 2 * Np, at);
   if (k > 0)
     emit_r_times(P, std::max(pa, pb), Rkc32.p, Rkp32.p, Rpk32.p, kk, kpk, k, No, Nc, Np, dc.p, 3, 4, 5, 0, k);
-  P.finalize(s);
+  P.finalize(s, streams.main);
   return P;
 }
 
@@ -112,7 +112,7 @@ const GProgram<float>& Refinement::pre_prog_b(cudaStream_t s) const {
   make_mixed();
   if (kk) P.gemm(0, Xo32.p, 2 * No, kk, 2 * No, 5, 0, k, 3, 0, 2 * No, -1.0, 1.0);
   if (kpk) P.gemm(0, Xp32.p, 2 * Np, kpk, 2 * Np, 5, kk, k, 4, 0, 2 * Np, -1.0, 1.0);
-  P.finalize(s);
+  P.finalize(s, streams.main);
   return P;
 }
 

@@ -204,7 +204,8 @@ def test_many_rhs_take_the_gemm_sweeps(star64):
 
 
 def test_invalid_refinements_rejected(star64):
-    for panels, levels in (([3, 5], [2, 2]), ([64], [1]), ([1, 2], [2, 13]), ([4, 4], [1, 1])):
+    nine_regions = list(range(0, 18, 2))   # nine contiguous runs: more than the eight a refinement groups
+    for panels, levels in ((nine_regions, [1] * 9), ([64], [1]), ([1, 2], [2, 13]), ([4, 4], [1, 1])):
         with pytest.raises(rwsolve.RWError) as e:
             star64.refine(panels, levels)
         assert e.value.code == -1
