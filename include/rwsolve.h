@@ -91,6 +91,15 @@ typedef struct {
                                the representation of A_pp at op_tol, so that
                                A~ + L R matches A_ext to about op_tol while the
                                reference wall's inverse stays at id_tol      */
+  int mixed_factor;         /* 0 (default) or 1: refinements of this wall
+                               compute X = A~^{-1} L with FP32 sweeps and form
+                               W = I + R X from it in FP64 -- a factorisation
+                               that serves only as the preconditioner of the
+                               iterative modes (RW_MODE_GMRES_*, and
+                               RW_MODE_DIRECT_IR, which needs more
+                               corrections); RW_MODE_DIRECT and
+                               RW_MODE_DIRECT_REFINED and batches refuse it
+                               with RW_ERR_INVALID                          */
 } rw_opts;
 
 typedef struct {

@@ -75,6 +75,7 @@ rw::Opts to_opts(const rw_opts* o) {
   rw::require(o->sketch_cols >= 64, "opts.sketch_cols must be >= 64");
   rw::require(o->gmres_tol > 0 && o->gmres_maxit >= 1 && o->gmres_restarts >= 1, "bad GMRES options");
   rw::require(o->op_tol == 0.0 || (o->op_tol > 0 && o->op_tol < 1), "opts.op_tol must be 0 or in (0, 1)");
+  rw::require(o->mixed_factor == 0 || o->mixed_factor == 1, "opts.mixed_factor must be 0 or 1");
   r.leaf_points = o->leaf_points;
   r.id_tol = o->id_tol;
   r.n_proxy = o->n_proxy;
@@ -90,6 +91,7 @@ rw::Opts to_opts(const rw_opts* o) {
   r.seed = o->seed;
   r.hole_div_ratio = o->hole_div_ratio;
   r.op_tol = o->op_tol;
+  r.mixed_factor = o->mixed_factor;
   return r;
 }
 
@@ -145,6 +147,7 @@ int rw_default_opts(rw_opts* o) {
   o->seed = d.seed;
   o->hole_div_ratio = d.hole_div_ratio;
   o->op_tol = d.op_tol;
+  o->mixed_factor = d.mixed_factor;
   return RW_OK;
 }
 
@@ -370,6 +373,8 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
   if (!r || !g || !tau || nrhs < 1 || n_targets < 0) return fail(RW_ERR_INVALID, "rw_solve: bad argument");
   if (n_targets > 0 && (!targets || !u)) return fail(RW_ERR_INVALID, "rw_solve: targets and u required");
   if (mode < RW_MODE_DIRECT || mode > RW_MODE_GMRES_MIXED) return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
+  if (r->ref.wall->opts.mixed_factor && (mode == RW_MODE_DIRECT || mode == RW_MODE_DIRECT_REFINED))
+    return fail(RW_ERR_INVALID, "rw_solve: this refinement's X is FP32 (opts.mixed_factor): use an iterative mode");
   int iters = 0;
   double relres = 0.0;
   int rc = guarded([&] {

@@ -75,6 +75,9 @@ int rw_batch_create(int n, const rw_ref_t* refs, void* stream, rw_batch_t* out) 
     b->off.push_back(0);
     for (int i = 0; i < n; ++i) {
       if (!refs[i]) throw rw::Error(RW_ERR_INVALID, "rw_batch_create: null refinement");
+      if (refs[i]->ref.wall->opts.mixed_factor)
+        throw rw::Error(RW_ERR_INVALID, "rw_batch_create: the batch solve is direct; a refinement with an FP32 X "
+                                        "(opts.mixed_factor) needs an iterative mode");
       b->refs.push_back(&refs[i]->ref);
       b->off.push_back(b->off.back() + 2LL * refs[i]->ref.Nn);
     }

@@ -32,6 +32,9 @@ struct Opts {
   // second forward representation at op_tol and a refinement's IDs and A_pp
   // are computed at op_tol.
   double op_tol = 0.0;
+  // 1: refinements compute X = A~^{-1} L with FP32 sweeps (a factorisation for
+  // the preconditioned modes only; see rw_opts.mixed_factor)
+  int mixed_factor = 0;
   double factor_tol() const { return (op_tol > 0.0 && op_tol < id_tol) ? op_tol : id_tol; }
 };
 

@@ -267,7 +267,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
   }
   // a5 (wall part): X_o = A_kk^{-1} L_o
   Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
-  if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
+  if (kk) solve_x(w.hbs, Lo.p, Xo.p, 2 * No, kk, s);
   auto dJk = to_device_tmp(Jk, s), dJpk = to_device_tmp(Jpk, s);
   Rkp.alloc(std::max<size_t>(size_t(kk) * 2 * Np, 1));
   Rpk.alloc(std::max<size_t>(size_t(kpk) * 2 * No, 1));
@@ -280,7 +280,7 @@ void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cu
   if (e1) std::rethrow_exception(e1);
   tr.mark("A_pp inverse (joined)");
   Xp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
-  if (kpk) hpp.apply_inverse_levels(Lp.p, Xp.p, kpk, s);
+  if (kpk) solve_x(hpp, Lp.p, Xp.p, 2 * Np, kpk, s);
   tr.mark("X_p = A_pp^-1 L_p");
   form_w(s);
   tr.mark("W, W^-1, solve program");

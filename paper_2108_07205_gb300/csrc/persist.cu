@@ -13,9 +13,9 @@
 
 namespace {
 
-// v03: options gained op_tol, and the wall may carry a second (forward-only)
-// HBS at that tolerance
-constexpr char kTag[8] = {'R', 'W', 'H', 'B', 'S', 'v', '0', '3'};
+// v04: options gained op_tol and mixed_factor, and the wall may carry a second
+// (forward-only) HBS at op_tol
+constexpr char kTag[8] = {'R', 'W', 'H', 'B', 'S', 'v', '0', '4'};
 
 struct File {
   FILE* f = nullptr;
@@ -100,7 +100,7 @@ void check_opts(const rw::Opts& o) {
                   o.hole_div_ratio > o.bas_ratio && o.sketch_cols >= 64 && o.sketch_width >= 16 &&
                   o.sketch_width <= 4096 && fin(o.gmres_tol) && o.gmres_tol > 0 && o.gmres_maxit >= 1 &&
                   o.gmres_maxit <= 10000 && o.gmres_restarts >= 1 && o.gmres_restarts <= 10000 &&
-                  fin(o.op_tol) && o.op_tol >= 0 && o.op_tol < 1,
+                  fin(o.op_tol) && o.op_tol >= 0 && o.op_tol < 1 && (o.mixed_factor == 0 || o.mixed_factor == 1),
               "rw_hbs_load: corrupt options");
 }
 

@@ -441,7 +441,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   k = kk + kpk;
   // a5 (o part): X_o = A_oo^{-1} L_o
   Xo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
-  if (kk) w.hbs.apply_inverse_levels(Lo.p, Xo.p, kk, s);
+  if (kk) solve_x(w.hbs, Lo.p, Xo.p, 2 * No, kk, s);
   auto dJk = to_device_tmp(Jk, s);
   Rkc.alloc(std::max<size_t>(size_t(kk) * 2 * Nc, 1));
   Rkp.alloc(std::max<size_t>(size_t(kk) * 2 * Np, 1));
@@ -455,12 +455,39 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   if (e1) std::rethrow_exception(e1);
   tr.mark("A_pp inverse (joined)");
   Xp.alloc(std::max<size_t>(size_t(2) * Np * kpk, 1));
-  if (kpk) hpp.apply_inverse_levels(Lp.p, Xp.p, kpk, s);
+  if (kpk) solve_x(hpp, Lp.p, Xp.p, 2 * Np, kpk, s);
   tr.mark("X_p = A_pp^-1 L_p");
   form_w(s);
   tr.mark("W, W^-1, solve program");
   bytes = Lo.bytes() + Lp.bytes() + Rkc.bytes() + Rkp.bytes() + Rpk.bytes() + Xo.bytes() + Xp.bytes() + Winv.bytes() +
           hpp.bytes + pn.buf.bytes() + nn.buf.bytes();
+}
+
+namespace {
+__global__ void k_d2f_x(const double* in, float* out, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    out[i] = float(in[i]);
+}
+__global__ void k_f2d_x(const float* in, double* out, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    out[i] = double(in[i]);
+}
+}  // namespace
+
+void Refinement::solve_x(const Hbs& H, const double* L, double* X, int m, int kc, cudaStream_t s) const {
+  if (!wall->opts.mixed_factor) {
+    H.apply_inverse_levels(L, X, kc, s);
+    return;
+  }
+  // FP32 sweeps: X serves the preconditioner only (W is formed from it in FP64)
+  const size_t n = size_t(m) * kc;
+  TBuf<float> l32(n, s), x32(n, s);
+  const int grid = int(std::min<size_t>((n + 255) / 256, 4096));
+  k_d2f_x<<<grid, 256, 0, s>>>(L, l32.p, n);
+  RW_CHECK_LAUNCH();
+  H.apply_inverse_f32(l32.p, x32.p, kc, s);
+  k_f2d_x<<<grid, 256, 0, s>>>(x32.p, X, n);
+  RW_CHECK_LAUNCH();
 }
 
 void Refinement::form_w(cudaStream_t s) {

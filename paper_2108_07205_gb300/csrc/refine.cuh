@@ -147,6 +147,9 @@ struct Refinement {
   ~Refinement();
 
  private:
+  // X = H^{-1} L (m x k): FP64 sweeps, or FP32 sweeps when the wall's
+  // opts.mixed_factor is set
+  void solve_x(const Hbs& H, const double* L, double* X, int m, int k, cudaStream_t s) const;
   // a6 and the solve program, shared by both factorisations: W = I + R X,
   // W^{-1}, its condition estimate, and the persistent solve program.
   void form_w(cudaStream_t s);

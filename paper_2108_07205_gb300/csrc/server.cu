@@ -296,6 +296,8 @@ int rw_server_submit(rw_server_t sv, const rw_request* q, long long* ticket) {
     return sfail(RW_ERR_INVALID, "rw_server_submit: bad request");
   if (q->mode < RW_MODE_DIRECT || q->mode > RW_MODE_GMRES_MIXED)
     return sfail(RW_ERR_INVALID, "rw_server_submit: unknown mode");
+  if (q->wall && q->wall->wall.opts.mixed_factor && (q->mode == RW_MODE_DIRECT || q->mode == RW_MODE_DIRECT_REFINED))
+    return sfail(RW_ERR_INVALID, "rw_server_submit: walls with opts.mixed_factor take an iterative mode");
   Req r;
   r.wall = q->wall;
   r.panels.assign(q->panel_ids, q->panel_ids + q->n_cut);

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("dense_pp_max_points", ctypes.c_int), ("sketch_cols", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
                 ("gmres_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("hole_div_ratio", ctypes.c_double),
-                ("op_tol", ctypes.c_double)]
+                ("op_tol", ctypes.c_double), ("mixed_factor", ctypes.c_int)]
 
 
 class HbsStats(ctypes.Structure):

@@ -18,7 +18,7 @@ import numpy as np
 
 from paper_2108_07205_gb300 import rwsolve
 
-TAG = b"RWHBSv03"
+TAG = b"RWHBSv04"
 
 
 class InternalOpts(ctypes.Structure):
@@ -28,7 +28,7 @@ class InternalOpts(ctypes.Structure):
                 ("bas_ratio", ctypes.c_double), ("dense_pp_max_points", ctypes.c_int), ("sketch_cols", ctypes.c_int),
                 ("sketch_width", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
                 ("gmres_restarts", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("hole_div_ratio", ctypes.c_double),
-                ("op_tol", ctypes.c_double)]
+                ("op_tol", ctypes.c_double), ("mixed_factor", ctypes.c_int)]
 
 
 def default_internal_opts():
@@ -37,7 +37,7 @@ def default_internal_opts():
     o.n_proxy_refine, o.div_ratio, o.bas_ratio = 96, 2.0, 1.5
     o.dense_pp_max_points, o.sketch_cols, o.sketch_width = 64, 2048, 192
     o.gmres_tol, o.gmres_maxit, o.gmres_restarts = 1e-10, 30, 4
-    o.seed, o.hole_div_ratio, o.op_tol = 0x5eed2108, 4.0, 0.0
+    o.seed, o.hole_div_ratio, o.op_tol, o.mixed_factor = 0x5eed2108, 4.0, 0.0, 0
     return o
 
 
@@ -86,7 +86,7 @@ def load(tmp_path, data, name):
 
 
 def test_internal_option_record_size():
-    assert ctypes.sizeof(InternalOpts) == 112
+    assert ctypes.sizeof(InternalOpts) == 120
 
 
 def test_intact_file_passes_the_checks(tmp_path):

@@ -96,6 +96,32 @@ def test_certified_residual_512_vs_oracle(lib, mode):
     w.close()
 
 
+def test_mixed_factor_preconditioner_only(lib):
+    """A wall with opts.mixed_factor: X = A~^{-1} L by FP32 sweeps, W formed
+    from it in FP64.  The preconditioned modes still certify 1e-10 against
+    the oracle's dense operator; the direct modes refuse the refinement."""
+    P = 256
+    panels, levels = inputs.refinement_window(23, P, 8, 3, 3)
+    w = rwsolve.Wall("channel", P, opts=rwsolve.default_opts(op_tol=1e-14, mixed_factor=1))
+    r = w.refine(panels, levels)
+    g, (sx, sy, f) = pair_data(r, 8, 16)
+    o = D.refine("channel", {}, P, panels, levels)
+    A = S.matrix(o["n"])
+    g_or = S.boundary_data(o["n"], sx, sy, f)
+    for m in (rwsolve.MODE_GMRES_MIXED, rwsolve.MODE_GMRES_FP32, rwsolve.MODE_DIRECT_IR):
+        tau = np.empty_like(g)
+        info = r.solve(g, tau, nrhs=16, mode=m)
+        rres = (np.linalg.norm(A @ tau.T - g_or, axis=0) / np.linalg.norm(g_or, axis=0)).max()
+        print(f"mixed factor, mode {m}: iters {info['iters']}, true residual {rres:.2e}")
+        assert info["rel_residual"] <= 1e-10 and rres <= 1e-10
+    for m in (rwsolve.MODE_DIRECT, rwsolve.MODE_DIRECT_REFINED):
+        with pytest.raises(rwsolve.RWError) as e:
+            r.solve(g, np.empty_like(g), nrhs=16, mode=m)
+        assert e.value.code == -1
+    r.close()
+    w.close()
+
+
 def test_certified_residual_2048_full_size(lib):
     P, nrhs = 2048, 64
     w = rwsolve.Wall("channel", P, opts=rwsolve.default_opts(op_tol=1e-14))
