@@ -14,12 +14,15 @@ reference wall's HBS (built once) is static and excluded, as the paper's
 T_static.
 
 Two arms run the same steps:
-  * the headline, RW_MODE_GMRES_MIXED: FP64 FGMRES whose preconditioner is
-    Algorithm 1 with FP32 HBS sweeps and an FP32 Woodbury correction (W^{-1}
-    in FP64) and whose operator products run in double-FP32;
-  * "fp64_arm", RW_MODE_DIRECT_IR: Algorithm 1 in FP64 plus FP64 iterative
-    refinement against the same operator, the plain FP64 path to the same
-    certified residual.
+  * the headline, RW_MODE_DIRECT_IR_DF: Algorithm 1 plus iterative
+    refinement against the operator at 1e-14, every product in double-FP32
+    (each FP64 factor held as a pair of FP32 numbers, products and sums
+    compensated: FP64-level accuracy from the FP32 units), X = A~^{-1} L of
+    the refinement by double-FP32 sweeps;
+  * "fp64_arm", RW_MODE_DIRECT_IR: the same algorithm in FP64 (the plain
+    FP64 path to the same certified residual).
+(--mode mixed: FP64 FGMRES preconditioned by Algorithm 1 with FP32 sweeps,
+operator products in double-FP32.)
 After the timed steps, sampled steps of each arm are re-run and their
 density checked against the exact refined operator A_nn (every entry
 evaluated on the fly): the true relative residual is printed per arm.
@@ -66,9 +69,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="mixed",
-                    choices=["mixed", "fp64_ir", "direct", "gmres", "gmres_bf16", "refined"])
-    ap.add_argument("--compare", default="fp64_ir", choices=["fp64_ir", "direct", "gmres", "none"],
+    ap.add_argument("--mode", default="df_ir",
+                    choices=["df_ir", "mixed", "fp64_ir", "direct", "gmres", "gmres_bf16", "refined"])
+    ap.add_argument("--compare", default="fp64_ir", choices=["fp64_ir", "mixed", "direct", "gmres", "none"],
                     help="second arm timed on the same steps (none: skip)")
     ap.add_argument("--verify-steps", type=int, default=3, help="steps of each arm re-run and checked against A_nn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -83,10 +86,15 @@ def parse():
     return ap.parse_args()
 
 
-MODE_NAMES = {"mixed": "MODE_GMRES_MIXED", "fp64_ir": "MODE_DIRECT_IR", "direct": "MODE_DIRECT",
-              "gmres": "MODE_GMRES_FP32", "gmres_bf16": "MODE_GMRES_BF16", "refined": "MODE_DIRECT_REFINED"}
-MODE_DTYPE = {"mixed": "f64+f32", "fp64_ir": "f64", "direct": "f64", "gmres": "f64+f32", "gmres_bf16": "f64+bf16",
-              "refined": "f64"}
+MODE_NAMES = {"df_ir": "MODE_DIRECT_IR_DF", "mixed": "MODE_GMRES_MIXED", "fp64_ir": "MODE_DIRECT_IR",
+              "direct": "MODE_DIRECT", "gmres": "MODE_GMRES_FP32", "gmres_bf16": "MODE_GMRES_BF16",
+              "refined": "MODE_DIRECT_REFINED"}
+MODE_DTYPE = {"df_ir": "f32x2+f64", "mixed": "f64+f32", "fp64_ir": "f64", "direct": "f64",
+              "gmres": "f64+f32", "gmres_bf16": "f64+bf16", "refined": "f64"}
+# how each arm's refinements compute X = A~^{-1} L (rw_opts.mixed_factor):
+# FP64 sweeps for the FP64 arms, double-FP32 sweeps for the double-FP32
+# iterative refinement, FP32 sweeps for the FP32-preconditioned FGMRES
+MODE_FACTOR = {"df_ir": 2, "mixed": 1, "gmres": 1, "gmres_bf16": 1}
 
 
 def mode_id(name):
@@ -397,7 +405,8 @@ def workload_config(args):
     return {"workload": w.get(args.workload, args.workload), "mode": MODE_NAMES[args.mode],
             "compare": None if args.compare == "none" else MODE_NAMES[args.compare],
             "hbs_leaf": 64, "id_tol": 1e-12, "op_tol": OP_TOL, "residual_tol": 1e-10,
-            "mixed_factor": "X = A~^-1 L by FP32 sweeps for the preconditioned modes (W and W^-1 in FP64)",
+            "x_factor": {m: ["FP64", "FP32", "double-FP32"][MODE_FACTOR.get(m, 0)] + " sweeps"
+                         for m in ([args.mode] + ([] if args.compare == "none" else [args.compare]))},
             "l2": "flushed (256 MB write) before each step"}
 
 
@@ -405,7 +414,8 @@ def refine_probe(k):
     import torch
     from paper_2108_07205_gb300 import rwsolve, inputs
     rwsolve.load(build_if_missing=True)
-    wall = rwsolve.Wall("channel", P_PANELS)
+    # the wall of the headline arm: operator tolerance 1e-14, double-FP32 sweeps for X
+    wall = rwsolve.Wall("channel", P_PANELS, opts=rwsolve.default_opts(op_tol=OP_TOL, mixed_factor=2))
     torch.cuda.synchronize()
     for panels, levels in inputs.time_schedule(17, P_PANELS, k):
         t0 = time.time()
@@ -420,7 +430,8 @@ def run_serving(args):
     """Serving workload: resident walls (channel 512/1024/2048 panels, star 1024
     panels, operator tolerance 1e-14); each request refines 1-64 contiguous
     panels by 2-6 levels and carries 1-32 right-hand sides from exterior point
-    forces, solved in --mode (default the mixed FGMRES to a certified 1e-10).
+    forces, solved in --mode (default the double-FP32 iterative refinement to
+    a certified 1e-10).
     Closed loop (all requests at once) gives the saturation rate; an open loop
     with Poisson arrivals at 0.8 x that rate gives p50/p99 latency.  Sampled
     open-loop requests are refactored afterwards and their densities checked
@@ -429,7 +440,7 @@ def run_serving(args):
     from paper_2108_07205_gb300 import rwsolve, inputs
     rwsolve.load(build_if_missing=True)
     mode = mode_id(args.mode)
-    op = rwsolve.default_opts(op_tol=OP_TOL)
+    op = rwsolve.default_opts(op_tol=OP_TOL, mixed_factor=MODE_FACTOR.get(args.mode, 0))
     walls = [rwsolve.Wall("channel", 512, opts=op), rwsolve.Wall("channel", 1024, opts=op),
              rwsolve.Wall("channel", 2048, opts=op), rwsolve.Wall("star", 1024, (0.3, 5, 1.0), opts=op)]
     torch.cuda.synchronize()
@@ -683,15 +694,22 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     rwsolve.load(build_if_missing=True)
-    t0 = time.time()
-    wall = rwsolve.Wall("channel", P_PANELS, opts=rwsolve.default_opts(op_tol=OP_TOL))
-    torch.cuda.synchronize()
-    build_s = time.time() - t0
+    arms = [args.mode] + ([args.compare] if args.compare not in ("none", args.mode) else [])
+    # one wall per factorisation kind the arms need (the HBS of A_oo is the
+    # same; only how refinements compute X differs)
+    walls = {}
+    build_s = None
+    for m in arms:
+        mf = MODE_FACTOR.get(m, 0)
+        if mf in walls:
+            continue
+        t0 = time.time()
+        walls[mf] = rwsolve.Wall("channel", P_PANELS, opts=rwsolve.default_opts(op_tol=OP_TOL, mixed_factor=mf))
+        torch.cuda.synchronize()
+        if build_s is None:
+            build_s = time.time() - t0
+    wall = walls[MODE_FACTOR.get(arms[0], 0)]
     hst = wall.stats()
-    # the preconditioned modes factor on a wall whose refinements compute
-    # X = A~^{-1} L with FP32 sweeps (it serves only their preconditioner)
-    wall_mixed = rwsolve.Wall("channel", P_PANELS, opts=rwsolve.default_opts(op_tol=OP_TOL, mixed_factor=1))
-    torch.cuda.synchronize()
     total = args.warmup + args.steps
     sched = inputs.time_schedule(replicas.schedule_seed(rank), P_PANELS, 2 * total + 1)
     dev_in, host_in = [], []
@@ -702,12 +720,11 @@ def run_ours(args, rank, world, local):
         dev_in.append(tuple(x.to(dev) for x in (torch.from_numpy(src), torch.from_numpy(fd), torch.from_numpy(tg))))
     # L2 flush buffer (> 129 MB L2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    arms = [args.mode] + ([args.compare] if args.compare not in ("none", args.mode) else [])
     res = {}
     for i, m in enumerate(arms):
         try:
-            w_arm = wall_mixed if m in ("mixed", "gmres", "gmres_bf16") else wall
-            res[m] = run_arm(args, w_arm, m, sched, dev_in, host_in, flush, local, profile=(i == 0),
+            res[m] = run_arm(args, walls[MODE_FACTOR.get(m, 0)], m, sched, dev_in, host_in, flush, local,
+                             profile=(i == 0),
                              verify=args.verify_steps)
         except rwsolve.RWError as e:
             res[m] = {"error": str(e)}
@@ -730,8 +747,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     sweep = {"ms": float(np.mean([a.elapsed_time(c) for a, c in times])),
              "bytes": 8 * hst["inv_elems"] + 8 * 4 * 2 * hst["n_points"]}
-    wall.close()
-    wall_mixed.close()
+    for w in walls.values():
+        w.close()
     for m in res:
         if "ms" in res[m]:
             res[m]["ms"], res[m]["ms_e2e"] = replicas.max_over_ranks([res[m]["ms"], res[m]["ms_e2e"]])

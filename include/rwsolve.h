@@ -91,15 +91,16 @@ typedef struct {
                                the representation of A_pp at op_tol, so that
                                A~ + L R matches A_ext to about op_tol while the
                                reference wall's inverse stays at id_tol      */
-  int mixed_factor;         /* 0 (default) or 1: refinements of this wall
-                               compute X = A~^{-1} L with FP32 sweeps and form
-                               W = I + R X from it in FP64 -- a factorisation
-                               that serves only as the preconditioner of the
-                               iterative modes (RW_MODE_GMRES_*, and
-                               RW_MODE_DIRECT_IR, which needs more
-                               corrections); RW_MODE_DIRECT and
-                               RW_MODE_DIRECT_REFINED and batches refuse it
-                               with RW_ERR_INVALID                          */
+  int mixed_factor;         /* 0 (default): refinements of this wall compute
+                               X = A~^{-1} L with FP64 sweeps.  1: with FP32
+                               sweeps, 2: with double-FP32 sweeps; W = I +
+                               R X is formed from X in FP64 either way.
+                               Such a factorisation serves only the
+                               iterative modes (RW_MODE_GMRES_*,
+                               RW_MODE_DIRECT_IR, RW_MODE_DIRECT_IR_DF; with
+                               1 they need more iterations);
+                               RW_MODE_DIRECT, RW_MODE_DIRECT_REFINED and
+                               batches refuse it with RW_ERR_INVALID        */
 } rw_opts;
 
 typedef struct {
@@ -302,6 +303,16 @@ int rw_stokeslet_data(rw_ref_t r, int n_src, const double* src, int nrhs,
                                  (relative error ~1e-14 per product) from the
                                  FP32 units; Krylov vectors, Hessenberg
                                  matrix, X and W^{-1} stay FP64 */
+#define RW_MODE_DIRECT_IR_DF 6 /* RW_MODE_DIRECT_IR with every product in
+                                 double-FP32 (the representation above): the
+                                 HBS inverse sweeps of A_oo and A_pp, the
+                                 Woodbury terms R, W^{-1} and X of Algorithm
+                                 1 and the op_tol operator A~ + L R of the
+                                 corrections; vectors, sums of corrections
+                                 and residual norms stay FP64.  One direct
+                                 solve reaches a relative residual near
+                                 1e-14 x the conditioning of A_nn, each
+                                 correction multiplies it by about as much  */
 
 /* y = A_nn tau with every entry of the refined operator evaluated on the fly
  * (Sec. 2, Eq. interior_BIE_discretized2 on the refined nodes): the exact

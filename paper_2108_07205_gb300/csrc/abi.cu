@@ -75,7 +75,7 @@ rw::Opts to_opts(const rw_opts* o) {
   rw::require(o->sketch_cols >= 64, "opts.sketch_cols must be >= 64");
   rw::require(o->gmres_tol > 0 && o->gmres_maxit >= 1 && o->gmres_restarts >= 1, "bad GMRES options");
   rw::require(o->op_tol == 0.0 || (o->op_tol > 0 && o->op_tol < 1), "opts.op_tol must be 0 or in (0, 1)");
-  rw::require(o->mixed_factor == 0 || o->mixed_factor == 1, "opts.mixed_factor must be 0 or 1");
+  rw::require(o->mixed_factor >= 0 && o->mixed_factor <= 2, "opts.mixed_factor must be 0, 1 or 2");
   r.leaf_points = o->leaf_points;
   r.id_tol = o->id_tol;
   r.n_proxy = o->n_proxy;
@@ -372,9 +372,10 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
              int mode, void* stream, rw_info* info) {
   if (!r || !g || !tau || nrhs < 1 || n_targets < 0) return fail(RW_ERR_INVALID, "rw_solve: bad argument");
   if (n_targets > 0 && (!targets || !u)) return fail(RW_ERR_INVALID, "rw_solve: targets and u required");
-  if (mode < RW_MODE_DIRECT || mode > RW_MODE_GMRES_MIXED) return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
+  if (mode < RW_MODE_DIRECT || mode > RW_MODE_DIRECT_IR_DF) return fail(RW_ERR_INVALID, "rw_solve: unknown mode");
   if (r->ref.wall->opts.mixed_factor && (mode == RW_MODE_DIRECT || mode == RW_MODE_DIRECT_REFINED))
-    return fail(RW_ERR_INVALID, "rw_solve: this refinement's X is FP32 (opts.mixed_factor): use an iterative mode");
+    return fail(RW_ERR_INVALID,
+                "rw_solve: this refinement's X is not FP64 (opts.mixed_factor): use an iterative mode");
   int iters = 0;
   double relres = 0.0;
   int rc = guarded([&] {
@@ -387,8 +388,8 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     } else if (mode == RW_MODE_DIRECT_REFINED) {
       f.solve_refined(ag.p, at.p, nrhs, 1, s);
       iters = 1;
-    } else if (mode == RW_MODE_DIRECT_IR) {
-      f.solve_ir(ag.p, at.p, nrhs, s, &iters, &relres);
+    } else if (mode == RW_MODE_DIRECT_IR || mode == RW_MODE_DIRECT_IR_DF) {
+      f.solve_ir(ag.p, at.p, nrhs, s, &iters, &relres, mode == RW_MODE_DIRECT_IR_DF);
     } else {
       f.solve_gmres(ag.p, at.p, nrhs, s, &iters, &relres, mode == RW_MODE_GMRES_BF16, mode == RW_MODE_GMRES_MIXED);
     }
@@ -402,7 +403,7 @@ int rw_solve(rw_ref_t r, int nrhs, const double* g, double* tau, int n_targets, 
     if ((mode == RW_MODE_GMRES_FP32 || mode == RW_MODE_GMRES_BF16 || mode == RW_MODE_GMRES_MIXED) &&
         relres > f.wall->opts.gmres_tol)
       throw rw::Error(RW_ERR_NOT_CONVERGED, "rw_solve: GMRES stopped at relative residual " + std::to_string(relres));
-    if (mode == RW_MODE_DIRECT_IR && relres > f.wall->opts.gmres_tol)
+    if ((mode == RW_MODE_DIRECT_IR || mode == RW_MODE_DIRECT_IR_DF) && relres > f.wall->opts.gmres_tol)
       throw rw::Error(RW_ERR_NOT_CONVERGED,
                       "rw_solve: iterative refinement stopped at relative residual " + std::to_string(relres));
   });

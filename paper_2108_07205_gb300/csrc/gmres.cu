@@ -86,7 +86,8 @@ void Refinement::make_mixed() const {
   cudaStream_t s = streams.main;
   AllocStreamScope scope(s);
   for (auto pr : {std::make_pair(&Lo, &Lo2), std::make_pair(&Lp, &Lp2), std::make_pair(&Rkc, &Rkc2),
-                  std::make_pair(&Rkp, &Rkp2), std::make_pair(&Rpk, &Rpk2)}) {
+                  std::make_pair(&Rkp, &Rkp2), std::make_pair(&Rpk, &Rpk2), std::make_pair(&Xo, &Xo2),
+                  std::make_pair(&Xp, &Xp2), std::make_pair(&Winv, &Winv2)}) {
     pr.second->alloc(pr.first->n);
     copy_d2df(pr.first->p, pr.second->p, pr.first->n, s);
   }
@@ -127,7 +128,7 @@ void Refinement::apply_els_df(const double* xo, const double* xp, double* yo, do
 }
 
 void Refinement::solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters_out,
-                          double* relres_out) const {
+                          double* relres_out, bool df) const {
   const Opts& o = wall->opts;
   const int no = 2 * No, np = 2 * Np;
   TBuf<double> go(size_t(no) * nrhs, s), gp(size_t(np) * nrhs, s), xo(size_t(no) * nrhs, s), xp(size_t(np) * nrhs, s);
@@ -137,9 +138,10 @@ void Refinement::solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s
   gather_scatter(g, 2 * Nn, n_from_o.p, go.p, no, n_to_o.p, nko, nrhs, s);
   gather_scatter(g, 2 * Nn, n_from_p.p, gp.p, np, n_to_p.p, nkp, nrhs, s);
   // Algorithm 1 in ext space: y = A~^{-1} v, then the Woodbury correction
+  // (double-FP32: the GEMM programs at any nrhs)
   auto direct = [&](const double* vo, const double* vp, double* yo, double* yp) {
-    if (nrhs > 8) {
-      run_prog(dir_prog(s), vo, vp, yo, yp, (double*)nullptr, nrhs, s);
+    if (df || nrhs > 8) {
+      run_prog(dir_prog(s, df), vo, vp, yo, yp, (double*)nullptr, nrhs, s);
       return;
     }
     wall->hbs.apply_inverse_levels(vo, yo, nrhs, s);
@@ -152,7 +154,8 @@ void Refinement::solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s
   double worst = 0.0;
   for (;; ++it) {
     // r = g - (A~ + L R) x
-    apply_els(xo.p, xp.p, ro.p, rp.p, nrhs, s);
+    if (df) apply_els_df(xo.p, xp.p, ro.p, rp.p, nrhs, s);
+    else apply_els(xo.p, xp.p, ro.p, rp.p, nrhs, s);
     axpby(go.p, ro.p, ro.n, 1.0, -1.0, s);
     axpby(gp.p, rp.p, rp.n, 1.0, -1.0, s);
     std::vector<double> rn = col_dots(ro.p, rp.p, ro.p, rp.p, no, np, nrhs, 1, dots.p, s);

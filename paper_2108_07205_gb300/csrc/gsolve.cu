@@ -125,9 +125,9 @@ int Hbs::emit_forward_g(GP& P, int p0, int xb, long long xo, int ldx, int yb, lo
 template <class GP>
 int Hbs::emit_inverse_g(GP& P, int p0, int xb, long long xo, int ldx, int yb, long long yo, int ldy, int atype) const {
   const int W = P.ws_base();
-  auto Fm = [&](const Level& LV) { return pick_ptr(atype, LV.F, &LV.F32, &LV.F16, (const DBuf<float2>*)nullptr); };
-  auto Gm = [&](const Level& LV) { return pick_ptr(atype, LV.G, &LV.G32, &LV.G16, (const DBuf<float2>*)nullptr); };
-  auto Em = [&](const Level& LV) { return pick_ptr(atype, LV.E, &LV.E32, &LV.E16, (const DBuf<float2>*)nullptr); };
+  auto Fm = [&](const Level& LV) { return pick_ptr(atype, LV.F, &LV.F32, &LV.F16, &LV.F2); };
+  auto Gm = [&](const Level& LV) { return pick_ptr(atype, LV.G, &LV.G32, &LV.G16, &LV.G2); };
+  auto Em = [&](const Level& LV) { return pick_ptr(atype, LV.E, &LV.E32, &LV.E16, &LV.E2); };
   if (L == 0) {
     const int n = 2 * N;
     put(P, p0, Gm(lev[0]), atype, 0, n, n, n, xb, xo, ldx, yb, yo, ldy, 1.0, 0.0);
@@ -226,6 +226,12 @@ void Hbs::forward_gemm(const double* x, double* y, int nrhs, bool df, cudaStream
 
 void Hbs::inverse_gemm(const double* b, double* x, int nrhs, cudaStream_t s) const {
   run_cached<double>(ginv64, [&](GProgram<double>& G) { emit_inverse_g(G, 0, 0, 0, 2 * N, 1, 0, 2 * N, MA_F64); },
+                     b, x, nrhs, own_stream, s);
+}
+
+void Hbs::inverse_gemm_df(const double* b, double* x, int nrhs, cudaStream_t s) const {
+  make_df_inv(s);
+  run_cached<double>(ginvdf, [&](GProgram<double>& G) { emit_inverse_g(G, 0, 0, 0, 2 * N, 1, 0, 2 * N, MA_DF); },
                      b, x, nrhs, own_stream, s);
 }
 

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <numeric>
 #include <type_traits>
 
@@ -290,7 +291,15 @@ TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdM
     batched_id_interp(ip, mxe, s);
     Pl.push_back(std::move(P));
     levels.push_back(cur);
-    tr.mark(cur.size() == 1 ? "level (root)" : "level");
+    if (tr.on) {
+      long long ksum = 0;
+      int kmax = 0;
+      for (auto& j : cur) { ksum += j.k; kmax = std::max(kmax, j.k); }
+      char msg[160];
+      std::snprintf(msg, sizeof msg, "%s: %zu problems, %d x %zu candidates, ranks sum %lld max %d",
+                    cur.size() == 1 ? "level (root)" : "level", cur.size(), nr, cand_all.size(), ksum, kmax);
+      tr.mark(msg);
+    }
     if (cur.size() == 1) break;
     // Next level: pairwise merges while the level has enough problems to
     // occupy the GPU; once it has few, one root over every remaining
@@ -973,6 +982,23 @@ void Hbs::make_df(cudaStream_t s_caller) const {
   }
   RW_CUDA(cudaStreamSynchronize(s));
   has_df = true;
+}
+
+void Hbs::make_df_inv(cudaStream_t s_caller) const {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (has_df_inv) return;
+  AllocStreamScope scope(own_stream);
+  cudaStream_t s = own_stream ? own_stream : s_caller;  // copies ordered after the allocation
+  for (int l = 0; l <= L; ++l) {
+    const Level& LV = lev[l];
+    for (auto pr : {std::make_pair(&LV.E, &LV.E2), std::make_pair(&LV.F, &LV.F2), std::make_pair(&LV.G, &LV.G2)}) {
+      pr.second->alloc(pr.first->n);
+      copy_d2df(pr.first->p, pr.second->p, pr.first->n, s);
+    }
+  }
+  RW_CUDA(cudaStreamSynchronize(s));
+  has_df_inv = true;
 }
 
 void Hbs::make_fp32_fwd(cudaStream_t s_caller) const {

@@ -32,8 +32,9 @@ struct Opts {
   // second forward representation at op_tol and a refinement's IDs and A_pp
   // are computed at op_tol.
   double op_tol = 0.0;
-  // 1: refinements compute X = A~^{-1} L with FP32 sweeps (a factorisation for
-  // the preconditioned modes only; see rw_opts.mixed_factor)
+  // How refinements compute X = A~^{-1} L (a factorisation for the iterative
+  // modes only when set; see rw_opts.mixed_factor): 0 FP64 sweeps, 1 FP32
+  // sweeps, 2 double-FP32 sweeps
   int mixed_factor = 0;
   double factor_tol() const { return (op_tol > 0.0 && op_tol < id_tol) ? op_tol : id_tol; }
 };
@@ -108,6 +109,7 @@ class Hbs {
     DBuf<__nv_bfloat16> G16, E16, F16;  // BF16 copies (preconditioner sweeps)
     mutable DBuf<float2> U2, Vt2, B2, D2;  // double-FP32 copies of the forward factors (made on first use)
     mutable DBuf<float> Uf, Vtf, Bf, Df;   // FP32 copies of the forward factors (made on first use)
+    mutable DBuf<float2> E2, F2, G2;       // double-FP32 copies of the inverse factors (made on first use)
   };
   std::vector<Level> lev;
   long long inv_elems = 0, fwd_elems = 0;
@@ -144,6 +146,8 @@ class Hbs {
   cudaStream_t own_stream = nullptr;
   void make_df(cudaStream_t s) const;
   mutable bool has_df = false;
+  void make_df_inv(cudaStream_t s) const;
+  mutable bool has_df_inv = false;
   void make_fp32_fwd(cudaStream_t s) const;
   mutable bool has_fp32_fwd = false;
   void make_fp32(cudaStream_t s);
@@ -170,11 +174,14 @@ class Hbs {
   int emit_forward_g(GP& P, int p0, int xb, long long xo, int ldx, int yb, long long yo, int ldy, int atype) const;
   template <class GP>
   int emit_inverse_g(GP& P, int p0, int xb, long long xo, int ldx, int yb, long long yo, int ldy, int atype) const;
-  mutable GProgram<double> gfwd64, gfwddf, ginv64;
+  mutable GProgram<double> gfwd64, gfwddf, ginv64, ginvdf;
   mutable GProgram<float> ginv32, ginv16;
   // one launch per 64 right-hand sides on the cached programs (built on first use)
   void forward_gemm(const double* x, double* y, int nrhs, bool df, cudaStream_t s) const;
   void inverse_gemm(const double* b, double* x, int nrhs, cudaStream_t s) const;
+  // x = A^{-1} b with the sweep's products in double-FP32 (FP64 vectors; the
+  // copies of E, F*, G are made on first use), any nrhs
+  void inverse_gemm_df(const double* b, double* x, int nrhs, cudaStream_t s) const;
   void inverse_gemm_f32(const float* b, float* x, int nrhs, bool bf16, cudaStream_t s) const;
 
  private:

@@ -100,7 +100,7 @@ void check_opts(const rw::Opts& o) {
                   o.hole_div_ratio > o.bas_ratio && o.sketch_cols >= 64 && o.sketch_width >= 16 &&
                   o.sketch_width <= 4096 && fin(o.gmres_tol) && o.gmres_tol > 0 && o.gmres_maxit >= 1 &&
                   o.gmres_maxit <= 10000 && o.gmres_restarts >= 1 && o.gmres_restarts <= 10000 &&
-                  fin(o.op_tol) && o.op_tol >= 0 && o.op_tol < 1 && (o.mixed_factor == 0 || o.mixed_factor == 1),
+                  fin(o.op_tol) && o.op_tol >= 0 && o.op_tol < 1 && (o.mixed_factor >= 0 && o.mixed_factor <= 2),
               "rw_hbs_load: corrupt options");
 }
 

@@ -479,6 +479,10 @@ void Refinement::solve_x(const Hbs& H, const double* L, double* X, int m, int kc
     H.apply_inverse_levels(L, X, kc, s);
     return;
   }
+  if (wall->opts.mixed_factor == 2) {  // double-FP32 sweeps, one launch per 64 columns
+    H.inverse_gemm_df(L, X, kc, s);
+    return;
+  }
   // FP32 sweeps: X serves the preconditioner only (W is formed from it in FP64)
   const size_t n = size_t(m) * kc;
   TBuf<float> l32(n, s), x32(n, s);

@@ -117,9 +117,12 @@ struct Refinement {
   void apply_els(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
   // the same with every product in double-FP32 (FP64-level accuracy)
   void apply_els_df(const double* xo, const double* xp, double* yo, double* yp, int nrhs, cudaStream_t s) const;
-  // Algorithm 1 solve plus FP64 iterative refinement against apply_els until
-  // the relative residual is <= gmres_tol (RW_MODE_DIRECT_IR).
-  void solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres) const;
+  // Algorithm 1 solve plus iterative refinement against apply_els until the
+  // relative residual is <= gmres_tol: FP64 (RW_MODE_DIRECT_IR), or with
+  // every product of the solves and of the operator in double-FP32 when df
+  // is set (RW_MODE_DIRECT_IR_DF).
+  void solve_ir(const double* g, double* tau, int nrhs, cudaStream_t s, int* iters, double* relres,
+                bool df = false) const;
   // Many right-hand sides: the whole ELS operator, the whole FP64 direct
   // solve (Algorithm 1 in ext space) and the low-precision preconditioner as
   // GEMM programs, the wall's and the refined arc's trees side by side in
@@ -130,25 +133,26 @@ struct Refinement {
   // iterations of the mixed mode): same bases, FP32.
   const GProgram<float>& els_prog32(cudaStream_t s) const;
   // Direct solve in ext space: bases 0 = g_o, 1 = g_p, 2 = workspace,
-  // 3 = y_o, 4 = y_p.
-  const GProgram<double>& dir_prog(cudaStream_t s) const;
+  // 3 = y_o, 4 = y_p; FP64 factors, or their double-FP32 copies (df).
+  const GProgram<double>& dir_prog(cudaStream_t s, bool df = false) const;
   // Preconditioner, FP32 vectors: part a = sweeps and r = R y (bases 0 = v_o,
   // 1 = v_p, 2 = workspace, 3 = y_o, 4 = y_p, 5 = r, k x nrhs); part b =
   // y -= X z (bases 3, 4, and 5 = z); W^{-1} is applied in FP64 between them.
   const GProgram<float>& pre_prog_a(bool bf16, cudaStream_t s) const;
   const GProgram<float>& pre_prog_b(cudaStream_t s) const;
-  mutable GProgram<double> g_els64, g_elsdf, g_dir64;
+  mutable GProgram<double> g_els64, g_elsdf, g_dir64, g_dirdf;
   mutable GProgram<float> g_pre32, g_pre16, g_preb, g_els32;
-  // double-FP32 copies of L and R, FP32 copies of R and X (made on first use)
+  // double-FP32 copies of L, R, X and W^{-1}, FP32 copies of R, X and L
+  // (made on first use)
   void make_mixed() const;
   mutable bool has_mixed = false;
-  mutable DBuf<float2> Lo2, Lp2, Rkc2, Rkp2, Rpk2;
+  mutable DBuf<float2> Lo2, Lp2, Rkc2, Rkp2, Rpk2, Xo2, Xp2, Winv2;
   mutable DBuf<float> Rkc32, Rkp32, Rpk32, Xo32, Xp32, Lo32, Lp32;
   ~Refinement();
 
  private:
-  // X = H^{-1} L (m x k): FP64 sweeps, or FP32 sweeps when the wall's
-  // opts.mixed_factor is set
+  // X = H^{-1} L (m x k): FP64 sweeps, or FP32 (opts.mixed_factor 1) or
+  // double-FP32 (2) sweeps
   void solve_x(const Hbs& H, const double* L, double* X, int m, int k, cudaStream_t s) const;
   // a6 and the solve program, shared by both factorisations: W = I + R X,
   // W^{-1}, its condition estimate, and the persistent solve program.

@@ -75,19 +75,38 @@ const GProgram<float>& Refinement::els_prog32(cudaStream_t s) const {
   return P;
 }
 
-const GProgram<double>& Refinement::dir_prog(cudaStream_t s) const {
-  GProgram<double>& P = g_dir64;
+namespace {
+// Algorithm 1's Woodbury correction after the sweeps (which end before phase
+// p0): r = R y, z = W^{-1} r, y -= X z (Eq. wood); factors of one type MT.
+template <class MT>
+void emit_woodbury(GProgram<double>& P, int p0, const MT* Rkc, const MT* Rkp, const MT* Rpk, const MT* Winv,
+                   const MT* Xo, const MT* Xp, int kk, int kpk, int k, int No, int Nc, int Np, const int* dc) {
+  const int W = P.ws_base();
+  const long long r = P.ws_alloc(k), z = P.ws_alloc(k);
+  int p = emit_r_times(P, p0, Rkc, Rkp, Rpk, kk, kpk, k, No, Nc, Np, dc, 3, 4, W, r, -1);
+  P.gemm(p, Winv, k, k, k, W, r, -1, W, z, -1, 1.0, 0.0);
+  ++p;
+  if (kk) P.gemm(p, Xo, 2 * No, kk, 2 * No, W, z, -1, 3, 0, 2 * No, -1.0, 1.0);
+  if (kpk) P.gemm(p, Xp, 2 * Np, kpk, 2 * Np, W, z + kk, -1, 4, 0, 2 * Np, -1.0, 1.0);
+}
+}  // namespace
+
+const GProgram<double>& Refinement::dir_prog(cudaStream_t s, bool df) const {
+  GProgram<double>& P = df ? g_dirdf : g_dir64;
   if (P.finalized()) return P;
-  const int pa = wall->hbs.emit_inverse_g(P, 0, 0, 0, 2 * No, 3, 0, 2 * No, MA_F64);
-  const int pb = hpp.emit_inverse_g(P, 0, 1, 0, 2 * Np, 4, 0, 2 * Np, MA_F64);
+  if (df) {
+    make_mixed();
+    wall->hbs.make_df_inv(s);
+    hpp.make_df_inv(s);
+  }
+  const int at = df ? MA_DF : MA_F64;
+  const int pa = wall->hbs.emit_inverse_g(P, 0, 0, 0, 2 * No, 3, 0, 2 * No, at);
+  const int pb = hpp.emit_inverse_g(P, 0, 1, 0, 2 * Np, 4, 0, 2 * Np, at);
   if (k > 0) {
-    const int W = P.ws_base();
-    const long long r = P.ws_alloc(k), z = P.ws_alloc(k);
-    int p = emit_r_times(P, std::max(pa, pb), Rkc.p, Rkp.p, Rpk.p, kk, kpk, k, No, Nc, Np, dc.p, 3, 4, W, r, -1);
-    P.gemm(p, Winv.p, k, k, k, W, r, -1, W, z, -1, 1.0, 0.0);
-    ++p;
-    if (kk) P.gemm(p, Xo.p, 2 * No, kk, 2 * No, W, z, -1, 3, 0, 2 * No, -1.0, 1.0);
-    if (kpk) P.gemm(p, Xp.p, 2 * Np, kpk, 2 * Np, W, z + kk, -1, 4, 0, 2 * Np, -1.0, 1.0);
+    if (df)
+      emit_woodbury(P, std::max(pa, pb), Rkc2.p, Rkp2.p, Rpk2.p, Winv2.p, Xo2.p, Xp2.p, kk, kpk, k, No, Nc, Np, dc.p);
+    else
+      emit_woodbury(P, std::max(pa, pb), Rkc.p, Rkp.p, Rpk.p, Winv.p, Xo.p, Xp.p, kk, kpk, k, No, Nc, Np, dc.p);
   }
   P.finalize(s, streams.main);
   return P;

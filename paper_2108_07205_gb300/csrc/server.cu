@@ -184,9 +184,10 @@ void rw_server_s::worker_loop(int wi) {
       rw::eval_stokeslets(ref.nn.view(), r->n_src, dsrc.p, r->nrhs, df.p, g.p, s);
       int iters = 0;
       double relres = 0.0;
+      const bool ir = r->mode == RW_MODE_DIRECT_IR || r->mode == RW_MODE_DIRECT_IR_DF;
       const bool gm = r->mode == RW_MODE_GMRES_FP32 || r->mode == RW_MODE_GMRES_BF16 ||
-                      r->mode == RW_MODE_GMRES_MIXED || r->mode == RW_MODE_DIRECT_IR;
-      if (r->mode == RW_MODE_DIRECT_IR) ref.solve_ir(g.p, tau.p, r->nrhs, s, &iters, &relres);
+                      r->mode == RW_MODE_GMRES_MIXED || ir;
+      if (ir) ref.solve_ir(g.p, tau.p, r->nrhs, s, &iters, &relres, r->mode == RW_MODE_DIRECT_IR_DF);
       else if (gm)
         ref.solve_gmres(g.p, tau.p, r->nrhs, s, &iters, &relres, r->mode == RW_MODE_GMRES_BF16,
                         r->mode == RW_MODE_GMRES_MIXED);
@@ -294,7 +295,7 @@ int rw_server_submit(rw_server_t sv, const rw_request* q, long long* ticket) {
   if (!sv || !q || !ticket || !q->wall || q->n_cut < 1 || !q->panel_ids || !q->levels || q->nrhs < 1 ||
       q->n_src < 1 || !q->src || !q->f || !q->tau || q->n_targets < 0 || (q->n_targets > 0 && (!q->targets || !q->u)))
     return sfail(RW_ERR_INVALID, "rw_server_submit: bad request");
-  if (q->mode < RW_MODE_DIRECT || q->mode > RW_MODE_GMRES_MIXED)
+  if (q->mode < RW_MODE_DIRECT || q->mode > RW_MODE_DIRECT_IR_DF)
     return sfail(RW_ERR_INVALID, "rw_server_submit: unknown mode");
   if (q->wall && q->wall->wall.opts.mixed_factor && (q->mode == RW_MODE_DIRECT || q->mode == RW_MODE_DIRECT_REFINED))
     return sfail(RW_ERR_INVALID, "rw_server_submit: walls with opts.mixed_factor take an iterative mode");

@@ -20,7 +20,7 @@ ERRORS = {-1: "RW_ERR_INVALID", -2: "RW_ERR_OOM", -3: "RW_ERR_SINGULAR",
           -4: "RW_ERR_NOT_CONVERGED", -5: "RW_ERR_TIMEOUT", -6: "RW_ERR_CUDA"}
 CURVE_STAR, CURVE_CHANNEL, CURVE_NODES = 0, 1, 2
 MODE_DIRECT, MODE_GMRES_FP32, MODE_DIRECT_REFINED, MODE_GMRES_BF16 = 0, 1, 2, 3
-MODE_DIRECT_IR, MODE_GMRES_MIXED = 4, 5
+MODE_DIRECT_IR, MODE_GMRES_MIXED, MODE_DIRECT_IR_DF = 4, 5, 6
 
 
 class RWError(RuntimeError):
@@ -338,7 +338,8 @@ class Refinement:
     refinement (cut panels split into sub-panels, Sec. 3.1) or, through
     Wall.add_holes, holes added inside the wall (App. B).  Both give the same
     handle: solve (MODE_DIRECT, MODE_DIRECT_REFINED, MODE_DIRECT_IR,
-    MODE_GMRES_FP32, MODE_GMRES_BF16, MODE_GMRES_MIXED), apply_refined,
+    MODE_DIRECT_IR_DF, MODE_GMRES_FP32, MODE_GMRES_BF16, MODE_GMRES_MIXED),
+    apply_refined,
     stokeslet_data, pressure, nodes, Batch."""
 
     def __init__(self, wall, panels, levels, stream=None, added=None, holes=None):

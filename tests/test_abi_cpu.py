@@ -43,6 +43,9 @@ def test_default_opts_and_validation_without_gpu():
     h1 = ctypes.c_void_p()
     assert L.rw_hbs_build(ctypes.byref(d1), ctypes.byref(bad_op), None, ctypes.byref(h1)) == -1
     assert b"op_tol" in L.rw_last_error()
+    bad_mf = rwsolve.default_opts(mixed_factor=3)
+    assert L.rw_hbs_build(ctypes.byref(d1), ctypes.byref(bad_mf), None, ctypes.byref(h1)) == -1
+    assert b"mixed_factor" in L.rw_last_error()
     bad = rwsolve.default_opts(hole_div_ratio=1.2)   # must exceed bas_ratio (1.5)
     d0 = rwsolve.WallDesc()
     d0.curve_kind = rwsolve.CURVE_STAR

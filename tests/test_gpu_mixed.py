@@ -1,5 +1,6 @@
 """The paths to a certified 1e-10 residual (Sec. 4.2): FP64 iterative
-refinement (RW_MODE_DIRECT_IR) and FGMRES with FP32 preconditioner sweeps and
+refinement (RW_MODE_DIRECT_IR), the same with every product in double-FP32
+(RW_MODE_DIRECT_IR_DF) and FGMRES with FP32 preconditioner sweeps and
 double-FP32 operator products (RW_MODE_GMRES_MIXED), on walls built with an
 operator tolerance of 1e-14; and the GEMM programs that run the sweeps and
 operator applies for many right-hand sides.
@@ -8,12 +9,12 @@ operator applies for many right-hand sides.
   time) on the same factors: forward apply and inverse sweep, FP64 and
   double-FP32.
 * 512-panel channel (16384 points, the 8-panel window at level 4; 24 RHS from
-  Stokeslet pairs): both modes against the oracle's dense LU of the refined
+  Stokeslet pairs): the three modes against the oracle's dense LU of the refined
   system, density relative error per RHS, and the true relative residual of
   every RHS against the exact refined operator assembled by the oracle
   (Sec. 2, Eq. interior_BIE_discretized2), <= 1e-10.
-* 2048-panel channel (65536 unknowns, the bench's configuration, 64 RHS):
-  the true relative residual of every RHS through the exact operator on the
+* 2048-panel channel (65536 unknowns, the bench's configuration, 64 RHS),
+  the three modes: the true relative residual of every RHS through the exact operator on the
   GPU (every entry evaluated on the fly) <= 1e-10, and 48 rows of the
   residual written out one at a time by the oracle within 1e-10 of each
   right-hand side's norm.
@@ -66,7 +67,10 @@ def test_gemm_programs_match_gemv_levels(lib):
     w.close()
 
 
-@pytest.mark.parametrize("mode", ["ir", "mixed"])
+MODES = {"ir": rwsolve.MODE_DIRECT_IR, "ir_df": rwsolve.MODE_DIRECT_IR_DF, "mixed": rwsolve.MODE_GMRES_MIXED}
+
+
+@pytest.mark.parametrize("mode", ["ir", "ir_df", "mixed"])
 def test_certified_residual_512_vs_oracle(lib, mode):
     P = 512
     panels, levels = inputs.refinement_window(21, P, 8, 4, 4)
@@ -75,8 +79,7 @@ def test_certified_residual_512_vs_oracle(lib, mode):
     nrhs = 24
     g, (sx, sy, f) = pair_data(r, 5, nrhs)
     tau = np.empty_like(g)
-    m = rwsolve.MODE_DIRECT_IR if mode == "ir" else rwsolve.MODE_GMRES_MIXED
-    info = r.solve(g, tau, nrhs=nrhs, mode=m)
+    info = r.solve(g, tau, nrhs=nrhs, mode=MODES[mode])
     assert info["rel_residual"] <= 1e-10
     o = D.refine("channel", {}, P, panels, levels)
     g_or = S.boundary_data(o["n"], sx, sy, f)                 # 2N_n x nrhs
@@ -96,23 +99,25 @@ def test_certified_residual_512_vs_oracle(lib, mode):
     w.close()
 
 
-def test_mixed_factor_preconditioner_only(lib):
-    """A wall with opts.mixed_factor: X = A~^{-1} L by FP32 sweeps, W formed
-    from it in FP64.  The preconditioned modes still certify 1e-10 against
-    the oracle's dense operator; the direct modes refuse the refinement."""
+@pytest.mark.parametrize("mixed_factor", [1, 2])
+def test_mixed_factor_preconditioner_only(lib, mixed_factor):
+    """A wall with opts.mixed_factor: X = A~^{-1} L by FP32 (1) or
+    double-FP32 (2) sweeps, W formed from it in FP64.  The iterative modes
+    still certify 1e-10 against the oracle's dense operator; the direct modes
+    refuse the refinement."""
     P = 256
     panels, levels = inputs.refinement_window(23, P, 8, 3, 3)
-    w = rwsolve.Wall("channel", P, opts=rwsolve.default_opts(op_tol=1e-14, mixed_factor=1))
+    w = rwsolve.Wall("channel", P, opts=rwsolve.default_opts(op_tol=1e-14, mixed_factor=mixed_factor))
     r = w.refine(panels, levels)
     g, (sx, sy, f) = pair_data(r, 8, 16)
     o = D.refine("channel", {}, P, panels, levels)
     A = S.matrix(o["n"])
     g_or = S.boundary_data(o["n"], sx, sy, f)
-    for m in (rwsolve.MODE_GMRES_MIXED, rwsolve.MODE_GMRES_FP32, rwsolve.MODE_DIRECT_IR):
+    for m in (rwsolve.MODE_GMRES_MIXED, rwsolve.MODE_GMRES_FP32, rwsolve.MODE_DIRECT_IR, rwsolve.MODE_DIRECT_IR_DF):
         tau = np.empty_like(g)
         info = r.solve(g, tau, nrhs=16, mode=m)
         rres = (np.linalg.norm(A @ tau.T - g_or, axis=0) / np.linalg.norm(g_or, axis=0)).max()
-        print(f"mixed factor, mode {m}: iters {info['iters']}, true residual {rres:.2e}")
+        print(f"mixed factor {mixed_factor}, mode {m}: iters {info['iters']}, true residual {rres:.2e}")
         assert info["rel_residual"] <= 1e-10 and rres <= 1e-10
     for m in (rwsolve.MODE_DIRECT, rwsolve.MODE_DIRECT_REFINED):
         with pytest.raises(rwsolve.RWError) as e:
@@ -133,7 +138,7 @@ def test_certified_residual_2048_full_size(lib):
     o = D.refine("channel", {}, P, panels, levels)
     rows = inputs.rng(99).choice(g.shape[1], 48, replace=False)
     taus = {}
-    for name, m in (("ir", rwsolve.MODE_DIRECT_IR), ("mixed", rwsolve.MODE_GMRES_MIXED)):
+    for name, m in MODES.items():
         tau = torch.empty_like(gd)
         info = r.solve(gd, tau, nrhs=nrhs, mode=m)
         assert info["rel_residual"] <= 1e-10
@@ -147,7 +152,8 @@ def test_certified_residual_2048_full_size(lib):
         assert rres <= 1e-10
         assert row_bar.max() <= 1e-10
         taus[name] = th
-    d = np.linalg.norm(taus["ir"] - taus["mixed"], axis=1) / np.linalg.norm(taus["ir"], axis=1)
-    print(f"mixed vs ir density {d.max():.2e}")
+    for name in ("ir_df", "mixed"):
+        d = np.linalg.norm(taus["ir"] - taus[name], axis=1) / np.linalg.norm(taus["ir"], axis=1)
+        print(f"{name} vs ir density {d.max():.2e}")
     r.close()
     w.close()
