@@ -53,6 +53,67 @@ Trace::Trace(cudaStream_t st, const char* w) : s(st), what(w) {
   if (on) { cudaStreamSynchronize(s); t0 = now_s(); }
 }
 
+namespace {
+constexpr int kSideStreams = 7;
+struct SidePool {
+  int dev = -1;
+  cudaStream_t st[kSideStreams] = {};
+  cudaEvent_t ev[kSideStreams + 1] = {};
+};
+thread_local SidePool tl_side;
+SidePool& side_pool() {
+  int dev = 0;
+  RW_CUDA(cudaGetDevice(&dev));
+  if (tl_side.dev != dev) {  // a thread that moved to another device starts a new pool
+    tl_side = SidePool();
+    tl_side.dev = dev;
+  }
+  return tl_side;
+}
+cudaEvent_t pool_event(SidePool& p, int i) {
+  if (!p.ev[i]) RW_CUDA(cudaEventCreateWithFlags(&p.ev[i], cudaEventDisableTiming));
+  return p.ev[i];
+}
+}  // namespace
+
+ForkJoin::ForkJoin(cudaStream_t s, int n) : s_(s), n_(std::min(n, kSideStreams + 1)) {
+  if (n_ > 1) RW_CUDA(cudaEventRecord(pool_event(side_pool(), 0), s_));
+}
+
+cudaStream_t ForkJoin::next() {
+  if (n_ <= 1 || used_ == 0 || used_ >= n_) {
+    if (used_ < n_) ++used_;
+    return s_;
+  }
+  SidePool& p = side_pool();
+  cudaStream_t& t = p.st[used_ - 1];
+  if (!t) RW_CUDA(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+  RW_CUDA(cudaStreamWaitEvent(t, pool_event(p, 0), 0));
+  ++used_;
+  return t;
+}
+
+void ForkJoin::join() {
+  if (joined_) return;
+  joined_ = true;
+  if (n_ <= 1) return;
+  SidePool& p = side_pool();
+  for (int i = 1; i < used_; ++i) {
+    cudaEvent_t e = pool_event(p, i);
+    RW_CUDA(cudaEventRecord(e, p.st[i - 1]));
+    RW_CUDA(cudaStreamWaitEvent(s_, e, 0));
+  }
+}
+
+ForkJoin::~ForkJoin() {
+  if (joined_ || n_ <= 1) return;
+  // best effort on an exceptional exit: keep s ordered after the side work
+  SidePool& p = tl_side;
+  for (int i = 1; i < used_; ++i)
+    if (p.st[i - 1] && p.ev[i] && cudaEventRecord(p.ev[i], p.st[i - 1]) == cudaSuccess)
+      cudaStreamWaitEvent(s_, p.ev[i], 0);
+}
+
 void Trace::mark(const char* phase) {
   if (!on) return;
   cudaStreamSynchronize(s);
@@ -783,6 +844,25 @@ __global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_
   }
 }
 
+// Threads per column in the column updates of a CTA holding cw columns
+// (a power of two <= 32, so that the CTA's threads cover its columns), and
+// the shared-memory column stride for it: with G < 16 threads on
+// consecutive rows of a column, a stride of G modulo 16 doubles puts the
+// columns of one warp in distinct banks.
+__host__ __device__ inline int cpqr_threads_per_col(int cw, int nt) {
+  int G = 32;
+  while (G > 1 && (nt / G) < cw) G >>= 1;
+  return G;
+}
+__host__ __device__ inline int cpqr_ld(int nr, int G) {
+  return G >= 16 ? nr : nr + ((G - nr % 16) + 16) % 16;
+}
+// Shared memory of a cluster-QR CTA (bytes): its columns, two published
+// columns, the Householder vector and two norm arrays.
+__host__ __device__ inline size_t cpqr_cluster_smem(int nr, int cw, int nt) {
+  return (size_t(cpqr_ld(nr, cpqr_threads_per_col(cw, nt))) * cw + 3 * size_t(nr) + 2 * size_t(cw)) * sizeof(double);
+}
+
 // One pivot step's update of a CTA's candidate columns (shared memory, nr
 // rows each) by the Householder reflector I - tau v v^T (v(s) = 1, v(i) =
 // vloc(i) below): G threads (a power of two <= 32, within one warp) per
@@ -792,13 +872,13 @@ __global__ void __launch_bounds__(512) k_cpqr_id(const IdProb* probs, int nprob_
 // <= sqrt(eps) x the square at the last exact computation: LAPACK xLAQP2's
 // test, stated on squares, which needs no division or square root).  Done
 // columns carry a negative value.
-__device__ __forceinline__ void cpqr_update_columns(double* Wl, int nr, int ncl, int ncl_pad, int G, int s,
+__device__ __forceinline__ void cpqr_update_columns(double* Wl, int ld, int nr, int ncl, int ncl_pad, int G, int s,
                                                     double tau, const double* vloc, double* nrm, double* nrm0,
                                                     double tol3z) {
   const int tid = threadIdx.x, nt = blockDim.x, gl = tid & (G - 1);
   for (int j = tid / G; j < ncl_pad; j += nt / G) {
     const bool live = j < ncl && nrm[j] >= 0.0;
-    double* cj = Wl + size_t(live ? j : 0) * nr;
+    double* cj = Wl + size_t(live ? j : 0) * ld;
     double dd = 0.0;
     if (live && tau != 0.0)
       for (int i = s + 1 + gl; i < nr; i += G) dd += vloc[i] * cj[i];
@@ -833,13 +913,19 @@ __device__ __forceinline__ void cpqr_update_columns(double* Wl, int nr, int ncl,
 
 // Cluster variant (thread-block cluster of CS CTAs per problem): CTA r of
 // the cluster keeps candidate columns [r cw, (r+1) cw) of W in its shared
-// memory.  Per pivot step: every CTA publishes its local column-norm maximum,
-// cluster barrier, all CTAs agree on the pivot; the owner forms the
-// Householder vector in its shared memory, cluster barrier, every CTA copies
-// it through distributed shared memory and updates its own columns.  Columns
-// are not swapped: column q keeps its data, piv[] records the pivot order,
-// and the factorisation is written back to global memory in this "no-swap"
-// layout (R(l, i) = W[l, piv[i]]; T for a non-pivot candidate q in column q).
+// memory, column stride cpqr_ld(nr, G) (padded so that the G threads of a
+// column and the columns of a warp fall in distinct banks).  One cluster
+// barrier per pivot step: every CTA publishes its local column-norm maximum
+// together with a copy of that column (two buffers, by step parity); after
+// the barrier warp 0 of every CTA reads all published maxima, so that every
+// CTA takes the same decisions, copies the winning column through
+// distributed shared memory and forms the Householder vector from it (the
+// same arithmetic in every CTA); then every CTA updates its own columns,
+// downdating their norms and finding its next local maximum in the same
+// pass.  Columns are not swapped: column q keeps its data, piv[] records the
+// pivot order, and the factorisation is written back to global memory in
+// this "no-swap" layout (R(l, i) = W[l, piv[i]]; T for a non-pivot candidate
+// q in column q).
 //
 // Paired mode (paired = 1): a cluster of 2 CS CTAs factors problems 2c and
 // 2c+1 side by side (CTAs [0, CS) and [CS, 2 CS)) with a joint stopping
@@ -855,35 +941,35 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
   const int half = crank / CS, lr = crank % CS;
   const int pidx = base + (blockIdx.x / (CS * np)) * np + half;
   const IdProb P = probs[pidx];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nr = P.nr, nc = P.nc;
   const int cw = (nc + CS - 1) / CS;
   const int c0 = min(nc, lr * cw), c1 = min(nc, c0 + cw), ncl = max(0, c1 - c0);
+  const int G = cpqr_threads_per_col(cw, nt);
+  const int ld = cpqr_ld(nr, G);
   extern __shared__ double smem[];
-  double* Wl = smem;                  // nr x cw
-  double* vbuf = Wl + size_t(nr) * cw;  // published Householder vector (owner)
-  double* vloc = vbuf + nr;           // local copy
-  double* nrm = vloc + nr;            // cw
-  double* nrm0 = nrm + cw;            // cw
-  __shared__ double pub_val, pub_tau, g_val, g_val_o;
-  __shared__ int pub_idx, g_idx;
+  double* Wl = smem;                   // ld x cw
+  double* pubc = Wl + size_t(ld) * cw;  // 2 x nr: published column, by step parity
+  double* vloc = pubc + 2 * size_t(nr);  // Householder vector of the current step
+  double* nrm = vloc + nr;              // cw
+  double* nrm0 = nrm + cw;              // cw
+  __shared__ double pubv[2], g_val, g_val_o, g_tau, g_beta;
+  __shared__ int pubi[2], g_idx;
   __shared__ double sval[32];
   __shared__ int sidx[32];
-  // load owned columns, norms
   for (int e = tid; e < nr * ncl; e += nt) {
     const int i = e % nr, j = e / nr;
-    Wl[i + size_t(j) * nr] = P.W[i + size_t(c0 + j) * P.ldw];
+    Wl[i + size_t(j) * ld] = P.W[i + size_t(c0 + j) * P.ldw];
   }
   __syncthreads();
-  for (int j = warp; j < ncl; j += nw) {
-    double s = 0.0;
-    for (int i = lane; i < nr; i += 32) { double v = Wl[i + size_t(j) * nr]; s += v * v; }
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) { nrm[j] = s; nrm0[j] = s; }
+  for (int j = warp; j < ncl; j += nt >> 5) {
+    double q = 0.0;
+    for (int i = lane; i < nr; i += 32) { const double v = Wl[i + size_t(j) * ld]; q += v * v; }
+    for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
+    if (lane == 0) { nrm[j] = q; nrm0[j] = q; }
   }
   __syncthreads();
   const int maxsteps = (nr <= 0 || nc <= 0) ? 0 : min(min(nr, nc), P.max_rank);
-  // the partner's stopping parameters (paired mode)
   int maxsteps_o = 0, minrank_o = 0;
   double tabs_o = 0.0, trel_o = 0.0;
   if (paired) {
@@ -894,30 +980,34 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
     trel_o = Q.tol_rel;
   }
   const double tol3z = sqrt(2.220446049250313e-16);
-  int G = 32;
-  while (G > 1 && (nt / G) < ncl) G >>= 1;
   const int ncl_pad = (ncl + (nt / G) - 1) / (nt / G) * (nt / G);
+  // the local maximum of the initial norms (smallest global index on ties)
+  double lv = -1.0;
+  int li = 0x7fffffff;
+  for (int j = tid; j < ncl; j += nt) if (nrm[j] > lv) { lv = nrm[j]; li = c0 + j; }
   double ref = 0.0, ref_o = 0.0;
   bool done = false, done_o = !paired;
   int s = 0;  // steps taken by this CTA's problem
   for (int it = 0;; ++it) {
-    // local argmax over remaining owned columns (done columns have norm -1)
-    double v = -1.0;
-    int idx = 0x7fffffff;
-    if (!done)
-      for (int j = tid; j < ncl; j += nt) if (nrm[j] > v) { v = nrm[j]; idx = c0 + j; }
-    int p;
-    double lm = block_reduce_max_abs_arg(v, idx, &p, sval, sidx);
-    if (tid == 0) { pub_val = lm; pub_idx = p; }
+    const int par = it & 1;
+    // publish the local maximum and a copy of its column
+    {
+      int p;
+      const double lm = block_reduce_max_abs_arg(done ? -1.0 : lv, done ? 0x7fffffff : li, &p, sval, sidx);
+      double* pc = pubc + size_t(par) * nr;
+      if (lm >= 0.0 && p >= c0 && p < c1)
+        for (int i = tid; i < nr; i += nt) pc[i] = Wl[i + size_t(p - c0) * ld];
+      if (tid == 0) { pubv[par] = lm; pubi[par] = p; }
+    }
     cluster.sync();
     if (warp == 0) {
-      // lane r reads CTA r's slot; warp arg-max over this problem's CTAs
+      // lane r reads CTA r's slot; arg-max over this problem's CTAs
       // (smallest index on ties) and the partner's maximum
       double bv = -1.0, ov_o = -1.0;
       int bi = 0x7fffffff;
       if (lane < CS * np) {
-        const double x = *cluster.map_shared_rank(&pub_val, lane);
-        const int xi = *cluster.map_shared_rank(&pub_idx, lane);
+        const double x = *cluster.map_shared_rank(&pubv[par], lane);
+        const int xi = *cluster.map_shared_rank(&pubi[par], lane);
         if (lane / CS == half) { bv = x; bi = xi; }
         else ov_o = x;
       }
@@ -927,65 +1017,72 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int b
         ov_o = fmax(ov_o, __shfl_down_sync(0xffffffffu, ov_o, off));
         if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
       }
-      if (lane == 0) { g_val = bv; g_idx = bi; g_val_o = ov_o; }
+      bv = __shfl_sync(0xffffffffu, bv, 0);
+      bi = __shfl_sync(0xffffffffu, bi, 0);
+      ov_o = __shfl_sync(0xffffffffu, ov_o, 0);
+      // the stopping rule (the same in every CTA), then the Householder
+      // vector of the winning column, formed by this warp
+      if (it == 0) { ref = sqrt(fmax(bv, 0.0)); ref_o = sqrt(fmax(ov_o, 0.0)); }
+      const double thr = fmax(P.tol_abs, P.tol_rel * ref), thr_o = fmax(tabs_o, trel_o * ref_o);
+      const bool hard = done || it >= maxsteps || bv <= 0.0;
+      const bool soft = hard || (it >= P.min_rank && bv <= thr * thr);
+      const bool hard_o = done_o || it >= maxsteps_o || ov_o <= 0.0;
+      const bool soft_o = hard_o || (it >= minrank_o && ov_o <= thr_o * thr_o);
+      int stop = (soft && soft_o) ? 1 : 0;
+      if (!stop && !hard) {
+        const int owner = half * CS + bi / cw;
+        const double* rc = cluster.map_shared_rank(pubc + size_t(par) * nr, owner);
+        double xn2 = 0.0;
+        for (int i = s + 1 + lane; i < nr; i += 32) { const double x = rc[i]; vloc[i] = x; xn2 += x * x; }
+        for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_down_sync(0xffffffffu, xn2, off);
+        xn2 = __shfl_sync(0xffffffffu, xn2, 0);
+        const double alpha = rc[s];
+        double tau = 0.0, beta = alpha;
+        if (xn2 != 0.0) {
+          beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+          tau = (beta - alpha) / beta;
+          const double sc = 1.0 / (alpha - beta);
+          __syncwarp();
+          for (int i = s + 1 + lane; i < nr; i += 32) vloc[i] *= sc;
+        }
+        if (lane == 0) { g_tau = tau; g_beta = beta; }
+      }
+      if (lane == 0) { g_val = bv; g_val_o = ov_o; g_idx = stop ? -1 : bi; }
     }
     __syncthreads();
-    // squared norms are published; ref is the first pivot norm itself
+    if (g_idx < 0) break;
     const double vmax = g_val, vmax_o = g_val_o;
     const int pg = g_idx;
     if (it == 0) { ref = sqrt(fmax(vmax, 0.0)); ref_o = sqrt(fmax(vmax_o, 0.0)); }
-    const double thr = fmax(P.tol_abs, P.tol_rel * ref), thr_o = fmax(tabs_o, trel_o * ref_o);
-    // the same decisions in every CTA of the cluster (same published data)
     const bool hard = done || it >= maxsteps || vmax <= 0.0;
-    const bool soft = hard || (it >= P.min_rank && vmax <= thr * thr);
     const bool hard_o = done_o || it >= maxsteps_o || vmax_o <= 0.0;
-    const bool soft_o = hard_o || (it >= minrank_o && vmax_o <= thr_o * thr_o);
-    if (soft && soft_o) break;
     done = hard;
     done_o = hard_o;
-    const int owner = half * CS + pg / cw;
     if (!done) {
+      const double tau = g_tau;
       if (lr == 0 && tid == 0) P.piv[s] = pg;
-      if (crank == owner) {
+      if (pg >= c0 && pg < c1) {
+        // the pivot column becomes R's column s over the reflector
         const int jl = pg - c0;
-        double* col = Wl + size_t(jl) * nr;
-        double part = 0.0;
-        for (int i = s + 1 + tid; i < nr; i += nt) part += col[i] * col[i];
-        const double xn2 = block_reduce_sum(part, sval);
-        const double alpha = col[s];
-        double tau = 0.0, sc = 0.0;
-        if (xn2 != 0.0) {
-          const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-          tau = (beta - alpha) / beta;
-          sc = 1.0 / (alpha - beta);
-        }
-        __syncthreads();
-        for (int i = s + 1 + tid; i < nr; i += nt) {
-          const double x = col[i] * sc;
-          col[i] = x;
-          vbuf[i] = x;
-        }
+        double* col = Wl + size_t(jl) * ld;
+        for (int i = s + 1 + tid; i < nr; i += nt) col[i] = vloc[i];
         if (tid == 0) {
-          if (xn2 != 0.0) col[s] = -copysign(sqrt(alpha * alpha + xn2), alpha);
-          pub_tau = tau;
+          col[s] = g_beta;
           nrm[jl] = -1.0;  // done
         }
       }
-    }
-    cluster.sync();
-    if (!done) {
-      const double* rv = cluster.map_shared_rank(vbuf, owner);
-      const double tau = *cluster.map_shared_rank(&pub_tau, owner);
-      for (int i = s + 1 + tid; i < nr; i += nt) vloc[i] = rv[i];
       __syncthreads();
-      cpqr_update_columns(Wl, nr, ncl, ncl_pad, G, s, tau, vloc, nrm, nrm0, tol3z);
+      cpqr_update_columns(Wl, ld, nr, ncl, ncl_pad, G, s, tau, vloc, nrm, nrm0, tol3z);
       ++s;
+      __syncthreads();
+      lv = -1.0;
+      li = 0x7fffffff;
+      for (int j = tid; j < ncl; j += nt) if (nrm[j] > lv) { lv = nrm[j]; li = c0 + j; }
     }
-    __syncthreads();
   }
   for (int e = tid; e < nr * ncl; e += nt) {
     const int i = e % nr, j = e / nr;
-    P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * nr];
+    P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * ld];
   }
   // done flags for the remaining-pivot bookkeeping: mark in global norms
   for (int j = tid; j < ncl; j += nt) P.norms[nc + c0 + j] = (nrm[j] < 0.0) ? -1.0 : 1.0;
@@ -1158,7 +1255,7 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int base
         if (tid == 0) { cp[s] = beta; nrm[jl] = -1.0; }
         __syncthreads();
       }
-      cpqr_update_columns(Wl, nr, ncl, ncl_pad, G2, s, tau, vloc, nrm, nrm0, tol3z);
+      cpqr_update_columns(Wl, nr, nr, ncl, ncl_pad, G2, s, tau, vloc, nrm, nrm0, tol3z);
     }
     __syncthreads();
     if (tid < np && s_act[tid]) s_s[tid] += 1;
@@ -1755,37 +1852,53 @@ bool grid_id_fits(int nr, int nc) {
 
 void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired) {
   if (probs_in.empty()) return;
-  if (int(probs_in.size()) <= kGridIdProbs && grid_id_enabled()) {
-    double work = 0.0;
-    for (auto& p : probs_in) work += double(p.nr) * p.nc;
-    std::vector<int> parts;
-    int G = 0, nrm = 0;
-    size_t smem = 0;
-    if (work >= kGridIdMinWork && grid_id_plan(probs_in, 200 * 1024, parts, &G, &smem, &nrm)) {
-      grid_id_run(probs_in, paired, parts, G, smem, nrm, s);
-      return;
-    }
-  }
   // Route each problem: a thread-block cluster of CS in {1, 2, 4, 8} CTAs
   // whose shared memory holds the matrix, or the global-memory kernel.
   // Pairs (paired: problems 2i and 2i+1) share one cluster of 2 CS <= 8 CTAs
-  // when both fit; otherwise they are routed one by one.
+  // when both fit; otherwise they are routed one by one.  CS is the
+  // smallest that holds the matrix, raised while the batch stays within
+  // about two CTAs per SM and every CTA keeps at least 32 columns: a pivot
+  // step's update (FP64-bound) is then shared by more SMs.
   const size_t cap = 200 * 1024;
   const int sizes[4] = {1, 2, 4, 8};
+  const int nsm = sm_count();
   // RW_ID_CS_MIN (tuning): smallest cluster size tried (1, 2, 4 or 8)
   static const int q_min = [] {
     const char* e = std::getenv("RW_ID_CS_MIN");
     const int v = e ? std::atoi(e) : 1;
     return v >= 8 ? 3 : v >= 4 ? 2 : v >= 2 ? 1 : 0;
   }();
+  const long long units = paired ? (long long)(probs_in.size() + 1) / 2 : (long long)probs_in.size();
+  int spread_q = 0;
+  while (spread_q < 3 && units * sizes[spread_q + 1] * (paired ? 2 : 1) <= 2LL * nsm) ++spread_q;
   auto fitq = [&](const IdProb& p) {
-    for (int q = q_min; q < 4; ++q) {
-      const int cw = (p.nc + sizes[q] - 1) / sizes[q];
-      const size_t b = (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double);
-      if (b <= cap && (q == q_min || p.nc >= 2 * sizes[q])) return q;
+    int q = -1;
+    for (int t = q_min; t < 4 && q < 0; ++t) {
+      const int cw = (p.nc + sizes[t] - 1) / sizes[t];
+      if (cpqr_cluster_smem(p.nr, cw, 256) <= cap) q = t;
     }
-    return -1;
+    if (q < 0) return -1;
+    while (q < spread_q && q < 3 && p.nc >= 32 * sizes[q + 1]) ++q;
+    return q;
   };
+  // A few problems that do not all fit a cluster (8 CTAs, or 4 per problem
+  // when paired) go to the grid-wide factorisation instead.
+  if (int(probs_in.size()) <= kGridIdProbs && grid_id_enabled()) {
+    double work = 0.0;
+    bool fit_all = true;
+    for (auto& p : probs_in) {
+      work += double(p.nr) * p.nc;
+      const int q = fitq(p);
+      fit_all = fit_all && q >= 0 && (!paired || q <= 2);
+    }
+    std::vector<int> parts;
+    int G = 0, nrm = 0;
+    size_t smem = 0;
+    if (!fit_all && work >= kGridIdMinWork && grid_id_plan(probs_in, 200 * 1024, parts, &G, &smem, &nrm)) {
+      grid_id_run(probs_in, paired, parts, G, smem, nrm, s);
+      return;
+    }
+  }
   std::vector<IdProb> grp[4], pgrp[3], gl;
   const size_t n = probs_in.size();
   for (size_t i = 0; i < n;) {
@@ -1812,13 +1925,18 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired
   all.insert(all.end(), gl.begin(), gl.end());
   init_smem_limits();
   auto dp = to_device_tmp(all, s);
+  // The groups (one launch per cluster shape) are independent: all but the
+  // first run on side streams forked from s and joined back, so that a
+  // group of a few large problems overlaps the bulk instead of following it.
+  int ngroups = int(!gl.empty());
+  for (int q = 0; q < 4; ++q) ngroups += int(!grp[q].empty());
+  for (int q = 0; q < 3; ++q) ngroups += int(!pgrp[q].empty());
+  ForkJoin fj(s, ngroups);
   auto launch = [&](const std::vector<IdProb>& g, int b0, int CS, int pr) {
     if (g.empty()) return;
+    const cudaStream_t s = fj.next();
     size_t smem = 0;
-    for (auto& p : g) {
-      const int cw = (p.nc + CS - 1) / CS;
-      smem = std::max(smem, (size_t(p.nr) * cw + 2 * size_t(p.nr) + 2 * size_t(cw)) * sizeof(double));
-    }
+    for (auto& p : g) smem = std::max(smem, cpqr_cluster_smem(p.nr, (p.nc + CS - 1) / CS, 256));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(g.size() * CS));
     cfg.blockDim = dim3(256);
@@ -1844,10 +1962,12 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired
     size_t gl_bytes = 0;
     for (auto& p : gl) gl_bytes = std::max(gl_bytes, size_t(p.nr) * sizeof(double));
     require(gl_bytes <= cap, "batched_id: more than 25600 feature rows");
-    ProfScope pg(KC_ID, s);
-    k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, s>>>(dp.p, gbase, id_flops_counter());
+    const cudaStream_t sg = fj.next();
+    ProfScope pg(KC_ID, sg);
+    k_cpqr_id<false><<<int(gl.size()), 512, gl_bytes, sg>>>(dp.p, gbase, id_flops_counter());
     RW_CHECK_LAUNCH();
   }
+  fj.join();
 }
 
 void batched_id_interp(const std::vector<IdProb>& probs, int max_elems, cudaStream_t s) {

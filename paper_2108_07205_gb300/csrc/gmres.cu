@@ -88,6 +88,7 @@ void Refinement::make_mixed() const {
   for (auto pr : {std::make_pair(&Lo, &Lo2), std::make_pair(&Lp, &Lp2), std::make_pair(&Rkc, &Rkc2),
                   std::make_pair(&Rkp, &Rkp2), std::make_pair(&Rpk, &Rpk2), std::make_pair(&Xo, &Xo2),
                   std::make_pair(&Xp, &Xp2), std::make_pair(&Winv, &Winv2)}) {
+    if (pr.second->p && pr.second->n == pr.first->n) continue;  // made with W (see form_w)
     pr.second->alloc(pr.first->n);
     copy_d2df(pr.first->p, pr.second->p, pr.first->n, s);
   }

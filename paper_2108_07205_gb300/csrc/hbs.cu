@@ -151,10 +151,94 @@ __global__ void k_gather_cols(const double* Z, int nr, const int* cand, int n, d
 }
 }  // namespace
 
+struct TreeId::Levels {
+  // each job: candidate positions (into rows), indices of its child jobs in
+  // the previous level, rank, skeleton positions, offset of its
+  // interpolation matrix (m_j x k_j, ld m_j) in the level's buffer
+  struct Job { std::vector<int> cand; std::vector<int> ch; int k = 0; std::vector<int> skel; size_t poff = 0; };
+  std::vector<std::vector<Job>> levels;
+  std::vector<DBuf<double>> Pl;
+  int mt = 0;
+};
+
+DBuf<double> TreeId::expand(const double* T, int ldT, int kout, cudaStream_t s) const {
+  if (!lv) {  // no rows at all
+    require(k == 0, "TreeId::expand: no levels");
+    return DBuf<double>(1);
+  }
+  if (!T) kout = k;
+  const int mt = lv->mt;
+  DBuf<double> out(std::max<size_t>(size_t(mt) * kout, 1));
+  if (kout == 0) return out;
+  if (k == 0) {
+    fill_zero(out.p, size_t(mt) * kout, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+    return out;
+  }
+  const auto& levels = lv->levels;
+  const auto& Pl = lv->Pl;
+  const auto& root = levels.back()[0];
+  const int top = int(levels.size()) - 1;
+  // the root's map of its candidates to the skeleton, times T
+  auto root_map = [&](double* dst, int ld) {
+    const int m = int(root.cand.size());
+    if (T)
+      batched_gemm({GemmProb{Pl[top].p + root.poff, T, dst, m, kout, k, m, ldT, ld, 0, 0, 1.0, 0.0}}, s);
+    else
+      RW_CUDA(cudaMemcpy2DAsync(dst, size_t(ld) * sizeof(double), Pl[top].p + root.poff, size_t(m) * sizeof(double),
+                                size_t(m) * sizeof(double), size_t(k), cudaMemcpyDeviceToDevice, s));
+  };
+  if (top == 0) {
+    root_map(out.p, mt);
+    RW_CUDA(cudaStreamSynchronize(s));
+    return out;
+  }
+  // top-down products: Wm[level][job] = (m_j x kout) map of candidates to
+  // the root skeleton (times T)
+  std::vector<DBuf<double>> Wm(levels.size());
+  {
+    size_t sz = 0;
+    for (auto& j : levels[top]) sz += j.cand.size() * size_t(kout);
+    Wm[top].alloc(std::max<size_t>(sz, 1));
+    root_map(Wm[top].p, int(root.cand.size()));
+  }
+  for (int l = top; l > 0; --l) {
+    auto& par = levels[l];
+    auto& ch = levels[l - 1];
+    std::vector<size_t> woff(ch.size());
+    size_t sz = 0;
+    for (size_t b = 0; b < ch.size(); ++b) { woff[b] = sz; sz += ch[b].cand.size() * size_t(kout); }
+    const bool bottom = (l - 1 == 0);
+    if (!bottom) Wm[l - 1].alloc(std::max<size_t>(sz, 1));
+    std::vector<GemmProb> gm;
+    std::vector<size_t> wpar(par.size());
+    { size_t o = 0; for (size_t b = 0; b < par.size(); ++b) { wpar[b] = o; o += par[b].cand.size() * size_t(kout); } }
+    for (size_t pb = 0; pb < par.size(); ++pb) {
+      const int mp = int(par[pb].cand.size());
+      int slice = 0;
+      for (int cidx : par[pb].ch) {
+        const auto& c = ch[cidx];
+        const double* M = Wm[l].p + wpar[pb] + slice;  // rows slice of the parent's map, ld mp
+        double* C;
+        int ldc;
+        if (bottom) { C = out.p + c.cand[0]; ldc = mt; } else { C = Wm[l - 1].p + woff[cidx]; ldc = int(c.cand.size()); }
+        gm.push_back(GemmProb{Pl[l - 1].p + c.poff, M, C, int(c.cand.size()), kout, c.k, int(c.cand.size()), mp, ldc,
+                              0, 0, 1.0, 0.0});
+        slice += c.k;
+      }
+    }
+    batched_gemm(gm, s);
+  }
+  // keep the temporaries alive until the stream has consumed them
+  RW_CUDA(cudaStreamSynchronize(s));
+  return out;
+}
+
 namespace {
 TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
                      const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
-                     int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s);
+                     int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s,
+                     bool defer);
 }  // namespace
 
 // Sketched problems first try a narrow sketch (kSketchTry rows) and keep it
@@ -164,10 +248,11 @@ constexpr int kSketchTry = 96, kSketchMargin = 16;
 
 TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
                    const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
-                   int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s) {
+                   int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s,
+                   bool defer) {
   const int ncol = idmat_ncol(0, colspec.n1, colspec.n2, idmat_nproxy(colspec), colspec.normal);
   if (ncol > sketch_cols && sketch_width > kSketchTry && ncol > kSketchTry) {
-    TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, kSketchTry, seed, chunk, s);
+    TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, kSketchTry, seed, chunk, s, defer);
     if (t.k <= kSketchTry - kSketchMargin) return t;
   }
   // A sketch of width w certifies ranks up to w - kSketchMargin only: a rank
@@ -176,7 +261,7 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
   // block itself (rows + margin, or every column).
   int w = sketch_width;
   for (;;) {
-    TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, w, seed, chunk, s);
+    TreeId t = tree_row_id_w(S, rows, colspec, E1, e1s, E2, e2s, tol, sketch_cols, w, seed, chunk, s, defer);
     const bool sketched = ncol > sketch_cols && w < ncol;
     if (!sketched || t.k <= w - kSketchMargin || w >= int(rows.size()) + kSketchMargin) return t;
     w = std::min(2 * w, std::max(int(rows.size()) + kSketchMargin, w + 1));
@@ -186,7 +271,8 @@ TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMat
 namespace {
 TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
                      const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
-                     int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s) {
+                     int sketch_cols, int sketch_width, unsigned long long seed, int chunk, cudaStream_t s,
+                     bool defer) {
   TreeId out;
   const int mt = int(rows.size());
   if (mt == 0) return out;
@@ -223,9 +309,11 @@ TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdM
 
   // level structure: each job has candidate positions (into rows) and the
   // indices of its child jobs in the previous level
-  struct TJob { std::vector<int> cand; std::vector<int> ch; int k = 0; std::vector<int> skel; size_t poff = 0; };
-  std::vector<std::vector<TJob>> levels;
-  std::vector<DBuf<double>> Pl;  // per level: interpolation matrices (m_j x k_j, ld m_j)
+  using TJob = TreeId::Levels::Job;
+  out.lv = std::make_shared<TreeId::Levels>();
+  out.lv->mt = mt;
+  std::vector<std::vector<TJob>>& levels = out.lv->levels;
+  std::vector<DBuf<double>>& Pl = out.lv->Pl;  // per level: interpolation matrices (m_j x k_j, ld m_j)
   std::vector<TJob> cur;
   if (const char* e = std::getenv("RW_TREE_CHUNK")) {
     const int x = std::atoi(e);
@@ -334,51 +422,9 @@ TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdM
   const TJob& root = levels.back()[0];
   out.k = root.k;
   out.skel = root.skel;
-  out.P.alloc(std::max<size_t>(size_t(mt) * out.k, 1));
-  if (out.k == 0) return out;
-  // top-down products: Wmap[level][job] = (m_j x k) map of candidates to the root skeleton
-  std::vector<DBuf<double>> Wm(levels.size());
-  const int top = int(levels.size()) - 1;
-  {
-    size_t sz = 0;
-    for (auto& j : levels[top]) sz += j.cand.size() * size_t(out.k);
-    Wm[top].alloc(std::max<size_t>(sz, 1));
-    RW_CUDA(cudaMemcpyAsync(Wm[top].p, Pl[top].p + root.poff, root.cand.size() * size_t(out.k) * sizeof(double),
-                            cudaMemcpyDeviceToDevice, s));
-  }
-  for (int lv = top; lv > 0; --lv) {
-    auto& par = levels[lv];
-    auto& ch = levels[lv - 1];
-    std::vector<size_t> woff(ch.size());
-    size_t sz = 0;
-    for (size_t b = 0; b < ch.size(); ++b) { woff[b] = sz; sz += ch[b].cand.size() * size_t(out.k); }
-    const bool bottom = (lv - 1 == 0);
-    if (!bottom) Wm[lv - 1].alloc(std::max<size_t>(sz, 1));
-    std::vector<GemmProb> gm;
-    std::vector<size_t> wpar(par.size());
-    { size_t o = 0; for (size_t b = 0; b < par.size(); ++b) { wpar[b] = o; o += par[b].cand.size() * size_t(out.k); } }
-    for (size_t pb = 0; pb < par.size(); ++pb) {
-      const int mp = int(par[pb].cand.size());
-      int slice = 0;
-      for (int cidx : par[pb].ch) {
-        const TJob& c = ch[cidx];
-        const double* M = Wm[lv].p + wpar[pb] + slice;  // rows slice of the parent's map, ld mp
-        double* C;
-        int ldc;
-        if (bottom) { C = out.P.p + c.cand[0]; ldc = mt; } else { C = Wm[lv - 1].p + woff[cidx]; ldc = int(c.cand.size()); }
-        gm.push_back(GemmProb{Pl[lv - 1].p + c.poff, M, C, int(c.cand.size()), out.k, c.k, int(c.cand.size()), mp, ldc,
-                              0, 0, 1.0, 0.0});
-        slice += c.k;
-      }
-    }
-    batched_gemm(gm, s);
-  }
-  if (top == 0) {
-    RW_CUDA(cudaMemcpyAsync(out.P.p, Pl[0].p + root.poff, size_t(mt) * out.k * sizeof(double),
-                            cudaMemcpyDeviceToDevice, s));
-  }
-  // keep buffers alive until the stream has consumed them
-  RW_CUDA(cudaStreamSynchronize(s));
+  RW_CUDA(cudaStreamSynchronize(s));  // the levels are complete (a deferred expansion may use another stream)
+  if (defer) return out;
+  out.P = out.expand(nullptr, 0, 0, s);
   tr.mark("top-down interpolation");
   return out;
 }
@@ -641,7 +687,16 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s, bool fwd_only
       }
     }
     batch.run(V, V, true, V, true, o.id_tol, {}, {}, {}, {}, o.seed + l, s);
-    tr.mark("  level IDs");
+    if (tr.on) {
+      long long msum = 0, ksum = 0;
+      int kmax = 0;
+      for (int t = 0; t < nn; ++t) msum += m[t];
+      for (int j = 0; j < 2 * nn; ++j) { ksum += batch.h_rank[j]; kmax = std::max(kmax, batch.h_rank[j]); }
+      char msg[160];
+      std::snprintf(msg, sizeof msg, "  level %d IDs: %d nodes, candidates %lld, feature rows %d..%d, ranks sum %lld max %d",
+                    l, nn, msum, batch.jobs.front().nr, batch.jobs.back().nr, ksum, kmax);
+      tr.mark(msg);
+    }
     std::vector<int> kfix(2 * nn), redo, minr(2 * nn, 0), maxr(2 * nn);
     for (int t = 0; t < nn; ++t) {
       int k = std::max(batch.h_rank[2 * t], batch.h_rank[2 * t + 1]);

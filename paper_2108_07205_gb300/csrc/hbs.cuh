@@ -4,6 +4,7 @@
 // preamble, Sec. 4.2).  Also the interpolative-decomposition helpers shared
 // with the refinement factorisation.
 #pragma once
+#include <memory>
 #include "dense.cuh"
 #include "eval.cuh"
 #include "program.cuh"
@@ -82,12 +83,20 @@ class IdBatch {
 struct TreeId {
   int k = 0;
   std::vector<int> skel;  // positions into `rows` of the skeleton rows
-  DBuf<double> P;         // m x k interpolation matrix, P[skel] = I
+  DBuf<double> P;         // m x k interpolation matrix, P[skel] = I (not formed when deferred)
+  // The tree's levels and their interpolation matrices: expand() forms
+  // P T (m x kout) for a k x kout matrix T (leading dimension ldT; null T:
+  // the identity, kout = k) by the top-down products, so that a later
+  // right factor (a recompression) costs products with kout columns only.
+  struct Levels;
+  std::shared_ptr<Levels> lv;
+  DBuf<double> expand(const double* T, int ldT, int kout, cudaStream_t s) const;
 };
+// defer: return the levels without forming P (see TreeId::expand).
 TreeId tree_row_id(const NodesView& S, const std::vector<int>& rows, const IdMatProb& colspec,
                    const NodesView& E1, bool e1s, const NodesView& E2, bool e2s, double tol,
                    int sketch_cols, int sketch_width, unsigned long long seed, int chunk,
-                   cudaStream_t s);
+                   cudaStream_t s, bool defer = false);
 
 struct HbsNode {
   int lo = 0, hi = 0;  // point range

@@ -320,7 +320,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       IdMatProb cs{};
       cs.cx = circ_bas[0]; cs.cy = circ_bas[1]; cs.R = circ_bas[2]; cs.M = o.n_proxy_refine; cs.normal = 1;
       if (nreg > 1) { cs.ncirc = nreg; cs.circ = dcirc_bas.p; }
-      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2);
+      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2,
+                       true);
     } catch (...) { e2 = std::current_exception(); }
   };
   // A_pk: rows of [A_{p,div} | A_pk^near | n_p], then (recompression) a row
@@ -405,7 +406,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     // near rows of I_k: [A_kc^near | A_kp^near]
     IdMatProb cs{};
     cs.n1 = 2 * Nc; cs.e1 = dc.p; cs.n2 = 2 * Np; cs.e2 = dall_p.p; cs.M = 0; cs.normal = 0;
-    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, ftol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s);
+    tn = tree_row_id(VW, near_d, cs, VW, true, VP, false, ftol, o.sketch_cols, o.sketch_width, o.seed + 202, 128, s,
+                     true);
   } catch (...) { e0 = std::current_exception(); }
   if (serial) tr.mark("  near ID");
   // X_o = A_oo^{-1} L_o needs only the far and near IDs: it runs on the main
@@ -415,27 +417,50 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   for (auto& e : {e0, e2}) if (e) std::rethrow_exception(e);
   tr.mark("IDs (concurrent with A_pp)");
   kf = tf.k; kn = tn.k; kk = kf + kn;
-
-  // L_o (2No x kk)
-  Lo.alloc(std::max<size_t>(size_t(2) * No * kk, 1));
-  Lo.zero(s);
-  {
-    auto dfar = to_device_tmp(far_d, s), dnear = to_device_tmp(near_d, s);
-    if (kf) gather_scatter(tf.P.p, int(far_d.size()), nullptr, Lo.p, 2 * No, dfar.p, int(far_d.size()), kf, s);
-    if (kn) gather_scatter(tn.P.p, int(near_d.size()), nullptr, Lo.p + size_t(2) * No * kf, 2 * No, dnear.p, int(near_d.size()), kn, s);
-    RW_CUDA(cudaStreamSynchronize(s));
-  }
   // skeleton DOFs
   std::vector<int> Jk;
   for (int i : tf.skel) Jk.push_back(far_d[i]);
   for (int i : tn.skel) Jk.push_back(near_d[i]);
-  if (recompress) {
-    // row ID of R_k = [A(J_k, I_c), A(J_k, I_p)]
+  // Recompression (Sec. 3.4): a row ID of R_k = [A(J_k, I_c), A(J_k, I_p)]
+  // whose interpolation matrix T (kk x k2) multiplies L_o = [P_far ; P_near]
+  // (block columns kf | kn, disjoint rows) from the right.  It needs only
+  // the skeletons, so it runs before L_o exists, and the far and near trees
+  // are expanded into P_far T(0:kf, :) and P_near T(kf:kk, :) directly.
+  TreeId rk;
+  bool reduced = false;
+  if (recompress && kk > 0) {
     IdMatProb ck{};
     ck.n1 = 2 * Nc; ck.e1 = dc.p; ck.n2 = 2 * Np; ck.e2 = dall_p.p;
-    recompress_rows(VW, Jk, ck, VW, true, VP, false, Lo, 2 * No, kk, rtol, o.seed + 404, s);
+    rk = tree_row_id(VW, Jk, ck, VW, true, VP, false, rtol, o.sketch_cols, o.sketch_width, o.seed + 404, 128, s);
+    reduced = rk.k < kk;
     tr.mark("recompression (wall rows)");
   }
+  const int k2 = reduced ? rk.k : kk;
+  // L_o (2No x k2)
+  Lo.alloc(std::max<size_t>(size_t(2) * No * k2, 1));
+  Lo.zero(s);
+  {
+    auto dfar = to_device_tmp(far_d, s), dnear = to_device_tmp(near_d, s);
+    const double* T = reduced ? rk.P.p : nullptr;
+    if (kf && k2) {
+      DBuf<double> Pf = tf.expand(T, kk, k2, s);
+      gather_scatter(Pf.p, int(far_d.size()), nullptr, Lo.p, 2 * No, dfar.p, int(far_d.size()), reduced ? k2 : kf, s);
+      RW_CUDA(cudaStreamSynchronize(s));
+    }
+    if (kn && k2) {
+      DBuf<double> Pn = tn.expand(T ? T + kf : nullptr, kk, k2, s);
+      double* dst = reduced ? Lo.p : Lo.p + size_t(2) * No * kf;
+      gather_scatter(Pn.p, int(near_d.size()), nullptr, dst, 2 * No, dnear.p, int(near_d.size()), reduced ? k2 : kn, s);
+      RW_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  if (reduced) {
+    std::vector<int> J2;
+    for (int i : rk.skel) J2.push_back(Jk[i]);
+    Jk = J2;
+  }
+  kk = k2;
+  tr.mark("L_o (deferred expansion)");
   if (th3.joinable()) th3.join();
   if (e3) std::rethrow_exception(e3);
   k = kk + kpk;
@@ -499,11 +524,26 @@ void Refinement::form_w(cudaStream_t s) {
   k_identity<<<ceil_div((long long)k * k, 256), 256, 0, s>>>(W.p, k);
   RW_CHECK_LAUNCH();
   if (kk && Nc) gather_scatter(Xo.p, 2 * No, dc.p, Xc.p, 2 * Nc, nullptr, 2 * Nc, kk, s);
-  std::vector<GemmProb> g;
-  if (kk && Nc) g.push_back(GemmProb{Rkc.p, Xc.p, W.p, kk, kk, 2 * Nc, kk, 2 * Nc, k, 0, 0, 1.0, 1.0});
-  if (kk && kpk) g.push_back(GemmProb{Rkp.p, Xp.p, W.p + size_t(kk) * k, kk, kpk, 2 * Np, kk, 2 * Np, k, 0, 0, 1.0, 1.0});
-  if (kk && kpk) g.push_back(GemmProb{Rpk.p, Xo.p, W.p + kk, kpk, kk, 2 * No, kpk, 2 * No, k, 0, 0, 1.0, 1.0});
-  batched_gemm(g, s);
+  if (wall->opts.mixed_factor) {
+    // a factorisation for the iterative modes: the products in double-FP32
+    // (R held as FP32 pairs; the copies serve the solve programs later)
+    AllocStreamScope scope(streams.main);
+    for (auto pr : {std::make_pair(&Rkc, &Rkc2), std::make_pair(&Rkp, &Rkp2), std::make_pair(&Rpk, &Rpk2)}) {
+      pr.second->alloc(pr.first->n);
+      copy_d2df(pr.first->p, pr.second->p, pr.first->n, s);
+    }
+    std::vector<GemmDfProb> g;
+    if (kk && Nc) g.push_back(GemmDfProb{Rkc2.p, Xc.p, W.p, kk, kk, 2 * Nc, kk, 2 * Nc, k, 1.0, 1.0});
+    if (kk && kpk) g.push_back(GemmDfProb{Rkp2.p, Xp.p, W.p + size_t(kk) * k, kk, kpk, 2 * Np, kk, 2 * Np, k, 1.0, 1.0});
+    if (kk && kpk) g.push_back(GemmDfProb{Rpk2.p, Xo.p, W.p + kk, kpk, kk, 2 * No, kpk, 2 * No, k, 1.0, 1.0});
+    batched_gemm_df(g, s);
+  } else {
+    std::vector<GemmProb> g;
+    if (kk && Nc) g.push_back(GemmProb{Rkc.p, Xc.p, W.p, kk, kk, 2 * Nc, kk, 2 * Nc, k, 0, 0, 1.0, 1.0});
+    if (kk && kpk) g.push_back(GemmProb{Rkp.p, Xp.p, W.p + size_t(kk) * k, kk, kpk, 2 * Np, kk, 2 * Np, k, 0, 0, 1.0, 1.0});
+    if (kk && kpk) g.push_back(GemmProb{Rpk.p, Xo.p, W.p + kk, kpk, kk, 2 * No, kpk, 2 * No, k, 0, 0, 1.0, 1.0});
+    batched_gemm(g, s);
+  }
   Winv.alloc(std::max<size_t>(size_t(k) * k, 1));
   DBuf<int> flag(1);
   DBuf<double> norms(2);
@@ -519,8 +559,9 @@ void Refinement::form_w(cudaStream_t s) {
     RW_CHECK_LAUNCH();
   }
   // the solve program depends on the buffers, not on their values: the host
-  // builds it while the GPU forms W and W^-1
-  build_solve_program(s);
+  // builds it while the GPU forms W and W^-1 (the direct modes it serves
+  // refuse a factorisation for the iterative modes)
+  if (!wall->opts.mixed_factor) build_solve_program(s);
   auto hf = flag.download(s);
   require(hf[0] == 0, "refine: Woodbury operator W = I + R X is singular", RW_ERR_SINGULAR);
   const auto hn = norms.download(s);
@@ -595,6 +636,7 @@ void Refinement::solve_direct(const double* g, double* tau, int nrhs, cudaStream
     solve_direct_levels(g, tau, nrhs, s);
     return;
   }
+  require(!wall->opts.mixed_factor, "solve_direct: a factorisation for the iterative modes (opts.mixed_factor)");
   const size_t need = size_t(std::max<long long>(solve_prog.ws_per_rhs(), 1)) * nrhs;
   if (solve_ws.n < need) solve_ws.alloc(need);
   double* bases[kMaxBases] = {const_cast<double*>(g), tau, solve_ws.p, nullptr};

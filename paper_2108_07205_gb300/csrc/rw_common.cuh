@@ -51,6 +51,26 @@ extern thread_local cudaStream_t tl_alloc_stream;
 // synchronisation, so a refinement's temporaries and factors are recycled
 // from one time step to the next instead of being mapped afresh.
 void pool_retain_once();
+// Fork-join over side streams of the calling host thread (up to 7, created
+// on first use and kept for the thread's lifetime): next() returns the
+// caller's stream s first, then side streams that wait for the work queued
+// on s so far; join() (or the destructor) makes s wait for every side stream
+// handed out.  With n <= 1 everything stays on s.
+class ForkJoin {
+ public:
+  ForkJoin(cudaStream_t s, int n);
+  ForkJoin(const ForkJoin&) = delete;
+  ForkJoin& operator=(const ForkJoin&) = delete;
+  cudaStream_t next();
+  void join();
+  ~ForkJoin();
+
+ private:
+  cudaStream_t s_;
+  int n_, used_ = 0;
+  bool joined_ = false;
+};
+
 struct AllocStreamScope {
   cudaStream_t prev;
   explicit AllocStreamScope(cudaStream_t s) : prev(tl_alloc_stream) { tl_alloc_stream = s; }
