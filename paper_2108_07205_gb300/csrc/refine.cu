@@ -8,7 +8,8 @@
 // Low-rank factors (Sec. 3.3-3.4, uniform row-ID format: L = interpolation
 // matrices, R = skeleton rows of A):
 //  * far rows of I_k (outside P^div): one hierarchical ID against proxy
-//    sources on P^bas, shared by A_kc and A_kp (Remark after Def. 3.1);
+//    sources on P^bas, shared by A_kc and A_kp (Remark after Def. 3.1),
+//    organised by the wall's own HBS tree (far_select / far_expand below);
 //  * near rows of I_k: one direct ID of [A_kc^near | A_kp^near];
 //  * A_pk: one hierarchical ID of the rows of [A_{p,div} | A_pk^near];
 //  so L = blkdiag(L_k, L_pk) with L_k = [P_far ; P_near] on the k rows and
@@ -21,6 +22,7 @@
 //  A(J_pk, I_k) (sketched when wide) fold into L and thin J (recompress_rows):
 //  226 -> 81 on the 1024-panel channel (the paper's k_opt ~ 79, Sec. 3.4).
 #include "refine.cuh"
+#include <functional>
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -55,6 +57,147 @@ __global__ void k_zero_cols(double* A, int ld, int nrows, const int* cols, int n
     const int r = e % nrows, c = e / nrows;
     A[r + size_t(cols[c]) * ld] = 0.0;
   }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- far ID on the wall's tree
+// The far-field rows of I_k against P^bas organised by the binary tree of the
+// wall's own HBS (Sec. 3.3 allows the binary tree used in the HBS forward
+// compression).  A node of the operator's HBS whose points are all far and
+// whose proxy circle leaves every P^bas disk outside already has a row ID of
+// its interaction with everything outside that circle: A(I_t, out) ~
+// U_t^full A(J_t, out), U_t^full the product of the nested U's down to its
+// leaves.  Such nodes (the largest ones, found top-down) contribute their
+// skeleton rows J_t, the far points of the remaining leaves contribute
+// themselves; one tree ID of these candidates against P^bas gives
+// A(cand, I_r) ~ P A(J, I_r), and the far block of L_o is U^full P (raw
+// candidates: the rows of P), formed top-down with P's right factor applied
+// first.  The per-step work then scales with the number of candidates
+// (about the skeletons of O(log N) nodes) instead of every far row.
+struct FarOnTree {
+  TreeId top;
+  std::vector<int> cand;          // candidate DOFs: selected skeletons and raw far rows, in curve order
+  std::vector<int> sel, sel_pos;  // selected heap nodes and the offset of their skeleton in cand
+  std::vector<int> raw_dof, raw_pos;
+};
+
+// RW_FAR_ON_TREE=0 (diagnostics): the far-field ID over every far row in
+// chunks of 128 instead.
+bool far_on_tree_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("RW_FAR_ON_TREE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+namespace {
+
+// Candidate selection.  isfar: per wall point; circ: (cx, cy, R) of each
+// region's P^bas.  Node centres are the exact centroids; radii are bounded
+// from the children up (a circle around both children's circles), which can
+// only enlarge a proxy circle and so only makes the test stricter.
+void far_select(const Hbs& H, const Wall& w, const std::vector<char>& isfar, const std::vector<double>& circ,
+                FarOnTree& f) {
+  const int L = H.L, nh = 2 << L;
+  std::vector<double> cx(nh, 0.0), cy(nh, 0.0), rad(nh, 0.0);
+  for (int h = 1 << L; h < nh; ++h) {
+    const HbsNode& nd = H.node[h];
+    double x = 0, y = 0;
+    for (int i = nd.lo; i < nd.hi; ++i) { x += w.nodes.hx[i]; y += w.nodes.hy[i]; }
+    const int n = std::max(nd.hi - nd.lo, 1);
+    x /= n;
+    y /= n;
+    double r2 = 0;
+    for (int i = nd.lo; i < nd.hi; ++i)
+      r2 = std::max(r2, (w.nodes.hx[i] - x) * (w.nodes.hx[i] - x) + (w.nodes.hy[i] - y) * (w.nodes.hy[i] - y));
+    cx[h] = x; cy[h] = y; rad[h] = std::sqrt(r2);
+  }
+  for (int h = (1 << L) - 1; h >= 1; --h) {
+    const int a = 2 * h, b = 2 * h + 1;
+    const double na = H.node[a].hi - H.node[a].lo, nb = H.node[b].hi - H.node[b].lo;
+    cx[h] = (na * cx[a] + nb * cx[b]) / std::max(na + nb, 1.0);
+    cy[h] = (na * cy[a] + nb * cy[b]) / std::max(na + nb, 1.0);
+    rad[h] = std::max(std::hypot(cx[a] - cx[h], cy[a] - cy[h]) + rad[a],
+                      std::hypot(cx[b] - cx[h], cy[b] - cy[h]) + rad[b]);
+  }
+  std::vector<int> pf(w.nodes.n + 1, 0);
+  for (int i = 0; i < w.nodes.n; ++i) pf[i + 1] = pf[i] + (isfar[i] ? 1 : 0);
+  const double ratio = w.opts.proxy_ratio;  // the proxy circles of the HBS compression
+  std::function<void(int, int)> visit = [&](int h, int l) {
+    const HbsNode& nd = H.node[h];
+    const bool allfar = nd.hi > nd.lo && pf[nd.hi] - pf[nd.lo] == nd.hi - nd.lo;
+    bool clear = allfar && l >= 1 && nd.k > 0;
+    for (size_t r = 0; clear && r + 3 <= circ.size(); r += 3) {
+      const double d = std::hypot(cx[h] - circ[r], cy[h] - circ[r + 1]);
+      clear = d > (1.0 + 1e-9) * (ratio * rad[h] + circ[r + 2]);
+    }
+    if (clear) {
+      f.sel.push_back(h);
+      f.sel_pos.push_back(int(f.cand.size()));
+      f.cand.insert(f.cand.end(), nd.skr.begin(), nd.skr.end());
+      return;
+    }
+    if (l == L) {
+      for (int i = nd.lo; i < nd.hi; ++i)
+        if (isfar[i])
+          for (int c = 0; c < 2; ++c) {
+            f.raw_dof.push_back(2 * i + c);
+            f.raw_pos.push_back(int(f.cand.size()));
+            f.cand.push_back(2 * i + c);
+          }
+      return;
+    }
+    visit(2 * h, l + 1);
+    visit(2 * h + 1, l + 1);
+  };
+  visit(1, 0);
+}
+
+// Rows of L_o (ld ldl) for the far rows: Pc (m_c x k2, ld m_c) is the top
+// ID's interpolation matrix times the recompression's right factor.
+void far_expand(const Hbs& H, const FarOnTree& f, const double* Pc, int k2, double* Lo, int ldl, cudaStream_t s) {
+  const int mc = int(f.cand.size());
+  if (!f.raw_dof.empty()) {
+    auto dpos = to_device_tmp(f.raw_pos, s), ddof = to_device_tmp(f.raw_dof, s);
+    gather_scatter(Pc, mc, dpos.p, Lo, ldl, ddof.p, int(f.raw_dof.size()), k2, s);
+    RW_CUDA(cudaStreamSynchronize(s));
+  }
+  // down the tree: Y_t (k_t x k2) -> [Y_a; Y_b] = U_t Y_t; leaves -> L_o
+  struct Act { int h, l; const double* Y; int ldy; };
+  std::vector<Act> act;
+  auto level_of = [](int h) { int l = 0; while (h > 1) { h >>= 1; ++l; } return l; };
+  for (size_t q = 0; q < f.sel.size(); ++q) act.push_back(Act{f.sel[q], level_of(f.sel[q]), Pc + f.sel_pos[q], mc});
+  std::vector<DBuf<double>> keep;
+  while (!act.empty()) {
+    size_t sz = 0;
+    for (const Act& a : act) if (a.l < H.L) sz += size_t(H.node[a.h].m) * k2;
+    DBuf<double> buf(std::max<size_t>(sz, 1));
+    std::vector<GemmProb> gm;
+    std::vector<Act> nxt;
+    size_t off = 0;
+    for (const Act& a : act) {
+      const HbsNode& nd = H.node[a.h];
+      const Hbs::Level& LV = H.lev[a.l];
+      const int t = a.h - (1 << a.l);
+      if (a.l == H.L) {
+        const int n = 2 * (nd.hi - nd.lo);
+        gm.push_back(GemmProb{LV.U.p + LV.oU[t], a.Y, Lo + 2 * size_t(nd.lo), n, k2, nd.k, n, a.ldy, ldl, 0, 0, 1.0, 0.0});
+      } else {
+        double* C = buf.p + off;
+        gm.push_back(GemmProb{LV.U.p + LV.oU[t], a.Y, C, nd.m, k2, nd.k, nd.m, a.ldy, nd.m, 0, 0, 1.0, 0.0});
+        const int ka = H.node[2 * a.h].k;
+        nxt.push_back(Act{2 * a.h, a.l + 1, C, nd.m});
+        nxt.push_back(Act{2 * a.h + 1, a.l + 1, C + ka, nd.m});
+        off += size_t(nd.m) * k2;
+      }
+    }
+    batched_gemm(gm, s);
+    keep.push_back(std::move(buf));
+    act = nxt;
+  }
+  RW_CUDA(cudaStreamSynchronize(s));  // the level buffers are released here
 }
 
 }  // namespace
@@ -276,6 +419,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   // A_pk IDs run concurrently on three streams driven by three host threads.
   const NodesView VW = w.nodes.view(), VP = pn.view();
   TreeId tf, tn;
+  FarOnTree ft;
+  const bool use_tree = far_on_tree_enabled();
   DBuf<int> dall_p;
   std::vector<DBuf<int>> dnear_r(nreg);
   DBuf<double> dcirc_bas;
@@ -320,8 +465,16 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       IdMatProb cs{};
       cs.cx = circ_bas[0]; cs.cy = circ_bas[1]; cs.R = circ_bas[2]; cs.M = o.n_proxy_refine; cs.normal = 1;
       if (nreg > 1) { cs.ncirc = nreg; cs.circ = dcirc_bas.p; }
-      tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101, 128, s2,
-                       true);
+      if (use_tree) {
+        std::vector<char> isfar(w.nodes.n, 0);
+        for (size_t q = 0; q < far_d.size(); q += 2) isfar[far_d[q] / 2] = 1;
+        far_select(w.op(), w, isfar, circ_bas, ft);
+        ft.top = tree_row_id(VW, ft.cand, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101,
+                             128, s2, true);
+      } else {
+        tf = tree_row_id(VW, far_d, cs, VW, true, VW, true, ftol, o.sketch_cols, o.sketch_width, o.seed + 101, 128,
+                         s2, true);
+      }
     } catch (...) { e2 = std::current_exception(); }
   };
   // A_pk: rows of [A_{p,div} | A_pk^near | n_p], then (recompression) a row
@@ -416,10 +569,11 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   RW_CUDA(cudaStreamSynchronize(s2));
   for (auto& e : {e0, e2}) if (e) std::rethrow_exception(e);
   tr.mark("IDs (concurrent with A_pp)");
-  kf = tf.k; kn = tn.k; kk = kf + kn;
+  kf = use_tree ? ft.top.k : tf.k; kn = tn.k; kk = kf + kn;
   // skeleton DOFs
   std::vector<int> Jk;
-  for (int i : tf.skel) Jk.push_back(far_d[i]);
+  if (use_tree) for (int i : ft.top.skel) Jk.push_back(ft.cand[i]);
+  else for (int i : tf.skel) Jk.push_back(far_d[i]);
   for (int i : tn.skel) Jk.push_back(near_d[i]);
   // Recompression (Sec. 3.4): a row ID of R_k = [A(J_k, I_c), A(J_k, I_p)]
   // whose interpolation matrix T (kk x k2) multiplies L_o = [P_far ; P_near]
@@ -442,7 +596,11 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   {
     auto dfar = to_device_tmp(far_d, s), dnear = to_device_tmp(near_d, s);
     const double* T = reduced ? rk.P.p : nullptr;
-    if (kf && k2) {
+    if (kf && k2 && use_tree) {
+      const int kout = reduced ? k2 : kf;
+      DBuf<double> Pc = ft.top.expand(T, kk, kout, s);
+      far_expand(w.op(), ft, Pc.p, kout, Lo.p, 2 * No, s);
+    } else if (kf && k2) {
       DBuf<double> Pf = tf.expand(T, kk, k2, s);
       gather_scatter(Pf.p, int(far_d.size()), nullptr, Lo.p, 2 * No, dfar.p, int(far_d.size()), reduced ? k2 : kf, s);
       RW_CUDA(cudaStreamSynchronize(s));
