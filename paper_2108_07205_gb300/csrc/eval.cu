@@ -263,38 +263,60 @@ __global__ void k_copy(const CopyProb* probs) {
     for (int i = threadIdx.x; i < P.m; i += blockDim.x) P.out[i + size_t(j) * P.ldo] = P.in[i + size_t(j) * P.ldi];
 }
 
-__global__ void k_velocity(NodesView nd, const double* tau, int ldt, int nt, const double* tg, double* u, int acc) {
-  // one CTA per (target, right-hand side); sources split over the threads.
-  // Wall sources carry the double layer; hole sources (kind 1) the combined
-  // field, whose single layer adds w_j S(x, y_j) tau_j.
-  const int t = blockIdx.x, r = blockIdx.y;
+// One CTA per (target, group of up to kVelRhs right-hand sides); sources
+// split over the threads.  The geometric factors of a (target, source) pair
+// are formed once and applied to every right-hand side of the group.  Wall
+// sources carry the double layer; hole sources (kind 1) the combined field,
+// whose single layer adds w_j S(x, y_j) tau_j.
+constexpr int kVelRhs = 8;
+__global__ void __launch_bounds__(256) k_velocity(NodesView nd, const double* tau, int ldt, int nt, int nrhs,
+                                                  const double* tg, double* u, int acc) {
+  const int t = blockIdx.x, r0 = blockIdx.y * kVelRhs, nr = min(kVelRhs, nrhs - r0);
   const double x = tg[2 * t], y = tg[2 * t + 1];
-  const double* tr = tau + size_t(r) * ldt;
-  double ux = 0.0, uy = 0.0;
+  double ux[kVelRhs], uy[kVelRhs];
+#pragma unroll
+  for (int q = 0; q < kVelRhs; ++q) ux[q] = uy[q] = 0.0;
   for (int j = threadIdx.x; j < nd.n; j += blockDim.x) {
-    const double rx = x - nd.x[j], ry = y - nd.y[j], r2 = rx * rx + ry * ry;
-    const double fac = nd.w[j] * (rx * nd.nx[j] + ry * nd.ny[j]) / (kPi * r2 * r2);
-    const double rt = rx * tr[2 * j] + ry * tr[2 * j + 1];
-    ux += fac * rx * rt;
-    uy += fac * ry * rt;
-    if (nd.kind) {
-      const double c = nd.w[j] * (0.25 / kPi), lg = -0.5 * log(r2), q = rt / r2;
-      ux += c * (lg * tr[2 * j] + rx * q);
-      uy += c * (lg * tr[2 * j + 1] + ry * q);
+    const double rx = x - nd.x[j], ry = y - nd.y[j], r2 = rx * rx + ry * ry, inv = 1.0 / r2;
+    const double fac = nd.w[j] * (rx * nd.nx[j] + ry * nd.ny[j]) * inv * inv * (1.0 / kPi);
+    const double c = nd.kind ? nd.w[j] * (0.25 / kPi) : 0.0, lg = nd.kind ? -0.5 * log(r2) : 0.0;
+#pragma unroll
+    for (int q = 0; q < kVelRhs; ++q) {
+      if (q >= nr) break;
+      const double* tr = tau + size_t(r0 + q) * ldt;
+      const double tx = tr[2 * j], ty = tr[2 * j + 1];
+      const double rt = rx * tx + ry * ty;
+      ux[q] += fac * rx * rt;
+      uy[q] += fac * ry * rt;
+      if (nd.kind) {
+        const double qq = rt * inv;
+        ux[q] += c * (lg * tx + rx * qq);
+        uy[q] += c * (lg * ty + ry * qq);
+      }
     }
   }
-  __shared__ double sx[256], sy[256];
-  sx[threadIdx.x] = ux;
-  sy[threadIdx.x] = uy;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) { sx[threadIdx.x] += sx[threadIdx.x + w]; sy[threadIdx.x] += sy[threadIdx.x + w]; }
-    __syncthreads();
+  // block sums in a fixed order: warps by shuffles, then warp 0 over warps
+  __shared__ double part[2 * kVelRhs][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kVelRhs; ++q) {
+    double a = ux[q], b = uy[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, off);
+      b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    if (lane == 0) { part[2 * q][warp] = a; part[2 * q + 1][warp] = b; }
   }
-  if (threadIdx.x == 0) {
-    double* ur = u + size_t(r) * 2 * nt;
-    ur[2 * t] = (acc ? ur[2 * t] : 0.0) + sx[0];
-    ur[2 * t + 1] = (acc ? ur[2 * t + 1] : 0.0) + sy[0];
+  __syncthreads();
+  if (warp == 0) {
+    for (int v = 0; v < 2 * nr; ++v) {
+      double a = lane < nw ? part[v][lane] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+      if (lane == 0) {
+        double* ur = u + size_t(r0 + v / 2) * 2 * nt + 2 * t + (v & 1);
+        *ur = (acc ? *ur : 0.0) + a;
+      }
+    }
   }
 }
 
@@ -329,14 +351,39 @@ __global__ void k_pressure(NodesView nd, const double* tau, int ldt, int nt, con
   }
 }
 
-__global__ void k_stokeslets(NodesView nd, int ns, const double* src, int nrhs, const double* f, double* g) {
+// Boundary data of point forces: one thread per node, one right-hand side
+// per blockIdx.y.  The sources with a nonzero force on this right-hand side
+// are listed first (warp 0, in increasing order, zero tested on the bit
+// pattern) in dynamic shared memory when there is room (list = 1), so that
+// each node visits only those; the sum runs in the same order either way.
+__global__ void k_stokeslets(NodesView nd, int ns, const double* src, int nrhs, const double* f, double* g, int list) {
+  extern __shared__ int live[];
+  __shared__ int nlive;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (i >= nd.n) return;
   const double* fr = f + size_t(r) * 2 * ns;
+  if (list) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      int base = 0;
+      for (int s0 = 0; s0 < ns; s0 += 32) {
+        const int s = s0 + lane;
+        const bool nz = s < ns && ((static_cast<unsigned long long>(__double_as_longlong(fr[2 * s])) |
+                                    static_cast<unsigned long long>(__double_as_longlong(fr[2 * s + 1]))) << 1) != 0ull;
+        const unsigned m = __ballot_sync(0xffffffffu, nz);
+        if (nz) live[base + __popc(m & ((1u << lane) - 1u))] = s;
+        base += __popc(m);
+      }
+      if (lane == 0) nlive = base;
+    }
+    __syncthreads();
+  }
+  if (i >= nd.n) return;
+  const int cnt = list ? nlive : ns;
   double gx = 0.0, gy = 0.0;
-  for (int s = 0; s < ns; ++s) {
-    if (fr[2 * s] == 0.0 && fr[2 * s + 1] == 0.0) continue;  // no force on this right-hand side
+  for (int q = 0; q < cnt; ++q) {
+    const int s = list ? live[q] : q;
+    if (!list && fr[2 * s] == 0.0 && fr[2 * s + 1] == 0.0) continue;  // no force on this right-hand side
     const double rx = nd.x[i] - src[2 * s], ry = nd.y[i] - src[2 * s + 1], r2 = rx * rx + ry * ry;
     const double lg = -0.5 * log(r2);
     const double rf = (rx * fr[2 * s] + ry * fr[2 * s + 1]) / r2;
@@ -743,7 +790,8 @@ void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, 
     return;
   }
   ProfScope prof_(KC_EVAL, s);
-  k_velocity<<<dim3(nt, nrhs), 256, 0, s>>>(nodes, tau, ldt > 0 ? ldt : 2 * nodes.n, nt, targets, u, accumulate);
+  k_velocity<<<dim3(nt, ceil_div(nrhs, kVelRhs)), 256, 0, s>>>(nodes, tau, ldt > 0 ? ldt : 2 * nodes.n, nt, nrhs,
+                                                                 targets, u, accumulate);
   RW_CHECK_LAUNCH();
 }
 
@@ -796,7 +844,9 @@ void eval_stokeslets(const NodesView& nodes, int ns, const double* src, int nrhs
                      cudaStream_t s) {
   if (nodes.n <= 0 || nrhs <= 0) return;
   ProfScope prof_(KC_EVAL, s);
-  k_stokeslets<<<dim3(ceil_div(nodes.n, 128), nrhs), 128, 0, s>>>(nodes, ns, src, nrhs, f, g);
+  const int list = ns <= 8192 ? 1 : 0;  // the list of live sources fits shared memory
+  k_stokeslets<<<dim3(ceil_div(nodes.n, 128), nrhs), 128, list ? size_t(ns) * sizeof(int) : 0, s>>>(nodes, ns, src, nrhs,
+                                                                                                   f, g, list);
   RW_CHECK_LAUNCH();
 }
 
