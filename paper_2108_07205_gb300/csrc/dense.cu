@@ -857,6 +857,8 @@ __host__ __device__ inline int cpqr_threads_per_col(int cw, int nt) {
 __host__ __device__ inline int cpqr_ld(int nr, int G) {
   return G >= 16 ? nr : nr + ((G - nr % 16) + 16) % 16;
 }
+// Threads of a cluster-QR CTA.
+constexpr int kCpqrThreads = 256;
 // Shared memory of a cluster-QR CTA (bytes): its columns, two published
 // columns, the Householder vector and two norm arrays.
 __host__ __device__ inline size_t cpqr_cluster_smem(int nr, int cw, int nt) {
@@ -933,7 +935,7 @@ __device__ __forceinline__ void cpqr_update_columns(double* Wl, int ld, int nr, 
 // with the larger of the two ranks (the common rank of a node's row and
 // column IDs) in one pass.  A problem that runs out of candidates or of
 // nonzero columns stops on its own while its partner continues.
-__global__ void __launch_bounds__(256) k_cpqr_cluster(const IdProb* probs, int base, int CS, int paired,
+__global__ void __launch_bounds__(kCpqrThreads) k_cpqr_cluster(const IdProb* probs, int base, int CS, int paired,
                                                       double* flops_out) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = int(cluster.block_rank());
@@ -1875,7 +1877,7 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired
     int q = -1;
     for (int t = q_min; t < 4 && q < 0; ++t) {
       const int cw = (p.nc + sizes[t] - 1) / sizes[t];
-      if (cpqr_cluster_smem(p.nr, cw, 256) <= cap) q = t;
+      if (cpqr_cluster_smem(p.nr, cw, kCpqrThreads) <= cap) q = t;
     }
     if (q < 0) return -1;
     while (q < spread_q && q < 3 && p.nc >= 32 * sizes[q + 1]) ++q;
@@ -1936,10 +1938,10 @@ void batched_id(const std::vector<IdProb>& probs_in, cudaStream_t s, bool paired
     if (g.empty()) return;
     const cudaStream_t s = fj.next();
     size_t smem = 0;
-    for (auto& p : g) smem = std::max(smem, cpqr_cluster_smem(p.nr, (p.nc + CS - 1) / CS, 256));
+    for (auto& p : g) smem = std::max(smem, cpqr_cluster_smem(p.nr, (p.nc + CS - 1) / CS, kCpqrThreads));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(g.size() * CS));
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kCpqrThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
