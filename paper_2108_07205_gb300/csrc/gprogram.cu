@@ -498,10 +498,18 @@ void GProgram<T>::finalize(cudaStream_t s_caller, cudaStream_t alloc) {
     for (int t = tile0[q]; t < tile0[q + 1]; ++t) top[t] = int(q);
   nph_ = int(out.size());
   ph_tiles_.clear();
+  ph_mac_.clear();
+  ph_kmax_.clear();
   for (auto& q : out) {
-    int tq = 0;
-    for (const MOp& o : q) tq += op_tiles(o, tk_);
+    int tq = 0, km = 0;
+    double mac = 0.0;
+    for (const MOp& o : q) {
+      tq += op_tiles(o, tk_);
+      if (o.kind == MOP_GEMM) { mac += double(o.m) * o.n; km = std::max(km, o.n); }
+    }
     ph_tiles_.push_back(tq);
+    ph_mac_.push_back(mac);
+    ph_kmax_.push_back(km);
   }
   d_ops_ = to_device(flat.empty() ? std::vector<MOp>(1) : flat, s);
   d_phase_ = to_device(phase, s);
@@ -554,13 +562,13 @@ void GProgram<T>::run(T* const* bases, int nrhs, cudaStream_t s) const {
       std::vector<long long> h(nph_ + 1);
       RW_CUDA(cudaMemcpyAsync(h.data(), times.p, h.size() * sizeof(long long), cudaMemcpyDeviceToHost, s));
       RW_CUDA(cudaStreamSynchronize(s));
-      std::fprintf(stderr, "[rw gprogram] kind %d, %d phases, grid %d:", tk_, nph_, grid_);
+      std::fprintf(stderr, "[rw gprogram] kind %d, %d phases, grid %d, %d right-hand sides:\n", tk_, nph_, grid_, nc);
       long long prev = h[nph_];
       for (int q = 0; q < nph_; ++q) {
-        std::fprintf(stderr, " %d:%lld", ph_tiles_[q], h[q] - prev);
+        std::fprintf(stderr, "[rw gprogram]   phase %2d: %5d tiles, K <= %5d, %9.3f M multiply-adds, %8lld cycles\n", q,
+                     ph_tiles_[q], ph_kmax_[q], 1e-6 * ph_mac_[q] * nc, h[q] - prev);
         prev = h[q];
       }
-      std::fprintf(stderr, " (tiles:cycles)\n");
     }
   }
 }

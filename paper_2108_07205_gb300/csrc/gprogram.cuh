@@ -82,6 +82,8 @@ class GProgram {
   bool prof_class_df_ = false;
   int tk_ = -1;  // tile kind of the program's products (one per program)
   std::vector<int> ph_tiles_;
+  std::vector<double> ph_mac_;   // multiply-adds per right-hand side of each phase (diagnostics)
+  std::vector<int> ph_kmax_;     // longest inner dimension of a tile in each phase (diagnostics)
   double flops_ = 0.0;
   DBuf<MOp> d_ops_;
   DBuf<int> d_tile0_, d_top_, d_phase_;
