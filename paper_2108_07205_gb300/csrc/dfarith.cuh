@@ -39,4 +39,43 @@ __device__ __forceinline__ void df_split(double v, float& h, float& l) {
   l = __double2float_rn(v - double(h));
 }
 
+// The same split from the bit pattern, with integer operations only (this
+// part's FP64 units run at 1/64 of its FP32 rate, so a conversion and a
+// subtraction in FP64 per staged entry would cost as much as the products):
+// hi = v with its significand truncated to 24 bits, lo = the remaining 29
+// bits truncated to 24, so |v - hi - lo| <= 2^-47 |v|.  Zero, and values
+// whose pieces would leave FP32's normal range, take the FP64 route.
+__device__ __forceinline__ void df_split_bits(double v, float& h, float& l) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = int((b >> 52) & 0x7FF);
+  if (e < 950 || e > 1150) {
+    df_split(v, h, l);
+    return;
+  }
+  const unsigned sign = static_cast<unsigned>(b >> 63) << 31;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  h = __uint_as_float(sign | (static_cast<unsigned>(e - 896) << 23) | static_cast<unsigned>(m >> 29));
+  const unsigned long long r = m & 0x1FFFFFFFull;
+  if (r == 0) {
+    l = 0.f;
+    return;
+  }
+  const int p = 63 - __clzll(static_cast<long long>(r));  // leading bit of the rest, 0..28
+  const unsigned frac = p >= 23 ? static_cast<unsigned>((r >> (p - 23)) & 0x7FFFFF)
+                                : static_cast<unsigned>((r << (23 - p)) & 0x7FFFFF);
+  l = __uint_as_float(sign | (static_cast<unsigned>(e - 948 + p) << 23) | frac);
+}
+
+// FP32 -> FP64 by its bit pattern (exact), the FP64 conversion only for
+// zero, subnormals, infinities and NaN.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xFF;
+  if (ex == 0 || ex == 255) return (u << 1) == 0u ? __longlong_as_double(static_cast<long long>(u >> 31) << 63) : double(f);
+  const unsigned long long b = (static_cast<unsigned long long>(u >> 31) << 63) |
+                               (static_cast<unsigned long long>(ex + 896) << 52) |
+                               (static_cast<unsigned long long>(u & 0x7FFFFF) << 29);
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
 }  // namespace rw

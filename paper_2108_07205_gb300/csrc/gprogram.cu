@@ -144,7 +144,7 @@ __device__ void tile_df(const MOp& o, int tile, const double* x, double* y, int 
     for (int r = 0; r < 2; ++r) {
       const int e = tid + r * 256;
       float h, l;
-      df_split(rb[r], h, l);
+      df_split_bits(rb[r], h, l);
       Bh[e & 15][e >> 4] = h;
       Bl[e & 15][e >> 4] = l;
     }
@@ -170,6 +170,9 @@ __device__ void tile_df(const MOp& o, int tile, const double* x, double* y, int 
         for (int j = 0; j < 2; ++j) df_flush(H[i][j], L[i][j], s[i][j], c[i][j]);
     }
   }
+  // alpha and beta are almost always +-1 / 0 / 1: tested once per tile, so
+  // that the epilogue's FP64 work is one addition per output (two with beta)
+  const bool a_one = o.alpha == 1.0, a_neg1 = o.alpha == -1.0, b_zero = o.beta == 0.0, b_one = o.beta == 1.0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int gi = m0 + ty + 16 * i;
@@ -179,8 +182,11 @@ __device__ void tile_df(const MOp& o, int tile, const double* x, double* y, int 
       const int gj = n0 + tx + 16 * j;
       if (gi >= o.m || gj >= nc) continue;
       double* yp = y + gi + size_t(gj) * o.ldy;
-      double v = o.alpha * (double(H[i][j]) + double(L[i][j]));
-      if (o.beta != 0.0) v += o.beta * *yp;
+      double v = f2d_bits(H[i][j]) + f2d_bits(L[i][j]);
+      if (a_neg1) v = -v;
+      else if (!a_one) v *= o.alpha;
+      if (b_one) v += *yp;
+      else if (!b_zero) v += o.beta * *yp;
       *yp = v;
     }
   }

@@ -217,9 +217,7 @@ __global__ void __launch_bounds__(256) k_gemm_df(const GemmDfWork* work, const i
       const int gj = n0 + j, gk = k0 + kk;
       float h = 0.f, l = 0.f;
       if (gj < P.n && gk < ke) {
-        const double v = P.B[gk + size_t(gj) * P.ldb];
-        h = __double2float_rn(v);
-        l = __double2float_rn(v - double(h));
+        df_split_bits(P.B[gk + size_t(gj) * P.ldb], h, l);
       }
       Bh[kk][j] = h;
       Bl[kk][j] = l;
@@ -258,7 +256,7 @@ __global__ void __launch_bounds__(256) k_gemm_df(const GemmDfWork* work, const i
     for (int j = 0; j < 4; ++j) {
       const int gj = n0 + tx + 16 * j;
       if (gj >= P.n) continue;
-      const double v = double(H[i][j]) + double(L[i][j]);
+      const double v = f2d_bits(H[i][j]) + f2d_bits(L[i][j]);
       if (Wk.nsplit > 1) {
         scratch[Wk.scratch_off + (size_t(split) * P.n + gj) * P.m + gi] = v;
       } else {
