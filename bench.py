@@ -81,6 +81,8 @@ def parse():
                     choices=["mixed2048", "channel1024", "serving", "batched", "holes"],
                     help="mixed2048: 2048-panel channel, 64 RHS per step from Stokeslet pairs (default); "
                          "channel1024: 1024-panel channel, 1 RHS per step")
+    ap.add_argument("--solve-probe", action="store_true",
+                    help="profiling driver: the headline wall, the second step's refinement, one 64-RHS solve")
     ap.add_argument("--refine-probe", type=int, default=0,
                     help="profiling driver: build the wall, run this many refinement steps, print their times")
     return ap.parse_args()
@@ -426,6 +428,32 @@ def refine_probe(k):
     wall.close()
 
 
+def solve_probe():
+    """One step of the headline arm for profiling: the wall (operator
+    tolerance 1e-14, double-FP32 X), the second step of the window schedule,
+    Stokeslet-pair data for 64 right-hand sides, one RW_MODE_DIRECT_IR_DF
+    solve."""
+    import torch
+    from paper_2108_07205_gb300 import rwsolve, inputs
+    rwsolve.load(build_if_missing=True)
+    dev = torch.device("cuda")
+    wall = rwsolve.Wall("channel", P_PANELS, opts=rwsolve.default_opts(op_tol=OP_TOL, mixed_factor=2))
+    panels, levels = inputs.time_schedule(17, P_PANELS, 2)[1]
+    ref = wall.refine(panels, levels)
+    sx, sy, f = inputs.stokeslet_pairs_channel(0, NRHS)
+    src = torch.from_numpy(np.ascontiguousarray(np.stack([sx, sy], 1))).to(dev)
+    fd = torch.from_numpy(np.ascontiguousarray(np.transpose(f, (2, 0, 1)))).to(dev)
+    g = torch.empty(NRHS, 2 * ref.stats()["n_n"], dtype=torch.float64, device=dev)
+    ref.stokeslet_data(src, fd, g, nrhs=NRHS)
+    tau = torch.empty_like(g)
+    info = ref.solve(g, tau, nrhs=NRHS, mode=rwsolve.MODE_DIRECT_IR_DF)
+    torch.cuda.synchronize()
+    print(json.dumps({"level": levels[0], "k": ref.stats()["k"], "iters": info["iters"],
+                      "rel_residual": info["rel_residual"]}))
+    ref.close()
+    wall.close()
+
+
 def run_serving(args):
     """Serving workload: resident walls (channel 512/1024/2048 panels, star 1024
     panels, operator tolerance 1e-14); each request refines 1-64 contiguous
@@ -462,7 +490,7 @@ def run_serving(args):
                 np.stack([tx, ty], 1))
 
     sv = rwsolve.Server(n_workers=4, max_device_bytes=200 << 30)
-    warm = [sv.submit(*make(10 ** 6 + i)[:5], nrhs=1)[0] for i in range(2)]
+    warm = [sv.submit(*make(10 ** 6 + i)[:5], nrhs=1, mode=mode)[0] for i in range(2)]
     for t in warm:
         sv.wait(t)
     reqs = [make(i) for i in range(args.requests)]
@@ -813,6 +841,9 @@ def main():
     if args.workload in WORKLOADS:
         wl = WORKLOADS[args.workload]
         P_PANELS, NRHS, PAIRS = wl["P"], wl["nrhs"], wl["pairs"]
+    if args.solve_probe:
+        solve_probe()
+        return
     if args.refine_probe:
         refine_probe(args.refine_probe)
         return

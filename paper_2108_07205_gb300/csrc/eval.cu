@@ -268,15 +268,18 @@ __global__ void k_copy(const CopyProb* probs) {
 // are formed once and applied to every right-hand side of the group.  Wall
 // sources carry the double layer; hole sources (kind 1) the combined field,
 // whose single layer adds w_j S(x, y_j) tau_j.
+// The sources may be cut into gridDim.z chunks (chunks != null): each
+// chunk's sums go to chunks[z] and k_velocity_sum adds them in order.
 constexpr int kVelRhs = 8;
 __global__ void __launch_bounds__(256) k_velocity(NodesView nd, const double* tau, int ldt, int nt, int nrhs,
-                                                  const double* tg, double* u, int acc) {
+                                                  const double* tg, double* u, int acc, double* chunks) {
   const int t = blockIdx.x, r0 = blockIdx.y * kVelRhs, nr = min(kVelRhs, nrhs - r0);
+  const int per = (nd.n + gridDim.z - 1) / gridDim.z, j0 = blockIdx.z * per, j1 = min(nd.n, j0 + per);
   const double x = tg[2 * t], y = tg[2 * t + 1];
   double ux[kVelRhs], uy[kVelRhs];
 #pragma unroll
   for (int q = 0; q < kVelRhs; ++q) ux[q] = uy[q] = 0.0;
-  for (int j = threadIdx.x; j < nd.n; j += blockDim.x) {
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const double rx = x - nd.x[j], ry = y - nd.y[j], r2 = rx * rx + ry * ry, inv = 1.0 / r2;
     const double fac = nd.w[j] * (rx * nd.nx[j] + ry * nd.ny[j]) * inv * inv * (1.0 / kPi);
     const double c = nd.kind ? nd.w[j] * (0.25 / kPi) : 0.0, lg = nd.kind ? -0.5 * log(r2) : 0.0;
@@ -313,10 +316,23 @@ __global__ void __launch_bounds__(256) k_velocity(NodesView nd, const double* ta
       double a = lane < nw ? part[v][lane] : 0.0;
       for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
       if (lane == 0) {
-        double* ur = u + size_t(r0 + v / 2) * 2 * nt + 2 * t + (v & 1);
-        *ur = (acc ? *ur : 0.0) + a;
+        const size_t o = size_t(r0 + v / 2) * 2 * nt + 2 * t + (v & 1);
+        if (chunks) {
+          chunks[size_t(blockIdx.z) * nrhs * 2 * nt + o] = a;
+        } else {
+          double* ur = u + o;
+          *ur = (acc ? *ur : 0.0) + a;
+        }
       }
     }
+  }
+}
+
+__global__ void k_velocity_sum(const double* part, int nchunk, size_t n, double* u, int acc) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    double a = 0.0;
+    for (int z = 0; z < nchunk; ++z) a += part[size_t(z) * n + i];
+    u[i] = (acc ? u[i] : 0.0) + a;
   }
 }
 
@@ -782,6 +798,20 @@ void batched_copy(const std::vector<CopyProb>& probs, cudaStream_t s) {
   RW_CHECK_LAUNCH();
 }
 
+namespace {
+int sm_count_dev() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 152;
+    }
+    return v;
+  }();
+  return n;
+}
+}  // namespace
+
 void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, const double* targets, double* u,
                    cudaStream_t s, int ldt, bool accumulate) {
   if (nt <= 0 || nrhs <= 0) return;
@@ -790,8 +820,22 @@ void eval_velocity(const NodesView& nodes, const double* tau, int nrhs, int nt, 
     return;
   }
   ProfScope prof_(KC_EVAL, s);
-  k_velocity<<<dim3(nt, ceil_div(nrhs, kVelRhs)), 256, 0, s>>>(nodes, tau, ldt > 0 ? ldt : 2 * nodes.n, nt, nrhs,
-                                                                 targets, u, accumulate);
+  // enough CTAs for the SMs: the sources are cut into chunks (at least 2048
+  // each) when targets x right-hand-side groups alone are few
+  const int groups = ceil_div(nrhs, kVelRhs);
+  const long long ctas = (long long)nt * groups;
+  const int nchunk = int(std::max(1LL, std::min<long long>(ceil_div(4LL * sm_count_dev(), ctas), nodes.n / 2048)));
+  const int ld = ldt > 0 ? ldt : 2 * nodes.n;
+  if (nchunk == 1) {
+    k_velocity<<<dim3(nt, groups, 1), 256, 0, s>>>(nodes, tau, ld, nt, nrhs, targets, u, accumulate, nullptr);
+    RW_CHECK_LAUNCH();
+    return;
+  }
+  const size_t n = size_t(2) * nt * nrhs;
+  TBuf<double> part(n * nchunk, s);
+  k_velocity<<<dim3(nt, groups, nchunk), 256, 0, s>>>(nodes, tau, ld, nt, nrhs, targets, u, accumulate, part.p);
+  RW_CHECK_LAUNCH();
+  k_velocity_sum<<<int(std::min<size_t>((n + 255) / 256, 1024)), 256, 0, s>>>(part.p, nchunk, n, u, accumulate);
   RW_CHECK_LAUNCH();
 }
 
