@@ -408,6 +408,19 @@ int rw_batch_create(int n, const rw_ref_t* refs, void* stream, rw_batch_t* out);
 int rw_batch_rows(rw_batch_t b, long long* offsets);
 int rw_batch_autotune(rw_batch_t b, int nrhs, void* stream, int* tile_rows, float* ms);
 int rw_batch_solve(rw_batch_t b, int nrhs, const double* g, double* tau, int use_graph, void* stream);
+/* The batch solved to a certified residual (Sec. 4.2, as RW_MODE_DIRECT_IR
+ * for each instance): Algorithm 1 for every instance in one persistent
+ * launch per 8 right-hand sides, then FP64 corrections tau_ext +=
+ * A_ext^{-1} (g_ext - (A~ + L R) tau_ext), every instance's operator (its
+ * wall's op_tol forward HBS, A_pp and L R) applied in one launch per 8
+ * right-hand sides, until the worst relative residual over all instances and
+ * right-hand sides is <= tol, at most maxit corrections.  iters and relres
+ * (may be NULL) receive the corrections made and that worst residual;
+ * RW_ERR_NOT_CONVERGED if it stayed above tol.  Same g/tau layout as
+ * rw_batch_solve; also takes refinements whose X is not FP64
+ * (opts.mixed_factor), which rw_batch_solve refuses. */
+int rw_batch_solve_ir(rw_batch_t b, int nrhs, const double* g, double* tau, double tol, int maxit, void* stream,
+                      int* iters, double* relres);
 void rw_batch_free(rw_batch_t b);
 
 /* Opt-in kernel profiler (diagnostics, no counterpart in the paper).

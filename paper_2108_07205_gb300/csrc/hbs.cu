@@ -987,6 +987,68 @@ int Hbs::emit_inverse_sweep(Program& P, int p0, int in_b, long long in_o, int in
   return p;
 }
 
+int Hbs::emit_forward_sweep(Program& P, int p0, int in_b, long long in_o, int in_ld, int out_b, long long out_o,
+                            int out_ld) const {
+  constexpr int WS = 2;  // workspace base
+  if (L == 0) {
+    P.gemv(p0, lev[0].D.p, 2 * N, 2 * N, 2 * N, in_b, in_o, in_ld, out_b, out_o, out_ld, 1.0, 0.0);
+    return p0 + 1;
+  }
+  std::vector<long long> xh(L + 1), yh(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    xh[l] = P.ws_alloc(lev[l].koff.back());
+    yh[l] = P.ws_alloc(lev[l].koff.back());
+  }
+  {  // leaves: x^ = V* x, y = D x
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      P.gemv(p0, LV.Vt.p + LV.oVt[t], nd.k, n, nd.k, in_b, in_o + 2 * nd.lo, in_ld, WS, xh[l] + LV.koff[t], -1, 1.0,
+             0.0);
+      P.gemv(p0, LV.D.p + LV.oD[t], n, n, n, in_b, in_o + 2 * nd.lo, in_ld, out_b, out_o + 2 * nd.lo, out_ld, 1.0, 0.0);
+    }
+  }
+  for (int l = L - 1; l >= 0; --l) {  // up: x^_l = V* x^_{l+1}; siblings: y^ = B x^
+    const int p = p0 + (L - l), h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      if (l >= 1)
+        P.gemv(p, LV.Vt.p + LV.oVt[t], nd.k, nd.m, nd.k, WS, xh[l + 1] + LC.koff[2 * t], -1, WS, xh[l] + LV.koff[t], -1,
+               1.0, 0.0);
+      const HbsNode& a = node[2 * (h0 + t)];
+      const HbsNode& b = node[2 * (h0 + t) + 1];
+      const long long ia = LC.koff[2 * t], ib = LC.koff[2 * t + 1];
+      P.gemv(p, LV.B.p + LV.oB12[t], a.k, b.k, a.k, WS, xh[l + 1] + ib, -1, WS, yh[l + 1] + ia, -1, 1.0, 0.0);
+      P.gemv(p, LV.B.p + LV.oB21[t], b.k, a.k, b.k, WS, xh[l + 1] + ia, -1, WS, yh[l + 1] + ib, -1, 1.0, 0.0);
+    }
+  }
+  for (int l = 1; l <= L - 1; ++l) {  // down: y^_{l+1} += U y^_l
+    const int p = p0 + L + l, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    const Level& LC = lev[l + 1];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      P.gemv(p, LV.U.p + LV.oU[t], nd.m, nd.k, nd.m, WS, yh[l] + LV.koff[t], -1, WS, yh[l + 1] + LC.koff[2 * t], -1,
+             1.0, 1.0);
+    }
+  }
+  {  // leaves: y += U y^
+    const int l = L, h0 = 1 << l, nn = 1 << l;
+    const Level& LV = lev[l];
+    for (int t = 0; t < nn; ++t) {
+      const HbsNode& nd = node[h0 + t];
+      const int n = 2 * (nd.hi - nd.lo);
+      P.gemv(p0 + 2 * L, LV.U.p + LV.oU[t], n, nd.k, n, WS, yh[l] + LV.koff[t], -1, out_b, out_o + 2 * nd.lo, out_ld, 1.0,
+             1.0);
+    }
+  }
+  return p0 + 2 * L + 1;
+}
+
 void Hbs::apply_inverse_program(const double* b, double* x, int nrhs, cudaStream_t s) const {
   if (!inv_prog_built) {
     emit_inverse_sweep(inv_prog, 0, 0, 0, 2 * N, 1, 0, 2 * N);

@@ -166,6 +166,10 @@ class Hbs {
   // (input and output addressed as program vectors); returns the next phase.
   int emit_inverse_sweep(Program& P, int p0, int in_b, long long in_o, int in_ld, int out_b, long long out_o,
                          int out_ld) const;
+  // The same for the forward apply y = A x (V* up the tree, B across
+  // siblings, U down, leaf D blocks), phases p0 .. p0 + 2L.
+  int emit_forward_sweep(Program& P, int p0, int in_b, long long in_o, int in_ld, int out_b, long long out_o,
+                         int out_ld) const;
   // single-launch inverse sweep on a program built on first use (bases:
   // b, x, workspace); same result as apply_inverse
   void apply_inverse_program(const double* b, double* x, int nrhs, cudaStream_t s) const;

@@ -774,6 +774,55 @@ void Refinement::emit_solve(Program& P, int gb, long long g_off, int ldg, int tb
   P.copy(p, nkp, WS, yp, -1, n_to_p.p, tb, t_off, ldt, n_from_p.p);
 }
 
+void Refinement::emit_to_ext(Program& P, int gb, long long g_off, int ldg, int eb, long long e_off, int lde) const {
+  P.zero(0, 2 * No, eb, e_off, lde, nullptr);
+  P.copy(0, nkp, gb, g_off, ldg, n_from_p.p, eb, e_off + 2LL * No, lde, n_to_p.p);
+  P.copy(1, nko, gb, g_off, ldg, n_from_o.p, eb, e_off, lde, n_to_o.p);
+}
+
+void Refinement::emit_from_ext(Program& P, int eb, long long e_off, int lde, int tb, long long t_off, int ldt) const {
+  P.copy(0, nko, eb, e_off, lde, n_to_o.p, tb, t_off, ldt, n_from_o.p);
+  P.copy(0, nkp, eb, e_off + 2LL * No, lde, n_to_p.p, tb, t_off, ldt, n_from_p.p);
+}
+
+void Refinement::emit_ext_direct(Program& P, int vb, long long vo, int ldv, int yb, long long yo, int ldy) const {
+  const int WS = 2;
+  const long long vp = vo + 2LL * No, yp = yo + 2LL * No;
+  const int pa = wall->hbs.emit_inverse_sweep(P, 0, vb, vo, ldv, yb, yo, ldy);
+  const int pb = hpp.emit_inverse_sweep(P, 0, vb, vp, ldv, yb, yp, ldy);
+  int p = std::max(pa, pb);
+  if (k == 0) return;
+  // r = R y, z = W^{-1} r, y -= X z (Eq. wood)
+  const long long yc = P.ws_alloc(std::max(2LL * Nc, 1LL)), r = P.ws_alloc(k), z = P.ws_alloc(k);
+  if (Nc) {
+    P.copy(p++, 2 * Nc, yb, yo, ldy, dc.p, WS, yc, -1, nullptr);
+    if (kk) P.gemv(p, Rkc.p, kk, 2 * Nc, kk, WS, yc, -1, WS, r, -1, 1.0, 0.0);
+  }
+  if (kpk) P.gemv(p, Rpk.p, kpk, 2 * No, kpk, yb, yo, ldy, WS, r + kk, -1, 1.0, 0.0);
+  if (kk && Np) P.gemv(p + 1, Rkp.p, kk, 2 * Np, kk, yb, yp, ldy, WS, r, -1, 1.0, Nc ? 1.0 : 0.0);
+  p += 2;
+  P.gemv(p++, Winv.p, k, k, k, WS, r, -1, WS, z, -1, 1.0, 0.0);
+  if (kk) P.gemv(p, Xo.p, 2 * No, kk, 2 * No, WS, z, -1, yb, yo, ldy, -1.0, 1.0);
+  if (kpk) P.gemv(p, Xp.p, 2 * Np, kpk, 2 * Np, WS, z + kk, -1, yb, yp, ldy, -1.0, 1.0);
+}
+
+void Refinement::emit_ext_operator(Program& P, int xb, long long xo, int ldx, int yb, long long yo, int ldy) const {
+  const int WS = 2;
+  const long long xp = xo + 2LL * No, yp = yo + 2LL * No;
+  const int pw = wall->op().emit_forward_sweep(P, 0, xb, xo, ldx, yb, yo, ldy);
+  const int pp = hpp.emit_forward_sweep(P, 0, xb, xp, ldx, yb, yp, ldy);
+  if (k == 0) return;
+  // r = R x (phases 0-2), then y += L r once the sweeps are done
+  const long long xc = P.ws_alloc(std::max(2LL * Nc, 1LL)), r = P.ws_alloc(k);
+  if (Nc) P.copy(0, 2 * Nc, xb, xo, ldx, dc.p, WS, xc, -1, nullptr);
+  if (kpk) P.gemv(0, Rpk.p, kpk, 2 * No, kpk, xb, xo, ldx, WS, r + kk, -1, 1.0, 0.0);
+  if (kk && Nc) P.gemv(1, Rkc.p, kk, 2 * Nc, kk, WS, xc, -1, WS, r, -1, 1.0, 0.0);
+  if (kk && Np) P.gemv(2, Rkp.p, kk, 2 * Np, kk, xb, xp, ldx, WS, r, -1, 1.0, Nc ? 1.0 : 0.0);
+  const int q = std::max(3, std::max(pw, pp));
+  if (kk) P.gemv(q, Lo.p, 2 * No, kk, 2 * No, WS, r, -1, yb, yo, ldy, 1.0, 1.0);
+  if (kpk) P.gemv(q, Lp.p, 2 * Np, kpk, 2 * Np, WS, r + kk, -1, yb, yp, ldy, 1.0, 1.0);
+}
+
 void Refinement::build_solve_program(cudaStream_t s) {
   // bases: 0 = g (2Nn x nrhs), 1 = tau (2Nn x nrhs), 2 = workspace
   emit_solve(solve_prog, 0, 0, 2 * Nn, 1, 0, 2 * Nn);

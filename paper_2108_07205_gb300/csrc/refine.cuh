@@ -81,6 +81,15 @@ struct Refinement {
   // Append this refinement's direct solve to a program: g = base gb + g_off
   // (ld ldg), tau = base tb + t_off (ld ldt), temporaries in base 2.
   void emit_solve(Program& P, int gb, long long g_off, int ldg, int tb, long long t_off, int ldt) const;
+  // GEMV-program pieces of the batched iterative refinement, on ext-space
+  // vectors (the o part at offset off, the p part at off + 2No, leading
+  // dimension ld): g_n -> g_ext (zeros on I_c), the direct solve y =
+  // A_ext^{-1} v (Algorithm 1), the operator y = (A~ + L R) x with the wall's
+  // op_tol forward representation, and x_ext -> tau_n.  Workspace in base 2.
+  void emit_to_ext(Program& P, int gb, long long g_off, int ldg, int eb, long long e_off, int lde) const;
+  void emit_ext_direct(Program& P, int vb, long long vo, int ldv, int yb, long long yo, int ldy) const;
+  void emit_ext_operator(Program& P, int xb, long long xo, int ldx, int yb, long long yo, int ldy) const;
+  void emit_from_ext(Program& P, int eb, long long e_off, int lde, int tb, long long t_off, int ldt) const;
   // added (optional): the added nodes, 6 x N_p host array (x, y, nx, ny, w,
   // kappa) in window order; without it they are evaluated on the wall's curve
   void factor(const Wall& w, const std::vector<int>& panels, const std::vector<int>& levels, cudaStream_t s,

@@ -93,7 +93,7 @@ EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_build_nodes", "rw_hbs_save
            "rw_hbs_apply_inverse_noalloc",
            "rw_hbs_apply_forward", "rw_refine_factor", "rw_ref_stats_get", "rw_ref_nodes", "rw_apply_refined",
            "rw_stokeslet_data", "rw_pressure",
-           "rw_solve", "rw_batch_create", "rw_batch_rows", "rw_batch_autotune", "rw_batch_solve",
+           "rw_solve", "rw_batch_create", "rw_batch_rows", "rw_batch_autotune", "rw_batch_solve", "rw_batch_solve_ir",
            "rw_batch_free", "rw_server_create", "rw_server_submit", "rw_server_poll", "rw_server_wait",
            "rw_server_destroy", "rw_server_set_cache", "rw_server_stats", "rw_kernel_launches", "rw_profile", "rw_profile_read", "rw_ref_free", "rw_hbs_free", "rw_last_error"]
 
@@ -143,6 +143,8 @@ def load(build_if_missing=False):
     L.rw_batch_rows.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.rw_batch_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     L.rw_batch_solve.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_int, vp]
+    L.rw_batch_solve_ir.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int, vp,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.rw_batch_free.argtypes = [vp]
     L.rw_server_create.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(vp)]
     L.rw_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]
@@ -506,6 +508,15 @@ class Batch:
     def solve(self, g, tau, nrhs=1, use_graph=True, stream=None):
         _check(load().rw_batch_solve(self.h, nrhs, _ptr(g), _ptr(tau, True), 1 if use_graph else 0, _stream(stream)))
         return tau
+
+    def solve_ir(self, g, tau, nrhs=1, tol=1e-10, maxit=30, stream=None):
+        """Certified solve of the whole batch (rw_batch_solve_ir); returns
+        {"iters", "rel_residual"}."""
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        _check(load().rw_batch_solve_ir(self.h, nrhs, _ptr(g), _ptr(tau, True), tol, maxit, _stream(stream),
+                                        ctypes.byref(it), ctypes.byref(rr)))
+        return {"iters": it.value, "rel_residual": rr.value}
 
     def close(self):
         if getattr(self, "h", None):
