@@ -319,6 +319,9 @@ TreeId tree_row_id_w(const NodesView& S, const std::vector<int>& rows, const IdM
     const int x = std::atoi(e);
     if (x >= 16 && x <= 1024) chunk = x;
   }
+  // a block of at most two chunks is one problem: a second level would add a
+  // whole chain of pivot steps for no reduction in work
+  if (mt <= 2 * chunk) chunk = mt;
   for (int r0 = 0; r0 < mt; r0 += chunk) {
     TJob j;
     for (int r = r0; r < std::min(mt, r0 + chunk); ++r) j.cand.push_back(r);
