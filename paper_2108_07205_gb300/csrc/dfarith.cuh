@@ -43,10 +43,14 @@ __device__ __forceinline__ void df_split(double v, float& h, float& l) {
 // part's FP64 units run at 1/64 of its FP32 rate, so a conversion and a
 // subtraction in FP64 per staged entry would cost as much as the products):
 // hi = v with its significand truncated to 24 bits, lo = the remaining 29
-// bits truncated to 24, so |v - hi - lo| <= 2^-47 |v|.  Zero, and values
-// whose pieces would leave FP32's normal range, take the FP64 route.
+// bits truncated to 24, so |v - hi - lo| <= 2^-47 |v|.  Values whose
+// pieces would leave FP32's normal range take the FP64 route.
 __device__ __forceinline__ void df_split_bits(double v, float& h, float& l) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  if ((b << 1) == 0ull) {  // +-0 (padding): no FP64 work
+    h = l = 0.f;
+    return;
+  }
   const int e = int((b >> 52) & 0x7FF);
   if (e < 950 || e > 1150) {
     df_split(v, h, l);
