@@ -876,8 +876,10 @@ __host__ __device__ inline size_t cpqr_cluster_smem(int nr, int cw, int nt) {
 // columns carry a negative value.
 __device__ __forceinline__ void cpqr_update_columns(double* Wl, int ld, int nr, int ncl, int ncl_pad, int G, int s,
                                                     double tau, const double* vloc, double* nrm, double* nrm0,
-                                                    double tol3z) {
+                                                    double tol3z, double& lv, int& li, int c0) {
   const int tid = threadIdx.x, nt = blockDim.x, gl = tid & (G - 1);
+  lv = -1.0;
+  li = 0x7fffffff;
   for (int j = tid / G; j < ncl_pad; j += nt / G) {
     const bool live = j < ncl && nrm[j] >= 0.0;
     double* cj = Wl + size_t(live ? j : 0) * ld;
@@ -909,6 +911,9 @@ __device__ __forceinline__ void cpqr_update_columns(double* Wl, int ld, int nr, 
     if (live && gl == 0) {
       if (tau != 0.0) cj[s] -= dd;
       if (recompute) { nrm[j] = q; nrm0[j] = q; }
+      // this thread's next-pivot candidate (its columns in increasing order)
+      const double nj = nrm[j];
+      if (nj > lv) { lv = nj; li = c0 + j; }
     }
   }
 }
@@ -1048,6 +1053,17 @@ __global__ void __launch_bounds__(kCpqrThreads) k_cpqr_cluster(const IdProb* pro
           for (int i = s + 1 + lane; i < nr; i += 32) vloc[i] *= sc;
         }
         if (lane == 0) { g_tau = tau; g_beta = beta; }
+        if (bi >= c0 && bi < c1) {
+          // the pivot column becomes R's column s over the reflector, and
+          // leaves the candidates
+          double* col = Wl + size_t(bi - c0) * ld;
+          for (int i = s + 1 + lane; i < nr; i += 32) col[i] = vloc[i];
+          if (lane == 0) {
+            col[s] = beta;
+            nrm[bi - c0] = -1.0;
+          }
+        }
+        if (lane == 0 && lr == 0) P.piv[s] = bi;
       }
       if (lane == 0) { g_val = bv; g_val_o = ov_o; g_idx = stop ? -1 : bi; }
     }
@@ -1060,28 +1076,15 @@ __global__ void __launch_bounds__(kCpqrThreads) k_cpqr_cluster(const IdProb* pro
     const bool hard_o = done_o || it >= maxsteps_o || vmax_o <= 0.0;
     done = hard;
     done_o = hard_o;
+    (void)pg;
     if (!done) {
-      const double tau = g_tau;
-      if (lr == 0 && tid == 0) P.piv[s] = pg;
-      if (pg >= c0 && pg < c1) {
-        // the pivot column becomes R's column s over the reflector
-        const int jl = pg - c0;
-        double* col = Wl + size_t(jl) * ld;
-        for (int i = s + 1 + tid; i < nr; i += nt) col[i] = vloc[i];
-        if (tid == 0) {
-          col[s] = g_beta;
-          nrm[jl] = -1.0;  // done
-        }
-      }
-      __syncthreads();
-      cpqr_update_columns(Wl, ld, nr, ncl, ncl_pad, G, s, tau, vloc, nrm, nrm0, tol3z);
+      // the update finds each thread's next candidate; the next step's
+      // block reduction (its barriers) orders it before the publication
+      cpqr_update_columns(Wl, ld, nr, ncl, ncl_pad, G, s, g_tau, vloc, nrm, nrm0, tol3z, lv, li, c0);
       ++s;
-      __syncthreads();
-      lv = -1.0;
-      li = 0x7fffffff;
-      for (int j = tid; j < ncl; j += nt) if (nrm[j] > lv) { lv = nrm[j]; li = c0 + j; }
     }
   }
+  __syncthreads();
   for (int e = tid; e < nr * ncl; e += nt) {
     const int i = e % nr, j = e / nr;
     P.W[i + size_t(c0 + j) * P.ldw] = Wl[i + size_t(j) * ld];
@@ -1257,7 +1260,9 @@ __global__ void __launch_bounds__(256) k_cpqr_grid(const IdProb* probs, int base
         if (tid == 0) { cp[s] = beta; nrm[jl] = -1.0; }
         __syncthreads();
       }
-      cpqr_update_columns(Wl, nr, nr, ncl, ncl_pad, G2, s, tau, vloc, nrm, nrm0, tol3z);
+      double lv_unused;
+      int li_unused;
+      cpqr_update_columns(Wl, nr, nr, ncl, ncl_pad, G2, s, tau, vloc, nrm, nrm0, tol3z, lv_unused, li_unused, 0);
     }
     __syncthreads();
     if (tid < np && s_act[tid]) s_s[tid] += 1;
