@@ -21,6 +21,8 @@ Modules
   dense       dense solve of the refined system; ELS and Woodbury (Sec. 3.2-3.4).
   holes       the wall with added holes (App. B): combined-field operator of
               Eq. exterior_BIE on the holes with a graded singular rule.
+  exterior    the exterior problem on one wall (Sec. 2.2, Eq. exterior_BIE),
+              reference and locally refined, with the same graded rule.
 
 Parity status of each function is stated in its module docstring; every
 function here is pinned by ``tests/test_oracle_*.py`` against closed forms,

@@ -22,6 +22,10 @@ Workload recipes (the paper's geometries are not available, Sec. 5):
   angles 2 pi i / 3 + U[0, 0.4].  Stokeslets inside a hole sit within 0.4 R
   of its centre; fluid targets are the wall's targets with those closer
   than 2 R to a hole centre redrawn.
+* exterior star (Sec. 2.2, Fig. demo_figs (b): the fluid outside the star
+  wall): 3 Stokeslets inside the curve at radius U[0, 0.4] with angles
+  U[0, 2 pi) and strengths N(0, I2); targets in the fluid at radius
+  U[2, 3].
 """
 import numpy as np
 
@@ -91,6 +95,24 @@ def stokeslet_pairs_channel(seed, nrhs):
 def targets_star(seed, n=16):
     g = rng(seed)
     r = g.uniform(0.0, 0.5, size=n)
+    th = g.uniform(0.0, 2.0 * np.pi, size=n)
+    return r * np.cos(th), r * np.sin(th)
+
+
+def stokeslets_inside_star(seed, nrhs=1, n=3, rmax=0.4):
+    """Point forces inside the star wall (the exterior problem's data):
+    positions (n,), (n,) and strengths (n, 2, nrhs)."""
+    g = rng(seed)
+    r = g.uniform(0.0, rmax, size=n)
+    th = g.uniform(0.0, 2.0 * np.pi, size=n)
+    f = g.standard_normal(size=(n, 2, nrhs))
+    return r * np.cos(th), r * np.sin(th), f
+
+
+def targets_outside_star(seed, n=16, r_lo=2.0, r_hi=3.0):
+    """Targets in the fluid outside the star wall."""
+    g = rng(seed)
+    r = g.uniform(r_lo, r_hi, size=n)
     th = g.uniform(0.0, 2.0 * np.pi, size=n)
     return r * np.cos(th), r * np.sin(th)
 

@@ -1,0 +1,106 @@
+"""Pins for oracle/exterior.py: the exterior Stokes problem on one wall
+(Sec. 2.2, Eq. exterior_BIE), reference and locally refined.
+
+* Closed form.  For data made by Stokeslets inside the curve, the combined
+  field of the solved density equals the Stokeslet field at points of the
+  fluid.  The decay is spectral under panel refinement.  This holds on the
+  reference star and on refined stars, where fine panels sit next to coarse
+  ones.
+* Total force.  The density's total force sum_j w_j tau_j equals the
+  Stokeslets' total force.
+* On one equal-panel curve the matrix equals oracle/holes.py's hole matrix,
+  which the Fourier closed forms pin.
+* The refined order of the panels is the interior wall's (discretize.refine).
+* Planted mistakes break the closed form: the interior jump -1/2, the plain
+  rule on the log singularity, and a sign flip of the single layer.
+"""
+import numpy as np
+import pytest
+
+from oracle import exterior as X, holes as H, discretize as D
+from paper_2108_07205_gb300 import inputs as I
+
+STAR = dict(a=0.3, k=5)
+
+
+def _field_error(P, cut=(), levels=(), seed=3):
+    a, b = X.panels(P, cut, levels)
+    nd = X.nodes("star", STAR, a, b)
+    sx, sy, f = I.stokeslets_inside_star(seed, nrhs=2)
+    from oracle import stokes as S
+    g = S.boundary_data(nd, sx, sy, f)
+    tau = X.solve("star", STAR, nd, g)
+    tx, ty = I.targets_outside_star(seed + 1, n=12)
+    u = X.velocity(nd, tau, tx, ty)
+    ue = S.stokeslet_velocity(tx, ty, sx, sy, f)
+    return np.abs(u - ue).max() / np.abs(ue).max(), nd, tau, f
+
+
+def test_closed_form_and_spectral_decay():
+    errs = [_field_error(P)[0] for P in (12, 16, 24)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-12
+    assert errs[0] > 1e-9   # the coarse mesh is visibly under-resolved: the pin has teeth
+
+
+@pytest.mark.parametrize("cut,levels", [((5, 6, 7), (3, 3, 3)), ((23, 0, 1), (2, 4, 3))])
+def test_closed_form_refined(cut, levels):
+    err = _field_error(24, cut, levels)[0]
+    assert err < 1e-11
+
+
+def test_total_force_identity():
+    _, nd, tau, f = _field_error(24, (2, 3), (3, 3))
+    F = X.total_force(nd, tau)
+    Fs = f.sum(axis=0)
+    assert np.abs(F - Fs).max() < 1e-11 * np.abs(Fs).max()
+
+
+def test_matches_pinned_hole_matrix():
+    P = 12
+    a, b = X.panels(P)
+    nd = X.nodes("star", STAR, a, b)
+    A = X.matrix("star", STAR, nd)
+    hl = [dict(cx=0.0, cy=0.0, R=1.0, a=STAR["a"], k=STAR["k"], P=P)]
+    hn = H.hole_nodes(hl)
+    assert np.abs(hn["x"] - nd["x"]).max() < 1e-14
+    Ah = H.hole_matrix(hn, hl, 0.5)
+    assert np.abs(A - Ah).max() < 1e-13 * np.abs(Ah).max()
+
+
+def test_refined_order_is_the_interior_walls():
+    P, cut, levels = 16, (15, 0, 1), (2, 3, 2)
+    a, b = X.panels(P, cut, levels)
+    nd = X.nodes("star", STAR, a, b)
+    ref = D.refine("star", STAR, P, list(cut), list(levels))
+    for key in ("x", "y", "w", "nx", "ny", "kappa"):
+        assert np.abs(nd[key] - ref["n"][key]).max() < 1e-13
+
+
+def test_near_panels_cover_the_refinement_boundary():
+    # the coarse nodes closest to a fine run take the graded rule on the fine
+    # panel beside them, and every fine node of that run on the coarse panel
+    P, cut, levels = 16, (4,), (4,)
+    a, b = X.panels(P, cut, levels)
+    nd = X.nodes("star", STAR, a, b)
+    coarse_left, fine_first = 3, 4
+    for i in range(16 * coarse_left + 13, 16 * (coarse_left + 1)):
+        assert fine_first in X.near_panels(nd, i)
+    assert fine_first not in X.near_panels(nd, 16 * coarse_left)
+    for i in range(16 * fine_first, 16 * (fine_first + 16)):
+        assert coarse_left in X.near_panels(nd, i)
+
+
+def test_planted_mistakes_break_the_closed_form(monkeypatch):
+    base = _field_error(24)[0]
+    assert base < 1e-12
+    with monkeypatch.context() as m:
+        m.setattr(X, "JUMP", -0.5)
+        assert _field_error(24)[0] > 1e-3
+    with monkeypatch.context() as m:
+        m.setattr(X, "NEAR_LOC", 0.0)
+        assert _field_error(24)[0] > 1e-6
+    with monkeypatch.context() as m:
+        sl = X.single_layer_matrix
+        m.setattr(X, "single_layer_matrix", lambda *a: -sl(*a))
+        assert _field_error(24)[0] > 1e-3
