@@ -158,6 +158,24 @@ int rw_default_opts(rw_opts* o);
 int rw_hbs_build(const rw_wall_desc* wall, const rw_opts* opts, void* stream,
                  rw_hbs_t* out);
 
+/* a0 for the exterior problem (Sec. 2.2, Fig. demo_figs (b)): the fluid
+ * fills the plane outside the closed curve (RW_CURVE_STAR or
+ * RW_CURVE_CHANNEL, n_panels >= 8 equal panels in t), the velocity is the
+ * combined field u = (D + S) tau and the density solves
+ * 1/2 tau + (D + S) tau = g (Eq. exterior_BIE; full rank, no N term).  The
+ * single layer's logarithm takes Legendre product integration (the
+ * generalised Gaussian corrections of Sec. 5, exact for the density's
+ * degree-15 interpolant on a panel, geometry exact) wherever a target lies
+ * within 3 half-widths (in t) of the source panel's midpoint; the plain
+ * panel rule elsewhere.  Every later call takes the handle as for an
+ * interior wall (Sec. 3 applies to exterior problems unchanged: the Remark
+ * closing Sec. 3.1): rw_refine_factor (nodes of the sub-panels evaluated on
+ * the curve; rw_refine_factor_nodes is refused), rw_solve in every mode,
+ * rw_apply_refined, velocity (D + S, plain rule: targets away from the
+ * curve), pressure, batches and the server.  rw_holes_factor and rw_hbs_save
+ * refuse an exterior wall with RW_ERR_INVALID. */
+int rw_hbs_build_exterior(const rw_wall_desc* wall, const rw_opts* opts, void* stream, rw_hbs_t* out);
+
 /* a0 for a wall given by its nodes (any geometry: the paper's spline
  * channel, fish or tube discretised elsewhere).  Checks n = 16 P >= 16,
  * finite values, positive weights and unit normals (|n| within 1e-8 of 1),

@@ -151,8 +151,22 @@ int rw_default_opts(rw_opts* o) {
   return RW_OK;
 }
 
+namespace {
+int build_curve_wall(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_hbs_t* out, bool exterior);
+}  // namespace
+
 int rw_hbs_build(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_hbs_t* out) {
-  if (!wd || !out) return fail(RW_ERR_INVALID, "rw_hbs_build: null argument");
+  return build_curve_wall(wd, opts, stream, out, false);
+}
+
+int rw_hbs_build_exterior(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_hbs_t* out) {
+  return build_curve_wall(wd, opts, stream, out, true);
+}
+
+namespace {
+int build_curve_wall(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_hbs_t* out, bool exterior) {
+  if (!wd || !out) return fail(RW_ERR_INVALID, exterior ? "rw_hbs_build_exterior: null argument"
+                                                         : "rw_hbs_build: null argument");
   *out = nullptr;
   std::unique_ptr<rw_hbs_s> h(new rw_hbs_s);
   int rc = guarded([&] {
@@ -185,11 +199,16 @@ int rw_hbs_build(const rw_wall_desc* wd, const rw_opts* opts, void* stream, rw_h
     auto all = w.nodes.buf.download(s);
     w.nodes.hx.assign(all.begin(), all.begin() + 16 * P);
     w.nodes.hy.assign(all.begin() + 16 * P, all.begin() + 32 * P);
+    if (exterior) {
+      rw::require(P >= 8, "exterior wall: at least 8 panels");
+      rw::set_exterior_panels(w.nodes, w.curve, ta, tb, s);
+    }
     w.build_hbs(s);
   });
   if (rc == RW_OK) *out = h.release();
   return rc;
 }
+}  // namespace
 
 int rw_hbs_build_nodes(const rw_nodes* nodes, const rw_opts* opts, void* stream, rw_hbs_t* out) {
   if (!nodes || !out) return fail(RW_ERR_INVALID, "rw_hbs_build_nodes: null argument");

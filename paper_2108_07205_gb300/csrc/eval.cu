@@ -106,6 +106,46 @@ __global__ void k_nodes(Curve c, const double* ta, const double* tb, int n_int, 
   out[i + 5 * size_t(ld)] = (g.dx * g.ddy - g.dy * g.ddx) / (sp * sp * sp);
 }
 
+// Moments M_n(t) = int_{-1}^{1} P_n(s) log|t - s| ds, n = 0..NM-1, of the
+// Legendre polynomials against the logarithm.  Integration by parts with
+// P_n = (P_{n+1}' - P_{n-1}') / (2n + 1) gives M_n = 2 (Q_{n+1}(t) -
+// Q_{n-1}(t)) / (2n + 1), where Q_m(t) = (1/2) int P_m(s) / (t - s) ds (a
+// principal value for |t| < 1) obeys the Legendre three-term recurrence from
+// Q_0 = (1/2) log|(1 + t) / (1 - t)|, Q_1 = t Q_0 - 1.  For |t| < 1 the
+// recurrence runs forward; for |t| > 1, where Q_m is the recurrence's
+// minimal solution, it runs backward from a start index past which the
+// neglected dominant part is below rounding (Miller's algorithm) and is
+// normalised by Q_0.  M_0 is the elementary integral.
+template <int NM>
+__device__ void log_moments(double t, double* M) {
+  double Q[NM + 1];
+  const double at = fabs(t);
+  if (at < 1.0) {
+    Q[0] = 0.5 * log((1.0 + t) / (1.0 - t));
+    Q[1] = t * Q[0] - 1.0;
+    for (int n = 1; n < NM; ++n) Q[n + 1] = ((2.0 * n + 1.0) * t * Q[n] - n * Q[n - 1]) / (n + 1.0);
+  } else {
+    const double rho = at + sqrt((at - 1.0) * (at + 1.0));
+    const int n0 = min(NM + 1 + int(ceil(40.0 / log(rho))), 20000);
+    double qn1 = 0.0, qn = 1.0;  // Q_{n+1}, Q_n up to a common factor
+    for (int n = n0; n >= 1; --n) {
+      const double qm = ((2.0 * n + 1.0) * t * qn - (n + 1.0) * qn1) / n;
+      qn1 = qn;
+      qn = qm;
+      if (n - 1 <= NM) Q[n - 1] = qn;
+      if (fabs(qn) > 1e200) {
+        qn *= 1e-200;
+        qn1 *= 1e-200;
+        for (int m = max(n - 1, 0); m <= NM; ++m) Q[m] *= 1e-200;
+      }
+    }
+    const double sc = 0.5 * log((t + 1.0) / (t - 1.0)) / Q[0];
+    for (int m = 0; m <= NM; ++m) Q[m] *= sc;
+  }
+  M[0] = (t + 1.0) * log(fabs(t + 1.0)) - (t - 1.0) * log(fabs(t - 1.0)) - 2.0;
+  for (int n = 1; n < NM; ++n) M[n] = 2.0 * (Q[n + 1] - Q[n - 1]) / (2.0 * n + 1.0);
+}
+
 // The 2 x 2 block of A between a target point t and a source point s
 // (A(t a, s b) for a, b in {0, 1}): one distance, one division.
 struct Blk2 { double v[2][2]; };
@@ -142,9 +182,141 @@ __device__ __forceinline__ Blk2 a_block(const NodesView& T, int t, const NodesVi
   return o;
 }
 
+// Entry of A = -1/2 I + D + N (Sec. 2, Remark 2.1) for row DOF (i, a) of node
+// set R and column DOF (j, b) of node set C.  same_set marks R == C, where
+// i == j gives the diagonal block -1/2 I - (kappa_i w_i / 2 pi) t t^T
+// + w_i n_i n_i^T (the smooth limit of the double layer on the curve).
+// With holes (App. B): a hole source (C.kind 1) contributes its combined
+// field w_j (D + S)(x_i, y_j) and a wall source seen at a hole point (R.kind
+// 1) its double layer w_j D(x_i, y_j), neither with the N term.  Pairs on
+// one hole are not evaluated here (their single layer needs the singular
+// rule of the hole matrix).
+__device__ __forceinline__ double a_entry(const NodesView& R, int i, int a,
+                                          const NodesView& C, int j, int b,
+                                          bool same_set) {
+  const double wj = C.w[j];
+  if (C.kind | R.kind) {
+    const double rx = R.x[i] - C.x[j], ry = R.y[i] - C.y[j];
+    const double r2 = rx * rx + ry * ry, inv = 1.0 / r2;
+    const double ra = a ? ry : rx, rb = b ? ry : rx;
+    double val = wj * (rx * C.nx[j] + ry * C.ny[j]) * inv * inv * (1.0 / kPi) * ra * rb;
+    if (C.kind) val += wj * (0.25 / kPi) * ((a == b ? -0.5 * log(r2) : 0.0) + ra * rb * inv);
+    return val;
+  }
+  const double nia = a ? R.ny[i] : R.nx[i];
+  const double njb = b ? C.ny[j] : C.nx[j];
+  double val = nia * njb * wj;
+  if (same_set && i == j) {
+    const double ta = a ? R.nx[i] : -R.ny[i];
+    const double tb = b ? R.nx[i] : -R.ny[i];
+    val -= R.kappa[i] * wj * (0.5 / kPi) * ta * tb;
+    if (a == b) val -= 0.5;
+  } else {
+    const double rx = R.x[i] - C.x[j], ry = R.y[i] - C.y[j];
+    const double r2 = rx * rx + ry * ry;
+    const double rdn = rx * C.nx[j] + ry * C.ny[j];
+    const double fac = wj * rdn / (kPi * r2 * r2);
+    val += fac * (a ? ry : rx) * (b ? ry : rx);
+  }
+  return val;
+}
+
+// Single layer of one exterior-wall pair (Sec. 2.2) whose target x_i sits
+// within kExtNear half-widths of the source's panel (midpoint tm, half-width
+// th in t, local coordinate loc of the target; source node q of the panel):
+// the density's degree-15 interpolant on the panel against the exact kernel,
+// with the geometry exact -- Legendre product integration of the logarithm
+// (generalised Gaussian corrections in the sense of Sec. 5, exact for the
+// interpolant) on a 32-point auxiliary rule (u_f, nu_f):
+//   int log|x_i - y(s)| l_q(s) |y'(s)| th ds
+//     ~ th sum_f [Lam_f(loc) + nu_f phi(u_f)] |y'(u_f)| l_q(u_f),
+//   Lam_f(loc) = nu_f sum_{n<32} (2n+1)/2 P_n(u_f) M_n(loc),
+//   phi(s) = log|x_i - y(s)| - log|loc - s|  (smooth),
+// and r r^T / |r|^2 by the auxiliary rule alone (it is smooth along the
+// curve).  out = w_j S(x_i, y_j) entries (xx, xy, yy).
+__device__ __noinline__ void ext_near_sl(double xi, double yi, double loc, const Curve& c, double tm, double th,
+                                         int q, double* out) {
+  double M[kAux];
+  log_moments<kAux>(loc, M);
+  double sl = 0.0, sxx = 0.0, sxy = 0.0, syy = 0.0;
+  for (int f = 0; f < kAux; ++f) {
+    const double u = c_ux[f];
+    double p0 = 1.0, p1 = u, acc = 0.5 * M[0] + 1.5 * u * M[1];
+    for (int n = 1; n < kAux - 1; ++n) {
+      const double p2 = ((2.0 * n + 1.0) * u * p1 - n * p0) / (n + 1.0);
+      p0 = p1;
+      p1 = p2;
+      acc += (n + 1.5) * p2 * M[n + 1];
+    }
+    const Pt g = curve_eval(c, tm + th * u);
+    const double gl = sqrt(g.dx * g.dx + g.dy * g.dy) * c_lag[f][q];
+    const double rx = xi - g.x, ry = yi - g.y, r2 = rx * rx + ry * ry;
+    const double phi = 0.5 * log(r2) - log(fabs(loc - u));
+    sl += c_uw[f] * (acc + phi) * gl;
+    const double wg = c_uw[f] * gl / r2;
+    sxx += wg * rx * rx;
+    sxy += wg * rx * ry;
+    syy += wg * ry * ry;
+  }
+  const double c4 = 0.25 / kPi;
+  out[0] = c4 * th * (sxx - sl);
+  out[1] = c4 * th * sxy;
+  out[2] = c4 * th * (syy - sl);
+}
+
+// The 2 x 2 block of 1/2 I + D + S (Eq. exterior_BIE) between a target t and
+// a source s of exterior-wall node sets (same_point: t and s are one node).
+// The double layer takes the plain panel rule with the curvature limit at
+// the same point; the single layer the plain rule, or ext_near_sl where the
+// target is near the source's panel.
+__device__ Blk2 a_block_ext(const NodesView& T, int t, const NodesView& Sv, int s, bool same_point) {
+  Blk2 o;
+  const double ws = Sv.w[s];
+  const double rx = T.x[t] - Sv.x[s], ry = T.y[t] - Sv.y[s];
+  const double r[2] = {rx, ry};
+  if (same_point) {
+    const double ta[2] = {-T.ny[t], T.nx[t]};
+    const double kap = -T.kappa[t] * ws * (0.5 / kPi);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) o.v[a][b] = kap * ta[a] * ta[b] + (a == b ? 0.5 : 0.0);
+  } else {
+    const double inv = 1.0 / (rx * rx + ry * ry);
+    const double fac = ws * (rx * Sv.nx[s] + ry * Sv.ny[s]) * inv * inv * (1.0 / kPi);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) o.v[a][b] = fac * r[a] * r[b];
+  }
+  const double loc = ext_loc(T.t[t], Sv.tm[s], Sv.th[s]);
+  if (fabs(loc) < kExtNear) {
+    double sl[3];
+    ext_near_sl(T.x[t], T.y[t], same_point ? c_glx[s & 15] : loc, Sv.curve, Sv.tm[s], Sv.th[s], s & 15, sl);
+    o.v[0][0] += sl[0];
+    o.v[0][1] += sl[1];
+    o.v[1][0] += sl[1];
+    o.v[1][1] += sl[2];
+  } else {
+    const double r2 = rx * rx + ry * ry, inv = 1.0 / r2, lg = -0.5 * log(r2), c = ws * (0.25 / kPi);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) o.v[a][b] += c * ((a == b ? lg : 0.0) + r[a] * r[b] * inv);
+  }
+  return o;
+}
+
+template <bool EXT>
+__device__ __forceinline__ Blk2 block_of(const NodesView& T, int t, const NodesView& Sv, int s, bool same_point) {
+  if constexpr (EXT) return a_block_ext(T, t, Sv, s, same_point);
+  else return a_block(T, t, Sv, s, same_point);
+}
+template <bool EXT>
+__device__ __forceinline__ double entry_of(const NodesView& R, int i, int a, const NodesView& C, int j, int b,
+                                           bool same_set) {
+  if constexpr (EXT) return a_block_ext(R, i, C, j, same_set && i == j).v[a][b];
+  else return a_entry(R, i, a, C, j, b, same_set);
+}
+
 // Feature list section (entries of A against the DOFs e[0..n)): pairs of
 // consecutive entries that are the two components of one point share one
 // 2 x 2 block evaluation.
+template <bool EXT>
 __device__ __forceinline__ void idmat_section(const IdMatProb& P, double* Wc, int ip, int ia, const NodesView& S,
                                               const int* e, int n, const NodesView& E, bool es) {
   for (int cp = threadIdx.x; 2 * cp < n; cp += blockDim.x) {
@@ -155,18 +327,19 @@ __device__ __forceinline__ void idmat_section(const IdMatProb& P, double* Wc, in
       const int j = e0 >> 1;
       const bool same = es && j == ip;
       if (P.kind == 0) {
-        const Blk2 B = a_block(S, ip, E, j, same);
+        const Blk2 B = block_of<EXT>(S, ip, E, j, same);
         Wc[c] = B.v[ia][0];
         Wc[c + 1] = B.v[ia][1];
       } else {
-        const Blk2 B = a_block(E, j, S, ip, same);
+        const Blk2 B = block_of<EXT>(E, j, S, ip, same);
         Wc[c] = B.v[0][ia];
         Wc[c + 1] = B.v[1][ia];
       }
     } else {
       for (int q = c; q < min(n, c + 2); ++q) {
         const int eq = e[q];
-        Wc[q] = P.kind == 0 ? a_entry(S, ip, ia, E, eq >> 1, eq & 1, es) : a_entry(E, eq >> 1, eq & 1, S, ip, ia, es);
+        Wc[q] = P.kind == 0 ? entry_of<EXT>(S, ip, ia, E, eq >> 1, eq & 1, es)
+                            : entry_of<EXT>(E, eq >> 1, eq & 1, S, ip, ia, es);
       }
     }
   }
@@ -176,6 +349,7 @@ __device__ __forceinline__ void idmat_section(const IdMatProb& P, double* Wc, in
 // near-field sections, then the proxy section (points tabulated once per
 // block; one distance, one division and at most one logarithm per proxy
 // point), then the normal column.
+template <bool EXT>
 __global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesView E1, bool e1s, NodesView E2,
                         bool e2s) {
   const IdMatProb P = probs[blockIdx.y];
@@ -203,8 +377,8 @@ __global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesVie
     double* Wc = P.W + size_t(i) * P.ldw;
     const int d = P.cand[i];
     const int ip = d >> 1, ia = d & 1;
-    idmat_section(P, Wc, ip, ia, S, P.e1, P.n1, E1, e1s);
-    idmat_section(P, Wc + P.n1, ip, ia, S, P.e2, P.n2, E2, e2s);
+    idmat_section<EXT>(P, Wc, ip, ia, S, P.e1, P.n1, E1, e1s);
+    idmat_section<EXT>(P, Wc + P.n1, ip, ia, S, P.e2, P.n2, E2, e2s);
     const double xi = S.x[ip], yi = S.y[ip];
     if (P.kind == 0) {
       // field at x_i of unit sources at z_q: Stokeslet (columns 4q, 4q+1)
@@ -228,6 +402,12 @@ __global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesVie
         const double fac = wi * (rx * nxi + ry * nyi) * inv * inv * (1.0 / kPi) * (ia ? ry : rx);
         Wc[base + 2 * q] = fac * rx;
         Wc[base + 2 * q + 1] = fac * ry;
+        if (EXT && P.sl_in) {
+          // single layer of the combined field: w_i S(z_q, x_i) e_ia
+          const double c = wi * (0.25 / kPi), lg = -0.5 * log(rx * rx + ry * ry), ra = ia ? ry : rx;
+          Wc[base + 2 * M + 2 * q] = c * ((ia == 0 ? lg : 0.0) + rx * ra * inv);
+          Wc[base + 2 * M + 2 * q + 1] = c * ((ia == 1 ? lg : 0.0) + ry * ra * inv);
+        }
       }
     }
     if (P.normal && threadIdx.x == 0) {
@@ -237,6 +417,7 @@ __global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesVie
   }
 }
 
+template <bool EXT>
 __global__ void k_blocks(const BlockProb* probs, NodesView s0, NodesView s1) {
   const BlockProb P = probs[blockIdx.y];
   const NodesView& R = P.rset ? s1 : s0;
@@ -246,7 +427,7 @@ __global__ void k_blocks(const BlockProb* probs, NodesView s0, NodesView s1) {
     const int dc = P.cols ? P.cols[c] : P.c0 + c;
     for (int r = threadIdx.x; r < P.mr; r += blockDim.x) {
       const int dr = P.rows ? P.rows[r] : P.r0 + r;
-      P.out[r + size_t(c) * P.ld] = P.scale * a_entry(R, dr >> 1, dr & 1, C, dc >> 1, dc & 1, same);
+      P.out[r + size_t(c) * P.ld] = P.scale * entry_of<EXT>(R, dr >> 1, dr & 1, C, dc >> 1, dc & 1, same);
     }
   }
 }
@@ -536,46 +717,6 @@ __global__ void __launch_bounds__(128) k_apply_cross(NodesView T, NodesView Sv, 
   }
 }
 
-// Moments M_n(t) = int_{-1}^{1} P_n(s) log|t - s| ds, n = 0..NM-1, of the
-// Legendre polynomials against the logarithm.  Integration by parts with
-// P_n = (P_{n+1}' - P_{n-1}') / (2n + 1) gives M_n = 2 (Q_{n+1}(t) -
-// Q_{n-1}(t)) / (2n + 1), where Q_m(t) = (1/2) int P_m(s) / (t - s) ds (a
-// principal value for |t| < 1) obeys the Legendre three-term recurrence from
-// Q_0 = (1/2) log|(1 + t) / (1 - t)|, Q_1 = t Q_0 - 1.  For |t| < 1 the
-// recurrence runs forward; for |t| > 1, where Q_m is the recurrence's
-// minimal solution, it runs backward from a start index past which the
-// neglected dominant part is below rounding (Miller's algorithm) and is
-// normalised by Q_0.  M_0 is the elementary integral.
-template <int NM>
-__device__ void log_moments(double t, double* M) {
-  double Q[NM + 1];
-  const double at = fabs(t);
-  if (at < 1.0) {
-    Q[0] = 0.5 * log((1.0 + t) / (1.0 - t));
-    Q[1] = t * Q[0] - 1.0;
-    for (int n = 1; n < NM; ++n) Q[n + 1] = ((2.0 * n + 1.0) * t * Q[n] - n * Q[n - 1]) / (n + 1.0);
-  } else {
-    const double rho = at + sqrt((at - 1.0) * (at + 1.0));
-    const int n0 = min(NM + 1 + int(ceil(40.0 / log(rho))), 20000);
-    double qn1 = 0.0, qn = 1.0;  // Q_{n+1}, Q_n up to a common factor
-    for (int n = n0; n >= 1; --n) {
-      const double qm = ((2.0 * n + 1.0) * t * qn - (n + 1.0) * qn1) / n;
-      qn1 = qn;
-      qn = qm;
-      if (n - 1 <= NM) Q[n - 1] = qn;
-      if (fabs(qn) > 1e200) {
-        qn *= 1e-200;
-        qn1 *= 1e-200;
-        for (int m = max(n - 1, 0); m <= NM; ++m) Q[m] *= 1e-200;
-      }
-    }
-    const double sc = 0.5 * log((t + 1.0) / (t - 1.0)) / Q[0];
-    for (int m = 0; m <= NM; ++m) Q[m] *= sc;
-  }
-  M[0] = (t + 1.0) * log(fabs(t + 1.0)) - (t - 1.0) * log(fabs(t - 1.0)) - 2.0;
-  for (int n = 1; n < NM; ++n) M[n] = 2.0 * (Q[n + 1] - Q[n - 1]) / (2.0 * n + 1.0);
-}
-
 // Dense A_pp = 1/2 I + D + S on the holes (App. B; Eq. exterior_BIE), column
 // major, ld = 2 N_p.  One CTA per target point i.  The double layer is
 // smooth along a hole: plain panel rule with the curvature limit on the
@@ -742,6 +883,49 @@ void eval_nodes(const Curve& c, const double* ta, const double* tb, int n_int, d
   RW_CHECK_LAUNCH();
 }
 
+void set_exterior_panels(Nodes& nd, const Curve& c, const std::vector<double>& ta, const std::vector<double>& tb,
+                         cudaStream_t s) {
+  require(ta.size() == tb.size() && nd.n == 16 * int(ta.size()), "exterior nodes: 16 nodes per panel");
+  double x[16], w[16];
+  gauss_legendre16(x, w);
+  const int n = nd.n;
+  nd.ht.resize(n);
+  nd.htm.resize(n);
+  nd.hth.resize(n);
+  std::vector<double> h(size_t(3) * n);
+  for (size_t p = 0; p < ta.size(); ++p) {
+    const double tm = 0.5 * (ta[p] + tb[p]), th = 0.5 * (tb[p] - ta[p]);
+    require(th > 0.0, "exterior nodes: empty panel");
+    for (int q = 0; q < 16; ++q) {
+      const size_t i = 16 * p + q;
+      nd.ht[i] = tm + th * x[q];
+      nd.htm[i] = tm;
+      nd.hth[i] = th;
+      h[i] = nd.ht[i];
+      h[n + i] = tm;
+      h[2 * size_t(n) + i] = th;
+    }
+  }
+  nd.pbuf.alloc(h.size());
+  RW_CUDA(cudaMemcpyAsync(nd.pbuf.p, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  RW_CUDA(cudaStreamSynchronize(s));
+  nd.kind = kNodesExterior;
+  nd.curve = c;
+}
+
+std::vector<std::vector<int>> ext_panel_neighbours(const Nodes& nd) {
+  require(nd.kind == kNodesExterior && int(nd.htm.size()) == nd.n, "ext_panel_neighbours: not an exterior node set");
+  const int np = nd.n / 16;
+  std::vector<std::vector<int>> nb(np);
+  for (int a = 0; a < np; ++a)
+    for (int b = a + 1; b < np; ++b)
+      if (ext_panels_interact(nd.htm[16 * a], nd.hth[16 * a], nd.htm[16 * b], nd.hth[16 * b])) {
+        nb[a].push_back(b);
+        nb[b].push_back(a);
+      }
+  return nb;
+}
+
 void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S, const NodesView& E1, bool e1_same,
                 const NodesView& E2, bool e2_same, cudaStream_t s) {
   if (probs.empty()) return;
@@ -757,7 +941,18 @@ void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S, const N
   auto d = to_device_tmp(probs, s);
   dim3 grid(std::min(grid1(mx), 1024), int(probs.size()));
   ProfScope prof_(KC_EVAL, s);
-  k_idmat<<<grid, 256, 4 * size_t(max_M) * sizeof(double), s>>>(d.p, max_M, S, E1, e1_same, E2, e2_same);
+  const bool ext = S.kind == kNodesExterior;
+  for (auto& p : probs) {
+    require(!ext || ((p.n1 == 0 || E1.kind == kNodesExterior) && (p.n2 == 0 || E2.kind == kNodesExterior)),
+            "eval_idmat: exterior candidates need exterior near sets");
+    require(!p.sl_in || (ext && p.kind == 1), "eval_idmat: sl_in is for incoming exterior problems");
+  }
+  if (ext) {
+    ensure_gl();
+    k_idmat<true><<<grid, 256, 4 * size_t(max_M) * sizeof(double), s>>>(d.p, max_M, S, E1, e1_same, E2, e2_same);
+  } else {
+    k_idmat<false><<<grid, 256, 4 * size_t(max_M) * sizeof(double), s>>>(d.p, max_M, S, E1, e1_same, E2, e2_same);
+  }
   RW_CHECK_LAUNCH();
 }
 
@@ -770,7 +965,14 @@ void eval_blocks(const std::vector<BlockProb>& probs, const NodesView& set0, con
   auto d = to_device_tmp(ps, s);
   dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
   ProfScope prof_(KC_EVAL, s);
-  k_blocks<<<grid, 256, 0, s>>>(d.p, set0, set1);
+  const bool ext = set0.kind == kNodesExterior;
+  require(ext == (set1.kind == kNodesExterior), "eval_blocks: exterior and other node sets mixed");
+  if (ext) {
+    ensure_gl();
+    k_blocks<true><<<grid, 256, 0, s>>>(d.p, set0, set1);
+  } else {
+    k_blocks<false><<<grid, 256, 0, s>>>(d.p, set0, set1);
+  }
   RW_CHECK_LAUNCH();
 }
 

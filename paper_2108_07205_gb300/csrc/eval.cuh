@@ -3,15 +3,10 @@
 // matrices whose interpolative decompositions give the HBS bases and the
 // low-rank factors of Q.
 #pragma once
+#include <cmath>
 #include "rw_common.cuh"
 
 namespace rw {
-
-// Curve description on the device (RW_CURVE_* and its parameters).
-struct Curve {
-  int kind;
-  double p[8];
-};
 
 // Gauss-Legendre nodes/weights of the 16-point rule on [-1, 1] (host table,
 // Newton iteration on the Legendre recurrence).
@@ -23,6 +18,34 @@ void gauss_legendre_n(int n, double* x, double* w);
 void eval_nodes(const Curve& c, const double* ta, const double* tb, int n_int,
                 double* out, int ld, cudaStream_t s);
 
+// Exterior walls (node sets of kind kNodesExterior; Sec. 2.2).  A target at
+// parameter t takes the singular rule of the single layer against a source
+// panel with midpoint tm and half-width th (in t) when the periodic distance
+// |t - tm| is below kExtNear th; the plain panel rule is then accurate to
+// (3 + sqrt 8)^-32 relative.  Node sets of this kind are panel aligned: the
+// nodes 16 p .. 16 p + 15 are panel p's Gauss-Legendre points in order.
+constexpr double kExtNear = 3.0;
+__host__ __device__ inline double ext_loc(double t, double tm, double th) {
+  const double twopi = 2.0 * kPi;
+  double d = t - tm;
+  d -= twopi * floor((d + kPi) / twopi);
+  return d / th;
+}
+// Whether some node of panel a takes the singular rule against panel b or
+// some node of b against a (whole panels: a conservative test).
+inline bool ext_panels_interact(double tma, double tha, double tmb, double thb) {
+  const double d = std::fabs(ext_loc(tma, tmb, 1.0));
+  return d - tha < kExtNear * thb || d - thb < kExtNear * tha;
+}
+// Make nd an exterior-wall node set on curve c whose panels are the
+// t-intervals [ta[p], tb[p]] (nd.n = 16 x panels): kind, curve, and the
+// per-node t, tm, th on the host and the device.
+void set_exterior_panels(Nodes& nd, const Curve& c, const std::vector<double>& ta, const std::vector<double>& tb,
+                         cudaStream_t s);
+// For each panel of an exterior node set, the other panels that share a
+// singular-rule pair with it (ext_panels_interact).
+std::vector<std::vector<int>> ext_panel_neighbours(const Nodes& nd);
+
 // Internal curve kind of a hole: x(t) = c + R (1 + a cos(k t)) (cos t, sin t),
 // p = {a, k, R, cx, cy} (counter-clockwise; the normal points into the fluid).
 constexpr int kCurveHole = 100;
@@ -31,7 +54,8 @@ constexpr int kCurveHole = 100;
 // kind 0 ("outgoing", rows of A): Y[i, :] = [A(cand_i, e1) | A(cand_i, e2) |
 //   S(x_i, z_q) e_b, D(x_i, z_q) e_b for proxy points z_q | n_i]
 // kind 1 ("incoming", columns of A): Y[i, :] = [A(e1, cand_i)^T |
-//   A(e2, cand_i)^T | w_i D(z_q, x_i)[a', .] for proxy points | w_i n_i].
+//   A(e2, cand_i)^T | w_i D(z_q, x_i)[a', .] for proxy points | w_i n_i],
+//   with sl_in also w_i S(z_q, x_i)[a', .] after the double layer's columns.
 // Candidates live in node set S; e1 in E1 and e2 in E2.  Proxy points are
 // z_q = c + R (cos 2 pi q / M, sin 2 pi q / M) with outward normal; with
 // ncirc > 1 the proxies are the union of M points on each of the circles
@@ -52,10 +76,12 @@ struct IdMatProb {
   int ncol;
   int ncirc;
   const double* circ;
+  int sl_in;  // kind 1 on exterior-wall candidates: the single layer's field
+              // at the proxy points too (2 more columns per proxy point)
 };
 inline int idmat_nproxy(const IdMatProb& p) { return p.M * (p.ncirc > 1 ? p.ncirc : 1); }
-inline int idmat_ncol(int kind, int n1, int n2, int M, int normal) {
-  return n1 + n2 + (kind == 0 ? 4 * M : 2 * M) + (normal ? 1 : 0);
+inline int idmat_ncol(int kind, int n1, int n2, int M, int normal, int sl_in = 0) {
+  return n1 + n2 + ((kind == 0 || sl_in) ? 4 * M : 2 * M) + (normal ? 1 : 0);
 }
 void eval_idmat(const std::vector<IdMatProb>& probs, const NodesView& S,
                 const NodesView& E1, bool e1_same, const NodesView& E2,

@@ -18,7 +18,7 @@ namespace rw {
 int IdBatch::add(const IdMatProb& spec, int sketch_cols, int sketch_width) {
   Job j;
   j.spec = spec;
-  j.spec.ncol = idmat_ncol(spec.kind, spec.n1, spec.n2, idmat_nproxy(spec), spec.normal);
+  j.spec.ncol = idmat_ncol(spec.kind, spec.n1, spec.n2, idmat_nproxy(spec), spec.normal, spec.sl_in);
   if (j.spec.ncol > sketch_cols && sketch_width < j.spec.ncol) {
     j.sk_width = sketch_width;
     j.nr = sketch_width;
@@ -634,6 +634,12 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s, bool fwd_only
     oDh_prev = oK;
   };
   // ---------------------------------------------------------- compression
+  // Exterior walls: besides the points inside a node's proxy circle, every
+  // point of a panel that shares a singular-rule pair with one of the node's
+  // panels is taken explicitly (its entries are not the smooth kernel's)
+  const bool ext = nodes.kind == kNodesExterior;
+  std::vector<std::vector<int>> ext_nb;
+  if (ext) ext_nb = ext_panel_neighbours(nodes);
   for (int l = L; l >= 1; --l) {
     const int h0 = 1 << l, nn = 1 << l;
     std::vector<int> idx;  // candidate / near index lists, concatenated
@@ -665,6 +671,19 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s, bool fwd_only
         const double dx = hx[j] - geo[t].cx, dy = hy[j] - geo[t].cy;
         if (dx * dx + dy * dy < R2) { idx.push_back(2 * j); idx.push_back(2 * j + 1); cnt += 2; }
       }
+      if (ext) {
+        std::vector<int> extra;
+        for (int p = nd.lo / 16; p <= (nd.hi - 1) / 16; ++p)
+          for (int qn : ext_nb[p])
+            for (int j = 16 * qn; j < 16 * qn + 16; ++j) {
+              if (j >= nd.lo && j < nd.hi) continue;
+              const double dx = hx[j] - geo[t].cx, dy = hy[j] - geo[t].cy;
+              if (dx * dx + dy * dy >= R2) extra.push_back(j);
+            }
+        std::sort(extra.begin(), extra.end());
+        extra.erase(std::unique(extra.begin(), extra.end()), extra.end());
+        for (int j : extra) { idx.push_back(2 * j); idx.push_back(2 * j + 1); cnt += 2; }
+      }
       n_near[t] = cnt;
     }
     DBuf<int> didx = to_device(idx, s);
@@ -685,7 +704,8 @@ void Hbs::build(const Nodes& nodes, const Opts& o, cudaStream_t s, bool fwd_only
         p.cy = geo[t].cy;
         p.R = R;
         p.M = o.n_proxy;
-        p.normal = 1;
+        p.normal = ext ? 0 : 1;            // the exterior operator has no N term
+        p.sl_in = (ext && kind == 1) ? 1 : 0;  // sources carry the combined field
         batch.add(p, o.sketch_cols, m[t] + 16);
       }
     }

@@ -25,6 +25,7 @@
 namespace rw {
 
 void Refinement::factor_holes(const Wall& w, const std::vector<HoleSpec>& hs, cudaStream_t s) {
+  require(w.nodes.kind != kNodesExterior, "holes: the wall must enclose the fluid (an interior wall)");
   wall = &w;
   holes = true;
   streams.main = s;

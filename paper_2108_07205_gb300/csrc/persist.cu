@@ -294,6 +294,8 @@ int rw_hbs_save(rw_hbs_t h, const char* path) {
   if (!h || !path) return rw::abi_fail(RW_ERR_INVALID, "rw_hbs_save: null argument");
   try {
     File f(path, "wb");
+    if (h->wall.nodes.kind == rw::kNodesExterior)
+      throw rw::Error(RW_ERR_INVALID, "rw_hbs_save: exterior walls are not saved (rebuild them)");
     if (!f.f) throw rw::Error(RW_ERR_INVALID, std::string("rw_hbs_save: cannot open ") + path);
     Writer o{f.f};
     save_wall(h->wall, o, nullptr);

@@ -319,6 +319,8 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
   Nn = Nk + Np;
   require(added || w.curve.kind != RW_CURVE_NODES,
           "refine: this wall was built from nodes; the added nodes must be given");
+  const bool ext = w.nodes.kind == kNodesExterior;
+  require(!ext || !added, "refine: an exterior wall's added nodes are evaluated on its curve");
   if (added) {
     // the caller's nodes for the sub-panels (window order)
     require(added->size() == size_t(6) * Np, "refine: added nodes do not match the cut panels and levels");
@@ -333,6 +335,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     auto all = pn.buf.download(s);
     pn.hx.assign(all.begin(), all.begin() + Np);
     pn.hy.assign(all.begin() + Np, all.begin() + 2 * Np);
+    if (ext) set_exterior_panels(pn, w.curve, ta, tb, s);
   }
   // refined order maps
   {
@@ -362,6 +365,16 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     auto sp = to_device_tmp(pts_p_src, s), dsp = to_device_tmp(pts_p_dst, s);
     gather_scatter(w.nodes.buf.p, No, so.p, nn.buf.p, Nn, dso.p, int(pts_o_src.size()), 6, s);
     gather_scatter(pn.buf.p, Np, sp.p, nn.buf.p, Nn, dsp.p, int(pts_p_src.size()), 6, s);
+    if (ext) {
+      // the refined order's panels: kept panels, each cut one by its sub-panels
+      std::vector<double> na, nb;
+      for (int j = 0; j < P; ++j) {
+        int ns = 1;
+        for (size_t i = 0; i < pan.size(); ++i) if (pan[i] == j) ns = 1 << lvl[i];
+        for (int q = 0; q < ns; ++q) { na.push_back(j * h + q * (h / ns)); nb.push_back(j * h + (q + 1) * (h / ns)); }
+      }
+      set_exterior_panels(nn, w.curve, na, nb, s);
+    }
     std::vector<int> dcv;
     for (int i : Ic) { dcv.push_back(2 * i); dcv.push_back(2 * i + 1); }
     dc = to_device(dcv, s);
@@ -397,13 +410,33 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
     circ_div.insert(circ_div.end(), {cx, cy, o.div_ratio * rho});
     circ_bas.insert(circ_bas.end(), {cx, cy, o.bas_ratio * rho});
   }
+  // Exterior walls: a kept panel that shares a singular-rule pair with a cut
+  // panel or an added sub-panel of region r is near r as well (its entries
+  // against them are not the smooth kernel's that the proxies stand for)
+  std::vector<char> ext_near_r;  // P x nreg
+  if (ext) {
+    ext_near_r.assign(size_t(P) * nreg, 0);
+    for (int j = 0; j < P; ++j) {
+      if (cut[j]) continue;
+      const double tmj = w.nodes.htm[16 * j], thj = w.nodes.hth[16 * j];
+      for (int r = 0; r < nreg; ++r) {
+        bool hit = false;
+        for (int i = rstart[r]; i < rstart[r + 1] && !hit; ++i)
+          hit = ext_panels_interact(tmj, thj, w.nodes.htm[16 * pan[i]], w.nodes.hth[16 * pan[i]]);
+        for (int q = poff[r]; q < poff[r + 1] && !hit; q += 16)
+          hit = ext_panels_interact(tmj, thj, pn.htm[q], pn.hth[q]);
+        ext_near_r[size_t(j) * nreg + r] = hit;
+      }
+    }
+  }
   std::vector<int> far_d, near_d;
   std::vector<std::vector<int>> near_r(nreg);
   for (int i : Ik) {
     bool near = false;
     for (int r = 0; r < nreg; ++r) {
       const double dx = w.nodes.hx[i] - circ_div[3 * r], dy = w.nodes.hy[i] - circ_div[3 * r + 1];
-      if (dx * dx + dy * dy < circ_div[3 * r + 2] * circ_div[3 * r + 2]) {
+      if (dx * dx + dy * dy < circ_div[3 * r + 2] * circ_div[3 * r + 2] ||
+          (ext && ext_near_r[size_t(i / 16) * nreg + r])) {
         near = true;
         near_r[r].push_back(2 * i);
         near_r[r].push_back(2 * i + 1);
@@ -463,7 +496,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
       // regions against the union of their P^bas circles (every source lies
       // inside its own region's circle, every far row outside all of them)
       IdMatProb cs{};
-      cs.cx = circ_bas[0]; cs.cy = circ_bas[1]; cs.R = circ_bas[2]; cs.M = o.n_proxy_refine; cs.normal = 1;
+      cs.cx = circ_bas[0]; cs.cy = circ_bas[1]; cs.R = circ_bas[2]; cs.M = o.n_proxy_refine; cs.normal = ext ? 0 : 1;
       if (nreg > 1) { cs.ncirc = nreg; cs.circ = dcirc_bas.p; }
       if (use_tree) {
         std::vector<char> isfar(w.nodes.n, 0);
@@ -493,7 +526,7 @@ void Refinement::factor(const Wall& w, const std::vector<int>& pan, const std::v
         IdMatProb cs{};
         cs.n1 = int(near_r[r].size()); cs.e1 = dnear_r[r].p;
         cs.cx = circ_div[3 * r]; cs.cy = circ_div[3 * r + 1]; cs.R = circ_div[3 * r + 2];
-        cs.M = o.n_proxy_refine; cs.normal = 1;
+        cs.M = o.n_proxy_refine; cs.normal = ext ? 0 : 1;
         tp[r] = tree_row_id(VP, prow, cs, VW, false, VW, false, ftol, o.sketch_cols, o.sketch_width,
                             o.seed + 303 + 7 * r, 128, s3);
         kpk += tp[r].k;
@@ -883,6 +916,20 @@ void Refinement::solve_refined(const double* g, double* tau, int nrhs, int steps
 }
 
 void Refinement::apply_nn(const double* x, double* y, int nrhs, cudaStream_t s) const {
+  if (nn.kind == kNodesExterior) {
+    // exterior wall: blocks of rows of A_nn = 1/2 I + D + S evaluated (with
+    // the singular rule) into a scratch matrix, each applied by a GEMM
+    const int n = 2 * Nn;
+    const int rb = std::max(2, std::min(n, int((size_t(1) << 25) / size_t(n)) & ~1));
+    TBuf<double> T(size_t(rb) * n, s);
+    const NodesView V = nn.view();
+    for (int r0 = 0; r0 < n; r0 += rb) {
+      const int m = std::min(rb, n - r0);
+      eval_blocks({BlockProb{m, n, nullptr, nullptr, r0, 0, 0, 0, 1.0, T.p, m}}, V, V, s);
+      batched_gemm({GemmProb{T.p, x, y + r0, m, nrhs, n, m, n, n, 0, 0, 1.0, 0.0}}, s);
+    }
+    return;
+  }
   if (!holes) {
     apply_exact(nn.view(), x, y, nrhs, s);
     return;

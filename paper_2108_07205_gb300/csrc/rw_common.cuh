@@ -184,69 +184,49 @@ DBuf<T> to_device(const std::vector<T>& h, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- nodes
+// Curve description on the device (RW_CURVE_* and its parameters).
+struct Curve {
+  int kind;
+  double p[8];
+};
+
 // Structure-of-arrays view of a node set on the device: position, outward
 // normal, smooth quadrature weight and signed curvature per point.  kind 0 is
 // a wall (double layer with the N term of Remark 2.1); kind 1 is a hole
-// carrying the combined field D + S of Eq. exterior_BIE (App. B).
+// carrying the combined field D + S of Eq. exterior_BIE (App. B); kind 2 is
+// an exterior wall (Sec. 2.2: 1/2 I + D + S on one closed curve), whose
+// single layer takes a singular rule on the panels next to each target and
+// needs, per node, its parameter t and its panel's midpoint tm and
+// half-width th in t, plus the curve itself.
 struct NodesView {
   const double *x, *y, *nx, *ny, *w, *kappa;
   int n;
   int kind;
+  const double *t, *tm, *th;  // kind 2 only (else null)
+  Curve curve;                // kind 2 only
 };
+
+constexpr int kNodesExterior = 2;  // NodesView::kind of an exterior wall
 
 struct Nodes {
   DBuf<double> buf;   // 6 x n column-major: x, y, nx, ny, w, kappa
+  DBuf<double> pbuf;  // kind 2: 3 x n column-major: t, tm, th
   int n = 0;
   int kind = 0;       // NodesView::kind
-  std::vector<double> hx, hy;  // host copy of positions (planning only)
+  Curve curve{};      // kind 2
+  std::vector<double> hx, hy;       // host copy of positions (planning only)
+  std::vector<double> ht, htm, hth; // kind 2: host copy of t, tm, th
   void alloc(int count) { n = count; buf.alloc(size_t(6) * count); }
   NodesView view() const {
     const double* b = buf.p;
+    const double* q = kind == kNodesExterior ? pbuf.p : nullptr;
     return NodesView{b, b + n, b + 2 * size_t(n), b + 3 * size_t(n),
-                     b + 4 * size_t(n), b + 5 * size_t(n), n, kind};
+                     b + 4 * size_t(n), b + 5 * size_t(n), n, kind,
+                     q, q ? q + n : nullptr, q ? q + 2 * size_t(n) : nullptr, curve};
   }
 };
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
-
-// Entry of A = -1/2 I + D + N (Sec. 2, Remark 2.1) for row DOF (i, a) of node
-// set R and column DOF (j, b) of node set C.  same_set marks R == C, where
-// i == j gives the diagonal block -1/2 I - (kappa_i w_i / 2 pi) t t^T
-// + w_i n_i n_i^T (the smooth limit of the double layer on the curve).
-// With holes (App. B): a hole source (C.kind 1) contributes its combined
-// field w_j (D + S)(x_i, y_j) and a wall source seen at a hole point (R.kind
-// 1) its double layer w_j D(x_i, y_j), neither with the N term.  Pairs on
-// one hole are not evaluated here (their single layer needs the singular
-// rule of the hole matrix).
-__device__ __forceinline__ double a_entry(const NodesView& R, int i, int a,
-                                          const NodesView& C, int j, int b,
-                                          bool same_set) {
-  const double wj = C.w[j];
-  if (C.kind | R.kind) {
-    const double rx = R.x[i] - C.x[j], ry = R.y[i] - C.y[j];
-    const double r2 = rx * rx + ry * ry, inv = 1.0 / r2;
-    const double ra = a ? ry : rx, rb = b ? ry : rx;
-    double val = wj * (rx * C.nx[j] + ry * C.ny[j]) * inv * inv * (1.0 / kPi) * ra * rb;
-    if (C.kind) val += wj * (0.25 / kPi) * ((a == b ? -0.5 * log(r2) : 0.0) + ra * rb * inv);
-    return val;
-  }
-  const double nia = a ? R.ny[i] : R.nx[i];
-  const double njb = b ? C.ny[j] : C.nx[j];
-  double val = nia * njb * wj;
-  if (same_set && i == j) {
-    const double ta = a ? R.nx[i] : -R.ny[i];
-    const double tb = b ? R.nx[i] : -R.ny[i];
-    val -= R.kappa[i] * wj * (0.5 / kPi) * ta * tb;
-    if (a == b) val -= 0.5;
-  } else {
-    const double rx = R.x[i] - C.x[j], ry = R.y[i] - C.y[j];
-    const double r2 = rx * rx + ry * ry;
-    const double rdn = rx * C.nx[j] + ry * C.ny[j];
-    const double fac = wj * rdn / (kPi * r2 * r2);
-    val += fac * (a ? ry : rx) * (b ? ry : rx);
-  }
-  return val;
-}
 
 // ---------------------------------------------------------------- stream
 struct StreamGuard {

@@ -87,7 +87,7 @@ class NodesDesc(ctypes.Structure):
                 ("ny", ctypes.c_void_p), ("w", ctypes.c_void_p), ("kappa", ctypes.c_void_p)]
 
 
-EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_build_nodes", "rw_hbs_save", "rw_hbs_load",
+EXPORTS = ["rw_default_opts", "rw_hbs_build", "rw_hbs_build_exterior", "rw_hbs_build_nodes", "rw_hbs_save", "rw_hbs_load",
            "rw_refine_factor_nodes", "rw_holes_factor",
            "rw_hbs_stats_get", "rw_hbs_nodes", "rw_hbs_apply_inverse",
            "rw_hbs_apply_inverse_noalloc",
@@ -119,6 +119,7 @@ def load(build_if_missing=False):
     vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p
     L.rw_default_opts.argtypes = [ctypes.POINTER(Opts)]
     L.rw_hbs_build.argtypes = [ctypes.POINTER(WallDesc), ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    L.rw_hbs_build_exterior.argtypes = [ctypes.POINTER(WallDesc), ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     L.rw_hbs_stats_get.argtypes = [vp, ctypes.POINTER(HbsStats)]
     L.rw_hbs_nodes.argtypes = [vp, dp, vp]
     L.rw_hbs_apply_inverse.argtypes = [vp, ctypes.c_int, dp, dp, vp]
@@ -250,7 +251,9 @@ def _nodes_desc(nodes):
 class Wall:
     """Reference wall: nodes, HBS forward representation and HBS inverse."""
 
-    def __init__(self, kind, n_panels=0, params=(), opts=None, stream=None, _handle=None):
+    def __init__(self, kind, n_panels=0, params=(), opts=None, stream=None, _handle=None, exterior=False):
+        """Wall on a built-in curve; exterior=True: the exterior problem
+        (rw_hbs_build_exterior: the fluid outside the curve, combined field)."""
         if _handle is not None:
             self.h = _handle
             self.n_panels = self.stats()["n_points"] // 16
@@ -263,7 +266,8 @@ class Wall:
             d.params[i] = float(v)
         o = opts if opts is not None else default_opts()
         h = ctypes.c_void_p()
-        _check(L.rw_hbs_build(ctypes.byref(d), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        build = L.rw_hbs_build_exterior if exterior else L.rw_hbs_build
+        _check(build(ctypes.byref(d), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self.h = h
         self.n_panels = int(n_panels)
 
