@@ -21,8 +21,9 @@ refined order of discretize.refine).
   whose parameter interval, mapped to [-1, 1], puts the target's parameter at
   |loc| < NEAR_LOC (periodic distance), the exact kernel is integrated
   against the panel's degree-15 interpolant of the density by the graded
-  brute-force rule of oracle/holes.py, with the geometry exact.  Every other
-  pair takes the plain rule.  NEAR_LOC = 5 covers two equal panels on either
+  brute-force rule of oracle/holes.py, with the geometry exact.  Its depth
+  on each side stops where the parameter's rounding would merge nodes with
+  the target (_grade_levels).  Every other pair takes the plain rule.  NEAR_LOC = 5 covers two equal panels on either
   side (the holes' choice).  On a refined mesh it also covers every fine panel
   next to a coarse one, and every coarse panel next to a fine one.
 * Velocity at a point of the fluid: the plain panel rule (targets away from
@@ -48,6 +49,8 @@ Parity: pinned by tests/test_oracle_exterior.py.
 * Planted mistakes break the closed form: the interior jump, the plain rule
   on the log singularity, and the single layer's sign.
 """
+from functools import lru_cache
+
 import numpy as np
 
 from .quadrature import NQ
@@ -84,6 +87,44 @@ def nodes(kind, params, a, b):
     return nd
 
 
+def _grade_levels(L, half, tau):
+    """Halvings of the graded rule on a side of length L (panel coordinate)
+    toward the target.  The grading stops where the innermost interval is
+    1e4 rounding units of the parameter long: closer nodes would merge with
+    the target's parameter.  Then e = L 2^-levels stays below 2e-11 / half
+    in the panel coordinate.  The closed-form innermost piece freezes the
+    density there and errs by O(e^2 log e), far below rounding."""
+    if L <= 0.0:
+        return 0   # no interval on this side
+    floor_t = 1e4 * np.spacing(abs(tau) + 2.0 * np.pi)
+    return int(np.clip(np.floor(np.log2(L * half / floor_t)), 8, 60))
+
+
+@lru_cache(maxsize=4096)
+def _graded_rule(sstar, singular, lev_left, lev_right):
+    """Composite Gauss rule on [-1, 1] graded toward sstar, lev_left /
+    lev_right halvings on either side.  Otherwise it is the rule of
+    oracle/holes.py: with a singular kernel, the two innermost intervals are
+    left to the caller's closed form (their lengths returned)."""
+    xi, om = H._gl()
+    pts, wts, ends = [], [], []
+    for side, L, lev in ((-1.0, sstar + 1.0, lev_left), (1.0, 1.0 - sstar, lev_right)):
+        if L <= 0.0:
+            continue
+        edges = [L * 0.5 ** m for m in range(lev + 1)]
+        if not singular:
+            edges.append(0.0)
+        for m in range(len(edges) - 1):
+            a, b = sstar + side * edges[m + 1], sstar + side * edges[m]
+            lo, hi = min(a, b), max(a, b)
+            pts.append(0.5 * (lo + hi) + 0.5 * (hi - lo) * xi)
+            wts.append(0.5 * (hi - lo) * om)
+        if singular:
+            ends.append(edges[-1])
+    s = np.concatenate(pts)
+    return s, np.concatenate(wts), tuple(ends), H._lagrange(xi, H._bary_weights(xi), s)
+
+
 def _near_single_layer(kind, params, nd, i, a, b):
     """Graded-rule integrals for target node i against the 16 nodes of the
     source panel [a, b]: log part Lg (16,) = int log|x_i - y| l_j |y'| dt and
@@ -93,7 +134,8 @@ def _near_single_layer(kind, params, nd, i, a, b):
     loc = (tau - mid) / half
     singular = -1.0 < loc < 1.0
     sstar = float(np.clip(loc, -1.0, 1.0))
-    s, ws, ends, lag = H._graded_rule(sstar, singular, H.GRADE_LEVELS)
+    s, ws, ends, lag = _graded_rule(sstar, singular, _grade_levels(sstar + 1.0, half, tau),
+                                    _grade_levels(1.0 - sstar, half, tau))
     g = evaluate(kind, mid + half * s, **params)
     speed = np.hypot(g["dx"], g["dy"])
     rx = nd["x"][i] - g["x"]
