@@ -44,6 +44,8 @@ __constant__ double c_glx[16], c_glw[16];
 // 16-point Lagrange basis at its nodes (c_lag[f][j])
 constexpr int kAux = 32;
 __constant__ double c_ux[kAux], c_uw[kAux], c_lag[kAux][16];
+// (n + 1/2) P_n(u_f): the Legendre factors of the product weights Lam_f
+__constant__ double c_pn[kAux][kAux];
 
 struct Pt { double x, y, dx, dy, ddx, ddy; };
 
@@ -241,17 +243,13 @@ __device__ __noinline__ void ext_near_sl(double xi, double yi, double loc, const
   double sl = 0.0, sxx = 0.0, sxy = 0.0, syy = 0.0;
   for (int f = 0; f < kAux; ++f) {
     const double u = c_ux[f];
-    double p0 = 1.0, p1 = u, acc = 0.5 * M[0] + 1.5 * u * M[1];
-    for (int n = 1; n < kAux - 1; ++n) {
-      const double p2 = ((2.0 * n + 1.0) * u * p1 - n * p0) / (n + 1.0);
-      p0 = p1;
-      p1 = p2;
-      acc += (n + 1.5) * p2 * M[n + 1];
-    }
+    double acc = 0.0;
+#pragma unroll 8
+    for (int n = 0; n < kAux; ++n) acc += c_pn[f][n] * M[n];
     const Pt g = curve_eval(c, tm + th * u);
     const double gl = sqrt(g.dx * g.dx + g.dy * g.dy) * c_lag[f][q];
     const double rx = xi - g.x, ry = yi - g.y, r2 = rx * rx + ry * ry;
-    const double phi = 0.5 * log(r2) - log(fabs(loc - u));
+    const double phi = 0.5 * log(r2 / ((loc - u) * (loc - u)));
     sl += c_uw[f] * (acc + phi) * gl;
     const double wg = c_uw[f] * gl / r2;
     sxx += wg * rx * rx;
@@ -413,6 +411,40 @@ __global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesVie
     if (P.normal && threadIdx.x == 0) {
       const double n = ia ? S.ny[ip] : S.nx[ip];
       Wc[P.ncol - 1] = P.kind == 0 ? n : n * S.w[ip];
+    }
+  }
+}
+
+// Exterior walls: a thread forms the whole 2 x 2 block of a point pair once
+// (the singular rule's weights are the expensive part) and writes the four
+// entries when the problem's rows and columns come in (2i, 2i + 1) pairs;
+// other entries one by one.
+__global__ void k_blocks_ext(const BlockProb* probs, NodesView s0, NodesView s1) {
+  const BlockProb P = probs[blockIdx.y];
+  const NodesView& R = P.rset ? s1 : s0;
+  const NodesView& C = P.cset ? s1 : s0;
+  const bool same = P.rset == P.cset;
+  for (int c = 2 * blockIdx.x; c < P.mc; c += 2 * gridDim.x) {
+    const int c1 = min(c + 2, P.mc);
+    const int dc0 = P.cols ? P.cols[c] : P.c0 + c;
+    const bool cp = c1 - c == 2 && (dc0 & 1) == 0 && (P.cols ? P.cols[c + 1] : P.c0 + c + 1) == dc0 + 1;
+    for (int r = 2 * threadIdx.x; r < P.mr; r += 2 * blockDim.x) {
+      const int r1 = min(r + 2, P.mr);
+      const int dr0 = P.rows ? P.rows[r] : P.r0 + r;
+      const bool rp = r1 - r == 2 && (dr0 & 1) == 0 && (P.rows ? P.rows[r + 1] : P.r0 + r + 1) == dr0 + 1;
+      if (rp && cp) {
+        const int i = dr0 >> 1, j = dc0 >> 1;
+        const Blk2 B = a_block_ext(R, i, C, j, same && i == j);
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) P.out[(r + a) + size_t(c + b) * P.ld] = P.scale * B.v[a][b];
+      } else {
+        for (int rr = r; rr < r1; ++rr)
+          for (int cc = c; cc < c1; ++cc) {
+            const int dr = P.rows ? P.rows[rr] : P.r0 + rr;
+            const int dc = P.cols ? P.cols[cc] : P.c0 + cc;
+            P.out[rr + size_t(cc) * P.ld] = P.scale * entry_of<true>(R, dr >> 1, dr & 1, C, dc >> 1, dc & 1, same);
+          }
+      }
     }
   }
 }
@@ -869,6 +901,19 @@ void ensure_gl() {
   RW_CUDA(cudaMemcpyToSymbol(c_ux, ux, sizeof(ux)));
   RW_CUDA(cudaMemcpyToSymbol(c_uw, uw, sizeof(uw)));
   RW_CUDA(cudaMemcpyToSymbol(c_lag, lag, sizeof(lag)));
+  double pn[kAux][kAux];
+  for (int f = 0; f < kAux; ++f) {
+    double p0 = 1.0, p1 = ux[f];
+    pn[f][0] = 0.5;
+    pn[f][1] = 1.5 * p1;
+    for (int n = 1; n < kAux - 1; ++n) {
+      const double p2 = ((2.0 * n + 1.0) * ux[f] * p1 - n * p0) / (n + 1.0);
+      p0 = p1;
+      p1 = p2;
+      pn[f][n + 1] = (n + 1.5) * p2;
+    }
+  }
+  RW_CUDA(cudaMemcpyToSymbol(c_pn, pn, sizeof(pn)));
   g_gl_ready = true;
 }
 
@@ -969,7 +1014,7 @@ void eval_blocks(const std::vector<BlockProb>& probs, const NodesView& set0, con
   require(ext == (set1.kind == kNodesExterior), "eval_blocks: exterior and other node sets mixed");
   if (ext) {
     ensure_gl();
-    k_blocks<true><<<grid, 256, 0, s>>>(d.p, set0, set1);
+    k_blocks_ext<<<grid, 256, 0, s>>>(d.p, set0, set1);
   } else {
     k_blocks<false><<<grid, 256, 0, s>>>(d.p, set0, set1);
   }
