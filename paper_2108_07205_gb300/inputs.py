@@ -25,7 +25,8 @@ Workload recipes (the paper's geometries are not available, Sec. 5):
 * exterior star (Sec. 2.2, Fig. demo_figs (b): the fluid outside the star
   wall): 3 Stokeslets inside the curve at radius U[0, 0.4] with angles
   U[0, 2 pi) and strengths N(0, I2); targets in the fluid at radius
-  U[2, 3].
+  U[2, 3].  Outside the channel: 3 Stokeslets inside it at x ~ U[-8, 8],
+  y ~ U[-0.1, 0.1]; targets at x ~ U[-12, 12], |y| ~ U[1.5, 3].
 """
 import numpy as np
 
@@ -115,6 +116,25 @@ def targets_outside_star(seed, n=16, r_lo=2.0, r_hi=3.0):
     r = g.uniform(r_lo, r_hi, size=n)
     th = g.uniform(0.0, 2.0 * np.pi, size=n)
     return r * np.cos(th), r * np.sin(th)
+
+
+def stokeslets_inside_channel(seed, nrhs=1, n=3):
+    """Point forces inside the channel, the exterior problem's data (within
+    the constriction's half-height 0.2): positions (n,), (n,) and strengths
+    (n, 2, nrhs)."""
+    g = rng(seed)
+    sx = g.uniform(-8.0, 8.0, size=n)
+    sy = g.uniform(-0.1, 0.1, size=n)
+    f = g.standard_normal(size=(n, 2, nrhs))
+    return sx, sy, f
+
+
+def targets_outside_channel(seed, n=16):
+    """Targets in the fluid outside the channel, above and below it."""
+    g = rng(seed)
+    tx = g.uniform(-12.0, 12.0, size=n)
+    ty = g.uniform(1.5, 3.0, size=n) * np.where(g.uniform(size=n) < 0.5, -1.0, 1.0)
+    return tx, ty
 
 
 def targets_channel(seed, n=16):

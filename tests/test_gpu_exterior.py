@@ -17,6 +17,8 @@ rounding.  Tolerances (relative 2-norm), from the arithmetic:
   oracle's dense refined matrix <= 1e-10 per right-hand side.
 * Velocity at points of the fluid against the closed-form field of the
   Stokeslets inside the wall: 1e-10.
+* The constricted channel as an exterior wall (128 panels, a refined window):
+  density against the oracle's LU and velocity outside the channel, 1e-10.
 """
 import numpy as np
 import pytest
@@ -149,6 +151,34 @@ def test_exterior_certified_modes(lib, mode, mixed_factor):
         res = np.linalg.norm(g_or[r] - A @ tau[r]) / np.linalg.norm(g_or[r])
         assert res <= 1e-10, (r, res)
     assert rel(tau, np.linalg.solve(A, g_or.T).T) < 1e-10
+    ref.close()
+    w.close()
+
+
+def test_exterior_channel_vs_oracle(lib):
+    # the constricted channel as an exterior wall (128 panels), a refined
+    # window at level 3: density against the oracle's LU, velocity outside
+    # the channel against the closed form
+    panels, levels = [40, 41, 42, 43], [3, 3, 3, 3]
+    w = rwsolve.Wall("channel", 128, exterior=True)
+    ref = w.refine(panels, levels)
+    a, b = X.panels(128, panels, levels)
+    nd = X.nodes("channel", {}, a, b)
+    sx, sy, f = inputs.stokeslets_inside_channel(11, nrhs=2)
+    src = np.ascontiguousarray(np.stack([sx, sy], 1))
+    fd = np.ascontiguousarray(np.transpose(f, (2, 0, 1)))
+    g = np.empty((2, 2 * ref.stats()["n_n"]))
+    ref.stokeslet_data(src, fd, g, nrhs=2)
+    g_or = S.boundary_data(nd, sx, sy, f).T
+    assert np.abs(g - g_or).max() <= 1e-13 * np.abs(g_or).max()
+    tx, ty = inputs.targets_outside_channel(12)
+    tg = np.ascontiguousarray(np.stack([tx, ty], 1))
+    u = np.empty((2, 2 * tx.size))
+    tau = np.empty_like(g)
+    ref.solve(g, tau, nrhs=2, targets=tg, u=u)
+    assert rel(tau, X.solve("channel", {}, nd, g_or.T).T) < 1e-10
+    ue = np.transpose(S.stokeslet_velocity(tx, ty, sx, sy, f), (2, 0, 1)).reshape(2, -1)
+    assert np.abs(u - ue).max() < 1e-10 * np.abs(ue).max()
     ref.close()
     w.close()
 

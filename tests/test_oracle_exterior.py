@@ -5,7 +5,7 @@
   field of the solved density equals the Stokeslet field at points of the
   fluid.  The decay is spectral under panel refinement.  This holds on the
   reference star and on refined stars, where fine panels sit next to coarse
-  ones.
+  ones, and outside the constricted channel.
 * Total force.  The density's total force sum_j w_j tau_j equals the
   Stokeslets' total force.
 * On one equal-panel curve the matrix equals oracle/holes.py's hole matrix,
@@ -47,6 +47,21 @@ def test_closed_form_and_spectral_decay():
 def test_closed_form_refined(cut, levels):
     err = _field_error(24, cut, levels)[0]
     assert err < 1e-11
+
+
+def test_closed_form_outside_the_channel():
+    # the constricted 20 x 1 channel as an exterior wall: 128 panels, and the
+    # same with a refined window
+    from oracle import stokes as S
+    sx, sy, f = I.stokeslets_inside_channel(4, nrhs=2)
+    tx, ty = I.targets_outside_channel(5, n=12)
+    ue = S.stokeslet_velocity(tx, ty, sx, sy, f)
+    for cut, levels in (((), ()), ((10, 11, 12), (3, 3, 3))):
+        a, b = X.panels(128, cut, levels)
+        nd = X.nodes("channel", {}, a, b)
+        tau = X.solve("channel", {}, nd, S.boundary_data(nd, sx, sy, f))
+        u = X.velocity(nd, tau, tx, ty)
+        assert np.abs(u - ue).max() < 1e-10 * np.abs(ue).max()
 
 
 def test_total_force_identity():
