@@ -18,7 +18,9 @@ rounding.  Tolerances (relative 2-norm), from the arithmetic:
 * Velocity at points of the fluid against the closed-form field of the
   Stokeslets inside the wall: 1e-10.
 * The constricted channel as an exterior wall (128 panels, a refined window):
-  density against the oracle's LU and velocity outside the channel, 1e-10.
+  density against the oracle's LU and velocity against the oracle's, 1e-10;
+  velocity against the closed form 1e-9 (the oracle's own discretisation
+  error there is 1.2e-10).
 """
 import numpy as np
 import pytest
@@ -176,9 +178,14 @@ def test_exterior_channel_vs_oracle(lib):
     u = np.empty((2, 2 * tx.size))
     tau = np.empty_like(g)
     ref.solve(g, tau, nrhs=2, targets=tg, u=u)
-    assert rel(tau, X.solve("channel", {}, nd, g_or.T).T) < 1e-10
+    tau_or = X.solve("channel", {}, nd, g_or.T).T
+    assert rel(tau, tau_or) < 1e-10
+    uo = np.transpose(X.velocity(nd, tau_or.T, tx, ty), (2, 0, 1)).reshape(2, -1)
+    assert np.abs(u - uo).max() < 1e-10 * np.abs(uo).max()
+    # 128 panels resolve these sources (0.1 from a wall 0.2 away) to 1.2e-10
+    # in the oracle itself
     ue = np.transpose(S.stokeslet_velocity(tx, ty, sx, sy, f), (2, 0, 1)).reshape(2, -1)
-    assert np.abs(u - ue).max() < 1e-10 * np.abs(ue).max()
+    assert np.abs(u - ue).max() < 1e-9 * np.abs(ue).max()
     ref.close()
     w.close()
 
