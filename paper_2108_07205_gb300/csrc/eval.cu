@@ -415,6 +415,108 @@ __global__ void k_idmat(const IdMatProb* probs, int max_M, NodesView S, NodesVie
   }
 }
 
+// ext_near_sl for all 16 source nodes of one panel at once: the moments, the
+// curve at the auxiliary nodes and the logarithms are shared by the 16, only
+// the Lagrange factor differs.  out[3 q + (0, 1, 2)] = entries xx, xy, yy of
+// w_j S(x_i, y_j) for source node q.
+__device__ __noinline__ void ext_near_sl_panel(double xi, double yi, double loc, const Curve& c, double tm, double th,
+                                               double* out) {
+  double M[kAux];
+  log_moments<kAux>(loc, M);
+  double sl[16], sxx[16], sxy[16], syy[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sl[q] = sxx[q] = sxy[q] = syy[q] = 0.0;
+  for (int f = 0; f < kAux; ++f) {
+    const double u = c_ux[f];
+    double acc = 0.0;
+#pragma unroll 8
+    for (int n = 0; n < kAux; ++n) acc += c_pn[f][n] * M[n];
+    const Pt g = curve_eval(c, tm + th * u);
+    const double sp = sqrt(g.dx * g.dx + g.dy * g.dy);
+    const double rx = xi - g.x, ry = yi - g.y, r2 = rx * rx + ry * ry;
+    const double phi = 0.5 * log(r2 / ((loc - u) * (loc - u)));
+    const double bl = c_uw[f] * (acc + phi) * sp, bt = c_uw[f] * sp / r2;
+    const double txx = bt * rx * rx, txy = bt * rx * ry, tyy = bt * ry * ry;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const double lq = c_lag[f][q];
+      sl[q] += bl * lq;
+      sxx[q] += txx * lq;
+      sxy[q] += txy * lq;
+      syy[q] += tyy * lq;
+    }
+  }
+  const double c4 = 0.25 / kPi;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    out[3 * q] = c4 * th * (sxx[q] - sl[q]);
+    out[3 * q + 1] = c4 * th * sxy[q];
+    out[3 * q + 2] = c4 * th * (syy[q] - sl[q]);
+  }
+}
+
+// Exterior walls, blocks with contiguous rows and columns: one CTA per source
+// panel (16 points = 32 columns), one thread per target point.  A target near
+// the panel forms the singular rule's weights for all 16 source nodes once
+// (ext_near_sl_panel); the double layer and the plain single layer per pair.
+__global__ void k_blocks_ext_panels(const BlockProb* probs, NodesView s0, NodesView s1) {
+  const BlockProb P = probs[blockIdx.y];
+  const NodesView& R = P.rset ? s1 : s0;
+  const NodesView& C = P.cset ? s1 : s0;
+  const bool same = P.rset == P.cset;
+  const int pc0 = P.c0 / 32, pc1 = (P.c0 + P.mc - 1) / 32;   // column panels
+  const int i0 = P.r0 / 2, i1 = (P.r0 + P.mr - 1) / 2;       // target points
+  for (int pc = pc0 + blockIdx.x; pc <= pc1; pc += gridDim.x) {
+    const int j0 = 16 * pc;
+    const double tm = C.tm[j0], th = C.th[j0];
+    for (int i = i0 + threadIdx.x; i <= i1; i += blockDim.x) {
+      const double loc = ext_loc(R.t[i], tm, th);
+      const bool near = fabs(loc) < kExtNear;
+      const bool own = same && (i >> 4) == pc;
+      double w[48];
+      if (near) ext_near_sl_panel(R.x[i], R.y[i], own ? c_glx[i & 15] : loc, C.curve, tm, th, w);
+      for (int q = 0; q < 16; ++q) {
+        const int j = j0 + q;
+        if (2 * j + 1 < P.c0 || 2 * j >= P.c0 + P.mc) continue;
+        const double ws = C.w[j];
+        const double rx = R.x[i] - C.x[j], ry = R.y[i] - C.y[j];
+        const double r[2] = {rx, ry};
+        double b[2][2];
+        if (same && i == j) {
+          const double ta[2] = {-R.ny[i], R.nx[i]};
+          const double kap = -R.kappa[i] * ws * (0.5 / kPi);
+          for (int a = 0; a < 2; ++a)
+            for (int e = 0; e < 2; ++e) b[a][e] = kap * ta[a] * ta[e] + (a == e ? 0.5 : 0.0);
+        } else {
+          const double inv = 1.0 / (rx * rx + ry * ry);
+          const double fac = ws * (rx * C.nx[j] + ry * C.ny[j]) * inv * inv * (1.0 / kPi);
+          for (int a = 0; a < 2; ++a)
+            for (int e = 0; e < 2; ++e) b[a][e] = fac * r[a] * r[e];
+        }
+        if (near) {
+          b[0][0] += w[3 * q];
+          b[0][1] += w[3 * q + 1];
+          b[1][0] += w[3 * q + 1];
+          b[1][1] += w[3 * q + 2];
+        } else {
+          const double r2 = rx * rx + ry * ry, inv = 1.0 / r2, lg = -0.5 * log(r2), cc = ws * (0.25 / kPi);
+          for (int a = 0; a < 2; ++a)
+            for (int e = 0; e < 2; ++e) b[a][e] += cc * ((a == e ? lg : 0.0) + r[a] * r[e] * inv);
+        }
+        for (int a = 0; a < 2; ++a) {
+          const int row = 2 * i + a - P.r0;
+          if (row < 0 || row >= P.mr) continue;
+          for (int e = 0; e < 2; ++e) {
+            const int col = 2 * j + e - P.c0;
+            if (col < 0 || col >= P.mc) continue;
+            P.out[row + size_t(col) * P.ld] = P.scale * b[a][e];
+          }
+        }
+      }
+    }
+  }
+}
+
 // Exterior walls: a thread forms the whole 2 x 2 block of a point pair once
 // (the singular rule's weights are the expensive part) and writes the four
 // entries when the problem's rows and columns come in (2i, 2i + 1) pairs;
@@ -1014,7 +1116,30 @@ void eval_blocks(const std::vector<BlockProb>& probs, const NodesView& set0, con
   require(ext == (set1.kind == kNodesExterior), "eval_blocks: exterior and other node sets mixed");
   if (ext) {
     ensure_gl();
-    k_blocks_ext<<<grid, 256, 0, s>>>(d.p, set0, set1);
+    // contiguous problems by source panel, the rest entry pair by entry pair
+    std::vector<BlockProb> pan, gen;
+    long long npan = 0, mg = 0;
+    for (auto& p : ps) {
+      if (!p.rows && !p.cols) {
+        pan.push_back(p);
+        npan = std::max<long long>(npan, (p.c0 + p.mc - 1) / 32 - p.c0 / 32 + 1);
+      } else {
+        gen.push_back(p);
+        mg = std::max(mg, (long long)p.mr * p.mc);
+      }
+    }
+    if (!pan.empty()) {
+      auto dp = to_device_tmp(pan, s);
+      k_blocks_ext_panels<<<dim3(int(std::min<long long>(npan, 4096)), int(pan.size())), 128, 0, s>>>(dp.p, set0,
+                                                                                                       set1);
+      RW_CHECK_LAUNCH();
+    }
+    if (!gen.empty()) {
+      auto dg = to_device_tmp(gen, s);
+      k_blocks_ext<<<dim3(std::min(grid1(mg), 1024), int(gen.size())), 256, 0, s>>>(dg.p, set0, set1);
+      RW_CHECK_LAUNCH();
+    }
+    return;
   } else {
     k_blocks<false><<<grid, 256, 0, s>>>(d.p, set0, set1);
   }
