@@ -48,6 +48,10 @@ Parity: pinned by tests/test_oracle_exterior.py.
 * The refined node order against discretize.refine.
 * Planted mistakes break the closed form: the interior jump, the plain rule
   on the log singularity, and the single layer's sign.
+* The extended linear system (Sec. 3.2) built from the exterior operator
+  reproduces the refined exterior solve, and the Woodbury formula with exact
+  and truncated-SVD factors of Q does too (the Remark closing Sec. 3.1: the
+  method applies to exterior problems unchanged).
 """
 from functools import lru_cache
 
@@ -228,3 +232,39 @@ def total_force(nd, tau):
     tau = np.asarray(tau, dtype=np.float64)
     w = nd["w"] if tau.ndim == 1 else nd["w"][:, None]
     return np.stack([(w * tau[0::2]).sum(0), (w * tau[1::2]).sum(0)])
+
+
+def extended_system(kind, params, n_panels, cut, levels):
+    """The extended linear system of Sec. 3.2 for an exterior wall: A_ext =
+    A~ + Q in the ordering [o ; p] (original points in panel order, then the
+    added points in window order), A~ = blkdiag(A_oo, A_pp) and the three
+    nonzero blocks of Q (-A_kc, A_kp, A_pk), every block from this module's
+    exterior operator on the panels it involves.  Returns the dict of
+    dense.extended_system (A_ext, At, Q, dk, dc, dp, No, Np) together with the
+    refinement's bookkeeping from discretize.refine (for dense.g_ext and
+    dense.ext_to_n)."""
+    from .discretize import refine, dof
+    ref = refine(kind, params, n_panels, list(cut), list(levels))
+    ao, bo = panels(n_panels)
+    h = 2.0 * np.pi / n_panels
+    ap, bp = [], []
+    for j, L in zip(cut, levels):
+        ns = 2 ** int(L)
+        for q in range(ns):
+            ap.append(j * h + q * (h / ns))
+            bp.append(j * h + (q + 1) * (h / ns))
+    a = np.concatenate([ao, np.asarray(ap)])
+    b = np.concatenate([bo, np.asarray(bp)])
+    allpts = nodes(kind, params, a, b)
+    No, Np = ao.size * NQ, len(ap) * NQ
+    Abig = matrix(kind, params, allpts)
+    dk, dc = dof(ref["I_k"]), dof(ref["I_c"])
+    dp = 2 * No + np.arange(2 * Np)
+    Aext = Abig.copy()
+    Aext[np.ix_(dk, dc)] = 0.0
+    Aext[np.ix_(dc, dp)] = 0.0
+    Aext[np.ix_(dp, dc)] = 0.0
+    At = np.zeros_like(Abig)
+    At[:2 * No, :2 * No] = Abig[:2 * No, :2 * No]
+    At[2 * No:, 2 * No:] = Abig[2 * No:, 2 * No:]
+    return dict(A_ext=Aext, At=At, Q=Aext - At, dk=dk, dc=dc, dp=dp, No=No, Np=Np, ref=ref, nodes=allpts)
