@@ -174,6 +174,7 @@ int build_curve_wall(const rw_wall_desc* wd, const rw_opts* opts, void* stream, 
     rw::Wall& w = h->wall;
     w.opts = to_opts(opts);
     rw::require(wd->n_panels >= 1 && wd->n_panels <= (1 << 20), "wall.n_panels must be in 1..2^20");
+    rw::require(!exterior || wd->n_panels >= 8, "exterior wall: at least 8 panels");
     w.n_panels = wd->n_panels;
     w.curve.kind = wd->curve_kind;
     for (int i = 0; i < 8; ++i) w.curve.p[i] = wd->params[i];
@@ -199,10 +200,7 @@ int build_curve_wall(const rw_wall_desc* wd, const rw_opts* opts, void* stream, 
     auto all = w.nodes.buf.download(s);
     w.nodes.hx.assign(all.begin(), all.begin() + 16 * P);
     w.nodes.hy.assign(all.begin() + 16 * P, all.begin() + 32 * P);
-    if (exterior) {
-      rw::require(P >= 8, "exterior wall: at least 8 panels");
-      rw::set_exterior_panels(w.nodes, w.curve, ta, tb, s);
-    }
+    if (exterior) rw::set_exterior_panels(w.nodes, w.curve, ta, tb, s);
     w.build_hbs(s);
   });
   if (rc == RW_OK) *out = h.release();

@@ -72,6 +72,21 @@ def test_default_opts_and_validation_without_gpu():
         rwsolve._ptr(np.zeros(3, dtype=np.float32))
 
 
+def test_exterior_build_validation_without_gpu():
+    L = rwsolve.load(build_if_missing=True)
+    h = ctypes.c_void_p()
+    assert L.rw_hbs_build_exterior(None, None, None, ctypes.byref(h)) == -1
+    d = rwsolve.WallDesc()
+    d.curve_kind = rwsolve.CURVE_STAR
+    d.n_panels = 4
+    assert L.rw_hbs_build_exterior(ctypes.byref(d), None, None, ctypes.byref(h)) == -1
+    assert b"at least 8 panels" in L.rw_last_error()
+    d.curve_kind = 7
+    d.n_panels = 64
+    assert L.rw_hbs_build_exterior(ctypes.byref(d), None, None, ctypes.byref(h)) == -1
+    assert b"unknown curve kind" in L.rw_last_error()
+
+
 def test_nodes_and_checkpoint_validation_without_gpu(tmp_path):
     L = rwsolve.load(build_if_missing=True)
     h = ctypes.c_void_p()
