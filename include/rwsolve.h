@@ -166,7 +166,7 @@ int rw_hbs_build(const rw_wall_desc* wall, const rw_opts* opts, void* stream,
  * single layer's logarithm takes Legendre product integration (the
  * generalised Gaussian corrections of Sec. 5, exact for the density's
  * degree-15 interpolant on a panel, geometry exact) wherever a target lies
- * within 3 half-widths (in t) of the source panel's midpoint; the plain
+ * within 2 half-widths (in t) of the source panel's midpoint; the plain
  * panel rule elsewhere.  Every later call takes the handle as for an
  * interior wall (Sec. 3 applies to exterior problems unchanged: the Remark
  * closing Sec. 3.1): rw_refine_factor (nodes of the sub-panels evaluated on

@@ -21,10 +21,12 @@ void eval_nodes(const Curve& c, const double* ta, const double* tb, int n_int,
 // Exterior walls (node sets of kind kNodesExterior; Sec. 2.2).  A target at
 // parameter t takes the singular rule of the single layer against a source
 // panel with midpoint tm and half-width th (in t) when the periodic distance
-// |t - tm| is below kExtNear th; the plain panel rule is then accurate to
-// (3 + sqrt 8)^-32 relative.  Node sets of this kind are panel aligned: the
+// |t - tm| is below kExtNear th.  Beyond that, the plain 16-point rule errs by
+// about (2 + sqrt 3)^-32 ~ 5e-19 relative: the logarithm's singularity lies
+// outside the Bernstein ellipse of parameter 2 + sqrt 3.  Node sets of this
+// kind are panel aligned: the
 // nodes 16 p .. 16 p + 15 are panel p's Gauss-Legendre points in order.
-constexpr double kExtNear = 3.0;
+constexpr double kExtNear = 2.0;
 __host__ __device__ inline double ext_loc(double t, double tm, double th) {
   const double twopi = 2.0 * kPi;
   double d = t - tm;
