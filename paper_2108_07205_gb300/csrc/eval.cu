@@ -1109,41 +1109,41 @@ void eval_blocks(const std::vector<BlockProb>& probs, const NodesView& set0, con
   long long mx = 0;
   for (auto& p : probs) if (p.mr > 0 && p.mc > 0) { ps.push_back(p); mx = std::max(mx, (long long)p.mr * p.mc); }
   if (ps.empty()) return;
-  auto d = to_device_tmp(ps, s);
-  dim3 grid(std::min(grid1(mx), 1024), int(ps.size()));
-  ProfScope prof_(KC_EVAL, s);
   const bool ext = set0.kind == kNodesExterior;
   require(ext == (set1.kind == kNodesExterior), "eval_blocks: exterior and other node sets mixed");
-  if (ext) {
-    ensure_gl();
-    // contiguous problems by source panel, the rest entry pair by entry pair
-    std::vector<BlockProb> pan, gen;
-    long long npan = 0, mg = 0;
-    for (auto& p : ps) {
-      if (!p.rows && !p.cols) {
-        pan.push_back(p);
-        npan = std::max<long long>(npan, (p.c0 + p.mc - 1) / 32 - p.c0 / 32 + 1);
-      } else {
-        gen.push_back(p);
-        mg = std::max(mg, (long long)p.mr * p.mc);
-      }
-    }
-    if (!pan.empty()) {
-      auto dp = to_device_tmp(pan, s);
-      k_blocks_ext_panels<<<dim3(int(std::min<long long>(npan, 4096)), int(pan.size())), 128, 0, s>>>(dp.p, set0,
-                                                                                                       set1);
-      RW_CHECK_LAUNCH();
-    }
-    if (!gen.empty()) {
-      auto dg = to_device_tmp(gen, s);
-      k_blocks_ext<<<dim3(std::min(grid1(mg), 1024), int(gen.size())), 256, 0, s>>>(dg.p, set0, set1);
-      RW_CHECK_LAUNCH();
-    }
+  if (!ext) {
+    auto d = to_device_tmp(ps, s);
+    ProfScope prof_(KC_EVAL, s);
+    k_blocks<false><<<dim3(std::min(grid1(mx), 1024), int(ps.size())), 256, 0, s>>>(d.p, set0, set1);
+    RW_CHECK_LAUNCH();
     return;
-  } else {
-    k_blocks<false><<<grid, 256, 0, s>>>(d.p, set0, set1);
   }
-  RW_CHECK_LAUNCH();
+  ensure_gl();
+  // exterior walls: contiguous problems by source panel, the rest entry pair
+  // by entry pair
+  std::vector<BlockProb> pan, gen;
+  long long npan = 0, mg = 0;
+  for (auto& p : ps) {
+    if (!p.rows && !p.cols) {
+      pan.push_back(p);
+      npan = std::max<long long>(npan, (p.c0 + p.mc - 1) / 32 - p.c0 / 32 + 1);
+    } else {
+      gen.push_back(p);
+      mg = std::max(mg, (long long)p.mr * p.mc);
+    }
+  }
+  TBuf<BlockProb> dp, dg;
+  if (!pan.empty()) dp = to_device_tmp(pan, s);
+  if (!gen.empty()) dg = to_device_tmp(gen, s);
+  ProfScope prof_(KC_EVAL, s);
+  if (!pan.empty()) {
+    k_blocks_ext_panels<<<dim3(int(std::min<long long>(npan, 4096)), int(pan.size())), 128, 0, s>>>(dp.p, set0, set1);
+    RW_CHECK_LAUNCH();
+  }
+  if (!gen.empty()) {
+    k_blocks_ext<<<dim3(std::min(grid1(mg), 1024), int(gen.size())), 256, 0, s>>>(dg.p, set0, set1);
+    RW_CHECK_LAUNCH();
+  }
 }
 
 void batched_transpose(const std::vector<TransProb>& probs, cudaStream_t s) {
